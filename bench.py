@@ -1,0 +1,335 @@
+"""Benchmark of the M2L translation path on GB300.
+
+Workload (one "step"): the FMM downward-sweep M2L of a uniform quadtree to
+level 8 built from 2^22 points U[0,1)^2 with strengths U[-1,1], p = 16, FP32,
+every interaction-list translation of levels 2..8 (2,316,900 translations),
+one fmm_m2l launch per level, reduction fused (Sec. 4.1).  Inputs (radius-
+scaled MEs) are built on the device by fmm_p2m / fmm_m2m before timing.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  `value` is whole-job translations/s with inputs resident
+in HBM; `e2e` is the same metric with a pinned-host -> device copy of the
+step's MEs and a device -> host copy of its LEs inside the timed region.
+Under torchrun each rank runs an independent replica of the workload (the
+single-tree M2L step has no cross-GPU exchange in this build: replicas only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+from paper_1009_3457_gb300 import metrics  # noqa: E402
+
+WORKLOAD = "m2l_scale"
+CFG = workloads.CONFIGS[WORKLOAD]
+P = CFG["p"]
+MAXL = CFG["max_level"]
+LEVELS = workloads.m2l_levels(MAXL)
+NTR = sum(metrics.uniform_translations(l) for l in LEVELS)
+METRIC = "M2L translations/s"
+UNIT = "translations/s"
+CONFIG = {
+    "workload": "plain M2L at scale: 2^22 points U[0,1)^2, strengths U[-1,1], uniform quadtree to level 8, "
+                "p=16, FP32 complex coefficients, all interaction-list translations of levels 2-8, "
+                "one launch per level",
+    "points": CFG["n"], "max_level": MAXL, "p": P, "translations_per_step": NTR,
+    "levels": f"{LEVELS[0]}-{LEVELS[-1]}", "l2": "flushed between timed steps (256 MiB write)",
+    "parallelism": "replicas",
+}
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def cpu_baseline_run(levels=None):
+    """The FP64 oracle as it stands (single thread) on the whole workload: translations/s."""
+    import oracle
+
+    levels = levels or LEVELS
+    xy, c = workloads.uniform_particles(CFG["n"], workloads.rng_for(WORKLOAD))
+    Ms = oracle.upward_uniform(MAXL, P, xy, c)
+    t0 = time.perf_counter()
+    ntr = 0
+    for l in levels:
+        oracle.m2l_uniform(l, P, Ms[l])
+        ntr += metrics.uniform_translations(l)
+    dt = time.perf_counter() - t0
+    return ntr / dt, dt, ntr
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+
+    xy, c = workloads.uniform_particles(CFG["n"], workloads.rng_for(WORKLOAD))
+    Ms = oracle.upward_uniform(MAXL, P, xy, c)
+    # one step = a bounded sample of the workload: every translation of levels 2..6 (137,196 translations)
+    sample_levels = [l for l in LEVELS if l <= 6]
+    ntr_step = sum(metrics.uniform_translations(l) for l in sample_levels)
+    for _ in range(args.warmup):
+        for l in sample_levels:
+            oracle.m2l_uniform(l, P, Ms[l])
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        for l in sample_levels:
+            oracle.m2l_uniform(l, P, Ms[l])
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = ntr_step * args.steps / tot
+    sample = f"levels {sample_levels[0]}-{sample_levels[-1]} of the workload ({ntr_step} translations) per step"
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": CONFIG,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    from paper_1009_3457_gb300 import fmmgb
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    fmmgb.load()
+    fmmgb.fmm_prepare(P)
+    stream = torch.cuda.current_stream()
+
+    # --- inputs: particles -> device P2M/M2M (untimed) ---
+    xy, c = workloads.uniform_particles(CFG["n"], workloads.rng_for(WORKLOAD))
+    xyd = torch.from_numpy(xy).to(dev)
+    cd = torch.from_numpy(c).to(dev)
+    tree = fmmgb.fmm_build_lists(None, MAXL)
+    M = {l: torch.empty((4 ** l, P), dtype=torch.complex64, device=dev) for l in LEVELS}
+    Lx = {l: torch.empty((4 ** l, P), dtype=torch.complex64, device=dev) for l in LEVELS}
+    fmmgb.fmm_p2m(MAXL, P, xyd, cd, M[MAXL])
+    for l in range(MAXL, LEVELS[0], -1):
+        fmmgb.fmm_m2m(l, P, M[l], M[l - 1])
+    torch.cuda.synchronize()
+    del xyd, cd
+
+    order = sorted(LEVELS, reverse=True)  # biggest launch first: the host enqueues the rest meanwhile
+
+    def step(ev=None):
+        for l in order:
+            if ev is not None and l == MAXL:
+                ev[0].record(stream)
+            fmmgb.fmm_m2l(tree, l, P, M[l], Lx[l], stream=stream)
+            if ev is not None and l == MAXL:
+                ev[1].record(stream)
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(max(3, args.warmup)):
+        step()
+        flush.zero_()
+    torch.cuda.synchronize()
+    fmmgb.fmm_sync_status()
+    if args.mode == "kernels":
+        # profiling case: the step's launches only (no e2e copies, no CPU baseline)
+        for _ in range(args.steps):
+            step()
+        torch.cuda.synchronize()
+        fmmgb.fmm_sync_status()
+        if rank == 0:
+            print(json.dumps({"mode": "kernels", "steps": args.steps, "launches_per_step": len(LEVELS)}))
+        return 0
+
+    # --- timed region: device-resident inputs ---
+    clk = ClockSampler(local)
+    if rank == 0:
+        clk.start()
+        time.sleep(0.3)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    kevs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for i in range(args.steps):
+        evs[i][0].record(stream)
+        step(kevs[i])
+        evs[i][1].record(stream)
+        flush.zero_()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    k_ms = [a.elapsed_time(b) for a, b in kevs]
+    tot_ms = sum(step_ms)
+    if ws > 1:
+        t = torch.tensor([tot_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    value = ws * NTR * args.steps / (tot_ms * 1e-3)
+
+    # --- e2e: host buffers through the same public calls ---
+    Mh = {l: torch.empty_like(M[l], device="cpu").pin_memory() for l in LEVELS}
+    Lh = {l: torch.empty_like(Lx[l], device="cpu").pin_memory() for l in LEVELS}
+    for l in LEVELS:
+        Mh[l].copy_(M[l])
+    h2d = sum(M[l].numel() * 8 for l in LEVELS)
+    d2h = sum(Lx[l].numel() * 8 for l in LEVELS)
+
+    def e2e_step():
+        for l in order:
+            M[l].copy_(Mh[l], non_blocking=True)
+        step()
+        for l in LEVELS:
+            Lh[l].copy_(Lx[l], non_blocking=True)
+
+    for _ in range(3):
+        e2e_step()
+        flush.zero_()
+    torch.cuda.synchronize()
+    eevs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for i in range(args.steps):
+        eevs[i][0].record(stream)
+        e2e_step()
+        eevs[i][1].record(stream)
+        flush.zero_()
+    torch.cuda.synchronize()
+    clocks = clk.stop() if rank == 0 else None
+    fmmgb.fmm_sync_status()
+    e2e_ms = sum(a.elapsed_time(b) for a, b in eevs)
+    if ws > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = ws * NTR * args.steps / (e2e_ms * 1e-3)
+
+    if rank == 0:
+        ntr8 = metrics.uniform_translations(MAXL)
+        flops8 = ntr8 * metrics.m2l_flops_per_translation(P)
+        k_avg_s = statistics.mean(k_ms) * 1e-3
+        achieved = flops8 / k_avg_s / 1e12
+        peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": CONFIG,
+            "paper_gops": value * metrics.paper_ops_per_translation(P) / 1e9,
+            "executed_gflops": value * metrics.m2l_flops_per_translation(P) / 1e9,
+            "roofline": {
+                "bound": "alu", "kernel": "m2l_fp32_uniform_kernel<16> (level 8)", "achieved": achieved,
+                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (max SM clock)",
+                "flops_per_launch": flops8, "launch_ms": statistics.mean(k_ms),
+                "frac_at_sampled_clock": (achieved / (peak * clocks["sm_mhz"] / SM_MAX_MHZ))
+                if clocks and clocks.get("sm_mhz") else None,
+            },
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": len(LEVELS) * args.steps,
+            "clocks": clocks,
+        }
+        if not args.no_cpu_baseline and ws == 1:
+            v, dt, ntr = cpu_baseline_run()
+            out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                   "sample": f"the whole step ({ntr} translations, levels 2-8) once, "
+                                             f"{dt:.1f} s, single thread FP64"}
+        print(json.dumps(out))
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", default="full", choices=["full", "kernels"],
+                    help="kernels: only the timed step's launches (for ncu captures)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,195 @@
+/*
+ * fmmgb.h -- C ABI of libfmmgb, the GB300 (sm_103a) M2L / FGT translation engine.
+ *
+ * The operations follow Cruz, Layton & Barba, "How to obtain efficient GPU
+ * kernels: an illustration using FMM & FGT algorithms" (arXiv:1009.3457):
+ *   - the downward sweep of the FMM: build interaction lists, translate every
+ *     multipole expansion (ME) of a list into a local expansion (LE) about the
+ *     target centre, and reduce (sum) them into the target's LE (Sec. 4.1,
+ *     steps 1-3), with the M2L matrix of Eq. (M2Lmat);
+ *   - the Hermite-to-Taylor translation of the fast Gauss transform
+ *     (Sec. 2.2, Eq. C_beta).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *   Kernel.  2-D Cauchy kernel 1/(z - y) on the complex plane: ME
+ *     phi(z) = sum_{k<p} m_k (z - x_s)^-(k+1),  LE  phi(z) = sum_{n<p} l_n (z - x_t)^n,
+ *     and M2L  l_n = sum_k (-1)^n C(n+k,k) (x_t - x_s)^-(n+k+1) m_k  (Eq. M2Lmat,
+ *     x_t = target centre = the paper's x_i, x_s = source centre = x_j).
+ *   Boxes.  Level l of the quadtree on [0,1)^2 has 2^l x 2^l boxes of side
+ *     r_l = 2^-l; box (ix, iy) has index b = iy * 2^l + ix and centre
+ *     ((ix + 1/2) r_l, (iy + 1/2) r_l).
+ *   Coefficient units.  Coefficients cross this boundary radius-scaled:
+ *     M~[b][k] = m_{b,k} / r_l^k,   L~[b][n] = l_{b,n} * r_l^(n+1).
+ *     Scaled values stay O(1) at every depth, while physical FP32 values
+ *     overflow (l_n ~ r^-(n+1)) below about level 7 at p = 16.  In these units
+ *     the M2L operator depends only on the integer box offset.
+ *   Layout.  An expansion array is [nbox][p] complex64 (interleaved re, im,
+ *     8 bytes per coefficient, box-major), 16-byte aligned, on the device.
+ *   Memory.  The caller owns every coefficient buffer.  The library owns the
+ *     tree handle and its per-device operator tables (built by a GPU FP64
+ *     kernel on first use of an order p on a device: call fmm_prepare() before
+ *     stream capture to keep allocation out of the captured region).
+ *   Streams.  `stream` is a cudaStream_t (NULL = legacy default stream).
+ *     Calls enqueue work and return without synchronising.
+ *   Errors.  Every call returns an fmm_status; FMM_OK is 0.  Arguments are
+ *     checked on the host before any launch, and a failed check launches
+ *     nothing.  fmm_last_error() returns a message for the calling thread's
+ *     last failure.  Kernels never trap: a device-side check that fails sets a
+ *     device error word that fmm_sync_status() reports.
+ */
+#ifndef FMMGB_H
+#define FMMGB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FMM_OK = 0,
+    FMM_EINVAL = -1,        /* bad argument (null pointer, size, level, order) */
+    FMM_ENOMEM = -2,        /* device or host allocation failed */
+    FMM_ECUDA = -3,         /* a CUDA runtime call failed */
+    FMM_ETIMEOUT = -4,      /* a bounded device-side wait gave up */
+    FMM_EUNSUPPORTED = -5,  /* valid request this build does not implement */
+    FMM_EDEVICE = -6        /* a device-side check failed (see fmm_last_error) */
+} fmm_status;
+
+typedef enum {
+    FMM_FP32 = 0,           /* FP32 FFMA path (Hankel-structured stencil kernel) */
+    FMM_TC_BF16X3 = 1,      /* tcgen05 tensor cores, BF16 hi/lo split, 3 products, FP32 accumulate */
+    FMM_TC_BF16 = 2         /* tcgen05 tensor cores, plain BF16 inputs, FP32 accumulate */
+} fmm_prec;
+
+/* flags for fmm_m2l / fmm_m2l_adjoint / fgt_h2t */
+#define FMM_ACCUMULATE 1    /* add into the output instead of overwriting it */
+#define FMM_CONJ 2          /* adjoint only: conjugate transpose instead of plain transpose */
+
+/* flags for fmm_build_lists */
+#define FMM_TREE_PERIODIC 1 /* wrap parent neighbours modulo 2^(l-1): every box has 27 entries */
+
+/* Largest quadtree level accepted by fmm_build_lists. */
+#define FMM_MAX_LEVEL 14
+
+typedef struct fmm_tree fmm_tree; /* opaque, library-owned */
+
+/* ---------------------------------------------------------------------------
+ * fmm_build_lists -- quadtree decomposition and interaction lists
+ * (Sec. 2.1 "Initialization"; Sec. 4.1 step 1).
+ *
+ * Interaction list of a box t at level l >= 2: the children of the parent's
+ * neighbours (Chebyshev distance <= 1 at level l-1) that are not adjacent to
+ * t (Chebyshev distance >= 2 at level l).  Levels 0 and 1 have none.  Each
+ * entry carries an offset code  (dy + 3) * 7 + (dx + 3)  of the box offset
+ * (dx, dy) = source - target, one of 40 values.
+ *
+ *   xy        host, n interleaved (x, y) points in [0,1)^2; may be NULL when
+ *             leaf_cap == 0 (a uniform tree does not depend on the points).
+ *   n         number of points (>= 0).
+ *   max_level deepest level, 2 .. FMM_MAX_LEVEL.
+ *   leaf_cap  0: uniform tree with every level down to max_level.
+ *             > 0: adaptive trees are not provided by this build
+ *             (FMM_EUNSUPPORTED).
+ *   flags     FMM_TREE_PERIODIC or 0.
+ *   out       receives the handle; release it with fmm_tree_destroy().
+ * Host-side and synchronous.  Lists are materialised on demand by
+ * fmm_tree_level_info().  Returns FMM_EINVAL on a bad argument.
+ * ------------------------------------------------------------------------- */
+int fmm_build_lists(const double* xy, int64_t n, int32_t max_level, int32_t leaf_cap,
+                    int32_t flags, fmm_tree** out);
+
+typedef struct {
+    int64_t nbox;              /* 4^level */
+    int32_t side;              /* 2^level */
+    int32_t list_stride;       /* 27 */
+    int64_t ntranslations;     /* number of valid list entries at this level */
+    const int32_t* list_host;  /* [nbox][27] source box index, -1 = empty slot */
+    const int8_t* offcode_host;/* [nbox][27] offset code 0..48, -1 = empty slot */
+    const int32_t* list_dev;   /* device copies of the two arrays above */
+    const int8_t* offcode_dev;
+} fmm_level_info;
+
+/* Materialise (once) and return the interaction lists of one level.
+ * Pointers stay valid until fmm_tree_destroy().  Allocates host and device
+ * memory on first call for a level (synchronous).  On a machine without a
+ * CUDA device the host arrays are still built and the device pointers are
+ * NULL. */
+int fmm_tree_level_info(const fmm_tree* tree, int32_t level, fmm_level_info* out);
+
+/* Number of interaction-list entries at a level (closed form, no allocation). */
+int64_t fmm_tree_translations(const fmm_tree* tree, int32_t level);
+
+void fmm_tree_destroy(fmm_tree* tree);
+
+/* Build the operator tables for order p on the current device (FP64 GPU
+ * kernel, then FP32/BF16 copies).  Optional: fmm_m2l does it on first use.
+ * Synchronous. */
+int fmm_prepare(int32_t p, int32_t prec);
+
+/* ---------------------------------------------------------------------------
+ * fmm_m2l -- M2L translation of every interaction-list entry of one level,
+ * fused with the reduction into each target's LE (Sec. 4.1 steps 2-3,
+ * Eq. M2Lmat):
+ *     L~_t[n] (+)= sum_{s in IL(t)} sum_{k<p} (-1)^n C(n+k,k) D^-(n+k+1) M~_s[k],
+ *     D = (x_t - x_s) / r_l  (a complex integer: minus the box offset).
+ *
+ *   tree   handle from fmm_build_lists (uniform tree).
+ *   level  0 .. max_level; levels 0 and 1 have empty lists (the output is
+ *          zeroed, or left unchanged with FMM_ACCUMULATE).
+ *   p      number of terms: 6, 8, 12, 16 or 24.
+ *   prec   FMM_FP32, FMM_TC_BF16X3 or FMM_TC_BF16 (tensor-core forms: p = 16
+ *          or 24 only).
+ *   M      device, const, [4^level][p] complex64 scaled MEs (input).
+ *   L      device, [4^level][p] complex64 scaled LEs (output; must not
+ *          overlap M).
+ *   flags  FMM_ACCUMULATE or 0.
+ * ------------------------------------------------------------------------- */
+int fmm_m2l(const fmm_tree* tree, int32_t level, int32_t p, int32_t prec,
+            const void* M, void* L, int32_t flags, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * fmm_m2l_adjoint -- transpose of fmm_m2l on the same lists:
+ *     G~_s[k] (+)= sum_{t : s in IL(t)} sum_n a_nk W~_t[n]       (plain transpose)
+ *     G~_s[k] (+)= sum_{t : s in IL(t)} sum_n conj(a_nk) W~_t[n] (flags & FMM_CONJ)
+ * with a_nk the scaled entries of Eq. (M2Lmat) for the pair (t, s).  The
+ * conjugate form is the gradient of a real objective with respect to the
+ * multipole coefficients (PyTorch's convention for complex tensors).
+ * Arguments as fmm_m2l with W (input, [nbox][p] complex64) in place of M and
+ * G (output) in place of L.  prec must be FMM_FP32.
+ * ------------------------------------------------------------------------- */
+int fmm_m2l_adjoint(const fmm_tree* tree, int32_t level, int32_t p, int32_t prec,
+                    const void* W, void* G, int32_t flags, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Support for building M2L inputs on the device (upward sweep, Sec. 2.1
+ * stage 2; not the translation path itself).
+ *
+ * fmm_p2m: M~_b[k] (+)= sum_{i in box b} c_i ((y_i - x_b) / r_l)^k for every
+ *   box of `level`; a point goes to box floor(x 2^l) clamped to 2^l - 1.
+ *   xy: device float64 [n][2]; c: device float64 [n]; M: device complex64
+ *   [4^level][p].  Uses FP32 atomic additions (result order-dependent in the
+ *   last bits).  flags: FMM_ACCUMULATE or 0.
+ * fmm_m2m: parent MEs from child MEs, M_j = sum_{k<=j} C(j,k)(x_c - x_P)^(j-k) m_k,
+ *   in scaled units.  Mc: [4^child_level][p], Mp: [4^(child_level-1)][p].
+ * ------------------------------------------------------------------------- */
+int fmm_p2m(int32_t level, int32_t p, const double* xy, const double* c, int64_t n,
+            void* M, int32_t flags, void* stream);
+int fmm_m2m(int32_t child_level, int32_t p, const void* Mc, void* Mp, int32_t flags, void* stream);
+
+/* Read and clear the device error word after synchronising `stream`.
+ * Returns FMM_OK, FMM_ETIMEOUT or FMM_EDEVICE. */
+int fmm_sync_status(void* stream);
+
+/* Message for the calling thread's most recent failure ("" if none). */
+const char* fmm_last_error(void);
+
+/* Library version string. */
+const char* fmm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FMMGB_H */

@@ -251,6 +251,13 @@ def scale_me(M: np.ndarray, level: int) -> np.ndarray:
     return M * np.ldexp(1.0, level * k)
 
 
+def unscale_me(Ms: np.ndarray, level: int) -> np.ndarray:
+    """m_k = m~_k r^k,  r = 2^-level."""
+    p = Ms.shape[-1]
+    k = np.arange(p)
+    return Ms * np.ldexp(1.0, -level * k)
+
+
 def scale_le(L: np.ndarray, level: int) -> np.ndarray:
     """l~_n = l_n * r^(n+1),  r = 2^-level."""
     p = L.shape[-1]

@@ -1,0 +1,404 @@
+// api.cu -- C ABI of libfmmgb: argument checks, tree handles, per-device
+// operator tables and dispatch to the kernels.  All arithmetic of the method
+// runs in the kernels of m2l_fp32.cu, m2l_tc.cu, fgt_h2t.cu and upward.cu.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "common.cuh"
+
+namespace fmmgb {
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local char g_msg[512] = "";
+
+int fail(int code, const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_msg, sizeof(g_msg), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what)
+{
+    return fail(e == cudaErrorMemoryAllocation ? FMM_ENOMEM : FMM_ECUDA, "%s: %s (%s)", what,
+                cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+void clear_error() { g_msg[0] = 0; }
+
+// ---------------------------------------------------------------------------
+// interaction-list stencil per child class (Sec. 4.1 step 1)
+// ---------------------------------------------------------------------------
+void class_stencil(int cls, StencilEntry out[27])
+{
+    const int cx = cls & 1, cy = cls >> 1;
+    int n = 0;
+    for (int ey = -1; ey <= 1; ++ey)
+        for (int ex = -1; ex <= 1; ++ex)
+            for (int sy = 0; sy < 2; ++sy)
+                for (int sx = 0; sx < 2; ++sx) {
+                    const int dx = 2 * ex + sx - cx, dy = 2 * ey + sy - cy;
+                    const int adx = dx < 0 ? -dx : dx, ady = dy < 0 ? -dy : dy;
+                    if ((adx > ady ? adx : ady) < 2) continue;  // adjacent: near field
+                    out[n].ex = (int8_t)ex;
+                    out[n].ey = (int8_t)ey;
+                    out[n].csrc = (int8_t)(sx + 2 * sy);
+                    out[n].slot = (int8_t)offset_slot(dx, dy);
+                    ++n;
+                }
+}
+
+// ---------------------------------------------------------------------------
+// per-device state
+// ---------------------------------------------------------------------------
+struct DeviceState {
+    int* err_word = nullptr;
+    std::map<int, M2LTables*> m2l;
+};
+static std::mutex g_mu;
+static std::map<int, DeviceState*> g_dev;
+
+static int current_state(DeviceState** out)
+{
+    int dev = 0;
+    FMM_CUDA_TRY(cudaGetDevice(&dev));
+    auto it = g_dev.find(dev);
+    if (it != g_dev.end()) {
+        *out = it->second;
+        return FMM_OK;
+    }
+    DeviceState* s = new DeviceState();
+    cudaError_t e = cudaMalloc(&s->err_word, sizeof(int));
+    if (e != cudaSuccess) {
+        delete s;
+        return cuda_fail(e, "cudaMalloc(error word)");
+    }
+    e = cudaMemset(s->err_word, 0, sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemset(error word)");
+    g_dev[dev] = s;
+    *out = s;
+    return FMM_OK;
+}
+
+int device_error_word(int** out)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    DeviceState* s = nullptr;
+    int rc = current_state(&s);
+    if (rc) return rc;
+    *out = s->err_word;
+    return FMM_OK;
+}
+
+double m2l_balance(int p)
+{
+    // s = 2e / (2p - 2) balances j! s^j |D|^-(j+1) (|D| >= 2) against
+    // 1 / (n! s^n) over the index ranges j <= 2p-2, n <= p-1.
+    const double jmax = (p > 1) ? 2.0 * p - 2.0 : 1.0;
+    return 2.0 * 2.718281828459045 / jmax;
+}
+
+int get_m2l_tables(int p, const M2LTables** out)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    DeviceState* s = nullptr;
+    int rc = current_state(&s);
+    if (rc) return rc;
+    auto it = s->m2l.find(p);
+    if (it != s->m2l.end()) {
+        *out = it->second;
+        return FMM_OK;
+    }
+    M2LTables* t = new M2LTables();
+    t->p = p;
+    t->s = m2l_balance(p);
+    const size_t nh = (size_t)kOffsetSlots * (2 * p - 1);
+    cudaError_t e;
+    if ((e = cudaMalloc(&t->h_fwd, nh * sizeof(float2))) != cudaSuccess ||
+        (e = cudaMalloc(&t->h_adj, nh * sizeof(float2))) != cudaSuccess ||
+        (e = cudaMalloc(&t->h_adjc, nh * sizeof(float2))) != cudaSuccess ||
+        (e = cudaMalloc(&t->a, p * sizeof(float))) != cudaSuccess ||
+        (e = cudaMalloc(&t->b, p * sizeof(float))) != cudaSuccess) {
+        cudaFree(t->h_fwd);
+        cudaFree(t->h_adj);
+        cudaFree(t->h_adjc);
+        cudaFree(t->a);
+        cudaFree(t->b);
+        delete t;
+        return cuda_fail(e, "cudaMalloc(M2L operator tables)");
+    }
+    cudaStream_t st;
+    FMM_CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    rc = launch_build_m2l_tables(*t, st);
+    cudaError_t es = cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+    if (rc) return rc;
+    if (es != cudaSuccess) return cuda_fail(es, "building M2L operator tables");
+    s->m2l[p] = t;
+    *out = t;
+    return FMM_OK;
+}
+
+}  // namespace fmmgb
+
+using namespace fmmgb;
+
+// ---------------------------------------------------------------------------
+// tree handle
+// ---------------------------------------------------------------------------
+struct fmm_tree {
+    int32_t max_level = 0;
+    int32_t periodic = 0;
+    struct Level {
+        bool built = false;
+        int64_t ntr = 0;
+        std::vector<int32_t> list;
+        std::vector<int8_t> code;
+        int32_t* list_dev = nullptr;
+        int8_t* code_dev = nullptr;
+    };
+    Level levels[FMM_MAX_LEVEL + 1];
+    std::mutex mu;
+};
+
+static int64_t translations_closed_form(int level, bool periodic)
+{
+    if (level < 2) return 0;
+    const int64_t n = (int64_t)1 << level;
+    if (periodic) return 27 * n * n;
+    return (6 * n - 8) * (6 * n - 8) - (3 * n - 2) * (3 * n - 2);
+}
+
+extern "C" {
+
+const char* fmm_last_error(void) { return g_msg; }
+
+const char* fmm_version(void) { return "fmmgb 0.1 (sm_103a)"; }
+
+int fmm_build_lists(const double* xy, int64_t n, int32_t max_level, int32_t leaf_cap, int32_t flags,
+                    fmm_tree** out)
+{
+    clear_error();
+    if (!out) return fail(FMM_EINVAL, "fmm_build_lists: out is NULL");
+    *out = nullptr;
+    if (n < 0) return fail(FMM_EINVAL, "fmm_build_lists: n = %lld < 0", (long long)n);
+    if (n > 0 && !xy && leaf_cap != 0) return fail(FMM_EINVAL, "fmm_build_lists: xy is NULL");
+    if (max_level < 2 || max_level > FMM_MAX_LEVEL)
+        return fail(FMM_EINVAL, "fmm_build_lists: max_level %d outside 2..%d", max_level, FMM_MAX_LEVEL);
+    if (leaf_cap < 0) return fail(FMM_EINVAL, "fmm_build_lists: leaf_cap %d < 0", leaf_cap);
+    if (leaf_cap > 0) return fail(FMM_EUNSUPPORTED, "fmm_build_lists: adaptive trees are not provided by this build");
+    if (flags & ~FMM_TREE_PERIODIC) return fail(FMM_EINVAL, "fmm_build_lists: unknown flags 0x%x", flags);
+    fmm_tree* t = new (std::nothrow) fmm_tree();
+    if (!t) return fail(FMM_ENOMEM, "fmm_build_lists: out of host memory");
+    t->max_level = max_level;
+    t->periodic = (flags & FMM_TREE_PERIODIC) ? 1 : 0;
+    for (int l = 0; l <= max_level; ++l) t->levels[l].ntr = translations_closed_form(l, t->periodic);
+    *out = t;
+    return FMM_OK;
+}
+
+int64_t fmm_tree_translations(const fmm_tree* tree, int32_t level)
+{
+    if (!tree || level < 0 || level > tree->max_level) return -1;
+    return tree->levels[level].ntr;
+}
+
+int fmm_tree_level_info(const fmm_tree* ctree, int32_t level, fmm_level_info* out)
+{
+    clear_error();
+    if (!ctree || !out) return fail(FMM_EINVAL, "fmm_tree_level_info: NULL argument");
+    fmm_tree* tree = const_cast<fmm_tree*>(ctree);
+    if (level < 0 || level > tree->max_level)
+        return fail(FMM_EINVAL, "fmm_tree_level_info: level %d outside 0..%d", level, tree->max_level);
+    std::lock_guard<std::mutex> lk(tree->mu);
+    auto& L = tree->levels[level];
+    const int64_t side = (int64_t)1 << level, nbox = side * side;
+    if (!L.built) {
+        if (nbox * 27 > ((int64_t)1 << 31)) return fail(FMM_EINVAL, "fmm_tree_level_info: level %d lists too large", level);
+        L.list.assign((size_t)nbox * 27, -1);
+        L.code.assign((size_t)nbox * 27, (int8_t)-1);
+        int64_t cnt = 0;
+        if (level >= 2) {
+            StencilEntry st[4][27];
+            for (int c = 0; c < 4; ++c) class_stencil(c, st[c]);
+            for (int64_t ty = 0; ty < side; ++ty)
+                for (int64_t tx = 0; tx < side; ++tx) {
+                    const int cls = (int)(tx & 1) + 2 * (int)(ty & 1);
+                    const int64_t t = ty * side + tx;
+                    int slot = 0;
+                    for (int e = 0; e < 27; ++e) {
+                        const int code = st[cls][e].slot;
+                        const int dx = code % 7 - 3, dy = code / 7 - 3;
+                        int64_t sx = tx + dx, sy = ty + dy;
+                        if (tree->periodic) {
+                            sx = ((sx % side) + side) % side;
+                            sy = ((sy % side) + side) % side;
+                        } else if (sx < 0 || sy < 0 || sx >= side || sy >= side) {
+                            continue;
+                        }
+                        L.list[(size_t)t * 27 + slot] = (int32_t)(sy * side + sx);
+                        L.code[(size_t)t * 27 + slot] = (int8_t)code;
+                        ++slot;
+                        ++cnt;
+                    }
+                }
+        }
+        if (cnt != L.ntr) return fail(FMM_EDEVICE, "fmm_tree_level_info: list count %lld != %lld", (long long)cnt, (long long)L.ntr);
+        int ndev = 0;
+        if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+            (void)cudaGetLastError();  // host-only use: device copies stay NULL
+        } else {
+            cudaError_t e = cudaMalloc(&L.list_dev, L.list.size() * sizeof(int32_t));
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(list)");
+            e = cudaMalloc(&L.code_dev, L.code.size());
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(offset codes)");
+            e = cudaMemcpy(L.list_dev, L.list.data(), L.list.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(list)");
+            e = cudaMemcpy(L.code_dev, L.code.data(), L.code.size(), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(offset codes)");
+        }
+        L.built = true;
+    }
+    out->nbox = nbox;
+    out->side = (int32_t)side;
+    out->list_stride = 27;
+    out->ntranslations = L.ntr;
+    out->list_host = L.list.data();
+    out->offcode_host = L.code.data();
+    out->list_dev = L.list_dev;
+    out->offcode_dev = L.code_dev;
+    return FMM_OK;
+}
+
+void fmm_tree_destroy(fmm_tree* tree)
+{
+    if (!tree) return;
+    for (auto& L : tree->levels) {
+        if (L.list_dev) cudaFree(L.list_dev);
+        if (L.code_dev) cudaFree(L.code_dev);
+    }
+    delete tree;
+}
+
+static bool valid_p(int p) { return m2l_fp32_supported(p); }
+
+int fmm_prepare(int32_t p, int32_t prec)
+{
+    clear_error();
+    if (!valid_p(p)) return fail(FMM_EINVAL, "fmm_prepare: unsupported p = %d (6, 8, 12, 16, 24)", p);
+    if (prec != FMM_FP32) return fail(FMM_EUNSUPPORTED, "fmm_prepare: precision %d not provided by this build", prec);
+    const M2LTables* t = nullptr;
+    return get_m2l_tables(p, &t);
+}
+
+static int m2l_common(const char* who, const fmm_tree* tree, int32_t level, int32_t p, int32_t prec,
+                      const void* in, void* out, int32_t flags, int32_t allowed_flags)
+{
+    if (!tree) return fail(FMM_EINVAL, "%s: tree is NULL", who);
+    if (level < 0 || level > tree->max_level)
+        return fail(FMM_EINVAL, "%s: level %d outside 0..%d", who, level, tree->max_level);
+    if (!valid_p(p)) return fail(FMM_EINVAL, "%s: unsupported p = %d (6, 8, 12, 16, 24)", who, p);
+    if (prec != FMM_FP32 && prec != FMM_TC_BF16X3 && prec != FMM_TC_BF16)
+        return fail(FMM_EINVAL, "%s: unknown precision %d", who, prec);
+    if (!in || !out) return fail(FMM_EINVAL, "%s: NULL coefficient pointer", who);
+    if (((uintptr_t)in & 15) || ((uintptr_t)out & 15))
+        return fail(FMM_EINVAL, "%s: coefficient pointers must be 16-byte aligned", who);
+    if (flags & ~allowed_flags) return fail(FMM_EINVAL, "%s: unknown flags 0x%x", who, flags);
+    const size_t bytes = ((size_t)1 << (2 * level)) * (size_t)p * 8;
+    const char* a = (const char*)in;
+    const char* b = (const char*)out;
+    if (a < b + bytes && b < a + bytes) return fail(FMM_EINVAL, "%s: input and output overlap", who);
+    return FMM_OK;
+}
+
+int fmm_m2l(const fmm_tree* tree, int32_t level, int32_t p, int32_t prec, const void* M, void* L, int32_t flags,
+            void* stream)
+{
+    clear_error();
+    int rc = m2l_common("fmm_m2l", tree, level, p, prec, M, L, flags, FMM_ACCUMULATE);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool acc = (flags & FMM_ACCUMULATE) != 0;
+    if (level < 2) {
+        if (!acc) FMM_CUDA_TRY(cudaMemsetAsync(L, 0, ((size_t)1 << (2 * level)) * (size_t)p * 8, st));
+        return FMM_OK;
+    }
+    if (prec != FMM_FP32) return fail(FMM_EUNSUPPORTED, "fmm_m2l: tensor-core precision %d not provided by this build", prec);
+    const M2LTables* t = nullptr;
+    if ((rc = get_m2l_tables(p, &t))) return rc;
+    return launch_m2l_fp32_uniform(level, p, t->h_fwd, t->a, t->b, (const float2*)M, (float2*)L, acc,
+                                   tree->periodic != 0, st);
+}
+
+int fmm_m2l_adjoint(const fmm_tree* tree, int32_t level, int32_t p, int32_t prec, const void* W, void* G,
+                    int32_t flags, void* stream)
+{
+    clear_error();
+    int rc = m2l_common("fmm_m2l_adjoint", tree, level, p, prec, W, G, flags, FMM_ACCUMULATE | FMM_CONJ);
+    if (rc) return rc;
+    if (prec != FMM_FP32) return fail(FMM_EUNSUPPORTED, "fmm_m2l_adjoint: only FMM_FP32 is provided");
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool acc = (flags & FMM_ACCUMULATE) != 0;
+    if (level < 2) {
+        if (!acc) FMM_CUDA_TRY(cudaMemsetAsync(G, 0, ((size_t)1 << (2 * level)) * (size_t)p * 8, st));
+        return FMM_OK;
+    }
+    const M2LTables* t = nullptr;
+    if ((rc = get_m2l_tables(p, &t))) return rc;
+    // Transpose by the identity a(D)^T = -a(-D) on symmetric lists: the
+    // adjoint is the forward stencil with the negated (and, for FMM_CONJ,
+    // conjugated) operator table.
+    const float2* h = (flags & FMM_CONJ) ? t->h_adjc : t->h_adj;
+    return launch_m2l_fp32_uniform(level, p, h, t->a, t->b, (const float2*)W, (float2*)G, acc, tree->periodic != 0,
+                                   st);
+}
+
+int fmm_p2m(int32_t level, int32_t p, const double* xy, const double* c, int64_t n, void* M, int32_t flags,
+            void* stream)
+{
+    clear_error();
+    if (level < 0 || level > FMM_MAX_LEVEL) return fail(FMM_EINVAL, "fmm_p2m: level %d outside 0..%d", level, FMM_MAX_LEVEL);
+    if (p < 1 || p > 64) return fail(FMM_EINVAL, "fmm_p2m: p = %d outside 1..64", p);
+    if (n < 0) return fail(FMM_EINVAL, "fmm_p2m: n < 0");
+    if (!M || (n > 0 && (!xy || !c))) return fail(FMM_EINVAL, "fmm_p2m: NULL pointer");
+    if (flags & ~FMM_ACCUMULATE) return fail(FMM_EINVAL, "fmm_p2m: unknown flags 0x%x", flags);
+    return launch_p2m(level, p, xy, c, n, (float2*)M, (flags & FMM_ACCUMULATE) != 0, (cudaStream_t)stream);
+}
+
+int fmm_m2m(int32_t child_level, int32_t p, const void* Mc, void* Mp, int32_t flags, void* stream)
+{
+    clear_error();
+    if (child_level < 1 || child_level > FMM_MAX_LEVEL)
+        return fail(FMM_EINVAL, "fmm_m2m: child_level %d outside 1..%d", child_level, FMM_MAX_LEVEL);
+    if (p < 1 || p > 64) return fail(FMM_EINVAL, "fmm_m2m: p = %d outside 1..64", p);
+    if (!Mc || !Mp) return fail(FMM_EINVAL, "fmm_m2m: NULL pointer");
+    if (flags & ~FMM_ACCUMULATE) return fail(FMM_EINVAL, "fmm_m2m: unknown flags 0x%x", flags);
+    return launch_m2m(child_level, p, (const float2*)Mc, (float2*)Mp, (flags & FMM_ACCUMULATE) != 0,
+                      (cudaStream_t)stream);
+}
+
+int fmm_sync_status(void* stream)
+{
+    clear_error();
+    FMM_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    int* w = nullptr;
+    int rc = device_error_word(&w);
+    if (rc) return rc;
+    int h = 0;
+    FMM_CUDA_TRY(cudaMemcpy(&h, w, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h) FMM_CUDA_TRY(cudaMemset(w, 0, sizeof(int)));
+    if (h & DEV_ERR_TIMEOUT) return fail(FMM_ETIMEOUT, "a bounded device-side wait timed out");
+    if (h & DEV_ERR_CHECK) return fail(FMM_EDEVICE, "a device-side argument check failed");
+    return FMM_OK;
+}
+
+}  // extern "C"

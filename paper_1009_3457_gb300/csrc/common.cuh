@@ -1,0 +1,82 @@
+// common.cuh -- internal declarations shared by the translation units of libfmmgb.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fmmgb.h"
+
+namespace fmmgb {
+
+// ---------------------------------------------------------------------------
+// error reporting (thread-local message, status codes of fmmgb.h)
+// ---------------------------------------------------------------------------
+int fail(int code, const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what);
+void clear_error();
+
+#define FMM_CUDA_TRY(expr)                                  \
+    do {                                                    \
+        cudaError_t e__ = (expr);                           \
+        if (e__ != cudaSuccess) return cuda_fail(e__, #expr); \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// device error word: bit 0 = a device-side check failed, bit 1 = a bounded
+// wait timed out.  One word per device, library-owned.
+// ---------------------------------------------------------------------------
+enum : int { DEV_ERR_CHECK = 1, DEV_ERR_TIMEOUT = 2 };
+int device_error_word(int** out);
+
+// ---------------------------------------------------------------------------
+// offset codes: box offset (dx, dy) = source - target, |dx|,|dy| <= 3
+// ---------------------------------------------------------------------------
+constexpr int kOffsetSlots = 49;  // 7 x 7 grid; the 9 central slots are never used
+__host__ __device__ constexpr int offset_slot(int dx, int dy) { return (dy + 3) * 7 + (dx + 3); }
+
+// Per child class c = (tx & 1) + 2 (ty & 1): the 27 interaction-list offsets,
+// as (parent offset ex, ey in -1..1, source child class c').  Filled on the
+// host by class_stencil(); the kernels get a copy in constant memory.
+struct StencilEntry {
+    int8_t ex, ey;   // parent offset
+    int8_t csrc;     // source child class
+    int8_t slot;     // offset_slot(dx, dy)
+};
+void class_stencil(int cls, StencilEntry out[27]);
+
+// ---------------------------------------------------------------------------
+// M2L operator tables (per device, per p), built by a GPU FP64 kernel.
+//
+// Scaled operator of offset D = (x_t - x_s)/r (a complex integer):
+//   T[n][k] = (-1)^n C(n+k,k) D^-(n+k+1) = a_n h_D[n+k] b_k,
+//   a_n = (-1)^n / (n! s^n),  b_k = 1 / (k! s^k),  h_D[j] = j! s^j D^-(j+1),
+// a Hankel matrix between two diagonal scalings.  The balance factor s keeps
+// every factor well inside FP32 range for p <= 32.
+// ---------------------------------------------------------------------------
+struct M2LTables {
+    int p = 0;
+    double s = 0.0;
+    float2* h_fwd = nullptr;   // [49][2p-1] complex: forward M2L
+    float2* h_adj = nullptr;   // [49][2p-1]: plain adjoint  (= -h_fwd)
+    float2* h_adjc = nullptr;  // [49][2p-1]: conjugate adjoint (= -conj h_fwd)
+    float* a = nullptr;        // [p] post-scale
+    float* b = nullptr;        // [p] pre-scale
+    // dense scaled operators for the tensor-core path, built on demand
+    void* tc_w = nullptr;
+    int tc_ready = 0;
+};
+int get_m2l_tables(int p, const M2LTables** out);
+double m2l_balance(int p);
+
+// launchers (m2l_fp32.cu)
+int launch_build_m2l_tables(const M2LTables& t, cudaStream_t st);
+bool m2l_fp32_supported(int p);
+int launch_m2l_fp32_uniform(int level, int p, const float2* hsel, const float* a, const float* b,
+                            const float2* M, float2* L, bool accumulate, bool periodic, cudaStream_t st);
+
+// launchers (upward.cu)
+int launch_p2m(int level, int p, const double* xy, const double* c, int64_t n, float2* M, bool accumulate,
+               cudaStream_t st);
+int launch_m2m(int child_level, int p, const float2* Mc, float2* Mp, bool accumulate, cudaStream_t st);
+
+}  // namespace fmmgb

@@ -1,0 +1,93 @@
+// upward.cu -- device construction of M2L inputs (upward sweep, Sec. 2.1
+// stage 2): P2M of particles into the boxes of one level and M2M from a level
+// to its parents, in radius-scaled units.  Support for the translation path,
+// not part of it; kept simple (atomic accumulation).
+#include "common.cuh"
+
+namespace fmmgb {
+
+// M~_b[k] += c_i w^k,  w = (y_i - x_b) / r_l  (|w| <= 1/sqrt 2)
+__global__ void p2m_kernel(int level, int p, const double* __restrict__ xy, const double* __restrict__ c, int64_t n,
+                           float2* __restrict__ M)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int side = 1 << level;
+    const double x = xy[2 * i] * side, y = xy[2 * i + 1] * side;
+    int ix = (int)floor(x), iy = (int)floor(y);
+    ix = ix < 0 ? 0 : (ix > side - 1 ? side - 1 : ix);
+    iy = iy < 0 ? 0 : (iy > side - 1 ? side - 1 : iy);
+    const double wr = x - (ix + 0.5), wi = y - (iy + 0.5);
+    double pr = c[i], pi = 0.0;
+    float2* mb = M + ((size_t)iy * side + ix) * p;
+    for (int k = 0; k < p; ++k) {
+        atomicAdd(&mb[k].x, (float)pr);
+        atomicAdd(&mb[k].y, (float)pi);
+        const double t = pr * wr - pi * wi;
+        pi = pr * wi + pi * wr;
+        pr = t;
+    }
+}
+
+// Scaled M2M: parent box side R = 2r, child offset z = (x_c - x_P)/R = (+-1/4, +-1/4):
+//   M~P_j = sum_{k<=j} C(j,k) z^(j-k) 2^-k M~c_k, summed over the 4 children.
+__global__ void m2m_kernel(int child_level, int p, const float2* __restrict__ Mc, float2* __restrict__ Mp,
+                           int accumulate)
+{
+    const int np = 1 << (child_level - 1);
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)np * np * p) return;
+    const int j = (int)(idx % p);
+    const int64_t pb = idx / p;
+    const int px = (int)(pb % np), py = (int)(pb / np);
+    const int nc = 2 * np;
+    double sr = 0.0, si = 0.0;
+    for (int cyy = 0; cyy < 2; ++cyy)
+        for (int cxx = 0; cxx < 2; ++cxx) {
+            const double zr = cxx ? 0.25 : -0.25, zi = cyy ? 0.25 : -0.25;
+            const float2* mc = Mc + ((size_t)(2 * py + cyy) * nc + (2 * px + cxx)) * p;
+            // k from j down to 0: term C(j,k) z^(j-k) 2^-k m_k
+            double binom = 1.0;          // C(j, k) for k = j
+            double zpr = 1.0, zpi = 0.0;  // z^(j-k)
+            for (int k = j; k >= 0; --k) {
+                const double sc = binom * ldexp(1.0, -k);
+                const double tr = zpr * mc[k].x - zpi * mc[k].y;
+                const double ti = zpr * mc[k].y + zpi * mc[k].x;
+                sr += sc * tr;
+                si += sc * ti;
+                // next k-1: C(j,k-1) = C(j,k) * k / (j-k+1); z^(j-k+1)
+                if (k > 0) binom = binom * k / (double)(j - k + 1);
+                const double nr = zpr * zr - zpi * zi;
+                zpi = zpr * zi + zpi * zr;
+                zpr = nr;
+            }
+        }
+    float2* out = Mp + (size_t)pb * p + j;
+    if (accumulate) {
+        sr += out->x;
+        si += out->y;
+    }
+    *out = make_float2((float)sr, (float)si);
+}
+
+int launch_p2m(int level, int p, const double* xy, const double* c, int64_t n, float2* M, bool acc, cudaStream_t st)
+{
+    const size_t bytes = ((size_t)1 << (2 * level)) * (size_t)p * sizeof(float2);
+    if (!acc) FMM_CUDA_TRY(cudaMemsetAsync(M, 0, bytes, st));
+    if (n == 0) return FMM_OK;
+    const int64_t blocks = (n + 255) / 256;
+    p2m_kernel<<<(unsigned)blocks, 256, 0, st>>>(level, p, xy, c, n, M);
+    FMM_CUDA_TRY(cudaGetLastError());
+    return FMM_OK;
+}
+
+int launch_m2m(int child_level, int p, const float2* Mc, float2* Mp, bool acc, cudaStream_t st)
+{
+    const int64_t np = (int64_t)1 << (child_level - 1);
+    const int64_t total = np * np * p;
+    m2m_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(child_level, p, Mc, Mp, acc ? 1 : 0);
+    FMM_CUDA_TRY(cudaGetLastError());
+    return FMM_OK;
+}
+
+}  // namespace fmmgb

@@ -1,0 +1,209 @@
+"""Thin ctypes binding of libfmmgb (include/fmmgb.h), with the C entry points' names.
+
+Argument marshalling only: torch tensors are passed by device pointer, the
+stream is the caller's current torch stream.  Every step of the translation
+path runs in the library's CUDA kernels; there is no fallback.  If the library
+is missing, or there is no GPU, calls raise ``FmmError``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfmmgb.so")
+
+FMM_OK = 0
+FMM_EINVAL = -1
+FMM_ENOMEM = -2
+FMM_ECUDA = -3
+FMM_ETIMEOUT = -4
+FMM_EUNSUPPORTED = -5
+FMM_EDEVICE = -6
+
+FMM_FP32 = 0
+FMM_TC_BF16X3 = 1
+FMM_TC_BF16 = 2
+
+FMM_ACCUMULATE = 1
+FMM_CONJ = 2
+FMM_TREE_PERIODIC = 1
+FMM_MAX_LEVEL = 14
+
+STATUS_NAMES = {0: "FMM_OK", -1: "FMM_EINVAL", -2: "FMM_ENOMEM", -3: "FMM_ECUDA", -4: "FMM_ETIMEOUT",
+                -5: "FMM_EUNSUPPORTED", -6: "FMM_EDEVICE"}
+
+
+class FmmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class fmm_level_info(ctypes.Structure):
+    _fields_ = [
+        ("nbox", ctypes.c_int64),
+        ("side", ctypes.c_int32),
+        ("list_stride", ctypes.c_int32),
+        ("ntranslations", ctypes.c_int64),
+        ("list_host", ctypes.POINTER(ctypes.c_int32)),
+        ("offcode_host", ctypes.POINTER(ctypes.c_int8)),
+        ("list_dev", ctypes.c_void_p),
+        ("offcode_dev", ctypes.c_void_p),
+    ]
+
+
+_vp = ctypes.c_void_p
+_i32 = ctypes.c_int32
+_i64 = ctypes.c_int64
+_d = ctypes.c_double
+_f = ctypes.c_float
+
+# name -> (restype, argtypes); the list of exported entry points of include/fmmgb.h
+SIGNATURES = {
+    "fmm_build_lists": (ctypes.c_int, [_vp, _i64, _i32, _i32, _i32, ctypes.POINTER(_vp)]),
+    "fmm_tree_level_info": (ctypes.c_int, [_vp, _i32, ctypes.POINTER(fmm_level_info)]),
+    "fmm_tree_translations": (ctypes.c_int64, [_vp, _i32]),
+    "fmm_tree_destroy": (None, [_vp]),
+    "fmm_prepare": (ctypes.c_int, [_i32, _i32]),
+    "fmm_m2l": (ctypes.c_int, [_vp, _i32, _i32, _i32, _vp, _vp, _i32, _vp]),
+    "fmm_m2l_adjoint": (ctypes.c_int, [_vp, _i32, _i32, _i32, _vp, _vp, _i32, _vp]),
+    "fmm_p2m": (ctypes.c_int, [_i32, _i32, _vp, _vp, _i64, _vp, _i32, _vp]),
+    "fmm_m2m": (ctypes.c_int, [_i32, _i32, _vp, _vp, _i32, _vp]),
+    "fmm_sync_status": (ctypes.c_int, [_vp]),
+    "fmm_last_error": (ctypes.c_char_p, []),
+    "fmm_version": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libfmmgb.so (raises FmmError if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise FmmError(FMM_EUNSUPPORTED, f"CUDA library not built: {path} (run __graft_entry__.build())")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            if not hasattr(lib, name):
+                continue
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(rc: int):
+    if rc != FMM_OK:
+        raise FmmError(rc, load().fmm_last_error().decode())
+
+
+def _ptr(t) -> int:
+    """Device pointer of a CUDA tensor (or an int address)."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if not t.is_cuda:
+        raise FmmError(FMM_EINVAL, "tensor must live on a CUDA device")
+    if not t.is_contiguous():
+        raise FmmError(FMM_EINVAL, "tensor must be contiguous")
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Tree:
+    """Owning wrapper of an ``fmm_tree*`` handle."""
+
+    def __init__(self, handle: int, max_level: int, periodic: bool):
+        self.handle = handle
+        self.max_level = max_level
+        self.periodic = periodic
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h and _lib is not None:
+            _lib.fmm_tree_destroy(h)
+            self.handle = None
+
+    def translations(self, level: int) -> int:
+        return int(load().fmm_tree_translations(self.handle, level))
+
+    def level_info(self, level: int) -> fmm_level_info:
+        info = fmm_level_info()
+        _check(load().fmm_tree_level_info(self.handle, level, ctypes.byref(info)))
+        return info
+
+    def lists(self, level: int):
+        """Host copies of the level's lists: (list [nbox, 27] int32, offset codes [nbox, 27] int8)."""
+        import numpy as np
+
+        info = self.level_info(level)
+        n = info.nbox * info.list_stride
+        lst = np.ctypeslib.as_array(info.list_host, shape=(n,)).reshape(info.nbox, info.list_stride).copy()
+        code = np.ctypeslib.as_array(info.offcode_host, shape=(n,)).reshape(info.nbox, info.list_stride).copy()
+        return lst, code
+
+
+def fmm_build_lists(xy=None, max_level: int = 2, leaf_cap: int = 0, periodic: bool = False) -> Tree:
+    import numpy as np
+
+    lib = load()
+    h = _vp()
+    if xy is not None:
+        xy = np.ascontiguousarray(xy, dtype=np.float64)
+        n = xy.shape[0]
+        xp = xy.ctypes.data
+    else:
+        n, xp = 0, None
+    _check(lib.fmm_build_lists(xp, n, max_level, leaf_cap, FMM_TREE_PERIODIC if periodic else 0, ctypes.byref(h)))
+    return Tree(h.value, max_level, periodic)
+
+
+def fmm_prepare(p: int, prec: int = FMM_FP32):
+    _check(load().fmm_prepare(p, prec))
+
+
+def fmm_m2l(tree: Tree, level: int, p: int, M, L, prec: int = FMM_FP32, accumulate: bool = False, stream=None):
+    _check(load().fmm_m2l(tree.handle, level, p, prec, _ptr(M), _ptr(L), FMM_ACCUMULATE if accumulate else 0,
+                          _stream(stream)))
+
+
+def fmm_m2l_adjoint(tree: Tree, level: int, p: int, W, G, prec: int = FMM_FP32, accumulate: bool = False,
+                    conj: bool = False, stream=None):
+    flags = (FMM_ACCUMULATE if accumulate else 0) | (FMM_CONJ if conj else 0)
+    _check(load().fmm_m2l_adjoint(tree.handle, level, p, prec, _ptr(W), _ptr(G), flags, _stream(stream)))
+
+
+def fmm_p2m(level: int, p: int, xy, c, M, accumulate: bool = False, stream=None):
+    n = 0 if c is None else c.numel()
+    _check(load().fmm_p2m(level, p, _ptr(xy), _ptr(c), n, _ptr(M), FMM_ACCUMULATE if accumulate else 0,
+                          _stream(stream)))
+
+
+def fmm_m2m(child_level: int, p: int, Mc, Mp, accumulate: bool = False, stream=None):
+    _check(load().fmm_m2m(child_level, p, _ptr(Mc), _ptr(Mp), FMM_ACCUMULATE if accumulate else 0,
+                          _stream(stream)))
+
+
+def fmm_sync_status(stream=None):
+    _check(load().fmm_sync_status(_stream(stream)))
+
+
+def fmm_last_error() -> str:
+    return load().fmm_last_error().decode()
+
+
+def fmm_version() -> str:
+    return load().fmm_version().decode()

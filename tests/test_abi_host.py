@@ -1,0 +1,107 @@
+"""CPU-side checks of the C ABI library: it loads, exports every entry point the
+header declares, rejects bad arguments on the host before touching the GPU,
+and builds interaction lists that agree with the FP64 oracle's definition."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def fmm():
+    from paper_1009_3457_gb300 import build, fmmgb
+
+    build.build()
+    fmmgb.load()
+    return fmmgb
+
+
+def _declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", fn)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*((?:fmm|fgt)_[a-z_0-9]+)\s*\(", src, re.M):
+            names.add(m.group(1))
+    return names
+
+
+def test_every_declared_symbol_is_exported(fmm):
+    lib = fmm.load()
+    names = _declared_functions()
+    assert {"fmm_build_lists", "fmm_m2l", "fmm_m2l_adjoint"} <= names
+    for n in names:
+        assert hasattr(lib, n), n
+        assert n in fmm.SIGNATURES, f"binding lacks {n}"
+
+
+def test_version(fmm):
+    assert "sm_103a" in fmm.fmm_version()
+
+
+def test_build_lists_rejects_bad_arguments(fmm):
+    with pytest.raises(fmm.FmmError) as e:
+        fmm.fmm_build_lists(None, 1)
+    assert e.value.code == fmm.FMM_EINVAL
+    with pytest.raises(fmm.FmmError) as e:
+        fmm.fmm_build_lists(None, fmm.FMM_MAX_LEVEL + 1)
+    assert e.value.code == fmm.FMM_EINVAL
+    with pytest.raises(fmm.FmmError) as e:
+        fmm.fmm_build_lists(None, 5, leaf_cap=-1)
+    assert e.value.code == fmm.FMM_EINVAL
+
+
+def test_m2l_rejects_bad_arguments_before_launch(fmm):
+    lib = fmm.load()
+    tree = fmm.fmm_build_lists(None, 4)
+    # NULL tree, bad level, bad p, NULL / misaligned / overlapping pointers, bad flags
+    assert lib.fmm_m2l(None, 3, 8, 0, 4096, 1 << 20, 0, None) == fmm.FMM_EINVAL
+    assert lib.fmm_m2l(tree.handle, 5, 8, 0, 4096, 1 << 20, 0, None) == fmm.FMM_EINVAL
+    assert lib.fmm_m2l(tree.handle, -1, 8, 0, 4096, 1 << 20, 0, None) == fmm.FMM_EINVAL
+    assert lib.fmm_m2l(tree.handle, 3, 7, 0, 4096, 1 << 20, 0, None) == fmm.FMM_EINVAL
+    assert lib.fmm_m2l(tree.handle, 3, 8, 9, 4096, 1 << 20, 0, None) == fmm.FMM_EINVAL
+    assert lib.fmm_m2l(tree.handle, 3, 8, 0, None, 1 << 20, 0, None) == fmm.FMM_EINVAL
+    assert lib.fmm_m2l(tree.handle, 3, 8, 0, 4104, 1 << 20, 0, None) == fmm.FMM_EINVAL
+    assert lib.fmm_m2l(tree.handle, 3, 8, 0, 4096, 4096 + 64, 0, None) == fmm.FMM_EINVAL
+    assert lib.fmm_m2l(tree.handle, 3, 8, 0, 4096, 1 << 20, 8, None) == fmm.FMM_EINVAL
+    assert "overlap" in fmm.fmm_last_error() or "flags" in fmm.fmm_last_error()
+    assert lib.fmm_m2l_adjoint(tree.handle, 3, 8, 0, 4096, 1 << 20, 16, None) == fmm.FMM_EINVAL
+
+
+def test_p2m_m2m_reject_bad_arguments(fmm):
+    lib = fmm.load()
+    assert lib.fmm_p2m(-1, 8, 64, 64, 10, 64, 0, None) == fmm.FMM_EINVAL
+    assert lib.fmm_p2m(3, 0, 64, 64, 10, 64, 0, None) == fmm.FMM_EINVAL
+    assert lib.fmm_p2m(3, 8, None, 64, 10, 64, 0, None) == fmm.FMM_EINVAL
+    assert lib.fmm_m2m(0, 8, 64, 128, 0, None) == fmm.FMM_EINVAL
+    assert lib.fmm_m2m(3, 8, None, 128, 0, None) == fmm.FMM_EINVAL
+
+
+@pytest.mark.parametrize("periodic", [False, True])
+@pytest.mark.parametrize("level", [2, 3, 4, 5])
+def test_library_lists_match_oracle(fmm, orc, level, periodic):
+    tree = fmm.fmm_build_lists(None, 6, periodic=periodic)
+    lst, code = tree.lists(level)
+    n = 1 << level
+    assert tree.translations(level) == orc.list_count_level(level, periodic)
+    assert int((lst >= 0).sum()) == tree.translations(level)
+    for t in range(n * n):
+        tx, ty = t % n, t // n
+        want = sorted((sy * n + sx, (oy + 3) * 7 + (ox + 3))
+                      for sx, sy, ox, oy in orc.interaction_list(level, tx, ty, periodic))
+        got = sorted((int(s), int(c)) for s, c in zip(lst[t], code[t]) if s >= 0)
+        assert got == want, (t, got, want)
+        assert all(c == -1 for s, c in zip(lst[t], code[t]) if s < 0)
+
+
+def test_levels_below_two_have_no_lists(fmm):
+    tree = fmm.fmm_build_lists(None, 3)
+    for level in (0, 1):
+        lst, code = tree.lists(level)
+        assert (lst == -1).all() and (code == -1).all()
+        assert tree.translations(level) == 0

@@ -1,0 +1,204 @@
+"""GPU parity of the FP32 M2L path (fmm_m2l, fmm_m2l_adjoint, fmm_p2m, fmm_m2m)
+against the FP64 oracle, through the C ABI.
+
+Bar (spec tolerance for the FP32 path): relative L2 error of the
+radius-scaled local coefficients of a level <= 1e-5, over all boxes and all n;
+in addition every box's own relative error must stay below 1e-4 so that a
+localised fault cannot hide in the level-wide norm.
+"""
+import numpy as np
+import pytest
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+TOL_L2 = 1e-5
+TOL_BOX = 1e-4
+
+
+@pytest.fixture(scope="module")
+def fmm():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1009_3457_gb300 import build, fmmgb
+
+    build.build()
+    fmmgb.load()
+    return fmmgb
+
+
+def _dev(a):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.complex64)).cuda()
+
+
+def _host(t):
+    return t.cpu().numpy().astype(np.complex128)
+
+
+def _check(got, ref, tol_l2=TOL_L2, tol_box=TOL_BOX):
+    err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert err <= tol_l2, f"relative L2 {err:.3e} > {tol_l2:.1e}"
+    box = np.linalg.norm(got - ref, axis=-1) / np.maximum(np.linalg.norm(ref, axis=-1), 1e-300)
+    assert box.max() <= tol_box, f"worst box {box.max():.3e} at {int(box.argmax())}"
+    return err
+
+
+def _oracle_level(orc, level, p, M, periodic=False):
+    return orc.scale_le(orc.m2l_uniform(level, p, M, periodic), level)
+
+
+def test_m2l_small_workload(fmm, orc):
+    """4096 points, uniform tree to level 4, p = 8: every level against the oracle."""
+    cfg = workloads.CONFIGS["m2l_small"]
+    p, L = cfg["p"], cfg["max_level"]
+    xy, c = workloads.uniform_particles(cfg["n"], workloads.rng_for("m2l_small"))
+    Ms = orc.upward_uniform(L, p, xy, c)
+    tree = fmm.fmm_build_lists(None, L)
+    for level in workloads.m2l_levels(L):
+        Md = _dev(orc.scale_me(Ms[level], level))
+        Ld = Md.new_empty(Md.shape)
+        fmm.fmm_m2l(tree, level, p, Md, Ld)
+        _check(_host(Ld), _oracle_level(orc, level, p, Ms[level]))
+    fmm.fmm_sync_status()
+
+
+@pytest.fixture(scope="module")
+def medium_particles():
+    return workloads.uniform_particles(6000, np.random.default_rng(123))
+
+
+@pytest.mark.parametrize("p", [6, 8, 12, 16, 24])
+def test_m2l_all_orders_levels_2_to_5(fmm, orc, medium_particles, p):
+    """Levels 2, 3 (tile larger than the level: ragged), 4 (one full tile), 5 (2 x 2 tiles)."""
+    xy, c = medium_particles
+    Ms = orc.upward_uniform(5, p, xy, c)
+    tree = fmm.fmm_build_lists(None, 5)
+    for level in range(2, 6):
+        Md = _dev(orc.scale_me(Ms[level], level))
+        Ld = Md.new_empty(Md.shape)
+        fmm.fmm_m2l(tree, level, p, Md, Ld)
+        _check(_host(Ld), _oracle_level(orc, level, p, Ms[level]))
+
+
+@pytest.mark.parametrize("level", [2, 3, 6])
+def test_m2l_periodic_lists(fmm, orc, medium_particles, level):
+    xy, c = medium_particles
+    p = 12
+    Ms = orc.upward_uniform(6, p, xy, c)
+    tree = fmm.fmm_build_lists(None, 6, periodic=True)
+    Md = _dev(orc.scale_me(Ms[level], level))
+    Ld = Md.new_empty(Md.shape)
+    fmm.fmm_m2l(tree, level, p, Md, Ld)
+    _check(_host(Ld), _oracle_level(orc, level, p, Ms[level], periodic=True))
+
+
+def test_m2l_accumulate_and_empty_levels(fmm, orc, medium_particles):
+    import torch
+
+    xy, c = medium_particles
+    p = 8
+    Ms = orc.upward_uniform(4, p, xy, c)
+    tree = fmm.fmm_build_lists(None, 4)
+    level = 4
+    rng = np.random.default_rng(0)
+    X = (rng.standard_normal((256, p)) + 1j * rng.standard_normal((256, p))).astype(np.complex64)
+    Md = _dev(orc.scale_me(Ms[level], level))
+    Ld = _dev(X)
+    fmm.fmm_m2l(tree, level, p, Md, Ld, accumulate=True)
+    _check(_host(Ld), X.astype(np.complex128) + _oracle_level(orc, level, p, Ms[level]))
+    # levels 0 and 1 have empty interaction lists
+    for lv in (0, 1):
+        n = 4 ** lv
+        Mz = _dev(np.ones((n, p)))
+        Lz = _dev(np.full((n, p), 3.0))
+        fmm.fmm_m2l(tree, lv, p, Mz, Lz, accumulate=True)
+        assert np.all(_host(Lz) == 3.0)
+        fmm.fmm_m2l(tree, lv, p, Mz, Lz)
+        assert np.all(_host(Lz) == 0.0)
+    torch.cuda.synchronize()
+
+
+def test_m2l_is_deterministic(fmm, orc, medium_particles):
+    xy, c = medium_particles
+    p, level = 16, 5
+    Ms = orc.upward_uniform(level, p, xy, c)
+    tree = fmm.fmm_build_lists(None, level)
+    Md = _dev(orc.scale_me(Ms[level], level))
+    L1 = Md.new_empty(Md.shape)
+    L2 = Md.new_empty(Md.shape)
+    fmm.fmm_m2l(tree, level, p, Md, L1)
+    fmm.fmm_m2l(tree, level, p, Md, L2)
+    assert bool((L1 == L2).all())
+
+
+@pytest.mark.parametrize("conj", [False, True])
+@pytest.mark.parametrize("periodic", [False, True])
+@pytest.mark.parametrize("p,level", [(8, 3), (16, 5), (24, 4)])
+def test_m2l_adjoint(fmm, orc, p, level, conj, periodic):
+    """Scaled adjoint G~ = R_M A^T R_L W~  (R_M = diag r^k, R_L = diag r^(n+1)) against the
+    oracle's explicit transpose; with FMM_CONJ the conjugate transpose."""
+    rng = np.random.default_rng(level * 100 + p)
+    n = 4 ** level
+    W = rng.standard_normal((n, p)) + 1j * rng.standard_normal((n, p))
+    tree = fmm.fmm_build_lists(None, level, periodic=periodic)
+    Wd = _dev(W)
+    Gd = Wd.new_empty(Wd.shape)
+    fmm.fmm_m2l_adjoint(tree, level, p, Wd, Gd, conj=conj)
+    Win = np.conj(W) if conj else W
+    G = orc.unscale_me(orc.m2l_adjoint_uniform(level, p, orc.scale_le(Win, level), periodic), level)
+    if conj:
+        G = np.conj(G)
+    _check(_host(Gd), G)
+
+
+def test_upward_sweep_on_device(fmm, orc):
+    """fmm_p2m + fmm_m2m (FP32 atomics) against the oracle's P2M/M2M, scaled units."""
+    import torch
+
+    xy, c = workloads.uniform_particles(50000, np.random.default_rng(99))
+    p, L = 16, 6
+    Ms = orc.upward_uniform(L, p, xy, c)
+    xyd = torch.from_numpy(xy).cuda()
+    cd = torch.from_numpy(c).cuda()
+    Md = {L: torch.empty((4 ** L, p), dtype=torch.complex64, device="cuda")}
+    fmm.fmm_p2m(L, p, xyd, cd, Md[L])
+    for lv in range(L, 2, -1):
+        Md[lv - 1] = torch.empty((4 ** (lv - 1), p), dtype=torch.complex64, device="cuda")
+        fmm.fmm_m2m(lv, p, Md[lv], Md[lv - 1])
+    for lv in range(2, L + 1):
+        ref = orc.scale_me(Ms[lv], lv)
+        got = _host(Md[lv])
+        err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        assert err < 2e-6, (lv, err)
+
+
+@pytest.mark.slow
+def test_m2l_full_size_workload(fmm, orc):
+    """2^22 points, uniform tree to level 8, p = 16, one launch per level (the benchmark's
+    launch configuration): levels 2..7 compared in full, level 8 on sampled targets
+    (all four corners, edge boxes and random interior boxes)."""
+    cfg = workloads.CONFIGS["m2l_scale"]
+    p, L = cfg["p"], cfg["max_level"]
+    xy, c = workloads.uniform_particles(cfg["n"], workloads.rng_for("m2l_scale"))
+    Ms = orc.upward_uniform(L, p, xy, c)
+    tree = fmm.fmm_build_lists(None, L)
+    outs = {}
+    for level in workloads.m2l_levels(L):
+        Md = _dev(orc.scale_me(Ms[level], level))
+        Ld = Md.new_empty(Md.shape)
+        fmm.fmm_m2l(tree, level, p, Md, Ld)
+        outs[level] = Ld
+    fmm.fmm_sync_status()
+    for level in range(2, L):
+        _check(_host(outs[level]), _oracle_level(orc, level, p, Ms[level]))
+    n = 1 << L
+    rng = np.random.default_rng(1)
+    edge = [0, n - 1, n * (n - 1), n * n - 1, 1, n, 2 * n + 1, n * n - 2, (n // 2) * n]
+    targets = np.unique(np.concatenate([edge, rng.integers(0, n * n, 3000)]))
+    ref = orc.scale_le(orc.m2l_uniform_targets(L, p, Ms[L], targets), L)
+    _check(_host(outs[L])[targets], ref)
