@@ -43,8 +43,8 @@ METRIC = "M2L translations/s"
 UNIT = "translations/s"
 CONFIG = {
     "workload": "plain M2L at scale: 2^22 points U[0,1)^2, strengths U[-1,1], uniform quadtree to level 8, "
-                "p=16, FP32 complex coefficients, all interaction-list translations of levels 2-8, "
-                "one launch per level",
+                "p=16, FP32 complex coefficients, all interaction-list translations of levels 2-8 "
+                "(one multi-level launch; one-launch-per-level timing under rows)",
     "points": CFG["n"], "max_level": MAXL, "p": P, "translations_per_step": NTR,
     "levels": f"{LEVELS[0]}-{LEVELS[-1]}", "l2": "flushed between timed steps (256 MiB write)",
     "parallelism": "replicas",
@@ -164,6 +164,18 @@ def run_reference(args):
     return 0
 
 
+def _timed(torch, fn, steps, stream, flush):
+    """Per-step CUDA-event durations (ms) of fn() on `stream`, L2 flushed between steps."""
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        evs[i][0].record(stream)
+        fn()
+        evs[i][1].record(stream)
+        flush.zero_()
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
 def run_ours(args):
     import torch
 
@@ -187,21 +199,18 @@ def run_ours(args):
     tree = fmmgb.fmm_build_lists(None, MAXL)
     M = {l: torch.empty((4 ** l, P), dtype=torch.complex64, device=dev) for l in LEVELS}
     Lx = {l: torch.empty((4 ** l, P), dtype=torch.complex64, device=dev) for l in LEVELS}
+    G = {l: torch.empty((4 ** l, P), dtype=torch.complex64, device=dev) for l in LEVELS}
     fmmgb.fmm_p2m(MAXL, P, xyd, cd, M[MAXL])
     for l in range(MAXL, LEVELS[0], -1):
         fmmgb.fmm_m2m(l, P, M[l], M[l - 1])
     torch.cuda.synchronize()
     del xyd, cd
+    Ms = [M[l] for l in LEVELS]
+    Ls = [Lx[l] for l in LEVELS]
+    Gs = [G[l] for l in LEVELS]
 
-    order = sorted(LEVELS, reverse=True)  # biggest launch first: the host enqueues the rest meanwhile
-
-    def step(ev=None):
-        for l in order:
-            if ev is not None and l == MAXL:
-                ev[0].record(stream)
-            fmmgb.fmm_m2l(tree, l, P, M[l], Lx[l], stream=stream)
-            if ev is not None and l == MAXL:
-                ev[1].record(stream)
+    def step():  # the whole hot path: every translation of levels 2..8, reduction fused, one launch
+        fmmgb.fmm_m2l_levels(tree, LEVELS[0], P, Ms, Ls, stream=stream)
 
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     for _ in range(max(3, args.warmup)):
@@ -210,13 +219,13 @@ def run_ours(args):
     torch.cuda.synchronize()
     fmmgb.fmm_sync_status()
     if args.mode == "kernels":
-        # profiling case: the step's launches only (no e2e copies, no CPU baseline)
+        # profiling case: the step's launch only (no e2e copies, no CPU baseline, no other rows)
         for _ in range(args.steps):
             step()
         torch.cuda.synchronize()
         fmmgb.fmm_sync_status()
         if rank == 0:
-            print(json.dumps({"mode": "kernels", "steps": args.steps, "launches_per_step": len(LEVELS)}))
+            print(json.dumps({"mode": "kernels", "steps": args.steps, "launches_per_step": 1}))
         return 0
 
     # --- timed region: device-resident inputs ---
@@ -227,18 +236,9 @@ def run_ours(args):
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    kevs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    for i in range(args.steps):
-        evs[i][0].record(stream)
-        step(kevs[i])
-        evs[i][1].record(stream)
-        flush.zero_()
-    torch.cuda.synchronize()
+    step_ms = _timed(torch, step, args.steps, stream, flush)
     if ws > 1:
         dist.barrier()
-    step_ms = [a.elapsed_time(b) for a, b in evs]
-    k_ms = [a.elapsed_time(b) for a, b in kevs]
     tot_ms = sum(step_ms)
     if ws > 1:
         t = torch.tensor([tot_ms], device=dev)
@@ -246,7 +246,7 @@ def run_ours(args):
         tot_ms = float(t.item())
     value = ws * NTR * args.steps / (tot_ms * 1e-3)
 
-    # --- e2e: host buffers through the same public calls ---
+    # --- e2e: host buffers through the same public call ---
     Mh = {l: torch.empty_like(M[l], device="cpu").pin_memory() for l in LEVELS}
     Lh = {l: torch.empty_like(Lx[l], device="cpu").pin_memory() for l in LEVELS}
     for l in LEVELS:
@@ -255,7 +255,7 @@ def run_ours(args):
     d2h = sum(Lx[l].numel() * 8 for l in LEVELS)
 
     def e2e_step():
-        for l in order:
+        for l in LEVELS:
             M[l].copy_(Mh[l], non_blocking=True)
         step()
         for l in LEVELS:
@@ -265,27 +265,61 @@ def run_ours(args):
         e2e_step()
         flush.zero_()
     torch.cuda.synchronize()
-    eevs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    for i in range(args.steps):
-        eevs[i][0].record(stream)
-        e2e_step()
-        eevs[i][1].record(stream)
-        flush.zero_()
-    torch.cuda.synchronize()
-    clocks = clk.stop() if rank == 0 else None
-    fmmgb.fmm_sync_status()
-    e2e_ms = sum(a.elapsed_time(b) for a, b in eevs)
+    e2e_ms = sum(_timed(torch, e2e_step, args.steps, stream, flush))
     if ws > 1:
         t = torch.tensor([e2e_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_ms = float(t.item())
     e2e_value = ws * NTR * args.steps / (e2e_ms * 1e-3)
+    clocks = clk.stop() if rank == 0 else None
+
+    # --- the other rows of the hot path, same device-resident protocol ---
+    rows = {}
+    if rank == 0 and not args.no_rows:
+        def per_level():
+            for l in sorted(LEVELS, reverse=True):
+                fmmgb.fmm_m2l(tree, l, P, M[l], Lx[l], stream=stream)
+
+        def adjoint():
+            fmmgb.fmm_m2l_adjoint_levels(tree, LEVELS[0], P, Ls, Gs, conj=True, stream=stream)
+
+        for name, fn, launches in (("m2l_fp32_one_launch_per_level", per_level, len(LEVELS)),
+                                   ("m2l_adjoint_fp32_levels_2_8", adjoint, 1)):
+            fn()
+            torch.cuda.synchronize()
+            ms = statistics.median(_timed(torch, fn, args.steps, stream, flush))
+            rows[name] = {"translations_per_s": NTR / (ms * 1e-3), "ms": ms, "launches": launches,
+                          "gflops": NTR * metrics.m2l_flops_per_translation(P) / (ms * 1e-3) / 1e9}
+        fcfg = workloads.CONFIGS["fgt"]
+        fx, fq = workloads.gmm_particles(fcfg["n"], workloads.rng_for("fgt"))
+        fxd = torch.from_numpy(fx).to(dev)
+        fqd = torch.from_numpy(fq).to(dev)
+        for sigma in fcfg["sigmas"]:
+            for fp in fcfg["orders"]:
+                g = workloads.fgt_grid_log2(sigma)
+                A = torch.empty((4 ** g, fp, fp), dtype=torch.float32, device=dev)
+                Cf = torch.empty_like(A)
+                W = torch.empty_like(A)
+                fmmgb.fgt_p2h(g, fp, sigma, fxd, fqd, A)
+
+                def fgt():
+                    fmmgb.fgt_h2t(g, fcfg["ncut"], fp, sigma, A, Cf, work=W, stream=stream)
+
+                fgt()
+                torch.cuda.synchronize()
+                ms = statistics.median(_timed(torch, fgt, args.steps, stream, flush))
+                ntr = metrics.fgt_translations(g, fcfg["ncut"])
+                taps = 2 * fcfg["ncut"] + 1
+                rows[f"fgt_h2t_sigma{sigma}_p{fp}"] = {
+                    "translations_per_s": ntr / (ms * 1e-3), "ms": ms, "launches": 2, "grid": f"{1 << g}^2",
+                    "gflops_separable": (4 ** g) * metrics.fgt_flops_per_box_separable(fp, taps, taps)
+                    / (ms * 1e-3) / 1e9}
+        fmmgb.fmm_sync_status()
 
     if rank == 0:
-        ntr8 = metrics.uniform_translations(MAXL)
-        flops8 = ntr8 * metrics.m2l_flops_per_translation(P)
-        k_avg_s = statistics.mean(k_ms) * 1e-3
-        achieved = flops8 / k_avg_s / 1e12
+        flops = NTR * metrics.m2l_flops_per_translation(P)
+        k_avg_s = statistics.mean(step_ms) * 1e-3
+        achieved = flops / k_avg_s / 1e12
         peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -294,16 +328,17 @@ def run_ours(args):
             "paper_gops": value * metrics.paper_ops_per_translation(P) / 1e9,
             "executed_gflops": value * metrics.m2l_flops_per_translation(P) / 1e9,
             "roofline": {
-                "bound": "alu", "kernel": "m2l_fp32_uniform_kernel<16> (level 8)", "achieved": achieved,
+                "bound": "alu", "kernel": "m2l_fp32_kernel<16> (levels 2-8, one launch)", "achieved": achieved,
                 "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (max SM clock)",
-                "flops_per_launch": flops8, "launch_ms": statistics.mean(k_ms),
+                "flops_per_launch": flops, "launch_ms": statistics.mean(step_ms),
                 "frac_at_sampled_clock": (achieved / (peak * clocks["sm_mhz"] / SM_MAX_MHZ))
                 if clocks and clocks.get("sm_mhz") else None,
             },
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": len(LEVELS) * args.steps,
+            "gpu_launches": args.steps,
             "clocks": clocks,
+            "rows": rows,
         }
         if not args.no_cpu_baseline and ws == 1:
             v, dt, ntr = cpu_baseline_run()
@@ -323,6 +358,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-rows", action="store_true", help="skip the adjoint / per-level / FGT rows")
     ap.add_argument("--mode", default="full", choices=["full", "kernels"],
                     help="kernels: only the timed step's launches (for ncu captures)")
     args = ap.parse_args()

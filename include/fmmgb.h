@@ -149,6 +149,13 @@ int fmm_prepare(int32_t p, int32_t prec);
 int fmm_m2l(const fmm_tree* tree, int32_t level, int32_t p, int32_t prec,
             const void* M, void* L, int32_t flags, void* stream);
 
+/* fmm_m2l_levels -- fmm_m2l for every level lmin..lmax in ONE launch (the
+ * levels are independent given their MEs).  M[i], L[i] are the arrays of
+ * level lmin + i (host array of device pointers, read during the call).
+ * Equivalent to lmax - lmin + 1 calls of fmm_m2l. */
+int fmm_m2l_levels(const fmm_tree* tree, int32_t lmin, int32_t lmax, int32_t p, int32_t prec,
+                   const void* const* M, void* const* L, int32_t flags, void* stream);
+
 /* ---------------------------------------------------------------------------
  * fmm_m2l_adjoint -- transpose of fmm_m2l on the same lists:
  *     G~_s[k] (+)= sum_{t : s in IL(t)} sum_n a_nk W~_t[n]       (plain transpose)
@@ -161,6 +168,36 @@ int fmm_m2l(const fmm_tree* tree, int32_t level, int32_t p, int32_t prec,
  * ------------------------------------------------------------------------- */
 int fmm_m2l_adjoint(const fmm_tree* tree, int32_t level, int32_t p, int32_t prec,
                     const void* W, void* G, int32_t flags, void* stream);
+
+/* fmm_m2l_adjoint over levels lmin..lmax in one launch (as fmm_m2l_levels). */
+int fmm_m2l_adjoint_levels(const fmm_tree* tree, int32_t lmin, int32_t lmax, int32_t p, int32_t prec,
+                           const void* const* W, void* const* G, int32_t flags, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * fgt_h2t -- Hermite-to-Taylor translation of the fast Gauss transform over
+ * a uniform grid of 2^g x 2^g boxes on [0,1)^2 (Sec. 2.2, Eq. C_beta, with
+ * the factor (-1)^|beta| / beta! that the printed equation omits):
+ *   C_t[b1][b2] (+)= sum_{s : max(|sx-tx|,|sy-ty|) <= n_cut}
+ *        ((-1)^(b1+b2) / (b1! b2!)) sum_{a1,a2 < p} A_s[a1][a2] h_{a1+b1}(u1) h_{a2+b2}(u2),
+ *   u = (t_C - s_B) / (sqrt(2) sigma),  h_n(t) = exp(-t^2) H_n(t)  (Hermite
+ *   functions, Sec. 2.2), tensor truncation a_i, b_i < p.
+ *
+ *   grid_log2  g, 0..12; box b = iy * 2^g + ix, centre ((ix+1/2) 2^-g, (iy+1/2) 2^-g).
+ *   n_cut      neighbourhood half-width in boxes, 0..16.
+ *   p          Hermite order per dimension: 4, 8, 12 or 16.
+ *   sigma      Gaussian width (exp(-|x-y|^2 / (2 sigma^2))), > 0.
+ *   A          device, const, [4^g][p][p] float32 Hermite coefficients
+ *              A[b][a1][a2] (a1: x order, a2: y order), Eq. A_alpha.
+ *   C          device, [4^g][p][p] float32 Taylor coefficients C[b][b1][b2].
+ *   work       device scratch of 4^g p^2 floats, or NULL to use a
+ *              library-owned per-device buffer (allocated on first use of a
+ *              size; concurrent calls on different streams must then not
+ *              overlap on the GPU).  Must not overlap A or C.
+ *   flags      FMM_ACCUMULATE or 0.
+ * All pointers 16-byte aligned; A and C must not overlap.
+ * ------------------------------------------------------------------------- */
+int fgt_h2t(int32_t grid_log2, int32_t n_cut, int32_t p, double sigma, const float* A, float* C,
+            float* work, int32_t flags, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Support for building M2L inputs on the device (upward sweep, Sec. 2.1
@@ -177,6 +214,14 @@ int fmm_m2l_adjoint(const fmm_tree* tree, int32_t level, int32_t p, int32_t prec
 int fmm_p2m(int32_t level, int32_t p, const double* xy, const double* c, int64_t n,
             void* M, int32_t flags, void* stream);
 int fmm_m2m(int32_t child_level, int32_t p, const void* Mc, void* Mp, int32_t flags, void* stream);
+
+/* fgt_p2h: FGT Hermite coefficients of every box of a 2^g grid (Eq. A_alpha),
+ *   A_b[a1][a2] (+)= sum_{j in box b} q_j t1^a1 t2^a2 / (a1! a2!),
+ *   t = (x_j - s_b) / (sqrt(2) sigma), s_b the box centre, a1, a2 < p.
+ *   x: device float64 [n][2]; q: device float64 [n]; A: device float32
+ *   [4^g][p][p].  FP32 atomic additions.  flags: FMM_ACCUMULATE or 0. */
+int fgt_p2h(int32_t grid_log2, int32_t p, double sigma, const double* x, const double* q, int64_t n,
+            float* A, int32_t flags, void* stream);
 
 /* Read and clear the device error word after synchronising `stream`.
  * Returns FMM_OK, FMM_ETIMEOUT or FMM_EDEVICE. */

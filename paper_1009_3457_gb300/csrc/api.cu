@@ -63,6 +63,8 @@ void class_stencil(int cls, StencilEntry out[27])
 struct DeviceState {
     int* err_word = nullptr;
     std::map<int, M2LTables*> m2l;
+    float* fgt_ws = nullptr;  // FGT H2T intermediate (grown on demand)
+    size_t fgt_ws_bytes = 0;
 };
 static std::mutex g_mu;
 static std::map<int, DeviceState*> g_dev;
@@ -96,6 +98,26 @@ int device_error_word(int** out)
     int rc = current_state(&s);
     if (rc) return rc;
     *out = s->err_word;
+    return FMM_OK;
+}
+
+int fgt_workspace(size_t bytes, float** out)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    DeviceState* s = nullptr;
+    int rc = current_state(&s);
+    if (rc) return rc;
+    if (s->fgt_ws_bytes < bytes) {
+        if (s->fgt_ws) {
+            FMM_CUDA_TRY(cudaDeviceSynchronize());
+            cudaFree(s->fgt_ws);
+            s->fgt_ws = nullptr;
+            s->fgt_ws_bytes = 0;
+        }
+        FMM_CUDA_TRY(cudaMalloc(&s->fgt_ws, bytes));
+        s->fgt_ws_bytes = bytes;
+    }
+    *out = s->fgt_ws;
     return FMM_OK;
 }
 
@@ -320,23 +342,67 @@ static int m2l_common(const char* who, const fmm_tree* tree, int32_t level, int3
     return FMM_OK;
 }
 
+// One launch over levels lmin..lmax (heaviest first) of the forward or adjoint stencil.
+static int m2l_dispatch(const char* who, const fmm_tree* tree, int32_t lmin, int32_t lmax, int32_t p, int32_t prec,
+                        const void* const* in, void* const* out, int32_t flags, bool adjoint, void* stream)
+{
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool acc = (flags & FMM_ACCUMULATE) != 0;
+    for (int l = lmin; l <= lmax && l < 2; ++l)
+        if (!acc) FMM_CUDA_TRY(cudaMemsetAsync(out[l - lmin], 0, ((size_t)1 << (2 * l)) * (size_t)p * 8, st));
+    if (lmax < 2) return FMM_OK;
+    if (prec != FMM_FP32)
+        return fail(FMM_EUNSUPPORTED, "%s: tensor-core precision %d is not provided for this call", who, prec);
+    const M2LTables* t = nullptr;
+    int rc = get_m2l_tables(p, &t);
+    if (rc) return rc;
+    M2LLaunch job{};
+    job.periodic = tree->periodic;
+    job.accumulate = acc ? 1 : 0;
+    for (int l = lmax; l >= lmin && l >= 2; --l) {
+        M2LLevel& d = job.lv[job.nlev++];
+        d.M = (const float2*)in[l - lmin];
+        d.L = (float2*)out[l - lmin];
+        d.level = l;
+    }
+    // The adjoint is the forward stencil with the table of -a(D) (plain) or
+    // -conj a(D) (FMM_CONJ): a(D)^T = -a(-D) on symmetric lists.
+    const float2* h = !adjoint ? t->h_fwd : ((flags & FMM_CONJ) ? t->h_adjc : t->h_adj);
+    return launch_m2l_fp32(job, p, h, t->a, t->b, st);
+}
+
+static int levels_common(const char* who, const fmm_tree* tree, int32_t lmin, int32_t lmax, int32_t p, int32_t prec,
+                         const void* const* in, void* const* out, int32_t flags, int32_t allowed)
+{
+    if (!tree) return fail(FMM_EINVAL, "%s: tree is NULL", who);
+    if (!in || !out) return fail(FMM_EINVAL, "%s: NULL pointer array", who);
+    if (lmin < 0 || lmax > tree->max_level || lmin > lmax)
+        return fail(FMM_EINVAL, "%s: levels %d..%d outside 0..%d", who, lmin, lmax, tree->max_level);
+    for (int l = lmin; l <= lmax; ++l) {
+        int rc = m2l_common(who, tree, l, p, prec, in[l - lmin], out[l - lmin], flags, allowed);
+        if (rc) return rc;
+    }
+    return FMM_OK;
+}
+
 int fmm_m2l(const fmm_tree* tree, int32_t level, int32_t p, int32_t prec, const void* M, void* L, int32_t flags,
             void* stream)
 {
     clear_error();
     int rc = m2l_common("fmm_m2l", tree, level, p, prec, M, L, flags, FMM_ACCUMULATE);
     if (rc) return rc;
-    cudaStream_t st = (cudaStream_t)stream;
-    const bool acc = (flags & FMM_ACCUMULATE) != 0;
-    if (level < 2) {
-        if (!acc) FMM_CUDA_TRY(cudaMemsetAsync(L, 0, ((size_t)1 << (2 * level)) * (size_t)p * 8, st));
-        return FMM_OK;
-    }
-    if (prec != FMM_FP32) return fail(FMM_EUNSUPPORTED, "fmm_m2l: tensor-core precision %d not provided by this build", prec);
-    const M2LTables* t = nullptr;
-    if ((rc = get_m2l_tables(p, &t))) return rc;
-    return launch_m2l_fp32_uniform(level, p, t->h_fwd, t->a, t->b, (const float2*)M, (float2*)L, acc,
-                                   tree->periodic != 0, st);
+    const void* in[1] = {M};
+    void* out[1] = {L};
+    return m2l_dispatch("fmm_m2l", tree, level, level, p, prec, in, out, flags, false, stream);
+}
+
+int fmm_m2l_levels(const fmm_tree* tree, int32_t lmin, int32_t lmax, int32_t p, int32_t prec, const void* const* M,
+                   void* const* L, int32_t flags, void* stream)
+{
+    clear_error();
+    int rc = levels_common("fmm_m2l_levels", tree, lmin, lmax, p, prec, M, L, flags, FMM_ACCUMULATE);
+    if (rc) return rc;
+    return m2l_dispatch("fmm_m2l_levels", tree, lmin, lmax, p, prec, M, L, flags, false, stream);
 }
 
 int fmm_m2l_adjoint(const fmm_tree* tree, int32_t level, int32_t p, int32_t prec, const void* W, void* G,
@@ -346,20 +412,20 @@ int fmm_m2l_adjoint(const fmm_tree* tree, int32_t level, int32_t p, int32_t prec
     int rc = m2l_common("fmm_m2l_adjoint", tree, level, p, prec, W, G, flags, FMM_ACCUMULATE | FMM_CONJ);
     if (rc) return rc;
     if (prec != FMM_FP32) return fail(FMM_EUNSUPPORTED, "fmm_m2l_adjoint: only FMM_FP32 is provided");
-    cudaStream_t st = (cudaStream_t)stream;
-    const bool acc = (flags & FMM_ACCUMULATE) != 0;
-    if (level < 2) {
-        if (!acc) FMM_CUDA_TRY(cudaMemsetAsync(G, 0, ((size_t)1 << (2 * level)) * (size_t)p * 8, st));
-        return FMM_OK;
-    }
-    const M2LTables* t = nullptr;
-    if ((rc = get_m2l_tables(p, &t))) return rc;
-    // Transpose by the identity a(D)^T = -a(-D) on symmetric lists: the
-    // adjoint is the forward stencil with the negated (and, for FMM_CONJ,
-    // conjugated) operator table.
-    const float2* h = (flags & FMM_CONJ) ? t->h_adjc : t->h_adj;
-    return launch_m2l_fp32_uniform(level, p, h, t->a, t->b, (const float2*)W, (float2*)G, acc, tree->periodic != 0,
-                                   st);
+    const void* in[1] = {W};
+    void* out[1] = {G};
+    return m2l_dispatch("fmm_m2l_adjoint", tree, level, level, p, prec, in, out, flags, true, stream);
+}
+
+int fmm_m2l_adjoint_levels(const fmm_tree* tree, int32_t lmin, int32_t lmax, int32_t p, int32_t prec,
+                           const void* const* W, void* const* G, int32_t flags, void* stream)
+{
+    clear_error();
+    int rc = levels_common("fmm_m2l_adjoint_levels", tree, lmin, lmax, p, prec, W, G, flags,
+                           FMM_ACCUMULATE | FMM_CONJ);
+    if (rc) return rc;
+    if (prec != FMM_FP32) return fail(FMM_EUNSUPPORTED, "fmm_m2l_adjoint_levels: only FMM_FP32 is provided");
+    return m2l_dispatch("fmm_m2l_adjoint_levels", tree, lmin, lmax, p, prec, W, G, flags, true, stream);
 }
 
 int fmm_p2m(int32_t level, int32_t p, const double* xy, const double* c, int64_t n, void* M, int32_t flags,
@@ -384,6 +450,48 @@ int fmm_m2m(int32_t child_level, int32_t p, const void* Mc, void* Mp, int32_t fl
     if (flags & ~FMM_ACCUMULATE) return fail(FMM_EINVAL, "fmm_m2m: unknown flags 0x%x", flags);
     return launch_m2m(child_level, p, (const float2*)Mc, (float2*)Mp, (flags & FMM_ACCUMULATE) != 0,
                       (cudaStream_t)stream);
+}
+
+int fgt_h2t(int32_t grid_log2, int32_t n_cut, int32_t p, double sigma, const float* A, float* C, float* work,
+            int32_t flags, void* stream)
+{
+    clear_error();
+    if (grid_log2 < 0 || grid_log2 > 12) return fail(FMM_EINVAL, "fgt_h2t: grid_log2 %d outside 0..12", grid_log2);
+    if (n_cut < 0 || n_cut > fgt_max_cut())
+        return fail(FMM_EINVAL, "fgt_h2t: n_cut %d outside 0..%d", n_cut, fgt_max_cut());
+    if (!fgt_supported(p)) return fail(FMM_EINVAL, "fgt_h2t: unsupported p = %d (4, 8, 12, 16)", p);
+    if (!(sigma > 0.0) || !(sigma < 1e300)) return fail(FMM_EINVAL, "fgt_h2t: sigma must be positive and finite");
+    if (!A || !C) return fail(FMM_EINVAL, "fgt_h2t: NULL coefficient pointer");
+    if (((uintptr_t)A & 15) || ((uintptr_t)C & 15) || ((uintptr_t)work & 15))
+        return fail(FMM_EINVAL, "fgt_h2t: pointers must be 16-byte aligned");
+    if (flags & ~FMM_ACCUMULATE) return fail(FMM_EINVAL, "fgt_h2t: unknown flags 0x%x", flags);
+    const size_t bytes = ((size_t)1 << (2 * grid_log2)) * (size_t)p * p * sizeof(float);
+    const char* a = (const char*)A;
+    const char* c = (const char*)C;
+    if (a < c + bytes && c < a + bytes) return fail(FMM_EINVAL, "fgt_h2t: A and C overlap");
+    float* Y = work;
+    if (!Y) {
+        int rc = fgt_workspace(bytes, &Y);
+        if (rc) return rc;
+    } else {
+        const char* w = (const char*)work;
+        if ((w < a + bytes && a < w + bytes) || (w < c + bytes && c < w + bytes))
+            return fail(FMM_EINVAL, "fgt_h2t: work overlaps A or C");
+    }
+    return launch_fgt_h2t(grid_log2, n_cut, p, sigma, A, Y, C, (flags & FMM_ACCUMULATE) != 0, (cudaStream_t)stream);
+}
+
+int fgt_p2h(int32_t grid_log2, int32_t p, double sigma, const double* x, const double* q, int64_t n, float* A,
+            int32_t flags, void* stream)
+{
+    clear_error();
+    if (grid_log2 < 0 || grid_log2 > 12) return fail(FMM_EINVAL, "fgt_p2h: grid_log2 %d outside 0..12", grid_log2);
+    if (p < 1 || p > 32) return fail(FMM_EINVAL, "fgt_p2h: p = %d outside 1..32", p);
+    if (!(sigma > 0.0) || !(sigma < 1e300)) return fail(FMM_EINVAL, "fgt_p2h: sigma must be positive and finite");
+    if (n < 0) return fail(FMM_EINVAL, "fgt_p2h: n < 0");
+    if (!A || (n > 0 && (!x || !q))) return fail(FMM_EINVAL, "fgt_p2h: NULL pointer");
+    if (flags & ~FMM_ACCUMULATE) return fail(FMM_EINVAL, "fgt_p2h: unknown flags 0x%x", flags);
+    return launch_fgt_p2h(grid_log2, p, sigma, x, q, n, A, (flags & FMM_ACCUMULATE) != 0, (cudaStream_t)stream);
 }
 
 int fmm_sync_status(void* stream)

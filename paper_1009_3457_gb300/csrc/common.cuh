@@ -68,15 +68,39 @@ struct M2LTables {
 int get_m2l_tables(int p, const M2LTables** out);
 double m2l_balance(int p);
 
+// One launch of the M2L stencil over several uniform levels (kernel parameter).
+struct M2LLevel {
+    const float2* M;   // [4^level][p] scaled MEs
+    float2* L;         // [4^level][p] scaled LEs
+    int level;
+    int tile_begin;    // first CTA of this level (filled by the launcher)
+};
+constexpr int kMaxLaunchLevels = FMM_MAX_LEVEL + 1;
+struct M2LLaunch {
+    M2LLevel lv[kMaxLaunchLevels];
+    int nlev;
+    int periodic;
+    int accumulate;
+};
+
 // launchers (m2l_fp32.cu)
 int launch_build_m2l_tables(const M2LTables& t, cudaStream_t st);
 bool m2l_fp32_supported(int p);
-int launch_m2l_fp32_uniform(int level, int p, const float2* hsel, const float* a, const float* b,
-                            const float2* M, float2* L, bool accumulate, bool periodic, cudaStream_t st);
+int m2l_tiles(int level);
+int launch_m2l_fp32(M2LLaunch& job, int p, const float2* hsel, const float* a, const float* b, cudaStream_t st);
+
+// launchers (fgt_h2t.cu)
+bool fgt_supported(int p);
+int fgt_max_cut();
+int launch_fgt_h2t(int g, int ncut, int p, double sigma, const float* A, float* Y, float* C, bool acc,
+                   cudaStream_t st);
+int fgt_workspace(size_t bytes, float** out);
 
 // launchers (upward.cu)
 int launch_p2m(int level, int p, const double* xy, const double* c, int64_t n, float2* M, bool accumulate,
                cudaStream_t st);
 int launch_m2m(int child_level, int p, const float2* Mc, float2* Mp, bool accumulate, cudaStream_t st);
+int launch_fgt_p2h(int g, int p, double sigma, const double* x, const double* q, int64_t n, float* A, bool acc,
+                   cudaStream_t st);
 
 }  // namespace fmmgb

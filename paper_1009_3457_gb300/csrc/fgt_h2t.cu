@@ -1,0 +1,191 @@
+// fgt_h2t.cu -- FGT Hermite-to-Taylor translation over a uniform box grid
+// (Sec. 2.2, Eq. C_beta with the factor (-1)^|beta| / beta!):
+//
+//   C_t[b1][b2] = sum_{s : max(|sx-tx|, |sy-ty|) <= n_cut}
+//                 ((-1)^(b1+b2) / (b1! b2!)) sum_{a1,a2} A_s[a1][a2] h_{a1+b1}(u1) h_{a2+b2}(u2),
+//   u = (t_C - s_B) / (sqrt(2) sigma),  h_n(t) = exp(-t^2) H_n(t).
+//
+// In 2-D with tensor truncation the kernel factorises: h_{a+b}(u) is a Hankel
+// matrix H(u) per axis, and the neighbourhood is a square, so the sum over
+// source boxes splits into two 1-D stencils along x and y:
+//
+//   Y[x,y]  = S H-pass along x:  Y[b1][a2] = s_b1 sum_{dx} sum_{a1} h_{a1+b1}(u(dx)) A[x+dx, y][a1][a2]
+//   C[x,y]  = S H-pass along y:  C[b1][b2] = s_b2 sum_{dy} sum_{a2} h_{a2+b2}(u(dy)) Y[x, y+dy][b1][a2]
+//
+// (s_b = (-1)^b / b!), which costs 2 (2 n_cut + 1) p^3 multiply-adds per box
+// instead of (2 n_cut + 1)^2 2 p^3 for the box-pair form -- the same result up
+// to rounding order.  Both passes run the same stencil kernel: out[box] =
+// diag(s) sum_d H_d^T in[box + d e_axis], written transposed so that the second
+// pass contracts the other Hermite index.  The intermediate Y is library-owned
+// scratch (one [4^g][p][p] float buffer per device, grown on demand).
+#include <math.h>
+
+#include <mutex>
+
+#include "common.cuh"
+
+namespace fmmgb {
+
+constexpr int kFgtSeg = 32;      // boxes per CTA along the pass axis
+constexpr int kFgtMaxCut = 16;   // largest n_cut accepted
+
+template <int P>
+struct FgtCfg {
+    static constexpr int RB = P / 2;            // rows (b) per thread
+    static constexpr int CB = P / 4;            // column blocks of 4 per box
+    static constexpr int TPB = 2 * CB;          // threads per box
+    static constexpr int THREADS = kFgtSeg * TPB;
+    static constexpr int NH = 2 * P - 1;
+    static constexpr int BS = P * P + 16;       // padded float stride between boxes in shared memory
+};
+
+template <int P>
+size_t fgt_smem_bytes(int ncut)
+{
+    using C = FgtCfg<P>;
+    return sizeof(float) * ((size_t)(kFgtSeg + 2 * ncut) * C::BS + (size_t)(2 * ncut + 1) * C::NH + P);
+}
+
+template <int P>
+__global__ void __launch_bounds__(FgtCfg<P>::THREADS) fgt_pass_kernel(int g, int ncut, double ustep, int axis,
+                                                                      const float* __restrict__ in,
+                                                                      float* __restrict__ out, int accumulate)
+{
+    using C = FgtCfg<P>;
+    constexpr int RB = C::RB, NH = C::NH, BS = C::BS;
+    extern __shared__ __align__(16) float fsm[];
+    const int taps = 2 * ncut + 1;
+    float* halo = fsm;                                   // [kFgtSeg + 2 ncut][BS]
+    float* hs = halo + (size_t)(kFgtSeg + 2 * ncut) * BS;  // [taps][NH]
+    float* ss = hs + taps * NH;                          // [P]
+
+    const int side = 1 << g;
+    const int seg0 = blockIdx.x * kFgtSeg;
+    const int other = blockIdx.y;
+    const int tid = threadIdx.x;
+
+    // Hermite-function table h_j(u_d), u_d = -(d - ncut) * ustep  (source offset d - ncut),
+    // by the recurrence h_{j+1} = 2u h_j - 2j h_{j-1}, in FP64.
+    for (int d = tid; d < taps; d += blockDim.x) {
+        const double u = -(double)(d - ncut) * ustep;
+        double hm = exp(-u * u), h = 2.0 * u * hm;
+        hs[d * NH + 0] = (float)hm;
+        if (NH > 1) hs[d * NH + 1] = (float)h;
+        for (int j = 1; j + 1 < NH; ++j) {
+            const double hn = 2.0 * u * h - 2.0 * (double)j * hm;
+            hm = h;
+            h = hn;
+            hs[d * NH + j + 1] = (float)h;
+        }
+    }
+    for (int b = tid; b < P; b += blockDim.x) {
+        double f = 1.0;
+        for (int i = 2; i <= b; ++i) f *= (double)i;
+        ss[b] = (float)(((b & 1) ? -1.0 : 1.0) / f);
+    }
+    // stage the boxes [seg0 - ncut, seg0 + kFgtSeg + ncut) of this row/column, zero outside the grid
+    const int nhb = kFgtSeg + 2 * ncut;
+    const float4* in4 = reinterpret_cast<const float4*>(in);
+    for (int i = tid; i < nhb * (P * P / 4); i += blockDim.x) {
+        const int q = i % (P * P / 4), hb = i / (P * P / 4);
+        const int pos = seg0 - ncut + hb;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (pos >= 0 && pos < side) {
+            const size_t box = axis == 0 ? (size_t)other * side + pos : (size_t)pos * side + other;
+            v = __ldg(in4 + box * (P * P / 4) + q);
+        }
+        *reinterpret_cast<float4*>(halo + (size_t)hb * BS + 4 * q) = v;
+    }
+    __syncthreads();
+
+    const int j = tid / C::TPB;              // box within the segment
+    const int r = tid % C::TPB;
+    const int b0 = (r & 1) * RB;             // first output row
+    const int c0 = (r >> 1) * 4;             // first of 4 columns
+    const int pos = seg0 + j;
+    if (pos >= side) return;
+
+    float acc[RB][4];
+#pragma unroll
+    for (int i = 0; i < RB; ++i)
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) acc[i][cc] = 0.f;
+
+    for (int d = 0; d < taps; ++d) {
+        const int spos = pos + d - ncut;
+        if (spos < 0 || spos >= side) continue;
+        const float* hrow = hs + d * NH + b0;
+        const float* src = halo + (size_t)(j + d) * BS + c0;
+        float w[RB];
+#pragma unroll
+        for (int i = 0; i < RB; ++i) w[i] = hrow[i];
+#pragma unroll
+        for (int a = 0; a < P; ++a) {
+            const float4 v = *reinterpret_cast<const float4*>(src + a * P);
+#pragma unroll
+            for (int i = 0; i < RB; ++i) {
+                acc[i][0] = fmaf(w[i], v.x, acc[i][0]);
+                acc[i][1] = fmaf(w[i], v.y, acc[i][1]);
+                acc[i][2] = fmaf(w[i], v.z, acc[i][2]);
+                acc[i][3] = fmaf(w[i], v.w, acc[i][3]);
+            }
+            if (a + 1 < P) {
+#pragma unroll
+                for (int i = 0; i + 1 < RB; ++i) w[i] = w[i + 1];
+                w[RB - 1] = hrow[RB + a];
+            }
+        }
+    }
+    // transposed store: out[box][c][b] = s_b acc[b][c]
+    const size_t box = axis == 0 ? (size_t)other * side + pos : (size_t)pos * side + other;
+    float* dst = out + box * (P * P);
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) {
+        float* row = dst + (size_t)(c0 + cc) * P + b0;
+#pragma unroll
+        for (int i = 0; i < RB; i += 2) {
+            float2 o = make_float2(ss[b0 + i] * acc[i][cc], ss[b0 + i + 1] * acc[i + 1][cc]);
+            if (accumulate) {
+                const float2 old = *reinterpret_cast<const float2*>(row + i);
+                o.x += old.x;
+                o.y += old.y;
+            }
+            *reinterpret_cast<float2*>(row + i) = o;
+        }
+    }
+}
+
+bool fgt_supported(int p) { return p == 4 || p == 8 || p == 12 || p == 16; }
+
+template <int P>
+static int fgt_launch(int g, int ncut, double ustep, const float* A, float* Y, float* Cout, bool acc,
+                      cudaStream_t st)
+{
+    using C = FgtCfg<P>;
+    const int side = 1 << g;
+    const size_t smem = fgt_smem_bytes<P>(ncut);
+    FMM_CUDA_TRY(cudaFuncSetAttribute(fgt_pass_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const dim3 grid((side + kFgtSeg - 1) / kFgtSeg, side);
+    fgt_pass_kernel<P><<<grid, C::THREADS, smem, st>>>(g, ncut, ustep, 0, A, Y, 0);
+    FMM_CUDA_TRY(cudaGetLastError());
+    fgt_pass_kernel<P><<<grid, C::THREADS, smem, st>>>(g, ncut, ustep, 1, Y, Cout, acc ? 1 : 0);
+    FMM_CUDA_TRY(cudaGetLastError());
+    return FMM_OK;
+}
+
+int launch_fgt_h2t(int g, int ncut, int p, double sigma, const float* A, float* Y, float* Cout, bool acc,
+                   cudaStream_t st)
+{
+    const double ustep = ldexp(1.0, -g) / (sqrt(2.0) * sigma);
+    switch (p) {
+        case 4: return fgt_launch<4>(g, ncut, ustep, A, Y, Cout, acc, st);
+        case 8: return fgt_launch<8>(g, ncut, ustep, A, Y, Cout, acc, st);
+        case 12: return fgt_launch<12>(g, ncut, ustep, A, Y, Cout, acc, st);
+        case 16: return fgt_launch<16>(g, ncut, ustep, A, Y, Cout, acc, st);
+        default: return fail(FMM_EINVAL, "fgt_h2t: unsupported p = %d", p);
+    }
+}
+
+int fgt_max_cut() { return kFgtMaxCut; }
+
+}  // namespace fmmgb

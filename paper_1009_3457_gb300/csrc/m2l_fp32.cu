@@ -1,5 +1,6 @@
-// m2l_fp32.cu -- FP32 M2L with the reduction fused in, on a uniform quadtree
-// level (Sec. 4.1 steps 2-3, Eq. M2Lmat), plus the FP64 operator-table builder.
+// m2l_fp32.cu -- FP32 M2L with the reduction fused in, over one or several
+// levels of a uniform quadtree in one launch (Sec. 4.1 steps 2-3, Eq. M2Lmat),
+// plus the FP64 operator-table builder.
 //
 // Formulation (radius-scaled units, D = (x_t - x_s)/r a complex integer):
 //   L~_t[n] = sum_{s in IL(t)} sum_k a_n h_D[n+k] b_k M~_s[k]
@@ -7,26 +8,28 @@
 // so each translation is a Hankel matrix-vector product between two diagonal
 // scalings that do not depend on the offset: b_k is applied once per source
 // box while it is staged into shared memory, a_n once per target box at the
-// store.  The Hankel structure means a thread that owns RN consecutive rows
-// n0..n0+RN-1 needs only one new operator value h[n0+RN+k] per k (a sliding
+// store.  Because the matrix is Hankel, a thread that owns RN consecutive
+// rows n0..n0+RN-1 needs one new operator value h[n0+RN+k] per k (a sliding
 // register window) instead of a column of the p x p matrix.
 //
-// Work decomposition (GB300-first, replaces the paper's thread-per-row,
+// Work decomposition (GB300-first; replaces the paper's thread-per-row,
 // source-centric kernel and its separate reduction kernel, Sec. 4.1.1):
-//   - a CTA owns an 8 x 8 tile of parent boxes = 256 target boxes; the 10 x 10
-//     parent halo (the tile's parents and their neighbours) holds every
-//     source any of its targets needs, so each source ME is read from HBM
-//     once per tile (1.56x halo overhead) and reused by up to 27 targets;
+//   - a CTA owns a 4 x 4 tile of parent boxes = 64 target boxes of one level;
+//     one launch covers every tile of every requested level (heaviest level
+//     first), and the hardware block scheduler balances the ~1.4k CTAs of the
+//     level 2..8 pass over the 152 SMs (7 resident CTAs per SM at p = 16, so
+//     one CTA's staging overlaps the others' arithmetic);
+//   - the 6 x 6 parent halo holds every source any of the 64 targets needs;
+//     each source ME is read once per tile and reused by up to 27 targets;
 //   - the halo is stored in shared memory split by child class
 //     c' = (ix & 1) + 2 (iy & 1) and transposed to [c'][k][hy][hx], so that
 //     for a target class c every interaction-list entry is a constant shift
 //     (ex, ey) inside one class plane;
-//   - warp w handles the 64 targets of child class c = w, whose 27 list
+//   - warp w handles the 16 targets of child class c = w, whose 27 list
 //     offsets are therefore warp-uniform (no divergence); lane = (i_t, i_n)
-//     owns RN = p/2 rows of 4 targets; target parents (bb + 2j, ry) make the
-//     16 distinct ME addresses of a warp fall in 16 distinct bank pairs;
+//     owns RN = p/2 rows of one target;
 //   - the reduction over the list is a register accumulation, written once
-//     per target with one coalesced row of stores (no separate kernel).
+//     per target (no separate reduction kernel, no atomics: deterministic).
 #include "common.cuh"
 
 namespace fmmgb {
@@ -85,17 +88,17 @@ int launch_build_m2l_tables(const M2LTables& t, cudaStream_t st)
 // ---------------------------------------------------------------------------
 // stencil kernel
 // ---------------------------------------------------------------------------
-constexpr int kTile = 8;              // parent boxes per tile side
-constexpr int kHalo = kTile + 2;      // halo parents per side
-constexpr int kPlane = kHalo * kHalo + 1;  // float2 stride between k-planes (padded)
-constexpr int kThreads = 128;         // 4 warps, one per target child class
+constexpr int kTile = 4;                   // parent boxes per tile side
+constexpr int kHalo = kTile + 2;           // halo parents per side
+constexpr int kPlane = kHalo * kHalo + 1;  // float2 stride between k-planes (odd: spreads staging stores)
+constexpr int kThreads = 128;              // 4 warps, one per target child class
 
 template <int P>
 struct M2LCfg {
-    static constexpr int RN = P / 2;          // rows per thread (2 row blocks per target)
-    static constexpr int NH = 2 * P - 1;      // Hankel diagonals
-    static constexpr int CS = P * kPlane;     // float2 stride between class planes
-    static constexpr int Q = P / 2;           // float4 per box
+    static constexpr int RN = P / 2;      // rows per thread (2 row blocks per target)
+    static constexpr int NH = 2 * P - 1;  // Hankel diagonals
+    static constexpr int CS = P * kPlane; // float2 stride between class planes
+    static constexpr int Q = P / 2;       // float4 per box
     static constexpr size_t smem = sizeof(float2) * (4 * CS + kOffsetSlots * NH) + sizeof(float) * 2 * P;
 };
 
@@ -108,12 +111,9 @@ __device__ __forceinline__ void cmac(float2& acc, const float2 w, const float2 m
 }
 
 template <int P>
-__global__ void __launch_bounds__(kThreads) m2l_fp32_uniform_kernel(int level, const float2* __restrict__ hsel,
-                                                                     const float* __restrict__ ascale,
-                                                                     const float* __restrict__ bscale,
-                                                                     const float2* __restrict__ M,
-                                                                     float2* __restrict__ L, int accumulate,
-                                                                     int periodic)
+__global__ void __launch_bounds__(kThreads) m2l_fp32_kernel(M2LLaunch job, const float2* __restrict__ hsel,
+                                                            const float* __restrict__ ascale,
+                                                            const float* __restrict__ bscale)
 {
     using C = M2LCfg<P>;
     constexpr int RN = C::RN, NH = C::NH, CS = C::CS, Q = C::Q;
@@ -123,12 +123,18 @@ __global__ void __launch_bounds__(kThreads) m2l_fp32_uniform_kernel(int level, c
     float* as = reinterpret_cast<float*>(hs + kOffsetSlots * NH);
     float* bs = as + P;
 
-    const int tid = threadIdx.x;
-    const int side = 1 << level;
+    // which level / tile this CTA owns (levels are listed heaviest first)
+    int li = 0;
+    while (li + 1 < job.nlev && (int)blockIdx.x >= job.lv[li + 1].tile_begin) ++li;
+    const M2LLevel lv = job.lv[li];
+    const int tile = (int)blockIdx.x - lv.tile_begin;
+    const int side = 1 << lv.level;
     const int np = side >> 1;
-    const int PX0 = blockIdx.x * kTile, PY0 = blockIdx.y * kTile;
+    const int tps = (np + kTile - 1) / kTile;
+    const int PX0 = (tile % tps) * kTile, PY0 = (tile / tps) * kTile;
     const int bx0 = 2 * PX0 - 2, by0 = 2 * PY0 - 2;  // first halo box (even)
 
+    const int tid = threadIdx.x;
     for (int i = tid; i < kOffsetSlots * NH; i += kThreads) hs[i] = hsel[i];
     for (int i = tid; i < P; i += kThreads) {
         as[i] = ascale[i];
@@ -136,17 +142,17 @@ __global__ void __launch_bounds__(kThreads) m2l_fp32_uniform_kernel(int level, c
     }
     __syncthreads();
 
-    // Stage the 2*kHalo x 2*kHalo halo boxes, pre-scaled by b_k, into the
+    // Stage the 2 kHalo x 2 kHalo halo boxes, pre-scaled by b_k, into the
     // class-split transposed layout.  Consecutive threads read consecutive
     // 16-byte chunks of a row of boxes (coalesced).
-    const float4* M4 = reinterpret_cast<const float4*>(M);
+    const float4* M4 = reinterpret_cast<const float4*>(lv.M);
     for (int i = tid; i < (2 * kHalo) * (2 * kHalo) * Q; i += kThreads) {
         const int q = i % Q;
         const int bxy = i / Q;
         const int hxb = bxy % (2 * kHalo), hyb = bxy / (2 * kHalo);
         int ix = bx0 + hxb, iy = by0 + hyb;
         bool inside = ix >= 0 && iy >= 0 && ix < side && iy < side;
-        if (periodic) {
+        if (job.periodic) {
             ix = (ix + 2 * side) % side;
             iy = (iy + 2 * side) % side;
             inside = true;
@@ -165,13 +171,11 @@ __global__ void __launch_bounds__(kThreads) m2l_fp32_uniform_kernel(int level, c
     const int cx = warp & 1, cy = warp >> 1;  // target child class
     const int i_n = lane & 1, i_t = lane >> 1;
     const int n0 = i_n * RN;
-    const int ry = i_t >> 1, bb = i_t & 1;  // target parents (bb + 2j, ry), j < 4
+    const int tpx = i_t & 3, tpy = i_t >> 2;  // target parent within the tile
 
-    float2 acc[RN][4];
+    float2 acc[RN];
 #pragma unroll
-    for (int i = 0; i < RN; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
+    for (int i = 0; i < RN; ++i) acc[i] = make_float2(0.f, 0.f);
 
 #pragma unroll 1
     for (int e = 0; e < 36; ++e) {
@@ -184,19 +188,15 @@ __global__ void __launch_bounds__(kThreads) m2l_fp32_uniform_kernel(int level, c
         if ((adx > ady ? adx : ady) < 2) continue;  // adjacent: not in the interaction list (warp-uniform)
 
         const float2* hrow = hs + offset_slot(dx, dy) * NH + n0;
-        const float2* src = halo + (sx + 2 * sy) * CS + (ry + ey + 1) * kHalo + (bb + ex + 1);
+        const float2* src = halo + (sx + 2 * sy) * CS + (tpy + ey + 1) * kHalo + (tpx + ex + 1);
         float2 w[RN];
 #pragma unroll
         for (int i = 0; i < RN; ++i) w[i] = hrow[i];
 #pragma unroll
         for (int k = 0; k < P; ++k) {
-            float2 m[4];
+            const float2 m = src[k * kPlane];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) m[j] = src[k * kPlane + 2 * j];
-#pragma unroll
-            for (int i = 0; i < RN; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) cmac(acc[i][j], w[i], m[j]);
+            for (int i = 0; i < RN; ++i) cmac(acc[i], w[i], m);
             if (k + 1 < P) {
 #pragma unroll
                 for (int i = 0; i + 1 < RN; ++i) w[i] = w[i + 1];
@@ -205,70 +205,75 @@ __global__ void __launch_bounds__(kThreads) m2l_fp32_uniform_kernel(int level, c
         }
     }
 
-    // store L~[n] = a_n * acc (fused reduction result), one row block per lane
+    // store L~[n] = a_n * acc (the fused reduction's result)
+    const int px = PX0 + tpx, py = PY0 + tpy;
+    if (px >= np || py >= np) return;
+    const int ix = 2 * px + cx, iy = 2 * py + cy;
+    float2* dst = lv.L + ((size_t)iy * side + ix) * P + n0;
+    if constexpr (RN % 2 == 0) {
+        float4* d4 = reinterpret_cast<float4*>(dst);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int px = PX0 + bb + 2 * j, py = PY0 + ry;
-        if (px >= np || py >= np) continue;
-        const int ix = 2 * px + cx, iy = 2 * py + cy;
-        float2* dst = L + ((size_t)iy * side + ix) * P + n0;
-        if constexpr (RN % 2 == 0) {
-            float4* d4 = reinterpret_cast<float4*>(dst);
-#pragma unroll
-            for (int i = 0; i < RN; i += 2) {
-                const float s0 = as[n0 + i], s1 = as[n0 + i + 1];
-                float4 o = make_float4(s0 * acc[i][j].x, s0 * acc[i][j].y, s1 * acc[i + 1][j].x, s1 * acc[i + 1][j].y);
-                if (accumulate) {
-                    const float4 old = d4[i / 2];
-                    o.x += old.x;
-                    o.y += old.y;
-                    o.z += old.z;
-                    o.w += old.w;
-                }
-                d4[i / 2] = o;
+        for (int i = 0; i < RN; i += 2) {
+            const float s0 = as[n0 + i], s1 = as[n0 + i + 1];
+            float4 o = make_float4(s0 * acc[i].x, s0 * acc[i].y, s1 * acc[i + 1].x, s1 * acc[i + 1].y);
+            if (job.accumulate) {
+                const float4 old = d4[i / 2];
+                o.x += old.x;
+                o.y += old.y;
+                o.z += old.z;
+                o.w += old.w;
             }
-        } else {
+            d4[i / 2] = o;
+        }
+    } else {
 #pragma unroll
-            for (int i = 0; i < RN; ++i) {
-                const float s0 = as[n0 + i];
-                float2 o = make_float2(s0 * acc[i][j].x, s0 * acc[i][j].y);
-                if (accumulate) {
-                    const float2 old = dst[i];
-                    o.x += old.x;
-                    o.y += old.y;
-                }
-                dst[i] = o;
+        for (int i = 0; i < RN; ++i) {
+            const float s0 = as[n0 + i];
+            float2 o = make_float2(s0 * acc[i].x, s0 * acc[i].y);
+            if (job.accumulate) {
+                const float2 old = dst[i];
+                o.x += old.x;
+                o.y += old.y;
             }
+            dst[i] = o;
         }
     }
 }
 
 bool m2l_fp32_supported(int p) { return p == 6 || p == 8 || p == 12 || p == 16 || p == 24; }
 
+int m2l_tiles(int level)
+{
+    if (level < 2) return 0;
+    const int np = 1 << (level - 1);
+    const int tps = (np + kTile - 1) / kTile;
+    return tps * tps;
+}
+
 template <int P>
-static int launch_p(int level, const float2* h, const float* a, const float* b, const float2* M, float2* L, bool acc,
-                    bool periodic, cudaStream_t st)
+static int launch_p(M2LLaunch& job, const float2* h, const float* a, const float* b, cudaStream_t st)
 {
     using C = M2LCfg<P>;
-    const int np = 1 << (level - 1);
-    const int tiles = (np + kTile - 1) / kTile;
-    FMM_CUDA_TRY(cudaFuncSetAttribute(m2l_fp32_uniform_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)C::smem));
-    m2l_fp32_uniform_kernel<P><<<dim3(tiles, tiles), kThreads, C::smem, st>>>(level, h, a, b, M, L, acc ? 1 : 0,
-                                                                             periodic ? 1 : 0);
+    int total = 0;
+    for (int i = 0; i < job.nlev; ++i) {
+        job.lv[i].tile_begin = total;
+        total += m2l_tiles(job.lv[i].level);
+    }
+    if (total == 0) return FMM_OK;
+    FMM_CUDA_TRY(cudaFuncSetAttribute(m2l_fp32_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem));
+    m2l_fp32_kernel<P><<<total, kThreads, C::smem, st>>>(job, h, a, b);
     FMM_CUDA_TRY(cudaGetLastError());
     return FMM_OK;
 }
 
-int launch_m2l_fp32_uniform(int level, int p, const float2* h, const float* a, const float* b, const float2* M,
-                            float2* L, bool acc, bool periodic, cudaStream_t st)
+int launch_m2l_fp32(M2LLaunch& job, int p, const float2* h, const float* a, const float* b, cudaStream_t st)
 {
     switch (p) {
-        case 6: return launch_p<6>(level, h, a, b, M, L, acc, periodic, st);
-        case 8: return launch_p<8>(level, h, a, b, M, L, acc, periodic, st);
-        case 12: return launch_p<12>(level, h, a, b, M, L, acc, periodic, st);
-        case 16: return launch_p<16>(level, h, a, b, M, L, acc, periodic, st);
-        case 24: return launch_p<24>(level, h, a, b, M, L, acc, periodic, st);
+        case 6: return launch_p<6>(job, h, a, b, st);
+        case 8: return launch_p<8>(job, h, a, b, st);
+        case 12: return launch_p<12>(job, h, a, b, st);
+        case 16: return launch_p<16>(job, h, a, b, st);
+        case 24: return launch_p<24>(job, h, a, b, st);
         default: return fail(FMM_EINVAL, "M2L FP32: unsupported p = %d", p);
     }
 }

@@ -70,6 +70,42 @@ __global__ void m2m_kernel(int child_level, int p, const float2* __restrict__ Mc
     *out = make_float2((float)sr, (float)si);
 }
 
+// FGT Hermite coefficients of every box of a 2^g grid (Eq. A_alpha):
+//   A_b[a1][a2] += q_j t1^a1 t2^a2 / (a1! a2!),  t = (x_j - s_b) / (sqrt(2) sigma)
+__global__ void fgt_p2h_kernel(int g, int p, double inv_scale, const double* __restrict__ x,
+                               const double* __restrict__ q, int64_t n, float* __restrict__ A)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const int side = 1 << g;
+    const double px = x[2 * j] * side, py = x[2 * j + 1] * side;
+    int ix = (int)floor(px), iy = (int)floor(py);
+    ix = ix < 0 ? 0 : (ix > side - 1 ? side - 1 : ix);
+    iy = iy < 0 ? 0 : (iy > side - 1 ? side - 1 : iy);
+    const double t1 = (px - (ix + 0.5)) / side * inv_scale, t2 = (py - (iy + 0.5)) / side * inv_scale;
+    float* Ab = A + ((size_t)iy * side + ix) * p * p;
+    double w1 = q[j];
+    for (int a1 = 0; a1 < p; ++a1) {
+        double w2 = w1;
+        for (int a2 = 0; a2 < p; ++a2) {
+            atomicAdd(&Ab[a1 * p + a2], (float)w2);
+            w2 = w2 * t2 / (double)(a2 + 1);
+        }
+        w1 = w1 * t1 / (double)(a1 + 1);
+    }
+}
+
+int launch_fgt_p2h(int g, int p, double sigma, const double* x, const double* q, int64_t n, float* A, bool acc,
+                   cudaStream_t st)
+{
+    const size_t bytes = ((size_t)1 << (2 * g)) * (size_t)p * p * sizeof(float);
+    if (!acc) FMM_CUDA_TRY(cudaMemsetAsync(A, 0, bytes, st));
+    if (n == 0) return FMM_OK;
+    fgt_p2h_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g, p, 1.0 / (sqrt(2.0) * sigma), x, q, n, A);
+    FMM_CUDA_TRY(cudaGetLastError());
+    return FMM_OK;
+}
+
 int launch_p2m(int level, int p, const double* xy, const double* c, int64_t n, float2* M, bool acc, cudaStream_t st)
 {
     const size_t bytes = ((size_t)1 << (2 * level)) * (size_t)p * sizeof(float2);

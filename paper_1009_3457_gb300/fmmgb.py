@@ -68,8 +68,14 @@ SIGNATURES = {
     "fmm_prepare": (ctypes.c_int, [_i32, _i32]),
     "fmm_m2l": (ctypes.c_int, [_vp, _i32, _i32, _i32, _vp, _vp, _i32, _vp]),
     "fmm_m2l_adjoint": (ctypes.c_int, [_vp, _i32, _i32, _i32, _vp, _vp, _i32, _vp]),
+    "fmm_m2l_levels": (ctypes.c_int, [_vp, _i32, _i32, _i32, _i32, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                                      _i32, _vp]),
+    "fmm_m2l_adjoint_levels": (ctypes.c_int, [_vp, _i32, _i32, _i32, _i32, ctypes.POINTER(_vp),
+                                              ctypes.POINTER(_vp), _i32, _vp]),
     "fmm_p2m": (ctypes.c_int, [_i32, _i32, _vp, _vp, _i64, _vp, _i32, _vp]),
     "fmm_m2m": (ctypes.c_int, [_i32, _i32, _vp, _vp, _i32, _vp]),
+    "fgt_h2t": (ctypes.c_int, [_i32, _i32, _i32, _d, _vp, _vp, _vp, _i32, _vp]),
+    "fgt_p2h": (ctypes.c_int, [_i32, _i32, _d, _vp, _vp, _i64, _vp, _i32, _vp]),
     "fmm_sync_status": (ctypes.c_int, [_vp]),
     "fmm_last_error": (ctypes.c_char_p, []),
     "fmm_version": (ctypes.c_char_p, []),
@@ -186,6 +192,26 @@ def fmm_m2l_adjoint(tree: Tree, level: int, p: int, W, G, prec: int = FMM_FP32, 
     _check(load().fmm_m2l_adjoint(tree.handle, level, p, prec, _ptr(W), _ptr(G), flags, _stream(stream)))
 
 
+def _ptr_array(ts):
+    return (_vp * len(ts))(*[_ptr(t) for t in ts])
+
+
+def fmm_m2l_levels(tree: Tree, lmin: int, p: int, Ms, Ls, prec: int = FMM_FP32, accumulate: bool = False,
+                   stream=None):
+    """One launch over levels lmin .. lmin + len(Ms) - 1; Ms[i], Ls[i] belong to level lmin + i."""
+    assert len(Ms) == len(Ls) and len(Ms) > 0
+    _check(load().fmm_m2l_levels(tree.handle, lmin, lmin + len(Ms) - 1, p, prec, _ptr_array(Ms), _ptr_array(Ls),
+                                 FMM_ACCUMULATE if accumulate else 0, _stream(stream)))
+
+
+def fmm_m2l_adjoint_levels(tree: Tree, lmin: int, p: int, Ws, Gs, prec: int = FMM_FP32, accumulate: bool = False,
+                           conj: bool = False, stream=None):
+    assert len(Ws) == len(Gs) and len(Ws) > 0
+    flags = (FMM_ACCUMULATE if accumulate else 0) | (FMM_CONJ if conj else 0)
+    _check(load().fmm_m2l_adjoint_levels(tree.handle, lmin, lmin + len(Ws) - 1, p, prec, _ptr_array(Ws),
+                                         _ptr_array(Gs), flags, _stream(stream)))
+
+
 def fmm_p2m(level: int, p: int, xy, c, M, accumulate: bool = False, stream=None):
     n = 0 if c is None else c.numel()
     _check(load().fmm_p2m(level, p, _ptr(xy), _ptr(c), n, _ptr(M), FMM_ACCUMULATE if accumulate else 0,
@@ -195,6 +221,18 @@ def fmm_p2m(level: int, p: int, xy, c, M, accumulate: bool = False, stream=None)
 def fmm_m2m(child_level: int, p: int, Mc, Mp, accumulate: bool = False, stream=None):
     _check(load().fmm_m2m(child_level, p, _ptr(Mc), _ptr(Mp), FMM_ACCUMULATE if accumulate else 0,
                           _stream(stream)))
+
+
+def fgt_h2t(grid_log2: int, n_cut: int, p: int, sigma: float, A, C, work=None, accumulate: bool = False,
+            stream=None):
+    _check(load().fgt_h2t(grid_log2, n_cut, p, float(sigma), _ptr(A), _ptr(C), _ptr(work),
+                          FMM_ACCUMULATE if accumulate else 0, _stream(stream)))
+
+
+def fgt_p2h(grid_log2: int, p: int, sigma: float, x, q, A, accumulate: bool = False, stream=None):
+    n = 0 if q is None else q.numel()
+    _check(load().fgt_p2h(grid_log2, p, float(sigma), _ptr(x), _ptr(q), n, _ptr(A),
+                          FMM_ACCUMULATE if accumulate else 0, _stream(stream)))
 
 
 def fmm_sync_status(stream=None):

@@ -202,3 +202,42 @@ def test_m2l_full_size_workload(fmm, orc):
     targets = np.unique(np.concatenate([edge, rng.integers(0, n * n, 3000)]))
     ref = orc.scale_le(orc.m2l_uniform_targets(L, p, Ms[L], targets), L)
     _check(_host(outs[L])[targets], ref)
+
+
+@pytest.mark.parametrize("p", [8, 16, 24])
+@pytest.mark.parametrize("periodic", [False, True])
+def test_m2l_levels_single_launch(fmm, orc, medium_particles, p, periodic):
+    """fmm_m2l_levels (levels 2..6 in one launch) equals the per-level oracle, and
+    fmm_m2l_adjoint_levels equals the per-level adjoint."""
+    xy, c = medium_particles
+    Lmax = 6
+    Ms = orc.upward_uniform(Lmax, p, xy, c)
+    tree = fmm.fmm_build_lists(None, Lmax, periodic=periodic)
+    levels = list(range(2, Lmax + 1))
+    Md = [_dev(orc.scale_me(Ms[l], l)) for l in levels]
+    Ld = [m.new_empty(m.shape) for m in Md]
+    fmm.fmm_m2l_levels(tree, 2, p, Md, Ld)
+    for l, out in zip(levels, Ld):
+        _check(_host(out), _oracle_level(orc, l, p, Ms[l], periodic))
+    Gd = [m.new_empty(m.shape) for m in Md]
+    fmm.fmm_m2l_adjoint_levels(tree, 2, p, Ld, Gd, conj=True)
+    for l, w, g in zip(levels, Ld, Gd):
+        W = _host(w)
+        G = np.conj(orc.unscale_me(orc.m2l_adjoint_uniform(l, p, orc.scale_le(np.conj(W), l), periodic), l))
+        _check(_host(g), G)
+
+
+def test_m2l_levels_including_empty_levels(fmm, orc, medium_particles):
+    import torch
+
+    xy, c = medium_particles
+    p = 6
+    Ms = orc.upward_uniform(3, p, xy, c)
+    tree = fmm.fmm_build_lists(None, 3)
+    Md = [_dev(np.ones((1, p))), _dev(np.ones((4, p))), _dev(orc.scale_me(Ms[2], 2)), _dev(orc.scale_me(Ms[3], 3))]
+    Ld = [_dev(np.full(m.shape, 5.0)) for m in Md]
+    fmm.fmm_m2l_levels(tree, 0, p, Md, Ld)
+    torch.cuda.synchronize()
+    assert np.all(_host(Ld[0]) == 0) and np.all(_host(Ld[1]) == 0)
+    for l in (2, 3):
+        _check(_host(Ld[l]), _oracle_level(orc, l, p, Ms[l]))
