@@ -164,6 +164,20 @@ def run_reference(args):
     return 0
 
 
+def _traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, or None if the kernel source changed since."""
+    import hashlib
+
+    try:
+        with open(os.path.join(ROOT, "profiles", "roofline_traffic.json")) as f:
+            rec = json.load(f)[kernel]
+        with open(os.path.join(ROOT, rec["source"]), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+        return rec["dram_bytes_per_launch"] if sha.startswith(rec["source_sha256_prefix"]) else None
+    except Exception:
+        return None
+
+
 def _timed(torch, fn, steps, stream, flush):
     """Per-step CUDA-event durations (ms) of fn() on `stream`, L2 flushed between steps."""
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
@@ -329,7 +343,7 @@ def run_ours(args):
             "executed_gflops": value * metrics.m2l_flops_per_translation(P) / 1e9,
             "roofline": {
                 "bound": "alu", "kernel": "m2l_fp32_kernel<16> (levels 2-8, one launch)", "achieved": achieved,
-                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": _traffic(f"m2l_fp32_kernel<{P}>"),
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (max SM clock)",
                 "flops_per_launch": flops, "launch_ms": statistics.mean(step_ms),
                 "frac_at_sampled_clock": (achieved / (peak * clocks["sm_mhz"] / SM_MAX_MHZ))
