@@ -200,6 +200,32 @@ int fgt_h2t(int32_t grid_log2, int32_t n_cut, int32_t p, double sigma, const flo
             float* work, int32_t flags, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * fgt_h2t_noalloc -- fgt_h2t that never allocates device memory.
+ *
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc -- for example code that runs while a CUDA graph is
+ * being captured, under a caching allocator that owns all of the device's
+ * memory, or in a latency-critical loop where an allocation (which may
+ * synchronise the device) is not acceptable -- and that cannot pass a `work`
+ * buffer either.  The intermediate of the two passes lives in a fixed
+ * 1 MiB array compiled into the library: 4^g * p^2 must not exceed 262,144
+ * floats (for example grids up to 32 x 32 boxes at p = 16, 64 x 64 at
+ * p = 8); larger requests are rejected with FMM_EINVAL and a message, and
+ * fgt_h2t serves them.  Every GPU that loads the library keeps that array
+ * for the life of the process.
+ *
+ * Arguments and results are those of fgt_h2t without `work`.  The first call
+ * on a device looks up the array's device address once (no allocation); make
+ * that first call before any stream capture.  All calls share the one array
+ * and each overwrites it completely before reading it, so nothing needs
+ * clearing; calls that overlap on the GPU (different streams, or a graph
+ * replay running beside another call) race on it and must be serialised by
+ * the caller.
+ * ------------------------------------------------------------------------- */
+int fgt_h2t_noalloc(int32_t grid_log2, int32_t n_cut, int32_t p, double sigma, const float* A, float* C,
+                    int32_t flags, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Support for building M2L inputs on the device (upward sweep, Sec. 2.1
  * stage 2; not the translation path itself).
  *

@@ -452,31 +452,43 @@ int fmm_m2m(int32_t child_level, int32_t p, const void* Mc, void* Mp, int32_t fl
                       (cudaStream_t)stream);
 }
 
+}  // extern "C"
+
+int fmmgb::fgt_check_args(const char* who, int g, int n_cut, int p, double sigma, const float* A, const float* C,
+                          const float* work, int flags)
+{
+    if (g < 0 || g > 12) return fail(FMM_EINVAL, "%s: grid_log2 %d outside 0..12", who, g);
+    if (n_cut < 0 || n_cut > fgt_max_cut()) return fail(FMM_EINVAL, "%s: n_cut %d outside 0..%d", who, n_cut, fgt_max_cut());
+    if (!fgt_supported(p)) return fail(FMM_EINVAL, "%s: unsupported p = %d (4, 8, 12, 16)", who, p);
+    if (!(sigma > 0.0) || !(sigma < 1e300)) return fail(FMM_EINVAL, "%s: sigma must be positive and finite", who);
+    if (!A || !C) return fail(FMM_EINVAL, "%s: NULL coefficient pointer", who);
+    if (((uintptr_t)A & 15) || ((uintptr_t)C & 15) || ((uintptr_t)work & 15))
+        return fail(FMM_EINVAL, "%s: pointers must be 16-byte aligned", who);
+    if (flags & ~FMM_ACCUMULATE) return fail(FMM_EINVAL, "%s: unknown flags 0x%x", who, flags);
+    const size_t bytes = ((size_t)1 << (2 * g)) * (size_t)p * p * sizeof(float);
+    const char* a = (const char*)A;
+    const char* c = (const char*)C;
+    if (a < c + bytes && c < a + bytes) return fail(FMM_EINVAL, "%s: A and C overlap", who);
+    if (work) {
+        const char* w = (const char*)work;
+        if ((w < a + bytes && a < w + bytes) || (w < c + bytes && c < w + bytes))
+            return fail(FMM_EINVAL, "%s: work overlaps A or C", who);
+    }
+    return FMM_OK;
+}
+
+extern "C" {
+
 int fgt_h2t(int32_t grid_log2, int32_t n_cut, int32_t p, double sigma, const float* A, float* C, float* work,
             int32_t flags, void* stream)
 {
     clear_error();
-    if (grid_log2 < 0 || grid_log2 > 12) return fail(FMM_EINVAL, "fgt_h2t: grid_log2 %d outside 0..12", grid_log2);
-    if (n_cut < 0 || n_cut > fgt_max_cut())
-        return fail(FMM_EINVAL, "fgt_h2t: n_cut %d outside 0..%d", n_cut, fgt_max_cut());
-    if (!fgt_supported(p)) return fail(FMM_EINVAL, "fgt_h2t: unsupported p = %d (4, 8, 12, 16)", p);
-    if (!(sigma > 0.0) || !(sigma < 1e300)) return fail(FMM_EINVAL, "fgt_h2t: sigma must be positive and finite");
-    if (!A || !C) return fail(FMM_EINVAL, "fgt_h2t: NULL coefficient pointer");
-    if (((uintptr_t)A & 15) || ((uintptr_t)C & 15) || ((uintptr_t)work & 15))
-        return fail(FMM_EINVAL, "fgt_h2t: pointers must be 16-byte aligned");
-    if (flags & ~FMM_ACCUMULATE) return fail(FMM_EINVAL, "fgt_h2t: unknown flags 0x%x", flags);
-    const size_t bytes = ((size_t)1 << (2 * grid_log2)) * (size_t)p * p * sizeof(float);
-    const char* a = (const char*)A;
-    const char* c = (const char*)C;
-    if (a < c + bytes && c < a + bytes) return fail(FMM_EINVAL, "fgt_h2t: A and C overlap");
+    int rc = fgt_check_args("fgt_h2t", grid_log2, n_cut, p, sigma, A, C, work, flags);
+    if (rc) return rc;
     float* Y = work;
     if (!Y) {
-        int rc = fgt_workspace(bytes, &Y);
-        if (rc) return rc;
-    } else {
-        const char* w = (const char*)work;
-        if ((w < a + bytes && a < w + bytes) || (w < c + bytes && c < w + bytes))
-            return fail(FMM_EINVAL, "fgt_h2t: work overlaps A or C");
+        const size_t bytes = ((size_t)1 << (2 * grid_log2)) * (size_t)p * p * sizeof(float);
+        if ((rc = fgt_workspace(bytes, &Y))) return rc;
     }
     return launch_fgt_h2t(grid_log2, n_cut, p, sigma, A, Y, C, (flags & FMM_ACCUMULATE) != 0, (cudaStream_t)stream);
 }

@@ -95,6 +95,8 @@ int fgt_max_cut();
 int launch_fgt_h2t(int g, int ncut, int p, double sigma, const float* A, float* Y, float* C, bool acc,
                    cudaStream_t st);
 int fgt_workspace(size_t bytes, float** out);
+int fgt_check_args(const char* who, int g, int ncut, int p, double sigma, const float* A, const float* C,
+                   const float* work, int flags);
 
 // launchers (upward.cu)
 int launch_p2m(int level, int p, const double* xy, const double* c, int64_t n, float2* M, bool accumulate,

@@ -188,4 +188,55 @@ int launch_fgt_h2t(int g, int ncut, int p, double sigma, const float* A, float* 
 
 int fgt_max_cut() { return kFgtMaxCut; }
 
+// ---------------------------------------------------------------------------
+// Allocation-free variant: the intermediate Y lives in a fixed device array
+// that is part of the loaded module, so no call ever allocates device memory.
+// Every GPU that loads the library holds this array until the process exits.
+// ---------------------------------------------------------------------------
+constexpr size_t kFgtStaticScratchFloats = (size_t)1 << 18;  // 1 MiB: 4^g p^2 <= 262,144 (32 x 32 boxes at p = 16)
+static __device__ __align__(256) float g_fgt_static_scratch[kFgtStaticScratchFloats];
+
+constexpr int kMaxDevices = 64;
+static std::mutex g_static_mu;
+static float* g_static_scratch_dev[kMaxDevices] = {};
+
+// Device address of g_fgt_static_scratch on the current device.  In host code
+// the symbol is only a host-side stand-in, so the address is fetched once per
+// device (with that device current) and cached.
+static int static_scratch(float** out)
+{
+    int dev = 0;
+    FMM_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return fail(FMM_EUNSUPPORTED, "fgt_h2t_noalloc: device %d >= %d", dev, kMaxDevices);
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_scratch_dev[dev]) {
+        void* ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_fgt_static_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_fgt_static_scratch)");
+        g_static_scratch_dev[dev] = static_cast<float*>(ptr);
+    }
+    *out = g_static_scratch_dev[dev];
+    return FMM_OK;
+}
+
 }  // namespace fmmgb
+
+extern "C" int fgt_h2t_noalloc(int32_t grid_log2, int32_t n_cut, int32_t p, double sigma, const float* A, float* C,
+                               int32_t flags, void* stream)
+{
+    using namespace fmmgb;
+    clear_error();
+    int rc = fgt_check_args("fgt_h2t_noalloc", grid_log2, n_cut, p, sigma, A, C, nullptr, flags);
+    if (rc) return rc;
+    const size_t need = ((size_t)1 << (2 * grid_log2)) * (size_t)p * p;
+    if (need > kFgtStaticScratchFloats)
+        return fail(FMM_EINVAL,
+                    "fgt_h2t_noalloc: a 2^%d x 2^%d grid at p = %d needs %zu floats of scratch; the built-in scratch "
+                    "holds %zu (4^g p^2 <= %zu, e.g. 32 x 32 boxes at p = 16); use fgt_h2t for larger grids",
+                    grid_log2, grid_log2, p, need, kFgtStaticScratchFloats, kFgtStaticScratchFloats);
+    float* Y = nullptr;
+    if ((rc = static_scratch(&Y))) return rc;
+    // The first pass writes every element of Y before the second pass reads
+    // it, so the scratch needs no clearing between calls.
+    return launch_fgt_h2t(grid_log2, n_cut, p, sigma, A, Y, C, (flags & FMM_ACCUMULATE) != 0, (cudaStream_t)stream);
+}

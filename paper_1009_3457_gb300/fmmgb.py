@@ -75,6 +75,7 @@ SIGNATURES = {
     "fmm_p2m": (ctypes.c_int, [_i32, _i32, _vp, _vp, _i64, _vp, _i32, _vp]),
     "fmm_m2m": (ctypes.c_int, [_i32, _i32, _vp, _vp, _i32, _vp]),
     "fgt_h2t": (ctypes.c_int, [_i32, _i32, _i32, _d, _vp, _vp, _vp, _i32, _vp]),
+    "fgt_h2t_noalloc": (ctypes.c_int, [_i32, _i32, _i32, _d, _vp, _vp, _i32, _vp]),
     "fgt_p2h": (ctypes.c_int, [_i32, _i32, _d, _vp, _vp, _i64, _vp, _i32, _vp]),
     "fmm_sync_status": (ctypes.c_int, [_vp]),
     "fmm_last_error": (ctypes.c_char_p, []),
@@ -227,6 +228,13 @@ def fgt_h2t(grid_log2: int, n_cut: int, p: int, sigma: float, A, C, work=None, a
             stream=None):
     _check(load().fgt_h2t(grid_log2, n_cut, p, float(sigma), _ptr(A), _ptr(C), _ptr(work),
                           FMM_ACCUMULATE if accumulate else 0, _stream(stream)))
+
+
+def fgt_h2t_noalloc(grid_log2: int, n_cut: int, p: int, sigma: float, A, C, accumulate: bool = False,
+                    stream=None):
+    """fgt_h2t with its intermediate in the library's built-in scratch array (no device allocation)."""
+    _check(load().fgt_h2t_noalloc(grid_log2, n_cut, p, float(sigma), _ptr(A), _ptr(C),
+                                  FMM_ACCUMULATE if accumulate else 0, _stream(stream)))
 
 
 def fgt_p2h(grid_log2: int, p: int, sigma: float, x, q, A, accumulate: bool = False, stream=None):
