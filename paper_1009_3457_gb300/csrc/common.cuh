@@ -86,7 +86,6 @@ struct M2LLaunch {
 // launchers (m2l_fp32.cu)
 int launch_build_m2l_tables(const M2LTables& t, cudaStream_t st);
 bool m2l_fp32_supported(int p);
-int m2l_tiles(int level);
 int launch_m2l_fp32(M2LLaunch& job, int p, const float2* hsel, const float* a, const float* b, cudaStream_t st);
 
 // launchers (fgt_h2t.cu)

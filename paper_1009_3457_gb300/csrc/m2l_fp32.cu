@@ -14,20 +14,22 @@
 //
 // Work decomposition (GB300-first; replaces the paper's thread-per-row,
 // source-centric kernel and its separate reduction kernel, Sec. 4.1.1):
-//   - a CTA owns a 4 x 4 tile of parent boxes = 64 target boxes of one level;
-//     one launch covers every tile of every requested level (heaviest level
-//     first), and the hardware block scheduler balances the ~1.4k CTAs of the
-//     level 2..8 pass over the 152 SMs (7 resident CTAs per SM at p = 16, so
-//     one CTA's staging overlaps the others' arithmetic);
-//   - the 6 x 6 parent halo holds every source any of the 64 targets needs;
-//     each source ME is read once per tile and reused by up to 27 targets;
+//   - a CTA owns an 8 x 4 tile of parent boxes = 128 target boxes of one level
+//     (4 x 4 tile for p = 24); one launch covers every tile of every requested
+//     level (heaviest level first), so the ~680 CTAs of the level 2..8 pass are
+//     resident in one wave (5 CTAs per SM at p = 16) and one CTA's staging
+//     overlaps the others' arithmetic;
+//   - the parent halo (tile + 1 on each side) holds every source any target
+//     needs; each source ME is read once per tile and reused by up to 27
+//     targets;
 //   - the halo is stored in shared memory split by child class
 //     c' = (ix & 1) + 2 (iy & 1) and transposed to [c'][k][hy][hx], so that
 //     for a target class c every interaction-list entry is a constant shift
 //     (ex, ey) inside one class plane;
-//   - warp w handles the 16 targets of child class c = w, whose 27 list
-//     offsets are therefore warp-uniform (no divergence); lane = (i_t, i_n)
-//     owns RN = p/2 rows of one target;
+//   - warp w handles the targets of child class c = w, whose 27 list offsets
+//     are therefore warp-uniform (no divergence); a lane owns all p rows of
+//     one target (two lanes of p/2 rows each for p = 24), so each k step costs
+//     two shared loads (one ME value, one new Hankel value) per 4p FFMA;
 //   - the reduction over the list is a register accumulation, written once
 //     per target (no separate reduction kernel, no atomics: deterministic).
 #include "common.cuh"
@@ -88,17 +90,22 @@ int launch_build_m2l_tables(const M2LTables& t, cudaStream_t st)
 // ---------------------------------------------------------------------------
 // stencil kernel
 // ---------------------------------------------------------------------------
-constexpr int kTile = 4;                   // parent boxes per tile side
-constexpr int kHalo = kTile + 2;           // halo parents per side
-constexpr int kPlane = kHalo * kHalo + 1;  // float2 stride between k-planes (odd: spreads staging stores)
-constexpr int kThreads = 128;              // 4 warps, one per target child class
+constexpr int kThreads = 128;  // 4 warps, one per target child class
+constexpr int kTileY = 4;      // parent rows per tile
 
+// NB = row blocks per target: NB = 1 (one lane = all p rows of one target,
+// 8 x 4 parent tile, 32 targets per class) for p <= 16; NB = 2 (two lanes per
+// target, 4 x 4 tile) for p = 24 to bound registers.
 template <int P>
 struct M2LCfg {
-    static constexpr int RN = P / 2;      // rows per thread (2 row blocks per target)
-    static constexpr int NH = 2 * P - 1;  // Hankel diagonals
-    static constexpr int CS = P * kPlane; // float2 stride between class planes
-    static constexpr int Q = P / 2;       // float4 per box
+    static constexpr int NB = P <= 16 ? 1 : 2;
+    static constexpr int TX = 8 / NB;                  // parent columns per tile
+    static constexpr int HX = TX + 2, HY = kTileY + 2;  // halo parents
+    static constexpr int PL = HX * HY + 1;            // float2 stride between k-planes
+    static constexpr int RN = P / NB;                 // rows per lane
+    static constexpr int NH = 2 * P - 1;              // Hankel diagonals
+    static constexpr int CS = P * PL;                 // float2 stride between class planes
+    static constexpr int Q = P / 2;                   // float4 per box
     static constexpr size_t smem = sizeof(float2) * (4 * CS + kOffsetSlots * NH) + sizeof(float) * 2 * P;
 };
 
@@ -111,14 +118,24 @@ __device__ __forceinline__ void cmac(float2& acc, const float2 w, const float2 m
 }
 
 template <int P>
+__host__ __device__ constexpr int m2l_tiles_p(int level)
+{
+    using C = M2LCfg<P>;
+    if (level < 2) return 0;
+    const int np = 1 << (level - 1);
+    return ((np + C::TX - 1) / C::TX) * ((np + kTileY - 1) / kTileY);
+}
+
+template <int P>
 __global__ void __launch_bounds__(kThreads) m2l_fp32_kernel(M2LLaunch job, const float2* __restrict__ hsel,
                                                             const float* __restrict__ ascale,
                                                             const float* __restrict__ bscale)
 {
     using C = M2LCfg<P>;
+    constexpr int NB = C::NB, TX = C::TX, HX = C::HX, HY = C::HY, PL = C::PL;
     constexpr int RN = C::RN, NH = C::NH, CS = C::CS, Q = C::Q;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2* halo = reinterpret_cast<float2*>(smem_raw);  // [4][P][kPlane]
+    float2* halo = reinterpret_cast<float2*>(smem_raw);  // [4][P][PL]
     float2* hs = halo + 4 * CS;                            // [49][NH]
     float* as = reinterpret_cast<float*>(hs + kOffsetSlots * NH);
     float* bs = as + P;
@@ -130,8 +147,8 @@ __global__ void __launch_bounds__(kThreads) m2l_fp32_kernel(M2LLaunch job, const
     const int tile = (int)blockIdx.x - lv.tile_begin;
     const int side = 1 << lv.level;
     const int np = side >> 1;
-    const int tps = (np + kTile - 1) / kTile;
-    const int PX0 = (tile % tps) * kTile, PY0 = (tile / tps) * kTile;
+    const int tpr = (np + TX - 1) / TX;  // tiles per row
+    const int PX0 = (tile % tpr) * TX, PY0 = (tile / tpr) * kTileY;
     const int bx0 = 2 * PX0 - 2, by0 = 2 * PY0 - 2;  // first halo box (even)
 
     const int tid = threadIdx.x;
@@ -142,14 +159,14 @@ __global__ void __launch_bounds__(kThreads) m2l_fp32_kernel(M2LLaunch job, const
     }
     __syncthreads();
 
-    // Stage the 2 kHalo x 2 kHalo halo boxes, pre-scaled by b_k, into the
-    // class-split transposed layout.  Consecutive threads read consecutive
-    // 16-byte chunks of a row of boxes (coalesced).
+    // Stage the 2 HX x 2 HY halo boxes, pre-scaled by b_k, into the class-split
+    // transposed layout.  Consecutive threads read consecutive 16-byte chunks of
+    // a row of boxes (coalesced).
     const float4* M4 = reinterpret_cast<const float4*>(lv.M);
-    for (int i = tid; i < (2 * kHalo) * (2 * kHalo) * Q; i += kThreads) {
+    for (int i = tid; i < (2 * HX) * (2 * HY) * Q; i += kThreads) {
         const int q = i % Q;
         const int bxy = i / Q;
-        const int hxb = bxy % (2 * kHalo), hyb = bxy / (2 * kHalo);
+        const int hxb = bxy % (2 * HX), hyb = bxy / (2 * HX);
         int ix = bx0 + hxb, iy = by0 + hyb;
         bool inside = ix >= 0 && iy >= 0 && ix < side && iy < side;
         if (job.periodic) {
@@ -160,18 +177,18 @@ __global__ void __launch_bounds__(kThreads) m2l_fp32_kernel(M2LLaunch job, const
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
         if (inside) v = __ldg(M4 + ((size_t)iy * side + ix) * Q + q);
         const int cls = (hxb & 1) + 2 * (hyb & 1);
-        float2* dst = halo + cls * CS + (hyb >> 1) * kHalo + (hxb >> 1);
+        float2* dst = halo + cls * CS + (hyb >> 1) * HX + (hxb >> 1);
         const float b0 = bs[2 * q], b1 = bs[2 * q + 1];
-        dst[(2 * q) * kPlane] = make_float2(v.x * b0, v.y * b0);
-        dst[(2 * q + 1) * kPlane] = make_float2(v.z * b1, v.w * b1);
+        dst[(2 * q) * PL] = make_float2(v.x * b0, v.y * b0);
+        dst[(2 * q + 1) * PL] = make_float2(v.z * b1, v.w * b1);
     }
     __syncthreads();
 
     const int warp = tid >> 5, lane = tid & 31;
     const int cx = warp & 1, cy = warp >> 1;  // target child class
-    const int i_n = lane & 1, i_t = lane >> 1;
+    const int i_n = lane % NB, i_t = lane / NB;
     const int n0 = i_n * RN;
-    const int tpx = i_t & 3, tpy = i_t >> 2;  // target parent within the tile
+    const int tpx = i_t % TX, tpy = i_t / TX;  // target parent within the tile
 
     float2 acc[RN];
 #pragma unroll
@@ -188,13 +205,13 @@ __global__ void __launch_bounds__(kThreads) m2l_fp32_kernel(M2LLaunch job, const
         if ((adx > ady ? adx : ady) < 2) continue;  // adjacent: not in the interaction list (warp-uniform)
 
         const float2* hrow = hs + offset_slot(dx, dy) * NH + n0;
-        const float2* src = halo + (sx + 2 * sy) * CS + (tpy + ey + 1) * kHalo + (tpx + ex + 1);
+        const float2* src = halo + (sx + 2 * sy) * CS + (tpy + ey + 1) * HX + (tpx + ex + 1);
         float2 w[RN];
 #pragma unroll
         for (int i = 0; i < RN; ++i) w[i] = hrow[i];
 #pragma unroll
         for (int k = 0; k < P; ++k) {
-            const float2 m = src[k * kPlane];
+            const float2 m = src[k * PL];
 #pragma unroll
             for (int i = 0; i < RN; ++i) cmac(acc[i], w[i], m);
             if (k + 1 < P) {
@@ -242,14 +259,6 @@ __global__ void __launch_bounds__(kThreads) m2l_fp32_kernel(M2LLaunch job, const
 
 bool m2l_fp32_supported(int p) { return p == 6 || p == 8 || p == 12 || p == 16 || p == 24; }
 
-int m2l_tiles(int level)
-{
-    if (level < 2) return 0;
-    const int np = 1 << (level - 1);
-    const int tps = (np + kTile - 1) / kTile;
-    return tps * tps;
-}
-
 template <int P>
 static int launch_p(M2LLaunch& job, const float2* h, const float* a, const float* b, cudaStream_t st)
 {
@@ -257,7 +266,7 @@ static int launch_p(M2LLaunch& job, const float2* h, const float* a, const float
     int total = 0;
     for (int i = 0; i < job.nlev; ++i) {
         job.lv[i].tile_begin = total;
-        total += m2l_tiles(job.lv[i].level);
+        total += m2l_tiles_p<P>(job.lv[i].level);
     }
     if (total == 0) return FMM_OK;
     FMM_CUDA_TRY(cudaFuncSetAttribute(m2l_fp32_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem));
