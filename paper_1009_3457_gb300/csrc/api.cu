@@ -65,7 +65,11 @@ struct DeviceState {
     std::map<int, M2LTables*> m2l;
     float* fgt_ws = nullptr;  // FGT H2T intermediate (grown on demand)
     size_t fgt_ws_bytes = 0;
+    int sm_count = 0;
+    int* counters = nullptr;  // ring of persistent-launch work counters
+    unsigned next_counter = 0;
 };
+constexpr int kCounterRing = 256;
 static std::mutex g_mu;
 static std::map<int, DeviceState*> g_dev;
 
@@ -98,6 +102,40 @@ int device_error_word(int** out)
     int rc = current_state(&s);
     if (rc) return rc;
     *out = s->err_word;
+    return FMM_OK;
+}
+
+int device_sm_count(int* out)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    DeviceState* s = nullptr;
+    int rc = current_state(&s);
+    if (rc) return rc;
+    if (!s->sm_count) {
+        int dev = 0;
+        FMM_CUDA_TRY(cudaGetDevice(&dev));
+        FMM_CUDA_TRY(cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount, dev));
+    }
+    *out = s->sm_count;
+    return FMM_OK;
+}
+
+int tile_counter(int** out, cudaStream_t st)
+{
+    int* slot = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        DeviceState* s = nullptr;
+        int rc = current_state(&s);
+        if (rc) return rc;
+        if (!s->counters) {
+            FMM_CUDA_TRY(cudaMalloc(&s->counters, kCounterRing * sizeof(int)));
+            FMM_CUDA_TRY(cudaMemset(s->counters, 0, kCounterRing * sizeof(int)));
+        }
+        slot = s->counters + (s->next_counter++ % kCounterRing);
+    }
+    FMM_CUDA_TRY(cudaMemsetAsync(slot, 0, sizeof(int), st));
+    *out = slot;
     return FMM_OK;
 }
 
@@ -319,7 +357,11 @@ int fmm_prepare(int32_t p, int32_t prec)
     if (!valid_p(p)) return fail(FMM_EINVAL, "fmm_prepare: unsupported p = %d (6, 8, 12, 16, 24)", p);
     if (prec != FMM_FP32) return fail(FMM_EUNSUPPORTED, "fmm_prepare: precision %d not provided by this build", prec);
     const M2LTables* t = nullptr;
-    return get_m2l_tables(p, &t);
+    int rc = get_m2l_tables(p, &t);
+    if (rc) return rc;
+    int* ctr = nullptr;
+    if ((rc = tile_counter(&ctr, nullptr))) return rc;
+    return cudaStreamSynchronize(nullptr) == cudaSuccess ? FMM_OK : fail(FMM_ECUDA, "fmm_prepare: sync failed");
 }
 
 static int m2l_common(const char* who, const fmm_tree* tree, int32_t level, int32_t p, int32_t prec,

@@ -28,6 +28,15 @@ void clear_error();
 enum : int { DEV_ERR_CHECK = 1, DEV_ERR_TIMEOUT = 2 };
 int device_error_word(int** out);
 
+// Number of SMs of the current device (cached).
+int device_sm_count(int* out);
+
+// A zeroed work counter for one persistent launch on `st`: a slot of a
+// per-device ring of 256 counters, reset by cudaMemsetAsync on `st` (so a
+// captured graph resets it on every replay).  Launches that overlap on the
+// GPU use different slots unless 256 or more are in flight at once.
+int tile_counter(int** out, cudaStream_t st);
+
 // ---------------------------------------------------------------------------
 // offset codes: box offset (dx, dy) = source - target, |dx|,|dy| <= 3
 // ---------------------------------------------------------------------------

@@ -14,24 +14,28 @@
 //
 // Work decomposition (GB300-first; replaces the paper's thread-per-row,
 // source-centric kernel and its separate reduction kernel, Sec. 4.1.1):
-//   - a CTA owns an 8 x 4 tile of parent boxes = 128 target boxes of one level
-//     (4 x 4 tile for p = 24); one launch covers every tile of every requested
-//     level (heaviest level first), so the ~680 CTAs of the level 2..8 pass are
-//     resident in one wave (5 CTAs per SM at p = 16) and one CTA's staging
-//     overlaps the others' arithmetic;
-//   - the parent halo (tile + 1 on each side) holds every source any target
-//     needs; each source ME is read once per tile and reused by up to 27
-//     targets;
+//   - the unit of work is a 4 x 4 tile of parent boxes = 64 target boxes of
+//     one level; one persistent launch covers every tile of every requested
+//     level: each CTA takes tile blockIdx.x, then pulls further tiles from a
+//     device counter, so the ~1.4k tiles of the level 2..8 pass spread evenly
+//     over the 152 SMs;
+//   - the parent halo (tile + 1 on each side) holds every source any of the
+//     64 targets needs; it is fetched with cp.async into one of two shared
+//     buffers while the other buffer's tile is being computed, then scaled by
+//     b_k in place;
 //   - the halo is stored in shared memory split by child class
 //     c' = (ix & 1) + 2 (iy & 1) and transposed to [c'][k][hy][hx], so that
 //     for a target class c every interaction-list entry is a constant shift
 //     (ex, ey) inside one class plane;
-//   - warp w handles the targets of child class c = w, whose 27 list offsets
-//     are therefore warp-uniform (no divergence); a lane owns all p rows of
-//     one target (two lanes of p/2 rows each for p = 24), so each k step costs
-//     two shared loads (one ME value, one new Hankel value) per 4p FFMA;
+//   - warp w handles the 16 targets of child class c = w, whose 27 list
+//     offsets are therefore warp-uniform; lane = (half, target): for p <= 16
+//     a lane keeps all p rows of its target and the two half-warps take 14
+//     and 13 of the 27 list entries (one shuffle adds the halves), so each k
+//     step costs two shared loads per 4p FFMA; for p = 24 the halves split
+//     the rows instead (register budget);
 //   - the reduction over the list is a register accumulation, written once
-//     per target (no separate reduction kernel, no atomics: deterministic).
+//     per target (no separate reduction kernel, no atomics on the data:
+//     deterministic).
 #include "common.cuh"
 
 namespace fmmgb {
@@ -91,22 +95,19 @@ int launch_build_m2l_tables(const M2LTables& t, cudaStream_t st)
 // stencil kernel
 // ---------------------------------------------------------------------------
 constexpr int kThreads = 128;  // 4 warps, one per target child class
-constexpr int kTileY = 4;      // parent rows per tile
+constexpr int kTile = 4;       // parent boxes per tile side
+constexpr int kHalo = kTile + 2;
+constexpr int kPlane = kHalo * kHalo + 1;  // float2 stride between k-planes
 
-// NB = row blocks per target: NB = 1 (one lane = all p rows of one target,
-// 8 x 4 parent tile, 32 targets per class) for p <= 16; NB = 2 (two lanes per
-// target, 4 x 4 tile) for p = 24 to bound registers.
 template <int P>
 struct M2LCfg {
-    static constexpr int NB = P <= 16 ? 1 : 2;
-    static constexpr int TX = 8 / NB;                  // parent columns per tile
-    static constexpr int HX = TX + 2, HY = kTileY + 2;  // halo parents
-    static constexpr int PL = HX * HY + 1;            // float2 stride between k-planes
-    static constexpr int RN = P / NB;                 // rows per lane
-    static constexpr int NH = 2 * P - 1;              // Hankel diagonals
-    static constexpr int CS = P * PL;                 // float2 stride between class planes
-    static constexpr int Q = P / 2;                   // float4 per box
-    static constexpr size_t smem = sizeof(float2) * (4 * CS + kOffsetSlots * NH) + sizeof(float) * 2 * P;
+    static constexpr bool SPLIT_ROWS = P > 16;     // p = 24: the two half-warps split the rows
+    static constexpr int RN = SPLIT_ROWS ? P / 2 : P;  // rows per lane
+    static constexpr int NH = 2 * P - 1;           // Hankel diagonals
+    static constexpr int CS = P * kPlane;          // float2 stride between class planes
+    static constexpr int HALO = 4 * CS;            // float2 per halo buffer
+    static constexpr size_t smem = sizeof(float2) * (2 * HALO + kOffsetSlots * NH) + sizeof(float) * 2 * P +
+                                   sizeof(int2) * 4 * 27 + 16;
 };
 
 __device__ __forceinline__ void cmac(float2& acc, const float2 w, const float2 m)
@@ -117,144 +118,267 @@ __device__ __forceinline__ void cmac(float2& acc, const float2 w, const float2 m
     acc.y = fmaf(w.y, m.x, acc.y);
 }
 
-template <int P>
-__host__ __device__ constexpr int m2l_tiles_p(int level)
+__device__ __forceinline__ void cp_async8(float2* dst, const float2* src, bool valid)
 {
-    using C = M2LCfg<P>;
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    const int n = valid ? 8 : 0;  // 0 source bytes: the 8 destination bytes are zero-filled
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+}
+
+__host__ __device__ inline int m2l_tiles(int level)
+{
     if (level < 2) return 0;
     const int np = 1 << (level - 1);
-    return ((np + C::TX - 1) / C::TX) * ((np + kTileY - 1) / kTileY);
+    const int t = (np + kTile - 1) / kTile;
+    return t * t;
+}
+
+struct TileGeom {
+    const float2* M;
+    float2* L;
+    int side, np, PX0, PY0;
+};
+
+__device__ __forceinline__ TileGeom tile_geom(const M2LLaunch& job, int tile)
+{
+    int li = 0;
+    while (li + 1 < job.nlev && tile >= job.lv[li + 1].tile_begin) ++li;
+    const M2LLevel& lv = job.lv[li];
+    TileGeom g;
+    g.M = lv.M;
+    g.L = lv.L;
+    g.side = 1 << lv.level;
+    g.np = g.side >> 1;
+    const int t = tile - lv.tile_begin;
+    const int tpr = (g.np + kTile - 1) / kTile;
+    g.PX0 = (t % tpr) * kTile;
+    g.PY0 = (t / tpr) * kTile;
+    return g;
+}
+
+// The halo box (hxb, hyb) of a tile, 0 <= hxb, hyb < 2 kHalo, and whether it exists.
+__device__ __forceinline__ bool halo_box(const TileGeom& g, int periodic, int hxb, int hyb, int& ix, int& iy)
+{
+    ix = 2 * g.PX0 - 2 + hxb;
+    iy = 2 * g.PY0 - 2 + hyb;
+    if (periodic) {
+        ix = (ix + 2 * g.side) % g.side;
+        iy = (iy + 2 * g.side) % g.side;
+        return true;
+    }
+    return ix >= 0 && iy >= 0 && ix < g.side && iy < g.side;
+}
+
+// Issue the cp.async copies of one tile's halo into `buf` (zero-filled outside the level).
+template <int P>
+__device__ __forceinline__ void stage_async(const M2LLaunch& job, int tile, float2* buf)
+{
+    using C = M2LCfg<P>;
+    const TileGeom g = tile_geom(job, tile);
+    for (int i = threadIdx.x; i < (2 * kHalo) * (2 * kHalo) * P; i += kThreads) {
+        const int k = i % P, bxy = i / P;
+        const int hxb = bxy % (2 * kHalo), hyb = bxy / (2 * kHalo);
+        int ix, iy;
+        const bool in = halo_box(g, job.periodic, hxb, hyb, ix, iy);
+        const float2* src = in ? g.M + ((size_t)iy * g.side + ix) * P + k : g.M;
+        float2* dst = buf + ((hxb & 1) + 2 * (hyb & 1)) * C::CS + k * kPlane + (hyb >> 1) * kHalo + (hxb >> 1);
+        cp_async8(dst, src, in);
+    }
+}
+
+// Scale the elements this thread copied by b_k (same index walk as stage_async).
+template <int P>
+__device__ __forceinline__ void scale_own(float2* buf, const float* bs)
+{
+    using C = M2LCfg<P>;
+    for (int i = threadIdx.x; i < (2 * kHalo) * (2 * kHalo) * P; i += kThreads) {
+        const int k = i % P, bxy = i / P;
+        const int hxb = bxy % (2 * kHalo), hyb = bxy / (2 * kHalo);
+        float2* d = buf + ((hxb & 1) + 2 * (hyb & 1)) * C::CS + k * kPlane + (hyb >> 1) * kHalo + (hxb >> 1);
+        float2 v = *d;
+        v.x *= bs[k];
+        v.y *= bs[k];
+        *d = v;
+    }
 }
 
 template <int P>
 __global__ void __launch_bounds__(kThreads) m2l_fp32_kernel(M2LLaunch job, const float2* __restrict__ hsel,
                                                             const float* __restrict__ ascale,
-                                                            const float* __restrict__ bscale)
+                                                            const float* __restrict__ bscale,
+                                                            int* __restrict__ tile_counter, int total_tiles)
 {
     using C = M2LCfg<P>;
-    constexpr int NB = C::NB, TX = C::TX, HX = C::HX, HY = C::HY, PL = C::PL;
-    constexpr int RN = C::RN, NH = C::NH, CS = C::CS, Q = C::Q;
+    constexpr int RN = C::RN, NH = C::NH;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2* halo = reinterpret_cast<float2*>(smem_raw);  // [4][P][PL]
-    float2* hs = halo + 4 * CS;                            // [49][NH]
+    float2* halo0 = reinterpret_cast<float2*>(smem_raw);  // 2 x [4][P][kPlane]
+    float2* hs = halo0 + 2 * C::HALO;                       // [49][NH]
     float* as = reinterpret_cast<float*>(hs + kOffsetSlots * NH);
     float* bs = as + P;
-
-    // which level / tile this CTA owns (levels are listed heaviest first)
-    int li = 0;
-    while (li + 1 < job.nlev && (int)blockIdx.x >= job.lv[li + 1].tile_begin) ++li;
-    const M2LLevel lv = job.lv[li];
-    const int tile = (int)blockIdx.x - lv.tile_begin;
-    const int side = 1 << lv.level;
-    const int np = side >> 1;
-    const int tpr = (np + TX - 1) / TX;  // tiles per row
-    const int PX0 = (tile % tpr) * TX, PY0 = (tile / tpr) * kTileY;
-    const int bx0 = 2 * PX0 - 2, by0 = 2 * PY0 - 2;  // first halo box (even)
+    int2* lst = reinterpret_cast<int2*>(bs + P);  // [4][27]: (Hankel row offset, halo offset)
+    int* s_next = reinterpret_cast<int*>(lst + 4 * 27);
 
     const int tid = threadIdx.x;
+    int tile = blockIdx.x;
+    stage_async<P>(job, tile, halo0);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+
     for (int i = tid; i < kOffsetSlots * NH; i += kThreads) hs[i] = hsel[i];
     for (int i = tid; i < P; i += kThreads) {
         as[i] = ascale[i];
         bs[i] = bscale[i];
     }
-    __syncthreads();
-
-    // Stage the 2 HX x 2 HY halo boxes, pre-scaled by b_k, into the class-split
-    // transposed layout.  Consecutive threads read consecutive 16-byte chunks of
-    // a row of boxes (coalesced).
-    const float4* M4 = reinterpret_cast<const float4*>(lv.M);
-    for (int i = tid; i < (2 * HX) * (2 * HY) * Q; i += kThreads) {
-        const int q = i % Q;
-        const int bxy = i / Q;
-        const int hxb = bxy % (2 * HX), hyb = bxy / (2 * HX);
-        int ix = bx0 + hxb, iy = by0 + hyb;
-        bool inside = ix >= 0 && iy >= 0 && ix < side && iy < side;
-        if (job.periodic) {
-            ix = (ix + 2 * side) % side;
-            iy = (iy + 2 * side) % side;
-            inside = true;
+    if (tid < 4) {  // the 27 interaction-list entries of child class tid, in (ey, ex, c') order
+        const int cx = tid & 1, cy = tid >> 1;
+        int n = 0;
+        for (int e = 0; e < 36; ++e) {
+            const int sx = e & 1, sy = (e >> 1) & 1, pe = e >> 2;
+            const int ex = pe % 3 - 1, ey = pe / 3 - 1;
+            const int dx = 2 * ex + sx - cx, dy = 2 * ey + sy - cy;
+            const int adx = dx < 0 ? -dx : dx, ady = dy < 0 ? -dy : dy;
+            if ((adx > ady ? adx : ady) < 2) continue;  // adjacent: near field
+            lst[tid * 27 + n++] = make_int2(offset_slot(dx, dy) * NH, (sx + 2 * sy) * C::CS + (ey + 1) * kHalo + (ex + 1));
         }
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (inside) v = __ldg(M4 + ((size_t)iy * side + ix) * Q + q);
-        const int cls = (hxb & 1) + 2 * (hyb & 1);
-        float2* dst = halo + cls * CS + (hyb >> 1) * HX + (hxb >> 1);
-        const float b0 = bs[2 * q], b1 = bs[2 * q + 1];
-        dst[(2 * q) * PL] = make_float2(v.x * b0, v.y * b0);
-        dst[(2 * q + 1) * PL] = make_float2(v.z * b1, v.w * b1);
     }
+    if (tid == 0) *s_next = gridDim.x + atomicAdd(tile_counter, 1);
     __syncthreads();
 
     const int warp = tid >> 5, lane = tid & 31;
-    const int cx = warp & 1, cy = warp >> 1;  // target child class
-    const int i_n = lane % NB, i_t = lane / NB;
-    const int n0 = i_n * RN;
-    const int tpx = i_t % TX, tpy = i_t / TX;  // target parent within the tile
+    const int cls = warp, cx = warp & 1, cy = warp >> 1;
+    const int half = lane >> 4, t = lane & 15;
+    const int tpx = t & 3, tpy = t >> 2;
+    const int2* mylist = lst + cls * 27;
+    int next = *s_next;
+    int b = 0;
 
-    float2 acc[RN];
+    while (true) {
+        float2* buf = halo0 + b * C::HALO;
+        if (next < total_tiles) stage_async<P>(job, next, halo0 + (b ^ 1) * C::HALO);
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+        asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+        __syncthreads();
+        scale_own<P>(buf, bs);
+        __syncthreads();
+
+        // ---- translate and reduce ----
+        float2 acc[RN];
 #pragma unroll
-    for (int i = 0; i < RN; ++i) acc[i] = make_float2(0.f, 0.f);
-
+        for (int i = 0; i < RN; ++i) acc[i] = make_float2(0.f, 0.f);
+        const float2* tbase = buf + tpy * kHalo + tpx;
+        if constexpr (!C::SPLIT_ROWS) {
+            // half-warp `half` takes list entries [14 half, 14 half + 14) of 27; all p rows
 #pragma unroll 1
-    for (int e = 0; e < 36; ++e) {
-        // (parent offset, source child class): e = ((ey+1)*3 + (ex+1))*4 + sy*2 + sx
-        const int sx = e & 1, sy = (e >> 1) & 1;
-        const int pe = e >> 2;
-        const int ex = pe % 3 - 1, ey = pe / 3 - 1;
-        const int dx = 2 * ex + sx - cx, dy = 2 * ey + sy - cy;
-        const int adx = dx < 0 ? -dx : dx, ady = dy < 0 ? -dy : dy;
-        if ((adx > ady ? adx : ady) < 2) continue;  // adjacent: not in the interaction list (warp-uniform)
+            for (int j = 0; j < 14; ++j) {
+                const int e = half * 14 + j;
+                if (e >= 27) break;
+                const int2 ent = mylist[e];
+                const float2* hrow = hs + ent.x;
+                const float2* src = tbase + ent.y;
+                float2 w[RN];
+#pragma unroll
+                for (int i = 0; i < RN; ++i) w[i] = hrow[i];
+#pragma unroll
+                for (int k = 0; k < P; ++k) {
+                    const float2 m = src[k * kPlane];
+#pragma unroll
+                    for (int i = 0; i < RN; ++i) cmac(acc[i], w[i], m);
+                    if (k + 1 < P) {
+#pragma unroll
+                        for (int i = 0; i + 1 < RN; ++i) w[i] = w[i + 1];
+                        w[RN - 1] = hrow[RN + k];
+                    }
+                }
+            }
+        } else {
+            // half-warp `half` takes rows [RN half, RN half + RN); all 27 entries
+            const int n0 = half * RN;
+#pragma unroll 1
+            for (int e = 0; e < 27; ++e) {
+                const int2 ent = mylist[e];
+                const float2* hrow = hs + ent.x + n0;
+                const float2* src = tbase + ent.y;
+                float2 w[RN];
+#pragma unroll
+                for (int i = 0; i < RN; ++i) w[i] = hrow[i];
+#pragma unroll
+                for (int k = 0; k < P; ++k) {
+                    const float2 m = src[k * kPlane];
+#pragma unroll
+                    for (int i = 0; i < RN; ++i) cmac(acc[i], w[i], m);
+                    if (k + 1 < P) {
+#pragma unroll
+                        for (int i = 0; i + 1 < RN; ++i) w[i] = w[i + 1];
+                        w[RN - 1] = hrow[RN + k];
+                    }
+                }
+            }
+        }
 
-        const float2* hrow = hs + offset_slot(dx, dy) * NH + n0;
-        const float2* src = halo + (sx + 2 * sy) * CS + (tpy + ey + 1) * HX + (tpx + ex + 1);
-        float2 w[RN];
+        // ---- combine the half-warps: each lane ends with p/2 finished rows ----
+        constexpr int HR = P / 2;
+        float2 res[HR];
+        if constexpr (!C::SPLIT_ROWS) {
 #pragma unroll
-        for (int i = 0; i < RN; ++i) w[i] = hrow[i];
-#pragma unroll
-        for (int k = 0; k < P; ++k) {
-            const float2 m = src[k * PL];
-#pragma unroll
-            for (int i = 0; i < RN; ++i) cmac(acc[i], w[i], m);
-            if (k + 1 < P) {
-#pragma unroll
-                for (int i = 0; i + 1 < RN; ++i) w[i] = w[i + 1];
-                w[RN - 1] = hrow[RN + k];
+            for (int i = 0; i < HR; ++i) {
+                const float2 send = half ? acc[i] : acc[HR + i];
+                const float2 mine = half ? acc[HR + i] : acc[i];
+                float2 r;
+                r.x = __shfl_xor_sync(0xffffffffu, send.x, 16);
+                r.y = __shfl_xor_sync(0xffffffffu, send.y, 16);
+                res[i] = make_float2(mine.x + r.x, mine.y + r.y);
             }
+        } else {
+#pragma unroll
+            for (int i = 0; i < HR; ++i) res[i] = acc[i];
         }
-    }
 
-    // store L~[n] = a_n * acc (the fused reduction's result)
-    const int px = PX0 + tpx, py = PY0 + tpy;
-    if (px >= np || py >= np) return;
-    const int ix = 2 * px + cx, iy = 2 * py + cy;
-    float2* dst = lv.L + ((size_t)iy * side + ix) * P + n0;
-    if constexpr (RN % 2 == 0) {
-        float4* d4 = reinterpret_cast<float4*>(dst);
+        // ---- store L~[n] = a_n * res (rows [HR half, HR half + HR)) ----
+        {
+            const TileGeom g = tile_geom(job, tile);
+            const int px = g.PX0 + tpx, py = g.PY0 + tpy;
+            if (px < g.np && py < g.np) {
+                const int ix = 2 * px + cx, iy = 2 * py + cy;
+                const int n0 = half * HR;
+                float2* dst = g.L + ((size_t)iy * g.side + ix) * P + n0;
+                if constexpr (HR % 2 == 0) {
+                    float4* d4 = reinterpret_cast<float4*>(dst);
 #pragma unroll
-        for (int i = 0; i < RN; i += 2) {
-            const float s0 = as[n0 + i], s1 = as[n0 + i + 1];
-            float4 o = make_float4(s0 * acc[i].x, s0 * acc[i].y, s1 * acc[i + 1].x, s1 * acc[i + 1].y);
-            if (job.accumulate) {
-                const float4 old = d4[i / 2];
-                o.x += old.x;
-                o.y += old.y;
-                o.z += old.z;
-                o.w += old.w;
-            }
-            d4[i / 2] = o;
-        }
-    } else {
+                    for (int i = 0; i < HR; i += 2) {
+                        const float s0 = as[n0 + i], s1 = as[n0 + i + 1];
+                        float4 o = make_float4(s0 * res[i].x, s0 * res[i].y, s1 * res[i + 1].x, s1 * res[i + 1].y);
+                        if (job.accumulate) {
+                            const float4 old = d4[i / 2];
+                            o.x += old.x;
+                            o.y += old.y;
+                            o.z += old.z;
+                            o.w += old.w;
+                        }
+                        d4[i / 2] = o;
+                    }
+                } else {
 #pragma unroll
-        for (int i = 0; i < RN; ++i) {
-            const float s0 = as[n0 + i];
-            float2 o = make_float2(s0 * acc[i].x, s0 * acc[i].y);
-            if (job.accumulate) {
-                const float2 old = dst[i];
-                o.x += old.x;
-                o.y += old.y;
+                    for (int i = 0; i < HR; ++i) {
+                        const float s0 = as[n0 + i];
+                        float2 o = make_float2(s0 * res[i].x, s0 * res[i].y);
+                        if (job.accumulate) {
+                            const float2 old = dst[i];
+                            o.x += old.x;
+                            o.y += old.y;
+                        }
+                        dst[i] = o;
+                    }
+                }
             }
-            dst[i] = o;
         }
+
+        if (next >= total_tiles) break;
+        if (tid == 0) *s_next = gridDim.x + atomicAdd(tile_counter, 1);
+        __syncthreads();  // every lane is done with `buf`; s_next is visible
+        tile = next;
+        next = *s_next;
+        b ^= 1;
     }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
 bool m2l_fp32_supported(int p) { return p == 6 || p == 8 || p == 12 || p == 16 || p == 24; }
@@ -266,11 +390,19 @@ static int launch_p(M2LLaunch& job, const float2* h, const float* a, const float
     int total = 0;
     for (int i = 0; i < job.nlev; ++i) {
         job.lv[i].tile_begin = total;
-        total += m2l_tiles_p<P>(job.lv[i].level);
+        total += m2l_tiles(job.lv[i].level);
     }
     if (total == 0) return FMM_OK;
     FMM_CUDA_TRY(cudaFuncSetAttribute(m2l_fp32_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem));
-    m2l_fp32_kernel<P><<<total, kThreads, C::smem, st>>>(job, h, a, b);
+    int sms = 0, per_sm = 0;
+    int rc = device_sm_count(&sms);
+    if (rc) return rc;
+    FMM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, m2l_fp32_kernel<P>, kThreads, C::smem));
+    if (per_sm < 1) return fail(FMM_ECUDA, "M2L FP32 p=%d: kernel does not fit on an SM", P);
+    const int grid = total < sms * per_sm ? total : sms * per_sm;
+    int* ctr = nullptr;
+    if ((rc = tile_counter(&ctr, st))) return rc;
+    m2l_fp32_kernel<P><<<grid, kThreads, C::smem, st>>>(job, h, a, b, ctr, total);
     FMM_CUDA_TRY(cudaGetLastError());
     return FMM_OK;
 }
