@@ -14,15 +14,14 @@
 //
 // Work decomposition (GB300-first; replaces the paper's thread-per-row,
 // source-centric kernel and its separate reduction kernel, Sec. 4.1.1):
-//   - the unit of work is a 4 x 4 tile of parent boxes = 64 target boxes of
-//     one level; one persistent launch covers every tile of every requested
-//     level: each CTA takes tile blockIdx.x, then pulls further tiles from a
-//     device counter, so the ~1.4k tiles of the level 2..8 pass spread evenly
-//     over the 152 SMs;
+//   - a CTA owns a 4 x 4 tile of parent boxes = 64 target boxes of one level;
+//     one launch covers every tile of every requested level (heaviest level
+//     first); the ~1.4k CTAs of the level 2..8 pass run about 9 per SM in two
+//     rounds of 5-6 resident CTAs, which the hardware block scheduler keeps
+//     balanced;
 //   - the parent halo (tile + 1 on each side) holds every source any of the
-//     64 targets needs; it is fetched with cp.async into one of two shared
-//     buffers while the other buffer's tile is being computed, then scaled by
-//     b_k in place;
+//     64 targets needs; each source ME is read once per tile (coalesced
+//     16-byte loads), scaled by b_k and reused by up to 27 targets;
 //   - the halo is stored in shared memory split by child class
 //     c' = (ix & 1) + 2 (iy & 1) and transposed to [c'][k][hy][hx], so that
 //     for a target class c every interaction-list entry is a constant shift
@@ -34,8 +33,7 @@
 //     step costs two shared loads per 4p FFMA; for p = 24 the halves split
 //     the rows instead (register budget);
 //   - the reduction over the list is a register accumulation, written once
-//     per target (no separate reduction kernel, no atomics on the data:
-//     deterministic).
+//     per target (no separate reduction kernel, no atomics: deterministic).
 #include "common.cuh"
 
 namespace fmmgb {
@@ -106,8 +104,9 @@ struct M2LCfg {
     static constexpr int NH = 2 * P - 1;           // Hankel diagonals
     static constexpr int CS = P * kPlane;          // float2 stride between class planes
     static constexpr int HALO = 4 * CS;            // float2 per halo buffer
-    static constexpr size_t smem = sizeof(float2) * (2 * HALO + kOffsetSlots * NH) + sizeof(float) * 2 * P +
-                                   sizeof(int2) * 4 * 27 + 16;
+    static constexpr int MIN_CTAS = P == 16 ? 6 : 1;  // p = 16: 6 resident CTAs per SM (<= 80 registers)
+    static constexpr size_t smem = sizeof(float2) * (HALO + kOffsetSlots * NH) + sizeof(float) * 2 * P +
+                                   sizeof(int2) * 4 * 27;
 };
 
 __device__ __forceinline__ void cmac(float2& acc, const float2 w, const float2 m)
@@ -116,13 +115,6 @@ __device__ __forceinline__ void cmac(float2& acc, const float2 w, const float2 m
     acc.x = fmaf(-w.y, m.y, acc.x);
     acc.y = fmaf(w.x, m.y, acc.y);
     acc.y = fmaf(w.y, m.x, acc.y);
-}
-
-__device__ __forceinline__ void cp_async8(float2* dst, const float2* src, bool valid)
-{
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    const int n = valid ? 8 : 0;  // 0 source bytes: the 8 destination bytes are zero-filled
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
 }
 
 __host__ __device__ inline int m2l_tiles(int level)
@@ -156,72 +148,23 @@ __device__ __forceinline__ TileGeom tile_geom(const M2LLaunch& job, int tile)
     return g;
 }
 
-// The halo box (hxb, hyb) of a tile, 0 <= hxb, hyb < 2 kHalo, and whether it exists.
-__device__ __forceinline__ bool halo_box(const TileGeom& g, int periodic, int hxb, int hyb, int& ix, int& iy)
-{
-    ix = 2 * g.PX0 - 2 + hxb;
-    iy = 2 * g.PY0 - 2 + hyb;
-    if (periodic) {
-        ix = (ix + 2 * g.side) % g.side;
-        iy = (iy + 2 * g.side) % g.side;
-        return true;
-    }
-    return ix >= 0 && iy >= 0 && ix < g.side && iy < g.side;
-}
-
-// Issue the cp.async copies of one tile's halo into `buf` (zero-filled outside the level).
 template <int P>
-__device__ __forceinline__ void stage_async(const M2LLaunch& job, int tile, float2* buf)
-{
-    using C = M2LCfg<P>;
-    const TileGeom g = tile_geom(job, tile);
-    for (int i = threadIdx.x; i < (2 * kHalo) * (2 * kHalo) * P; i += kThreads) {
-        const int k = i % P, bxy = i / P;
-        const int hxb = bxy % (2 * kHalo), hyb = bxy / (2 * kHalo);
-        int ix, iy;
-        const bool in = halo_box(g, job.periodic, hxb, hyb, ix, iy);
-        const float2* src = in ? g.M + ((size_t)iy * g.side + ix) * P + k : g.M;
-        float2* dst = buf + ((hxb & 1) + 2 * (hyb & 1)) * C::CS + k * kPlane + (hyb >> 1) * kHalo + (hxb >> 1);
-        cp_async8(dst, src, in);
-    }
-}
-
-// Scale the elements this thread copied by b_k (same index walk as stage_async).
-template <int P>
-__device__ __forceinline__ void scale_own(float2* buf, const float* bs)
-{
-    using C = M2LCfg<P>;
-    for (int i = threadIdx.x; i < (2 * kHalo) * (2 * kHalo) * P; i += kThreads) {
-        const int k = i % P, bxy = i / P;
-        const int hxb = bxy % (2 * kHalo), hyb = bxy / (2 * kHalo);
-        float2* d = buf + ((hxb & 1) + 2 * (hyb & 1)) * C::CS + k * kPlane + (hyb >> 1) * kHalo + (hxb >> 1);
-        float2 v = *d;
-        v.x *= bs[k];
-        v.y *= bs[k];
-        *d = v;
-    }
-}
-
-template <int P>
-__global__ void __launch_bounds__(kThreads) m2l_fp32_kernel(M2LLaunch job, const float2* __restrict__ hsel,
+__global__ void __launch_bounds__(kThreads, M2LCfg<P>::MIN_CTAS) m2l_fp32_kernel(M2LLaunch job, const float2* __restrict__ hsel,
                                                             const float* __restrict__ ascale,
-                                                            const float* __restrict__ bscale,
-                                                            int* __restrict__ tile_counter, int total_tiles)
+                                                            const float* __restrict__ bscale)
 {
     using C = M2LCfg<P>;
-    constexpr int RN = C::RN, NH = C::NH;
+    constexpr int RN = C::RN, NH = C::NH, Q = P / 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2* halo0 = reinterpret_cast<float2*>(smem_raw);  // 2 x [4][P][kPlane]
-    float2* hs = halo0 + 2 * C::HALO;                       // [49][NH]
+    float2* buf = reinterpret_cast<float2*>(smem_raw);  // [4][P][kPlane]
+    float2* hs = buf + C::HALO;                           // [49][NH]
     float* as = reinterpret_cast<float*>(hs + kOffsetSlots * NH);
     float* bs = as + P;
     int2* lst = reinterpret_cast<int2*>(bs + P);  // [4][27]: (Hankel row offset, halo offset)
-    int* s_next = reinterpret_cast<int*>(lst + 4 * 27);
 
     const int tid = threadIdx.x;
-    int tile = blockIdx.x;
-    stage_async<P>(job, tile, halo0);
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    const int tile = blockIdx.x;
+    const TileGeom g = tile_geom(job, tile);
 
     for (int i = tid; i < kOffsetSlots * NH; i += kThreads) hs[i] = hsel[i];
     for (int i = tid; i < P; i += kThreads) {
@@ -240,7 +183,29 @@ __global__ void __launch_bounds__(kThreads) m2l_fp32_kernel(M2LLaunch job, const
             lst[tid * 27 + n++] = make_int2(offset_slot(dx, dy) * NH, (sx + 2 * sy) * C::CS + (ey + 1) * kHalo + (ex + 1));
         }
     }
-    if (tid == 0) *s_next = gridDim.x + atomicAdd(tile_counter, 1);
+    __syncthreads();
+
+    // Stage the 2 kHalo x 2 kHalo halo boxes, pre-scaled by b_k, into the
+    // class-split transposed layout; consecutive threads read consecutive
+    // 16-byte chunks of a row of boxes (coalesced); zero outside the level.
+    const float4* M4 = reinterpret_cast<const float4*>(g.M);
+    for (int i = tid; i < (2 * kHalo) * (2 * kHalo) * Q; i += kThreads) {
+        const int q = i % Q, bxy = i / Q;
+        const int hxb = bxy % (2 * kHalo), hyb = bxy / (2 * kHalo);
+        int ix = 2 * g.PX0 - 2 + hxb, iy = 2 * g.PY0 - 2 + hyb;
+        bool in = ix >= 0 && iy >= 0 && ix < g.side && iy < g.side;
+        if (job.periodic) {
+            ix = (ix + 2 * g.side) % g.side;
+            iy = (iy + 2 * g.side) % g.side;
+            in = true;
+        }
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (in) v = __ldg(M4 + ((size_t)iy * g.side + ix) * Q + q);
+        float2* dst = buf + ((hxb & 1) + 2 * (hyb & 1)) * C::CS + (hyb >> 1) * kHalo + (hxb >> 1);
+        const float b0 = bs[2 * q], b1 = bs[2 * q + 1];
+        dst[(2 * q) * kPlane] = make_float2(v.x * b0, v.y * b0);
+        dst[(2 * q + 1) * kPlane] = make_float2(v.z * b1, v.w * b1);
+    }
     __syncthreads();
 
     const int warp = tid >> 5, lane = tid & 31;
@@ -248,18 +213,7 @@ __global__ void __launch_bounds__(kThreads) m2l_fp32_kernel(M2LLaunch job, const
     const int half = lane >> 4, t = lane & 15;
     const int tpx = t & 3, tpy = t >> 2;
     const int2* mylist = lst + cls * 27;
-    int next = *s_next;
-    int b = 0;
-
-    while (true) {
-        float2* buf = halo0 + b * C::HALO;
-        if (next < total_tiles) stage_async<P>(job, next, halo0 + (b ^ 1) * C::HALO);
-        asm volatile("cp.async.commit_group;\n" ::: "memory");
-        asm volatile("cp.async.wait_group 1;\n" ::: "memory");
-        __syncthreads();
-        scale_own<P>(buf, bs);
-        __syncthreads();
-
+    {
         // ---- translate and reduce ----
         float2 acc[RN];
 #pragma unroll
@@ -334,7 +288,6 @@ __global__ void __launch_bounds__(kThreads) m2l_fp32_kernel(M2LLaunch job, const
 
         // ---- store L~[n] = a_n * res (rows [HR half, HR half + HR)) ----
         {
-            const TileGeom g = tile_geom(job, tile);
             const int px = g.PX0 + tpx, py = g.PY0 + tpy;
             if (px < g.np && py < g.np) {
                 const int ix = 2 * px + cx, iy = 2 * py + cy;
@@ -371,14 +324,7 @@ __global__ void __launch_bounds__(kThreads) m2l_fp32_kernel(M2LLaunch job, const
             }
         }
 
-        if (next >= total_tiles) break;
-        if (tid == 0) *s_next = gridDim.x + atomicAdd(tile_counter, 1);
-        __syncthreads();  // every lane is done with `buf`; s_next is visible
-        tile = next;
-        next = *s_next;
-        b ^= 1;
     }
-    asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
 bool m2l_fp32_supported(int p) { return p == 6 || p == 8 || p == 12 || p == 16 || p == 24; }
@@ -394,15 +340,7 @@ static int launch_p(M2LLaunch& job, const float2* h, const float* a, const float
     }
     if (total == 0) return FMM_OK;
     FMM_CUDA_TRY(cudaFuncSetAttribute(m2l_fp32_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem));
-    int sms = 0, per_sm = 0;
-    int rc = device_sm_count(&sms);
-    if (rc) return rc;
-    FMM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, m2l_fp32_kernel<P>, kThreads, C::smem));
-    if (per_sm < 1) return fail(FMM_ECUDA, "M2L FP32 p=%d: kernel does not fit on an SM", P);
-    const int grid = total < sms * per_sm ? total : sms * per_sm;
-    int* ctr = nullptr;
-    if ((rc = tile_counter(&ctr, st))) return rc;
-    m2l_fp32_kernel<P><<<grid, kThreads, C::smem, st>>>(job, h, a, b, ctr, total);
+    m2l_fp32_kernel<P><<<total, kThreads, C::smem, st>>>(job, h, a, b);
     FMM_CUDA_TRY(cudaGetLastError());
     return FMM_OK;
 }
