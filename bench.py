@@ -297,13 +297,49 @@ def run_ours(args):
         def adjoint():
             fmmgb.fmm_m2l_adjoint_levels(tree, LEVELS[0], P, Ls, Gs, conj=True, stream=stream)
 
+        def tc_x3():
+            fmmgb.fmm_m2l_levels(tree, LEVELS[0], P, Ms, Ls, prec=fmmgb.FMM_TC_BF16X3, stream=stream)
+
+        def tc_x1():
+            fmmgb.fmm_m2l_levels(tree, LEVELS[0], P, Ms, Ls, prec=fmmgb.FMM_TC_BF16, stream=stream)
+
         for name, fn, launches in (("m2l_fp32_one_launch_per_level", per_level, len(LEVELS)),
-                                   ("m2l_adjoint_fp32_levels_2_8", adjoint, 1)):
+                                   ("m2l_adjoint_fp32_levels_2_8", adjoint, 1),
+                                   ("m2l_tc_bf16x3_levels_2_8", tc_x3, 1),
+                                   ("m2l_tc_bf16_levels_2_8", tc_x1, 1)):
             fn()
             torch.cuda.synchronize()
             ms = statistics.median(_timed(torch, fn, args.steps, stream, flush))
             rows[name] = {"translations_per_s": NTR / (ms * 1e-3), "ms": ms, "launches": launches,
                           "gflops": NTR * metrics.m2l_flops_per_translation(P) / (ms * 1e-3) / 1e9}
+        # precision study at p = 24 on the same tree: FP32 kernel vs tensor cores (BF16x3)
+        p24 = workloads.CONFIGS["m2l_tc"]["p"]
+        xyd = torch.from_numpy(xy).to(dev)
+        cd = torch.from_numpy(c).to(dev)
+        M24 = {l: torch.empty((4 ** l, p24), dtype=torch.complex64, device=dev) for l in LEVELS}
+        L24 = {l: torch.empty((4 ** l, p24), dtype=torch.complex64, device=dev) for l in LEVELS}
+        fmmgb.fmm_p2m(MAXL, p24, xyd, cd, M24[MAXL])
+        for l in range(MAXL, LEVELS[0], -1):
+            fmmgb.fmm_m2m(l, p24, M24[l], M24[l - 1])
+        del xyd, cd
+        M24s, L24s = [M24[l] for l in LEVELS], [L24[l] for l in LEVELS]
+        t24 = {}
+        for name, prec in (("m2l_fp32_p24_levels_2_8", fmmgb.FMM_FP32), ("m2l_tc_bf16x3_p24_levels_2_8",
+                                                                         fmmgb.FMM_TC_BF16X3)):
+            def run24(prec=prec):
+                fmmgb.fmm_m2l_levels(tree, LEVELS[0], p24, M24s, L24s, prec=prec, stream=stream)
+
+            run24()
+            torch.cuda.synchronize()
+            ms = statistics.median(_timed(torch, run24, args.steps, stream, flush))
+            t24[prec] = ms
+            rows[name] = {"translations_per_s": NTR / (ms * 1e-3), "ms": ms, "launches": 1,
+                          "gflops": NTR * metrics.m2l_flops_per_translation(p24) / (ms * 1e-3) / 1e9}
+        rows["tc_vs_fp32_speedup_p24"] = {"speedup": t24[fmmgb.FMM_FP32] / t24[fmmgb.FMM_TC_BF16X3],
+                                          "note": "both meet the tensor-core bar (truncation + 1e-4); "
+                                                  "measured coefficient errors in tests/test_m2l_tc_gpu.py"}
+        rows["tc_vs_fp32_speedup_p16"] = {"speedup": statistics.median(step_ms) / rows["m2l_tc_bf16x3_levels_2_8"]["ms"]}
+        del M24, L24, M24s, L24s
         fcfg = workloads.CONFIGS["fgt"]
         fx, fq = workloads.gmm_particles(fcfg["n"], workloads.rng_for("fgt"))
         fxd = torch.from_numpy(fx).to(dev)

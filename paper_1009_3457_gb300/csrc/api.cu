@@ -208,6 +208,31 @@ int get_m2l_tables(int p, const M2LTables** out)
     return FMM_OK;
 }
 
+int get_tc_image(int p, const void** out)
+{
+    if (!m2l_tc_supported(p)) return fail(FMM_EUNSUPPORTED, "tensor-core M2L is provided for p = 16 and 24, not %d", p);
+    const M2LTables* tc = nullptr;
+    int rc = get_m2l_tables(p, &tc);
+    if (rc) return rc;
+    M2LTables* t = const_cast<M2LTables*>(tc);
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!t->tc_ready) {
+        const size_t bytes = m2l_tc_image_bytes(p);
+        cudaError_t e = cudaMalloc(&t->tc_w, bytes);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(tensor-core operator image)");
+        cudaStream_t st;
+        FMM_CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        rc = launch_build_tc_image(p, t->s, t->tc_w, st);
+        cudaError_t es = cudaStreamSynchronize(st);
+        cudaStreamDestroy(st);
+        if (rc) return rc;
+        if (es != cudaSuccess) return cuda_fail(es, "building the tensor-core operator image");
+        t->tc_ready = 1;
+    }
+    *out = t->tc_w;
+    return FMM_OK;
+}
+
 }  // namespace fmmgb
 
 using namespace fmmgb;
@@ -355,10 +380,15 @@ int fmm_prepare(int32_t p, int32_t prec)
 {
     clear_error();
     if (!valid_p(p)) return fail(FMM_EINVAL, "fmm_prepare: unsupported p = %d (6, 8, 12, 16, 24)", p);
-    if (prec != FMM_FP32) return fail(FMM_EUNSUPPORTED, "fmm_prepare: precision %d not provided by this build", prec);
+    if (prec != FMM_FP32 && prec != FMM_TC_BF16X3 && prec != FMM_TC_BF16)
+        return fail(FMM_EINVAL, "fmm_prepare: unknown precision %d", prec);
     const M2LTables* t = nullptr;
     int rc = get_m2l_tables(p, &t);
     if (rc) return rc;
+    if (prec != FMM_FP32) {
+        const void* img = nullptr;
+        if ((rc = get_tc_image(p, &img))) return rc;
+    }
     int* ctr = nullptr;
     if ((rc = tile_counter(&ctr, nullptr))) return rc;
     return cudaStreamSynchronize(nullptr) == cudaSuccess ? FMM_OK : fail(FMM_ECUDA, "fmm_prepare: sync failed");
@@ -393,8 +423,9 @@ static int m2l_dispatch(const char* who, const fmm_tree* tree, int32_t lmin, int
     for (int l = lmin; l <= lmax && l < 2; ++l)
         if (!acc) FMM_CUDA_TRY(cudaMemsetAsync(out[l - lmin], 0, ((size_t)1 << (2 * l)) * (size_t)p * 8, st));
     if (lmax < 2) return FMM_OK;
-    if (prec != FMM_FP32)
-        return fail(FMM_EUNSUPPORTED, "%s: tensor-core precision %d is not provided for this call", who, prec);
+    if (prec != FMM_FP32 && (adjoint || !m2l_tc_supported(p)))
+        return fail(FMM_EUNSUPPORTED, "%s: tensor-core precision %d is provided for the forward M2L at p = 16, 24",
+                    who, prec);
     const M2LTables* t = nullptr;
     int rc = get_m2l_tables(p, &t);
     if (rc) return rc;
@@ -409,6 +440,11 @@ static int m2l_dispatch(const char* who, const fmm_tree* tree, int32_t lmin, int
     }
     // The adjoint is the forward stencil with the table of -a(D) (plain) or
     // -conj a(D) (FMM_CONJ): a(D)^T = -a(-D) on symmetric lists.
+    if (prec != FMM_FP32) {
+        const void* img = nullptr;
+        if ((rc = get_tc_image(p, &img))) return rc;
+        return launch_m2l_tc(job, p, img, prec == FMM_TC_BF16X3, st);
+    }
     const float2* h = !adjoint ? t->h_fwd : ((flags & FMM_CONJ) ? t->h_adjc : t->h_adj);
     return launch_m2l_fp32(job, p, h, t->a, t->b, st);
 }

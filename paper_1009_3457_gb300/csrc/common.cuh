@@ -97,6 +97,13 @@ int launch_build_m2l_tables(const M2LTables& t, cudaStream_t st);
 bool m2l_fp32_supported(int p);
 int launch_m2l_fp32(M2LLaunch& job, int p, const float2* hsel, const float* a, const float* b, cudaStream_t st);
 
+// launchers (m2l_tc.cu)
+bool m2l_tc_supported(int p);
+size_t m2l_tc_image_bytes(int p);
+int launch_build_tc_image(int p, double s, void* img, cudaStream_t st);
+int launch_m2l_tc(M2LLaunch& job, int p, const void* img, bool split, cudaStream_t st);
+int get_tc_image(int p, const void** out);
+
 // launchers (fgt_h2t.cu)
 bool fgt_supported(int p);
 int fgt_max_cut();

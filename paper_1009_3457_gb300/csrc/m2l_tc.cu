@@ -1,0 +1,448 @@
+// m2l_tc.cu -- M2L + reduction on the 5th-generation tensor cores (tcgen05,
+// TMEM accumulators), BF16 inputs with an optional hi/lo split, FP32
+// accumulation (Sec. 4.1 steps 2-3, Eq. M2Lmat recast as a dense contraction).
+//
+// Recasting.  In radius-scaled units the M2L operator of a list entry depends
+// only on the box offset.  Group a level's boxes by parent: a target of child
+// class c under parent P receives, for each parent offset e in the 3x3
+// neighbourhood (e != 0: siblings are all adjacent) and each source child
+// class c', the translation T(delta) with delta = 2e + c' - c, or nothing when
+// delta is adjacent.  So for one parent P
+//
+//   out[c, n, re/im](P) = sum_{e, c'} W[(c,n,re/im)][(e,c'), (k,re/im)] in[c'](P + e)[k, re/im]
+//
+// -- a 3x3 convolution over the parent grid whose "channels" are the 4 child
+// classes x 2p real coefficients.  With D[rows][parents] in TMEM:
+//   M rows  = 4 classes x 2p       (128 at p = 16; 192 -> two M=128 tiles at p = 24)
+//   N       = the 8 x TPY parents of a tile
+//   K       = 32 blocks (e, c') x 2p, processed 16 at a time.
+// A (the operator blocks) streams from an L2-resident image through a ring
+// of shared-memory stages (cp.async.bulk, mbarrier transaction counts).  B
+// (the source MEs) is the tile's halo, staged once: for block (e, c') the B
+// operand is the class-c' plane seen through a descriptor whose start is
+// shifted by e -- the 8 parents of one tile row are 8 consecutive 16-byte
+// rows, and the stride to the next tile row is the halo row pitch (SBO).
+//
+// Precision.  BF16 keeps 8 significant bits.  With the hi/lo split
+// x = hi + lo (both BF16), the three products A_hi B_hi + A_hi B_lo +
+// A_lo B_hi recover ~16 bits per product, accumulated in FP32.
+//
+// Synchronisation.  One thread issues bulk copies (producer), one issues
+// MMAs; stages are handed over with mbarriers.  Every wait is bounded: on
+// timeout the CTA records FMM_ETIMEOUT in the device error word, waits
+// (bounded) for its own copies and MMAs, frees its TMEM and returns.
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+
+namespace fmmgb {
+
+constexpr int kTcThreads = 128;
+constexpr int kTcTileX = 8;               // parents per tile row (one core-matrix group)
+constexpr uint32_t kWaitCap = 1u << 22;   // bounded mbarrier waits
+
+template <int P>
+struct TcCfg {
+    static constexpr int K2 = 2 * P;                  // real K per block
+    static constexpr int KCH = K2 / 8;                // 16-byte BF16 chunks per block row
+    static constexpr int KSTEP = K2 / 16;             // MMAs of K = 16 per block
+    static constexpr int MT = (8 * P + 127) / 128;    // M tiles of 128 rows
+    static constexpr int TPY = P <= 16 ? 8 : 8;       // parent rows per tile
+    static constexpr int N = kTcTileX * TPY;          // parents per tile (MMA N)
+    static constexpr int HX = kTcTileX + 2, HY = TPY + 2;
+    static constexpr int NPOS = HX * HY;              // halo parent positions
+    static constexpr int PLANE = NPOS * 16;           // bytes of one (class, chunk) plane
+    static constexpr int BPART = 4 * KCH * PLANE;     // bytes of the hi (or lo) halo
+    static constexpr int APART = MT * 128 * K2 * 2;   // bytes of one block's hi (or lo) operator image
+    static constexpr int STAGES = P <= 16 ? 3 : 2;
+    static constexpr int TMEM_COLS = (MT * N) <= 32 ? 32 : ((MT * N) <= 64 ? 64 : ((MT * N) <= 128 ? 128 : 256));
+    // shared memory: B hi, B lo, A stages (hi+lo each), barriers
+    static constexpr size_t smem = 2 * (size_t)BPART + (size_t)STAGES * 2 * APART + 1024;
+};
+
+constexpr int kTcBlocks = 32;  // (e != 0) x 4 source classes
+
+// block index b = pe * 4 + c', pe = 0..7 enumerating the 8 non-central parent offsets
+__host__ __device__ inline void tc_block(int b, int& ex, int& ey, int& cs)
+{
+    cs = b & 3;
+    int pe = b >> 2;
+    if (pe >= 4) ++pe;  // skip the centre (ex, ey) = (0, 0)
+    ex = pe % 3 - 1;
+    ey = pe / 3 - 1;
+}
+
+// ---------------------------------------------------------------------------
+// operator image: W[(c, n, r_out)][(k, r_in)] per block, BF16 hi and lo, in
+// the canonical K-major no-swizzle layout (8-row x 16-byte core matrices):
+//   byte offset of (row R, real column q) = (R / 8) * (KCH * 128) + (q / 8) * 128 + (R % 8) * 16 + (q % 8) * 2
+// built in FP64 on the GPU from a(D) = (-1)^n C(n+k,k) D^-(n+k+1).
+// ---------------------------------------------------------------------------
+template <int P>
+__global__ void build_tc_image_kernel(double s, unsigned char* __restrict__ img)
+{
+    using C = TcCfg<P>;
+    const int rows = C::MT * 128;
+    const int64_t total = (int64_t)kTcBlocks * rows * C::K2;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    const int q = (int)(idx % C::K2);
+    const int R = (int)((idx / C::K2) % rows);
+    const int b = (int)(idx / ((int64_t)C::K2 * rows));
+    double w = 0.0;
+    if (R < 8 * P) {
+        const int c = R / (2 * P), n = (R % (2 * P)) / 2, ro = R & 1;
+        const int k = q / 2, ri = q & 1;
+        int ex, ey, cs;
+        tc_block(b, ex, ey, cs);
+        const int dx = 2 * ex + (cs & 1) - (c & 1), dy = 2 * ey + (cs >> 1) - (c >> 1);
+        const int adx = dx < 0 ? -dx : dx, ady = dy < 0 ? -dy : dy;
+        if ((adx > ady ? adx : ady) >= 2) {
+            // T[n][k] = a_n h_D[n+k] b_k with the balanced factors of the FP32 path, in FP64
+            const double Dr = -(double)dx, Di = -(double)dy, den = Dr * Dr + Di * Di;
+            const double ir = Dr / den, ii = -Di / den;
+            double hr = ir, hi = ii;
+            for (int i = 1; i <= n + k; ++i) {
+                const double f = (double)i * s;
+                const double nr = (hr * ir - hi * ii) * f;
+                const double ni = (hr * ii + hi * ir) * f;
+                hr = nr;
+                hi = ni;
+            }
+            double fa = 1.0, fb = 1.0;
+            for (int i = 1; i <= n; ++i) fa *= (double)i * s;
+            for (int i = 1; i <= k; ++i) fb *= (double)i * s;
+            const double scale = ((n & 1) ? -1.0 : 1.0) / (fa * fb);
+            const double tr = hr * scale, ti = hi * scale;
+            // out_re = Re T in_re - Im T in_im;  out_im = Im T in_re + Re T in_im
+            w = ro == 0 ? (ri == 0 ? tr : -ti) : (ri == 0 ? ti : tr);
+        }
+    }
+    const __nv_bfloat16 whi = __double2bfloat16(w);
+    const __nv_bfloat16 wlo = __double2bfloat16(w - (double)__bfloat162float(whi));
+    const size_t off = (size_t)(R / 8) * (C::KCH * 128) + (size_t)(q / 8) * 128 + (R % 8) * 16 + (q % 8) * 2;
+    unsigned char* blk = img + (size_t)b * 2 * C::APART;
+    *reinterpret_cast<__nv_bfloat16*>(blk + off) = whi;
+    *reinterpret_cast<__nv_bfloat16*>(blk + C::APART + off) = wlo;
+}
+
+// ---------------------------------------------------------------------------
+// PTX helpers (tcgen05, mbarrier, bulk copy)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity)
+{
+    for (uint32_t it = 0; it < kWaitCap; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(ok)
+            : "r"(su32(b)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     su32(dst)),
+                 "l"(src), "r"(bytes), "r"(su32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    // start >> 4 [0,14), LBO >> 4 [16,30), SBO >> 4 [32,46), version 1 [46,48), no swizzle
+    return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b)
+{
+    __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&v);
+}
+
+// ---------------------------------------------------------------------------
+// the kernel: one CTA = one tile of 8 x TPY parents of one level
+// ---------------------------------------------------------------------------
+template <int P>
+__global__ void __launch_bounds__(kTcThreads, 1) m2l_tc_kernel(M2LLaunch job, const unsigned char* __restrict__ img,
+                                                               int split, int* __restrict__ err)
+{
+    using C = TcCfg<P>;
+    extern __shared__ __align__(1024) unsigned char tsm[];
+    unsigned char* bhi = tsm;
+    unsigned char* blo = tsm + C::BPART;
+    unsigned char* astage = tsm + 2 * C::BPART;  // STAGES x (hi APART, lo APART)
+    uint64_t* full = reinterpret_cast<uint64_t*>(astage + (size_t)C::STAGES * 2 * C::APART);
+    uint64_t* empty = full + C::STAGES;
+    uint64_t* done = empty + C::STAGES;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    // tile geometry
+    int li = 0;
+    while (li + 1 < job.nlev && (int)blockIdx.x >= job.lv[li + 1].tile_begin) ++li;
+    const M2LLevel lv = job.lv[li];
+    const int t = (int)blockIdx.x - lv.tile_begin;
+    const int side = 1 << lv.level, np = side >> 1;
+    const int tpr = (np + kTcTileX - 1) / kTcTileX;
+    const int PX0 = (t % tpr) * kTcTileX, PY0 = (t / tpr) * C::TPY;
+
+    const uint32_t abytes = split ? 2u * C::APART : (uint32_t)C::APART;  // bytes per stage fill
+    if (tid == 0) {
+        for (int s = 0; s < C::STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                     "r"((uint32_t)C::TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    // producer: first STAGES operator blocks (overlaps the halo staging below)
+    if (tid == 0) {
+        for (int s = 0; s < C::STAGES && s < kTcBlocks; ++s) {
+            mbar_expect_tx(&full[s], abytes);
+            bulk_load(astage + (size_t)s * 2 * C::APART, img + (size_t)s * 2 * C::APART, abytes, &full[s]);
+        }
+    }
+
+    // halo -> BF16 hi/lo planes [c'][chunk][position] x 16 bytes
+    {
+        const float4* M4 = reinterpret_cast<const float4*>(lv.M);
+        const int items = 4 * C::NPOS * C::KCH;  // (box, chunk) pairs
+        for (int i = tid; i < items; i += kTcThreads) {
+            const int ch = i % C::KCH;
+            const int box = i / C::KCH;  // 2HX x 2HY boxes, row-major
+            const int hxb = box % (2 * C::HX), hyb = box / (2 * C::HX);
+            int ix = 2 * PX0 - 2 + hxb, iy = 2 * PY0 - 2 + hyb;
+            bool in = ix >= 0 && iy >= 0 && ix < side && iy < side;
+            if (job.periodic) {
+                ix = (ix + 2 * side) % side;
+                iy = (iy + 2 * side) % side;
+                in = true;
+            }
+            float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
+            if (in) {
+                const float4* src = M4 + ((size_t)iy * side + ix) * (P / 2) + 2 * ch;
+                v0 = __ldg(src);
+                v1 = __ldg(src + 1);
+            }
+            const float f[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+            uint32_t h[4], l[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                __nv_bfloat162 hv = __floats2bfloat162_rn(f[2 * j], f[2 * j + 1]);
+                const float2 hf = __bfloat1622float2(hv);
+                h[j] = *reinterpret_cast<uint32_t*>(&hv);
+                l[j] = pack_bf16(f[2 * j] - hf.x, f[2 * j + 1] - hf.y);
+            }
+            const int cls = (hxb & 1) + 2 * (hyb & 1);
+            const int pos = (hyb >> 1) * C::HX + (hxb >> 1);
+            const size_t off = ((size_t)(cls * C::KCH + ch) * C::NPOS + pos) * 16;
+            *reinterpret_cast<uint4*>(bhi + off) = make_uint4(h[0], h[1], h[2], h[3]);
+            if (split) *reinterpret_cast<uint4*>(blo + off) = make_uint4(l[0], l[1], l[2], l[3]);
+        }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic-proxy writes -> tensor core reads
+    __syncthreads();
+
+    bool ok = true;
+    // kind::f16, D = F32, A = B = BF16, K-major both, N, M = 128
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(C::N >> 3) << 17) | ((128u >> 4) << 24);
+    if (tid == 32) {
+        // MMA issuer
+        for (int b = 0; b < kTcBlocks && ok; ++b) {
+            const int s = b % C::STAGES;
+            if (!mbar_wait(&full[s], (uint32_t)((b / C::STAGES) & 1))) {
+                ok = false;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            int ex, ey, cs;
+            tc_block(b, ex, ey, cs);
+            const uint32_t a_hi = su32(astage + (size_t)s * 2 * C::APART), a_lo = a_hi + C::APART;
+            const uint32_t shift = (uint32_t)(((ey + 1) * C::HX + (ex + 1)) * 16);
+            const uint32_t b_hi = su32(bhi) + (uint32_t)(cs * C::KCH * C::PLANE) + shift;
+            const uint32_t b_lo = su32(blo) + (uint32_t)(cs * C::KCH * C::PLANE) + shift;
+            for (int kk = 0; kk < C::KSTEP; ++kk) {
+                const uint64_t db_hi = umma_desc(b_hi + (uint32_t)(2 * kk * C::PLANE), C::PLANE, C::HX * 16);
+                const uint64_t db_lo = umma_desc(b_lo + (uint32_t)(2 * kk * C::PLANE), C::PLANE, C::HX * 16);
+#pragma unroll
+                for (int mt = 0; mt < C::MT; ++mt) {
+                    const uint32_t moff = (uint32_t)(mt * 16 * C::KCH * 128 + 2 * kk * 128);
+                    const uint64_t da_hi = umma_desc(a_hi + moff, 128, C::KCH * 128);
+                    const uint64_t da_lo = umma_desc(a_lo + moff, 128, C::KCH * 128);
+                    const uint32_t d = tmem + (uint32_t)(mt * C::N);
+                    umma_bf16(d, da_hi, db_hi, idesc, (b | kk) ? 1u : 0u);
+                    if (split) {
+                        umma_bf16(d, da_hi, db_lo, idesc, 1u);
+                        umma_bf16(d, da_lo, db_hi, idesc, 1u);
+                    }
+                }
+            }
+            umma_commit(&empty[s]);  // stage s is free once these MMAs have read it
+        }
+        umma_commit(done);
+        if (!ok) atomicOr(err, DEV_ERR_TIMEOUT);
+    } else if (tid == 0) {
+        // producer: refill stage s with block b once the MMAs of block b - STAGES are done
+        for (int b = C::STAGES; b < kTcBlocks; ++b) {
+            const int s = b % C::STAGES;
+            if (!mbar_wait(&empty[s], (uint32_t)(((b / C::STAGES) - 1) & 1))) {
+                atomicOr(err, DEV_ERR_TIMEOUT);
+                break;
+            }
+            mbar_expect_tx(&full[s], abytes);
+            bulk_load(astage + (size_t)s * 2 * C::APART, img + (size_t)b * 2 * C::APART, abytes, &full[s]);
+        }
+    }
+
+    // epilogue: every warp reads its 32 TMEM lanes (rows) for all N columns (parents)
+    const bool fin = mbar_wait(done, 0);
+    if (!fin && lane == 0) atomicOr(err, DEV_ERR_TIMEOUT);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (fin) {
+#pragma unroll 1
+        for (int mt = 0; mt < C::MT; ++mt) {
+            const int R = mt * 128 + warp * 32 + lane;  // output row (c, n, re/im)
+            const bool valid_row = R < 8 * P;
+            const int c = R / (2 * P), q = R % (2 * P);
+            for (int j0 = 0; j0 < C::N; j0 += 16) {
+                uint32_t r[16];
+                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(mt * C::N + j0), r);
+                if (!valid_row) continue;
+#pragma unroll
+                for (int jj = 0; jj < 16; ++jj) {
+                    const int j = j0 + jj;
+                    const int px = PX0 + (j % kTcTileX), py = PY0 + (j / kTcTileX);
+                    if (px >= np || py >= np) continue;
+                    const int ix = 2 * px + (c & 1), iy = 2 * py + (c >> 1);
+                    float* dst = reinterpret_cast<float*>(lv.L + ((size_t)iy * side + ix) * P) + q;
+                    float v = __uint_as_float(r[jj]);
+                    if (job.accumulate) v += *dst;
+                    *dst = v;
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)C::TMEM_COLS)
+                     : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+bool m2l_tc_supported(int p) { return p == 16 || p == 24; }
+
+size_t m2l_tc_image_bytes(int p)
+{
+    switch (p) {
+        case 16: return (size_t)kTcBlocks * 2 * TcCfg<16>::APART;
+        case 24: return (size_t)kTcBlocks * 2 * TcCfg<24>::APART;
+        default: return 0;
+    }
+}
+
+template <int P>
+static int build_image_p(double s, unsigned char* img, cudaStream_t st)
+{
+    using C = TcCfg<P>;
+    const int64_t total = (int64_t)kTcBlocks * C::MT * 128 * C::K2;
+    build_tc_image_kernel<P><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(s, img);
+    FMM_CUDA_TRY(cudaGetLastError());
+    return FMM_OK;
+}
+
+int launch_build_tc_image(int p, double s, void* img, cudaStream_t st)
+{
+    switch (p) {
+        case 16: return build_image_p<16>(s, (unsigned char*)img, st);
+        case 24: return build_image_p<24>(s, (unsigned char*)img, st);
+        default: return fail(FMM_EINVAL, "M2L TC: unsupported p = %d", p);
+    }
+}
+
+template <int P>
+static int launch_tc_p(M2LLaunch& job, const void* img, bool split, int* err, cudaStream_t st)
+{
+    using C = TcCfg<P>;
+    int total = 0;
+    for (int i = 0; i < job.nlev; ++i) {
+        job.lv[i].tile_begin = total;
+        const int np = 1 << (job.lv[i].level - 1);
+        total += ((np + kTcTileX - 1) / kTcTileX) * ((np + C::TPY - 1) / C::TPY);
+    }
+    if (total == 0) return FMM_OK;
+    FMM_CUDA_TRY(cudaFuncSetAttribute(m2l_tc_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem));
+    m2l_tc_kernel<P><<<total, kTcThreads, C::smem, st>>>(job, (const unsigned char*)img, split ? 1 : 0, err);
+    FMM_CUDA_TRY(cudaGetLastError());
+    return FMM_OK;
+}
+
+int launch_m2l_tc(M2LLaunch& job, int p, const void* img, bool split, cudaStream_t st)
+{
+    int* err = nullptr;
+    int rc = device_error_word(&err);
+    if (rc) return rc;
+    switch (p) {
+        case 16: return launch_tc_p<16>(job, img, split, err, st);
+        case 24: return launch_tc_p<24>(job, img, split, err, st);
+        default: return fail(FMM_EINVAL, "M2L TC: unsupported p = %d", p);
+    }
+}
+
+}  // namespace fmmgb
