@@ -27,17 +27,20 @@
 // x = hi + lo (both BF16), the three products A_hi B_hi + A_hi B_lo +
 // A_lo B_hi recover ~16 bits per product, accumulated in FP32.
 //
-// Synchronisation.  One thread issues bulk copies (producer), one issues
-// MMAs; stages are handed over with mbarriers.  Every wait is bounded: on
-// timeout the CTA records FMM_ETIMEOUT in the device error word, waits
-// (bounded) for its own copies and MMAs, frees its TMEM and returns.
+// Schedule.  A persistent CTA per SM takes tiles round-robin and runs four
+// roles concurrently: a producer thread streams the 32 operator blocks of
+// every tile through a ring of shared-memory stages; an MMA thread issues the
+// tcgen05 products into one of two TMEM accumulators; two staging warps fill
+// the next tile's halo; four epilogue warps drain the other accumulator.
+// Hand-overs use mbarriers; every wait is bounded: on timeout the CTA records
+// FMM_ETIMEOUT in the device error word, waits (bounded) for its own copies,
+// frees its TMEM and returns.
 #include <cuda_bf16.h>
 
 #include "common.cuh"
 
 namespace fmmgb {
 
-constexpr int kTcThreads = 128;
 constexpr int kTcTileX = 8;               // parents per tile row (one core-matrix group)
 constexpr uint32_t kWaitCap = 1u << 22;   // bounded mbarrier waits
 
@@ -47,17 +50,18 @@ struct TcCfg {
     static constexpr int KCH = K2 / 8;                // 16-byte BF16 chunks per block row
     static constexpr int KSTEP = K2 / 16;             // MMAs of K = 16 per block
     static constexpr int MT = (8 * P + 127) / 128;    // M tiles of 128 rows
-    static constexpr int TPY = P <= 16 ? 8 : 8;       // parent rows per tile
+    static constexpr int TPY = 8;                     // parent rows per tile
     static constexpr int N = kTcTileX * TPY;          // parents per tile (MMA N)
     static constexpr int HX = kTcTileX + 2, HY = TPY + 2;
     static constexpr int NPOS = HX * HY;              // halo parent positions
     static constexpr int PLANE = NPOS * 16;           // bytes of one (class, chunk) plane
     static constexpr int BPART = 4 * KCH * PLANE;     // bytes of the hi (or lo) halo
     static constexpr int APART = MT * 128 * K2 * 2;   // bytes of one block's hi (or lo) operator image
-    static constexpr int STAGES = P <= 16 ? 3 : 2;
-    static constexpr int TMEM_COLS = (MT * N) <= 32 ? 32 : ((MT * N) <= 64 ? 64 : ((MT * N) <= 128 ? 128 : 256));
-    // shared memory: B hi, B lo, A stages (hi+lo each), barriers
-    static constexpr size_t smem = 2 * (size_t)BPART + (size_t)STAGES * 2 * APART + 1024;
+    static constexpr int NBUF = P <= 16 ? 2 : 1;      // halo buffers
+    static constexpr int STAGES = P <= 16 ? 7 : 3;    // operator ring depth
+    static constexpr int DCOLS = MT * N;              // TMEM columns of one accumulator
+    static constexpr int TMEM_COLS = 2 * DCOLS <= 128 ? 128 : 256;  // two accumulators
+    static constexpr size_t smem = (size_t)NBUF * 2 * BPART + (size_t)STAGES * 2 * APART + 1024;
 };
 
 constexpr int kTcBlocks = 32;  // (e != 0) x 4 source classes
@@ -202,43 +206,82 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b)
 }
 
 // ---------------------------------------------------------------------------
-// the kernel: one CTA = one tile of 8 x TPY parents of one level
+// the kernel: persistent, one CTA per SM, warp-specialised
+//   warp 0 lane 0   producer: streams the 32 operator blocks of every tile
+//                   through a ring of STAGES shared-memory stages (bulk copies)
+//   warp 1 lane 0   MMA issuer (warp 1 also owns the TMEM allocation)
+//   warps 2-3       halo staging (FP32 -> BF16 hi/lo planes), NBUF buffers
+//   warps 4-7       epilogue: TMEM -> registers -> coalesced LE stores; two
+//                   TMEM accumulators so tile i's epilogue overlaps tile i+1's MMAs
+// Tiles are handed out round-robin (tile = blockIdx.x + i * gridDim.x); all
+// tiles cost the same.
 // ---------------------------------------------------------------------------
+constexpr int kTcCtaThreads = 256;
+
+struct TcTile {
+    const float2* M;
+    float2* L;
+    int side, np, PX0, PY0;
+};
+
 template <int P>
-__global__ void __launch_bounds__(kTcThreads, 1) m2l_tc_kernel(M2LLaunch job, const unsigned char* __restrict__ img,
-                                                               int split, int* __restrict__ err)
+__device__ __forceinline__ TcTile tc_tile(const M2LLaunch& job, int tile)
+{
+    using C = TcCfg<P>;
+    int li = 0;
+    while (li + 1 < job.nlev && tile >= job.lv[li + 1].tile_begin) ++li;
+    const M2LLevel& lv = job.lv[li];
+    TcTile g;
+    g.M = lv.M;
+    g.L = lv.L;
+    g.side = 1 << lv.level;
+    g.np = g.side >> 1;
+    const int t = tile - lv.tile_begin;
+    const int tpr = (g.np + kTcTileX - 1) / kTcTileX;
+    g.PX0 = (t % tpr) * kTcTileX;
+    g.PY0 = (t / tpr) * C::TPY;
+    return g;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* b)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+
+template <int P>
+__global__ void __launch_bounds__(kTcCtaThreads, 1) m2l_tc_kernel(M2LLaunch job, const unsigned char* __restrict__ img,
+                                                                   int split, int total_tiles, int* __restrict__ err)
 {
     using C = TcCfg<P>;
     extern __shared__ __align__(1024) unsigned char tsm[];
-    unsigned char* bhi = tsm;
-    unsigned char* blo = tsm + C::BPART;
-    unsigned char* astage = tsm + 2 * C::BPART;  // STAGES x (hi APART, lo APART)
-    uint64_t* full = reinterpret_cast<uint64_t*>(astage + (size_t)C::STAGES * 2 * C::APART);
-    uint64_t* empty = full + C::STAGES;
-    uint64_t* done = empty + C::STAGES;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+    unsigned char* bbuf = tsm;                                   // NBUF x (hi BPART, lo BPART)
+    unsigned char* astage = tsm + (size_t)C::NBUF * 2 * C::BPART;  // STAGES x (hi APART, lo APART)
+    uint64_t* afull = reinterpret_cast<uint64_t*>(astage + (size_t)C::STAGES * 2 * C::APART);
+    uint64_t* aempty = afull + C::STAGES;
+    uint64_t* bfull = aempty + C::STAGES;
+    uint64_t* bfree = bfull + 2;
+    uint64_t* dfull = bfree + 2;
+    uint64_t* dfree = dfull + 2;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(dfree + 2);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int ntiles = blockIdx.x < (unsigned)total_tiles ? (total_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const uint32_t abytes = split ? 2u * C::APART : (uint32_t)C::APART;
 
-    // tile geometry
-    int li = 0;
-    while (li + 1 < job.nlev && (int)blockIdx.x >= job.lv[li + 1].tile_begin) ++li;
-    const M2LLevel lv = job.lv[li];
-    const int t = (int)blockIdx.x - lv.tile_begin;
-    const int side = 1 << lv.level, np = side >> 1;
-    const int tpr = (np + kTcTileX - 1) / kTcTileX;
-    const int PX0 = (t % tpr) * kTcTileX, PY0 = (t / tpr) * C::TPY;
-
-    const uint32_t abytes = split ? 2u * C::APART : (uint32_t)C::APART;  // bytes per stage fill
     if (tid == 0) {
         for (int s = 0; s < C::STAGES; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 1);
+            mbar_init(&afull[s], 1);
+            mbar_init(&aempty[s], 1);
         }
-        mbar_init(done, 1);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&bfull[i], 1);
+            mbar_init(&bfree[i], 1);
+            mbar_init(&dfull[i], 1);
+            mbar_init(&dfree[i], 4);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) {
+    if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
                      "r"((uint32_t)C::TMEM_COLS)
                      : "memory");
@@ -249,136 +292,164 @@ __global__ void __launch_bounds__(kTcThreads, 1) m2l_tc_kernel(M2LLaunch job, co
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
 
-    // producer: first STAGES operator blocks (overlaps the halo staging below)
     if (tid == 0) {
-        for (int s = 0; s < C::STAGES && s < kTcBlocks; ++s) {
-            mbar_expect_tx(&full[s], abytes);
-            bulk_load(astage + (size_t)s * 2 * C::APART, img + (size_t)s * 2 * C::APART, abytes, &full[s]);
+        // ---------------- producer ----------------
+        int g = 0;
+        bool ok = true;
+        for (int i = 0; i < ntiles && ok; ++i) {
+            for (int b = 0; b < kTcBlocks; ++b, ++g) {
+                const int s = g % C::STAGES;
+                if (g >= C::STAGES && !mbar_wait(&aempty[s], (uint32_t)(((g / C::STAGES) - 1) & 1))) {
+                    ok = false;
+                    break;
+                }
+                mbar_expect_tx(&afull[s], abytes);
+                bulk_load(astage + (size_t)s * 2 * C::APART, img + (size_t)b * 2 * C::APART, abytes, &afull[s]);
+            }
         }
-    }
-
-    // halo -> BF16 hi/lo planes [c'][chunk][position] x 16 bytes
-    {
-        const float4* M4 = reinterpret_cast<const float4*>(lv.M);
-        const int items = 4 * C::NPOS * C::KCH;  // (box, chunk) pairs
-        for (int i = tid; i < items; i += kTcThreads) {
-            const int ch = i % C::KCH;
-            const int box = i / C::KCH;  // 2HX x 2HY boxes, row-major
-            const int hxb = box % (2 * C::HX), hyb = box / (2 * C::HX);
-            int ix = 2 * PX0 - 2 + hxb, iy = 2 * PY0 - 2 + hyb;
-            bool in = ix >= 0 && iy >= 0 && ix < side && iy < side;
-            if (job.periodic) {
-                ix = (ix + 2 * side) % side;
-                iy = (iy + 2 * side) % side;
-                in = true;
-            }
-            float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
-            if (in) {
-                const float4* src = M4 + ((size_t)iy * side + ix) * (P / 2) + 2 * ch;
-                v0 = __ldg(src);
-                v1 = __ldg(src + 1);
-            }
-            const float f[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
-            uint32_t h[4], l[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                __nv_bfloat162 hv = __floats2bfloat162_rn(f[2 * j], f[2 * j + 1]);
-                const float2 hf = __bfloat1622float2(hv);
-                h[j] = *reinterpret_cast<uint32_t*>(&hv);
-                l[j] = pack_bf16(f[2 * j] - hf.x, f[2 * j + 1] - hf.y);
-            }
-            const int cls = (hxb & 1) + 2 * (hyb & 1);
-            const int pos = (hyb >> 1) * C::HX + (hxb >> 1);
-            const size_t off = ((size_t)(cls * C::KCH + ch) * C::NPOS + pos) * 16;
-            *reinterpret_cast<uint4*>(bhi + off) = make_uint4(h[0], h[1], h[2], h[3]);
-            if (split) *reinterpret_cast<uint4*>(blo + off) = make_uint4(l[0], l[1], l[2], l[3]);
-        }
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic-proxy writes -> tensor core reads
-    __syncthreads();
-
-    bool ok = true;
-    // kind::f16, D = F32, A = B = BF16, K-major both, N, M = 128
-    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(C::N >> 3) << 17) | ((128u >> 4) << 24);
-    if (tid == 32) {
-        // MMA issuer
-        for (int b = 0; b < kTcBlocks && ok; ++b) {
-            const int s = b % C::STAGES;
-            if (!mbar_wait(&full[s], (uint32_t)((b / C::STAGES) & 1))) {
-                ok = false;
-                break;
-            }
+        if (!ok) atomicOr(err, DEV_ERR_TIMEOUT);
+        // do not leave while copies are in flight: the last min(g, STAGES) fills must have landed
+        for (int q = (g > C::STAGES ? g - C::STAGES : 0); q < g; ++q)
+            if (!mbar_wait(&afull[q % C::STAGES], (uint32_t)((q / C::STAGES) & 1))) atomicOr(err, DEV_ERR_TIMEOUT);
+    } else if (tid == 32) {
+        // ---------------- MMA issuer ----------------
+        const uint32_t idesc =
+            (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(C::N >> 3) << 17) | ((128u >> 4) << 24);
+        int g = 0;
+        bool ok = true;
+        for (int i = 0; i < ntiles && ok; ++i) {
+            const int ts = i % C::NBUF, td = i & 1;
+            if (!mbar_wait(&bfull[ts], (uint32_t)((i / C::NBUF) & 1))) ok = false;
+            if (ok && i >= 2 && !mbar_wait(&dfree[td], (uint32_t)(((i >> 1) - 1) & 1))) ok = false;
+            if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            int ex, ey, cs;
-            tc_block(b, ex, ey, cs);
-            const uint32_t a_hi = su32(astage + (size_t)s * 2 * C::APART), a_lo = a_hi + C::APART;
-            const uint32_t shift = (uint32_t)(((ey + 1) * C::HX + (ex + 1)) * 16);
-            const uint32_t b_hi = su32(bhi) + (uint32_t)(cs * C::KCH * C::PLANE) + shift;
-            const uint32_t b_lo = su32(blo) + (uint32_t)(cs * C::KCH * C::PLANE) + shift;
-            for (int kk = 0; kk < C::KSTEP; ++kk) {
-                const uint64_t db_hi = umma_desc(b_hi + (uint32_t)(2 * kk * C::PLANE), C::PLANE, C::HX * 16);
-                const uint64_t db_lo = umma_desc(b_lo + (uint32_t)(2 * kk * C::PLANE), C::PLANE, C::HX * 16);
+            const uint32_t bh = su32(bbuf + (size_t)ts * 2 * C::BPART), bl = bh + C::BPART;
+            const uint32_t dbase = tmem + (uint32_t)(td * C::DCOLS);
+            for (int b = 0; b < kTcBlocks; ++b, ++g) {
+                const int s = g % C::STAGES;
+                if (!mbar_wait(&afull[s], (uint32_t)((g / C::STAGES) & 1))) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                int ex, ey, cs;
+                tc_block(b, ex, ey, cs);
+                const uint32_t a_hi = su32(astage + (size_t)s * 2 * C::APART), a_lo = a_hi + C::APART;
+                const uint32_t boff = (uint32_t)(cs * C::KCH * C::PLANE + ((ey + 1) * C::HX + (ex + 1)) * 16);
+                for (int kk = 0; kk < C::KSTEP; ++kk) {
+                    const uint64_t db_hi = umma_desc(bh + boff + (uint32_t)(2 * kk * C::PLANE), C::PLANE, C::HX * 16);
+                    const uint64_t db_lo = umma_desc(bl + boff + (uint32_t)(2 * kk * C::PLANE), C::PLANE, C::HX * 16);
 #pragma unroll
-                for (int mt = 0; mt < C::MT; ++mt) {
-                    const uint32_t moff = (uint32_t)(mt * 16 * C::KCH * 128 + 2 * kk * 128);
-                    const uint64_t da_hi = umma_desc(a_hi + moff, 128, C::KCH * 128);
-                    const uint64_t da_lo = umma_desc(a_lo + moff, 128, C::KCH * 128);
-                    const uint32_t d = tmem + (uint32_t)(mt * C::N);
-                    umma_bf16(d, da_hi, db_hi, idesc, (b | kk) ? 1u : 0u);
-                    if (split) {
-                        umma_bf16(d, da_hi, db_lo, idesc, 1u);
-                        umma_bf16(d, da_lo, db_hi, idesc, 1u);
+                    for (int mt = 0; mt < C::MT; ++mt) {
+                        const uint32_t moff = (uint32_t)(mt * 16 * C::KCH * 128 + 2 * kk * 128);
+                        const uint64_t da_hi = umma_desc(a_hi + moff, 128, C::KCH * 128);
+                        const uint64_t da_lo = umma_desc(a_lo + moff, 128, C::KCH * 128);
+                        const uint32_t d = dbase + (uint32_t)(mt * C::N);
+                        umma_bf16(d, da_hi, db_hi, idesc, (b | kk) ? 1u : 0u);
+                        if (split) {
+                            umma_bf16(d, da_hi, db_lo, idesc, 1u);
+                            umma_bf16(d, da_lo, db_hi, idesc, 1u);
+                        }
                     }
                 }
+                umma_commit(&aempty[s]);  // the stage is free once these MMAs have read it
             }
-            umma_commit(&empty[s]);  // stage s is free once these MMAs have read it
+            umma_commit(&dfull[td]);  // accumulator td holds tile i
+            umma_commit(&bfree[ts]);  // halo buffer ts may be restaged
         }
-        umma_commit(done);
         if (!ok) atomicOr(err, DEV_ERR_TIMEOUT);
-    } else if (tid == 0) {
-        // producer: refill stage s with block b once the MMAs of block b - STAGES are done
-        for (int b = C::STAGES; b < kTcBlocks; ++b) {
-            const int s = b % C::STAGES;
-            if (!mbar_wait(&empty[s], (uint32_t)(((b / C::STAGES) - 1) & 1))) {
+    } else if (warp == 2 || warp == 3) {
+        // ---------------- halo staging ----------------
+        const int st = tid - 64;  // 0..63
+        for (int i = 0; i < ntiles; ++i) {
+            const int ts = i % C::NBUF;
+            if (i >= C::NBUF && !mbar_wait(&bfree[ts], (uint32_t)(((i / C::NBUF) - 1) & 1))) {
                 atomicOr(err, DEV_ERR_TIMEOUT);
                 break;
             }
-            mbar_expect_tx(&full[s], abytes);
-            bulk_load(astage + (size_t)s * 2 * C::APART, img + (size_t)b * 2 * C::APART, abytes, &full[s]);
+            const TcTile g = tc_tile<P>(job, (int)blockIdx.x + i * (int)gridDim.x);
+            unsigned char* bh = bbuf + (size_t)ts * 2 * C::BPART;
+            unsigned char* bl = bh + C::BPART;
+            const float4* M4 = reinterpret_cast<const float4*>(g.M);
+            for (int it = st; it < 4 * C::NPOS * C::KCH; it += 64) {
+                const int ch = it % C::KCH;
+                const int box = it / C::KCH;  // 2HX x 2HY boxes, row-major
+                const int hxb = box % (2 * C::HX), hyb = box / (2 * C::HX);
+                int ix = 2 * g.PX0 - 2 + hxb, iy = 2 * g.PY0 - 2 + hyb;
+                bool in = ix >= 0 && iy >= 0 && ix < g.side && iy < g.side;
+                if (job.periodic) {
+                    ix = (ix + 2 * g.side) % g.side;
+                    iy = (iy + 2 * g.side) % g.side;
+                    in = true;
+                }
+                float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
+                if (in) {
+                    const float4* src = M4 + ((size_t)iy * g.side + ix) * (P / 2) + 2 * ch;
+                    v0 = __ldg(src);
+                    v1 = __ldg(src + 1);
+                }
+                const float f[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+                uint32_t h[4], l[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    __nv_bfloat162 hv = __floats2bfloat162_rn(f[2 * j], f[2 * j + 1]);
+                    const float2 hf = __bfloat1622float2(hv);
+                    h[j] = *reinterpret_cast<uint32_t*>(&hv);
+                    l[j] = pack_bf16(f[2 * j] - hf.x, f[2 * j + 1] - hf.y);
+                }
+                const int cls = (hxb & 1) + 2 * (hyb & 1);
+                const int pos = (hyb >> 1) * C::HX + (hxb >> 1);
+                const size_t off = ((size_t)(cls * C::KCH + ch) * C::NPOS + pos) * 16;
+                *reinterpret_cast<uint4*>(bh + off) = make_uint4(h[0], h[1], h[2], h[3]);
+                if (split) *reinterpret_cast<uint4*>(bl + off) = make_uint4(l[0], l[1], l[2], l[3]);
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("bar.sync 1, 64;" ::: "memory");
+            if (st == 0) mbar_arrive(&bfull[ts]);
+        }
+    } else if (warp >= 4) {
+        // ---------------- epilogue ----------------
+        const int q4 = warp - 4;  // TMEM lane quarter
+        for (int i = 0; i < ntiles; ++i) {
+            const int td = i & 1;
+            const bool fin = mbar_wait(&dfull[td], (uint32_t)((i >> 1) & 1));
+            if (!fin) {
+                if (lane == 0) atomicOr(err, DEV_ERR_TIMEOUT);
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const TcTile g = tc_tile<P>(job, (int)blockIdx.x + i * (int)gridDim.x);
+#pragma unroll 1
+            for (int mt = 0; mt < C::MT; ++mt) {
+                const int R = mt * 128 + q4 * 32 + lane;  // output row (c, n, re/im)
+                const bool valid_row = R < 8 * P;
+                const int c = R / (2 * P), q = R % (2 * P);
+                for (int j0 = 0; j0 < C::N; j0 += 16) {
+                    uint32_t r[16];
+                    tmem_ld16(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(td * C::DCOLS + mt * C::N + j0), r);
+                    if (!valid_row) continue;
+#pragma unroll
+                    for (int jj = 0; jj < 16; ++jj) {
+                        const int j = j0 + jj;
+                        const int px = g.PX0 + (j % kTcTileX), py = g.PY0 + (j / kTcTileX);
+                        if (px >= g.np || py >= g.np) continue;
+                        const int ix = 2 * px + (c & 1), iy = 2 * py + (c >> 1);
+                        float* dst = reinterpret_cast<float*>(g.L + ((size_t)iy * g.side + ix) * P) + q;
+                        float v = __uint_as_float(r[jj]);
+                        if (job.accumulate) v += *dst;
+                        *dst = v;
+                    }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&dfree[td]);
         }
     }
 
-    // epilogue: every warp reads its 32 TMEM lanes (rows) for all N columns (parents)
-    const bool fin = mbar_wait(done, 0);
-    if (!fin && lane == 0) atomicOr(err, DEV_ERR_TIMEOUT);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (fin) {
-#pragma unroll 1
-        for (int mt = 0; mt < C::MT; ++mt) {
-            const int R = mt * 128 + warp * 32 + lane;  // output row (c, n, re/im)
-            const bool valid_row = R < 8 * P;
-            const int c = R / (2 * P), q = R % (2 * P);
-            for (int j0 = 0; j0 < C::N; j0 += 16) {
-                uint32_t r[16];
-                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(mt * C::N + j0), r);
-                if (!valid_row) continue;
-#pragma unroll
-                for (int jj = 0; jj < 16; ++jj) {
-                    const int j = j0 + jj;
-                    const int px = PX0 + (j % kTcTileX), py = PY0 + (j / kTcTileX);
-                    if (px >= np || py >= np) continue;
-                    const int ix = 2 * px + (c & 1), iy = 2 * py + (c >> 1);
-                    float* dst = reinterpret_cast<float*>(lv.L + ((size_t)iy * side + ix) * P) + q;
-                    float v = __uint_as_float(r[jj]);
-                    if (job.accumulate) v += *dst;
-                    *dst = v;
-                }
-            }
-        }
-    }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0)
+    if (warp == 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)C::TMEM_COLS)
                      : "memory");
 }
@@ -427,8 +498,12 @@ static int launch_tc_p(M2LLaunch& job, const void* img, bool split, int* err, cu
         total += ((np + kTcTileX - 1) / kTcTileX) * ((np + C::TPY - 1) / C::TPY);
     }
     if (total == 0) return FMM_OK;
+    int sms = 0;
+    int rc = device_sm_count(&sms);
+    if (rc) return rc;
     FMM_CUDA_TRY(cudaFuncSetAttribute(m2l_tc_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem));
-    m2l_tc_kernel<P><<<total, kTcThreads, C::smem, st>>>(job, (const unsigned char*)img, split ? 1 : 0, err);
+    const int grid = total < sms ? total : sms;
+    m2l_tc_kernel<P><<<grid, kTcCtaThreads, C::smem, st>>>(job, (const unsigned char*)img, split ? 1 : 0, total, err);
     FMM_CUDA_TRY(cudaGetLastError());
     return FMM_OK;
 }
