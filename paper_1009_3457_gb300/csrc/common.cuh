@@ -79,10 +79,11 @@ double m2l_balance(int p);
 
 // One launch of the M2L stencil over several uniform levels (kernel parameter).
 struct M2LLevel {
-    const float2* M;   // [4^level][p] scaled MEs
-    float2* L;         // [4^level][p] scaled LEs
+    const float2* M;          // [4^level][p] scaled MEs
+    float2* L;                // [4^level][p] scaled LEs
     int level;
-    int tile_begin;    // first CTA of this level (filled by the launcher)
+    int tile_begin;           // first CTA of this level (filled by the launcher)
+    unsigned char* planes;    // tensor-core path: BF16 hi/lo planes of M (library scratch)
 };
 constexpr int kMaxLaunchLevels = FMM_MAX_LEVEL + 1;
 struct M2LLaunch {
@@ -103,6 +104,7 @@ size_t m2l_tc_image_bytes(int p);
 int launch_build_tc_image(int p, double s, void* img, cudaStream_t st);
 int launch_m2l_tc(M2LLaunch& job, int p, const void* img, bool split, cudaStream_t st);
 int get_tc_image(int p, const void** out);
+int tc_plane_workspace(size_t bytes, unsigned char** out);
 
 // launchers (fgt_h2t.cu)
 bool fgt_supported(int p);

@@ -206,11 +206,58 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b)
 }
 
 // ---------------------------------------------------------------------------
+// pre-pass: every level's MEs -> BF16 hi/lo planes, laid out as the kernel's
+// shared-memory halo wants them: [part][child class][16-byte chunk][py][px]
+// (part 0 = hi, 1 = lo; chunk = 8 consecutive real coefficients of a box)
+// ---------------------------------------------------------------------------
+template <int P>
+__global__ void me_planes_kernel(M2LLaunch job, int split)
+{
+    using C = TcCfg<P>;
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int li = 0;
+    for (; li < job.nlev; ++li) {
+        const int64_t n = ((int64_t)1 << (2 * job.lv[li].level)) * C::KCH;
+        if (idx < n) break;
+        idx -= n;
+    }
+    if (li >= job.nlev) return;
+    const M2LLevel& lv = job.lv[li];
+    const int side = 1 << lv.level, np = side >> 1;
+    const int ch = (int)(idx % C::KCH);
+    const int64_t box = idx / C::KCH;
+    const int ix = (int)(box % side), iy = (int)(box / side);
+    const float4* src = reinterpret_cast<const float4*>(lv.M) + box * (P / 2) + 2 * ch;
+    const float4 v0 = __ldg(src), v1 = __ldg(src + 1);
+    const float f[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        __nv_bfloat162 hv = __floats2bfloat162_rn(f[2 * j], f[2 * j + 1]);
+        const float2 hf = __bfloat1622float2(hv);
+        h[j] = *reinterpret_cast<uint32_t*>(&hv);
+        l[j] = pack_bf16(f[2 * j] - hf.x, f[2 * j + 1] - hf.y);
+    }
+    const int cls = (ix & 1) + 2 * (iy & 1);
+    const size_t plane = (size_t)np * np * 16;
+    const size_t off = (size_t)(cls * C::KCH + ch) * plane + ((size_t)(iy >> 1) * np + (ix >> 1)) * 16;
+    *reinterpret_cast<uint4*>(lv.planes + off) = make_uint4(h[0], h[1], h[2], h[3]);
+    if (split) *reinterpret_cast<uint4*>(lv.planes + 4 * C::KCH * plane + off) = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(su32(dst)), "l"(src), "r"(valid ? 16 : 0)
+                 : "memory");
+}
+
+// ---------------------------------------------------------------------------
 // the kernel: persistent, one CTA per SM, warp-specialised
 //   warp 0 lane 0   producer: streams the 32 operator blocks of every tile
 //                   through a ring of STAGES shared-memory stages (bulk copies)
 //   warp 1 lane 0   MMA issuer (warp 1 also owns the TMEM allocation)
-//   warps 2-3       halo staging (FP32 -> BF16 hi/lo planes), NBUF buffers
+//   warps 2-3       halo staging: cp.async of the tile's halo from the BF16
+//                   hi/lo planes written by me_planes_kernel, NBUF buffers
 //   warps 4-7       epilogue: TMEM -> registers -> coalesced LE stores; two
 //                   TMEM accumulators so tile i's epilogue overlaps tile i+1's MMAs
 // Tiles are handed out round-robin (tile = blockIdx.x + i * gridDim.x); all
@@ -219,7 +266,7 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b)
 constexpr int kTcCtaThreads = 256;
 
 struct TcTile {
-    const float2* M;
+    const unsigned char* planes;
     float2* L;
     int side, np, PX0, PY0;
 };
@@ -232,7 +279,7 @@ __device__ __forceinline__ TcTile tc_tile(const M2LLaunch& job, int tile)
     while (li + 1 < job.nlev && tile >= job.lv[li + 1].tile_begin) ++li;
     const M2LLevel& lv = job.lv[li];
     TcTile g;
-    g.M = lv.M;
+    g.planes = lv.planes;
     g.L = lv.L;
     g.side = 1 << lv.level;
     g.np = g.side >> 1;
@@ -369,40 +416,24 @@ __global__ void __launch_bounds__(kTcCtaThreads, 1) m2l_tc_kernel(M2LLaunch job,
             }
             const TcTile g = tc_tile<P>(job, (int)blockIdx.x + i * (int)gridDim.x);
             unsigned char* bh = bbuf + (size_t)ts * 2 * C::BPART;
-            unsigned char* bl = bh + C::BPART;
-            const float4* M4 = reinterpret_cast<const float4*>(g.M);
-            for (int it = st; it < 4 * C::NPOS * C::KCH; it += 64) {
-                const int ch = it % C::KCH;
-                const int box = it / C::KCH;  // 2HX x 2HY boxes, row-major
-                const int hxb = box % (2 * C::HX), hyb = box / (2 * C::HX);
-                int ix = 2 * g.PX0 - 2 + hxb, iy = 2 * g.PY0 - 2 + hyb;
-                bool in = ix >= 0 && iy >= 0 && ix < g.side && iy < g.side;
+            const size_t plane = (size_t)g.np * g.np * 16;
+            const int units = (split ? 2 : 1) * 4 * C::KCH * C::NPOS;  // 16-byte halo units
+            for (int it = st; it < units; it += 64) {
+                const int pos = it % C::NPOS;
+                const int pc = it / C::NPOS;  // (part, class, chunk)
+                const int hx = pos % C::HX, hy = pos / C::HX;
+                int qx = g.PX0 - 1 + hx, qy = g.PY0 - 1 + hy;  // source parent
+                bool in = qx >= 0 && qy >= 0 && qx < g.np && qy < g.np;
                 if (job.periodic) {
-                    ix = (ix + 2 * g.side) % g.side;
-                    iy = (iy + 2 * g.side) % g.side;
+                    qx = (qx + g.np) % g.np;
+                    qy = (qy + g.np) % g.np;
                     in = true;
                 }
-                float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
-                if (in) {
-                    const float4* src = M4 + ((size_t)iy * g.side + ix) * (P / 2) + 2 * ch;
-                    v0 = __ldg(src);
-                    v1 = __ldg(src + 1);
-                }
-                const float f[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
-                uint32_t h[4], l[4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    __nv_bfloat162 hv = __floats2bfloat162_rn(f[2 * j], f[2 * j + 1]);
-                    const float2 hf = __bfloat1622float2(hv);
-                    h[j] = *reinterpret_cast<uint32_t*>(&hv);
-                    l[j] = pack_bf16(f[2 * j] - hf.x, f[2 * j + 1] - hf.y);
-                }
-                const int cls = (hxb & 1) + 2 * (hyb & 1);
-                const int pos = (hyb >> 1) * C::HX + (hxb >> 1);
-                const size_t off = ((size_t)(cls * C::KCH + ch) * C::NPOS + pos) * 16;
-                *reinterpret_cast<uint4*>(bh + off) = make_uint4(h[0], h[1], h[2], h[3]);
-                if (split) *reinterpret_cast<uint4*>(bl + off) = make_uint4(l[0], l[1], l[2], l[3]);
+                const unsigned char* src = in ? g.planes + (size_t)pc * plane + ((size_t)qy * g.np + qx) * 16 : g.planes;
+                cp_async16(bh + (size_t)pc * C::PLANE + (size_t)pos * 16, src, in);
             }
+            asm volatile("cp.async.commit_group;\n" ::: "memory");
+            asm volatile("cp.async.wait_all;\n" ::: "memory");
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             asm volatile("bar.sync 1, 64;" ::: "memory");
             if (st == 0) mbar_arrive(&bfull[ts]);
@@ -501,6 +532,21 @@ static int launch_tc_p(M2LLaunch& job, const void* img, bool split, int* err, cu
     int sms = 0;
     int rc = device_sm_count(&sms);
     if (rc) return rc;
+    // BF16 hi/lo planes of every level's MEs (library scratch), then the main kernel
+    size_t bytes = 0;
+    int64_t items = 0;
+    for (int i = 0; i < job.nlev; ++i) {
+        bytes += ((size_t)1 << (2 * job.lv[i].level)) * (size_t)P * 8;
+        items += ((int64_t)1 << (2 * job.lv[i].level)) * C::KCH;
+    }
+    unsigned char* ws = nullptr;
+    if ((rc = tc_plane_workspace(bytes, &ws))) return rc;
+    for (int i = 0; i < job.nlev; ++i) {
+        job.lv[i].planes = ws;
+        ws += ((size_t)1 << (2 * job.lv[i].level)) * (size_t)P * 8;
+    }
+    me_planes_kernel<P><<<(unsigned)((items + 255) / 256), 256, 0, st>>>(job, split ? 1 : 0);
+    FMM_CUDA_TRY(cudaGetLastError());
     FMM_CUDA_TRY(cudaFuncSetAttribute(m2l_tc_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem));
     const int grid = total < sms ? total : sms;
     m2l_tc_kernel<P><<<grid, kTcCtaThreads, C::smem, st>>>(job, (const unsigned char*)img, split ? 1 : 0, total, err);
