@@ -234,8 +234,9 @@ def run_ours(args):
     fmmgb.fmm_sync_status()
     if args.mode == "kernels":
         # profiling case: the step's launch only (no e2e copies, no CPU baseline, no other rows)
+        prec = {"fp32": fmmgb.FMM_FP32, "tc3": fmmgb.FMM_TC_BF16X3, "tc1": fmmgb.FMM_TC_BF16}[args.prec]
         for _ in range(args.steps):
-            step()
+            fmmgb.fmm_m2l_levels(tree, LEVELS[0], P, Ms, Ls, prec=prec, stream=stream)
         torch.cuda.synchronize()
         fmmgb.fmm_sync_status()
         if rank == 0:
@@ -411,6 +412,8 @@ def main():
     ap.add_argument("--no-rows", action="store_true", help="skip the adjoint / per-level / FGT rows")
     ap.add_argument("--mode", default="full", choices=["full", "kernels"],
                     help="kernels: only the timed step's launches (for ncu captures)")
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "tc3", "tc1"],
+                    help="precision of the launches in --mode kernels")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

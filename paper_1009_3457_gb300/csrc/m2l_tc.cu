@@ -64,7 +64,8 @@ struct TcCfg {
     static constexpr size_t smem = (size_t)NBUF * 2 * BPART + (size_t)STAGES * 2 * APART + 1024;
 };
 
-constexpr int kTcBlocks = 32;  // (e != 0) x 4 source classes
+constexpr int kTcBlocks = 32;   // (e != 0) x 4 source classes
+constexpr int kTcReplicas = 4;  // copies of the operator image in global memory
 
 // block index b = pe * 4 + c', pe = 0..7 enumerating the 8 non-central parent offsets
 __host__ __device__ inline void tc_block(int b, int& ex, int& ey, int& cs)
@@ -314,6 +315,11 @@ __global__ void __launch_bounds__(kTcCtaThreads, 1) m2l_tc_kernel(M2LLaunch job,
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ntiles = blockIdx.x < (unsigned)total_tiles ? (total_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     const uint32_t abytes = split ? 2u * C::APART : (uint32_t)C::APART;
+    // Every CTA walks the same operator blocks; starting at a CTA-dependent
+    // block and reading one of kTcReplicas copies of the image spreads the
+    // simultaneous reads of all SMs over many L2 lines.
+    const int rot = (int)(blockIdx.x % kTcBlocks);
+    const unsigned char* rimg = img + (size_t)(blockIdx.x % kTcReplicas) * kTcBlocks * 2 * C::APART;
 
     if (tid == 0) {
         for (int s = 0; s < C::STAGES; ++s) {
@@ -344,14 +350,15 @@ __global__ void __launch_bounds__(kTcCtaThreads, 1) m2l_tc_kernel(M2LLaunch job,
         int g = 0;
         bool ok = true;
         for (int i = 0; i < ntiles && ok; ++i) {
-            for (int b = 0; b < kTcBlocks; ++b, ++g) {
+            for (int bi = 0; bi < kTcBlocks; ++bi, ++g) {
+                const int b = (bi + rot) % kTcBlocks;
                 const int s = g % C::STAGES;
                 if (g >= C::STAGES && !mbar_wait(&aempty[s], (uint32_t)(((g / C::STAGES) - 1) & 1))) {
                     ok = false;
                     break;
                 }
                 mbar_expect_tx(&afull[s], abytes);
-                bulk_load(astage + (size_t)s * 2 * C::APART, img + (size_t)b * 2 * C::APART, abytes, &afull[s]);
+                bulk_load(astage + (size_t)s * 2 * C::APART, rimg + (size_t)b * 2 * C::APART, abytes, &afull[s]);
             }
         }
         if (!ok) atomicOr(err, DEV_ERR_TIMEOUT);
@@ -372,7 +379,8 @@ __global__ void __launch_bounds__(kTcCtaThreads, 1) m2l_tc_kernel(M2LLaunch job,
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t bh = su32(bbuf + (size_t)ts * 2 * C::BPART), bl = bh + C::BPART;
             const uint32_t dbase = tmem + (uint32_t)(td * C::DCOLS);
-            for (int b = 0; b < kTcBlocks; ++b, ++g) {
+            for (int bi = 0; bi < kTcBlocks; ++bi, ++g) {
+                const int b = (bi + rot) % kTcBlocks;
                 const int s = g % C::STAGES;
                 if (!mbar_wait(&afull[s], (uint32_t)((g / C::STAGES) & 1))) {
                     ok = false;
@@ -392,7 +400,7 @@ __global__ void __launch_bounds__(kTcCtaThreads, 1) m2l_tc_kernel(M2LLaunch job,
                         const uint64_t da_hi = umma_desc(a_hi + moff, 128, C::KCH * 128);
                         const uint64_t da_lo = umma_desc(a_lo + moff, 128, C::KCH * 128);
                         const uint32_t d = dbase + (uint32_t)(mt * C::N);
-                        umma_bf16(d, da_hi, db_hi, idesc, (b | kk) ? 1u : 0u);
+                        umma_bf16(d, da_hi, db_hi, idesc, (bi | kk) ? 1u : 0u);
                         if (split) {
                             umma_bf16(d, da_hi, db_lo, idesc, 1u);
                             umma_bf16(d, da_lo, db_hi, idesc, 1u);
@@ -493,8 +501,8 @@ bool m2l_tc_supported(int p) { return p == 16 || p == 24; }
 size_t m2l_tc_image_bytes(int p)
 {
     switch (p) {
-        case 16: return (size_t)kTcBlocks * 2 * TcCfg<16>::APART;
-        case 24: return (size_t)kTcBlocks * 2 * TcCfg<24>::APART;
+        case 16: return (size_t)kTcReplicas * kTcBlocks * 2 * TcCfg<16>::APART;
+        case 24: return (size_t)kTcReplicas * kTcBlocks * 2 * TcCfg<24>::APART;
         default: return 0;
     }
 }
@@ -506,6 +514,8 @@ static int build_image_p(double s, unsigned char* img, cudaStream_t st)
     const int64_t total = (int64_t)kTcBlocks * C::MT * 128 * C::K2;
     build_tc_image_kernel<P><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(s, img);
     FMM_CUDA_TRY(cudaGetLastError());
+    const size_t one = (size_t)kTcBlocks * 2 * C::APART;
+    for (int r = 1; r < kTcReplicas; ++r) FMM_CUDA_TRY(cudaMemcpyAsync(img + r * one, img, one, cudaMemcpyDeviceToDevice, st));
     return FMM_OK;
 }
 
