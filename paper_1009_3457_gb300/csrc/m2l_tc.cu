@@ -58,7 +58,9 @@ struct TcCfg {
     static constexpr int BPART = 4 * KCH * PLANE;     // bytes of the hi (or lo) halo
     static constexpr int APART = MT * 128 * K2 * 2;   // bytes of one block's hi (or lo) operator image
     static constexpr int NBUF = P <= 16 ? 2 : 1;      // halo buffers
-    static constexpr int STAGES = P <= 16 ? 7 : 3;    // operator ring depth
+    static constexpr int NPROD = 3;                   // producer warps (one bulk copy in flight each)
+    static constexpr int SP = P <= 16 ? 2 : 1;        // ring stages per producer
+    static constexpr int STAGES = NPROD * SP;         // operator ring depth
     static constexpr int DCOLS = MT * N;              // TMEM columns of one accumulator
     static constexpr int TMEM_COLS = 2 * DCOLS <= 128 ? 128 : 256;  // two accumulators
     static constexpr size_t smem = (size_t)NBUF * 2 * BPART + (size_t)STAGES * 2 * APART + 1024;
@@ -254,17 +256,20 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src, bool vali
 
 // ---------------------------------------------------------------------------
 // the kernel: persistent, one CTA per SM, warp-specialised
-//   warp 0 lane 0   producer: streams the 32 operator blocks of every tile
-//                   through a ring of STAGES shared-memory stages (bulk copies)
-//   warp 1 lane 0   MMA issuer (warp 1 also owns the TMEM allocation)
-//   warps 2-3       halo staging: cp.async of the tile's halo from the BF16
+//   warps 0-2, lane 0  producers: operator block g of the continuous stream
+//                   (32 per tile) comes from producer g % 3 into that
+//                   producer's share of the ring; each issuing thread keeps
+//                   one bulk copy in flight, so three producers triple the rate
+//   warp 4, lane 0  MMA issuer (warp 4 also owns the TMEM allocation)
+//   warps 5-7       halo staging: cp.async of the tile's halo from the BF16
 //                   hi/lo planes written by me_planes_kernel, NBUF buffers
-//   warps 4-7       epilogue: TMEM -> registers -> coalesced LE stores; two
+//   warps 8-11      epilogue: TMEM -> registers -> coalesced LE stores; two
 //                   TMEM accumulators so tile i's epilogue overlaps tile i+1's MMAs
 // Tiles are handed out round-robin (tile = blockIdx.x + i * gridDim.x); all
 // tiles cost the same.
 // ---------------------------------------------------------------------------
-constexpr int kTcCtaThreads = 256;
+constexpr int kTcCtaThreads = 384;
+constexpr int kMmaWarp = 4, kStageWarp0 = 5, kStageWarps = 3, kEpiWarp0 = 8;
 
 struct TcTile {
     const unsigned char* planes;
@@ -334,7 +339,7 @@ __global__ void __launch_bounds__(kTcCtaThreads, 1) m2l_tc_kernel(M2LLaunch job,
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 1) {
+    if (warp == kMmaWarp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
                      "r"((uint32_t)C::TMEM_COLS)
                      : "memory");
@@ -345,27 +350,29 @@ __global__ void __launch_bounds__(kTcCtaThreads, 1) m2l_tc_kernel(M2LLaunch job,
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
 
-    if (tid == 0) {
-        // ---------------- producer ----------------
-        int g = 0;
-        bool ok = true;
-        for (int i = 0; i < ntiles && ok; ++i) {
-            for (int bi = 0; bi < kTcBlocks; ++bi, ++g) {
-                const int b = (bi + rot) % kTcBlocks;
-                const int s = g % C::STAGES;
-                if (g >= C::STAGES && !mbar_wait(&aempty[s], (uint32_t)(((g / C::STAGES) - 1) & 1))) {
+    if (warp < C::NPROD) {
+        // ---------------- producer `warp` ----------------
+        if (lane == 0) {
+            const int pr = warp;
+            const int total_blocks = ntiles * kTcBlocks;
+            int k = 0;  // local fill index of this producer
+            bool ok = true;
+            for (int g = pr; g < total_blocks; g += C::NPROD, ++k) {
+                const int s = pr * C::SP + k % C::SP;
+                if (k >= C::SP && !mbar_wait(&aempty[s], (uint32_t)(((k / C::SP) - 1) & 1))) {
                     ok = false;
                     break;
                 }
+                const int b = (g % kTcBlocks + rot) % kTcBlocks;
                 mbar_expect_tx(&afull[s], abytes);
                 bulk_load(astage + (size_t)s * 2 * C::APART, rimg + (size_t)b * 2 * C::APART, abytes, &afull[s]);
             }
+            if (!ok) atomicOr(err, DEV_ERR_TIMEOUT);
+            // do not leave while copies are in flight: this producer's last min(k, SP) fills must have landed
+            for (int q = (k > C::SP ? k - C::SP : 0); q < k; ++q)
+                if (!mbar_wait(&afull[pr * C::SP + q % C::SP], (uint32_t)((q / C::SP) & 1))) atomicOr(err, DEV_ERR_TIMEOUT);
         }
-        if (!ok) atomicOr(err, DEV_ERR_TIMEOUT);
-        // do not leave while copies are in flight: the last min(g, STAGES) fills must have landed
-        for (int q = (g > C::STAGES ? g - C::STAGES : 0); q < g; ++q)
-            if (!mbar_wait(&afull[q % C::STAGES], (uint32_t)((q / C::STAGES) & 1))) atomicOr(err, DEV_ERR_TIMEOUT);
-    } else if (tid == 32) {
+    } else if (warp == kMmaWarp && lane == 0) {
         // ---------------- MMA issuer ----------------
         const uint32_t idesc =
             (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(C::N >> 3) << 17) | ((128u >> 4) << 24);
@@ -381,8 +388,9 @@ __global__ void __launch_bounds__(kTcCtaThreads, 1) m2l_tc_kernel(M2LLaunch job,
             const uint32_t dbase = tmem + (uint32_t)(td * C::DCOLS);
             for (int bi = 0; bi < kTcBlocks; ++bi, ++g) {
                 const int b = (bi + rot) % kTcBlocks;
-                const int s = g % C::STAGES;
-                if (!mbar_wait(&afull[s], (uint32_t)((g / C::STAGES) & 1))) {
+                const int pk = g / C::NPROD;  // fill index within producer g % NPROD
+                const int s = (g % C::NPROD) * C::SP + pk % C::SP;
+                if (!mbar_wait(&afull[s], (uint32_t)((pk / C::SP) & 1))) {
                     ok = false;
                     break;
                 }
@@ -413,9 +421,10 @@ __global__ void __launch_bounds__(kTcCtaThreads, 1) m2l_tc_kernel(M2LLaunch job,
             umma_commit(&bfree[ts]);  // halo buffer ts may be restaged
         }
         if (!ok) atomicOr(err, DEV_ERR_TIMEOUT);
-    } else if (warp == 2 || warp == 3) {
+    } else if (warp >= kStageWarp0 && warp < kStageWarp0 + kStageWarps) {
         // ---------------- halo staging ----------------
-        const int st = tid - 64;  // 0..63
+        constexpr int NST = 32 * kStageWarps;
+        const int st = tid - 32 * kStageWarp0;
         for (int i = 0; i < ntiles; ++i) {
             const int ts = i % C::NBUF;
             if (i >= C::NBUF && !mbar_wait(&bfree[ts], (uint32_t)(((i / C::NBUF) - 1) & 1))) {
@@ -426,7 +435,7 @@ __global__ void __launch_bounds__(kTcCtaThreads, 1) m2l_tc_kernel(M2LLaunch job,
             unsigned char* bh = bbuf + (size_t)ts * 2 * C::BPART;
             const size_t plane = (size_t)g.np * g.np * 16;
             const int units = (split ? 2 : 1) * 4 * C::KCH * C::NPOS;  // 16-byte halo units
-            for (int it = st; it < units; it += 64) {
+            for (int it = st; it < units; it += NST) {
                 const int pos = it % C::NPOS;
                 const int pc = it / C::NPOS;  // (part, class, chunk)
                 const int hx = pos % C::HX, hy = pos / C::HX;
@@ -443,12 +452,12 @@ __global__ void __launch_bounds__(kTcCtaThreads, 1) m2l_tc_kernel(M2LLaunch job,
             asm volatile("cp.async.commit_group;\n" ::: "memory");
             asm volatile("cp.async.wait_all;\n" ::: "memory");
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            asm volatile("bar.sync 1, 64;" ::: "memory");
+            asm volatile("bar.sync 1, %0;" ::"n"(NST) : "memory");
             if (st == 0) mbar_arrive(&bfull[ts]);
         }
-    } else if (warp >= 4) {
+    } else if (warp >= kEpiWarp0) {
         // ---------------- epilogue ----------------
-        const int q4 = warp - 4;  // TMEM lane quarter
+        const int q4 = warp - kEpiWarp0;  // TMEM lane quarter (= warp % 4)
         for (int i = 0; i < ntiles; ++i) {
             const int td = i & 1;
             const bool fin = mbar_wait(&dfull[td], (uint32_t)((i >> 1) & 1));
@@ -488,7 +497,7 @@ __global__ void __launch_bounds__(kTcCtaThreads, 1) m2l_tc_kernel(M2LLaunch job,
 
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 1)
+    if (warp == kMmaWarp)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)C::TMEM_COLS)
                      : "memory");
 }
