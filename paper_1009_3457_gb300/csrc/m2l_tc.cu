@@ -48,22 +48,26 @@ template <int P>
 struct TcCfg {
     static constexpr int K2 = 2 * P;                  // real K per block
     static constexpr int KCH = K2 / 8;                // 16-byte BF16 chunks per block row
-    static constexpr int KSTEP = K2 / 16;             // MMAs of K = 16 per block
+    static constexpr int KSTEP = K2 / 16;             // MMA K steps of 16 per block
     static constexpr int MT = (8 * P + 127) / 128;    // M tiles of 128 rows
     static constexpr int TPY = 8;                     // parent rows per tile
-    static constexpr int N = kTcTileX * TPY;          // parents per tile (MMA N)
+    static constexpr int N = kTcTileX * TPY;          // parents per tile
     static constexpr int HX = kTcTileX + 2, HY = TPY + 2;
     static constexpr int NPOS = HX * HY;              // halo parent positions
-    static constexpr int PLANE = NPOS * 16;           // bytes of one (class, chunk) plane
-    static constexpr int BPART = 4 * KCH * PLANE;     // bytes of the hi (or lo) halo
+    // one (class, chunk) plane of a halo buffer: 2 HY rows (halo row, hi/lo interleaved) x HX x 16 B
+    static constexpr int ROWB = HX * 16;
+    static constexpr int IPLANE = 2 * HY * ROWB;
+    static constexpr int BBUF = 4 * KCH * IPLANE;     // bytes of one halo buffer (hi and lo)
     static constexpr int APART = MT * 128 * K2 * 2;   // bytes of one block's hi (or lo) operator image
     static constexpr int NBUF = P <= 16 ? 2 : 1;      // halo buffers
     static constexpr int NPROD = 3;                   // producer warps (one bulk copy in flight each)
     static constexpr int SP = P <= 16 ? 2 : 1;        // ring stages per producer
     static constexpr int STAGES = NPROD * SP;         // operator ring depth
-    static constexpr int DCOLS = MT * N;              // TMEM columns of one accumulator
-    static constexpr int TMEM_COLS = 2 * DCOLS <= 128 ? 128 : 256;  // two accumulators
-    static constexpr size_t smem = (size_t)NBUF * 2 * BPART + (size_t)STAGES * 2 * APART + 1024;
+    // TMEM: per M tile a 2N-column accumulator (A_hi x [B_hi|B_lo] interleaved) + an N-column one (A_lo x B_hi)
+    static constexpr int SETCOLS = MT * 3 * N;
+    static constexpr int NACC = 2 * SETCOLS <= 512 ? 2 : 1;
+    static constexpr int TMEM_COLS = 512;
+    static constexpr size_t smem = (size_t)NBUF * BBUF + (size_t)STAGES * 2 * APART + 1024;
 };
 
 constexpr int kTcBlocks = 32;   // (e != 0) x 4 source classes
@@ -307,8 +311,8 @@ __global__ void __launch_bounds__(kTcCtaThreads, 1) m2l_tc_kernel(M2LLaunch job,
 {
     using C = TcCfg<P>;
     extern __shared__ __align__(1024) unsigned char tsm[];
-    unsigned char* bbuf = tsm;                                   // NBUF x (hi BPART, lo BPART)
-    unsigned char* astage = tsm + (size_t)C::NBUF * 2 * C::BPART;  // STAGES x (hi APART, lo APART)
+    unsigned char* bbuf = tsm;                                 // NBUF halo buffers
+    unsigned char* astage = tsm + (size_t)C::NBUF * C::BBUF;   // STAGES x (hi APART, lo APART)
     uint64_t* afull = reinterpret_cast<uint64_t*>(astage + (size_t)C::STAGES * 2 * C::APART);
     uint64_t* aempty = afull + C::STAGES;
     uint64_t* bfull = aempty + C::STAGES;
@@ -316,6 +320,7 @@ __global__ void __launch_bounds__(kTcCtaThreads, 1) m2l_tc_kernel(M2LLaunch job,
     uint64_t* dfull = bfree + 2;
     uint64_t* dfree = dfull + 2;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(dfree + 2);
+    uint32_t* boff16 = tmem_slot + 4;  // [32] B-operand offset of each (e, c') block, in 16-byte units
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ntiles = blockIdx.x < (unsigned)total_tiles ? (total_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
@@ -338,6 +343,11 @@ __global__ void __launch_bounds__(kTcCtaThreads, 1) m2l_tc_kernel(M2LLaunch job,
             mbar_init(&dfree[i], 4);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (tid < kTcBlocks) {
+        int ex, ey, cs;
+        tc_block(tid, ex, ey, cs);
+        boff16[tid] = (uint32_t)((cs * C::KCH * C::IPLANE + 2 * (ey + 1) * C::ROWB + (ex + 1) * 16) >> 4);
     }
     if (warp == kMmaWarp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
@@ -374,18 +384,25 @@ __global__ void __launch_bounds__(kTcCtaThreads, 1) m2l_tc_kernel(M2LLaunch job,
         }
     } else if (warp == kMmaWarp && lane == 0) {
         // ---------------- MMA issuer ----------------
-        const uint32_t idesc =
-            (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(C::N >> 3) << 17) | ((128u >> 4) << 24);
+        // per K step of 16: D1 (2N cols) += A_hi x [B_hi | B_lo] (rows interleaved, N = 2 x 64),
+        //                   D2 (N cols)  += A_lo x B_hi; result = D1 hi cols + D1 lo cols + D2.
+        // Without the split: D2 += A_hi x B_hi only.
+        const uint32_t id2n = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)((2 * C::N) >> 3) << 17) | ((128u >> 4) << 24);
+        const uint32_t idn = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(C::N >> 3) << 17) | ((128u >> 4) << 24);
+        const uint64_t a0 = umma_desc(su32(astage), 128, C::KCH * 128);  // stage 0, hi part
+        constexpr uint64_t alo_off = (uint64_t)(C::APART >> 4);
         int g = 0;
         bool ok = true;
         for (int i = 0; i < ntiles && ok; ++i) {
-            const int ts = i % C::NBUF, td = i & 1;
+            const int ts = i % C::NBUF, td = i % C::NACC;
             if (!mbar_wait(&bfull[ts], (uint32_t)((i / C::NBUF) & 1))) ok = false;
-            if (ok && i >= 2 && !mbar_wait(&dfree[td], (uint32_t)(((i >> 1) - 1) & 1))) ok = false;
+            if (ok && i >= C::NACC && !mbar_wait(&dfree[td], (uint32_t)(((i / C::NACC) - 1) & 1))) ok = false;
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t bh = su32(bbuf + (size_t)ts * 2 * C::BPART), bl = bh + C::BPART;
-            const uint32_t dbase = tmem + (uint32_t)(td * C::DCOLS);
+            const uint32_t bb = su32(bbuf + (size_t)ts * C::BBUF);
+            const uint64_t bint0 = umma_desc(bb, C::IPLANE, C::ROWB);     // hi/lo rows interleaved
+            const uint64_t bhi0 = umma_desc(bb, C::IPLANE, 2 * C::ROWB);  // hi rows only
+            const uint32_t dset = tmem + (uint32_t)(td * C::SETCOLS);
             for (int bi = 0; bi < kTcBlocks; ++bi, ++g) {
                 const int b = (bi + rot) % kTcBlocks;
                 const int pk = g / C::NPROD;  // fill index within producer g % NPROD
@@ -394,30 +411,27 @@ __global__ void __launch_bounds__(kTcCtaThreads, 1) m2l_tc_kernel(M2LLaunch job,
                     ok = false;
                     break;
                 }
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                int ex, ey, cs;
-                tc_block(b, ex, ey, cs);
-                const uint32_t a_hi = su32(astage + (size_t)s * 2 * C::APART), a_lo = a_hi + C::APART;
-                const uint32_t boff = (uint32_t)(cs * C::KCH * C::PLANE + ((ey + 1) * C::HX + (ex + 1)) * 16);
+                const uint64_t boff = (uint64_t)boff16[b];
+#pragma unroll
                 for (int kk = 0; kk < C::KSTEP; ++kk) {
-                    const uint64_t db_hi = umma_desc(bh + boff + (uint32_t)(2 * kk * C::PLANE), C::PLANE, C::HX * 16);
-                    const uint64_t db_lo = umma_desc(bl + boff + (uint32_t)(2 * kk * C::PLANE), C::PLANE, C::HX * 16);
+                    const uint64_t kb = (uint64_t)((2 * kk * C::IPLANE) >> 4);
+                    const uint64_t dbi = bint0 + boff + kb, dbh = bhi0 + boff + kb;
 #pragma unroll
                     for (int mt = 0; mt < C::MT; ++mt) {
-                        const uint32_t moff = (uint32_t)(mt * 16 * C::KCH * 128 + 2 * kk * 128);
-                        const uint64_t da_hi = umma_desc(a_hi + moff, 128, C::KCH * 128);
-                        const uint64_t da_lo = umma_desc(a_lo + moff, 128, C::KCH * 128);
-                        const uint32_t d = dbase + (uint32_t)(mt * C::N);
-                        umma_bf16(d, da_hi, db_hi, idesc, (bi | kk) ? 1u : 0u);
+                        const uint64_t da = a0 + (uint64_t)(((size_t)s * 2 * C::APART + mt * 16 * C::KCH * 128 + 2 * kk * 128) >> 4);
+                        const uint32_t d1 = dset + (uint32_t)(mt * 3 * C::N), d2 = d1 + (uint32_t)(2 * C::N);
+                        const uint32_t acc = (bi | kk) ? 1u : 0u;
                         if (split) {
-                            umma_bf16(d, da_hi, db_lo, idesc, 1u);
-                            umma_bf16(d, da_lo, db_hi, idesc, 1u);
+                            umma_bf16(d1, da, dbi, id2n, acc);
+                            umma_bf16(d2, da + alo_off, dbh, idn, acc);
+                        } else {
+                            umma_bf16(d2, da, dbh, idn, acc);
                         }
                     }
                 }
                 umma_commit(&aempty[s]);  // the stage is free once these MMAs have read it
             }
-            umma_commit(&dfull[td]);  // accumulator td holds tile i
+            umma_commit(&dfull[td]);  // accumulator set td holds tile i
             umma_commit(&bfree[ts]);  // halo buffer ts may be restaged
         }
         if (!ok) atomicOr(err, DEV_ERR_TIMEOUT);
@@ -432,12 +446,13 @@ __global__ void __launch_bounds__(kTcCtaThreads, 1) m2l_tc_kernel(M2LLaunch job,
                 break;
             }
             const TcTile g = tc_tile<P>(job, (int)blockIdx.x + i * (int)gridDim.x);
-            unsigned char* bh = bbuf + (size_t)ts * 2 * C::BPART;
+            unsigned char* bb = bbuf + (size_t)ts * C::BBUF;
             const size_t plane = (size_t)g.np * g.np * 16;
             const int units = (split ? 2 : 1) * 4 * C::KCH * C::NPOS;  // 16-byte halo units
             for (int it = st; it < units; it += NST) {
                 const int pos = it % C::NPOS;
                 const int pc = it / C::NPOS;  // (part, class, chunk)
+                const int part = pc / (4 * C::KCH), cc = pc % (4 * C::KCH);
                 const int hx = pos % C::HX, hy = pos / C::HX;
                 int qx = g.PX0 - 1 + hx, qy = g.PY0 - 1 + hy;  // source parent
                 bool in = qx >= 0 && qy >= 0 && qx < g.np && qy < g.np;
@@ -447,7 +462,7 @@ __global__ void __launch_bounds__(kTcCtaThreads, 1) m2l_tc_kernel(M2LLaunch job,
                     in = true;
                 }
                 const unsigned char* src = in ? g.planes + (size_t)pc * plane + ((size_t)qy * g.np + qx) * 16 : g.planes;
-                cp_async16(bh + (size_t)pc * C::PLANE + (size_t)pos * 16, src, in);
+                cp_async16(bb + (size_t)cc * C::IPLANE + (size_t)(2 * hy + part) * C::ROWB + (size_t)hx * 16, src, in);
             }
             asm volatile("cp.async.commit_group;\n" ::: "memory");
             asm volatile("cp.async.wait_all;\n" ::: "memory");
@@ -459,31 +474,43 @@ __global__ void __launch_bounds__(kTcCtaThreads, 1) m2l_tc_kernel(M2LLaunch job,
         // ---------------- epilogue ----------------
         const int q4 = warp - kEpiWarp0;  // TMEM lane quarter (= warp % 4)
         for (int i = 0; i < ntiles; ++i) {
-            const int td = i & 1;
-            const bool fin = mbar_wait(&dfull[td], (uint32_t)((i >> 1) & 1));
+            const int td = i % C::NACC;
+            const bool fin = mbar_wait(&dfull[td], (uint32_t)((i / C::NACC) & 1));
             if (!fin) {
                 if (lane == 0) atomicOr(err, DEV_ERR_TIMEOUT);
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const TcTile g = tc_tile<P>(job, (int)blockIdx.x + i * (int)gridDim.x);
+            const uint32_t lanes = (uint32_t)(q4 * 32) << 16;
 #pragma unroll 1
             for (int mt = 0; mt < C::MT; ++mt) {
                 const int R = mt * 128 + q4 * 32 + lane;  // output row (c, n, re/im)
                 const bool valid_row = R < 8 * P;
                 const int c = R / (2 * P), q = R % (2 * P);
-                for (int j0 = 0; j0 < C::N; j0 += 16) {
-                    uint32_t r[16];
-                    tmem_ld16(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(td * C::DCOLS + mt * C::N + j0), r);
+                const uint32_t d1 = tmem + lanes + (uint32_t)(td * C::SETCOLS + mt * 3 * C::N);
+                const uint32_t d2 = d1 + (uint32_t)(2 * C::N);
+#pragma unroll 1
+                for (int y2 = 0; y2 < C::TPY / 2; ++y2) {  // two tile rows = 16 parents per round
+                    uint32_t a0[16], a1[16], b[16];
+                    tmem_ld16(d2 + (uint32_t)(16 * y2), b);  // D2 columns of tile rows 2y2, 2y2+1
+                    if (split) {
+                        tmem_ld16(d1 + (uint32_t)(32 * y2), a0);       // row 2y2: hi cols 0-7, lo cols 8-15
+                        tmem_ld16(d1 + (uint32_t)(32 * y2 + 16), a1);  // row 2y2+1
+                    }
                     if (!valid_row) continue;
 #pragma unroll
                     for (int jj = 0; jj < 16; ++jj) {
-                        const int j = j0 + jj;
-                        const int px = g.PX0 + (j % kTcTileX), py = g.PY0 + (j / kTcTileX);
+                        const int yy = 2 * y2 + (jj >> 3), xx = jj & 7;
+                        float v = __uint_as_float(b[jj]);
+                        if (split) {
+                            const uint32_t* a = (jj >> 3) ? a1 : a0;
+                            v += __uint_as_float(a[xx]) + __uint_as_float(a[8 + xx]);
+                        }
+                        const int px = g.PX0 + xx, py = g.PY0 + yy;
                         if (px >= g.np || py >= g.np) continue;
                         const int ix = 2 * px + (c & 1), iy = 2 * py + (c >> 1);
                         float* dst = reinterpret_cast<float*>(g.L + ((size_t)iy * g.side + ix) * P) + q;
-                        float v = __uint_as_float(r[jj]);
                         if (job.accumulate) v += *dst;
                         *dst = v;
                     }
