@@ -50,8 +50,8 @@ struct TcCfg {
     static constexpr int KCH = K2 / 8;                // 16-byte BF16 chunks per block row
     static constexpr int KSTEP = K2 / 16;             // MMA K steps of 16 per block
     static constexpr int MT = (8 * P + 127) / 128;    // M tiles of 128 rows
-    static constexpr int TPY = 8;                     // parent rows per tile
-    static constexpr int N = kTcTileX * TPY;          // parents per tile
+    static constexpr int TPY = P <= 16 ? 16 : 8;      // parent rows per tile
+    static constexpr int N = kTcTileX * TPY;          // parents per tile (the split MMA has N = 2 x this)
     static constexpr int HX = kTcTileX + 2, HY = TPY + 2;
     static constexpr int NPOS = HX * HY;              // halo parent positions
     // one (class, chunk) plane of a halo buffer: 2 HY rows (halo row, hi/lo interleaved) x HX x 16 B
@@ -59,7 +59,7 @@ struct TcCfg {
     static constexpr int IPLANE = 2 * HY * ROWB;
     static constexpr int BBUF = 4 * KCH * IPLANE;     // bytes of one halo buffer (hi and lo)
     static constexpr int APART = MT * 128 * K2 * 2;   // bytes of one block's hi (or lo) operator image
-    static constexpr int NBUF = P <= 16 ? 2 : 1;      // halo buffers
+    static constexpr int NBUF = 1;                    // halo buffers
     static constexpr int NPROD = 3;                   // producer warps (one bulk copy in flight each)
     static constexpr int SP = P <= 16 ? 2 : 1;        // ring stages per producer
     static constexpr int STAGES = NPROD * SP;         // operator ring depth
@@ -158,6 +158,22 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity)
         uint32_t ok;
         asm volatile(
             "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(ok)
+            : "r"(su32(b)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+// Spin on a non-blocking test (a single issuing thread; a blocking try_wait
+// that finds the phase complete still costs ~150 cycles).
+__device__ __forceinline__ bool mbar_spin(uint64_t* b, uint32_t parity)
+{
+    for (uint32_t it = 0; it < (kWaitCap << 6); ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
             : "=r"(ok)
             : "r"(su32(b)), "r"(parity)
             : "memory");
@@ -395,8 +411,8 @@ __global__ void __launch_bounds__(kTcCtaThreads, 1) m2l_tc_kernel(M2LLaunch job,
         bool ok = true;
         for (int i = 0; i < ntiles && ok; ++i) {
             const int ts = i % C::NBUF, td = i % C::NACC;
-            if (!mbar_wait(&bfull[ts], (uint32_t)((i / C::NBUF) & 1))) ok = false;
-            if (ok && i >= C::NACC && !mbar_wait(&dfree[td], (uint32_t)(((i / C::NACC) - 1) & 1))) ok = false;
+            if (!mbar_spin(&bfull[ts], (uint32_t)((i / C::NBUF) & 1))) ok = false;
+            if (ok && i >= C::NACC && !mbar_spin(&dfree[td], (uint32_t)(((i / C::NACC) - 1) & 1))) ok = false;
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t bb = su32(bbuf + (size_t)ts * C::BBUF);
@@ -407,7 +423,7 @@ __global__ void __launch_bounds__(kTcCtaThreads, 1) m2l_tc_kernel(M2LLaunch job,
                 const int b = (bi + rot) % kTcBlocks;
                 const int pk = g / C::NPROD;  // fill index within producer g % NPROD
                 const int s = (g % C::NPROD) * C::SP + pk % C::SP;
-                if (!mbar_wait(&afull[s], (uint32_t)((pk / C::SP) & 1))) {
+                if (!mbar_spin(&afull[s], (uint32_t)((pk / C::SP) & 1))) {
                     ok = false;
                     break;
                 }
