@@ -35,7 +35,11 @@
 // Hand-overs use mbarriers; every wait is bounded: on timeout the CTA records
 // FMM_ETIMEOUT in the device error word, waits (bounded) for its own copies,
 // frees its TMEM and returns.
+#include <cuda.h>
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
 
 #include "common.cuh"
 
@@ -190,6 +194,16 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
                  : "memory");
 }
 
+__device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3, int c4,
+                                            uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(
+            su32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(su32(bar))
+        : "memory");
+}
+
 __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
 {
     // start >> 4 [0,14), LBO >> 4 [16,30), SBO >> 4 [32,46), version 1 [46,48), no swizzle
@@ -229,9 +243,10 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b)
 }
 
 // ---------------------------------------------------------------------------
-// pre-pass: every level's MEs -> BF16 hi/lo planes, laid out as the kernel's
-// shared-memory halo wants them: [part][child class][16-byte chunk][py][px]
-// (part 0 = hi, 1 = lo; chunk = 8 consecutive real coefficients of a box)
+// pre-pass: every level's MEs -> BF16 hi/lo planes laid out so that a tile's
+// halo is one TMA box that lands in exactly the shared-memory layout the MMAs
+// read: [cc = class * KCH + chunk][parent row qy][part: hi, lo][parent column qx]
+// x 16 bytes (a chunk = 8 consecutive real coefficients of a box)
 // ---------------------------------------------------------------------------
 template <int P>
 __global__ void me_planes_kernel(M2LLaunch job, int split)
@@ -261,11 +276,12 @@ __global__ void me_planes_kernel(M2LLaunch job, int split)
         h[j] = *reinterpret_cast<uint32_t*>(&hv);
         l[j] = pack_bf16(f[2 * j] - hf.x, f[2 * j + 1] - hf.y);
     }
-    const int cls = (ix & 1) + 2 * (iy & 1);
-    const size_t plane = (size_t)np * np * 16;
-    const size_t off = (size_t)(cls * C::KCH + ch) * plane + ((size_t)(iy >> 1) * np + (ix >> 1)) * 16;
+    const int cc = ((ix & 1) + 2 * (iy & 1)) * C::KCH + ch;
+    const size_t row = (size_t)np * 16;  // one (cc, qy, part) row of np positions
+    const size_t off = ((size_t)cc * np + (iy >> 1)) * 2 * row + (size_t)(ix >> 1) * 16;
     *reinterpret_cast<uint4*>(lv.planes + off) = make_uint4(h[0], h[1], h[2], h[3]);
-    if (split) *reinterpret_cast<uint4*>(lv.planes + 4 * C::KCH * plane + off) = make_uint4(l[0], l[1], l[2], l[3]);
+    *reinterpret_cast<uint4*>(lv.planes + off + row) = make_uint4(l[0], l[1], l[2], l[3]);
+    (void)split;
 }
 
 __device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid)
@@ -281,8 +297,9 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src, bool vali
 //                   producer's share of the ring; each issuing thread keeps
 //                   one bulk copy in flight, so three producers triple the rate
 //   warp 4, lane 0  MMA issuer (warp 4 also owns the TMEM allocation)
-//   warps 5-7       halo staging: cp.async of the tile's halo from the BF16
-//                   hi/lo planes written by me_planes_kernel, NBUF buffers
+//   warps 5-7       halo staging: one TMA tensor load of the tile's halo from
+//                   the BF16 hi/lo planes written by me_planes_kernel (cp.async
+//                   when the halo is larger than the level or lists are periodic)
 //   warps 8-11      epilogue: TMEM -> registers -> coalesced LE stores; two
 //                   TMEM accumulators so tile i's epilogue overlaps tile i+1's MMAs
 // Tiles are handed out round-robin (tile = blockIdx.x + i * gridDim.x); all
@@ -294,7 +311,7 @@ constexpr int kMmaWarp = 4, kStageWarp0 = 5, kStageWarps = 3, kEpiWarp0 = 8;
 struct TcTile {
     const unsigned char* planes;
     float2* L;
-    int side, np, PX0, PY0;
+    int side, np, PX0, PY0, li;
 };
 
 template <int P>
@@ -313,6 +330,7 @@ __device__ __forceinline__ TcTile tc_tile(const M2LLaunch& job, int tile)
     const int tpr = (g.np + kTcTileX - 1) / kTcTileX;
     g.PX0 = (t % tpr) * kTcTileX;
     g.PY0 = (t / tpr) * C::TPY;
+    g.li = li;
     return g;
 }
 
@@ -321,9 +339,15 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* b)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
 }
 
+struct TcMaps {
+    CUtensorMap map[kMaxLaunchLevels];  // per launch level: 5-D map over its planes (when use_tma)
+    int use_tma[kMaxLaunchLevels];
+};
+
 template <int P>
-__global__ void __launch_bounds__(kTcCtaThreads, 1) m2l_tc_kernel(M2LLaunch job, const unsigned char* __restrict__ img,
-                                                                   int split, int total_tiles, int* __restrict__ err)
+__global__ void __launch_bounds__(kTcCtaThreads, 1) m2l_tc_kernel(M2LLaunch job, const __grid_constant__ TcMaps maps,
+                                                                   const unsigned char* __restrict__ img, int split,
+                                                                   int total_tiles, int* __restrict__ err)
 {
     using C = TcCfg<P>;
     extern __shared__ __align__(1024) unsigned char tsm[];
@@ -463,11 +487,19 @@ __global__ void __launch_bounds__(kTcCtaThreads, 1) m2l_tc_kernel(M2LLaunch job,
             }
             const TcTile g = tc_tile<P>(job, (int)blockIdx.x + i * (int)gridDim.x);
             unsigned char* bb = bbuf + (size_t)ts * C::BBUF;
-            const size_t plane = (size_t)g.np * g.np * 16;
-            const int units = (split ? 2 : 1) * 4 * C::KCH * C::NPOS;  // 16-byte halo units
+            if (maps.use_tma[g.li]) {
+                // one TMA box: {8 bf16, HX columns, 2 parts, HY rows, 4 KCH planes}, zero-filled outside the level
+                if (st == 0) {
+                    mbar_expect_tx(&bfull[ts], (uint32_t)C::BBUF);
+                    tma_load_5d(bb, &maps.map[g.li], 0, g.PX0 - 1, 0, g.PY0 - 1, 0, &bfull[ts]);
+                }
+                continue;
+            }
+            const size_t row = (size_t)g.np * 16;
+            const int units = 2 * 4 * C::KCH * C::NPOS;  // 16-byte halo units
             for (int it = st; it < units; it += NST) {
                 const int pos = it % C::NPOS;
-                const int pc = it / C::NPOS;  // (part, class, chunk)
+                const int pc = it / C::NPOS;  // (part, cc)
                 const int part = pc / (4 * C::KCH), cc = pc % (4 * C::KCH);
                 const int hx = pos % C::HX, hy = pos / C::HX;
                 int qx = g.PX0 - 1 + hx, qy = g.PY0 - 1 + hy;  // source parent
@@ -477,7 +509,8 @@ __global__ void __launch_bounds__(kTcCtaThreads, 1) m2l_tc_kernel(M2LLaunch job,
                     qy = (qy + g.np) % g.np;
                     in = true;
                 }
-                const unsigned char* src = in ? g.planes + (size_t)pc * plane + ((size_t)qy * g.np + qx) * 16 : g.planes;
+                const unsigned char* src =
+                    in ? g.planes + (((size_t)cc * g.np + qy) * 2 + part) * row + (size_t)qx * 16 : g.planes;
                 cp_async16(bb + (size_t)cc * C::IPLANE + (size_t)(2 * hy + part) * C::ROWB + (size_t)hx * 16, src, in);
             }
             asm volatile("cp.async.commit_group;\n" ::: "memory");
@@ -580,6 +613,23 @@ int launch_build_tc_image(int p, double s, void* img, cudaStream_t st)
     }
 }
 
+// cuTensorMapEncodeTiled from the driver, looked up once (no link against libcuda)
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            (void)cudaGetLastError();
+    });
+    return fn;
+}
+
 template <int P>
 static int launch_tc_p(M2LLaunch& job, const void* img, bool split, int* err, cudaStream_t st)
 {
@@ -609,9 +659,26 @@ static int launch_tc_p(M2LLaunch& job, const void* img, bool split, int* err, cu
     }
     me_planes_kernel<P><<<(unsigned)((items + 255) / 256), 256, 0, st>>>(job, split ? 1 : 0);
     FMM_CUDA_TRY(cudaGetLastError());
+    TcMaps maps;
+    memset(&maps, 0, sizeof(maps));
+    PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+    for (int i = 0; i < job.nlev; ++i) {
+        const int np = 1 << (job.lv[i].level - 1);
+        if (!encode || job.periodic || np < C::HX || np < C::HY) continue;  // halo larger than the level: cp.async path
+        const cuuint64_t dims[5] = {8, (cuuint64_t)np, 2, (cuuint64_t)np, (cuuint64_t)(4 * C::KCH)};
+        const cuuint64_t strides[4] = {16, (cuuint64_t)np * 16, (cuuint64_t)np * 32, (cuuint64_t)np * np * 32};
+        const cuuint32_t box[5] = {8, (cuuint32_t)C::HX, 2, (cuuint32_t)C::HY, (cuuint32_t)(4 * C::KCH)};
+        const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+        const CUresult r = encode(&maps.map[i], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, (void*)job.lv[i].planes, dims,
+                                  strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(FMM_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+        maps.use_tma[i] = 1;
+    }
     FMM_CUDA_TRY(cudaFuncSetAttribute(m2l_tc_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem));
     const int grid = total < sms ? total : sms;
-    m2l_tc_kernel<P><<<grid, kTcCtaThreads, C::smem, st>>>(job, (const unsigned char*)img, split ? 1 : 0, total, err);
+    m2l_tc_kernel<P><<<grid, kTcCtaThreads, C::smem, st>>>(job, maps, (const unsigned char*)img, split ? 1 : 0, total,
+                                                            err);
     FMM_CUDA_TRY(cudaGetLastError());
     return FMM_OK;
 }
