@@ -236,6 +236,18 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// asynchronous 32-lane x 16-column TMEM load; complete with tmem_wait_ld()
+__device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t (&r)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b)
 {
     __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
@@ -542,11 +554,12 @@ __global__ void __launch_bounds__(kTcCtaThreads, 1) m2l_tc_kernel(M2LLaunch job,
 #pragma unroll 1
                 for (int y2 = 0; y2 < C::TPY / 2; ++y2) {  // two tile rows = 16 parents per round
                     uint32_t a0[16], a1[16], b[16];
-                    tmem_ld16(d2 + (uint32_t)(16 * y2), b);  // D2 columns of tile rows 2y2, 2y2+1
+                    tmem_ld16_async(d2 + (uint32_t)(16 * y2), b);  // D2 columns of tile rows 2y2, 2y2+1
                     if (split) {
-                        tmem_ld16(d1 + (uint32_t)(32 * y2), a0);       // row 2y2: hi cols 0-7, lo cols 8-15
-                        tmem_ld16(d1 + (uint32_t)(32 * y2 + 16), a1);  // row 2y2+1
+                        tmem_ld16_async(d1 + (uint32_t)(32 * y2), a0);       // row 2y2: hi cols 0-7, lo cols 8-15
+                        tmem_ld16_async(d1 + (uint32_t)(32 * y2 + 16), a1);  // row 2y2+1
                     }
+                    tmem_wait_ld();
                     if (!valid_row) continue;
 #pragma unroll
                     for (int jj = 0; jj < 16; ++jj) {
