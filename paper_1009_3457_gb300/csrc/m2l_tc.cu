@@ -156,9 +156,12 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes)
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
 }
 
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity)
+// Bounded wait that yields the issue slot between polls (for warps that are
+// not on the critical path: they share an SM sub-partition with the MMA warp).
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, uint32_t sleep_ns = 64)
 {
     for (uint32_t it = 0; it < kWaitCap; ++it) {
+        if (it) __nanosleep(sleep_ns);
         uint32_t ok;
         asm volatile(
             "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
@@ -493,7 +496,7 @@ __global__ void __launch_bounds__(kTcCtaThreads, 1) m2l_tc_kernel(M2LLaunch job,
         const int st = tid - 32 * kStageWarp0;
         for (int i = 0; i < ntiles; ++i) {
             const int ts = i % C::NBUF;
-            if (i >= C::NBUF && !mbar_wait(&bfree[ts], (uint32_t)(((i / C::NBUF) - 1) & 1))) {
+            if (i >= C::NBUF && !mbar_wait(&bfree[ts], (uint32_t)(((i / C::NBUF) - 1) & 1), 256)) {
                 atomicOr(err, DEV_ERR_TIMEOUT);
                 break;
             }
@@ -536,7 +539,7 @@ __global__ void __launch_bounds__(kTcCtaThreads, 1) m2l_tc_kernel(M2LLaunch job,
         const int q4 = warp - kEpiWarp0;  // TMEM lane quarter (= warp % 4)
         for (int i = 0; i < ntiles; ++i) {
             const int td = i % C::NACC;
-            const bool fin = mbar_wait(&dfull[td], (uint32_t)((i / C::NACC) & 1));
+            const bool fin = mbar_wait(&dfull[td], (uint32_t)((i / C::NACC) & 1), 256);
             if (!fin) {
                 if (lane == 0) atomicOr(err, DEV_ERR_TIMEOUT);
                 break;
