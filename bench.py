@@ -190,6 +190,35 @@ def _timed(torch, fn, steps, stream, flush):
     return [a.elapsed_time(b) for a, b in evs]
 
 
+def _batched_setup(torch, fmmgb, dev, autotune=True):
+    """The 256-problem batch: particles -> device P2M/M2M per problem (untimed),
+    one plan over every problem's levels 2..depth."""
+    cfg = workloads.CONFIGS["m2l_batched"]
+    rng = workloads.rng_for("m2l_batched")
+    shapes = workloads.batched_problems(cfg["nprob"], rng, depths=cfg["depths"], orders=cfg["orders"],
+                                        n_range=cfg["n_range"])
+    trees, ps, Ms, Ls = [], [], [], []
+    flops = 0
+    for sh in shapes:
+        L, p = sh["max_level"], sh["p"]
+        xy, c = workloads.uniform_particles(sh["n"], rng)
+        xyd = torch.from_numpy(xy).to(dev)
+        cd = torch.from_numpy(c).to(dev)
+        M = {l: torch.empty((4 ** l, p), dtype=torch.complex64, device=dev) for l in range(2, L + 1)}
+        fmmgb.fmm_p2m(L, p, xyd, cd, M[L])
+        for l in range(L, 2, -1):
+            fmmgb.fmm_m2m(l, p, M[l], M[l - 1])
+        tree = fmmgb.fmm_build_lists(None, L)
+        trees.append(tree)
+        ps.append(p)
+        Ms.append([M[l] for l in range(2, L + 1)])
+        Ls.append([torch.empty_like(M[l]) for l in range(2, L + 1)])
+        flops += sum(tree.translations(l) for l in range(2, L + 1)) * metrics.m2l_flops_per_translation(p)
+    torch.cuda.synchronize()
+    plan = fmmgb.fmm_batch_create(trees, ps, Ms, Ls, autotune=autotune)
+    return dict(plan=plan, trees=trees, ps=ps, Ms=Ms, Ls=Ls, flops=flops, info=plan.info())
+
+
 def run_ours(args):
     import torch
 
@@ -232,6 +261,16 @@ def run_ours(args):
         flush.zero_()
     torch.cuda.synchronize()
     fmmgb.fmm_sync_status()
+    if args.mode == "kernels" and args.prec == "batched":
+        # profiling case: the 256-problem batched launch only
+        bt = _batched_setup(torch, fmmgb, dev)
+        for _ in range(args.steps):
+            bt["plan"].run(stream)
+        torch.cuda.synchronize()
+        fmmgb.fmm_sync_status()
+        if rank == 0:
+            print(json.dumps({"mode": "kernels", "steps": args.steps, "launches_per_step": 1, "batch": bt["info"]}))
+        return 0
     if args.mode == "kernels":
         # profiling case: the step's launch only (no e2e copies, no CPU baseline, no other rows)
         prec = {"fp32": fmmgb.FMM_FP32, "tc3": fmmgb.FMM_TC_BF16X3, "tc1": fmmgb.FMM_TC_BF16}[args.prec]
@@ -341,6 +380,30 @@ def run_ours(args):
                                                   "measured coefficient errors in tests/test_m2l_tc_gpu.py"}
         rows["tc_vs_fp32_speedup_p16"] = {"speedup": statistics.median(step_ms) / rows["m2l_tc_bf16x3_levels_2_8"]["ms"]}
         del M24, L24, M24s, L24s
+        # batched persistent launch: 256 independent problems (depth 4..9, p in {6, 8, 12, 16})
+        bt = _batched_setup(torch, fmmgb, dev)
+        bplan = bt["plan"]
+        bplan.run(stream)
+        torch.cuda.synchronize()
+        ms = statistics.median(_timed(torch, lambda: bplan.run(stream), args.steps, stream, flush))
+
+        def per_problem():
+            for tr, p_, m_, l_ in zip(bt["trees"], bt["ps"], bt["Ms"], bt["Ls"]):
+                fmmgb.fmm_m2l_levels(tr, 2, p_, m_, l_, stream=stream)
+
+        per_problem()
+        torch.cuda.synchronize()
+        ms_seq = statistics.median(_timed(torch, per_problem, args.steps, stream, flush))
+        ntr_b = bt["info"]["translations"]
+        rows["m2l_batched_256_problems"] = {
+            "translations_per_s": ntr_b / (ms * 1e-3), "ms": ms, "launches": 1, "translations": ntr_b,
+            "gflops": bt["flops"] / (ms * 1e-3) / 1e9,
+            "alu_frac": bt["flops"] / (ms * 1e-3) / 1e12
+            / (SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12),
+            "plan": bt["info"], "one_launch_per_problem_ms": ms_seq,
+            "speedup_vs_one_launch_per_problem": ms_seq / ms}
+        del bt, bplan
+        fmmgb.fmm_sync_status()
         fcfg = workloads.CONFIGS["fgt"]
         fx, fq = workloads.gmm_particles(fcfg["n"], workloads.rng_for("fgt"))
         fxd = torch.from_numpy(fx).to(dev)
@@ -412,8 +475,8 @@ def main():
     ap.add_argument("--no-rows", action="store_true", help="skip the adjoint / per-level / FGT rows")
     ap.add_argument("--mode", default="full", choices=["full", "kernels"],
                     help="kernels: only the timed step's launches (for ncu captures)")
-    ap.add_argument("--prec", default="fp32", choices=["fp32", "tc3", "tc1"],
-                    help="precision of the launches in --mode kernels")
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "tc3", "tc1", "batched"],
+                    help="precision of the launches in --mode kernels (batched: the 256-problem batch)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

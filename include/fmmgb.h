@@ -174,6 +174,79 @@ int fmm_m2l_adjoint_levels(const fmm_tree* tree, int32_t lmin, int32_t lmax, int
                            const void* const* W, void* const* G, int32_t flags, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Batched M2L: many independent uniform-tree problems (each with its own
+ * depth and p) translated in ONE persistent launch.  Each problem's levels
+ * 2..max_level are split into work items (a 4 x 4 tile of parent boxes of one
+ * level of one problem, the unit of fmm_m2l), ordered heaviest first
+ * (p^2 x translations per tile); resident CTAs claim items from a work counter,
+ * so the launch load-balances across problems of very different sizes.  The
+ * per-problem semantics are exactly fmm_m2l_levels(trees[i], 2, max_level_i,
+ * p[i], FMM_FP32, ...): levels 0 and 1 have no interaction lists and are not
+ * passed.  (Sec. 4.1 steps 2-3, Eq. M2Lmat, applied per problem.)
+ *
+ * A plan (fmm_batch) owns the device copy of the item list and the launch
+ * configuration; running it launches one kernel after a 4-byte counter reset,
+ * both of which a CUDA stream capture can record, so a plan replays inside a
+ * CUDA graph.
+ *
+ * fmm_batch_create
+ *   trees     host array [nprob] of tree handles (uniform trees); must outlive
+ *             the call only.
+ *   p         host array [nprob]: 6, 8, 12 or 16 per problem.
+ *   nprob     number of problems, 1..65536.
+ *   M_levels  host array of device pointers: problem 0's levels 2..max_level_0,
+ *             then problem 1's levels 2..max_level_1, and so on (sum over
+ *             problems of max_level_i - 1 entries); level l of problem i is
+ *             const complex64 [4^l][p_i] scaled MEs.  Pointers are copied into
+ *             the plan: the buffers must stay allocated while the plan runs.
+ *   L_levels  the same layout for the outputs (scaled LEs), each [4^l][p_i],
+ *             none overlapping its own level's input.
+ *   prec      FMM_FP32 (the only precision of the batched path).
+ *   flags     FMM_ACCUMULATE (add into L), FMM_BATCH_AUTOTUNE (time the
+ *             candidate launch configurations on this plan before returning,
+ *             writing only library scratch, never L; the choice is cached per
+ *             device and workload signature).
+ *   stream    the plan's device arrays are uploaded on this stream; the call
+ *             returns after they are resident (it synchronises the stream).
+ *   out       receives the plan.
+ * Errors: FMM_EINVAL (bad argument; nothing allocated), FMM_EUNSUPPORTED (p or
+ * prec outside the batched set), FMM_ENOMEM / FMM_ECUDA.
+ * ------------------------------------------------------------------------- */
+typedef struct fmm_batch fmm_batch; /* opaque, library-owned */
+#define FMM_BATCH_AUTOTUNE 4
+
+int fmm_batch_create(const fmm_tree* const* trees, const int32_t* p, int32_t nprob,
+                     const void* const* M_levels, void* const* L_levels, int32_t prec, int32_t flags,
+                     void* stream, fmm_batch** out);
+
+/* Launch the plan on `stream` (asynchronous; no host synchronisation, no
+ * allocation).  Runs of one plan must be ordered (same stream, or events):
+ * they share the plan's work counter. */
+int fmm_batch_run(fmm_batch* batch, void* stream);
+
+/* Launch configuration and size of a plan. */
+typedef struct {
+    int64_t items;         /* work items (tiles) */
+    int64_t translations;  /* interaction-list entries over all problems and levels */
+    int32_t grid;          /* CTAs launched */
+    int32_t chunk;         /* items claimed per work-counter update */
+    int32_t persistent;    /* 1: grid < items, CTAs loop over claimed items */
+    int32_t tuned;         /* 1: configuration chosen by timing (FMM_BATCH_AUTOTUNE) */
+    float tuned_ms;        /* best timed run of the autotuner, 0 if not tuned */
+} fmm_batch_info_t;
+int fmm_batch_info(const fmm_batch* batch, fmm_batch_info_t* out);
+
+/* Free the plan's device arrays in stream order on `stream` (the plan may
+ * still be running there) and the plan itself. */
+void fmm_batch_destroy(fmm_batch* batch, void* stream);
+
+/* One-shot form: create (without autotuning), run and destroy on `stream`,
+ * fully stream-ordered (no host synchronisation after the upload). */
+int fmm_m2l_batched(const fmm_tree* const* trees, const int32_t* p, int32_t nprob,
+                    const void* const* M_levels, void* const* L_levels, int32_t prec, int32_t flags,
+                    void* stream);
+
+/* ---------------------------------------------------------------------------
  * fgt_h2t -- Hermite-to-Taylor translation of the fast Gauss transform over
  * a uniform grid of 2^g x 2^g boxes on [0,1)^2 (Sec. 2.2, Eq. C_beta, with
  * the factor (-1)^|beta| / beta! that the printed equation omits):

@@ -277,6 +277,9 @@ struct fmm_tree {
     std::mutex mu;
 };
 
+int fmmgb::tree_max_level(const fmm_tree* t) { return t->max_level; }
+int fmmgb::tree_periodic(const fmm_tree* t) { return t->periodic; }
+
 static int64_t translations_closed_form(int level, bool periodic)
 {
     if (level < 2) return 0;

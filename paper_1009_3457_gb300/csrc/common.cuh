@@ -93,6 +93,10 @@ struct M2LLaunch {
     int accumulate;
 };
 
+// tree handle accessors (api.cu)
+int tree_max_level(const fmm_tree* t);
+int tree_periodic(const fmm_tree* t);
+
 // launchers (m2l_fp32.cu)
 int launch_build_m2l_tables(const M2LTables& t, cudaStream_t st);
 bool m2l_fp32_supported(int p);

@@ -1,0 +1,291 @@
+// m2l_fp32_tile.cuh -- the FP32 M2L work unit shared by the per-level stencil
+// kernel (m2l_fp32.cu) and the batched persistent kernel (m2l_batched.cu):
+// one CTA translates and reduces every interaction list of the 64 target boxes
+// of a 4 x 4 tile of parent boxes of one uniform level (Sec. 4.1 steps 2-3,
+// Eq. M2Lmat).
+//
+// Formulation (radius-scaled units, D = (x_t - x_s)/r a complex integer):
+//   L~_t[n] = sum_{s in IL(t)} sum_k a_n h_D[n+k] b_k M~_s[k]
+//           = a_n * sum_{s} sum_k h_D[n+k] (b_k M~_s[k])
+// so each translation is a Hankel matrix-vector product between two diagonal
+// scalings that do not depend on the offset: b_k is applied once per source
+// box while it is staged into shared memory, a_n once per target box at the
+// store.  Because the matrix is Hankel, a thread that owns RN consecutive
+// rows n0..n0+RN-1 needs one new operator value h[n0+RN+k] per k (a sliding
+// register window) instead of a column of the p x p matrix.
+//
+// Work unit (GB300-first; replaces the paper's thread-per-row, source-centric
+// kernel and its separate reduction kernel, Sec. 4.1.1):
+//   - the parent halo (tile + 1 on each side) holds every source any of the
+//     64 targets needs; each source ME is read once per tile (coalesced
+//     16-byte loads), scaled by b_k and reused by up to 27 targets;
+//   - the halo is stored in shared memory split by child class
+//     c' = (ix & 1) + 2 (iy & 1) and transposed to [c'][k][hy][hx], so that
+//     for a target class c every interaction-list entry is a constant shift
+//     (ex, ey) inside one class plane;
+//   - warp w handles the 16 targets of child class c = w, whose 27 list
+//     offsets are therefore warp-uniform; lane = (half, target): for p <= 16
+//     a lane keeps all p rows of its target and the two half-warps take 14
+//     and 13 of the 27 list entries (one shuffle adds the halves), so each k
+//     step costs two shared loads per 4p FFMA; for p = 24 the halves split
+//     the rows instead (register budget);
+//   - the reduction over the list is a register accumulation, written once
+//     per target (no separate reduction kernel, no atomics: deterministic).
+#pragma once
+
+#include "common.cuh"
+
+namespace fmmgb {
+
+constexpr int kThreads = 128;  // 4 warps, one per target child class
+constexpr int kTile = 4;       // parent boxes per tile side
+constexpr int kHalo = kTile + 2;
+constexpr int kPlane = kHalo * kHalo + 1;  // float2 stride between k-planes
+
+template <int P>
+struct M2LCfg {
+    static constexpr bool SPLIT_ROWS = P > 16;     // p = 24: the two half-warps split the rows
+    static constexpr int RN = SPLIT_ROWS ? P / 2 : P;  // rows per lane
+    static constexpr int NH = 2 * P - 1;           // Hankel diagonals
+    static constexpr int CS = P * kPlane;          // float2 stride between class planes
+    static constexpr int HALO = 4 * CS;            // float2 per halo buffer
+    static constexpr int MIN_CTAS = P == 16 ? 6 : 1;  // p = 16: 6 resident CTAs per SM (<= 80 registers)
+    static constexpr size_t smem = sizeof(float2) * (HALO + kOffsetSlots * NH) + sizeof(float) * 2 * P +
+                                   sizeof(int2) * 4 * 27;
+};
+
+__device__ __forceinline__ void cmac(float2& acc, const float2 w, const float2 m)
+{
+    acc.x = fmaf(w.x, m.x, acc.x);
+    acc.x = fmaf(-w.y, m.y, acc.x);
+    acc.y = fmaf(w.x, m.y, acc.y);
+    acc.y = fmaf(w.y, m.x, acc.y);
+}
+
+// Number of 4 x 4-parent tiles of a level (levels 0 and 1 have no lists).
+__host__ __device__ inline int m2l_tiles(int level)
+{
+    if (level < 2) return 0;
+    const int np = 1 << (level - 1);
+    const int t = (np + kTile - 1) / kTile;
+    return t * t;
+}
+
+// One tile of one level: its coefficient arrays and its first parent box.
+struct TileGeom {
+    const float2* M;
+    float2* L;
+    int side, np, PX0, PY0;
+};
+
+__device__ __forceinline__ TileGeom tile_geom_of(const float2* M, float2* L, int level, int t)
+{
+    TileGeom g;
+    g.M = M;
+    g.L = L;
+    g.side = 1 << level;
+    g.np = g.side >> 1;
+    const int tpr = (g.np + kTile - 1) / kTile;
+    g.PX0 = (t % tpr) * kTile;
+    g.PY0 = (t / tpr) * kTile;
+    return g;
+}
+
+// Shared-memory layout of the work unit for order P.
+template <int P>
+struct TileSmem {
+    float2* buf;  // [4][P][kPlane] class-split halo
+    float2* hs;   // [49][NH] Hankel operator values
+    float* as;    // [P] post-scale
+    float* bs;    // [P] pre-scale
+    int2* lst;    // [4][27]: (Hankel row offset, halo offset) per target class
+    __device__ __forceinline__ explicit TileSmem(unsigned char* raw)
+    {
+        using C = M2LCfg<P>;
+        buf = reinterpret_cast<float2*>(raw);
+        hs = buf + C::HALO;
+        as = reinterpret_cast<float*>(hs + kOffsetSlots * C::NH);
+        bs = as + P;
+        lst = reinterpret_cast<int2*>(bs + P);
+    }
+};
+
+// Load the operator tables of order P and the per-class list stencils into
+// shared memory.  The caller synchronises before the next m2l_tile.
+template <int P>
+__device__ __forceinline__ void m2l_load_operator(unsigned char* raw, const float2* __restrict__ hsel,
+                                                  const float* __restrict__ ascale, const float* __restrict__ bscale)
+{
+    using C = M2LCfg<P>;
+    constexpr int NH = C::NH;
+    const TileSmem<P> s(raw);
+    const int tid = threadIdx.x;
+    for (int i = tid; i < kOffsetSlots * NH; i += kThreads) s.hs[i] = hsel[i];
+    for (int i = tid; i < P; i += kThreads) {
+        s.as[i] = ascale[i];
+        s.bs[i] = bscale[i];
+    }
+    if (tid < 4) {  // the 27 interaction-list entries of child class tid, in (ey, ex, c') order
+        const int cx = tid & 1, cy = tid >> 1;
+        int n = 0;
+        for (int e = 0; e < 36; ++e) {
+            const int sx = e & 1, sy = (e >> 1) & 1, pe = e >> 2;
+            const int ex = pe % 3 - 1, ey = pe / 3 - 1;
+            const int dx = 2 * ex + sx - cx, dy = 2 * ey + sy - cy;
+            const int adx = dx < 0 ? -dx : dx, ady = dy < 0 ? -dy : dy;
+            if ((adx > ady ? adx : ady) < 2) continue;  // adjacent: near field
+            s.lst[tid * 27 + n++] = make_int2(offset_slot(dx, dy) * NH, (sx + 2 * sy) * C::CS + (ey + 1) * kHalo + (ex + 1));
+        }
+    }
+}
+
+// Translate and reduce one tile.  Requires the operator of order P in shared
+// memory (m2l_load_operator + a barrier) and no thread still reading the halo
+// buffer of a previous tile (a barrier).  All 128 threads call it.
+template <int P>
+__device__ __forceinline__ void m2l_tile(unsigned char* raw, const TileGeom& g, int periodic, int accumulate)
+{
+    using C = M2LCfg<P>;
+    constexpr int RN = C::RN, Q = P / 2;
+    const TileSmem<P> s(raw);
+    const int tid = threadIdx.x;
+
+    // Stage the 2 kHalo x 2 kHalo halo boxes, pre-scaled by b_k, into the
+    // class-split transposed layout; consecutive threads read consecutive
+    // 16-byte chunks of a row of boxes (coalesced); zero outside the level.
+    const float4* M4 = reinterpret_cast<const float4*>(g.M);
+    for (int i = tid; i < (2 * kHalo) * (2 * kHalo) * Q; i += kThreads) {
+        const int q = i % Q, bxy = i / Q;
+        const int hxb = bxy % (2 * kHalo), hyb = bxy / (2 * kHalo);
+        int ix = 2 * g.PX0 - 2 + hxb, iy = 2 * g.PY0 - 2 + hyb;
+        bool in = ix >= 0 && iy >= 0 && ix < g.side && iy < g.side;
+        if (periodic) {
+            ix = (ix + 2 * g.side) % g.side;
+            iy = (iy + 2 * g.side) % g.side;
+            in = true;
+        }
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (in) v = __ldg(M4 + ((size_t)iy * g.side + ix) * Q + q);
+        float2* dst = s.buf + ((hxb & 1) + 2 * (hyb & 1)) * C::CS + (hyb >> 1) * kHalo + (hxb >> 1);
+        const float b0 = s.bs[2 * q], b1 = s.bs[2 * q + 1];
+        dst[(2 * q) * kPlane] = make_float2(v.x * b0, v.y * b0);
+        dst[(2 * q + 1) * kPlane] = make_float2(v.z * b1, v.w * b1);
+    }
+    __syncthreads();
+
+    const int warp = tid >> 5, lane = tid & 31;
+    const int cls = warp, cx = warp & 1, cy = warp >> 1;
+    const int half = lane >> 4, t = lane & 15;
+    const int tpx = t & 3, tpy = t >> 2;
+    const int2* mylist = s.lst + cls * 27;
+
+    // ---- translate and reduce ----
+    float2 acc[RN];
+#pragma unroll
+    for (int i = 0; i < RN; ++i) acc[i] = make_float2(0.f, 0.f);
+    const float2* tbase = s.buf + tpy * kHalo + tpx;
+    if constexpr (!C::SPLIT_ROWS) {
+        // half-warp `half` takes list entries [14 half, 14 half + 14) of 27; all p rows
+#pragma unroll 1
+        for (int j = 0; j < 14; ++j) {
+            const int e = half * 14 + j;
+            if (e >= 27) break;
+            const int2 ent = mylist[e];
+            const float2* hrow = s.hs + ent.x;
+            const float2* src = tbase + ent.y;
+            float2 w[RN];
+#pragma unroll
+            for (int i = 0; i < RN; ++i) w[i] = hrow[i];
+#pragma unroll
+            for (int k = 0; k < P; ++k) {
+                const float2 m = src[k * kPlane];
+#pragma unroll
+                for (int i = 0; i < RN; ++i) cmac(acc[i], w[i], m);
+                if (k + 1 < P) {
+#pragma unroll
+                    for (int i = 0; i + 1 < RN; ++i) w[i] = w[i + 1];
+                    w[RN - 1] = hrow[RN + k];
+                }
+            }
+        }
+    } else {
+        // half-warp `half` takes rows [RN half, RN half + RN); all 27 entries
+        const int n0 = half * RN;
+#pragma unroll 1
+        for (int e = 0; e < 27; ++e) {
+            const int2 ent = mylist[e];
+            const float2* hrow = s.hs + ent.x + n0;
+            const float2* src = tbase + ent.y;
+            float2 w[RN];
+#pragma unroll
+            for (int i = 0; i < RN; ++i) w[i] = hrow[i];
+#pragma unroll
+            for (int k = 0; k < P; ++k) {
+                const float2 m = src[k * kPlane];
+#pragma unroll
+                for (int i = 0; i < RN; ++i) cmac(acc[i], w[i], m);
+                if (k + 1 < P) {
+#pragma unroll
+                    for (int i = 0; i + 1 < RN; ++i) w[i] = w[i + 1];
+                    w[RN - 1] = hrow[RN + k];
+                }
+            }
+        }
+    }
+
+    // ---- combine the half-warps: each lane ends with p/2 finished rows ----
+    constexpr int HR = P / 2;
+    float2 res[HR];
+    if constexpr (!C::SPLIT_ROWS) {
+#pragma unroll
+        for (int i = 0; i < HR; ++i) {
+            const float2 send = half ? acc[i] : acc[HR + i];
+            const float2 mine = half ? acc[HR + i] : acc[i];
+            float2 r;
+            r.x = __shfl_xor_sync(0xffffffffu, send.x, 16);
+            r.y = __shfl_xor_sync(0xffffffffu, send.y, 16);
+            res[i] = make_float2(mine.x + r.x, mine.y + r.y);
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < HR; ++i) res[i] = acc[i];
+    }
+
+    // ---- store L~[n] = a_n * res (rows [HR half, HR half + HR)) ----
+    const int px = g.PX0 + tpx, py = g.PY0 + tpy;
+    if (px < g.np && py < g.np) {
+        const int ix = 2 * px + cx, iy = 2 * py + cy;
+        const int n0 = half * HR;
+        float2* dst = g.L + ((size_t)iy * g.side + ix) * P + n0;
+        if constexpr (HR % 2 == 0) {
+            float4* d4 = reinterpret_cast<float4*>(dst);
+#pragma unroll
+            for (int i = 0; i < HR; i += 2) {
+                const float s0 = s.as[n0 + i], s1 = s.as[n0 + i + 1];
+                float4 o = make_float4(s0 * res[i].x, s0 * res[i].y, s1 * res[i + 1].x, s1 * res[i + 1].y);
+                if (accumulate) {
+                    const float4 old = d4[i / 2];
+                    o.x += old.x;
+                    o.y += old.y;
+                    o.z += old.z;
+                    o.w += old.w;
+                }
+                d4[i / 2] = o;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < HR; ++i) {
+                const float s0 = s.as[n0 + i];
+                float2 o = make_float2(s0 * res[i].x, s0 * res[i].y);
+                if (accumulate) {
+                    const float2 old = dst[i];
+                    o.x += old.x;
+                    o.y += old.y;
+                }
+                dst[i] = o;
+            }
+        }
+    }
+}
+
+}  // namespace fmmgb

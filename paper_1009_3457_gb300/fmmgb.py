@@ -29,6 +29,7 @@ FMM_ACCUMULATE = 1
 FMM_CONJ = 2
 FMM_TREE_PERIODIC = 1
 FMM_MAX_LEVEL = 14
+FMM_BATCH_AUTOTUNE = 4
 
 STATUS_NAMES = {0: "FMM_OK", -1: "FMM_EINVAL", -2: "FMM_ENOMEM", -3: "FMM_ECUDA", -4: "FMM_ETIMEOUT",
                 -5: "FMM_EUNSUPPORTED", -6: "FMM_EDEVICE"}
@@ -53,6 +54,18 @@ class fmm_level_info(ctypes.Structure):
     ]
 
 
+class fmm_batch_info_t(ctypes.Structure):
+    _fields_ = [
+        ("items", ctypes.c_int64),
+        ("translations", ctypes.c_int64),
+        ("grid", ctypes.c_int32),
+        ("chunk", ctypes.c_int32),
+        ("persistent", ctypes.c_int32),
+        ("tuned", ctypes.c_int32),
+        ("tuned_ms", ctypes.c_float),
+    ]
+
+
 _vp = ctypes.c_void_p
 _i32 = ctypes.c_int32
 _i64 = ctypes.c_int64
@@ -72,6 +85,13 @@ SIGNATURES = {
                                       _i32, _vp]),
     "fmm_m2l_adjoint_levels": (ctypes.c_int, [_vp, _i32, _i32, _i32, _i32, ctypes.POINTER(_vp),
                                               ctypes.POINTER(_vp), _i32, _vp]),
+    "fmm_batch_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(_i32), _i32, ctypes.POINTER(_vp),
+                                        ctypes.POINTER(_vp), _i32, _i32, _vp, ctypes.POINTER(_vp)]),
+    "fmm_batch_run": (ctypes.c_int, [_vp, _vp]),
+    "fmm_batch_info": (ctypes.c_int, [_vp, ctypes.POINTER(fmm_batch_info_t)]),
+    "fmm_batch_destroy": (None, [_vp, _vp]),
+    "fmm_m2l_batched": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(_i32), _i32, ctypes.POINTER(_vp),
+                                       ctypes.POINTER(_vp), _i32, _i32, _vp]),
     "fmm_p2m": (ctypes.c_int, [_i32, _i32, _vp, _vp, _i64, _vp, _i32, _vp]),
     "fmm_m2m": (ctypes.c_int, [_i32, _i32, _vp, _vp, _i32, _vp]),
     "fgt_h2t": (ctypes.c_int, [_i32, _i32, _i32, _d, _vp, _vp, _vp, _i32, _vp]),
@@ -211,6 +231,59 @@ def fmm_m2l_adjoint_levels(tree: Tree, lmin: int, p: int, Ws, Gs, prec: int = FM
     flags = (FMM_ACCUMULATE if accumulate else 0) | (FMM_CONJ if conj else 0)
     _check(load().fmm_m2l_adjoint_levels(tree.handle, lmin, lmin + len(Ws) - 1, p, prec, _ptr_array(Ws),
                                          _ptr_array(Gs), flags, _stream(stream)))
+
+
+def _batch_args(trees, ps, Ms, Ls):
+    """Marshal a batch: Ms[i], Ls[i] are problem i's level lists (levels 2..trees[i].max_level)."""
+    n = len(trees)
+    assert len(ps) == n and len(Ms) == n and len(Ls) == n and n > 0
+    flatM, flatL = [], []
+    for t, m, l in zip(trees, Ms, Ls):
+        if len(m) != t.max_level - 1 or len(l) != t.max_level - 1:
+            raise FmmError(FMM_EINVAL, "each problem needs one M and one L per level 2..max_level")
+        flatM += list(m)
+        flatL += list(l)
+    return ((_vp * n)(*[t.handle for t in trees]), (_i32 * n)(*[int(p) for p in ps]), n, _ptr_array(flatM),
+            _ptr_array(flatL))
+
+
+class Batch:
+    """Owning wrapper of an ``fmm_batch*`` plan (fmm_batch_create / run / info / destroy)."""
+
+    def __init__(self, handle: int, keep, stream):
+        self.handle = handle
+        self._keep = keep  # the trees and coefficient tensors the plan points into
+        self._stream = stream  # the plan's device arrays are freed in order on the last stream used
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h and _lib is not None:
+            _lib.fmm_batch_destroy(h, self._stream)
+            self.handle = None
+
+    def run(self, stream=None):
+        self._stream = _stream(stream)
+        _check(load().fmm_batch_run(self.handle, self._stream))
+
+    def info(self) -> dict:
+        inf = fmm_batch_info_t()
+        _check(load().fmm_batch_info(self.handle, ctypes.byref(inf)))
+        return {k: getattr(inf, k) for k, _ in fmm_batch_info_t._fields_}
+
+
+def fmm_batch_create(trees, ps, Ms, Ls, prec: int = FMM_FP32, accumulate: bool = False, autotune: bool = False,
+                     stream=None) -> Batch:
+    tr, pa, n, mp, lp = _batch_args(trees, ps, Ms, Ls)
+    flags = (FMM_ACCUMULATE if accumulate else 0) | (FMM_BATCH_AUTOTUNE if autotune else 0)
+    h = _vp()
+    st = _stream(stream)
+    _check(load().fmm_batch_create(tr, pa, n, mp, lp, prec, flags, st, ctypes.byref(h)))
+    return Batch(h.value, (list(trees), [list(m) for m in Ms], [list(l) for l in Ls]), st)
+
+
+def fmm_m2l_batched(trees, ps, Ms, Ls, prec: int = FMM_FP32, accumulate: bool = False, stream=None):
+    tr, pa, n, mp, lp = _batch_args(trees, ps, Ms, Ls)
+    _check(load().fmm_m2l_batched(tr, pa, n, mp, lp, prec, FMM_ACCUMULATE if accumulate else 0, _stream(stream)))
 
 
 def fmm_p2m(level: int, p: int, xy, c, M, accumulate: bool = False, stream=None):

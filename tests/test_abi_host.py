@@ -105,3 +105,40 @@ def test_levels_below_two_have_no_lists(fmm):
         lst, code = tree.lists(level)
         assert (lst == -1).all() and (code == -1).all()
         assert tree.translations(level) == 0
+
+
+def test_batch_rejects_bad_arguments_before_launch(fmm):
+    """fmm_batch_create / fmm_m2l_batched validate everything on the host."""
+    import ctypes
+
+    lib = fmm.load()
+    t3 = fmm.fmm_build_lists(None, 3)  # levels 2, 3 -> two pointers per problem
+    vp, i32 = ctypes.c_void_p, ctypes.c_int32
+
+    def call(trees, ps, Ms, Ls, prec=0, flags=0, nprob=None):
+        n = len(trees) if nprob is None else nprob
+        out = vp()
+        return lib.fmm_batch_create((vp * max(len(trees), 1))(*trees), (i32 * max(len(ps), 1))(*ps), n,
+                                    (vp * max(len(Ms), 1))(*Ms), (vp * max(len(Ls), 1))(*Ls), prec, flags, None,
+                                    ctypes.byref(out))
+
+    good_M, good_L = [1 << 20, 1 << 22], [1 << 24, 1 << 26]
+    assert call([t3.handle], [8], good_M, good_L, nprob=0) == fmm.FMM_EINVAL
+    assert call([None], [8], good_M, good_L) == fmm.FMM_EINVAL
+    assert call([t3.handle], [7], good_M, good_L) == fmm.FMM_EINVAL
+    assert call([t3.handle], [24], good_M, good_L) == fmm.FMM_EUNSUPPORTED
+    assert call([t3.handle], [8], good_M, good_L, prec=fmm.FMM_TC_BF16X3) == fmm.FMM_EUNSUPPORTED
+    assert call([t3.handle], [8], good_M, good_L, prec=9) == fmm.FMM_EINVAL
+    assert call([t3.handle], [8], good_M, good_L, flags=16) == fmm.FMM_EINVAL
+    assert call([t3.handle], [8], [1 << 20, None], good_L) == fmm.FMM_EINVAL
+    assert call([t3.handle], [8], [(1 << 20) + 8, 1 << 22], good_L) == fmm.FMM_EINVAL
+    # level 3 at p = 8 spans 64 * 8 * 8 = 4096 bytes: L inside M's range overlaps
+    assert call([t3.handle], [8], good_M, [1 << 24, (1 << 22) + 1024]) == fmm.FMM_EINVAL
+    assert "overlap" in fmm.fmm_last_error()
+    out = vp()
+    assert lib.fmm_batch_create(None, None, 1, None, None, 0, 0, None, ctypes.byref(out)) == fmm.FMM_EINVAL
+    one = (vp * 1)(t3.handle)
+    assert lib.fmm_m2l_batched(one, (i32 * 1)(8), 1, (vp * 2)(*good_M), (vp * 2)(*good_L), 0,
+                               fmm.FMM_BATCH_AUTOTUNE, None) == fmm.FMM_EINVAL
+    assert lib.fmm_batch_run(None, None) == fmm.FMM_EINVAL
+    lib.fmm_batch_destroy(None, None)  # no-op

@@ -19,6 +19,9 @@ uses no public dataset):
               tree (q = 64, level <= 9), p = 16
   fgt         2^20 Gaussian-mixture sources (same generator), weights U[-1,1],
               bandwidth sigma in {0.05, 0.1, 0.2}, Hermite order p in 8..16
+  m2l_batched 256 independent problems: N ~ logU[1e3, 1e5] points U[0,1)^2,
+              strengths U[-1,1], uniform quadtree of depth ~ U{4..9}, p ~
+              U{6, 8, 12, 16}, FP32, all translated in one launch
 """
 from __future__ import annotations
 
@@ -28,7 +31,7 @@ import numpy as np
 
 SEED_BASE = 20100913
 
-WORKLOAD_IDS = {"m2l_small": 1, "m2l_scale": 2, "m2l_tc": 3, "m2l_gmm": 4, "fgt": 5}
+WORKLOAD_IDS = {"m2l_small": 1, "m2l_scale": 2, "m2l_tc": 3, "m2l_gmm": 4, "fgt": 5, "m2l_batched": 6}
 
 
 def rng_for(workload: str, salt: int = 0) -> np.random.Generator:
@@ -58,6 +61,21 @@ def gmm_particles(n: int, rng: np.random.Generator, ncomp: int = 16,
     return np.ascontiguousarray(out[:n]), np.ascontiguousarray(c)
 
 
+def batched_problems(nprob: int, rng: np.random.Generator, depths=(4, 9), orders=(6, 8, 12, 16),
+                     n_range=(1e3, 1e5)):
+    """Shapes of a batch of independent uniform-tree problems: a list of
+    dicts (n, max_level, p), n log-uniform in n_range, depth uniform in the
+    closed range `depths`, p uniform over `orders`."""
+    lo, hi = math.log(n_range[0]), math.log(n_range[1])
+    out = []
+    for _ in range(nprob):
+        n = int(round(math.exp(rng.uniform(lo, hi))))
+        depth = int(rng.integers(depths[0], depths[1] + 1))
+        p = int(orders[int(rng.integers(0, len(orders)))])
+        out.append(dict(n=n, max_level=depth, p=p))
+    return out
+
+
 def m2l_levels(max_level: int):
     """Levels that carry M2L translations in a uniform tree: 2..max_level."""
     return list(range(2, max_level + 1))
@@ -76,4 +94,5 @@ CONFIGS = {
     "m2l_tc": dict(n=4096, max_level=4, p=24),
     "m2l_gmm": dict(n=1 << 20, max_level=9, leaf_cap=64, p=16),
     "fgt": dict(n=1 << 20, sigmas=(0.05, 0.1, 0.2), orders=(8, 12, 16), ncut=FGT_NCUT),
+    "m2l_batched": dict(nprob=256, depths=(4, 9), orders=(6, 8, 12, 16), n_range=(1e3, 1e5)),
 }
