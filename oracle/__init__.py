@@ -42,6 +42,7 @@ def build(force: bool = False) -> str:
 _D = ctypes.POINTER(ctypes.c_double)
 _I = ctypes.POINTER(ctypes.c_int)
 _I64 = ctypes.POINTER(ctypes.c_int64)
+_U8 = ctypes.POINTER(ctypes.c_uint8)
 _i = ctypes.c_int
 _i64 = ctypes.c_int64
 _d = ctypes.c_double
@@ -63,6 +64,15 @@ _SIGS = {
     "orc_m2p": (None, [_i, _D, _d, _d, _i64, _D, _D]),
     "orc_direct": (None, [_i64, _D, _D, _i64, _D, _D]),
     "orc_l2l": (None, [_i, _D, _d, _d, _D]),
+    "orc_level_offset": (_i64, [_i]),
+    "orc_adaptive_tree": (_i, [_i64, _D, _i, _i, _U8]),
+    "orc_vlist": (_i, [_i, _i, _i, _U8, _I, _I, _I, _I]),
+    "orc_vlist_count_level": (_i64, [_i, _U8]),
+    "orc_m2l_adaptive": (None, [_i, _i, _U8, _D, _D]),
+    "orc_m2l_adjoint_adaptive": (None, [_i, _i, _U8, _D, _D]),
+    "orc_m2l_adaptive_from_sources": (None, [_i, _i, _U8, _i64, _I64, _D, _D]),
+    "orc_p2m_assigned": (None, [_i, _i, _i64, _D, _D, _I64, _D]),
+    "orc_l2l_level": (None, [_i, _i, _U8, _D, _D]),
     "orc_hermite_functions": (None, [_i, _d, _D]),
     "orc_fgt_direct": (None, [_i64, _D, _D, _d, _i64, _D, _D]),
     "orc_fgt_p2h": (None, [_i64, _D, _D, _d, _d, _d, _i, _D]),
@@ -238,6 +248,169 @@ def l2l(p: int, lp: np.ndarray, shift: complex) -> np.ndarray:
     lc = np.zeros((p, 2))
     lib().orc_l2l(p, _dp(lpr), shift.real, shift.imag, _dp(lc))
     return _r2c(lc)
+
+
+# ---------------------------------------------------------------------------
+# adaptive quadtree, V-lists and the far field on it (reading R7, R11)
+# ---------------------------------------------------------------------------
+
+class AdaptiveTree:
+    """Box existence over levels 0..max_level of an adaptive quadtree (reading R7)."""
+
+    def __init__(self, exists: np.ndarray, max_level: int, depth: int, q: int):
+        self.exists = exists  # uint8, level-major: level l at [(4^l - 1)/3, (4^(l+1) - 1)/3)
+        self.max_level = max_level
+        self.depth = depth
+        self.q = q
+
+    def level(self, l: int) -> np.ndarray:
+        """Existence of the 4^l boxes of level l (bool, b = iy * 2^l + ix)."""
+        off = ((1 << (2 * l)) - 1) // 3
+        return self.exists[off:off + (1 << (2 * l))].astype(bool)
+
+    def _ptr(self):
+        return self.exists.ctypes.data_as(_U8)
+
+
+def adaptive_tree(xy, q: int, max_level: int) -> AdaptiveTree:
+    """Split boxes holding more than q points down to max_level; empty children are dropped."""
+    xy = _f64(xy)
+    ex = np.zeros(((1 << (2 * (max_level + 1))) - 1) // 3, dtype=np.uint8)
+    depth = lib().orc_adaptive_tree(xy.shape[0], _dp(xy), q, max_level, ex.ctypes.data_as(_U8))
+    return AdaptiveTree(ex, max_level, int(depth), q)
+
+
+def vlist(tree: AdaptiveTree, level: int, tx: int, ty: int):
+    """V-list of (tx, ty): [(sx, sy, ox, oy)], offsets = source minus target in box units."""
+    bufs = [np.zeros(27, dtype=np.int32) for _ in range(4)]
+    ptrs = [b.ctypes.data_as(_I) for b in bufs]
+    n = lib().orc_vlist(level, tx, ty, tree._ptr(), *ptrs)
+    return [tuple(int(b[i]) for b in bufs) for i in range(n)]
+
+
+def vlist_count_level(tree: AdaptiveTree, level: int) -> int:
+    return int(lib().orc_vlist_count_level(level, tree._ptr()))
+
+
+def m2l_adaptive(tree: AdaptiveTree, level: int, p: int, M: np.ndarray) -> np.ndarray:
+    """Physical-unit M2L over the V-lists of one level (zero at absent boxes)."""
+    Mr = _c2r(M)
+    L = np.zeros_like(Mr)
+    lib().orc_m2l_adaptive(level, p, tree._ptr(), _dp(Mr), _dp(L))
+    return _r2c(L)
+
+
+def m2l_adjoint_adaptive(tree: AdaptiveTree, level: int, p: int, W: np.ndarray) -> np.ndarray:
+    """Plain transpose of ``m2l_adaptive`` by explicit transposed loops."""
+    Wr = _c2r(W)
+    G = np.zeros_like(Wr)
+    lib().orc_m2l_adjoint_adaptive(level, p, tree._ptr(), _dp(Wr), _dp(G))
+    return _r2c(G)
+
+
+def leaf_boxes(tree: AdaptiveTree, xy):
+    """(leaf level, leaf box index) of every point: the deepest existing box containing it (reading R5)."""
+    xy = _f64(xy)
+    lev = np.zeros(xy.shape[0], dtype=np.int64)
+    box = np.zeros(xy.shape[0], dtype=np.int64)
+    for l in range(tree.depth + 1):
+        n = 1 << l
+        ix = np.clip(np.floor(xy[:, 0] * n).astype(np.int64), 0, n - 1)
+        iy = np.clip(np.floor(xy[:, 1] * n).astype(np.int64), 0, n - 1)
+        b = iy * n + ix
+        here = tree.level(l)[b]
+        lev = np.where(here, l, lev)
+        box = np.where(here, b, box)
+    return lev, box
+
+
+def ancestor_box(leaf_level, leaf_box, level: int) -> np.ndarray:
+    """Box of `level` containing each leaf (-1 where the leaf is shallower than `level`)."""
+    leaf_level = np.asarray(leaf_level, dtype=np.int64)
+    leaf_box = np.asarray(leaf_box, dtype=np.int64)
+    sh = leaf_level - level
+    side = np.left_shift(1, leaf_level)
+    ix = np.right_shift(leaf_box % side, np.maximum(sh, 0))
+    iy = np.right_shift(leaf_box // side, np.maximum(sh, 0))
+    return np.where(sh >= 0, iy * (1 << level) + ix, -1)
+
+
+def p2m_assigned(level: int, p: int, xy, c, box) -> np.ndarray:
+    """ME of every box of `level` from the points assigned to it (box[i] = -1: none)."""
+    xy, c = _f64(xy), _f64(c)
+    b = np.ascontiguousarray(box, dtype=np.int64)
+    M = np.zeros(((1 << (2 * level)), p, 2))
+    lib().orc_p2m_assigned(level, p, len(c), _dp(xy), _dp(c), b.ctypes.data_as(_I64), _dp(M))
+    return _r2c(M)
+
+
+def _l2p_at_leaves(p: int, L: dict, z, z_lev, z_box) -> np.ndarray:
+    """phi(z_j) = sum_n L[leaf_j][n] (z_j - x_leaf)^n for every evaluation point."""
+    z = np.asarray(z, dtype=np.complex128)
+    phi = np.zeros(len(z), dtype=np.complex128)
+    for l in np.unique(z_lev):
+        sel = np.nonzero(z_lev == l)[0]
+        if l < 2:
+            continue  # no far field above level 2
+        n = 1 << int(l)
+        bx, by = z_box[sel] % n, z_box[sel] // n
+        centre = (bx + 0.5) / n + 1j * (by + 0.5) / n
+        d = z[sel] - centre
+        acc = np.zeros(len(sel), dtype=np.complex128)
+        for k in range(p - 1, -1, -1):  # Horner
+            acc = acc * d + L[int(l)][z_box[sel], k]
+        phi[sel] = acc
+    return phi
+
+
+def far_field_objective(tree: AdaptiveTree, p: int, xy, c, leaf, z, z_leaf, omega) -> float:
+    """J = sum_j omega_j Re phi_far(z_j) (reading R11): the MEs of every level from
+    the points assigned to the frozen leaves `leaf` = (levels, boxes), M2L over the
+    V-lists of levels 2..depth, L2L down, L2P at each evaluation point's leaf."""
+    lev, box = leaf
+    L = {}
+    for l in range(2, tree.depth + 1):
+        M = p2m_assigned(l, p, xy, c, ancestor_box(lev, box, l))
+        Lr = _c2r(m2l_adaptive(tree, l, p, M))
+        if l > 2:
+            lib().orc_l2l_level(l, p, tree._ptr(), _dp(_c2r(L[l - 1])), _dp(Lr))
+        L[l] = _r2c(Lr)
+    phi = _l2p_at_leaves(p, L, z, z_leaf[0], z_leaf[1])
+    return float(np.sum(np.asarray(omega) * phi.real))
+
+
+def far_field_fd_gradient(tree: AdaptiveTree, p: int, xy, c, leaf, z, z_leaf, omega, idx, h: float = 1e-4):
+    """Central differences (J(y + h e) - J(y - h e)) / 2h of `far_field_objective`
+    with respect to the coordinates of the points `idx` (frozen topology).  J is
+    linear in the MEs, so each difference is J's pipeline applied to the
+    difference of the perturbed MEs, which is non-zero only in the point's
+    ancestor boxes (one per level): the M2L runs from those boxes only.
+    Returns [len(idx), 2] (d/dx, d/dy)."""
+    xy, c = _f64(xy), _f64(c)
+    lev, box = leaf
+    out = np.zeros((len(idx), 2))
+    for r, i in enumerate(idx):
+        for axis in range(2):
+            plus, minus = xy[i].copy(), xy[i].copy()
+            plus[axis] += h
+            minus[axis] -= h
+            L = {}
+            for l in range(2, tree.depth + 1):
+                Lr = np.zeros(((1 << (2 * l)), p, 2))
+                b = int(ancestor_box(lev[i:i + 1], box[i:i + 1], l)[0])
+                if b >= 0:
+                    n = 1 << l
+                    centre = complex((b % n + 0.5) / n, (b // n + 0.5) / n)
+                    dM = p2m_box(plus[None, :], c[i:i + 1], centre, p) - p2m_box(minus[None, :], c[i:i + 1], centre, p)
+                    src = np.array([b], dtype=np.int64)
+                    lib().orc_m2l_adaptive_from_sources(l, p, tree._ptr(), 1, src.ctypes.data_as(_I64),
+                                                        _dp(_c2r(dM[None, :])), _dp(Lr))
+                if l > 2:
+                    lib().orc_l2l_level(l, p, tree._ptr(), _dp(_c2r(L[l - 1])), _dp(Lr))
+                L[l] = _r2c(Lr)
+            phi = _l2p_at_leaves(p, L, z, z_leaf[0], z_leaf[1])
+            out[r, axis] = float(np.sum(np.asarray(omega) * phi.real)) / (2.0 * h)
+    return out
 
 
 # ---------------------------------------------------------------------------

@@ -40,6 +40,16 @@
  *   R6  FGT: B_beta carries no (-1)^|beta| and the sum runs j = 1..N_B;
  *       C_beta carries the factor (-1)^|beta| / beta! that Eq. (C_beta) omits;
  *       delta = 2 sigma^2; tensor truncation alpha_i, beta_i < p.
+ *   R7  adaptive tree (the paper describes only uniform subdivision): the
+ *       root exists; an existing box holding more than q points is split
+ *       while its level is below max_level; children holding no point are
+ *       not created.  M2L on it runs over V-lists: the existing same-level
+ *       children of the parent's colleagues (and of the parent) that are not
+ *       adjacent to the target.  U/W/X lists are not part of the path.
+ *   R11 far-field objective for gradients: J = sum_j w_j Re phi_far(z_j) at
+ *       fixed evaluation points, phi_far(z) the L2P of the LE of z's leaf
+ *       after M2L over V-lists at every level and L2L down; the topology
+ *       (each point's leaf) is frozen when points move.
  */
 #include <complex.h>
 #include <math.h>
@@ -618,4 +628,206 @@ void orc_fgt_p2h_grid(int g, int p, double sigma, int64_t n, const double* x, co
     free(f);
     free(w1);
     free(w2);
+}
+
+/* ------------------------------------------------------------------ */
+/* adaptive quadtree, V-lists and the far field on it (reading R7)      */
+/* ------------------------------------------------------------------ */
+
+/* Boxes of all levels 0..L are numbered level by level: box b of level l is
+ * entry (4^l - 1)/3 + b of a per-tree array, b = iy * 2^l + ix. */
+static int64_t level_offset(int l) { return (((int64_t)1 << (2 * l)) - 1) / 3; }
+
+int64_t orc_level_offset(int l) { return level_offset(l); }
+
+/* Adaptive tree over levels 0..max_level (reading R7): the root exists; an
+ * existing box of level l < max_level holding more than q points is split,
+ * and each of its four children that holds at least one point exists.
+ * exists[] has level_offset(max_level + 1) entries.  Returns the deepest
+ * level that has an existing box. */
+int orc_adaptive_tree(int64_t n, const double* xy, int q, int max_level, uint8_t* exists)
+{
+    memset(exists, 0, (size_t)level_offset(max_level + 1));
+    exists[0] = 1;
+    int depth = 0;
+    int64_t* cnt_parent = NULL;
+    for (int l = 0; l <= max_level; ++l) {
+        int side = 1 << l;
+        int64_t* cnt = (int64_t*)calloc((size_t)side * side, sizeof(int64_t));
+        for (int64_t i = 0; i < n; ++i) {
+            int ix, iy;
+            point_box(l, xy[2 * i], xy[2 * i + 1], &ix, &iy);
+            cnt[(int64_t)iy * side + ix] += 1;
+        }
+        if (l > 0) {
+            int pside = side / 2;
+            for (int iy = 0; iy < side; ++iy)
+                for (int ix = 0; ix < side; ++ix) {
+                    int64_t pb = (int64_t)(iy / 2) * pside + ix / 2;
+                    int parent_split = exists[level_offset(l - 1) + pb] && cnt_parent[pb] > q;
+                    if (parent_split && cnt[(int64_t)iy * side + ix] > 0) {
+                        exists[level_offset(l) + (int64_t)iy * side + ix] = 1;
+                        depth = l;
+                    }
+                }
+        }
+        free(cnt_parent);
+        cnt_parent = cnt;
+    }
+    free(cnt_parent);
+    return depth;
+}
+
+/* V-list of target (tx, ty) at `level` of an adaptive tree: the existing
+ * boxes of the same level that are children of the target's parent or of
+ * one of the parent's colleagues (same-level boxes at Chebyshev distance 1
+ * from the parent) and are not adjacent to the target.  Empty when the
+ * target does not exist.  Output as orc_interaction_list (no periodicity). */
+int orc_vlist(int level, int tx, int ty, const uint8_t* exists, int* sx, int* sy, int* ox, int* oy)
+{
+    if (level < 2) return 0;
+    int side = 1 << level, pside = side / 2;
+    if (!exists[level_offset(level) + (int64_t)ty * side + tx]) return 0;
+    int ptx = tx / 2, pty = ty / 2;
+    int cnt = 0;
+    for (int qy = pty - 1; qy <= pty + 1; ++qy) {
+        for (int qx = ptx - 1; qx <= ptx + 1; ++qx) {
+            if (qx < 0 || qy < 0 || qx >= pside || qy >= pside) continue;
+            if (!exists[level_offset(level - 1) + (int64_t)qy * pside + qx]) continue; /* not a colleague */
+            for (int cy = 0; cy < 2; ++cy) {
+                for (int cx = 0; cx < 2; ++cx) {
+                    int ix = 2 * qx + cx, iy = 2 * qy + cy;
+                    if (!exists[level_offset(level) + (int64_t)iy * side + ix]) continue;
+                    int dx = ix - tx, dy = iy - ty;
+                    int adx = dx < 0 ? -dx : dx, ady = dy < 0 ? -dy : dy;
+                    if ((adx > ady ? adx : ady) <= 1) continue; /* adjacent: U-list, near field */
+                    sx[cnt] = ix;
+                    sy[cnt] = iy;
+                    ox[cnt] = dx;
+                    oy[cnt] = dy;
+                    ++cnt;
+                }
+            }
+        }
+    }
+    return cnt;
+}
+
+int64_t orc_vlist_count_level(int level, const uint8_t* exists)
+{
+    int side = 1 << level;
+    int64_t total = 0;
+    int sx[27], sy[27], ox[27], oy[27];
+    for (int ty = 0; ty < side; ++ty)
+        for (int tx = 0; tx < side; ++tx) total += orc_vlist(level, tx, ty, exists, sx, sy, ox, oy);
+    return total;
+}
+
+/* M2L of one level of an adaptive tree over the V-lists (Sec. 4.1 steps 2-3,
+ * Eq. M2Lmat): L_t = sum_{s in V(t)} a(x_t - x_s) M_s for existing t; zero
+ * for boxes that do not exist.  M, L: [4^level][p] complex, physical units. */
+void orc_m2l_adaptive(int level, int p, const uint8_t* exists, const double* M, double* L)
+{
+    int side = 1 << level;
+    double h = ldexp(1.0, -level);
+    memset(L, 0, sizeof(double) * 2 * (size_t)p * (size_t)side * (size_t)side);
+    int sx[27], sy[27], ox[27], oy[27];
+    for (int ty = 0; ty < side; ++ty)
+        for (int tx = 0; tx < side; ++tx) {
+            int cnt = orc_vlist(level, tx, ty, exists, sx, sy, ox, oy);
+            double* lt = L + 2 * (size_t)p * ((size_t)ty * side + tx);
+            for (int e = 0; e < cnt; ++e)
+                orc_m2l_pair(p, -(double)ox[e] * h, -(double)oy[e] * h,
+                             M + 2 * (size_t)p * ((size_t)sy[e] * side + sx[e]), lt);
+        }
+}
+
+/* Plain transpose of orc_m2l_adaptive by explicit transposed loops:
+ * G_s[k] = sum_{t : s in V(t)} sum_n a_nk(x_t - x_s) W_t[n]. */
+void orc_m2l_adjoint_adaptive(int level, int p, const uint8_t* exists, const double* W, double* G)
+{
+    int side = 1 << level;
+    double h = ldexp(1.0, -level);
+    memset(G, 0, sizeof(double) * 2 * (size_t)p * (size_t)side * (size_t)side);
+    int sx[27], sy[27], ox[27], oy[27];
+    double* a = (double*)malloc(sizeof(double) * 2 * (size_t)p * (size_t)p);
+    for (int ty = 0; ty < side; ++ty)
+        for (int tx = 0; tx < side; ++tx) {
+            int cnt = orc_vlist(level, tx, ty, exists, sx, sy, ox, oy);
+            const double* wt = W + 2 * (size_t)p * ((size_t)ty * side + tx);
+            for (int e = 0; e < cnt; ++e) {
+                orc_m2l_matrix(p, -(double)ox[e] * h, -(double)oy[e] * h, a);
+                double* gs = G + 2 * (size_t)p * ((size_t)sy[e] * side + sx[e]);
+                for (int k = 0; k < p; ++k) {
+                    cplx s = 0.0;
+                    for (int nn = 0; nn < p; ++nn)
+                        s += (a[2 * (nn * p + k)] + I * a[2 * (nn * p + k) + 1]) * (wt[2 * nn] + I * wt[2 * nn + 1]);
+                    gs[2 * k] += creal(s);
+                    gs[2 * k + 1] += cimag(s);
+                }
+            }
+        }
+    free(a);
+}
+
+/* M2L contributions of a few source boxes only: for every existing target t
+ * of the level within Chebyshev distance 3 of a listed source s, adds
+ * a(x_t - x_s) M_s to L_t when s is in V(t).  M: [nsrc][p] complex (the
+ * sources' MEs), L: [4^level][p] complex (accumulated). */
+void orc_m2l_adaptive_from_sources(int level, int p, const uint8_t* exists, int64_t nsrc, const int64_t* src,
+                                   const double* M, double* L)
+{
+    int side = 1 << level;
+    double h = ldexp(1.0, -level);
+    int sx[27], sy[27], ox[27], oy[27];
+    for (int64_t i = 0; i < nsrc; ++i) {
+        int bx = (int)(src[i] % side), by = (int)(src[i] / side);
+        for (int ty = by - 3; ty <= by + 3; ++ty)
+            for (int tx = bx - 3; tx <= bx + 3; ++tx) {
+                if (tx < 0 || ty < 0 || tx >= side || ty >= side) continue;
+                int cnt = orc_vlist(level, tx, ty, exists, sx, sy, ox, oy);
+                for (int e = 0; e < cnt; ++e) {
+                    if (sx[e] != bx || sy[e] != by) continue;
+                    orc_m2l_pair(p, -(double)ox[e] * h, -(double)oy[e] * h, M + 2 * (size_t)p * i,
+                                 L + 2 * (size_t)p * ((size_t)ty * side + tx));
+                }
+            }
+    }
+}
+
+/* P2M with a given box per point (frozen topology): for every point i with
+ * box[i] >= 0, M[box[i]][k] += c_i (y_i - x_box)^k.  M: [4^level][p] complex,
+ * accumulated. */
+void orc_p2m_assigned(int level, int p, int64_t n, const double* xy, const double* c, const int64_t* box, double* M)
+{
+    int side = 1 << level;
+    for (int64_t i = 0; i < n; ++i) {
+        if (box[i] < 0) continue;
+        int bx = (int)(box[i] % side), by = (int)(box[i] / side);
+        cplx d = (xy[2 * i] + I * xy[2 * i + 1]) - box_centre(level, bx, by);
+        cplx pw = c[i];
+        double* m = M + 2 * (size_t)p * (size_t)box[i];
+        for (int k = 0; k < p; ++k) {
+            m[2 * k] += creal(pw);
+            m[2 * k + 1] += cimag(pw);
+            pw *= d;
+        }
+    }
+}
+
+/* L2L from level child_level - 1 to the existing boxes of child_level:
+ * Lc[child] += l2l(Lp[parent]) (Sec. 2.1 stage 3, downward sweep). */
+void orc_l2l_level(int child_level, int p, const uint8_t* exists, const double* Lp, double* Lc)
+{
+    int side = 1 << child_level, pside = side / 2;
+    double* tmp = (double*)malloc(sizeof(double) * 2 * (size_t)p);
+    for (int iy = 0; iy < side; ++iy)
+        for (int ix = 0; ix < side; ++ix) {
+            if (!exists[level_offset(child_level) + (int64_t)iy * side + ix]) continue;
+            cplx shift = box_centre(child_level, ix, iy) - box_centre(child_level - 1, ix / 2, iy / 2);
+            orc_l2l(p, Lp + 2 * (size_t)p * ((size_t)(iy / 2) * pside + ix / 2), creal(shift), cimag(shift), tmp);
+            double* lc = Lc + 2 * (size_t)p * ((size_t)iy * side + ix);
+            for (int k = 0; k < 2 * p; ++k) lc[k] += tmp[k];
+        }
+    free(tmp);
 }
