@@ -380,6 +380,55 @@ def run_ours(args):
                                                   "measured coefficient errors in tests/test_m2l_tc_gpu.py"}
         rows["tc_vs_fp32_speedup_p16"] = {"speedup": statistics.median(step_ms) / rows["m2l_tc_bf16x3_levels_2_8"]["ms"]}
         del M24, L24, M24s, L24s
+        # adaptive tree: 2^20 Gaussian-mixture points, q = 64, levels 2..9, p = 16: V-list M2L,
+        # its adjoint, and one gradient of the far-field objective (forward + backward)
+        gcfg = workloads.CONFIGS["m2l_gmm"]
+        gx, gc = workloads.gmm_particles(gcfg["n"], workloads.rng_for("m2l_gmm"))
+        gtree = fmmgb.fmm_build_lists(gx, gcfg["max_level"], leaf_cap=gcfg["leaf_cap"])
+        glev = list(range(2, gcfg["max_level"] + 1))
+        gp = gcfg["p"]
+        gxd = torch.from_numpy(gx).to(dev)
+        gcd = torch.from_numpy(gc).to(dev)
+        gM = [torch.empty((4 ** l, gp), dtype=torch.complex64, device=dev) for l in glev]
+        for l, m in zip(glev, gM):
+            fmmgb.fmm_p2m(l, gp, gxd, gcd, m)
+        gL = [torch.zeros_like(m) for m in gM]
+        gG = [torch.zeros_like(m) for m in gM]
+        gntr = sum(gtree.translations(l) for l in glev)
+        for name, fn in (("m2l_adaptive_gmm_levels_2_9",
+                          lambda: fmmgb.fmm_m2l_levels(gtree, 2, gp, gM, gL, stream=stream)),
+                         ("m2l_adjoint_adaptive_gmm_levels_2_9",
+                          lambda: fmmgb.fmm_m2l_adjoint_levels(gtree, 2, gp, gL, gG, conj=True, stream=stream))):
+            fn()
+            torch.cuda.synchronize()
+            ms = statistics.median(_timed(torch, fn, args.steps, stream, flush))
+            rows[name] = {"translations_per_s": gntr / (ms * 1e-3), "ms": ms, "launches": 1, "translations": gntr,
+                          "gflops": gntr * metrics.m2l_flops_per_translation(gp) / (ms * 1e-3) / 1e9,
+                          "boxes": {l: int(gtree.level_info(l).nexist) for l in glev}}
+        from paper_1009_3457_gb300 import farfield
+
+        zr = np.random.default_rng(workloads.SEED_BASE + 5)
+        zz = zr.random(4096) + 1j * zr.random(4096)
+        zw = torch.from_numpy(zr.uniform(-1, 1, 4096)).to(dev)
+        gxr = gxd.clone().requires_grad_(True)
+        gleaf = farfield.leaf_boxes(gtree, gxd)
+        gzl = farfield.leaf_boxes(gtree, torch.from_numpy(np.stack([zz.real, zz.imag], 1)).to(dev))
+        zzd = torch.from_numpy(zz).to(dev)
+
+        def grad_step():
+            gxr.grad = None
+            J = farfield.far_field_objective(gtree, gp, gxr, gcd, gleaf, zzd, gzl, zw)
+            J.backward()
+
+        grad_step()
+        torch.cuda.synchronize()
+        ms = statistics.median(_timed(torch, grad_step, max(3, args.steps // 4), stream, flush))
+        rows["far_field_gradient_gmm"] = {"ms": ms, "m2l_launches": 2, "points": int(gcfg["n"]),
+                                          "note": "forward J + backward to all 2^20 source positions; "
+                                                  "M2L and adjoint in the library, P2M/L2L/L2P FP64 tensor ops"}
+        del gM, gL, gG, gxd, gcd, gxr
+        fmmgb.fmm_sync_status()
+
         # batched persistent launch: 256 independent problems (depth 4..9, p in {6, 8, 12, 16})
         bt = _batched_setup(torch, fmmgb, dev)
         bplan = bt["plan"]

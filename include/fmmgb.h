@@ -85,14 +85,26 @@ typedef struct fmm_tree fmm_tree; /* opaque, library-owned */
  * entry carries an offset code  (dy + 3) * 7 + (dx + 3)  of the box offset
  * (dx, dy) = source - target, one of 40 values.
  *
- *   xy        host, n interleaved (x, y) points in [0,1)^2; may be NULL when
- *             leaf_cap == 0 (a uniform tree does not depend on the points).
+ * Adaptive tree (leaf_cap = q > 0): the root exists; an existing box of
+ * level l < max_level holding more than q points is split, and each of its
+ * children holding at least one point exists (empty children are not
+ * created).  Its lists are V-lists: the interaction-list rule above applied
+ * to existing boxes only (the existing children of the parent's colleagues
+ * that are not adjacent to t); a box that does not exist has an empty list.
+ * Coefficient arrays stay dense, [4^level][p] per level: the translation
+ * reads only existing sources and writes only existing targets (entries of
+ * absent boxes are ignored on input and left untouched on output).
+ *
+ *   xy        host, n interleaved (x, y) points; a point goes to box
+ *             floor(x 2^l) of each level, clamped to 0 .. 2^l - 1.  May be
+ *             NULL when leaf_cap == 0 (a uniform tree does not depend on the
+ *             points).
  *   n         number of points (>= 0).
  *   max_level deepest level, 2 .. FMM_MAX_LEVEL.
  *   leaf_cap  0: uniform tree with every level down to max_level.
- *             > 0: adaptive trees are not provided by this build
- *             (FMM_EUNSUPPORTED).
- *   flags     FMM_TREE_PERIODIC or 0.
+ *             q > 0: adaptive tree with at most q points per leaf above
+ *             max_level.
+ *   flags     FMM_TREE_PERIODIC or 0 (periodic lists: uniform trees only).
  *   out       receives the handle; release it with fmm_tree_destroy().
  * Host-side and synchronous.  Lists are materialised on demand by
  * fmm_tree_level_info().  Returns FMM_EINVAL on a bad argument.
@@ -109,6 +121,8 @@ typedef struct {
     const int8_t* offcode_host;/* [nbox][27] offset code 0..48, -1 = empty slot */
     const int32_t* list_dev;   /* device copies of the two arrays above */
     const int8_t* offcode_dev;
+    int64_t nexist;            /* boxes of the level that exist (nbox for a uniform tree) */
+    const uint8_t* exists_host;/* [nbox] 1 = box exists; NULL when every box of the level exists */
 } fmm_level_info;
 
 /* Materialise (once) and return the interaction lists of one level.
@@ -118,7 +132,7 @@ typedef struct {
  * NULL. */
 int fmm_tree_level_info(const fmm_tree* tree, int32_t level, fmm_level_info* out);
 
-/* Number of interaction-list entries at a level (closed form, no allocation). */
+/* Number of interaction-list entries at a level (no allocation). */
 int64_t fmm_tree_translations(const fmm_tree* tree, int32_t level);
 
 void fmm_tree_destroy(fmm_tree* tree);
@@ -135,12 +149,12 @@ int fmm_prepare(int32_t p, int32_t prec);
  *     L~_t[n] (+)= sum_{s in IL(t)} sum_{k<p} (-1)^n C(n+k,k) D^-(n+k+1) M~_s[k],
  *     D = (x_t - x_s) / r_l  (a complex integer: minus the box offset).
  *
- *   tree   handle from fmm_build_lists (uniform tree).
+ *   tree   handle from fmm_build_lists (uniform or adaptive tree).
  *   level  0 .. max_level; levels 0 and 1 have empty lists (the output is
  *          zeroed, or left unchanged with FMM_ACCUMULATE).
  *   p      number of terms: 6, 8, 12, 16 or 24.
  *   prec   FMM_FP32, FMM_TC_BF16X3 or FMM_TC_BF16 (tensor-core forms: p = 16
- *          or 24 only).
+ *          or 24, uniform trees; FMM_EUNSUPPORTED otherwise).
  *   M      device, const, [4^level][p] complex64 scaled MEs (input).
  *   L      device, [4^level][p] complex64 scaled LEs (output; must not
  *          overlap M).

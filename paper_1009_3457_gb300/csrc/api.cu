@@ -5,6 +5,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <cmath>
 #include <map>
 #include <mutex>
 #include <vector>
@@ -265,6 +266,7 @@ using namespace fmmgb;
 struct fmm_tree {
     int32_t max_level = 0;
     int32_t periodic = 0;
+    int32_t leaf_cap = 0;  // 0: uniform tree
     struct Level {
         bool built = false;
         int64_t ntr = 0;
@@ -272,6 +274,13 @@ struct fmm_tree {
         std::vector<int8_t> code;
         int32_t* list_dev = nullptr;
         int8_t* code_dev = nullptr;
+        // adaptive trees: box existence (empty vector: every box of the level exists)
+        std::vector<uint8_t> exists;
+        int64_t nexist = 0;
+        bool dev_ready = false;
+        uint8_t* exists_dev = nullptr;
+        int32_t* tiles_dev = nullptr;  // 4 x 4-parent tiles holding at least one existing box
+        int32_t ntiles = 0;
     };
     Level levels[FMM_MAX_LEVEL + 1];
     std::mutex mu;
@@ -279,6 +288,7 @@ struct fmm_tree {
 
 int fmmgb::tree_max_level(const fmm_tree* t) { return t->max_level; }
 int fmmgb::tree_periodic(const fmm_tree* t) { return t->periodic; }
+int fmmgb::tree_adaptive(const fmm_tree* t) { return t->leaf_cap > 0; }
 
 static int64_t translations_closed_form(int level, bool periodic)
 {
@@ -286,6 +296,124 @@ static int64_t translations_closed_form(int level, bool periodic)
     const int64_t n = (int64_t)1 << level;
     if (periodic) return 27 * n * n;
     return (6 * n - 8) * (6 * n - 8) - (3 * n - 2) * (3 * n - 2);
+}
+
+static inline bool box_exists(const fmm_tree::Level& L, int64_t b) { return L.exists.empty() || L.exists[b]; }
+
+// Calls fn(source box, offset code) for every list entry of target (tx, ty):
+// the class stencil of the target, cut at the domain edge (or wrapped), and
+// for an adaptive tree restricted to existing sources (V-list).
+template <class F>
+static void for_each_entry(const fmm_tree* t, int level, int64_t tx, int64_t ty, const StencilEntry* st, F fn)
+{
+    const int64_t side = (int64_t)1 << level;
+    const fmm_tree::Level& L = t->levels[level];
+    for (int e = 0; e < 27; ++e) {
+        const int code = st[e].slot;
+        int64_t sx = tx + (code % 7 - 3), sy = ty + (code / 7 - 3);
+        if (t->periodic) {
+            sx = ((sx % side) + side) % side;
+            sy = ((sy % side) + side) % side;
+        } else if (sx < 0 || sy < 0 || sx >= side || sy >= side) {
+            continue;
+        }
+        if (!box_exists(L, sy * side + sx)) continue;
+        fn(sy * side + sx, code);
+    }
+}
+
+// Adaptive subdivision: the root exists; an existing box of level l <
+// max_level holding more than q points is split and its non-empty children
+// exist.  Then the per-level V-list counts.
+static int build_adaptive(fmm_tree* t, const double* xy, int64_t n, int q)
+{
+    std::vector<int64_t> cnt_parent;
+    for (int l = 0; l <= t->max_level; ++l) {
+        const int64_t side = (int64_t)1 << l;
+        std::vector<int64_t> cnt((size_t)(side * side), 0);
+        for (int64_t i = 0; i < n; ++i) {
+            double fx = std::floor(xy[2 * i] * (double)side), fy = std::floor(xy[2 * i + 1] * (double)side);
+            int64_t ix = fx < 0.0 || fx != fx ? 0 : (fx > (double)(side - 1) ? side - 1 : (int64_t)fx);
+            int64_t iy = fy < 0.0 || fy != fy ? 0 : (fy > (double)(side - 1) ? side - 1 : (int64_t)fy);
+            cnt[(size_t)(iy * side + ix)] += 1;
+        }
+        auto& L = t->levels[l];
+        L.exists.assign((size_t)(side * side), 0);
+        if (l == 0) {
+            L.exists[0] = 1;
+        } else {
+            const int64_t pside = side / 2;
+            const auto& P = t->levels[l - 1];
+            for (int64_t iy = 0; iy < side; ++iy)
+                for (int64_t ix = 0; ix < side; ++ix) {
+                    const int64_t pb = (iy / 2) * pside + ix / 2;
+                    if (P.exists[(size_t)pb] && cnt_parent[(size_t)pb] > q && cnt[(size_t)(iy * side + ix)] > 0)
+                        L.exists[(size_t)(iy * side + ix)] = 1;
+                }
+        }
+        L.nexist = 0;
+        for (uint8_t e : L.exists) L.nexist += e;
+        cnt_parent.swap(cnt);
+    }
+    StencilEntry st[4][27];
+    for (int c = 0; c < 4; ++c) class_stencil(c, st[c]);
+    for (int l = 0; l <= t->max_level; ++l) {
+        auto& L = t->levels[l];
+        const int64_t side = (int64_t)1 << l;
+        L.ntr = 0;
+        if (l >= 2)
+            for (int64_t ty = 0; ty < side; ++ty)
+                for (int64_t tx = 0; tx < side; ++tx) {
+                    if (!L.exists[(size_t)(ty * side + tx)]) continue;
+                    for_each_entry(t, l, tx, ty, st[(tx & 1) + 2 * (ty & 1)], [&](int64_t, int) { ++L.ntr; });
+                }
+    }
+    // Levels where every box exists take the uniform fast path.
+    for (int l = 0; l <= t->max_level; ++l) {
+        auto& L = t->levels[l];
+        if (L.nexist == ((int64_t)1 << (2 * l))) std::vector<uint8_t>().swap(L.exists);
+    }
+    return FMM_OK;
+}
+
+int fmmgb::tree_device_level(const fmm_tree* ctree, int level, const uint8_t** exists, const int32_t** tiles,
+                             int* ntiles)
+{
+    fmm_tree* t = const_cast<fmm_tree*>(ctree);
+    auto& L = t->levels[level];
+    *exists = nullptr;
+    *tiles = nullptr;
+    *ntiles = -1;  // every tile of the level
+    if (L.exists.empty()) return FMM_OK;
+    std::lock_guard<std::mutex> lk(t->mu);
+    if (!L.dev_ready) {
+        const int64_t side = (int64_t)1 << level, np = side / 2;
+        const int64_t tpr = (np + 3) / 4;
+        std::vector<int32_t> tl;
+        for (int64_t tt = 0; tt < tpr * tpr; ++tt) {
+            const int64_t x0 = (tt % tpr) * 8, y0 = (tt / tpr) * 8;
+            bool any = false;
+            for (int64_t y = y0; y < y0 + 8 && y < side && !any; ++y)
+                for (int64_t x = x0; x < x0 + 8 && x < side; ++x)
+                    if (L.exists[(size_t)(y * side + x)]) {
+                        any = true;
+                        break;
+                    }
+            if (any) tl.push_back((int32_t)tt);
+        }
+        FMM_CUDA_TRY(cudaMalloc(&L.exists_dev, L.exists.size()));
+        FMM_CUDA_TRY(cudaMemcpy(L.exists_dev, L.exists.data(), L.exists.size(), cudaMemcpyHostToDevice));
+        if (!tl.empty()) {
+            FMM_CUDA_TRY(cudaMalloc(&L.tiles_dev, tl.size() * sizeof(int32_t)));
+            FMM_CUDA_TRY(cudaMemcpy(L.tiles_dev, tl.data(), tl.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+        }
+        L.ntiles = (int32_t)tl.size();
+        L.dev_ready = true;
+    }
+    *exists = L.exists_dev;
+    *tiles = L.tiles_dev;
+    *ntiles = L.ntiles;
+    return FMM_OK;
 }
 
 extern "C" {
@@ -305,13 +433,26 @@ int fmm_build_lists(const double* xy, int64_t n, int32_t max_level, int32_t leaf
     if (max_level < 2 || max_level > FMM_MAX_LEVEL)
         return fail(FMM_EINVAL, "fmm_build_lists: max_level %d outside 2..%d", max_level, FMM_MAX_LEVEL);
     if (leaf_cap < 0) return fail(FMM_EINVAL, "fmm_build_lists: leaf_cap %d < 0", leaf_cap);
-    if (leaf_cap > 0) return fail(FMM_EUNSUPPORTED, "fmm_build_lists: adaptive trees are not provided by this build");
     if (flags & ~FMM_TREE_PERIODIC) return fail(FMM_EINVAL, "fmm_build_lists: unknown flags 0x%x", flags);
+    if (leaf_cap > 0 && (flags & FMM_TREE_PERIODIC))
+        return fail(FMM_EINVAL, "fmm_build_lists: periodic lists need a uniform tree (leaf_cap = 0)");
     fmm_tree* t = new (std::nothrow) fmm_tree();
     if (!t) return fail(FMM_ENOMEM, "fmm_build_lists: out of host memory");
     t->max_level = max_level;
     t->periodic = (flags & FMM_TREE_PERIODIC) ? 1 : 0;
-    for (int l = 0; l <= max_level; ++l) t->levels[l].ntr = translations_closed_form(l, t->periodic);
+    t->leaf_cap = leaf_cap;
+    if (leaf_cap > 0) {
+        int rc = build_adaptive(t, xy, n, leaf_cap);
+        if (rc) {
+            delete t;
+            return rc;
+        }
+    } else {
+        for (int l = 0; l <= max_level; ++l) {
+            t->levels[l].ntr = translations_closed_form(l, t->periodic);
+            t->levels[l].nexist = (int64_t)1 << (2 * l);
+        }
+    }
     *out = t;
     return FMM_OK;
 }
@@ -342,24 +483,15 @@ int fmm_tree_level_info(const fmm_tree* ctree, int32_t level, fmm_level_info* ou
             for (int c = 0; c < 4; ++c) class_stencil(c, st[c]);
             for (int64_t ty = 0; ty < side; ++ty)
                 for (int64_t tx = 0; tx < side; ++tx) {
-                    const int cls = (int)(tx & 1) + 2 * (int)(ty & 1);
                     const int64_t t = ty * side + tx;
+                    if (!box_exists(L, t)) continue;  // absent box: empty V-list
                     int slot = 0;
-                    for (int e = 0; e < 27; ++e) {
-                        const int code = st[cls][e].slot;
-                        const int dx = code % 7 - 3, dy = code / 7 - 3;
-                        int64_t sx = tx + dx, sy = ty + dy;
-                        if (tree->periodic) {
-                            sx = ((sx % side) + side) % side;
-                            sy = ((sy % side) + side) % side;
-                        } else if (sx < 0 || sy < 0 || sx >= side || sy >= side) {
-                            continue;
-                        }
-                        L.list[(size_t)t * 27 + slot] = (int32_t)(sy * side + sx);
+                    for_each_entry(tree, level, tx, ty, st[(tx & 1) + 2 * (ty & 1)], [&](int64_t s, int code) {
+                        L.list[(size_t)t * 27 + slot] = (int32_t)s;
                         L.code[(size_t)t * 27 + slot] = (int8_t)code;
                         ++slot;
                         ++cnt;
-                    }
+                    });
                 }
         }
         if (cnt != L.ntr) return fail(FMM_EDEVICE, "fmm_tree_level_info: list count %lld != %lld", (long long)cnt, (long long)L.ntr);
@@ -386,6 +518,8 @@ int fmm_tree_level_info(const fmm_tree* ctree, int32_t level, fmm_level_info* ou
     out->offcode_host = L.code.data();
     out->list_dev = L.list_dev;
     out->offcode_dev = L.code_dev;
+    out->nexist = L.nexist;
+    out->exists_host = L.exists.empty() ? nullptr : L.exists.data();
     return FMM_OK;
 }
 
@@ -395,6 +529,8 @@ void fmm_tree_destroy(fmm_tree* tree)
     for (auto& L : tree->levels) {
         if (L.list_dev) cudaFree(L.list_dev);
         if (L.code_dev) cudaFree(L.code_dev);
+        if (L.exists_dev) cudaFree(L.exists_dev);
+        if (L.tiles_dev) cudaFree(L.tiles_dev);
     }
     delete tree;
 }
@@ -458,11 +594,22 @@ static int m2l_dispatch(const char* who, const fmm_tree* tree, int32_t lmin, int
     job.periodic = tree->periodic;
     job.accumulate = acc ? 1 : 0;
     for (int l = lmax; l >= lmin && l >= 2; --l) {
+        const uint8_t* ex = nullptr;
+        const int32_t* tiles = nullptr;
+        int ntiles = -1;
+        if ((rc = tree_device_level(tree, l, &ex, &tiles, &ntiles))) return rc;
+        if (ntiles == 0) continue;  // no existing box at this level
+        if (ex && prec != FMM_FP32)
+            return fail(FMM_EUNSUPPORTED, "%s: tensor-core precisions are provided for uniform trees", who);
         M2LLevel& d = job.lv[job.nlev++];
         d.M = (const float2*)in[l - lmin];
         d.L = (float2*)out[l - lmin];
         d.level = l;
+        d.exists = ex;
+        d.tiles = tiles;
+        d.ntiles = ntiles;
     }
+    if (job.nlev == 0) return FMM_OK;
     // The adjoint is the forward stencil with the table of -a(D) (plain) or
     // -conj a(D) (FMM_CONJ): a(D)^T = -a(-D) on symmetric lists.
     if (prec != FMM_FP32) {

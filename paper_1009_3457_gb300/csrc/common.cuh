@@ -84,6 +84,9 @@ struct M2LLevel {
     int level;
     int tile_begin;           // first CTA of this level (filled by the launcher)
     unsigned char* planes;    // tensor-core path: BF16 hi/lo planes of M (library scratch)
+    const uint8_t* exists;    // adaptive level: [4^level] box existence, NULL = every box exists
+    const int32_t* tiles;     // adaptive level: the tiles to run (ntiles of them), NULL = all
+    int ntiles;
 };
 constexpr int kMaxLaunchLevels = FMM_MAX_LEVEL + 1;
 struct M2LLaunch {
@@ -96,6 +99,11 @@ struct M2LLaunch {
 // tree handle accessors (api.cu)
 int tree_max_level(const fmm_tree* t);
 int tree_periodic(const fmm_tree* t);
+int tree_adaptive(const fmm_tree* t);
+// Device data of an adaptive level: box existence [4^level] and the list of
+// 4 x 4-parent tiles that hold an existing box (uploaded on first use,
+// synchronously).  For a level where every box exists: NULL, NULL, -1.
+int tree_device_level(const fmm_tree* t, int level, const uint8_t** exists, const int32_t** tiles, int* ntiles);
 
 // launchers (m2l_fp32.cu)
 int launch_build_m2l_tables(const M2LTables& t, cudaStream_t st);

@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(kThreads, kBatchMinCtas)
                 }
                 cur_p = d.p;
             }
-            const TileGeom g = tile_geom_of(d.M, d.L, d.level, item.y);
+            const TileGeom g = tile_geom_of(d.M, d.L, nullptr, d.level, item.y);
             __syncthreads();  // operator visible; previous tile done with the halo buffer
             switch (d.p) {
                 case 6: m2l_tile<6>(smem_raw, g, d.periodic, accumulate); break;
@@ -295,6 +295,10 @@ int create_batch(const fmm_tree* const* trees, const int32_t* p, int32_t nprob, 
             delete b;
             return fail(pi == 24 ? FMM_EUNSUPPORTED : FMM_EINVAL,
                         "%s: p[%d] = %d outside the batched set 6, 8, 12, 16", who, i, pi);
+        }
+        if (tree_adaptive(t)) {
+            delete b;
+            return fail(FMM_EUNSUPPORTED, "%s: trees[%d] is adaptive; the batched path takes uniform trees", who, i);
         }
         const int lmax = tree_max_level(t), per = tree_periodic(t);
         for (int l = 2; l <= lmax; ++l, ++k) {

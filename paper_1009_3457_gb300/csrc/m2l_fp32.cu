@@ -65,7 +65,7 @@ int launch_build_m2l_tables(const M2LTables& t, cudaStream_t st)
 // about 9 per SM in two rounds of 5-6 resident CTAs, which the hardware block
 // scheduler keeps balanced.
 // ---------------------------------------------------------------------------
-template <int P>
+template <int P, bool ADAPTIVE>
 __global__ void __launch_bounds__(kThreads, M2LCfg<P>::MIN_CTAS) m2l_fp32_kernel(M2LLaunch job, const float2* __restrict__ hsel,
                                                             const float* __restrict__ ascale,
                                                             const float* __restrict__ bscale)
@@ -76,9 +76,12 @@ __global__ void __launch_bounds__(kThreads, M2LCfg<P>::MIN_CTAS) m2l_fp32_kernel
     int li = 0;
     while (li + 1 < job.nlev && tile >= job.lv[li + 1].tile_begin) ++li;
     const M2LLevel& lv = job.lv[li];
-    const TileGeom g = tile_geom_of(lv.M, lv.L, lv.level, tile - lv.tile_begin);
+    int t = tile - lv.tile_begin;
+    if constexpr (ADAPTIVE)
+        if (lv.tiles) t = lv.tiles[t];  // the level's tiles that hold an existing box
+    const TileGeom g = tile_geom_of(lv.M, lv.L, ADAPTIVE ? lv.exists : nullptr, lv.level, t);
     __syncthreads();
-    m2l_tile<P>(smem_raw, g, job.periodic, job.accumulate);
+    m2l_tile<P, ADAPTIVE>(smem_raw, g, job.periodic, job.accumulate);
 }
 
 bool m2l_fp32_supported(int p) { return p == 6 || p == 8 || p == 12 || p == 16 || p == 24; }
@@ -90,11 +93,14 @@ static int launch_p(M2LLaunch& job, const float2* h, const float* a, const float
     int total = 0;
     for (int i = 0; i < job.nlev; ++i) {
         job.lv[i].tile_begin = total;
-        total += m2l_tiles(job.lv[i].level);
+        total += job.lv[i].tiles ? job.lv[i].ntiles : m2l_tiles(job.lv[i].level);
     }
     if (total == 0) return FMM_OK;
-    FMM_CUDA_TRY(cudaFuncSetAttribute(m2l_fp32_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem));
-    m2l_fp32_kernel<P><<<total, kThreads, C::smem, st>>>(job, h, a, b);
+    bool adaptive = false;
+    for (int i = 0; i < job.nlev; ++i) adaptive |= job.lv[i].exists != nullptr;
+    auto kern = adaptive ? m2l_fp32_kernel<P, true> : m2l_fp32_kernel<P, false>;
+    FMM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem));
+    kern<<<total, kThreads, C::smem, st>>>(job, h, a, b);
     FMM_CUDA_TRY(cudaGetLastError());
     return FMM_OK;
 }

@@ -71,18 +71,21 @@ __host__ __device__ inline int m2l_tiles(int level)
     return t * t;
 }
 
-// One tile of one level: its coefficient arrays and its first parent box.
+// One tile of one level: its coefficient arrays, its first parent box and,
+// on an adaptive level, which boxes exist (NULL: all of them).
 struct TileGeom {
     const float2* M;
     float2* L;
+    const uint8_t* exists;
     int side, np, PX0, PY0;
 };
 
-__device__ __forceinline__ TileGeom tile_geom_of(const float2* M, float2* L, int level, int t)
+__device__ __forceinline__ TileGeom tile_geom_of(const float2* M, float2* L, const uint8_t* exists, int level, int t)
 {
     TileGeom g;
     g.M = M;
     g.L = L;
+    g.exists = exists;
     g.side = 1 << level;
     g.np = g.side >> 1;
     const int tpr = (g.np + kTile - 1) / kTile;
@@ -139,10 +142,11 @@ __device__ __forceinline__ void m2l_load_operator(unsigned char* raw, const floa
     }
 }
 
-// Translate and reduce one tile.  Requires the operator of order P in shared
+// Translate and reduce one tile (ADAPTIVE and g.exists set: only existing
+// sources are read and existing targets written).  Requires the operator of order P in shared
 // memory (m2l_load_operator + a barrier) and no thread still reading the halo
 // buffer of a previous tile (a barrier).  All 128 threads call it.
-template <int P>
+template <int P, bool ADAPTIVE = false>
 __device__ __forceinline__ void m2l_tile(unsigned char* raw, const TileGeom& g, int periodic, int accumulate)
 {
     using C = M2LCfg<P>;
@@ -164,6 +168,8 @@ __device__ __forceinline__ void m2l_tile(unsigned char* raw, const TileGeom& g, 
             iy = (iy + 2 * g.side) % g.side;
             in = true;
         }
+        if constexpr (ADAPTIVE)
+            if (in && g.exists) in = g.exists[(size_t)iy * g.side + ix] != 0;  // V-list: existing sources only
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
         if (in) v = __ldg(M4 + ((size_t)iy * g.side + ix) * Q + q);
         float2* dst = s.buf + ((hxb & 1) + 2 * (hyb & 1)) * C::CS + (hyb >> 1) * kHalo + (hxb >> 1);
@@ -253,7 +259,10 @@ __device__ __forceinline__ void m2l_tile(unsigned char* raw, const TileGeom& g, 
 
     // ---- store L~[n] = a_n * res (rows [HR half, HR half + HR)) ----
     const int px = g.PX0 + tpx, py = g.PY0 + tpy;
-    if (px < g.np && py < g.np) {
+    bool target = px < g.np && py < g.np;
+    if constexpr (ADAPTIVE)
+        if (target && g.exists) target = g.exists[(size_t)(2 * py + cy) * g.side + 2 * px + cx] != 0;
+    if (target) {
         const int ix = 2 * px + cx, iy = 2 * py + cy;
         const int n0 = half * HR;
         float2* dst = g.L + ((size_t)iy * g.side + ix) * P + n0;

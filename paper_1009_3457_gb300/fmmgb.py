@@ -51,6 +51,8 @@ class fmm_level_info(ctypes.Structure):
         ("offcode_host", ctypes.POINTER(ctypes.c_int8)),
         ("list_dev", ctypes.c_void_p),
         ("offcode_dev", ctypes.c_void_p),
+        ("nexist", ctypes.c_int64),
+        ("exists_host", ctypes.POINTER(ctypes.c_uint8)),
     ]
 
 
@@ -153,10 +155,12 @@ def _stream(stream):
 class Tree:
     """Owning wrapper of an ``fmm_tree*`` handle."""
 
-    def __init__(self, handle: int, max_level: int, periodic: bool):
+    def __init__(self, handle: int, max_level: int, periodic: bool, leaf_cap: int = 0):
         self.handle = handle
         self.max_level = max_level
         self.periodic = periodic
+        self.leaf_cap = leaf_cap
+        self.adaptive = leaf_cap > 0
 
     def __del__(self):
         h = getattr(self, "handle", None)
@@ -171,6 +175,15 @@ class Tree:
         info = fmm_level_info()
         _check(load().fmm_tree_level_info(self.handle, level, ctypes.byref(info)))
         return info
+
+    def exists(self, level: int):
+        """Box existence of a level, numpy bool [4^level] (all True on a uniform tree)."""
+        import numpy as np
+
+        info = self.level_info(level)
+        if not info.exists_host:
+            return np.ones(info.nbox, dtype=bool)
+        return np.ctypeslib.as_array(info.exists_host, shape=(info.nbox,)).astype(bool)
 
     def lists(self, level: int):
         """Host copies of the level's lists: (list [nbox, 27] int32, offset codes [nbox, 27] int8)."""
@@ -195,7 +208,7 @@ def fmm_build_lists(xy=None, max_level: int = 2, leaf_cap: int = 0, periodic: bo
     else:
         n, xp = 0, None
     _check(lib.fmm_build_lists(xp, n, max_level, leaf_cap, FMM_TREE_PERIODIC if periodic else 0, ctypes.byref(h)))
-    return Tree(h.value, max_level, periodic)
+    return Tree(h.value, max_level, periodic, leaf_cap)
 
 
 def fmm_prepare(p: int, prec: int = FMM_FP32):

@@ -142,3 +142,54 @@ def test_batch_rejects_bad_arguments_before_launch(fmm):
                                fmm.FMM_BATCH_AUTOTUNE, None) == fmm.FMM_EINVAL
     assert lib.fmm_batch_run(None, None) == fmm.FMM_EINVAL
     lib.fmm_batch_destroy(None, None)  # no-op
+
+
+@pytest.fixture(scope="module")
+def gmm_points():
+    import workloads
+
+    return workloads.gmm_particles(5000, np.random.default_rng(31), ncomp=6)[0]
+
+
+def test_adaptive_tree_matches_oracle(fmm, orc, gmm_points):
+    """Library adaptive tree (leaf_cap > 0): box existence, V-lists and their
+    offset codes equal the oracle's reading R7, level by level."""
+    xy = gmm_points
+    q, L = 16, 8
+    tree = fmm.fmm_build_lists(xy, L, leaf_cap=q)
+    otree = orc.adaptive_tree(xy, q, L)
+    assert tree.adaptive
+    for level in range(L + 1):
+        assert (tree.exists(level) == otree.level(level)).all(), level
+    for level in range(2, L + 1):
+        n = 1 << level
+        assert tree.translations(level) == orc.vlist_count_level(otree, level)
+        lst, code = tree.lists(level)
+        for t in np.nonzero(otree.level(level) | (lst >= 0).any(axis=1))[0]:
+            tx, ty = int(t % n), int(t // n)
+            want = sorted((sy * n + sx, (oy + 3) * 7 + (ox + 3)) for sx, sy, ox, oy in orc.vlist(otree, level, tx, ty))
+            got = sorted((int(s), int(c)) for s, c in zip(lst[t], code[t]) if s >= 0)
+            assert got == want, (level, t)
+
+
+def test_adaptive_tree_arguments(fmm, gmm_points):
+    import ctypes
+
+    lib = fmm.load()
+
+    h = ctypes.c_void_p()
+    assert lib.fmm_build_lists(None, 10, 5, 8, 0, ctypes.byref(h)) == fmm.FMM_EINVAL  # xy needed
+    xy = np.ascontiguousarray(gmm_points)
+    assert lib.fmm_build_lists(xy.ctypes.data, len(xy), 5, 8, fmm.FMM_TREE_PERIODIC,
+                               ctypes.byref(h)) == fmm.FMM_EINVAL  # periodic + adaptive
+    # a tree with no point splitting below the root: empty lists everywhere
+    t = fmm.fmm_build_lists(xy[:5], 6, leaf_cap=8)
+    assert all(t.translations(l) == 0 for l in range(7))
+    assert t.level_info(3).nexist == 0
+    # batched path takes uniform trees only
+    tb = fmm.fmm_build_lists(xy, 5, leaf_cap=8)
+    vp, i32 = ctypes.c_void_p, ctypes.c_int32
+    ptrs = (vp * 4)(*[(1 << 20) * (k + 1) for k in range(4)])
+    outs = (vp * 4)(*[(1 << 28) * (k + 1) for k in range(4)])
+    assert lib.fmm_batch_create((vp * 1)(tb.handle), (i32 * 1)(8), 1, ptrs, outs, 0, 0, None,
+                                ctypes.byref(h)) == fmm.FMM_EUNSUPPORTED
