@@ -217,3 +217,14 @@ def test_fd_gradient_single_source_closed_form(orc):
     assert np.linalg.norm(fd - want) <= 1e-6 * np.linalg.norm(want), (fd, want)
     J = orc.far_field_objective(tree, 16, xy, c, leaf, z, zl, om)
     assert abs(J - om[0] * (c[0] / (z[0] - y)).real) <= 1e-8
+
+
+def test_fd_gradient_step_converges(orc):
+    """Central differences at h and h/10 agree to O(h^2): the step used against the
+    GPU gradient (1e-6) is inside the converged range even on the finest boxes."""
+    xy, c, tree, leaf, z, zl, om = _objective_case(orc, n=6000, seed=3, q=8, max_level=9)
+    assert tree.depth >= 8
+    idx = [int(i) for i in np.nonzero(leaf[0] >= 8)[0][:4]]
+    f6 = orc.far_field_fd_gradient(tree, 16, xy, c, leaf, z, zl, om, idx, 1e-6)
+    f7 = orc.far_field_fd_gradient(tree, 16, xy, c, leaf, z, zl, om, idx, 1e-7)
+    assert np.linalg.norm(f6 - f7) <= 1e-6 * np.linalg.norm(f6)
