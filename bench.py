@@ -171,9 +171,11 @@ def _traffic(kernel: str):
     try:
         with open(os.path.join(ROOT, "profiles", "roofline_traffic.json")) as f:
             rec = json.load(f)[kernel]
-        with open(os.path.join(ROOT, rec["source"]), "rb") as f:
-            sha = hashlib.sha256(f.read()).hexdigest()
-        return rec["dram_bytes_per_launch"] if sha.startswith(rec["source_sha256_prefix"]) else None
+        h = hashlib.sha256()
+        for src in rec["sources"]:
+            with open(os.path.join(ROOT, src), "rb") as f:
+                h.update(f.read())
+        return rec["dram_bytes_per_launch"] if h.hexdigest().startswith(rec["sources_sha256_prefix"]) else None
     except Exception:
         return None
 
@@ -190,13 +192,13 @@ def _timed(torch, fn, steps, stream, flush):
     return [a.elapsed_time(b) for a, b in evs]
 
 
-def _batched_setup(torch, fmmgb, dev, autotune=True):
-    """The 256-problem batch: particles -> device P2M/M2M per problem (untimed),
-    one plan over every problem's levels 2..depth."""
+def _batched_setup(torch, fmmgb, dev, autotune=True, nprob=None):
+    """The 256-problem batch (or its first nprob problems): particles -> device
+    P2M/M2M per problem (untimed), one plan over every problem's levels 2..depth."""
     cfg = workloads.CONFIGS["m2l_batched"]
     rng = workloads.rng_for("m2l_batched")
     shapes = workloads.batched_problems(cfg["nprob"], rng, depths=cfg["depths"], orders=cfg["orders"],
-                                        n_range=cfg["n_range"])
+                                        n_range=cfg["n_range"])[:nprob]
     trees, ps, Ms, Ls = [], [], [], []
     flops = 0
     for sh in shapes:
@@ -263,7 +265,7 @@ def run_ours(args):
     fmmgb.fmm_sync_status()
     if args.mode == "kernels" and args.prec == "batched":
         # profiling case: the 256-problem batched launch only
-        bt = _batched_setup(torch, fmmgb, dev)
+        bt = _batched_setup(torch, fmmgb, dev, autotune=False, nprob=args.nprob)
         for _ in range(args.steps):
             bt["plan"].run(stream)
         torch.cuda.synchronize()
@@ -526,6 +528,8 @@ def main():
                     help="kernels: only the timed step's launches (for ncu captures)")
     ap.add_argument("--prec", default="fp32", choices=["fp32", "tc3", "tc1", "batched"],
                     help="precision of the launches in --mode kernels (batched: the 256-problem batch)")
+    ap.add_argument("--nprob", type=int, default=None,
+                    help="--mode kernels --prec batched: the first N problems of the batch (profiling case)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
