@@ -251,11 +251,11 @@ def l2l(p: int, lp: np.ndarray, shift: complex) -> np.ndarray:
 
 
 # ---------------------------------------------------------------------------
-# adaptive quadtree, V-lists and the far field on it (reading R7, R11)
+# adaptive quadtree, V-lists and the far field on it (readings R12, R13)
 # ---------------------------------------------------------------------------
 
 class AdaptiveTree:
-    """Box existence over levels 0..max_level of an adaptive quadtree (reading R7)."""
+    """Box existence over levels 0..max_level of an adaptive quadtree (reading R12)."""
 
     def __init__(self, exists: np.ndarray, max_level: int, depth: int, q: int):
         self.exists = exists  # uint8, level-major: level l at [(4^l - 1)/3, (4^(l+1) - 1)/3)
@@ -364,7 +364,7 @@ def _l2p_at_leaves(p: int, L: dict, z, z_lev, z_box) -> np.ndarray:
 
 
 def far_field_objective(tree: AdaptiveTree, p: int, xy, c, leaf, z, z_leaf, omega) -> float:
-    """J = sum_j omega_j Re phi_far(z_j) (reading R11): the MEs of every level from
+    """J = sum_j omega_j Re phi_far(z_j) (reading R13): the MEs of every level from
     the points assigned to the frozen leaves `leaf` = (levels, boxes), M2L over the
     V-lists of levels 2..depth, L2L down, L2P at each evaluation point's leaf."""
     lev, box = leaf

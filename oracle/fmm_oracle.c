@@ -21,7 +21,9 @@
  *   - FGT Hermite / Taylor / Hermite-to-Taylor series: Eqs. (A_alpha),
  *     (B_beta), (C_beta), (hermite), (taylor), Sec. 2.2.
  *
- * Readings where the paper is silent or garbled (each is listed in the design doc):
+ * Readings where the paper is silent or garbled (numbered as in the design
+ * notes; R6, R10 and R11 concern the CUDA side, the error metric and the op
+ * count, not this file):
  *   R1  the kernel is the 2-D Cauchy kernel 1/(z - y): Eq. (M2Lmat) is exactly
  *       its M2L with ME  phi(z) = sum_k m_k (z - x_s)^-(k+1),
  *       m_k = sum_i c_i (y_i - x_s)^k, and LE  phi(z) = sum_n l_n (z - x_t)^n.
@@ -37,16 +39,17 @@
  *       periodic image.
  *   R5  points go to box floor(x * 2^l), clamped to 2^l - 1; box centres are
  *       geometric centres.
- *   R6  FGT: B_beta carries no (-1)^|beta| and the sum runs j = 1..N_B;
- *       C_beta carries the factor (-1)^|beta| / beta! that Eq. (C_beta) omits;
- *       delta = 2 sigma^2; tensor truncation alpha_i, beta_i < p.
- *   R7  adaptive tree (the paper describes only uniform subdivision): the
+ *   R7  FGT: B_beta carries no (-1)^|beta| and the sum runs j = 1..N_B.
+ *   R8  FGT: C_beta carries the factor (-1)^|beta| / beta! that Eq. (C_beta)
+ *       omits.
+ *   R9  FGT: delta = 2 sigma^2; tensor truncation alpha_i, beta_i < p.
+ *   R12 adaptive tree (the paper describes only uniform subdivision): the
  *       root exists; an existing box holding more than q points is split
  *       while its level is below max_level; children holding no point are
  *       not created.  M2L on it runs over V-lists: the existing same-level
  *       children of the parent's colleagues (and of the parent) that are not
  *       adjacent to the target.  U/W/X lists are not part of the path.
- *   R11 far-field objective for gradients: J = sum_j w_j Re phi_far(z_j) at
+ *   R13 far-field objective for gradients: J = sum_j w_j Re phi_far(z_j) at
  *       fixed evaluation points, phi_far(z) the L2P of the LE of z's leaf
  *       after M2L over V-lists at every level and L2L down; the topology
  *       (each point's leaf) is frozen when points move.
@@ -499,7 +502,7 @@ void orc_fgt_hermite_eval(int p, const double* A, double sbx, double sby, double
     free(h2);
 }
 
-/* Taylor coefficients about t_C (Eq. B_beta, reading R6):
+/* Taylor coefficients about t_C (Eq. B_beta, reading R7):
  * B[b1][b2] = sum_j q_j h_b1(s1) h_b2(s2) / (b1! b2!),  s = (x_j - t_C)/(sqrt(2) sigma). */
 void orc_fgt_p2t(int64_t n, const double* x, const double* q, double tcx, double tcy,
                  double sigma, int p, double* B)
@@ -533,7 +536,7 @@ void orc_fgt_taylor_eval(int p, const double* B, double tcx, double tcy, double 
     }
 }
 
-/* One Hermite-to-Taylor translation (Eq. C_beta with reading R6):
+/* One Hermite-to-Taylor translation (Eq. C_beta with reading R8):
  * C[b1][b2] += ((-1)^(b1+b2) / (b1! b2!)) sum_{a1,a2} A[a1][a2] h_{a1+b1}(u1) h_{a2+b2}(u2),
  * u = (t_C - s_B)/(sqrt(2) sigma). */
 void orc_fgt_h2t_pair(int p, const double* A, double u1, double u2, double* C)
@@ -631,7 +634,7 @@ void orc_fgt_p2h_grid(int g, int p, double sigma, int64_t n, const double* x, co
 }
 
 /* ------------------------------------------------------------------ */
-/* adaptive quadtree, V-lists and the far field on it (reading R7)      */
+/* adaptive quadtree, V-lists and the far field on it (reading R12)     */
 /* ------------------------------------------------------------------ */
 
 /* Boxes of all levels 0..L are numbered level by level: box b of level l is
@@ -640,7 +643,7 @@ static int64_t level_offset(int l) { return (((int64_t)1 << (2 * l)) - 1) / 3; }
 
 int64_t orc_level_offset(int l) { return level_offset(l); }
 
-/* Adaptive tree over levels 0..max_level (reading R7): the root exists; an
+/* Adaptive tree over levels 0..max_level (reading R12): the root exists; an
  * existing box of level l < max_level holding more than q points is split,
  * and each of its four children that holds at least one point exists.
  * exists[] has level_offset(max_level + 1) entries.  Returns the deepest

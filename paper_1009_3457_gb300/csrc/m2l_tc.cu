@@ -28,10 +28,13 @@
 // A_lo B_hi recover ~16 bits per product, accumulated in FP32.
 //
 // Schedule.  A persistent CTA per SM takes tiles round-robin and runs four
-// roles concurrently: a producer thread streams the 32 operator blocks of
-// every tile through a ring of shared-memory stages; an MMA thread issues the
-// tcgen05 products into one of two TMEM accumulators; two staging warps fill
-// the next tile's halo; four epilogue warps drain the other accumulator.
+// roles concurrently: three producer warps (warps 0-2; one bulk copy in
+// flight per warp) stream the 32 operator blocks of every tile through a ring
+// of shared-memory stages; an MMA thread (warp 4) issues the tcgen05 products
+// into one of two TMEM accumulators; three staging warps (5-7) load the next
+// tile's halo (TMA tensor-map copies of the BF16 hi/lo planes that a pre-pass
+// writes, or bulk copies where a level is too small for the tensor map); four
+// epilogue warps (8-11) drain the other accumulator.
 // Hand-overs use mbarriers; every wait is bounded: on timeout the CTA records
 // FMM_ETIMEOUT in the device error word, waits (bounded) for its own copies,
 // frees its TMEM and returns.

@@ -153,7 +153,7 @@ def gmm_points():
 
 def test_adaptive_tree_matches_oracle(fmm, orc, gmm_points):
     """Library adaptive tree (leaf_cap > 0): box existence, V-lists and their
-    offset codes equal the oracle's reading R7, level by level."""
+    offset codes equal the oracle's reading R12, level by level."""
     xy = gmm_points
     q, L = 16, 8
     tree = fmm.fmm_build_lists(xy, L, leaf_cap=q)

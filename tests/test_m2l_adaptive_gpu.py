@@ -1,5 +1,5 @@
-"""GPU parity of the M2L path on adaptive trees (V-lists, reading R7) and of its
-gradients (the autograd binding and the far-field objective of reading R11)
+"""GPU parity of the M2L path on adaptive trees (V-lists, reading R12) and of its
+gradients (the autograd binding and the far-field objective of reading R13)
 against the FP64 oracle, through the C ABI.
 
 Bars: FP32 forward and adjoint, relative L2 of the scaled coefficients of the

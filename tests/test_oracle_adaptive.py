@@ -1,6 +1,6 @@
-"""Pins of the FP64 oracle's adaptive-tree path (reading R7: split boxes holding
+"""Pins of the FP64 oracle's adaptive-tree path (reading R12: split boxes holding
 more than q points, drop empty children; V-lists; far-field objective of
-reading R11) against things other than the oracle itself: an independent
+reading R13) against things other than the oracle itself: an independent
 recursive tree builder, brute-force list scans, the uniform special case, the
 direct sum within the truncation error, and closed-form derivatives."""
 import numpy as np
