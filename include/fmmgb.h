@@ -178,7 +178,8 @@ int fmm_m2l_levels(const fmm_tree* tree, int32_t lmin, int32_t lmax, int32_t p, 
  * conjugate form is the gradient of a real objective with respect to the
  * multipole coefficients (PyTorch's convention for complex tensors).
  * Arguments as fmm_m2l with W (input, [nbox][p] complex64) in place of M and
- * G (output) in place of L.  prec must be FMM_FP32.
+ * G (output) in place of L; prec as fmm_m2l (the tensor-core forms run the
+ * forward kernel with the operator image of -T or -conj T).
  * ------------------------------------------------------------------------- */
 int fmm_m2l_adjoint(const fmm_tree* tree, int32_t level, int32_t p, int32_t prec,
                     const void* W, void* G, int32_t flags, void* stream);

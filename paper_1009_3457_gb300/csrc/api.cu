@@ -231,7 +231,7 @@ int get_m2l_tables(int p, const M2LTables** out)
     return FMM_OK;
 }
 
-int get_tc_image(int p, const void** out)
+int get_tc_image(int p, int variant, const void** out)
 {
     if (!m2l_tc_supported(p)) return fail(FMM_EUNSUPPORTED, "tensor-core M2L is provided for p = 16 and 24, not %d", p);
     const M2LTables* tc = nullptr;
@@ -239,20 +239,20 @@ int get_tc_image(int p, const void** out)
     if (rc) return rc;
     M2LTables* t = const_cast<M2LTables*>(tc);
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!t->tc_ready) {
+    if (!t->tc_ready[variant]) {
         const size_t bytes = m2l_tc_image_bytes(p);
-        cudaError_t e = cudaMalloc(&t->tc_w, bytes);
+        cudaError_t e = cudaMalloc(&t->tc_w[variant], bytes);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(tensor-core operator image)");
         cudaStream_t st;
         FMM_CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
-        rc = launch_build_tc_image(p, t->s, t->tc_w, st);
+        rc = launch_build_tc_image(p, t->s, variant, t->tc_w[variant], st);
         cudaError_t es = cudaStreamSynchronize(st);
         cudaStreamDestroy(st);
         if (rc) return rc;
         if (es != cudaSuccess) return cuda_fail(es, "building the tensor-core operator image");
-        t->tc_ready = 1;
+        t->tc_ready[variant] = 1;
     }
-    *out = t->tc_w;
+    *out = t->tc_w[variant];
     return FMM_OK;
 }
 
@@ -548,7 +548,7 @@ int fmm_prepare(int32_t p, int32_t prec)
     if (rc) return rc;
     if (prec != FMM_FP32) {
         const void* img = nullptr;
-        if ((rc = get_tc_image(p, &img))) return rc;
+        if ((rc = get_tc_image(p, 0, &img))) return rc;
     }
     int* ctr = nullptr;
     if ((rc = tile_counter(&ctr, nullptr))) return rc;
@@ -584,9 +584,8 @@ static int m2l_dispatch(const char* who, const fmm_tree* tree, int32_t lmin, int
     for (int l = lmin; l <= lmax && l < 2; ++l)
         if (!acc) FMM_CUDA_TRY(cudaMemsetAsync(out[l - lmin], 0, ((size_t)1 << (2 * l)) * (size_t)p * 8, st));
     if (lmax < 2) return FMM_OK;
-    if (prec != FMM_FP32 && (adjoint || !m2l_tc_supported(p)))
-        return fail(FMM_EUNSUPPORTED, "%s: tensor-core precision %d is provided for the forward M2L at p = 16, 24",
-                    who, prec);
+    if (prec != FMM_FP32 && !m2l_tc_supported(p))
+        return fail(FMM_EUNSUPPORTED, "%s: tensor-core precision %d is provided at p = 16, 24", who, prec);
     const M2LTables* t = nullptr;
     int rc = get_m2l_tables(p, &t);
     if (rc) return rc;
@@ -613,8 +612,9 @@ static int m2l_dispatch(const char* who, const fmm_tree* tree, int32_t lmin, int
     // The adjoint is the forward stencil with the table of -a(D) (plain) or
     // -conj a(D) (FMM_CONJ): a(D)^T = -a(-D) on symmetric lists.
     if (prec != FMM_FP32) {
+        const int variant = !adjoint ? 0 : ((flags & FMM_CONJ) ? 2 : 1);
         const void* img = nullptr;
-        if ((rc = get_tc_image(p, &img))) return rc;
+        if ((rc = get_tc_image(p, variant, &img))) return rc;
         return launch_m2l_tc(job, p, img, prec == FMM_TC_BF16X3, st);
     }
     const float2* h = !adjoint ? t->h_fwd : ((flags & FMM_CONJ) ? t->h_adjc : t->h_adj);
@@ -661,7 +661,6 @@ int fmm_m2l_adjoint(const fmm_tree* tree, int32_t level, int32_t p, int32_t prec
     clear_error();
     int rc = m2l_common("fmm_m2l_adjoint", tree, level, p, prec, W, G, flags, FMM_ACCUMULATE | FMM_CONJ);
     if (rc) return rc;
-    if (prec != FMM_FP32) return fail(FMM_EUNSUPPORTED, "fmm_m2l_adjoint: only FMM_FP32 is provided");
     const void* in[1] = {W};
     void* out[1] = {G};
     return m2l_dispatch("fmm_m2l_adjoint", tree, level, level, p, prec, in, out, flags, true, stream);
@@ -674,7 +673,6 @@ int fmm_m2l_adjoint_levels(const fmm_tree* tree, int32_t lmin, int32_t lmax, int
     int rc = levels_common("fmm_m2l_adjoint_levels", tree, lmin, lmax, p, prec, W, G, flags,
                            FMM_ACCUMULATE | FMM_CONJ);
     if (rc) return rc;
-    if (prec != FMM_FP32) return fail(FMM_EUNSUPPORTED, "fmm_m2l_adjoint_levels: only FMM_FP32 is provided");
     return m2l_dispatch("fmm_m2l_adjoint_levels", tree, lmin, lmax, p, prec, W, G, flags, true, stream);
 }
 

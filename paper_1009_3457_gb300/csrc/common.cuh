@@ -70,9 +70,10 @@ struct M2LTables {
     float2* h_adjc = nullptr;  // [49][2p-1]: conjugate adjoint (= -conj h_fwd)
     float* a = nullptr;        // [p] post-scale
     float* b = nullptr;        // [p] pre-scale
-    // dense scaled operators for the tensor-core path, built on demand
-    void* tc_w = nullptr;
-    int tc_ready = 0;
+    // dense scaled operators for the tensor-core path, built on demand:
+    // [0] forward, [1] plain adjoint (-T), [2] conjugate adjoint (-conj T)
+    void* tc_w[3] = {nullptr, nullptr, nullptr};
+    int tc_ready[3] = {0, 0, 0};
 };
 int get_m2l_tables(int p, const M2LTables** out);
 double m2l_balance(int p);
@@ -113,9 +114,9 @@ int launch_m2l_fp32(M2LLaunch& job, int p, const float2* hsel, const float* a, c
 // launchers (m2l_tc.cu)
 bool m2l_tc_supported(int p);
 size_t m2l_tc_image_bytes(int p);
-int launch_build_tc_image(int p, double s, void* img, cudaStream_t st);
+int launch_build_tc_image(int p, double s, int variant, void* img, cudaStream_t st);
 int launch_m2l_tc(M2LLaunch& job, int p, const void* img, bool split, cudaStream_t st);
-int get_tc_image(int p, const void** out);
+int get_tc_image(int p, int variant, const void** out);
 int tc_plane_workspace(size_t bytes, unsigned char** out);
 
 // launchers (fgt_h2t.cu)

@@ -3,8 +3,12 @@
 // plus the FP64 operator-table builder.
 //
 // The work unit (a 4 x 4 tile of parent boxes, the Hankel factorisation of the
-// operator and the class-split shared-memory halo) is in m2l_fp32_tile.cuh.
+// operator and the class-split shared-memory halo) and the stencil kernel are
+// in m2l_fp32_tile.cuh; this file holds the operator-table builder and the
+// launcher.
 #include "m2l_fp32_tile.cuh"
+
+#include <atomic>
 
 namespace fmmgb {
 
@@ -59,31 +63,6 @@ int launch_build_m2l_tables(const M2LTables& t, cudaStream_t st)
     return FMM_OK;
 }
 
-// ---------------------------------------------------------------------------
-// stencil kernel: one CTA per 4 x 4-parent tile, every requested level in one
-// launch (heaviest level first); the ~1.4k CTAs of the level 2..8 pass run
-// about 9 per SM in two rounds of 5-6 resident CTAs, which the hardware block
-// scheduler keeps balanced.
-// ---------------------------------------------------------------------------
-template <int P, bool ADAPTIVE>
-__global__ void __launch_bounds__(kThreads, M2LCfg<P>::MIN_CTAS) m2l_fp32_kernel(M2LLaunch job, const float2* __restrict__ hsel,
-                                                            const float* __restrict__ ascale,
-                                                            const float* __restrict__ bscale)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    m2l_load_operator<P>(smem_raw, hsel, ascale, bscale);
-    const int tile = blockIdx.x;
-    int li = 0;
-    while (li + 1 < job.nlev && tile >= job.lv[li + 1].tile_begin) ++li;
-    const M2LLevel& lv = job.lv[li];
-    int t = tile - lv.tile_begin;
-    if constexpr (ADAPTIVE)
-        if (lv.tiles) t = lv.tiles[t];  // the level's tiles that hold an existing box
-    const TileGeom g = tile_geom_of(lv.M, lv.L, ADAPTIVE ? lv.exists : nullptr, lv.level, t);
-    __syncthreads();
-    m2l_tile<P, ADAPTIVE>(smem_raw, g, job.periodic, job.accumulate);
-}
-
 bool m2l_fp32_supported(int p) { return p == 6 || p == 8 || p == 12 || p == 16 || p == 24; }
 
 template <int P>
@@ -99,7 +78,16 @@ static int launch_p(M2LLaunch& job, const float2* h, const float* a, const float
     bool adaptive = false;
     for (int i = 0; i < job.nlev; ++i) adaptive |= job.lv[i].exists != nullptr;
     auto kern = adaptive ? m2l_fp32_kernel<P, true> : m2l_fp32_kernel<P, false>;
-    FMM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem));
+    // The shared-memory opt-in is set once per device and instantiation, so
+    // that launches inside a stream capture make no other runtime call.
+    static std::atomic<unsigned> opted[2];
+    int dev = 0;
+    FMM_CUDA_TRY(cudaGetDevice(&dev));
+    const unsigned bit = 1u << (dev & 31);
+    if (!(opted[adaptive].load() & bit)) {
+        FMM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem));
+        opted[adaptive].fetch_or(bit);
+    }
     kern<<<total, kThreads, C::smem, st>>>(job, h, a, b);
     FMM_CUDA_TRY(cudaGetLastError());
     return FMM_OK;

@@ -297,4 +297,29 @@ __device__ __forceinline__ void m2l_tile(unsigned char* raw, const TileGeom& g, 
     }
 }
 
+// ---------------------------------------------------------------------------
+// stencil kernel: one CTA per 4 x 4-parent tile, every requested level in one
+// launch (heaviest level first); the ~1.4k CTAs of the level 2..8 pass run
+// about 9 per SM in two rounds of 5-6 resident CTAs, which the hardware block
+// scheduler keeps balanced.
+// ---------------------------------------------------------------------------
+template <int P, bool ADAPTIVE>
+__global__ void __launch_bounds__(kThreads, M2LCfg<P>::MIN_CTAS) m2l_fp32_kernel(M2LLaunch job, const float2* __restrict__ hsel,
+                                                            const float* __restrict__ ascale,
+                                                            const float* __restrict__ bscale)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    m2l_load_operator<P>(smem_raw, hsel, ascale, bscale);
+    const int tile = blockIdx.x;
+    int li = 0;
+    while (li + 1 < job.nlev && tile >= job.lv[li + 1].tile_begin) ++li;
+    const M2LLevel& lv = job.lv[li];
+    int t = tile - lv.tile_begin;
+    if constexpr (ADAPTIVE)
+        if (lv.tiles) t = lv.tiles[t];  // the level's tiles that hold an existing box
+    const TileGeom g = tile_geom_of(lv.M, lv.L, ADAPTIVE ? lv.exists : nullptr, lv.level, t);
+    __syncthreads();
+    m2l_tile<P, ADAPTIVE>(smem_raw, g, job.periodic, job.accumulate);
+}
+
 }  // namespace fmmgb

@@ -97,7 +97,7 @@ __host__ __device__ inline void tc_block(int b, int& ex, int& ey, int& cs)
 // built in FP64 on the GPU from a(D) = (-1)^n C(n+k,k) D^-(n+k+1).
 // ---------------------------------------------------------------------------
 template <int P>
-__global__ void build_tc_image_kernel(double s, unsigned char* __restrict__ img)
+__global__ void build_tc_image_kernel(double s, int variant, unsigned char* __restrict__ img)
 {
     using C = TcCfg<P>;
     const int rows = C::MT * 128;
@@ -131,7 +131,9 @@ __global__ void build_tc_image_kernel(double s, unsigned char* __restrict__ img)
             for (int i = 1; i <= n; ++i) fa *= (double)i * s;
             for (int i = 1; i <= k; ++i) fb *= (double)i * s;
             const double scale = ((n & 1) ? -1.0 : 1.0) / (fa * fb);
-            const double tr = hr * scale, ti = hi * scale;
+            // variant 0: T (forward); 1: -T (plain adjoint); 2: -conj T (conjugate adjoint),
+            // by a(D)^T = -a(-D) on the symmetric lists
+            const double tr = (variant ? -hr : hr) * scale, ti = (variant == 1 ? -hi : hi) * scale;
             // out_re = Re T in_re - Im T in_im;  out_im = Im T in_re + Re T in_im
             w = ro == 0 ? (ri == 0 ? tr : -ti) : (ri == 0 ? ti : tr);
         }
@@ -612,22 +614,22 @@ size_t m2l_tc_image_bytes(int p)
 }
 
 template <int P>
-static int build_image_p(double s, unsigned char* img, cudaStream_t st)
+static int build_image_p(double s, int variant, unsigned char* img, cudaStream_t st)
 {
     using C = TcCfg<P>;
     const int64_t total = (int64_t)kTcBlocks * C::MT * 128 * C::K2;
-    build_tc_image_kernel<P><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(s, img);
+    build_tc_image_kernel<P><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(s, variant, img);
     FMM_CUDA_TRY(cudaGetLastError());
     const size_t one = (size_t)kTcBlocks * 2 * C::APART;
     for (int r = 1; r < kTcReplicas; ++r) FMM_CUDA_TRY(cudaMemcpyAsync(img + r * one, img, one, cudaMemcpyDeviceToDevice, st));
     return FMM_OK;
 }
 
-int launch_build_tc_image(int p, double s, void* img, cudaStream_t st)
+int launch_build_tc_image(int p, double s, int variant, void* img, cudaStream_t st)
 {
     switch (p) {
-        case 16: return build_image_p<16>(s, (unsigned char*)img, st);
-        case 24: return build_image_p<24>(s, (unsigned char*)img, st);
+        case 16: return build_image_p<16>(s, variant, (unsigned char*)img, st);
+        case 24: return build_image_p<24>(s, variant, (unsigned char*)img, st);
         default: return fail(FMM_EINVAL, "M2L TC: unsupported p = %d", p);
     }
 }

@@ -155,3 +155,24 @@ def test_tc_full_size_workload(fmm, orc):
     targets = np.unique(np.concatenate([[0, n - 1, n * (n - 1), n * n - 1], rng.integers(0, n * n, 2000)]))
     ref = orc.scale_le(orc.m2l_uniform_targets(L, p, Ms[L], targets), L)
     assert _rel(_host(Ld[-1])[targets], ref) <= 1e-4
+
+
+@pytest.mark.parametrize("conj", [False, True])
+@pytest.mark.parametrize("p", [16, 24])
+def test_tc_bf16x3_adjoint_levels(fmm, orc, p, conj):
+    """Tensor-core adjoint (the forward kernel with the image of -T or -conj T) against the
+    oracle's explicit transpose, scaled units G~ = R_M A^T R_L W~, levels 2..5 in one launch."""
+    rng = np.random.default_rng(40 + p + int(conj))
+    levels = list(range(2, 6))
+    tree = fmm.fmm_build_lists(None, 5)
+    W = {l: rng.standard_normal((4 ** l, p)) + 1j * rng.standard_normal((4 ** l, p)) for l in levels}
+    Wd = [_dev(W[l]) for l in levels]
+    Gd = [w.new_empty(w.shape) for w in Wd]
+    fmm.fmm_m2l_adjoint_levels(tree, 2, p, Wd, Gd, prec=fmm.FMM_TC_BF16X3, conj=conj)
+    fmm.fmm_sync_status()
+    for l, g in zip(levels, Gd):
+        Win = np.conj(W[l]) if conj else W[l]
+        G = orc.unscale_me(orc.m2l_adjoint_uniform(l, p, orc.scale_le(Win, l)), l)
+        if conj:
+            G = np.conj(G)
+        assert _rel(_host(g), G) <= 1e-4, (l, _rel(_host(g), G))
