@@ -390,9 +390,9 @@ def run_ours(args):
     # --- the other rows of the hot path, same device-resident protocol ---
     rows = {}
     if rank == 0 and not args.no_rows:
-        def per_level():
+        def per_level(st=stream):
             for l in sorted(LEVELS, reverse=True):
-                fmmgb.fmm_m2l(tree, l, P, M[l], Lx[l], stream=stream)
+                fmmgb.fmm_m2l(tree, l, P, M[l], Lx[l], stream=st)
 
         def adjoint():
             fmmgb.fmm_m2l_adjoint_levels(tree, LEVELS[0], P, Ls, Gs, conj=True, stream=stream)
@@ -411,7 +411,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(graph):
-            per_level()
+            per_level(st=None)  # the capture stream (torch's current stream inside the context)
         torch.cuda.synchronize()
 
         for name, fn, launches in (("m2l_fp32_one_launch_per_level", per_level, len(LEVELS)),
