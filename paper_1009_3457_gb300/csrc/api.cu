@@ -123,6 +123,17 @@ int device_sm_count(int* out)
     return FMM_OK;
 }
 
+int smem_opt_in(const void* func, int bytes, unsigned* done)
+{
+    int dev = 0;
+    FMM_CUDA_TRY(cudaGetDevice(&dev));
+    const unsigned bit = 1u << (dev & 31);
+    if (__atomic_load_n(done, __ATOMIC_ACQUIRE) & bit) return FMM_OK;
+    FMM_CUDA_TRY(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    __atomic_fetch_or(done, bit, __ATOMIC_RELEASE);
+    return FMM_OK;
+}
+
 int tile_counter(int** out, cudaStream_t st)
 {
     int* slot = nullptr;

@@ -31,6 +31,12 @@ int device_error_word(int** out);
 // Number of SMs of the current device (cached).
 int device_sm_count(int* out);
 
+// Opt `func` into `bytes` of dynamic shared memory on the current device,
+// once per device (`done` is a per-kernel bitmask of devices): the attribute
+// persists, so later launches, including those inside a stream capture,
+// make no runtime call besides the launch itself.
+int smem_opt_in(const void* func, int bytes, unsigned* done);
+
 // A zeroed work counter for one persistent launch on `st`: a slot of a
 // per-device ring of 256 counters, reset by cudaMemsetAsync on `st` (so a
 // captured graph resets it on every replay).  Launches that overlap on the

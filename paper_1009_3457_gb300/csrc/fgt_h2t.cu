@@ -164,7 +164,8 @@ static int fgt_launch(int g, int ncut, double ustep, const float* A, float* Y, f
     using C = FgtCfg<P>;
     const int side = 1 << g;
     const size_t smem = fgt_smem_bytes<P>(ncut);
-    FMM_CUDA_TRY(cudaFuncSetAttribute(fgt_pass_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    static unsigned opted;
+    if (int rc = smem_opt_in((const void*)fgt_pass_kernel<P>, (int)smem, &opted)) return rc;
     const dim3 grid((side + kFgtSeg - 1) / kFgtSeg, side);
     fgt_pass_kernel<P><<<grid, C::THREADS, smem, st>>>(g, ncut, ustep, 0, A, Y, 0);
     FMM_CUDA_TRY(cudaGetLastError());

@@ -8,8 +8,6 @@
 // launcher.
 #include "m2l_fp32_tile.cuh"
 
-#include <atomic>
-
 namespace fmmgb {
 
 // ---------------------------------------------------------------------------
@@ -78,17 +76,23 @@ static int launch_p(M2LLaunch& job, const float2* h, const float* a, const float
     bool adaptive = false;
     for (int i = 0; i < job.nlev; ++i) adaptive |= job.lv[i].exists != nullptr;
     auto kern = adaptive ? m2l_fp32_kernel<P, true> : m2l_fp32_kernel<P, false>;
-    // The shared-memory opt-in is set once per device and instantiation, so
-    // that launches inside a stream capture make no other runtime call.
-    static std::atomic<unsigned> opted[2];
-    int dev = 0;
-    FMM_CUDA_TRY(cudaGetDevice(&dev));
-    const unsigned bit = 1u << (dev & 31);
-    if (!(opted[adaptive].load() & bit)) {
-        FMM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem));
-        opted[adaptive].fetch_or(bit);
+    // persistent grid: resident CTAs x SMs, tiles claimed from a zeroed counter
+    int sms = 0, occ = 0;
+    int rc = device_sm_count(&sms);
+    if (rc) return rc;
+    static unsigned opted[2];
+    if ((rc = smem_opt_in((const void*)kern, (int)C::smem, &opted[adaptive]))) return rc;
+    static int occ_cache[2];  // resident CTAs per SM (same on every device of one model)
+    if (!(occ = __atomic_load_n(&occ_cache[adaptive], __ATOMIC_ACQUIRE))) {
+        FMM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, C::smem));
+        __atomic_store_n(&occ_cache[adaptive], occ, __ATOMIC_RELEASE);
     }
-    kern<<<total, kThreads, C::smem, st>>>(job, h, a, b);
+    int grid = total, *counter = nullptr;
+    if (occ > 0 && (int64_t)occ * sms < total) {
+        grid = occ * sms;
+        if ((rc = tile_counter(&counter, st))) return rc;
+    }
+    kern<<<grid, kThreads, C::smem, st>>>(job, h, a, b, total, counter);
     FMM_CUDA_TRY(cudaGetLastError());
     return FMM_OK;
 }

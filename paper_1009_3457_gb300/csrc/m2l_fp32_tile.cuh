@@ -298,28 +298,39 @@ __device__ __forceinline__ void m2l_tile(unsigned char* raw, const TileGeom& g, 
 }
 
 // ---------------------------------------------------------------------------
-// stencil kernel: one CTA per 4 x 4-parent tile, every requested level in one
-// launch (heaviest level first); the ~1.4k CTAs of the level 2..8 pass run
-// about 9 per SM in two rounds of 5-6 resident CTAs, which the hardware block
-// scheduler keeps balanced.
+// stencil kernel: every requested level in one launch, tiles ordered heaviest
+// level first.  Persistent when `counter` is set: each resident CTA (6 per SM
+// at p = 16) loads the operator once, takes its first tile by blockIdx and
+// claims the next from the work counter, so the operator table is staged
+// once per CTA instead of once per tile and no second round of CTAs leaves
+// SMs half empty at the end.  With counter == NULL the grid covers every
+// tile, one CTA each.
 // ---------------------------------------------------------------------------
 template <int P, bool ADAPTIVE>
-__global__ void __launch_bounds__(kThreads, M2LCfg<P>::MIN_CTAS) m2l_fp32_kernel(M2LLaunch job, const float2* __restrict__ hsel,
-                                                            const float* __restrict__ ascale,
-                                                            const float* __restrict__ bscale)
+__global__ void __launch_bounds__(kThreads, M2LCfg<P>::MIN_CTAS)
+    m2l_fp32_kernel(M2LLaunch job, const float2* __restrict__ hsel, const float* __restrict__ ascale,
+                    const float* __restrict__ bscale, int total, int* __restrict__ counter)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_next;
     m2l_load_operator<P>(smem_raw, hsel, ascale, bscale);
-    const int tile = blockIdx.x;
-    int li = 0;
-    while (li + 1 < job.nlev && tile >= job.lv[li + 1].tile_begin) ++li;
-    const M2LLevel& lv = job.lv[li];
-    int t = tile - lv.tile_begin;
-    if constexpr (ADAPTIVE)
-        if (lv.tiles) t = lv.tiles[t];  // the level's tiles that hold an existing box
-    const TileGeom g = tile_geom_of(lv.M, lv.L, ADAPTIVE ? lv.exists : nullptr, lv.level, t);
-    __syncthreads();
-    m2l_tile<P, ADAPTIVE>(smem_raw, g, job.periodic, job.accumulate);
+    int tile = blockIdx.x;
+    while (tile < total) {
+        int li = 0;
+        while (li + 1 < job.nlev && tile >= job.lv[li + 1].tile_begin) ++li;
+        const M2LLevel& lv = job.lv[li];
+        int t = tile - lv.tile_begin;
+        if constexpr (ADAPTIVE)
+            if (lv.tiles) t = lv.tiles[t];  // the level's tiles that hold an existing box
+        const TileGeom g = tile_geom_of(lv.M, lv.L, ADAPTIVE ? lv.exists : nullptr, lv.level, t);
+        __syncthreads();  // operator visible; the previous tile is done with the halo buffer
+        m2l_tile<P, ADAPTIVE>(smem_raw, g, job.periodic, job.accumulate);
+        if (!counter) break;
+        // every thread read s_next of the previous claim before the barrier inside m2l_tile
+        if (threadIdx.x == 0) s_next = (int)gridDim.x + atomicAdd(counter, 1);
+        __syncthreads();
+        tile = s_next;
+    }
 }
 
 }  // namespace fmmgb

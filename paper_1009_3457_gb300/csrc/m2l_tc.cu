@@ -28,13 +28,14 @@
 // A_lo B_hi recover ~16 bits per product, accumulated in FP32.
 //
 // Schedule.  A persistent CTA per SM takes tiles round-robin and runs four
-// roles concurrently: three producer warps (warps 0-2; one bulk copy in
-// flight per warp) stream the 32 operator blocks of every tile through a ring
-// of shared-memory stages; an MMA thread (warp 4) issues the tcgen05 products
-// into one of two TMEM accumulators; three staging warps (5-7) load the next
-// tile's halo (TMA tensor-map copies of the BF16 hi/lo planes that a pre-pass
-// writes, or bulk copies where a level is too small for the tensor map); four
-// epilogue warps (8-11) drain the other accumulator.
+// roles concurrently: producer warps (eight at p = 16, three at p = 24; one
+// bulk copy in flight per warp, one ring stage each) stream the 32 operator
+// blocks of every tile through a ring of shared-memory stages; an MMA thread
+// (warp 8) issues the tcgen05 products into a TMEM accumulator; three staging
+// warps (9-11) load the next tile's halo (TMA tensor-map copies of the BF16
+// hi/lo planes that a pre-pass writes, or bulk copies where a level is too
+// small for the tensor map); four epilogue warps (12-15) drain the
+// accumulator.
 // Hand-overs use mbarriers; every wait is bounded: on timeout the CTA records
 // FMM_ETIMEOUT in the device error word, waits (bounded) for its own copies,
 // frees its TMEM and returns.
@@ -67,9 +68,21 @@ struct TcCfg {
     static constexpr int BBUF = 4 * KCH * IPLANE;     // bytes of one halo buffer (hi and lo)
     static constexpr int APART = MT * 128 * K2 * 2;   // bytes of one block's hi (or lo) operator image
     static constexpr int NBUF = 1;                    // halo buffers
-    static constexpr int NPROD = 3;                   // producer warps (one bulk copy in flight each)
-    static constexpr int SP = P <= 16 ? 2 : 1;        // ring stages per producer
+    // Producer warps, one ring stage each.  A stage is refilled only after the
+    // MMAs that read it complete, so the operator stream is bound by the ring
+    // depth over that round trip (completion, wake-up, one bulk-copy latency):
+    // as many stages as shared memory holds (8 x 16 KB at p = 16, 3 x 48 KB at
+    // p = 24, beside the halo buffer).
+    static constexpr int NPROD = P <= 16 ? 8 : 3;
+    static constexpr int SP = 1;                      // ring stages per producer
     static constexpr int STAGES = NPROD * SP;         // operator ring depth
+    // Stages are released in groups of G by one tcgen05.commit: the arrival
+    // of a commit on its mbarrier comes ~600 cycles after the previous one
+    // (measured), so a commit per 16 KB block caps the stream below the
+    // tensor pipe's rate at p = 16.  Blocks per CTA (32 per tile) are a
+    // multiple of G.
+    static constexpr int G = P <= 16 ? 2 : 1;
+    static_assert(STAGES % G == 0 && 32 % G == 0, "stage groups");
     // TMEM: per M tile a 2N-column accumulator (A_hi x [B_hi|B_lo] interleaved) + an N-column one (A_lo x B_hi)
     static constexpr int SETCOLS = MT * 3 * N;
     static constexpr int NACC = 2 * SETCOLS <= 512 ? 2 : 1;
@@ -202,13 +215,13 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
                  : "memory");
 }
 
-__device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3, int c4,
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
                                             uint64_t* bar)
 {
     asm volatile(
-        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(
             su32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(su32(bar))
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(su32(bar))
         : "memory");
 }
 
@@ -325,8 +338,10 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src, bool vali
 // Tiles are handed out round-robin (tile = blockIdx.x + i * gridDim.x); all
 // tiles cost the same.
 // ---------------------------------------------------------------------------
-constexpr int kTcCtaThreads = 384;
-constexpr int kMmaWarp = 4, kStageWarp0 = 5, kStageWarps = 3, kEpiWarp0 = 8;
+// warps 0-7 producers (NPROD of them active), 8 MMA issuer, 9-11 halo staging,
+// 12-15 epilogue (a multiple of 4, so that warp % 4 is its TMEM lane quarter)
+constexpr int kTcCtaThreads = 512;
+constexpr int kMmaWarp = 8, kStageWarp0 = 9, kStageWarps = 3, kEpiWarp0 = 12;
 
 struct TcTile {
     const unsigned char* planes;
@@ -394,7 +409,7 @@ __global__ void __launch_bounds__(kTcCtaThreads, 1) m2l_tc_kernel(M2LLaunch job,
     if (tid == 0) {
         for (int s = 0; s < C::STAGES; ++s) {
             mbar_init(&afull[s], 1);
-            mbar_init(&aempty[s], 1);
+            if (s % C::G == 0) mbar_init(&aempty[s / C::G], 1);
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(&bfull[i], 1);
@@ -429,7 +444,7 @@ __global__ void __launch_bounds__(kTcCtaThreads, 1) m2l_tc_kernel(M2LLaunch job,
             bool ok = true;
             for (int g = pr; g < total_blocks; g += C::NPROD, ++k) {
                 const int s = pr * C::SP + k % C::SP;
-                if (k >= C::SP && !mbar_wait(&aempty[s], (uint32_t)(((k / C::SP) - 1) & 1))) {
+                if (k >= C::SP && !mbar_wait(&aempty[s / C::G], (uint32_t)(((k / C::SP) - 1) & 1))) {
                     ok = false;
                     break;
                 }
@@ -489,7 +504,7 @@ __global__ void __launch_bounds__(kTcCtaThreads, 1) m2l_tc_kernel(M2LLaunch job,
                         }
                     }
                 }
-                umma_commit(&aempty[s]);  // the stage is free once these MMAs have read it
+                if (s % C::G == C::G - 1) umma_commit(&aempty[s / C::G]);  // the group's stages are free once read
             }
             umma_commit(&dfull[td]);  // accumulator set td holds tile i
             umma_commit(&bfree[ts]);  // halo buffer ts may be restaged
@@ -508,10 +523,11 @@ __global__ void __launch_bounds__(kTcCtaThreads, 1) m2l_tc_kernel(M2LLaunch job,
             const TcTile g = tc_tile<P>(job, (int)blockIdx.x + i * (int)gridDim.x);
             unsigned char* bb = bbuf + (size_t)ts * C::BBUF;
             if (maps.use_tma[g.li]) {
-                // one TMA box: {8 bf16, HX columns, 2 parts, HY rows, 4 KCH planes}, zero-filled outside the level
+                // one TMA box: {HX columns x 8 bf16 (160 contiguous bytes), 2 parts, HY rows, 4 KCH planes},
+                // zero-filled outside the level; x = 8 (PX0 - 1) elements is a multiple of 16 bytes
                 if (st == 0) {
                     mbar_expect_tx(&bfull[ts], (uint32_t)C::BBUF);
-                    tma_load_5d(bb, &maps.map[g.li], 0, g.PX0 - 1, 0, g.PY0 - 1, 0, &bfull[ts]);
+                    tma_load_4d(bb, &maps.map[g.li], 8 * (g.PX0 - 1), 0, g.PY0 - 1, 0, &bfull[ts]);
                 }
                 continue;
             }
@@ -686,17 +702,19 @@ static int launch_tc_p(M2LLaunch& job, const void* img, bool split, int* err, cu
     for (int i = 0; i < job.nlev; ++i) {
         const int np = 1 << (job.lv[i].level - 1);
         if (!encode || job.periodic || np < C::HX || np < C::HY) continue;  // halo larger than the level: cp.async path
-        const cuuint64_t dims[5] = {8, (cuuint64_t)np, 2, (cuuint64_t)np, (cuuint64_t)(4 * C::KCH)};
-        const cuuint64_t strides[4] = {16, (cuuint64_t)np * 16, (cuuint64_t)np * 32, (cuuint64_t)np * np * 32};
-        const cuuint32_t box[5] = {8, (cuuint32_t)C::HX, 2, (cuuint32_t)C::HY, (cuuint32_t)(4 * C::KCH)};
-        const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
-        const CUresult r = encode(&maps.map[i], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, (void*)job.lv[i].planes, dims,
+        // planes [cc][qy][part][qx][8 bf16]: (qx, 8) merge into one contiguous dimension of 8 np elements
+        const cuuint64_t dims[4] = {(cuuint64_t)np * 8, 2, (cuuint64_t)np, (cuuint64_t)(4 * C::KCH)};
+        const cuuint64_t strides[3] = {(cuuint64_t)np * 16, (cuuint64_t)np * 32, (cuuint64_t)np * np * 32};
+        const cuuint32_t box[4] = {(cuuint32_t)(8 * C::HX), 2, (cuuint32_t)C::HY, (cuuint32_t)(4 * C::KCH)};
+        const cuuint32_t estr[4] = {1, 1, 1, 1};
+        const CUresult r = encode(&maps.map[i], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)job.lv[i].planes, dims,
                                   strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return fail(FMM_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
         maps.use_tma[i] = 1;
     }
-    FMM_CUDA_TRY(cudaFuncSetAttribute(m2l_tc_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem));
+    static unsigned opted;
+    if ((rc = smem_opt_in((const void*)m2l_tc_kernel<P>, (int)C::smem, &opted))) return rc;
     const int grid = total < sms ? total : sms;
     m2l_tc_kernel<P><<<grid, kTcCtaThreads, C::smem, st>>>(job, maps, (const unsigned char*)img, split ? 1 : 0, total,
                                                             err);
