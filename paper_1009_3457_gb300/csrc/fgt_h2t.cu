@@ -26,24 +26,32 @@
 
 namespace fmmgb {
 
-constexpr int kFgtSeg = 32;      // boxes per CTA along the pass axis
+constexpr int kFgtSeg = 8;       // boxes per CTA along the pass axis
+constexpr int kFgtGroups = 3;    // tap groups per box: partial sums reduced in shared memory
 constexpr int kFgtMaxCut = 16;   // largest n_cut accepted
 
+// Thread mapping: (tap group, box of the segment, 4-row block, 4-column block);
+// a thread accumulates a 4 x 4 block of one box's output over a third of the
+// taps.  At sigma = 0.05 (32 x 32 boxes) and p = 16 a pass runs 128 CTAs of
+// 384 threads, ten warps per SM.
 template <int P>
 struct FgtCfg {
-    static constexpr int RB = P / 2;            // rows (b) per thread
+    static constexpr int RB = 4;                // output rows (b) per thread
+    static constexpr int RBLK = P / RB;         // row blocks per box
     static constexpr int CB = P / 4;            // column blocks of 4 per box
-    static constexpr int TPB = 2 * CB;          // threads per box
-    static constexpr int THREADS = kFgtSeg * TPB;
+    static constexpr int TPB = RBLK * CB;       // threads per box and tap group
+    static constexpr int THREADS = kFgtGroups * kFgtSeg * TPB;
     static constexpr int NH = 2 * P - 1;
     static constexpr int BS = P * P + 16;       // padded float stride between boxes in shared memory
+    static_assert(P % 4 == 0 && BS % 4 == 0, "16-byte aligned float4 rows");
 };
 
 template <int P>
 size_t fgt_smem_bytes(int ncut)
 {
     using C = FgtCfg<P>;
-    return sizeof(float) * ((size_t)(kFgtSeg + 2 * ncut) * C::BS + (size_t)(2 * ncut + 1) * C::NH + P);
+    return sizeof(float) * ((size_t)(kFgtSeg + 2 * ncut) * C::BS + (size_t)(2 * ncut + 1) * C::NH + P +
+                            (size_t)(kFgtGroups - 1) * kFgtSeg * P * P);
 }
 
 template <int P>
@@ -55,9 +63,12 @@ __global__ void __launch_bounds__(FgtCfg<P>::THREADS) fgt_pass_kernel(int g, int
     constexpr int RB = C::RB, NH = C::NH, BS = C::BS;
     extern __shared__ __align__(16) float fsm[];
     const int taps = 2 * ncut + 1;
-    float* halo = fsm;                                   // [kFgtSeg + 2 ncut][BS]
-    float* hs = halo + (size_t)(kFgtSeg + 2 * ncut) * BS;  // [taps][NH]
-    float* ss = hs + taps * NH;                          // [P]
+    // float4-accessed arrays first: BS and P * P are multiples of 4 floats, so
+    // halo and part start on 16-byte boundaries; the scalar tables follow
+    float* halo = fsm;                                              // [kFgtSeg + 2 ncut][BS]
+    float* part = halo + (size_t)(kFgtSeg + 2 * ncut) * BS;         // [kFgtGroups - 1][kFgtSeg][P][P]
+    float* hs = part + (size_t)(kFgtGroups - 1) * kFgtSeg * P * P;  // [taps][NH]
+    float* ss = hs + taps * NH;                                     // [P]
 
     const int side = 1 << g;
     const int seg0 = blockIdx.x * kFgtSeg;
@@ -98,12 +109,15 @@ __global__ void __launch_bounds__(FgtCfg<P>::THREADS) fgt_pass_kernel(int g, int
     }
     __syncthreads();
 
-    const int j = tid / C::TPB;              // box within the segment
-    const int r = tid % C::TPB;
-    const int b0 = (r & 1) * RB;             // first output row
-    const int c0 = (r >> 1) * 4;             // first of 4 columns
+    const int grp = tid / (kFgtSeg * C::TPB);
+    const int rem = tid % (kFgtSeg * C::TPB);
+    const int j = rem / C::TPB;                  // box within the segment
+    const int r = rem % C::TPB;
+    const int b0 = (r % C::RBLK) * RB;           // first output row
+    const int c0 = (r / C::RBLK) * 4;            // first of 4 columns
     const int pos = seg0 + j;
-    if (pos >= side) return;
+    const int per = (taps + kFgtGroups - 1) / kFgtGroups;
+    const int d0 = grp * per, d1 = min(taps, d0 + per);
 
     float acc[RB][4];
 #pragma unroll
@@ -111,29 +125,52 @@ __global__ void __launch_bounds__(FgtCfg<P>::THREADS) fgt_pass_kernel(int g, int
 #pragma unroll
         for (int cc = 0; cc < 4; ++cc) acc[i][cc] = 0.f;
 
-    for (int d = 0; d < taps; ++d) {
-        const int spos = pos + d - ncut;
-        if (spos < 0 || spos >= side) continue;
-        const float* hrow = hs + d * NH + b0;
-        const float* src = halo + (size_t)(j + d) * BS + c0;
-        float w[RB];
+    if (pos < side) {
+        for (int d = d0; d < d1; ++d) {
+            const int spos = pos + d - ncut;
+            if (spos < 0 || spos >= side) continue;
+            const float* hrow = hs + d * NH + b0;
+            const float* src = halo + (size_t)(j + d) * BS + c0;
+            float w[RB];
 #pragma unroll
-        for (int i = 0; i < RB; ++i) w[i] = hrow[i];
+            for (int i = 0; i < RB; ++i) w[i] = hrow[i];
 #pragma unroll
-        for (int a = 0; a < P; ++a) {
-            const float4 v = *reinterpret_cast<const float4*>(src + a * P);
+            for (int a = 0; a < P; ++a) {
+                const float4 v = *reinterpret_cast<const float4*>(src + a * P);
 #pragma unroll
-            for (int i = 0; i < RB; ++i) {
-                acc[i][0] = fmaf(w[i], v.x, acc[i][0]);
-                acc[i][1] = fmaf(w[i], v.y, acc[i][1]);
-                acc[i][2] = fmaf(w[i], v.z, acc[i][2]);
-                acc[i][3] = fmaf(w[i], v.w, acc[i][3]);
+                for (int i = 0; i < RB; ++i) {
+                    acc[i][0] = fmaf(w[i], v.x, acc[i][0]);
+                    acc[i][1] = fmaf(w[i], v.y, acc[i][1]);
+                    acc[i][2] = fmaf(w[i], v.z, acc[i][2]);
+                    acc[i][3] = fmaf(w[i], v.w, acc[i][3]);
+                }
+                if (a + 1 < P) {
+#pragma unroll
+                    for (int i = 0; i + 1 < RB; ++i) w[i] = w[i + 1];
+                    w[RB - 1] = hrow[RB + a];
+                }
             }
-            if (a + 1 < P) {
+        }
+    }
+    // tap groups 1.. hand their partial sums to group 0 through shared memory
+    if (grp > 0) {
+        float* pp = part + ((size_t)(grp - 1) * kFgtSeg + j) * (P * P);
 #pragma unroll
-                for (int i = 0; i + 1 < RB; ++i) w[i] = w[i + 1];
-                w[RB - 1] = hrow[RB + a];
-            }
+        for (int i = 0; i < RB; ++i)
+            *reinterpret_cast<float4*>(pp + (b0 + i) * P + c0) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+    }
+    __syncthreads();
+    if (grp != 0 || pos >= side) return;
+#pragma unroll
+    for (int q = 0; q < kFgtGroups - 1; ++q) {
+        const float* pp = part + ((size_t)q * kFgtSeg + j) * (P * P);
+#pragma unroll
+        for (int i = 0; i < RB; ++i) {
+            const float4 v = *reinterpret_cast<const float4*>(pp + (b0 + i) * P + c0);
+            acc[i][0] += v.x;
+            acc[i][1] += v.y;
+            acc[i][2] += v.z;
+            acc[i][3] += v.w;
         }
     }
     // transposed store: out[box][c][b] = s_b acc[b][c]
@@ -142,16 +179,16 @@ __global__ void __launch_bounds__(FgtCfg<P>::THREADS) fgt_pass_kernel(int g, int
 #pragma unroll
     for (int cc = 0; cc < 4; ++cc) {
         float* row = dst + (size_t)(c0 + cc) * P + b0;
-#pragma unroll
-        for (int i = 0; i < RB; i += 2) {
-            float2 o = make_float2(ss[b0 + i] * acc[i][cc], ss[b0 + i + 1] * acc[i + 1][cc]);
-            if (accumulate) {
-                const float2 old = *reinterpret_cast<const float2*>(row + i);
-                o.x += old.x;
-                o.y += old.y;
-            }
-            *reinterpret_cast<float2*>(row + i) = o;
+        float4 o = make_float4(ss[b0] * acc[0][cc], ss[b0 + 1] * acc[1][cc], ss[b0 + 2] * acc[2][cc],
+                               ss[b0 + 3] * acc[3][cc]);
+        if (accumulate) {
+            const float4 old = *reinterpret_cast<const float4*>(row);
+            o.x += old.x;
+            o.y += old.y;
+            o.z += old.z;
+            o.w += old.w;
         }
+        *reinterpret_cast<float4*>(row) = o;
     }
 }
 
@@ -164,8 +201,8 @@ static int fgt_launch(int g, int ncut, double ustep, const float* A, float* Y, f
     using C = FgtCfg<P>;
     const int side = 1 << g;
     const size_t smem = fgt_smem_bytes<P>(ncut);
-    static unsigned opted;
-    if (int rc = smem_opt_in((const void*)fgt_pass_kernel<P>, (int)smem, &opted)) return rc;
+    static unsigned opted;  // opted in once for the largest neighbourhood, so every n_cut fits
+    if (int rc = smem_opt_in((const void*)fgt_pass_kernel<P>, (int)fgt_smem_bytes<P>(kFgtMaxCut), &opted)) return rc;
     const dim3 grid((side + kFgtSeg - 1) / kFgtSeg, side);
     fgt_pass_kernel<P><<<grid, C::THREADS, smem, st>>>(g, ncut, ustep, 0, A, Y, 0);
     FMM_CUDA_TRY(cudaGetLastError());

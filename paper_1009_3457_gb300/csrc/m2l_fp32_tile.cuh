@@ -185,12 +185,23 @@ __device__ __forceinline__ void m2l_tile(unsigned char* raw, const TileGeom& g, 
     const int tpx = t & 3, tpy = t >> 2;
     const int2* mylist = s.lst + cls * 27;
 
+    // On an adaptive level a warp (one child class, 16 targets) whose targets
+    // are all absent skips the translation; the vote is warp-uniform.
+    const int px = g.PX0 + tpx, py = g.PY0 + tpy;
+    bool target = px < g.np && py < g.np;
+    if constexpr (ADAPTIVE)
+        if (target && g.exists) target = g.exists[(size_t)(2 * py + cy) * g.side + 2 * px + cx] != 0;
+    bool work = true;
+    if constexpr (ADAPTIVE) work = __any_sync(0xffffffffu, target);
+
     // ---- translate and reduce ----
     float2 acc[RN];
 #pragma unroll
     for (int i = 0; i < RN; ++i) acc[i] = make_float2(0.f, 0.f);
     const float2* tbase = s.buf + tpy * kHalo + tpx;
-    if constexpr (!C::SPLIT_ROWS) {
+    if (!work) {
+        // nothing to store for this warp
+    } else if constexpr (!C::SPLIT_ROWS) {
         // half-warp `half` takes list entries [14 half, 14 half + 14) of 27; all p rows
 #pragma unroll 1
         for (int j = 0; j < 14; ++j) {
@@ -258,10 +269,6 @@ __device__ __forceinline__ void m2l_tile(unsigned char* raw, const TileGeom& g, 
     }
 
     // ---- store L~[n] = a_n * res (rows [HR half, HR half + HR)) ----
-    const int px = g.PX0 + tpx, py = g.PY0 + tpy;
-    bool target = px < g.np && py < g.np;
-    if constexpr (ADAPTIVE)
-        if (target && g.exists) target = g.exists[(size_t)(2 * py + cy) * g.side + 2 * px + cx] != 0;
     if (target) {
         const int ix = 2 * px + cx, iy = 2 * py + cy;
         const int n0 = half * HR;

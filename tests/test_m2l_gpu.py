@@ -241,3 +241,36 @@ def test_m2l_levels_including_empty_levels(fmm, orc, medium_particles):
     assert np.all(_host(Ld[0]) == 0) and np.all(_host(Ld[1]) == 0)
     for l in (2, 3):
         _check(_host(Ld[l]), _oracle_level(orc, l, p, Ms[l]))
+
+
+@pytest.mark.parametrize("prec_name", ["FMM_FP32", "FMM_TC_BF16X3"])
+def test_levels_call_replays_from_a_cuda_graph(fmm, orc, prec_name):
+    """fmm_m2l_levels recorded by a caller's stream capture (the persistent FP32 kernel with its
+    work-counter reset; the tensor-core pre-pass and kernel) and replayed twice, accumulating:
+    L = X + 3 M2L(M) after the warm call and two replays."""
+    import torch
+
+    prec = getattr(fmm, prec_name)
+    p, L = 16, 7
+    xy, c = workloads.uniform_particles(60000, np.random.default_rng(8))
+    Ms = orc.upward_uniform(L, p, xy, c)
+    tree = fmm.fmm_build_lists(None, L)
+    levels = list(range(2, L + 1))
+    rng = np.random.default_rng(9)
+    X = {l: (rng.standard_normal((4 ** l, p)) + 1j * rng.standard_normal((4 ** l, p))) for l in levels}
+    Md = [_dev(orc.scale_me(Ms[l], l)) for l in levels]
+    Ld = [_dev(X[l]) for l in levels]
+    fmm.fmm_m2l_levels(tree, 2, p, Md, Ld, prec=prec, accumulate=True)  # warm: tables, opt-ins, scratch
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, capture_error_mode="thread_local"):
+        fmm.fmm_m2l_levels(tree, 2, p, Md, Ld, prec=prec, accumulate=True)
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    fmm.fmm_sync_status()
+    tol = TOL_L2 if prec == fmm.FMM_FP32 else 1e-4
+    for l, out in zip(levels, Ld):
+        ref = orc.scale_le(orc.m2l_uniform(l, p, Ms[l]), l)
+        got = (_host(out) - X[l].astype(np.complex64).astype(np.complex128)) / 3.0
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= tol, l
