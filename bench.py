@@ -349,6 +349,23 @@ def run_ours(args):
         if rank == 0:
             print(json.dumps({"mode": "kernels", "steps": args.steps, "launches_per_step": 1, "batch": bt["info"]}))
         return 0
+    if args.mode == "kernels" and args.prec == "fgt":
+        # profiling case: the FGT H2T of the sigma = 0.05, p = 16 workload (two passes per call)
+        fcfg = workloads.CONFIGS["fgt"]
+        fx, fq = workloads.gmm_particles(fcfg["n"], workloads.rng_for("fgt"))
+        sigma, fp = 0.05, 16
+        g = workloads.fgt_grid_log2(sigma)
+        A = torch.empty((4 ** g, fp, fp), dtype=torch.float32, device=dev)
+        Cf = torch.empty_like(A)
+        W = torch.empty_like(A)
+        fmmgb.fgt_p2h(g, fp, sigma, torch.from_numpy(fx).to(dev), torch.from_numpy(fq).to(dev), A)
+        for _ in range(args.steps):
+            fmmgb.fgt_h2t(g, fcfg["ncut"], fp, sigma, A, Cf, work=W)
+        torch.cuda.synchronize()
+        fmmgb.fmm_sync_status()
+        if rank == 0:
+            print(json.dumps({"mode": "kernels", "steps": args.steps, "launches_per_step": 2}))
+        return 0
     if args.mode == "kernels":
         # profiling case: the step's launch only (no e2e copies, no CPU baseline, no other rows)
         prec = {"fp32": fmmgb.FMM_FP32, "tc3": fmmgb.FMM_TC_BF16X3, "tc1": fmmgb.FMM_TC_BF16}[args.prec]
@@ -639,8 +656,9 @@ def main():
     ap.add_argument("--no-rows", action="store_true", help="skip the adjoint / per-level / FGT rows")
     ap.add_argument("--mode", default="full", choices=["full", "kernels"],
                     help="kernels: only the timed step's launches (for ncu captures)")
-    ap.add_argument("--prec", default="fp32", choices=["fp32", "tc3", "tc1", "batched"],
-                    help="precision of the launches in --mode kernels (batched: the 256-problem batch)")
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "tc3", "tc1", "batched", "fgt"],
+                    help="launches of --mode kernels: the step at this precision, or the 256-problem batch, "
+                         "or the FGT H2T at sigma 0.05, p 16")
     ap.add_argument("--nprob", type=int, default=None,
                     help="--mode kernels --prec batched: the first N problems of the batch (profiling case)")
     args = ap.parse_args()
