@@ -749,7 +749,8 @@ int fgt_h2t(int32_t grid_log2, int32_t n_cut, int32_t p, double sigma, const flo
         const size_t bytes = ((size_t)1 << (2 * grid_log2)) * (size_t)p * p * sizeof(float);
         if ((rc = fgt_workspace(bytes, &Y))) return rc;
     }
-    return launch_fgt_h2t(grid_log2, n_cut, p, sigma, A, Y, C, (flags & FMM_ACCUMULATE) != 0, (cudaStream_t)stream);
+    return launch_fgt_h2t(grid_log2, n_cut, p, sigma, A, Y, C, (flags & FMM_ACCUMULATE) != 0, true,
+                          (cudaStream_t)stream);
 }
 
 int fgt_p2h(int32_t grid_log2, int32_t p, double sigma, const double* x, const double* q, int64_t n, float* A,

@@ -129,7 +129,7 @@ int tc_plane_workspace(size_t bytes, unsigned char** out);
 bool fgt_supported(int p);
 int fgt_max_cut();
 int launch_fgt_h2t(int g, int ncut, int p, double sigma, const float* A, float* Y, float* C, bool acc,
-                   cudaStream_t st);
+                   bool cached_table, cudaStream_t st);
 int fgt_workspace(size_t bytes, float** out);
 int fgt_check_args(const char* who, int g, int ncut, int p, double sigma, const float* A, const float* C,
                    const float* work, int flags);

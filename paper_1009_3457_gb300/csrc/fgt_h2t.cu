@@ -16,24 +16,30 @@
 // instead of (2 n_cut + 1)^2 2 p^3 for the box-pair form -- the same result up
 // to rounding order.  Both passes run the same stencil kernel: out[box] =
 // diag(s) sum_d H_d^T in[box + d e_axis], written transposed so that the second
-// pass contracts the other Hermite index.  The intermediate Y is library-owned
+// pass contracts the other Hermite index.  The Hermite-function values of the
+// 2 n_cut + 1 offsets are computed once per (p, n_cut, sigma, grid) by an FP64
+// kernel and cached per device (the allocation-free entry point computes them
+// in every CTA instead).  The intermediate Y is library-owned
 // scratch (one [4^g][p][p] float buffer per device, grown on demand).
 #include <math.h>
 
+#include <cstring>
+#include <map>
 #include <mutex>
+#include <tuple>
 
 #include "common.cuh"
 
 namespace fmmgb {
 
-constexpr int kFgtSeg = 8;       // boxes per CTA along the pass axis
+constexpr int kFgtSeg = 4;       // boxes per CTA along the pass axis
 constexpr int kFgtGroups = 3;    // tap groups per box: partial sums reduced in shared memory
 constexpr int kFgtMaxCut = 16;   // largest n_cut accepted
 
 // Thread mapping: (tap group, box of the segment, 4-row block, 4-column block);
 // a thread accumulates a 4 x 4 block of one box's output over a third of the
-// taps.  At sigma = 0.05 (32 x 32 boxes) and p = 16 a pass runs 128 CTAs of
-// 384 threads, ten warps per SM.
+// taps.  At sigma = 0.05 (32 x 32 boxes) and p = 16 a pass runs 256 CTAs of
+// 192 threads.
 template <int P>
 struct FgtCfg {
     static constexpr int RB = 4;                // output rows (b) per thread
@@ -54,10 +60,34 @@ size_t fgt_smem_bytes(int ncut)
                             (size_t)(kFgtGroups - 1) * kFgtSeg * P * P);
 }
 
+// Hermite-function values h_j(u_d), j < nh, u_d = -(d - ncut) * ustep (source
+// offset d - ncut), by the recurrence h_{j+1} = 2u h_j - 2j h_{j-1}, in FP64.
+__device__ __forceinline__ void fgt_hermite_row(int d, int ncut, int nh, double ustep, float* row)
+{
+    const double u = -(double)(d - ncut) * ustep;
+    double hm = exp(-u * u), h = 2.0 * u * hm;
+    row[0] = (float)hm;
+    if (nh > 1) row[1] = (float)h;
+    for (int j = 1; j + 1 < nh; ++j) {
+        const double hn = 2.0 * u * h - 2.0 * (double)j * hm;
+        hm = h;
+        h = hn;
+        row[j + 1] = (float)h;
+    }
+}
+
+// The table of one (p, n_cut, step): [2 n_cut + 1][2p - 1], cached per device.
+__global__ void fgt_table_kernel(int nh, int ncut, double ustep, float* __restrict__ tab)
+{
+    const int d = blockIdx.x * blockDim.x + threadIdx.x;
+    if (d < 2 * ncut + 1) fgt_hermite_row(d, ncut, nh, ustep, tab + (size_t)d * nh);
+}
+
 template <int P>
 __global__ void __launch_bounds__(FgtCfg<P>::THREADS) fgt_pass_kernel(int g, int ncut, double ustep, int axis,
                                                                       const float* __restrict__ in,
-                                                                      float* __restrict__ out, int accumulate)
+                                                                      float* __restrict__ out, int accumulate,
+                                                                      const float* __restrict__ htab)
 {
     using C = FgtCfg<P>;
     constexpr int RB = C::RB, NH = C::NH, BS = C::BS;
@@ -75,19 +105,11 @@ __global__ void __launch_bounds__(FgtCfg<P>::THREADS) fgt_pass_kernel(int g, int
     const int other = blockIdx.y;
     const int tid = threadIdx.x;
 
-    // Hermite-function table h_j(u_d), u_d = -(d - ncut) * ustep  (source offset d - ncut),
-    // by the recurrence h_{j+1} = 2u h_j - 2j h_{j-1}, in FP64.
-    for (int d = tid; d < taps; d += blockDim.x) {
-        const double u = -(double)(d - ncut) * ustep;
-        double hm = exp(-u * u), h = 2.0 * u * hm;
-        hs[d * NH + 0] = (float)hm;
-        if (NH > 1) hs[d * NH + 1] = (float)h;
-        for (int j = 1; j + 1 < NH; ++j) {
-            const double hn = 2.0 * u * h - 2.0 * (double)j * hm;
-            hm = h;
-            h = hn;
-            hs[d * NH + j + 1] = (float)h;
-        }
+    // Hermite-function table: the cached copy, or computed here (allocation-free entry point)
+    if (htab) {
+        for (int i = tid; i < taps * NH; i += blockDim.x) hs[i] = __ldg(htab + i);
+    } else {
+        for (int d = tid; d < taps; d += blockDim.x) fgt_hermite_row(d, ncut, NH, ustep, hs + d * NH);
     }
     for (int b = tid; b < P; b += blockDim.x) {
         double f = 1.0;
@@ -194,32 +216,70 @@ __global__ void __launch_bounds__(FgtCfg<P>::THREADS) fgt_pass_kernel(int g, int
 
 bool fgt_supported(int p) { return p == 4 || p == 8 || p == 12 || p == 16; }
 
+// Per-device cache of Hermite tables, keyed by (device, p, n_cut, step bits).
+static std::mutex g_tab_mu;
+static std::map<std::tuple<int, int, int, uint64_t>, float*> g_tabs;
+
+static int fgt_table(int p, int ncut, double ustep, const float** out)
+{
+    int dev = 0;
+    FMM_CUDA_TRY(cudaGetDevice(&dev));
+    uint64_t bits;
+    memcpy(&bits, &ustep, sizeof bits);
+    const auto key = std::make_tuple(dev, p, ncut, bits);
+    std::lock_guard<std::mutex> lk(g_tab_mu);
+    auto it = g_tabs.find(key);
+    if (it != g_tabs.end()) {
+        *out = it->second;
+        return FMM_OK;
+    }
+    const int nh = 2 * p - 1, taps = 2 * ncut + 1;
+    float* tab = nullptr;
+    FMM_CUDA_TRY(cudaMalloc(&tab, sizeof(float) * (size_t)taps * nh));
+    cudaStream_t st;
+    FMM_CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    fgt_table_kernel<<<1, 64, 0, st>>>(nh, ncut, ustep, tab);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+    if (e != cudaSuccess) {
+        cudaFree(tab);
+        return cuda_fail(e, "building the FGT Hermite table");
+    }
+    g_tabs[key] = tab;
+    *out = tab;
+    return FMM_OK;
+}
+
 template <int P>
 static int fgt_launch(int g, int ncut, double ustep, const float* A, float* Y, float* Cout, bool acc,
-                      cudaStream_t st)
+                      bool cached_table, cudaStream_t st)
 {
     using C = FgtCfg<P>;
     const int side = 1 << g;
     const size_t smem = fgt_smem_bytes<P>(ncut);
     static unsigned opted;  // opted in once for the largest neighbourhood, so every n_cut fits
     if (int rc = smem_opt_in((const void*)fgt_pass_kernel<P>, (int)fgt_smem_bytes<P>(kFgtMaxCut), &opted)) return rc;
+    const float* htab = nullptr;
+    if (cached_table)
+        if (int rc = fgt_table(P, ncut, ustep, &htab)) return rc;
     const dim3 grid((side + kFgtSeg - 1) / kFgtSeg, side);
-    fgt_pass_kernel<P><<<grid, C::THREADS, smem, st>>>(g, ncut, ustep, 0, A, Y, 0);
+    fgt_pass_kernel<P><<<grid, C::THREADS, smem, st>>>(g, ncut, ustep, 0, A, Y, 0, htab);
     FMM_CUDA_TRY(cudaGetLastError());
-    fgt_pass_kernel<P><<<grid, C::THREADS, smem, st>>>(g, ncut, ustep, 1, Y, Cout, acc ? 1 : 0);
+    fgt_pass_kernel<P><<<grid, C::THREADS, smem, st>>>(g, ncut, ustep, 1, Y, Cout, acc ? 1 : 0, htab);
     FMM_CUDA_TRY(cudaGetLastError());
     return FMM_OK;
 }
 
 int launch_fgt_h2t(int g, int ncut, int p, double sigma, const float* A, float* Y, float* Cout, bool acc,
-                   cudaStream_t st)
+                   bool cached_table, cudaStream_t st)
 {
     const double ustep = ldexp(1.0, -g) / (sqrt(2.0) * sigma);
     switch (p) {
-        case 4: return fgt_launch<4>(g, ncut, ustep, A, Y, Cout, acc, st);
-        case 8: return fgt_launch<8>(g, ncut, ustep, A, Y, Cout, acc, st);
-        case 12: return fgt_launch<12>(g, ncut, ustep, A, Y, Cout, acc, st);
-        case 16: return fgt_launch<16>(g, ncut, ustep, A, Y, Cout, acc, st);
+        case 4: return fgt_launch<4>(g, ncut, ustep, A, Y, Cout, acc, cached_table, st);
+        case 8: return fgt_launch<8>(g, ncut, ustep, A, Y, Cout, acc, cached_table, st);
+        case 12: return fgt_launch<12>(g, ncut, ustep, A, Y, Cout, acc, cached_table, st);
+        case 16: return fgt_launch<16>(g, ncut, ustep, A, Y, Cout, acc, cached_table, st);
         default: return fail(FMM_EINVAL, "fgt_h2t: unsupported p = %d", p);
     }
 }
@@ -276,5 +336,6 @@ extern "C" int fgt_h2t_noalloc(int32_t grid_log2, int32_t n_cut, int32_t p, doub
     if ((rc = static_scratch(&Y))) return rc;
     // The first pass writes every element of Y before the second pass reads
     // it, so the scratch needs no clearing between calls.
-    return launch_fgt_h2t(grid_log2, n_cut, p, sigma, A, Y, C, (flags & FMM_ACCUMULATE) != 0, (cudaStream_t)stream);
+    return launch_fgt_h2t(grid_log2, n_cut, p, sigma, A, Y, C, (flags & FMM_ACCUMULATE) != 0, false,
+                          (cudaStream_t)stream);
 }
