@@ -300,6 +300,7 @@ def _batched_setup(torch, fmmgb, dev, autotune=True, nprob=None):
 def run_ours(args):
     import torch
 
+    from paper_1009_3457_gb300 import dist as fdist
     from paper_1009_3457_gb300 import fmmgb
 
     ws, rank, local = _dist()
@@ -400,12 +401,9 @@ def run_ours(args):
     step_ms = _timed(torch, step_graph.replay, args.steps, stream, flush)
     if ws > 1:
         dist.barrier()
-    tot_ms = sum(step_ms)
-    if ws > 1:
-        t = torch.tensor([tot_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
-    value = ws * NTR * args.steps / (tot_ms * 1e-3)
+    # whole job: every rank's translations over the slowest rank's time (replicas, weak scaling)
+    tot_ms = fdist.max_over_ranks(sum(step_ms))
+    value = fdist.job_rate(NTR * args.steps, sum(step_ms) * 1e-3)
 
     # --- e2e: host buffers through the same public call ---
     Mh = {l: torch.empty_like(M[l], device="cpu").pin_memory() for l in LEVELS}
@@ -427,11 +425,7 @@ def run_ours(args):
         flush.zero_()
     torch.cuda.synchronize()
     e2e_ms = sum(_timed(torch, e2e_step, args.steps, stream, flush))
-    if ws > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = ws * NTR * args.steps / (e2e_ms * 1e-3)
+    e2e_value = fdist.job_rate(NTR * args.steps, e2e_ms * 1e-3)
     clocks = clk.stop() if rank == 0 else None
 
     # --- the other rows of the hot path, same device-resident protocol ---
