@@ -47,8 +47,8 @@ CONFIG = {
                 "(one multi-level launch; one-launch-per-level timing under rows)",
     "points": CFG["n"], "max_level": MAXL, "p": P, "translations_per_step": NTR,
     "levels": f"{LEVELS[0]}-{LEVELS[-1]}", "l2": "flushed between timed steps (256 MiB write)",
-    "timing": "device-resident step captured once as a CUDA graph (work-counter reset + one kernel) and "
-              "replayed between CUDA events; e2e calls the library from the host every step",
+    "timing": "device-resident step captured once as a CUDA graph (one kernel) and replayed between "
+              "CUDA events; e2e calls the library from the host every step",
     "parallelism": "replicas",
 }
 SM_COUNT = 152

@@ -136,20 +136,16 @@ int smem_opt_in(const void* func, int bytes, unsigned* done)
 
 int tile_counter(int** out, cudaStream_t st)
 {
-    int* slot = nullptr;
-    {
-        std::lock_guard<std::mutex> lk(g_mu);
-        DeviceState* s = nullptr;
-        int rc = current_state(&s);
-        if (rc) return rc;
-        if (!s->counters) {
-            FMM_CUDA_TRY(cudaMalloc(&s->counters, kCounterRing * sizeof(int)));
-            FMM_CUDA_TRY(cudaMemset(s->counters, 0, kCounterRing * sizeof(int)));
-        }
-        slot = s->counters + (s->next_counter++ % kCounterRing);
+    (void)st;  // nothing is enqueued: the slot is zero on allocation and the kernel resets it
+    std::lock_guard<std::mutex> lk(g_mu);
+    DeviceState* s = nullptr;
+    int rc = current_state(&s);
+    if (rc) return rc;
+    if (!s->counters) {
+        FMM_CUDA_TRY(cudaMalloc(&s->counters, kCounterRing * 2 * sizeof(int)));
+        FMM_CUDA_TRY(cudaMemset(s->counters, 0, kCounterRing * 2 * sizeof(int)));
     }
-    FMM_CUDA_TRY(cudaMemsetAsync(slot, 0, sizeof(int), st));
-    *out = slot;
+    *out = s->counters + 2 * (s->next_counter++ % kCounterRing);
     return FMM_OK;
 }
 

@@ -37,10 +37,12 @@ int device_sm_count(int* out);
 // make no runtime call besides the launch itself.
 int smem_opt_in(const void* func, int bytes, unsigned* done);
 
-// A zeroed work counter for one persistent launch on `st`: a slot of a
-// per-device ring of 256 counters, reset by cudaMemsetAsync on `st` (so a
-// captured graph resets it on every replay).  Launches that overlap on the
-// GPU use different slots unless 256 or more are in flight at once.
+// A work counter for one persistent launch: a slot of two ints (claimed
+// work, CTAs finished) from a per-device ring of 256, zero when allocated.
+// The kernel's last CTA to finish sets both back to zero, so no reset is
+// enqueued per launch and a captured graph replays with the same slot.
+// Launches that overlap on the GPU use different slots unless 256 or more
+// are in flight at once.
 int tile_counter(int** out, cudaStream_t st);
 
 // ---------------------------------------------------------------------------

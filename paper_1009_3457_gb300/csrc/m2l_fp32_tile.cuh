@@ -308,7 +308,8 @@ __device__ __forceinline__ void m2l_tile(unsigned char* raw, const TileGeom& g, 
 // stencil kernel: every requested level in one launch, tiles ordered heaviest
 // level first.  Persistent when `counter` is set: each resident CTA (6 per SM
 // at p = 16) loads the operator once, takes its first tile by blockIdx and
-// claims the next from the work counter, so the operator table is staged
+// claims the next from the work counter (counter[0]; counter[1] counts the
+// CTAs that finished, and the last one resets both), so the operator table is staged
 // once per CTA instead of once per tile and no second round of CTAs leaves
 // SMs half empty at the end.  With counter == NULL the grid covers every
 // tile, one CTA each.
@@ -337,6 +338,14 @@ __global__ void __launch_bounds__(kThreads, M2LCfg<P>::MIN_CTAS)
         if (threadIdx.x == 0) s_next = (int)gridDim.x + atomicAdd(counter, 1);
         __syncthreads();
         tile = s_next;
+    }
+    // the last CTA to finish returns the counter slot to zero for its next use
+    if (counter && threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(counter + 1, 1) == (int)gridDim.x - 1) {
+            atomicExch(counter, 0);
+            atomicExch(counter + 1, 0);
+        }
     }
 }
 
