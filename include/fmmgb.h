@@ -329,6 +329,48 @@ int fmm_p2m(int32_t level, int32_t p, const double* xy, const double* c, int64_t
             void* M, int32_t flags, void* stream);
 int fmm_m2m(int32_t child_level, int32_t p, const void* Mc, void* Mp, int32_t flags, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Far-field stages around the M2L path (Sec. 2.1 stages 3-4), scaled units,
+ * with the conjugate transposes that carry the gradient of a real objective
+ * back through them (PyTorch's convention for complex tensors).  p: 1..64.
+ * Coefficient arrays complex64, 8-byte aligned.  Support for the gradient
+ * chain of the translation path, not part of the translation itself.
+ *
+ * fmm_l2l: L~c[j] (+)= sum_{n>=j} C(n,j) u^(n-j) 2^-(j+1) L~p[n] for every box
+ *   of child_level, u = (x_child - x_parent) / r_parent = (+-1/4, +-1/4).
+ *   Lp: [4^(child_level-1)][p]; Lc: [4^child_level][p].  flags: FMM_ACCUMULATE.
+ * fmm_l2l_adjoint: Wp[parent] (+)= sum_{its 4 children} T_c^H Wc[child]
+ *   (Wc: [4^child_level][p], Wp: [4^(child_level-1)][p]).
+ * ------------------------------------------------------------------------- */
+int fmm_l2l(int32_t child_level, int32_t p, const void* Lp, void* Lc, int32_t flags, void* stream);
+int fmm_l2l_adjoint(int32_t child_level, int32_t p, const void* Wc, void* Wp, int32_t flags, void* stream);
+
+/* fmm_l2p: far field at n points from the LE of each point's box:
+ *     phi_j (+)= (1/r_l) sum_n L~_l[b][n] ((z_j - x_b) / r_l)^n,  l = lev[j], b = box[j],
+ *   phi_j = 0 where lev[j] < 2.
+ *   z: device float64 [n][2]; lev: device int32 [n]; box: device int64 [n]
+ *   (b = iy * 2^l + ix); L_levels: host array of max_level + 1 device pointers,
+ *   entry l = level l's [4^l][p] LEs (NULL for levels no point uses);
+ *   phi: device complex64 [n].  flags: FMM_ACCUMULATE.  A point whose
+ *   (level, box) does not address a given array is skipped and reported by
+ *   fmm_sync_status (FMM_EDEVICE).
+ * fmm_l2p_adjoint: G_l[b][n] += conj(((z_j - x_b) / r_l)^n / r_l) cot_j for every
+ *   point (FP32 atomic additions, order-dependent in the last bits); cot:
+ *   device complex64 [n]; G_levels like L_levels (accumulated into). */
+int fmm_l2p(int32_t p, int64_t n, const double* z, const int32_t* lev, const int64_t* box,
+            const void* const* L_levels, int32_t max_level, void* phi, int32_t flags, void* stream);
+int fmm_l2p_adjoint(int32_t p, int64_t n, const double* z, const int32_t* lev, const int64_t* box,
+                    const void* cot, void* const* G_levels, int32_t max_level, void* stream);
+
+/* fmm_p2m_adjoint: for the P2M of fmm_p2m at `level` (M~_b[k] = sum_i c_i d_i^k,
+ *   d_i = (y_i - x_b) / r_l) and G = dJ/dM~ of a real objective J, the gradient
+ *   in the point positions:
+ *     grad[i] (+)= (Re, Im) of sum_k G[b_i][k] conj(c_i k d_i^(k-1) / r_l) = (dJ/dx_i, dJ/dy_i).
+ *   xy, c: device float64 as fmm_p2m; G: device complex64 [4^level][p];
+ *   grad: device float64 [n][2].  flags: FMM_ACCUMULATE. */
+int fmm_p2m_adjoint(int32_t level, int32_t p, const double* xy, const double* c, int64_t n,
+                    const void* G, double* grad, int32_t flags, void* stream);
+
 /* fgt_p2h: FGT Hermite coefficients of every box of a 2^g grid (Eq. A_alpha),
  *   A_b[a1][a2] (+)= sum_{j in box b} q_j t1^a1 t2^a2 / (a1! a2!),
  *   t = (x_j - s_b) / (sqrt(2) sigma), s_b the box centre, a1, a2 < p.

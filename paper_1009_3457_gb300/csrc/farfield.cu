@@ -1,0 +1,325 @@
+// farfield.cu -- the far-field stages around the M2L path on the device, in
+// radius-scaled units (Sec. 2.1 stages 3-4), with the adjoints that carry a
+// gradient back through them:
+//   L2L   L~c[j] = sum_{n>=j} C(n,j) u^(n-j) 2^-(j+1) L~p[n],  u = (x_c - x_P) / r_P = (+-1/4, +-1/4)
+//   L2P   phi(z) = (1/r) sum_n L~[leaf][n] w^n,  w = (z - x_leaf) / r
+//   P2M^T grad of sum_k <G_k, M~_k(y)> in the point positions, M~_k = sum_i c_i d_i^k, d = (y - x_b)/r
+// The L2L entries (binomials, powers of (+-1 +- i)/4, powers of 2) are exact
+// in FP32; L2P forms w in FP64.  Adjoints are conjugate transposes (the
+// gradient of a real objective in PyTorch's convention for complex tensors).
+#include "common.cuh"
+
+namespace fmmgb {
+
+// One thread per (child box, j): Lc[child][j] (+)= sum_n T_c[j][n] Lp[parent][n].
+__global__ void l2l_kernel(int child_level, int p, const float2* __restrict__ Lp, float2* __restrict__ Lc,
+                           int accumulate)
+{
+    const int side = 1 << child_level, ps = side >> 1;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)side * side * p) return;
+    const int j = (int)(idx % p);
+    const int64_t b = idx / p;
+    const int ix = (int)(b % side), iy = (int)(b / side);
+    const float ur = (ix & 1) ? 0.25f : -0.25f, ui = (iy & 1) ? 0.25f : -0.25f;
+    const float2* lp = Lp + ((size_t)(iy >> 1) * ps + (ix >> 1)) * p;
+    // n from j upward: C(n, j) u^(n-j)
+    float sr = 0.f, si = 0.f, binom = 1.f, pr = 1.f, pim = 0.f;
+    for (int n = j; n < p; ++n) {
+        const float2 v = lp[n];
+        const float tr = pr * v.x - pim * v.y, ti = pr * v.y + pim * v.x;
+        sr = fmaf(binom, tr, sr);
+        si = fmaf(binom, ti, si);
+        binom = binom * (float)(n + 1) / (float)(n + 1 - j);  // C(n+1, j) = C(n, j) (n+1) / (n+1-j)
+        const float nr = pr * ur - pim * ui;
+        pim = pr * ui + pim * ur;
+        pr = nr;
+    }
+    const float sc = ldexpf(1.f, -(j + 1));
+    float2* out = Lc + (size_t)b * p + j;
+    float2 o = make_float2(sc * sr, sc * si);
+    if (accumulate) {
+        o.x += out->x;
+        o.y += out->y;
+    }
+    *out = o;
+}
+
+// Conjugate transpose: one thread per (parent box, n):
+//   Wp[parent][n] (+)= sum_{children c} sum_{j<=n} conj(T_c[j][n]) Wc[child][j].
+__global__ void l2l_adjoint_kernel(int child_level, int p, const float2* __restrict__ Wc, float2* __restrict__ Wp,
+                                   int accumulate)
+{
+    const int side = 1 << child_level, ps = side >> 1;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)ps * ps * p) return;
+    const int n = (int)(idx % p);
+    const int64_t pb = idx / p;
+    const int px = (int)(pb % ps), py = (int)(pb / ps);
+    float sr = 0.f, si = 0.f;
+    for (int cy = 0; cy < 2; ++cy)
+        for (int cx = 0; cx < 2; ++cx) {
+            const float ur = cx ? 0.25f : -0.25f, ui = cy ? 0.25f : -0.25f;
+            const float2* wc = Wc + ((size_t)(2 * py + cy) * side + (2 * px + cx)) * p;
+            // j from n down to 0: entry C(n, j) u^(n-j) 2^-(j+1), conjugated
+            float binom = 1.f, pr = 1.f, pim = 0.f;  // C(n, n), u^0
+            for (int j = n; j >= 0; --j) {
+                const float sc = binom * ldexpf(1.f, -(j + 1));
+                const float2 w = wc[j];
+                // conj(u^(n-j)) * w
+                const float tr = pr * w.x + pim * w.y, ti = pr * w.y - pim * w.x;
+                sr = fmaf(sc, tr, sr);
+                si = fmaf(sc, ti, si);
+                if (j > 0) binom = binom * (float)j / (float)(n - j + 1);  // C(n, j-1) = C(n, j) j / (n-j+1)
+                const float nr = pr * ur - pim * ui;
+                pim = pr * ui + pim * ur;
+                pr = nr;
+            }
+        }
+    float2* out = Wp + (size_t)pb * p + n;
+    float2 o = make_float2(sr, si);
+    if (accumulate) {
+        o.x += out->x;
+        o.y += out->y;
+    }
+    *out = o;
+}
+
+struct LevelPtrs {
+    const float2* L[FMM_MAX_LEVEL + 1];
+};
+struct LevelOutPtrs {
+    float2* G[FMM_MAX_LEVEL + 1];
+};
+
+// One thread per point: phi_j (+)= (1/r) sum_n L~[leaf][n] w^n (Horner in FP64).
+// A point's (level, box) must address an existing array; otherwise it is
+// skipped and the device error word records the failed check.
+__device__ __forceinline__ bool leaf_ok(int l, int64_t b, const void* const* tab, int max_level, int* err)
+{
+    const bool ok = l >= 0 && l <= max_level && b >= 0 && b < ((int64_t)1 << (2 * l)) && tab[l] != nullptr;
+    if (!ok && l >= 2) atomicOr(err, DEV_ERR_CHECK);
+    return ok;
+}
+
+__global__ void l2p_kernel(int p, int64_t n, const double* __restrict__ z, const int32_t* __restrict__ lev,
+                           const int64_t* __restrict__ box, LevelPtrs Ls, int max_level, float2* __restrict__ phi,
+                           int accumulate, int* err)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int l = lev[i];
+    double ar = 0.0, ai = 0.0;
+    if (l >= 2 && leaf_ok(l, box[i], (const void* const*)Ls.L, max_level, err)) {
+        const int side = 1 << l;
+        const int64_t b = box[i];
+        const double wr = z[2 * i] * side - ((double)(b % side) + 0.5);
+        const double wi = z[2 * i + 1] * side - ((double)(b / side) + 0.5);
+        const float2* lb = Ls.L[l] + (size_t)b * p;
+        for (int k = p - 1; k >= 0; --k) {
+            const double tr = ar * wr - ai * wi + (double)lb[k].x;
+            ai = ar * wi + ai * wr + (double)lb[k].y;
+            ar = tr;
+        }
+        ar *= side;
+        ai *= side;
+    }
+    float2 o = make_float2((float)ar, (float)ai);
+    if (accumulate) {
+        o.x += phi[i].x;
+        o.y += phi[i].y;
+    }
+    phi[i] = o;
+}
+
+// Conjugate transpose of L2P: G[leaf][n] += conj(w^n / r) c_j (FP32 atomic additions).
+__global__ void l2p_adjoint_kernel(int p, int64_t n, const double* __restrict__ z, const int32_t* __restrict__ lev,
+                                   const int64_t* __restrict__ box, const float2* __restrict__ cot, LevelOutPtrs Gs,
+                                   int max_level, int* err)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int l = lev[i];
+    if (l < 2 || !leaf_ok(l, box[i], (const void* const*)Gs.G, max_level, err)) return;
+    const int side = 1 << l;
+    const int64_t b = box[i];
+    const double wr = z[2 * i] * side - ((double)(b % side) + 0.5);
+    const double wi = -(z[2 * i + 1] * side - ((double)(b / side) + 0.5));  // conj(w)
+    const double cr = (double)cot[i].x * side, ci = (double)cot[i].y * side;
+    double pr = cr, pi = ci;  // conj(w)^k c side
+    float2* gb = Gs.G[l] + (size_t)b * p;
+    for (int k = 0; k < p; ++k) {
+        atomicAdd(&gb[k].x, (float)pr);
+        atomicAdd(&gb[k].y, (float)pi);
+        const double t = pr * wr - pi * wi;
+        pi = pr * wi + pi * wr;
+        pr = t;
+    }
+}
+
+// P2M adjoint in the positions: grad_i (+)= sum_k G[b][k] conj(c_i k d^(k-1) / r),
+// returned as (d/dx, d/dy) = (Re, Im) of that sum.
+__global__ void p2m_adjoint_kernel(int level, int p, const double* __restrict__ xy, const double* __restrict__ c,
+                                   int64_t n, const float2* __restrict__ G, double* __restrict__ grad, int accumulate)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int side = 1 << level;
+    const double x = xy[2 * i] * side, y = xy[2 * i + 1] * side;
+    int ix = (int)floor(x), iy = (int)floor(y);
+    ix = ix < 0 ? 0 : (ix > side - 1 ? side - 1 : ix);
+    iy = iy < 0 ? 0 : (iy > side - 1 ? side - 1 : iy);
+    const double dr = x - (ix + 0.5), di = -(y - (iy + 0.5));  // conj(d)
+    const float2* gb = G + ((size_t)iy * side + ix) * p;
+    // sum_k G_k k conj(d)^(k-1)
+    double sr = 0.0, si = 0.0, pr = 1.0, pi = 0.0;
+    for (int k = 1; k < p; ++k) {
+        const double gr = (double)gb[k].x * k, gi = (double)gb[k].y * k;
+        sr += gr * pr - gi * pi;
+        si += gr * pi + gi * pr;
+        const double t = pr * dr - pi * di;
+        pi = pr * di + pi * dr;
+        pr = t;
+    }
+    const double f = c[i] * side;  // c_i / r
+    if (accumulate) {
+        grad[2 * i] += f * sr;
+        grad[2 * i + 1] += f * si;
+    } else {
+        grad[2 * i] = f * sr;
+        grad[2 * i + 1] = f * si;
+    }
+}
+
+int launch_l2l(int child_level, int p, const float2* Lp, float2* Lc, bool acc, bool adjoint, cudaStream_t st)
+{
+    const int64_t side = (int64_t)1 << child_level;
+    const int64_t total = (adjoint ? side * side / 4 : side * side) * p;
+    const unsigned blocks = (unsigned)((total + 255) / 256);
+    if (adjoint)
+        l2l_adjoint_kernel<<<blocks, 256, 0, st>>>(child_level, p, Lp, Lc, acc ? 1 : 0);
+    else
+        l2l_kernel<<<blocks, 256, 0, st>>>(child_level, p, Lp, Lc, acc ? 1 : 0);
+    FMM_CUDA_TRY(cudaGetLastError());
+    return FMM_OK;
+}
+
+int launch_l2p(int p, int64_t n, const double* z, const int32_t* lev, const int64_t* box, const void* const* L,
+               int max_level, void* phi, bool acc, bool adjoint, cudaStream_t st)
+{
+    if (n == 0) return FMM_OK;
+    int* err = nullptr;
+    int rc = device_error_word(&err);
+    if (rc) return rc;
+    const unsigned blocks = (unsigned)((n + 255) / 256);
+    if (!adjoint) {
+        LevelPtrs Ls{};
+        for (int l = 0; l <= max_level; ++l) Ls.L[l] = (const float2*)L[l];
+        l2p_kernel<<<blocks, 256, 0, st>>>(p, n, z, lev, box, Ls, max_level, (float2*)phi, acc ? 1 : 0, err);
+    } else {
+        LevelOutPtrs Gs{};
+        for (int l = 0; l <= max_level; ++l) Gs.G[l] = (float2*)L[l];
+        l2p_adjoint_kernel<<<blocks, 256, 0, st>>>(p, n, z, lev, box, (const float2*)phi, Gs, max_level, err);
+    }
+    FMM_CUDA_TRY(cudaGetLastError());
+    return FMM_OK;
+}
+
+int launch_p2m_adjoint(int level, int p, const double* xy, const double* c, int64_t n, const float2* G, double* grad,
+                       bool acc, cudaStream_t st)
+{
+    if (n == 0) return FMM_OK;
+    p2m_adjoint_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(level, p, xy, c, n, G, grad, acc ? 1 : 0);
+    FMM_CUDA_TRY(cudaGetLastError());
+    return FMM_OK;
+}
+
+}  // namespace fmmgb
+
+using namespace fmmgb;
+
+static int far_common(const char* who, int32_t p, const void* a, const void* b)
+{
+    if (p < 1 || p > 64) return fail(FMM_EINVAL, "%s: p = %d outside 1..64", who, p);
+    if (!a || !b) return fail(FMM_EINVAL, "%s: NULL pointer", who);
+    if (((uintptr_t)a & 7) || ((uintptr_t)b & 7)) return fail(FMM_EINVAL, "%s: pointers must be 8-byte aligned", who);
+    return FMM_OK;
+}
+
+extern "C" {
+
+int fmm_l2l(int32_t child_level, int32_t p, const void* Lp, void* Lc, int32_t flags, void* stream)
+{
+    clear_error();
+    if (child_level < 1 || child_level > FMM_MAX_LEVEL)
+        return fail(FMM_EINVAL, "fmm_l2l: child_level %d outside 1..%d", child_level, FMM_MAX_LEVEL);
+    if (int rc = far_common("fmm_l2l", p, Lp, Lc)) return rc;
+    if (flags & ~FMM_ACCUMULATE) return fail(FMM_EINVAL, "fmm_l2l: unknown flags 0x%x", flags);
+    return launch_l2l(child_level, p, (const float2*)Lp, (float2*)Lc, (flags & FMM_ACCUMULATE) != 0, false,
+                      (cudaStream_t)stream);
+}
+
+int fmm_l2l_adjoint(int32_t child_level, int32_t p, const void* Wc, void* Wp, int32_t flags, void* stream)
+{
+    clear_error();
+    if (child_level < 1 || child_level > FMM_MAX_LEVEL)
+        return fail(FMM_EINVAL, "fmm_l2l_adjoint: child_level %d outside 1..%d", child_level, FMM_MAX_LEVEL);
+    if (int rc = far_common("fmm_l2l_adjoint", p, Wc, Wp)) return rc;
+    if (flags & ~FMM_ACCUMULATE) return fail(FMM_EINVAL, "fmm_l2l_adjoint: unknown flags 0x%x", flags);
+    return launch_l2l(child_level, p, (const float2*)Wc, (float2*)Wp, (flags & FMM_ACCUMULATE) != 0, true,
+                      (cudaStream_t)stream);
+}
+
+static int l2p_common(const char* who, int32_t p, int64_t n, const double* z, const int32_t* lev, const int64_t* box,
+                      const void* const* L, int32_t max_level, const void* phi)
+{
+    if (p < 1 || p > 64) return fail(FMM_EINVAL, "%s: p = %d outside 1..64", who, p);
+    if (n < 0) return fail(FMM_EINVAL, "%s: n < 0", who);
+    if (max_level < 0 || max_level > FMM_MAX_LEVEL)
+        return fail(FMM_EINVAL, "%s: max_level %d outside 0..%d", who, max_level, FMM_MAX_LEVEL);
+    if (!L) return fail(FMM_EINVAL, "%s: NULL level array", who);
+    if (n > 0 && (!z || !lev || !box || !phi)) return fail(FMM_EINVAL, "%s: NULL pointer", who);
+    if (((uintptr_t)z & 7) || ((uintptr_t)phi & 7) || ((uintptr_t)box & 7) || ((uintptr_t)lev & 3))
+        return fail(FMM_EINVAL, "%s: misaligned pointer", who);
+    for (int l = 0; l <= max_level; ++l)
+        if ((uintptr_t)L[l] & 7) return fail(FMM_EINVAL, "%s: level %d array misaligned", who, l);
+    return FMM_OK;
+}
+
+int fmm_l2p(int32_t p, int64_t n, const double* z, const int32_t* lev, const int64_t* box, const void* const* L_levels,
+            int32_t max_level, void* phi, int32_t flags, void* stream)
+{
+    clear_error();
+    if (int rc = l2p_common("fmm_l2p", p, n, z, lev, box, L_levels, max_level, phi)) return rc;
+    if (flags & ~FMM_ACCUMULATE) return fail(FMM_EINVAL, "fmm_l2p: unknown flags 0x%x", flags);
+    return launch_l2p(p, n, z, lev, box, L_levels, max_level, phi, (flags & FMM_ACCUMULATE) != 0, false,
+                      (cudaStream_t)stream);
+}
+
+int fmm_l2p_adjoint(int32_t p, int64_t n, const double* z, const int32_t* lev, const int64_t* box, const void* cot,
+                    void* const* G_levels, int32_t max_level, void* stream)
+{
+    clear_error();
+    if (int rc = l2p_common("fmm_l2p_adjoint", p, n, z, lev, box, (const void* const*)G_levels, max_level, cot))
+        return rc;
+    return launch_l2p(p, n, z, lev, box, (const void* const*)G_levels, max_level, const_cast<void*>(cot), true, true,
+                      (cudaStream_t)stream);
+}
+
+int fmm_p2m_adjoint(int32_t level, int32_t p, const double* xy, const double* c, int64_t n, const void* G,
+                    double* grad, int32_t flags, void* stream)
+{
+    clear_error();
+    if (level < 0 || level > FMM_MAX_LEVEL)
+        return fail(FMM_EINVAL, "fmm_p2m_adjoint: level %d outside 0..%d", level, FMM_MAX_LEVEL);
+    if (p < 1 || p > 64) return fail(FMM_EINVAL, "fmm_p2m_adjoint: p = %d outside 1..64", p);
+    if (n < 0) return fail(FMM_EINVAL, "fmm_p2m_adjoint: n < 0");
+    if (!G || (n > 0 && (!xy || !c || !grad))) return fail(FMM_EINVAL, "fmm_p2m_adjoint: NULL pointer");
+    if (((uintptr_t)G & 7) || ((uintptr_t)xy & 7) || ((uintptr_t)c & 7) || ((uintptr_t)grad & 7))
+        return fail(FMM_EINVAL, "fmm_p2m_adjoint: misaligned pointer");
+    if (flags & ~FMM_ACCUMULATE) return fail(FMM_EINVAL, "fmm_p2m_adjoint: unknown flags 0x%x", flags);
+    return launch_p2m_adjoint(level, p, xy, c, n, (const float2*)G, grad, (flags & FMM_ACCUMULATE) != 0,
+                              (cudaStream_t)stream);
+}
+
+}  // extern "C"

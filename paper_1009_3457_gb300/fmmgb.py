@@ -94,6 +94,11 @@ SIGNATURES = {
     "fmm_batch_destroy": (None, [_vp, _vp]),
     "fmm_m2l_batched": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(_i32), _i32, ctypes.POINTER(_vp),
                                        ctypes.POINTER(_vp), _i32, _i32, _vp]),
+    "fmm_l2l": (ctypes.c_int, [_i32, _i32, _vp, _vp, _i32, _vp]),
+    "fmm_l2l_adjoint": (ctypes.c_int, [_i32, _i32, _vp, _vp, _i32, _vp]),
+    "fmm_l2p": (ctypes.c_int, [_i32, _i64, _vp, _vp, _vp, ctypes.POINTER(_vp), _i32, _vp, _i32, _vp]),
+    "fmm_l2p_adjoint": (ctypes.c_int, [_i32, _i64, _vp, _vp, _vp, _vp, ctypes.POINTER(_vp), _i32, _vp]),
+    "fmm_p2m_adjoint": (ctypes.c_int, [_i32, _i32, _vp, _vp, _i64, _vp, _vp, _i32, _vp]),
     "fmm_p2m": (ctypes.c_int, [_i32, _i32, _vp, _vp, _i64, _vp, _i32, _vp]),
     "fmm_m2m": (ctypes.c_int, [_i32, _i32, _vp, _vp, _i32, _vp]),
     "fgt_h2t": (ctypes.c_int, [_i32, _i32, _i32, _d, _vp, _vp, _vp, _i32, _vp]),
@@ -308,6 +313,39 @@ def fmm_p2m(level: int, p: int, xy, c, M, accumulate: bool = False, stream=None)
 def fmm_m2m(child_level: int, p: int, Mc, Mp, accumulate: bool = False, stream=None):
     _check(load().fmm_m2m(child_level, p, _ptr(Mc), _ptr(Mp), FMM_ACCUMULATE if accumulate else 0,
                           _stream(stream)))
+
+
+def fmm_l2l(child_level: int, p: int, Lp, Lc, accumulate: bool = False, stream=None):
+    _check(load().fmm_l2l(child_level, p, _ptr(Lp), _ptr(Lc), FMM_ACCUMULATE if accumulate else 0, _stream(stream)))
+
+
+def fmm_l2l_adjoint(child_level: int, p: int, Wc, Wp, accumulate: bool = False, stream=None):
+    _check(load().fmm_l2l_adjoint(child_level, p, _ptr(Wc), _ptr(Wp), FMM_ACCUMULATE if accumulate else 0,
+                                  _stream(stream)))
+
+
+def _level_table(arrays, max_level):
+    """Host array of max_level + 1 device pointers from {level: tensor} (NULL where absent)."""
+    return (_vp * (max_level + 1))(*[_ptr(arrays[l]) if l in arrays else None for l in range(max_level + 1)])
+
+
+def fmm_l2p(p: int, z, lev, box, L_levels: dict, max_level: int, phi, accumulate: bool = False, stream=None):
+    """phi (complex64 [n]) from the LEs of each point's (lev, box); L_levels: {level: [4^l, p] complex64}."""
+    n = 0 if lev is None else lev.numel()
+    _check(load().fmm_l2p(p, n, _ptr(z), _ptr(lev), _ptr(box), _level_table(L_levels, max_level), max_level,
+                          _ptr(phi), FMM_ACCUMULATE if accumulate else 0, _stream(stream)))
+
+
+def fmm_l2p_adjoint(p: int, z, lev, box, cot, G_levels: dict, max_level: int, stream=None):
+    n = 0 if lev is None else lev.numel()
+    _check(load().fmm_l2p_adjoint(p, n, _ptr(z), _ptr(lev), _ptr(box), _ptr(cot), _level_table(G_levels, max_level),
+                                  max_level, _stream(stream)))
+
+
+def fmm_p2m_adjoint(level: int, p: int, xy, c, G, grad, accumulate: bool = False, stream=None):
+    n = 0 if c is None else c.numel()
+    _check(load().fmm_p2m_adjoint(level, p, _ptr(xy), _ptr(c), n, _ptr(G), _ptr(grad),
+                                  FMM_ACCUMULATE if accumulate else 0, _stream(stream)))
 
 
 def fgt_h2t(grid_log2: int, n_cut: int, p: int, sigma: float, A, C, work=None, accumulate: bool = False,

@@ -193,3 +193,22 @@ def test_adaptive_tree_arguments(fmm, gmm_points):
     outs = (vp * 4)(*[(1 << 28) * (k + 1) for k in range(4)])
     assert lib.fmm_batch_create((vp * 1)(tb.handle), (i32 * 1)(8), 1, ptrs, outs, 0, 0, None,
                                 ctypes.byref(h)) == fmm.FMM_EUNSUPPORTED
+
+
+def test_far_field_entry_points_reject_bad_arguments(fmm):
+    import ctypes
+
+    lib = fmm.load()
+    vp = ctypes.c_void_p
+    assert lib.fmm_l2l(0, 8, 64, 4096, 0, None) == fmm.FMM_EINVAL          # child level 0
+    assert lib.fmm_l2l(3, 0, 64, 4096, 0, None) == fmm.FMM_EINVAL          # p
+    assert lib.fmm_l2l(3, 8, None, 4096, 0, None) == fmm.FMM_EINVAL
+    assert lib.fmm_l2l(3, 8, 68, 4096, 0, None) == fmm.FMM_EINVAL          # misaligned
+    assert lib.fmm_l2l_adjoint(3, 8, 64, 4096, 2, None) == fmm.FMM_EINVAL  # flags
+    tab = (vp * 4)(None, None, None, 4096)
+    assert lib.fmm_l2p(8, 10, 64, 128, 256, tab, 15, 512, 0, None) == fmm.FMM_EINVAL   # max_level
+    assert lib.fmm_l2p(8, 10, None, 128, 256, tab, 3, 512, 0, None) == fmm.FMM_EINVAL  # z
+    assert lib.fmm_l2p(8, 10, 64, 128, 260, tab, 3, 512, 0, None) == fmm.FMM_EINVAL   # box misaligned
+    assert lib.fmm_l2p_adjoint(8, 10, 64, 128, 256, None, tab, 3, None) == fmm.FMM_EINVAL
+    assert lib.fmm_p2m_adjoint(3, 8, 64, 128, 10, None, 256, 0, None) == fmm.FMM_EINVAL
+    assert lib.fmm_p2m_adjoint(3, 65, 64, 128, 10, 512, 256, 0, None) == fmm.FMM_EINVAL
