@@ -323,11 +323,17 @@ int fgt_h2t_noalloc(int32_t grid_log2, int32_t n_cut, int32_t p, double sigma, c
  *   [4^level][p].  Uses FP32 atomic additions (result order-dependent in the
  *   last bits).  flags: FMM_ACCUMULATE or 0.
  * fmm_m2m: parent MEs from child MEs, M_j = sum_{k<=j} C(j,k)(x_c - x_P)^(j-k) m_k,
- *   in scaled units.  Mc: [4^child_level][p], Mp: [4^(child_level-1)][p].
+ *   in scaled units (FP32; the scaled entries are exact in FP32).
+ *   Mc: [4^child_level][p], Mp: [4^(child_level-1)][p].
  * ------------------------------------------------------------------------- */
 int fmm_p2m(int32_t level, int32_t p, const double* xy, const double* c, int64_t n,
             void* M, int32_t flags, void* stream);
 int fmm_m2m(int32_t child_level, int32_t p, const void* Mc, void* Mp, int32_t flags, void* stream);
+/* fmm_m2m_adjoint: conjugate transpose of fmm_m2m:
+ *   Wc[child][k] (+)= sum_{j>=k} conj(C(j,k) z^(j-k) 2^-k) Wp[parent][j],
+ *   z = (x_child - x_parent) / r_parent.  Wp: [4^(child_level-1)][p], Wc: [4^child_level][p].
+ *   flags: FMM_ACCUMULATE. */
+int fmm_m2m_adjoint(int32_t child_level, int32_t p, const void* Wp, void* Wc, int32_t flags, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Far-field stages around the M2L path (Sec. 2.1 stages 3-4), scaled units,

@@ -695,6 +695,19 @@ int fmm_p2m(int32_t level, int32_t p, const double* xy, const double* c, int64_t
     return launch_p2m(level, p, xy, c, n, (float2*)M, (flags & FMM_ACCUMULATE) != 0, (cudaStream_t)stream);
 }
 
+int fmm_m2m_adjoint(int32_t child_level, int32_t p, const void* Wp, void* Wc, int32_t flags, void* stream)
+{
+    clear_error();
+    if (child_level < 1 || child_level > FMM_MAX_LEVEL)
+        return fail(FMM_EINVAL, "fmm_m2m_adjoint: child_level %d outside 1..%d", child_level, FMM_MAX_LEVEL);
+    if (p < 1 || p > 64) return fail(FMM_EINVAL, "fmm_m2m_adjoint: p = %d outside 1..64", p);
+    if (!Wp || !Wc) return fail(FMM_EINVAL, "fmm_m2m_adjoint: NULL pointer");
+    if (((uintptr_t)Wp & 7) || ((uintptr_t)Wc & 7)) return fail(FMM_EINVAL, "fmm_m2m_adjoint: misaligned pointer");
+    if (flags & ~FMM_ACCUMULATE) return fail(FMM_EINVAL, "fmm_m2m_adjoint: unknown flags 0x%x", flags);
+    return launch_m2m_adjoint(child_level, p, (const float2*)Wp, (float2*)Wc, (flags & FMM_ACCUMULATE) != 0,
+                              (cudaStream_t)stream);
+}
+
 int fmm_m2m(int32_t child_level, int32_t p, const void* Mc, void* Mp, int32_t flags, void* stream)
 {
     clear_error();

@@ -140,6 +140,7 @@ int fgt_check_args(const char* who, int g, int ncut, int p, double sigma, const 
 int launch_p2m(int level, int p, const double* xy, const double* c, int64_t n, float2* M, bool accumulate,
                cudaStream_t st);
 int launch_m2m(int child_level, int p, const float2* Mc, float2* Mp, bool accumulate, cudaStream_t st);
+int launch_m2m_adjoint(int child_level, int p, const float2* Wp, float2* Wc, bool accumulate, cudaStream_t st);
 int launch_fgt_p2h(int g, int p, double sigma, const double* x, const double* q, int64_t n, float* A, bool acc,
                    cudaStream_t st);
 

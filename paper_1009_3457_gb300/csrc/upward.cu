@@ -1,7 +1,8 @@
 // upward.cu -- device construction of M2L inputs (upward sweep, Sec. 2.1
 // stage 2): P2M of particles into the boxes of one level and M2M from a level
-// to its parents, in radius-scaled units.  Support for the translation path,
-// not part of it; kept simple (atomic accumulation).
+// to its parents (and M2M's conjugate transpose, for gradients), in
+// radius-scaled units.  Support for the translation path, not part of it;
+// kept simple (atomic accumulation in P2M).
 #include "common.cuh"
 
 namespace fmmgb {
@@ -31,6 +32,7 @@ __global__ void p2m_kernel(int level, int p, const double* __restrict__ xy, cons
 
 // Scaled M2M: parent box side R = 2r, child offset z = (x_c - x_P)/R = (+-1/4, +-1/4):
 //   M~P_j = sum_{k<=j} C(j,k) z^(j-k) 2^-k M~c_k, summed over the 4 children.
+// The entries (binomials, powers of (+-1 +- i)/4, powers of 2) are exact in FP32.
 __global__ void m2m_kernel(int child_level, int p, const float2* __restrict__ Mc, float2* __restrict__ Mp,
                            int accumulate)
 {
@@ -41,33 +43,66 @@ __global__ void m2m_kernel(int child_level, int p, const float2* __restrict__ Mc
     const int64_t pb = idx / p;
     const int px = (int)(pb % np), py = (int)(pb / np);
     const int nc = 2 * np;
-    double sr = 0.0, si = 0.0;
+    float sr = 0.f, si = 0.f;
     for (int cyy = 0; cyy < 2; ++cyy)
         for (int cxx = 0; cxx < 2; ++cxx) {
-            const double zr = cxx ? 0.25 : -0.25, zi = cyy ? 0.25 : -0.25;
+            const float zr = cxx ? 0.25f : -0.25f, zi = cyy ? 0.25f : -0.25f;
             const float2* mc = Mc + ((size_t)(2 * py + cyy) * nc + (2 * px + cxx)) * p;
             // k from j down to 0: term C(j,k) z^(j-k) 2^-k m_k
-            double binom = 1.0;          // C(j, k) for k = j
-            double zpr = 1.0, zpi = 0.0;  // z^(j-k)
+            float binom = 1.f;          // C(j, k) for k = j
+            float zpr = 1.f, zpi = 0.f;  // z^(j-k)
             for (int k = j; k >= 0; --k) {
-                const double sc = binom * ldexp(1.0, -k);
-                const double tr = zpr * mc[k].x - zpi * mc[k].y;
-                const double ti = zpr * mc[k].y + zpi * mc[k].x;
-                sr += sc * tr;
-                si += sc * ti;
-                // next k-1: C(j,k-1) = C(j,k) * k / (j-k+1); z^(j-k+1)
-                if (k > 0) binom = binom * k / (double)(j - k + 1);
-                const double nr = zpr * zr - zpi * zi;
+                const float sc = binom * ldexpf(1.f, -k);
+                const float2 m = mc[k];
+                sr = fmaf(sc, zpr * m.x - zpi * m.y, sr);
+                si = fmaf(sc, zpr * m.y + zpi * m.x, si);
+                if (k > 0) binom = binom * (float)k / (float)(j - k + 1);  // C(j, k-1)
+                const float nr = zpr * zr - zpi * zi;
                 zpi = zpr * zi + zpi * zr;
                 zpr = nr;
             }
         }
     float2* out = Mp + (size_t)pb * p + j;
+    float2 o = make_float2(sr, si);
     if (accumulate) {
-        sr += out->x;
-        si += out->y;
+        o.x += out->x;
+        o.y += out->y;
     }
-    *out = make_float2((float)sr, (float)si);
+    *out = o;
+}
+
+// Conjugate transpose of M2M: one thread per (child box, k):
+//   Wc[child][k] (+)= sum_{j>=k} conj(C(j,k) z^(j-k) 2^-k) WP[parent][j].
+__global__ void m2m_adjoint_kernel(int child_level, int p, const float2* __restrict__ Wp, float2* __restrict__ Wc,
+                                   int accumulate)
+{
+    const int side = 1 << child_level, np = side >> 1;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)side * side * p) return;
+    const int k = (int)(idx % p);
+    const int64_t b = idx / p;
+    const int ix = (int)(b % side), iy = (int)(b / side);
+    const float zr = (ix & 1) ? 0.25f : -0.25f, zi = (iy & 1) ? 0.25f : -0.25f;
+    const float2* wp = Wp + ((size_t)(iy >> 1) * np + (ix >> 1)) * p;
+    float sr = 0.f, si = 0.f, binom = 1.f, pr = 1.f, pim = 0.f;  // C(j, k) for j = k; z^(j-k)
+    for (int j = k; j < p; ++j) {
+        const float2 w = wp[j];
+        // conj(z^(j-k)) w
+        sr = fmaf(binom, pr * w.x + pim * w.y, sr);
+        si = fmaf(binom, pr * w.y - pim * w.x, si);
+        binom = binom * (float)(j + 1) / (float)(j + 1 - k);  // C(j+1, k)
+        const float nr = pr * zr - pim * zi;
+        pim = pr * zi + pim * zr;
+        pr = nr;
+    }
+    const float sc = ldexpf(1.f, -k);
+    float2* out = Wc + (size_t)b * p + k;
+    float2 o = make_float2(sc * sr, sc * si);
+    if (accumulate) {
+        o.x += out->x;
+        o.y += out->y;
+    }
+    *out = o;
 }
 
 // FGT Hermite coefficients of every box of a 2^g grid (Eq. A_alpha):
@@ -113,6 +148,15 @@ int launch_p2m(int level, int p, const double* xy, const double* c, int64_t n, f
     if (n == 0) return FMM_OK;
     const int64_t blocks = (n + 255) / 256;
     p2m_kernel<<<(unsigned)blocks, 256, 0, st>>>(level, p, xy, c, n, M);
+    FMM_CUDA_TRY(cudaGetLastError());
+    return FMM_OK;
+}
+
+int launch_m2m_adjoint(int child_level, int p, const float2* Wp, float2* Wc, bool acc, cudaStream_t st)
+{
+    const int64_t side = (int64_t)1 << child_level;
+    const int64_t total = side * side * p;
+    m2m_adjoint_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(child_level, p, Wp, Wc, acc ? 1 : 0);
     FMM_CUDA_TRY(cudaGetLastError());
     return FMM_OK;
 }

@@ -7,13 +7,15 @@ phi_far(z) the local expansion of z's leaf, after M2L over the lists of every
 level 2..depth and L2L down the tree, evaluated at z.  Every stage runs in the
 library's kernels, forward and backward:
 
-    forward   fmm_p2m (each level)  -> fmm_m2l_levels -> fmm_l2l (coarse to fine) -> fmm_l2p
-    backward  fmm_l2p_adjoint -> fmm_l2l_adjoint (fine to coarse) -> fmm_m2l_adjoint_levels
-              (conjugate) -> fmm_p2m_adjoint (each level), giving dJ/dx, dJ/dy per point.
+    forward   fmm_p2m (finest level) -> fmm_m2m (upward) -> fmm_m2l_levels -> fmm_l2l (downward)
+              -> fmm_l2p
+    backward  fmm_l2p_adjoint -> fmm_l2l_adjoint (upward) -> fmm_m2l_adjoint_levels (conjugate)
+              -> fmm_m2m_adjoint (downward) -> fmm_p2m_adjoint, giving dJ/dx, dJ/dy per point.
 
-Each point is deposited in its box at every level; on an adaptive tree the M2L
-reads existing boxes only, so a point contributes down to its leaf and no
-further, which is the frozen-leaf assignment.  Units at the library boundary
+Every level's MEs come from the finest level's P2M by M2M, which equals the
+P2M of all points in each box (exact for truncated series); on an adaptive tree
+the M2L reads existing boxes only, so a point contributes down to its leaf and
+no further, which is the frozen-leaf assignment.  Units at the library boundary
 are radius-scaled: M~_k = m_k / r^k, L~_n = l_n r^(n+1).
 """
 from __future__ import annotations
@@ -48,8 +50,9 @@ class FarFieldObjective(torch.autograd.Function):
         dev = xy.device
         levels = list(range(2, L + 1))
         Ms = [torch.empty((4 ** l, p), dtype=torch.complex64, device=dev) for l in levels]
-        for l, M in zip(levels, Ms):
-            fmmgb.fmm_p2m(l, p, xy, c, M)
+        fmmgb.fmm_p2m(L, p, xy, c, Ms[-1])  # finest level, then M2M upward (exact for truncated series)
+        for i in range(len(levels) - 1, 0, -1):
+            fmmgb.fmm_m2m(levels[i], p, Ms[i], Ms[i - 1])
         Ls = [torch.zeros_like(M) for M in Ms]
         fmmgb.fmm_m2l_levels(tree, 2, p, Ms, Ls)
         for i in range(1, len(levels)):
@@ -74,9 +77,10 @@ class FarFieldObjective(torch.autograd.Function):
             fmmgb.fmm_l2l_adjoint(levels[i], p, Gs[i], Gs[i - 1], accumulate=True)
         Ws = [torch.zeros_like(G) for G in Gs]
         fmmgb.fmm_m2l_adjoint_levels(tree, 2, p, Gs, Ws, conj=True)
+        for i in range(1, len(levels)):  # M_l = M2M(M_{l+1}): coarse to fine
+            fmmgb.fmm_m2m_adjoint(levels[i], p, Ws[i - 1], Ws[i], accumulate=True)
         grad = torch.zeros_like(xy)
-        for l, W in zip(levels, Ws):
-            fmmgb.fmm_p2m_adjoint(l, p, xy, c, W, grad, accumulate=True)
+        fmmgb.fmm_p2m_adjoint(L, p, xy, c, Ws[-1], grad)
         return grad, None, None, None, None, None, None, None
 
 

@@ -94,6 +94,7 @@ SIGNATURES = {
     "fmm_batch_destroy": (None, [_vp, _vp]),
     "fmm_m2l_batched": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(_i32), _i32, ctypes.POINTER(_vp),
                                        ctypes.POINTER(_vp), _i32, _i32, _vp]),
+    "fmm_m2m_adjoint": (ctypes.c_int, [_i32, _i32, _vp, _vp, _i32, _vp]),
     "fmm_l2l": (ctypes.c_int, [_i32, _i32, _vp, _vp, _i32, _vp]),
     "fmm_l2l_adjoint": (ctypes.c_int, [_i32, _i32, _vp, _vp, _i32, _vp]),
     "fmm_l2p": (ctypes.c_int, [_i32, _i64, _vp, _vp, _vp, ctypes.POINTER(_vp), _i32, _vp, _i32, _vp]),
@@ -313,6 +314,11 @@ def fmm_p2m(level: int, p: int, xy, c, M, accumulate: bool = False, stream=None)
 def fmm_m2m(child_level: int, p: int, Mc, Mp, accumulate: bool = False, stream=None):
     _check(load().fmm_m2m(child_level, p, _ptr(Mc), _ptr(Mp), FMM_ACCUMULATE if accumulate else 0,
                           _stream(stream)))
+
+
+def fmm_m2m_adjoint(child_level: int, p: int, Wp, Wc, accumulate: bool = False, stream=None):
+    _check(load().fmm_m2m_adjoint(child_level, p, _ptr(Wp), _ptr(Wc), FMM_ACCUMULATE if accumulate else 0,
+                                  _stream(stream)))
 
 
 def fmm_l2l(child_level: int, p: int, Lp, Lc, accumulate: bool = False, stream=None):

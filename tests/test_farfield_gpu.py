@@ -174,3 +174,29 @@ def test_p2m_adjoint_matches_central_differences(fmm, orc):
             ref[i, a] = (J(i, pp) - J(i, pm)) / (2 * h)
     got = grad.cpu().numpy()
     assert np.linalg.norm(got - ref) <= 1e-6 * np.linalg.norm(ref), np.linalg.norm(got - ref) / np.linalg.norm(ref)
+
+
+def test_m2m_adjoint(fmm, orc):
+    """Conjugate transpose of M2M against the oracle's M2M applied to unit child vectors."""
+    rng = np.random.default_rng(21)
+    p, cl = 12, 4
+    nb_c, nb_p = 4 ** cl, 4 ** (cl - 1)
+    W = rng.standard_normal((nb_p, p)) + 1j * rng.standard_normal((nb_p, p))
+    Wc = _dev(np.zeros((nb_c, p)))
+    fmm.fmm_m2m_adjoint(cl, p, _dev(W), Wc)
+    fmm.fmm_sync_status()
+    n = 1 << cl
+    ref = np.zeros((nb_c, p), dtype=np.complex128)
+    for c in range(4):  # scaled M2M matrix of child class c: parent[j] from child[k]
+        ix, iy = c & 1, c >> 1
+        cols = []
+        for k in range(p):
+            e = np.zeros((nb_c, p), dtype=np.complex128)
+            e[iy * n + ix, k] = 1.0
+            Mp = orc.scale_me(orc.m2m_uniform(cl, p, orc.unscale_me(e, cl)), cl - 1)
+            cols.append(Mp[0])
+        T = np.stack(cols, axis=1)
+        for py in range(n // 2):
+            for px in range(n // 2):
+                ref[(2 * py + iy) * n + 2 * px + ix] = T.conj().T @ W[py * (n // 2) + px]
+    assert _rel(_host(Wc), ref) <= 1e-6
