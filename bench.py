@@ -596,6 +596,22 @@ def run_ours(args):
                 ms = statistics.median(_timed(torch, _graph(torch, fgt), args.steps, stream, flush))
                 ntr = metrics.fgt_translations(g, fcfg["ncut"])
                 taps = 2 * fcfg["ncut"] + 1
+                if sigma == 0.05 and fp == 16:
+                    # the whole transform: 2^20 sources -> P2H -> H2T -> T2P at 2^20 targets
+                    fy = torch.rand((fcfg["n"], 2), dtype=torch.float64, device=dev,
+                                    generator=torch.Generator(device=dev).manual_seed(workloads.SEED_BASE + 5))
+                    Gy = torch.empty(fcfg["n"], dtype=torch.float32, device=dev)
+
+                    def fgt_all():
+                        fmmgb.fgt_p2h(g, fp, sigma, fxd, fqd, A)
+                        fmmgb.fgt_h2t(g, fcfg["ncut"], fp, sigma, A, Cf, work=W)
+                        fmmgb.fgt_t2p(g, fp, sigma, Cf, fy, Gy)
+
+                    ms_all = statistics.median(_timed(torch, _graph(torch, fgt_all), args.steps, stream, flush))
+                    rows["fgt_transform_sigma0.05_p16"] = {
+                        "ms": ms_all, "sources": int(fcfg["n"]), "targets": int(fcfg["n"]),
+                        "points_per_s": fcfg["n"] / (ms_all * 1e-3), "launches": 5,
+                        "note": "fgt_p2h (memset + atomics), fgt_h2t (2 passes), fgt_t2p"}
                 rows[f"fgt_h2t_sigma{sigma}_p{fp}"] = {
                     "translations_per_s": ntr / (ms * 1e-3), "ms": ms, "launches": 2, "grid": f"{1 << g}^2",
                     "gflops_separable": (4 ** g) * metrics.fgt_flops_per_box_separable(fp, taps, taps)

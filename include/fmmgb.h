@@ -385,6 +385,16 @@ int fmm_p2m_adjoint(int32_t level, int32_t p, const double* xy, const double* c,
 int fgt_p2h(int32_t grid_log2, int32_t p, double sigma, const double* x, const double* q, int64_t n,
             float* A, int32_t flags, void* stream);
 
+/* fgt_t2p: the transform at n targets from the Taylor coefficients of each
+ *   target's box (Sec. 2.2, Eq. taylor):
+ *     G(y_j) (+)= sum_{b1,b2 < p} C[b][b1][b2] t1^b1 t2^b2,  t = (y_j - t_C) / (sqrt(2) sigma),
+ *   b = the box floor(y 2^g) (clamped) of the 2^g grid, t_C its centre.
+ *   C: device float32 [4^g][p][p] (fgt_h2t's output, 16-byte aligned); y: device
+ *   float64 [n][2]; G: device float32 [n].  p: 4, 8, 12 or 16.  flags: FMM_ACCUMULATE.
+ *   With fgt_p2h and fgt_h2t this is the whole transform on the device. */
+int fgt_t2p(int32_t grid_log2, int32_t p, double sigma, const float* C, const double* y, int64_t n,
+            float* G, int32_t flags, void* stream);
+
 /* Read and clear the device error word after synchronising `stream`.
  * Returns FMM_OK, FMM_ETIMEOUT or FMM_EDEVICE. */
 int fmm_sync_status(void* stream);

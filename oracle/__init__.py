@@ -461,6 +461,21 @@ def fgt_direct(x, q, sigma: float, y) -> np.ndarray:
     return G
 
 
+def fgt_taylor_eval_grid(g: int, p: int, sigma: float, C: np.ndarray, y) -> np.ndarray:
+    """Eq. (taylor) at every target from the Taylor coefficients of its own box of the
+    2^g grid (box floor(y 2^g), clamped; centre the box centre)."""
+    y = _f64(y)
+    side = 1 << g
+    ix = np.clip(np.floor(y[:, 0] * side).astype(np.int64), 0, side - 1)
+    iy = np.clip(np.floor(y[:, 1] * side).astype(np.int64), 0, side - 1)
+    G = np.zeros(y.shape[0])
+    for b in np.unique(iy * side + ix):
+        sel = np.nonzero(iy * side + ix == b)[0]
+        tc = ((b % side + 0.5) / side, (b // side + 0.5) / side)
+        G[sel] = fgt_taylor_eval(C[b], tc, sigma, y[sel])
+    return G
+
+
 def fgt_p2h(x, q, sB, sigma: float, p: int) -> np.ndarray:
     x, q = _f64(x), _f64(q)
     A = np.zeros((p, p))

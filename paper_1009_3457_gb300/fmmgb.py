@@ -104,6 +104,7 @@ SIGNATURES = {
     "fmm_m2m": (ctypes.c_int, [_i32, _i32, _vp, _vp, _i32, _vp]),
     "fgt_h2t": (ctypes.c_int, [_i32, _i32, _i32, _d, _vp, _vp, _vp, _i32, _vp]),
     "fgt_h2t_noalloc": (ctypes.c_int, [_i32, _i32, _i32, _d, _vp, _vp, _i32, _vp]),
+    "fgt_t2p": (ctypes.c_int, [_i32, _i32, _d, _vp, _vp, _i64, _vp, _i32, _vp]),
     "fgt_p2h": (ctypes.c_int, [_i32, _i32, _d, _vp, _vp, _i64, _vp, _i32, _vp]),
     "fmm_sync_status": (ctypes.c_int, [_vp]),
     "fmm_last_error": (ctypes.c_char_p, []),
@@ -370,6 +371,13 @@ def fgt_h2t_noalloc(grid_log2: int, n_cut: int, p: int, sigma: float, A, C, accu
 def fgt_p2h(grid_log2: int, p: int, sigma: float, x, q, A, accumulate: bool = False, stream=None):
     n = 0 if q is None else q.numel()
     _check(load().fgt_p2h(grid_log2, p, float(sigma), _ptr(x), _ptr(q), n, _ptr(A),
+                          FMM_ACCUMULATE if accumulate else 0, _stream(stream)))
+
+
+def fgt_t2p(grid_log2: int, p: int, sigma: float, C, y, G, accumulate: bool = False, stream=None):
+    """G (float32 [n]) at the targets y (float64 [n, 2]) from the Taylor coefficients C of their boxes."""
+    n = 0 if G is None else G.numel()
+    _check(load().fgt_t2p(grid_log2, p, float(sigma), _ptr(C), _ptr(y), n, _ptr(G),
                           FMM_ACCUMULATE if accumulate else 0, _stream(stream)))
 
 

@@ -137,3 +137,45 @@ def test_fgt_p2h_on_device(fmm, orc, gmm_sources):
         fmm.fgt_p2h(g, p, sigma, torch.from_numpy(x).cuda(), torch.from_numpy(q).cuda(), Ad)
         got = Ad.cpu().numpy().astype(np.float64)
         assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-5
+
+
+@pytest.mark.parametrize("p", [4, 8, 12, 16])
+def test_fgt_t2p_matches_oracle(fmm, orc, p):
+    """fgt_t2p (Eq. taylor at each target's box) against the oracle's evaluation."""
+    import torch
+
+    rng = np.random.default_rng(70 + p)
+    g = 4
+    C = rng.standard_normal((4 ** g, p, p)) / (1.0 + np.add.outer(np.arange(p), np.arange(p)))[None]
+    y = rng.random((3000, 2))
+    G = torch.empty(3000, dtype=torch.float32, device="cuda")
+    fmm.fgt_t2p(g, p, 0.1, _dev(C), torch.from_numpy(y).cuda(), G)
+    fmm.fmm_sync_status()
+    ref = orc.fgt_taylor_eval_grid(g, p, 0.1, C, y)
+    got = G.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 1e-6
+
+
+@pytest.mark.parametrize("sigma,p", [(0.1, 8), (0.05, 12), (0.2, 16)])
+def test_fgt_whole_transform_on_device(fmm, orc, sigma, p):
+    """fgt_p2h -> fgt_h2t -> fgt_t2p on the device against the oracle's pipeline
+    (FP32 bar 1e-5) and against the direct Gauss sum (truncation and cutoff)."""
+    import torch
+
+    rng = np.random.default_rng(int(sigma * 1000) + p)
+    x, q = workloads.gmm_particles(20000, rng)
+    y = rng.random((2000, 2))
+    g = workloads.fgt_grid_log2(sigma)
+    A = torch.empty((4 ** g, p, p), dtype=torch.float32, device="cuda")
+    Cd = torch.empty_like(A)
+    G = torch.empty(2000, dtype=torch.float32, device="cuda")
+    fmm.fgt_p2h(g, p, sigma, torch.from_numpy(x).cuda(), torch.from_numpy(q).cuda(), A)
+    fmm.fgt_h2t(g, workloads.FGT_NCUT, p, sigma, A, Cd)
+    fmm.fgt_t2p(g, p, sigma, Cd, torch.from_numpy(y).cuda(), G)
+    fmm.fmm_sync_status()
+    got = G.cpu().numpy().astype(np.float64)
+    Ao = orc.fgt_p2h_grid(g, p, sigma, x, q)
+    ref = orc.fgt_taylor_eval_grid(g, p, sigma, orc.fgt_h2t_grid(g, workloads.FGT_NCUT, p, sigma, Ao), y)
+    direct = orc.fgt_direct(x, q, sigma, y)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 1e-5
+    assert np.linalg.norm(got - direct) / np.linalg.norm(direct) <= 1e-5

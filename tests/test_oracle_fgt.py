@@ -153,3 +153,24 @@ def test_full_fgt_grid_pipeline_matches_direct(orc):
         tC = ((tx + 0.5) * side, (ty + 0.5) * side)
         approx[j] = orc.fgt_taylor_eval(C[ty * n + tx], tC, sigma, y[j:j + 1])[0]
     assert np.abs(approx - G).max() / np.abs(q).sum() < 1e-7
+
+
+def test_grid_pipeline_converges_to_direct_gauss_sum(orc):
+    """P2H on the grid, H2T over the n_cut neighbourhood, Taylor evaluation at each
+    target's box (Eqs. A_alpha, C_beta, taylor) against the direct sum (Eq. dgt):
+    the error falls with p and is below 1e-6 from p = 8 (truncation and cutoff)."""
+    import workloads
+
+    x, q = workloads.gmm_particles(3000, np.random.default_rng(5), ncomp=4)
+    y = np.random.default_rng(6).random((300, 2))
+    sigma = 0.1
+    g = workloads.fgt_grid_log2(sigma)
+    D = orc.fgt_direct(x, q, sigma, y)
+    errs = []
+    for p in (4, 8, 12):
+        A = orc.fgt_p2h_grid(g, p, sigma, x, q)
+        C = orc.fgt_h2t_grid(g, workloads.FGT_NCUT, p, sigma, A)
+        G = orc.fgt_taylor_eval_grid(g, p, sigma, C, y)
+        errs.append(np.linalg.norm(G - D) / np.linalg.norm(D))
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[1] < 1e-6 and errs[2] < 1e-8, errs
