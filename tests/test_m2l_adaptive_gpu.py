@@ -178,3 +178,16 @@ def test_gradient_matches_oracle_fd_gmm_workload(fmm, orc):
     J, Jo, g, fd = _gradient_case(orc, fmm, cfg["n"], cfg["leaf_cap"], cfg["max_level"], workloads.SEED_BASE + 4)
     assert abs(J - Jo) <= 1e-5 * abs(Jo)
     assert np.linalg.norm(g - fd) <= 1e-4 * np.linalg.norm(fd), np.linalg.norm(g - fd) / np.linalg.norm(fd)
+
+
+def test_tensor_core_precisions_refuse_adaptive_levels(fmm, orc):
+    import torch
+
+    xy, c = workloads.gmm_particles(20000, np.random.default_rng(3), ncomp=4)
+    tree = fmm.fmm_build_lists(xy, 7, leaf_cap=30)
+    levels = list(range(2, 8))
+    Md = [torch.zeros((4 ** l, 16), dtype=torch.complex64, device="cuda") for l in levels]
+    Ld = [torch.zeros_like(m) for m in Md]
+    with pytest.raises(fmm.FmmError) as e:
+        fmm.fmm_m2l_levels(tree, 2, 16, Md, Ld, prec=fmm.FMM_TC_BF16X3)
+    assert e.value.code == fmm.FMM_EUNSUPPORTED

@@ -274,3 +274,32 @@ def test_levels_call_replays_from_a_cuda_graph(fmm, orc, prec_name):
         ref = orc.scale_le(orc.m2l_uniform(l, p, Ms[l]), l)
         got = (_host(out) - X[l].astype(np.complex64).astype(np.complex128)) / 3.0
         assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= tol, l
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("prec_name", ["FMM_FP32", "FMM_TC_BF16X3"])
+def test_level_11_sampled_targets(fmm, orc, prec_name):
+    """A level of 2048 x 2048 boxes (4M boxes, 65,536 FP32 tiles): seeded random scaled MEs,
+    sampled targets on the corners, edges and interior against the oracle."""
+    import torch
+
+    prec = getattr(fmm, prec_name)
+    p, level = 16, 11
+    n = 1 << level
+    rng = np.random.default_rng(1111)
+    Ms = (rng.standard_normal((n * n, p)) + 1j * rng.standard_normal((n * n, p))).astype(np.complex64)
+    tree = fmm.fmm_build_lists(None, level)
+    Md = torch.from_numpy(Ms).cuda()
+    Ld = torch.empty_like(Md)
+    fmm.fmm_m2l(tree, level, p, Md, Ld, prec=prec)
+    fmm.fmm_sync_status()
+    edges = [0, 1, n - 2, n - 1]
+    targets = [y * n + x for y in edges for x in edges] + list(rng.integers(0, n * n, 300))
+    targets += [int(rng.integers(0, n)) for _ in range(20)]              # bottom row
+    targets += [(n - 1) * n + int(rng.integers(0, n)) for _ in range(20)]  # top row
+    targets = np.unique(np.array(targets, dtype=np.int64))
+    M = orc.unscale_me(Ms.astype(np.complex128), level)
+    ref = orc.scale_le(orc.m2l_uniform_targets(level, p, M, targets), level)
+    got = _host(Ld)[targets]
+    tol = TOL_L2 if prec == fmm.FMM_FP32 else 1e-4
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= tol
