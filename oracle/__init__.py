@@ -83,6 +83,7 @@ _SIGS = {
     "orc_fgt_h2t_grid": (None, [_i, _i, _i, _d, _D, _D]),
     "orc_fgt_h2t_targets": (None, [_i, _i, _i, _d, _D, _i64, _I64, _D]),
     "orc_fgt_p2h_grid": (None, [_i, _i, _d, _i64, _D, _D, _D]),
+    "orc_fgt_hermite_eval_grid": (None, [_i, _i, _i, _d, _D, _i64, _D, _D]),
 }
 
 
@@ -524,6 +525,15 @@ def fgt_h2t_targets(g: int, ncut: int, p: int, sigma: float, A: np.ndarray, targ
     C = np.zeros((len(t), p, p))
     lib().orc_fgt_h2t_targets(g, ncut, p, sigma, _dp(A), len(t), t.ctypes.data_as(_I64), _dp(C))
     return C
+
+
+def fgt_hermite_eval_grid(g: int, ncut: int, p: int, sigma: float, A: np.ndarray, y) -> np.ndarray:
+    """Eq. (hermite) at every target, summed over the source boxes of the 2^g grid within
+    Chebyshev distance ncut of the target's own box (reading R14).  A: [4^g, p, p]."""
+    A, y = _f64(A), _f64(y)
+    G = np.zeros(y.shape[0])
+    lib().orc_fgt_hermite_eval_grid(g, ncut, p, sigma, _dp(A), y.shape[0], _dp(y), _dp(G))
+    return G
 
 
 def fgt_p2h_grid(g: int, p: int, sigma: float, x, q) -> np.ndarray:

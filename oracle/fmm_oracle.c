@@ -53,6 +53,9 @@
  *       fixed evaluation points, phi_far(z) the L2P of the LE of z's leaf
  *       after M2L over V-lists at every level and L2L down; the topology
  *       (each point's leaf) is frozen when points move.
+ *   R14 FGT Hermite evaluation on the grid (Sec. 4.2 takes the clusters of a
+ *       target as given): a target takes every box within Chebyshev distance
+ *       ncut of its own box, the neighbourhood the H2T uses (R9).
  */
 #include <complex.h>
 #include <math.h>
@@ -600,6 +603,33 @@ void orc_fgt_h2t_targets(int g, int ncut, int p, double sigma, const double* A,
                                  Cout + (size_t)p * p * i);
             }
         }
+    }
+}
+
+/* Hermite-series evaluation on the uniform FGT grid (Eq. hermite, reading R14):
+ * each target y takes every source box B whose Chebyshev distance, in boxes,
+ * from y's own box is at most ncut (boxes outside the grid do not exist),
+ *   G(y) = sum_B sum_{a1,a2 < p} A_B[a1][a2] h_a1((y1 - sB1)/(sqrt2 sigma)) h_a2((y2 - sB2)/(sqrt2 sigma)),
+ * s_B the centre of B.  Source boxes in row-major order (sy outer, sx inner). */
+void orc_fgt_hermite_eval_grid(int g, int ncut, int p, double sigma, const double* A, int64_t ny,
+                               const double* y, double* G)
+{
+    int nb = 1 << g;
+    double side = ldexp(1.0, -g);
+    for (int64_t j = 0; j < ny; ++j) {
+        int tx, ty;
+        point_box(g, y[2 * j], y[2 * j + 1], &tx, &ty);
+        double acc = 0.0;
+        for (int sy = ty - ncut; sy <= ty + ncut; ++sy) {
+            for (int sx = tx - ncut; sx <= tx + ncut; ++sx) {
+                if (sx < 0 || sy < 0 || sx >= nb || sy >= nb) continue;
+                double v = 0.0;
+                orc_fgt_hermite_eval(p, A + (size_t)p * p * ((size_t)sy * nb + sx), ((double)sx + 0.5) * side,
+                                     ((double)sy + 0.5) * side, sigma, 1, y + 2 * j, &v);
+                acc += v;
+            }
+        }
+        G[j] = acc;
     }
 }
 

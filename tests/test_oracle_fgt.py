@@ -174,3 +174,88 @@ def test_grid_pipeline_converges_to_direct_gauss_sum(orc):
         errs.append(np.linalg.norm(G - D) / np.linalg.norm(D))
     assert errs[0] > errs[1] > errs[2]
     assert errs[1] < 1e-6 and errs[2] < 1e-8, errs
+
+
+def test_hermite_grid_eval_converges_to_direct_gauss_sum(orc):
+    """P2H on the grid, then Eq. (hermite) summed over each target's n_cut
+    neighbourhood (reading R14), against the direct sum (Eq. dgt): the error
+    falls with p until the cutoff (about 2e-10 here) dominates."""
+    import workloads
+
+    x, q = workloads.gmm_particles(3000, np.random.default_rng(15), ncomp=4)
+    y = np.random.default_rng(16).random((300, 2))
+    sigma = 0.1
+    g = workloads.fgt_grid_log2(sigma)
+    D = orc.fgt_direct(x, q, sigma, y)
+    errs = []
+    for p in (4, 8, 12, 16):
+        A = orc.fgt_p2h_grid(g, p, sigma, x, q)
+        G = orc.fgt_hermite_eval_grid(g, workloads.FGT_NCUT, p, sigma, A, y)
+        errs.append(np.linalg.norm(G - D) / np.linalg.norm(D))
+    assert errs[0] > errs[1] > errs[2] and errs[3] <= errs[2] * 1.01, errs
+    assert errs[0] < 1e-3 and errs[1] < 1e-6 and errs[2] < 1e-9, errs
+
+
+@pytest.mark.parametrize("ncut", [1, 2, 3, 4])
+def test_hermite_grid_eval_sums_exactly_the_neighbourhood(orc, ncut):
+    """With p = 16 the Hermite truncation is ~1e-13 of sum|q|, so G must equal the
+    direct Gauss sum over exactly the sources whose boxes lie within Chebyshev
+    distance ncut of the target's box (a box too many or too few changes G by
+    ~1e-2 of sum|q| here).  The omitted part is bounded by the Gaussian tail
+    sum|q| exp(-(ncut side)^2 / 2 sigma^2), since every omitted source lies at
+    least ncut box sides from the target."""
+    rng = np.random.default_rng(30 + ncut)
+    sigma, g, p = 0.1, 4, 16
+    n = 1 << g
+    side = 2.0 ** -g
+    x = rng.random((400, 2))
+    q = rng.uniform(-1, 1, 400)
+    y = rng.random((200, 2))
+    A = orc.fgt_p2h_grid(g, p, sigma, x, q)
+    G = orc.fgt_hermite_eval_grid(g, ncut, p, sigma, A, y)
+    sbx = np.minimum((x * n).astype(int), n - 1)
+    tby = np.minimum((y * n).astype(int), n - 1)
+    near = np.zeros(len(y))
+    for j in range(len(y)):
+        keep = np.maximum(np.abs(sbx[:, 0] - tby[j, 0]), np.abs(sbx[:, 1] - tby[j, 1])) <= ncut
+        d2 = ((x[keep] - y[j]) ** 2).sum(axis=1)
+        near[j] = (q[keep] * np.exp(-d2 / (2 * sigma ** 2))).sum()
+    assert np.abs(G - near).max() <= 1e-11 * np.abs(q).sum()
+    D = orc.fgt_direct(x, q, sigma, y)
+    assert np.abs(G - D).max() <= np.abs(q).sum() * math.exp(-((ncut * side) ** 2) / (2 * sigma ** 2))
+
+
+def test_hermite_grid_eval_equals_taylor_route_on_same_neighbourhood(orc):
+    """H2T over the n_cut neighbourhood followed by Taylor evaluation (Eqs. C_beta,
+    taylor) sums the same source boxes as the Hermite evaluation (Eq. hermite,
+    R14); with a small n_cut the neighbourhood decides the answer, so the two
+    routes agree only if both take the same boxes.  They differ by truncation."""
+    rng = np.random.default_rng(12)
+    sigma, g, p, ncut = 0.2, 3, 16, 2
+    x = rng.random((300, 2))
+    q = rng.uniform(-1, 1, 300)
+    y = rng.random((150, 2))
+    A = orc.fgt_p2h_grid(g, p, sigma, x, q)
+    Gh = orc.fgt_hermite_eval_grid(g, ncut, p, sigma, A, y)
+    C = orc.fgt_h2t_grid(g, ncut, p, sigma, A)
+    Gt = orc.fgt_taylor_eval_grid(g, p, sigma, C, y)
+    D = orc.fgt_direct(x, q, sigma, y)
+    assert np.linalg.norm(Gh - D) / np.linalg.norm(D) > 1e-3  # the cutoff matters here
+    assert np.linalg.norm(Gh - Gt) / np.linalg.norm(Gh) < 1e-8
+    # and each target box's sum is that of its own neighbourhood: brute force on two targets
+    n = 1 << g
+    sc = math.sqrt(2.0) * sigma
+    side = 2.0 ** -g
+    for j in (0, 77):
+        tx, ty = min(int(y[j, 0] * n), n - 1), min(int(y[j, 1] * n), n - 1)
+        acc = 0.0
+        for b in range(n * n):
+            sx, sy = b % n, b // n
+            if max(abs(sx - tx), abs(sy - ty)) > ncut:
+                continue
+            t1 = (y[j, 0] - (sx + 0.5) * side) / sc
+            t2 = (y[j, 1] - (sy + 0.5) * side) / sc
+            h1 = orc.hermite_functions(p, t1)
+            h2 = orc.hermite_functions(p, t2)
+            acc += h1 @ A[b] @ h2
+        assert abs(acc - Gh[j]) <= 1e-12 * max(1.0, abs(acc))
