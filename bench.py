@@ -224,6 +224,72 @@ def run_reference(args):
     return 0
 
 
+def _fgt_hermite_setup(torch, fmmgb, dev, fxd, fqd, fyd, sigma, fp):
+    """Sources binned and P2H'd, targets binned, for Hermite evaluation on the grid of sigma."""
+    g = workloads.fgt_grid_log2(sigma)
+    nb = 4 ** g
+
+    def bins(pts):
+        perm = torch.empty(pts.shape[0], dtype=torch.int32, device=dev)
+        start = torch.empty(nb + 1, dtype=torch.int32, device=dev)
+        work = torch.empty(nb, dtype=torch.int32, device=dev)
+        fmmgb.fgt_bin_points(g, pts, perm, start, work)
+        return perm, start, work
+
+    sperm, sstart, swork = bins(fxd)
+    A = torch.empty((nb, fp, fp), dtype=torch.float32, device=dev)
+    fmmgb.fgt_p2h_binned(g, fp, sigma, fxd, fqd, sperm, A)
+    tperm, tstart, twork = bins(fyd)
+    G = torch.empty(fyd.shape[0], dtype=torch.float32, device=dev)
+    torch.cuda.synchronize()
+    counts = torch.diff(tstart).cpu().numpy()
+    nonempty = (torch.diff(sstart) > 0).cpu().numpy()
+    pairs = metrics.fgt_h2p_pairs(g, workloads.FGT_NCUT, counts, nonempty)
+    return dict(g=g, A=A, G=G, sperm=sperm, sstart=sstart, swork=swork, tperm=tperm, tstart=tstart,
+                twork=twork, pairs=pairs)
+
+
+def _fgt_hermite_rows(torch, fmmgb, dev, fxd, fqd, args, stream, flush):
+    """FGT Hermite evaluation (Sec. 4.2, Eq. hermite) at 2^20 Gaussian-mixture targets from the
+    Hermite coefficients of 2^20 mixture sources, n_cut = 10, for every sigma and order; and the
+    whole transform through it (bin sources, P2H, bin targets, evaluate) at sigma 0.05, p 16."""
+    fcfg = workloads.CONFIGS["fgt"]
+    ncut = fcfg["ncut"]
+    fy, _ = workloads.gmm_particles(fcfg["n"], workloads.rng_for("fgt_targets"))
+    fyd = torch.from_numpy(fy).to(dev)
+    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    rows = {}
+    for sigma in fcfg["sigmas"]:
+        for fp in fcfg["orders"]:
+            st = _fgt_hermite_setup(torch, fmmgb, dev, fxd, fqd, fyd, sigma, fp)
+            g = st["g"]
+
+            def h2p():
+                fmmgb.fgt_h2p(g, ncut, fp, sigma, st["A"], fyd, st["tperm"], st["tstart"], st["G"])
+
+            ms = statistics.median(_timed(torch, _graph(torch, h2p), args.steps, stream, flush))
+            flops = st["pairs"] * metrics.fgt_h2p_flops_per_pair(fp)
+            rows[f"fgt_h2p_sigma{sigma}_p{fp}"] = {
+                "ms": ms, "targets": int(fcfg["n"]), "targets_per_s": fcfg["n"] / (ms * 1e-3),
+                "box_pairs": st["pairs"], "gflops": flops / (ms * 1e-3) / 1e9,
+                "alu_frac": flops / (ms * 1e-3) / 1e12 / peak, "launches": 1, "grid": f"{1 << g}^2"}
+            if sigma == 0.05 and fp == 16:
+                def transform():
+                    fmmgb.fgt_bin_points(g, fxd, st["sperm"], st["sstart"], st["swork"])
+                    fmmgb.fgt_p2h_binned(g, fp, sigma, fxd, fqd, st["sperm"], st["A"])
+                    fmmgb.fgt_bin_points(g, fyd, st["tperm"], st["tstart"], st["twork"])
+                    fmmgb.fgt_h2p(g, ncut, fp, sigma, st["A"], fyd, st["tperm"], st["tstart"], st["G"])
+
+                ms_all = statistics.median(_timed(torch, _graph(torch, transform), args.steps, stream, flush))
+                rows["fgt_hermite_transform_sigma0.05_p16"] = {
+                    "ms": ms_all, "sources": int(fcfg["n"]), "targets": int(fcfg["n"]),
+                    "points_per_s": fcfg["n"] / (ms_all * 1e-3), "launches": 8,
+                    "note": "fgt_bin_points (3 kernels) x 2, fgt_p2h_binned, fgt_h2p; mixture targets"}
+            del st
+    fmmgb.fmm_sync_status()
+    return rows
+
+
 def _traffic(kernel: str):
     """DRAM bytes per launch from the committed ncu summary, or None if the kernel source changed since."""
     import hashlib
@@ -366,6 +432,22 @@ def run_ours(args):
         fmmgb.fmm_sync_status()
         if rank == 0:
             print(json.dumps({"mode": "kernels", "steps": args.steps, "launches_per_step": 2}))
+        return 0
+    if args.mode == "kernels" and args.prec == "h2p":
+        # profiling case: FGT Hermite evaluation, sigma = 0.05, p = 16, 2^20 mixture targets
+        fcfg = workloads.CONFIGS["fgt"]
+        fx, fq = workloads.gmm_particles(fcfg["n"], workloads.rng_for("fgt"))
+        fy, _ = workloads.gmm_particles(fcfg["n"], workloads.rng_for("fgt_targets"))
+        fyd = torch.from_numpy(fy).to(dev)
+        st = _fgt_hermite_setup(torch, fmmgb, dev, torch.from_numpy(fx).to(dev), torch.from_numpy(fq).to(dev),
+                                fyd, 0.05, 16)
+        for _ in range(args.steps):
+            fmmgb.fgt_h2p(st["g"], fcfg["ncut"], 16, 0.05, st["A"], fyd, st["tperm"], st["tstart"], st["G"])
+        torch.cuda.synchronize()
+        fmmgb.fmm_sync_status()
+        if rank == 0:
+            print(json.dumps({"mode": "kernels", "steps": args.steps, "launches_per_step": 1,
+                              "box_pairs": st["pairs"]}))
         return 0
     if args.mode == "kernels":
         # profiling case: the step's launch only (no e2e copies, no CPU baseline, no other rows)
@@ -597,25 +679,31 @@ def run_ours(args):
                 ntr = metrics.fgt_translations(g, fcfg["ncut"])
                 taps = 2 * fcfg["ncut"] + 1
                 if sigma == 0.05 and fp == 16:
-                    # the whole transform: 2^20 sources -> P2H -> H2T -> T2P at 2^20 targets
+                    # the whole transform: 2^20 sources -> bin -> P2H -> H2T -> T2P at 2^20 targets
                     fy = torch.rand((fcfg["n"], 2), dtype=torch.float64, device=dev,
                                     generator=torch.Generator(device=dev).manual_seed(workloads.SEED_BASE + 5))
                     Gy = torch.empty(fcfg["n"], dtype=torch.float32, device=dev)
+                    sperm = torch.empty(fcfg["n"], dtype=torch.int32, device=dev)
+                    sstart = torch.empty(4 ** g + 1, dtype=torch.int32, device=dev)
+                    swork = torch.empty(4 ** g, dtype=torch.int32, device=dev)
 
                     def fgt_all():
-                        fmmgb.fgt_p2h(g, fp, sigma, fxd, fqd, A)
+                        fmmgb.fgt_bin_points(g, fxd, sperm, sstart, swork)
+                        fmmgb.fgt_p2h_binned(g, fp, sigma, fxd, fqd, sperm, A)
                         fmmgb.fgt_h2t(g, fcfg["ncut"], fp, sigma, A, Cf, work=W)
                         fmmgb.fgt_t2p(g, fp, sigma, Cf, fy, Gy)
 
                     ms_all = statistics.median(_timed(torch, _graph(torch, fgt_all), args.steps, stream, flush))
                     rows["fgt_transform_sigma0.05_p16"] = {
                         "ms": ms_all, "sources": int(fcfg["n"]), "targets": int(fcfg["n"]),
-                        "points_per_s": fcfg["n"] / (ms_all * 1e-3), "launches": 5,
-                        "note": "fgt_p2h (memset + atomics), fgt_h2t (2 passes), fgt_t2p"}
+                        "points_per_s": fcfg["n"] / (ms_all * 1e-3), "launches": 7,
+                        "note": "fgt_bin_points (3 kernels), fgt_p2h_binned, fgt_h2t (2 passes), fgt_t2p; "
+                                "uniform targets"}
                 rows[f"fgt_h2t_sigma{sigma}_p{fp}"] = {
                     "translations_per_s": ntr / (ms * 1e-3), "ms": ms, "launches": 2, "grid": f"{1 << g}^2",
                     "gflops_separable": (4 ** g) * metrics.fgt_flops_per_box_separable(fp, taps, taps)
                     / (ms * 1e-3) / 1e9}
+        rows.update(_fgt_hermite_rows(torch, fmmgb, dev, fxd, fqd, args, stream, flush))
         fmmgb.fmm_sync_status()
 
     if rank == 0:
@@ -666,7 +754,7 @@ def main():
     ap.add_argument("--no-rows", action="store_true", help="skip the adjoint / per-level / FGT rows")
     ap.add_argument("--mode", default="full", choices=["full", "kernels"],
                     help="kernels: only the timed step's launches (for ncu captures)")
-    ap.add_argument("--prec", default="fp32", choices=["fp32", "tc3", "tc1", "batched", "fgt"],
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "tc3", "tc1", "batched", "fgt", "h2p"],
                     help="launches of --mode kernels: the step at this precision, or the 256-problem batch, "
                          "or the FGT H2T at sigma 0.05, p 16")
     ap.add_argument("--nprob", type=int, default=None,

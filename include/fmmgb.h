@@ -395,6 +395,48 @@ int fgt_p2h(int32_t grid_log2, int32_t p, double sigma, const double* x, const d
 int fgt_t2p(int32_t grid_log2, int32_t p, double sigma, const float* C, const double* y, int64_t n,
             float* G, int32_t flags, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * FGT Hermite-series evaluation at targets (Sec. 4.2, Eq. hermite), the
+ * paper's own FGT GPU kernel, on the uniform 2^g x 2^g grid:
+ *
+ * fgt_bin_points -- counting sort of n points by box of the grid (box
+ *   floor(y 2^g), clamped to the grid; NaN coordinates go to box 0).
+ *   y: device float64 [n][2]; perm: device int32 [n], written with the point
+ *   indices box by box (order within a box unspecified); box_start: device
+ *   int32 [4^g + 1], box b's points are perm[box_start[b] .. box_start[b+1]);
+ *   work: device int32 [4^g] scratch (not overlapping box_start).
+ *   grid_log2 0..10, n < 2^31.  No allocation, no synchronisation.
+ *
+ * fgt_p2h_binned -- fgt_p2h (Eq. A_alpha) for sources binned by
+ *   fgt_bin_points(grid_log2, x, ...): one atomic addition per coefficient per
+ *   run of a box's points within a block of 256, instead of one per point.
+ *   Summation order within a box follows the binning, so the FP32 result
+ *   varies by rounding from run to run.  p: 4, 8, 12 or 16.
+ *
+ * fgt_h2p -- for every target y_j,
+ *   G(y_j) (+)= sum_{B : max(|sx-tx|,|sy-ty|) <= n_cut}
+ *                sum_{a1,a2 < p} A_B[a1][a2] h_a1((y_j1 - sB1)/(sqrt2 sigma)) h_a2((y_j2 - sB2)/(sqrt2 sigma)),
+ *   (tx, ty) the box of y_j, s_B the centre of source box B, h_n(t) = exp(-t^2) H_n(t).
+ *   A: device float32 [4^g][p][p] Hermite coefficients (fgt_p2h), 16-byte
+ *   aligned; y: device float64 [n][2]; perm, box_start: fgt_bin_points(grid_log2,
+ *   y, n, ...) of these targets; G: device float32 [n], indexed like y.
+ *   n_cut 0..16, p 4, 8, 12 or 16, flags FMM_ACCUMULATE or 0.  FP32 on CUDA
+ *   cores.  Source boxes whose coefficients are all zero are skipped: a first
+ *   kernel writes one flag per box into a 1 MiB per-device array that the
+ *   library allocates on the first call (or in fmm_prepare; make one of them
+ *   before any stream capture); calls that overlap on the GPU (different
+ *   streams) share that array and must be serialised by the caller.  A perm
+ *   entry outside [0, n) or a box_start that does not bin [0, n) sets the
+ *   device error word's check bit (fmm_sync_status returns FMM_EDEVICE); the
+ *   affected targets are skipped.
+ * ------------------------------------------------------------------------- */
+int fgt_bin_points(int32_t grid_log2, const double* y, int64_t n, int32_t* perm, int32_t* box_start, int32_t* work,
+                   void* stream);
+int fgt_p2h_binned(int32_t grid_log2, int32_t p, double sigma, const double* x, const double* q, int64_t n,
+                   const int32_t* perm, float* A, int32_t flags, void* stream);
+int fgt_h2p(int32_t grid_log2, int32_t n_cut, int32_t p, double sigma, const float* A, const double* y, int64_t n,
+            const int32_t* perm, const int32_t* box_start, float* G, int32_t flags, void* stream);
+
 /* Read and clear the device error word after synchronising `stream`.
  * Returns FMM_OK, FMM_ETIMEOUT or FMM_EDEVICE. */
 int fmm_sync_status(void* stream);

@@ -71,6 +71,7 @@ struct DeviceState {
     int sm_count = 0;
     int* counters = nullptr;  // ring of persistent-launch work counters
     unsigned next_counter = 0;
+    unsigned char* fgt_flags = nullptr;  // FGT Hermite evaluation: non-empty flag per grid box
 };
 constexpr int kCounterRing = 256;
 static std::mutex g_mu;
@@ -146,6 +147,17 @@ int tile_counter(int** out, cudaStream_t st)
         FMM_CUDA_TRY(cudaMemset(s->counters, 0, kCounterRing * 2 * sizeof(int)));
     }
     *out = s->counters + 2 * (s->next_counter++ % kCounterRing);
+    return FMM_OK;
+}
+
+int fgt_flag_buffer(unsigned char** out)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    DeviceState* s = nullptr;
+    int rc = current_state(&s);
+    if (rc) return rc;
+    if (!s->fgt_flags) FMM_CUDA_TRY(cudaMalloc(&s->fgt_flags, kFgtScratchBytes));
+    *out = s->fgt_flags;
     return FMM_OK;
 }
 
@@ -559,6 +571,8 @@ int fmm_prepare(int32_t p, int32_t prec)
     }
     int* ctr = nullptr;
     if ((rc = tile_counter(&ctr, nullptr))) return rc;
+    unsigned char* flags = nullptr;
+    if ((rc = fgt_flag_buffer(&flags))) return rc;
     return cudaStreamSynchronize(nullptr) == cudaSuccess ? FMM_OK : fail(FMM_ECUDA, "fmm_prepare: sync failed");
 }
 

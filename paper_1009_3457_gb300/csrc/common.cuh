@@ -45,6 +45,14 @@ int smem_opt_in(const void* func, int bytes, unsigned* done);
 // are in flight at once.
 int tile_counter(int** out, cudaStream_t st);
 
+// A per-device scratch for the FGT Hermite evaluation (grids up to 1024 x
+// 1024 boxes): 4^10 bytes of non-empty flags, one per box, then 4^10 + 1
+// ints of the claim table; refilled before each evaluation, allocated on
+// first use (or by fmm_prepare).
+constexpr size_t kFgtFlagBytes = (size_t)1 << 20;
+constexpr size_t kFgtScratchBytes = kFgtFlagBytes + (((size_t)1 << 20) + 1) * sizeof(int);
+int fgt_flag_buffer(unsigned char** out);
+
 // ---------------------------------------------------------------------------
 // offset codes: box offset (dx, dy) = source - target, |dx|,|dy| <= 3
 // ---------------------------------------------------------------------------

@@ -106,6 +106,9 @@ SIGNATURES = {
     "fgt_h2t_noalloc": (ctypes.c_int, [_i32, _i32, _i32, _d, _vp, _vp, _i32, _vp]),
     "fgt_t2p": (ctypes.c_int, [_i32, _i32, _d, _vp, _vp, _i64, _vp, _i32, _vp]),
     "fgt_p2h": (ctypes.c_int, [_i32, _i32, _d, _vp, _vp, _i64, _vp, _i32, _vp]),
+    "fgt_bin_points": (ctypes.c_int, [_i32, _vp, _i64, _vp, _vp, _vp, _vp]),
+    "fgt_p2h_binned": (ctypes.c_int, [_i32, _i32, _d, _vp, _vp, _i64, _vp, _vp, _i32, _vp]),
+    "fgt_h2p": (ctypes.c_int, [_i32, _i32, _i32, _d, _vp, _vp, _i64, _vp, _vp, _vp, _i32, _vp]),
     "fmm_sync_status": (ctypes.c_int, [_vp]),
     "fmm_last_error": (ctypes.c_char_p, []),
     "fmm_version": (ctypes.c_char_p, []),
@@ -379,6 +382,31 @@ def fgt_t2p(grid_log2: int, p: int, sigma: float, C, y, G, accumulate: bool = Fa
     n = 0 if G is None else G.numel()
     _check(load().fgt_t2p(grid_log2, p, float(sigma), _ptr(C), _ptr(y), n, _ptr(G),
                           FMM_ACCUMULATE if accumulate else 0, _stream(stream)))
+
+
+def fgt_bin_points(grid_log2: int, y, perm, box_start, work, stream=None):
+    """Counting sort of the points y (float64 [n, 2]) by box of the 2^g grid: perm (int32 [n])
+    lists the points box by box, box_start (int32 [4^g + 1]) where each box's run begins;
+    work: int32 [4^g] scratch."""
+    n = 0 if y is None else y.shape[0]
+    _check(load().fgt_bin_points(grid_log2, _ptr(y), n, _ptr(perm), _ptr(box_start), _ptr(work),
+                                 _stream(stream)))
+
+
+def fgt_p2h_binned(grid_log2: int, p: int, sigma: float, x, q, perm, A, accumulate: bool = False, stream=None):
+    """fgt_p2h for sources binned by fgt_bin_points (perm)."""
+    n = 0 if q is None else q.numel()
+    _check(load().fgt_p2h_binned(grid_log2, p, float(sigma), _ptr(x), _ptr(q), n, _ptr(perm), _ptr(A),
+                                 FMM_ACCUMULATE if accumulate else 0, _stream(stream)))
+
+
+def fgt_h2p(grid_log2: int, n_cut: int, p: int, sigma: float, A, y, perm, box_start, G, accumulate: bool = False,
+            stream=None):
+    """G (float32 [n]) at the targets y (float64 [n, 2], binned by fgt_bin_points into perm and
+    box_start) from the Hermite coefficients A of every box within n_cut of each target's box."""
+    n = 0 if G is None else G.numel()
+    _check(load().fgt_h2p(grid_log2, n_cut, p, float(sigma), _ptr(A), _ptr(y), n, _ptr(perm), _ptr(box_start),
+                          _ptr(G), FMM_ACCUMULATE if accumulate else 0, _stream(stream)))
 
 
 def fmm_sync_status(stream=None):

@@ -46,3 +46,32 @@ def fgt_translations(g: int, ncut: int) -> int:
 def fgt_flops_per_box_separable(p: int, taps_x: int, taps_y: int) -> int:
     """Two 1-D passes of p x p by p x p real products: 2 p^3 flops per tap."""
     return 2 * p ** 3 * (taps_x + taps_y)
+
+
+def fgt_h2p_flops_per_pair(p: int) -> int:
+    """Eq. (hermite) for one target and one source box, as the bilinear form
+    h(t1)^T A h(t2): p^2 + p multiply-adds (the Hermite functions themselves are
+    not counted)."""
+    return 2 * (p * p + p)
+
+
+def fgt_h2p_pairs(g: int, ncut: int, target_counts, source_nonempty) -> int:
+    """Target-source box pairs that Hermite evaluation on the 2^g grid works on:
+    every target times the source boxes holding coefficients (non-empty boxes)
+    within Chebyshev distance ncut of its box.  target_counts: targets per box
+    (4^g, row-major); source_nonempty: bool per box."""
+    import numpy as np
+
+    n = 1 << g
+    s = np.asarray(source_nonempty, dtype=np.int64).reshape(n, n)
+    c = np.zeros((n + 1, n + 1), dtype=np.int64)  # 2-D prefix sums of the non-empty mask
+    c[1:, 1:] = s.cumsum(0).cumsum(1)
+    t = np.asarray(target_counts, dtype=np.int64).reshape(n, n)
+    total = 0
+    for ty in range(n):
+        y0, y1 = max(0, ty - ncut), min(n - 1, ty + ncut) + 1
+        for tx in range(n):
+            if t[ty, tx]:
+                x0, x1 = max(0, tx - ncut), min(n - 1, tx + ncut) + 1
+                total += int(t[ty, tx]) * int(c[y1, x1] - c[y0, x1] - c[y1, x0] + c[y0, x0])
+    return total

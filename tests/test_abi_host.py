@@ -212,3 +212,28 @@ def test_far_field_entry_points_reject_bad_arguments(fmm):
     assert lib.fmm_l2p_adjoint(8, 10, 64, 128, 256, None, tab, 3, None) == fmm.FMM_EINVAL
     assert lib.fmm_p2m_adjoint(3, 8, 64, 128, 10, None, 256, 0, None) == fmm.FMM_EINVAL
     assert lib.fmm_p2m_adjoint(3, 65, 64, 128, 10, 512, 256, 0, None) == fmm.FMM_EINVAL
+
+
+def test_fgt_hermite_entry_points_reject_bad_arguments(fmm):
+    lib = fmm.load()
+    # fgt_bin_points(g, y, n, perm, box_start, work, stream)
+    assert lib.fgt_bin_points(11, 64, 10, 128, 256, 512, None) == fmm.FMM_EINVAL        # grid_log2
+    assert lib.fgt_bin_points(3, 64, -1, 128, 256, 512, None) == fmm.FMM_EINVAL         # n
+    assert lib.fgt_bin_points(3, 64, 1 << 31, 128, 256, 512, None) == fmm.FMM_EINVAL    # n > int32
+    assert lib.fgt_bin_points(3, None, 10, 128, 256, 512, None) == fmm.FMM_EINVAL       # y
+    assert lib.fgt_bin_points(3, 64, 10, 128, 256, None, None) == fmm.FMM_EINVAL        # work
+    assert lib.fgt_bin_points(3, 68, 10, 128, 256, 4096, None) == fmm.FMM_EINVAL        # y misaligned
+    assert lib.fgt_bin_points(3, 64, 10, 128, 256, 300, None) == fmm.FMM_EINVAL         # work overlaps box_start
+    # fgt_p2h_binned(g, p, sigma, x, q, n, perm, A, flags, stream)
+    assert lib.fgt_p2h_binned(3, 6, 0.1, 64, 128, 10, 256, 512, 0, None) == fmm.FMM_EINVAL   # p
+    assert lib.fgt_p2h_binned(3, 8, -0.1, 64, 128, 10, 256, 512, 0, None) == fmm.FMM_EINVAL  # sigma
+    assert lib.fgt_p2h_binned(3, 8, 0.1, 64, 128, 10, None, 512, 0, None) == fmm.FMM_EINVAL  # perm
+    assert lib.fgt_p2h_binned(3, 8, 0.1, 64, 128, 10, 256, 512, 4, None) == fmm.FMM_EINVAL   # flags
+    # fgt_h2p(g, ncut, p, sigma, A, y, n, perm, box_start, G, flags, stream)
+    assert lib.fgt_h2p(3, 17, 8, 0.1, 64, 128, 10, 256, 512, 1024, 0, None) == fmm.FMM_EINVAL  # n_cut
+    assert lib.fgt_h2p(3, 2, 10, 0.1, 64, 128, 10, 256, 512, 1024, 0, None) == fmm.FMM_EINVAL  # p
+    assert lib.fgt_h2p(3, 2, 8, 0.0, 64, 128, 10, 256, 512, 1024, 0, None) == fmm.FMM_EINVAL   # sigma
+    assert lib.fgt_h2p(3, 2, 8, 0.1, 72, 128, 10, 256, 512, 1024, 0, None) == fmm.FMM_EINVAL   # A misaligned
+    assert lib.fgt_h2p(3, 2, 8, 0.1, 64, 128, 10, 256, None, 1024, 0, None) == fmm.FMM_EINVAL  # box_start
+    assert lib.fgt_h2p(3, 2, 8, 0.1, 64, 128, 10, 256, 512, 1024, 2, None) == fmm.FMM_EINVAL   # flags
+    assert "n_cut" in fmm.fmm_last_error() or "flags" in fmm.fmm_last_error()

@@ -31,7 +31,8 @@ import numpy as np
 
 SEED_BASE = 20100913
 
-WORKLOAD_IDS = {"m2l_small": 1, "m2l_scale": 2, "m2l_tc": 3, "m2l_gmm": 4, "fgt": 5, "m2l_batched": 6}
+WORKLOAD_IDS = {"m2l_small": 1, "m2l_scale": 2, "m2l_tc": 3, "m2l_gmm": 4, "fgt": 5, "m2l_batched": 6,
+                "fgt_targets": 7}
 
 
 def rng_for(workload: str, salt: int = 0) -> np.random.Generator:
