@@ -56,6 +56,18 @@ FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
 
 
+def _measured_bf16_tflops() -> float:
+    """Dense BF16 GEMM throughput measured on the GB300s (burst), else the fallback figure."""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"])
+    except (OSError, KeyError, ValueError):
+        return 1900.0
+
+
+BF16_PEAK_TFLOPS = _measured_bf16_tflops()
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -273,6 +285,24 @@ def _fgt_hermite_rows(torch, fmmgb, dev, fxd, fqd, args, stream, flush):
                 "ms": ms, "targets": int(fcfg["n"]), "targets_per_s": fcfg["n"] / (ms * 1e-3),
                 "box_pairs": st["pairs"], "gflops": flops / (ms * 1e-3) / 1e9,
                 "alu_frac": flops / (ms * 1e-3) / 1e12 / peak, "launches": 1, "grid": f"{1 << g}^2"}
+            if fp == 16:
+                for pname, prec, prods in (("bf16x3", fmmgb.FMM_TC_BF16X3, 3), ("bf16", fmmgb.FMM_TC_BF16, 1)):
+                    Gt = torch.empty_like(st["G"])
+
+                    def h2p_tc():
+                        fmmgb.fgt_h2p(g, ncut, fp, sigma, st["A"], fyd, st["tperm"], st["tstart"], Gt, prec=prec)
+
+                    ms_tc = statistics.median(_timed(torch, _graph(torch, h2p_tc), args.steps, stream, flush))
+                    counts = torch.diff(st["tstart"]).cpu().numpy()
+                    mma = metrics.fgt_h2p_tc_mma_flops(g, ncut, counts, products=prods)
+                    rel = float(torch.linalg.vector_norm((Gt - st["G"]).double())
+                                / torch.linalg.vector_norm(st["G"].double()))
+                    rows[f"fgt_h2p_tc_{pname}_sigma{sigma}_p16"] = {
+                        "ms": ms_tc, "targets_per_s": fcfg["n"] / (ms_tc * 1e-3), "launches": 3,
+                        "tensor_tflops": mma / (ms_tc * 1e-3) / 1e12,
+                        "tensor_frac_of_measured_bf16": mma / (ms_tc * 1e-3) / 1e12 / BF16_PEAK_TFLOPS,
+                        "speedup_vs_fp32": ms / ms_tc, "rel_l2_vs_fp32_path": rel,
+                        "note": "claim table, BF16 image of A, tcgen05 kernel"}
             if sigma == 0.05 and fp == 16:
                 def transform():
                     fmmgb.fgt_bin_points(g, fxd, st["sperm"], st["sstart"], st["swork"])
@@ -441,8 +471,10 @@ def run_ours(args):
         fyd = torch.from_numpy(fy).to(dev)
         st = _fgt_hermite_setup(torch, fmmgb, dev, torch.from_numpy(fx).to(dev), torch.from_numpy(fq).to(dev),
                                 fyd, 0.05, 16)
+        hprec = fmmgb.FMM_TC_BF16X3 if args.tc else fmmgb.FMM_FP32
         for _ in range(args.steps):
-            fmmgb.fgt_h2p(st["g"], fcfg["ncut"], 16, 0.05, st["A"], fyd, st["tperm"], st["tstart"], st["G"])
+            fmmgb.fgt_h2p(st["g"], fcfg["ncut"], 16, 0.05, st["A"], fyd, st["tperm"], st["tstart"], st["G"],
+                          prec=hprec)
         torch.cuda.synchronize()
         fmmgb.fmm_sync_status()
         if rank == 0:
@@ -754,6 +786,7 @@ def main():
     ap.add_argument("--no-rows", action="store_true", help="skip the adjoint / per-level / FGT rows")
     ap.add_argument("--mode", default="full", choices=["full", "kernels"],
                     help="kernels: only the timed step's launches (for ncu captures)")
+    ap.add_argument("--tc", action="store_true", help="with --prec h2p: the tensor-core (BF16x3) form")
     ap.add_argument("--prec", default="fp32", choices=["fp32", "tc3", "tc1", "batched", "fgt", "h2p"],
                     help="launches of --mode kernels: the step at this precision, or the 256-problem batch, "
                          "or the FGT H2T at sigma 0.05, p 16")

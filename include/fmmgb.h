@@ -420,8 +420,9 @@ int fgt_t2p(int32_t grid_log2, int32_t p, double sigma, const float* C, const do
  *   A: device float32 [4^g][p][p] Hermite coefficients (fgt_p2h), 16-byte
  *   aligned; y: device float64 [n][2]; perm, box_start: fgt_bin_points(grid_log2,
  *   y, n, ...) of these targets; G: device float32 [n], indexed like y.
- *   n_cut 0..16, p 4, 8, 12 or 16, flags FMM_ACCUMULATE or 0.  FP32 on CUDA
- *   cores.  Source boxes whose coefficients are all zero are skipped: a first
+ *   n_cut 0..16, p 4, 8, 12 or 16, flags FMM_ACCUMULATE or 0.
+ *   prec FMM_FP32: CUDA cores.  Source boxes whose coefficients are all zero
+ *   are skipped: a first
  *   kernel writes one flag per box into a 1 MiB per-device array that the
  *   library allocates on the first call (or in fmm_prepare; make one of them
  *   before any stream capture); calls that overlap on the GPU (different
@@ -429,13 +430,22 @@ int fgt_t2p(int32_t grid_log2, int32_t p, double sigma, const float* C, const do
  *   entry outside [0, n) or a box_start that does not bin [0, n) sets the
  *   device error word's check bit (fmm_sync_status returns FMM_EDEVICE); the
  *   affected targets are skipped.
+ *   prec FMM_TC_BF16X3 / FMM_TC_BF16: tensor cores, p = 16 and n_cut <= 15
+ *   only (else FMM_EUNSUPPORTED).  Per target box the evaluation is the
+ *   product of the targets' y-direction Hermite values with the
+ *   neighbourhood's coefficients, reduced against the x-direction values;
+ *   FP32 accumulation, BF16 operands split into hi + lo (three products,
+ *   ~16 significant bits each) or hi only.  Every box of the neighbourhood
+ *   is evaluated (no skipping).  A BF16 copy of A (1 KiB per box) lives in a
+ *   per-device buffer grown on demand (the first call of a grid size
+ *   allocates: make it before any stream capture).
  * ------------------------------------------------------------------------- */
 int fgt_bin_points(int32_t grid_log2, const double* y, int64_t n, int32_t* perm, int32_t* box_start, int32_t* work,
                    void* stream);
 int fgt_p2h_binned(int32_t grid_log2, int32_t p, double sigma, const double* x, const double* q, int64_t n,
                    const int32_t* perm, float* A, int32_t flags, void* stream);
-int fgt_h2p(int32_t grid_log2, int32_t n_cut, int32_t p, double sigma, const float* A, const double* y, int64_t n,
-            const int32_t* perm, const int32_t* box_start, float* G, int32_t flags, void* stream);
+int fgt_h2p(int32_t grid_log2, int32_t n_cut, int32_t p, int32_t prec, double sigma, const float* A, const double* y,
+            int64_t n, const int32_t* perm, const int32_t* box_start, float* G, int32_t flags, void* stream);
 
 /* Read and clear the device error word after synchronising `stream`.
  * Returns FMM_OK, FMM_ETIMEOUT or FMM_EDEVICE. */

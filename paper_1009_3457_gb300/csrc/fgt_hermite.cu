@@ -30,7 +30,7 @@
 //   - boxes whose coefficients are all zero (no sources) are skipped.
 #include <mutex>
 
-#include "common.cuh"
+#include "fgt_hermite.cuh"
 
 namespace fmmgb {
 
@@ -233,16 +233,6 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-// h_n(t) = exp(-t^2) H_n(t), n < P, by h_{n+1} = 2t h_n - 2n h_{n-1}.
-template <int P>
-__device__ __forceinline__ void hermite_functions(float t, float (&h)[P])
-{
-    const float tt = t + t;
-    h[0] = __expf(-t * t);
-    if (P > 1) h[1] = tt * h[0];
-#pragma unroll
-    for (int m = 1; m + 1 < P; ++m) h[m + 1] = fmaf(tt, h[m], -(float)(2 * m) * h[m - 1]);
-}
 
 // claims[0..nbox]: exclusive scan of ceil(targets of box b / ch), the table that maps a claim
 // index to its box; a box_start that decreases counts as empty and is reported.
@@ -266,21 +256,8 @@ __device__ bool h2p_claim(const H2pArgs& a, int nbox, int ch, int* first, int* e
     const int total = __ldg(a.claims + nbox);
     const int k = atomicAdd(a.cursor, 1);
     if (k >= total) return false;
-    int lo = 0, hi = nbox;  // largest b with claims[b] <= k
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (__ldg(a.claims + mid) <= k) lo = mid;
-        else hi = mid;
-    }
-    const int f = __ldg(a.box_start + lo) + (k - __ldg(a.claims + lo)) * ch;
-    const int e = min(min(f + ch, __ldg(a.box_start + lo + 1)), a.n);
-    *first = f;
-    *end = e;
-    *box = lo;
-    if (!(0 <= f && f < e)) {  // box_start does not bin [0, n): nothing to do for this claim
-        atomicOr(a.err, DEV_ERR_CHECK);
-        *first = *end = 0;
-    }
+    h2p_claim_range(a.claims, a.box_start, nbox, a.n, ch, k, first, end, box);
+    if (*first >= *end) atomicOr(a.err, DEV_ERR_CHECK);  // box_start does not bin [0, n)
     return true;
 }
 
@@ -440,6 +417,13 @@ __global__ void __launch_bounds__(kH2pThreads) fgt_h2p_kernel(H2pArgs a)
     }
 }
 
+int launch_h2p_claims(int nbox, const int* box_start, int ch, int* claims, int* err, cudaStream_t st)
+{
+    h2p_claims_kernel<<<1, kScanThreads, 0, st>>>(nbox, box_start, ch, claims, err);
+    FMM_CUDA_TRY(cudaGetLastError());
+    return FMM_OK;
+}
+
 template <int P>
 static int h2p_launch(const H2pArgs& args, cudaStream_t st)
 {
@@ -460,8 +444,7 @@ static int h2p_launch(const H2pArgs& args, cudaStream_t st)
     const int nbox = 1 << (2 * args.g);
     fgt_box_flags_kernel<<<(nbox + 7) / 8, 256, 0, st>>>(args.A, nbox, C::PP, const_cast<unsigned char*>(args.nz));
     FMM_CUDA_TRY(cudaGetLastError());
-    h2p_claims_kernel<<<1, kScanThreads, 0, st>>>(nbox, args.box_start, C::CH, const_cast<int*>(args.claims), args.err);
-    FMM_CUDA_TRY(cudaGetLastError());
+    if (int rc = launch_h2p_claims(nbox, args.box_start, C::CH, const_cast<int*>(args.claims), args.err, st)) return rc;
     const int64_t most = (int64_t)args.n / C::CH + nbox;  // claims can be no more
     const int grid = (int)std::min<int64_t>((int64_t)occ * sms, most > 0 ? most : 1);
     fgt_h2p_kernel<P><<<grid, kH2pThreads, C::smem, st>>>(args);
@@ -531,11 +514,17 @@ extern "C" int fgt_p2h_binned(int32_t grid_log2, int32_t p, double sigma, const 
     return FMM_OK;
 }
 
-extern "C" int fgt_h2p(int32_t grid_log2, int32_t n_cut, int32_t p, double sigma, const float* A, const double* y,
-                       int64_t n, const int32_t* perm, const int32_t* box_start, float* G, int32_t flags,
-                       void* stream)
+extern "C" int fgt_h2p(int32_t grid_log2, int32_t n_cut, int32_t p, int32_t prec, double sigma, const float* A,
+                       const double* y, int64_t n, const int32_t* perm, const int32_t* box_start, float* G,
+                       int32_t flags, void* stream)
 {
     clear_error();
+    if (prec != FMM_FP32 && prec != FMM_TC_BF16X3 && prec != FMM_TC_BF16)
+        return fail(FMM_EINVAL, "fgt_h2p: unknown precision %d", prec);
+    if (prec != FMM_FP32 && p != 16)
+        return fail(FMM_EUNSUPPORTED, "fgt_h2p: the tensor-core forms take p = 16 (got %d)", p);
+    if (prec != FMM_FP32 && n_cut > 15)
+        return fail(FMM_EUNSUPPORTED, "fgt_h2p: the tensor-core forms take n_cut <= 15 (got %d)", n_cut);
     if (grid_log2 < 0 || grid_log2 > 10) return fail(FMM_EINVAL, "fgt_h2p: grid_log2 %d outside 0..10", grid_log2);
     if (n_cut < 0 || n_cut > kH2pMaxCut) return fail(FMM_EINVAL, "fgt_h2p: n_cut %d outside 0..%d", n_cut, kH2pMaxCut);
     if (!fgt_supported(p)) return fail(FMM_EINVAL, "fgt_h2p: unsupported p = %d (4, 8, 12, 16)", p);
@@ -565,6 +554,12 @@ extern "C" int fgt_h2p(int32_t grid_log2, int32_t n_cut, int32_t p, double sigma
     if (int rc = fgt_flag_buffer(&nzbuf)) return rc;
     args.nz = nzbuf;
     args.claims = reinterpret_cast<const int*>(nzbuf + kFgtFlagBytes);
+    if (prec != FMM_FP32) {
+        const int nbox = 1 << (2 * grid_log2);
+        if (int rc = launch_h2p_claims(nbox, box_start, 128, const_cast<int*>(args.claims), args.err, st)) return rc;
+        return launch_fgt_h2p_tc(grid_log2, n_cut, args.d, prec == FMM_TC_BF16X3, A, y, args.n, perm, box_start,
+                                 args.claims, G, args.accumulate != 0, args.err, st);
+    }
     switch (p) {
         case 4: return h2p_launch<4>(args, st);
         case 8: return h2p_launch<8>(args, st);

@@ -108,7 +108,7 @@ SIGNATURES = {
     "fgt_p2h": (ctypes.c_int, [_i32, _i32, _d, _vp, _vp, _i64, _vp, _i32, _vp]),
     "fgt_bin_points": (ctypes.c_int, [_i32, _vp, _i64, _vp, _vp, _vp, _vp]),
     "fgt_p2h_binned": (ctypes.c_int, [_i32, _i32, _d, _vp, _vp, _i64, _vp, _vp, _i32, _vp]),
-    "fgt_h2p": (ctypes.c_int, [_i32, _i32, _i32, _d, _vp, _vp, _i64, _vp, _vp, _vp, _i32, _vp]),
+    "fgt_h2p": (ctypes.c_int, [_i32, _i32, _i32, _i32, _d, _vp, _vp, _i64, _vp, _vp, _vp, _i32, _vp]),
     "fmm_sync_status": (ctypes.c_int, [_vp]),
     "fmm_last_error": (ctypes.c_char_p, []),
     "fmm_version": (ctypes.c_char_p, []),
@@ -401,12 +401,13 @@ def fgt_p2h_binned(grid_log2: int, p: int, sigma: float, x, q, perm, A, accumula
 
 
 def fgt_h2p(grid_log2: int, n_cut: int, p: int, sigma: float, A, y, perm, box_start, G, accumulate: bool = False,
-            stream=None):
+            prec: int = FMM_FP32, stream=None):
     """G (float32 [n]) at the targets y (float64 [n, 2], binned by fgt_bin_points into perm and
-    box_start) from the Hermite coefficients A of every box within n_cut of each target's box."""
+    box_start) from the Hermite coefficients A of every box within n_cut of each target's box.
+    prec: FMM_FP32 (CUDA cores), FMM_TC_BF16X3 or FMM_TC_BF16 (tensor cores, p = 16)."""
     n = 0 if G is None else G.numel()
-    _check(load().fgt_h2p(grid_log2, n_cut, p, float(sigma), _ptr(A), _ptr(y), n, _ptr(perm), _ptr(box_start),
-                          _ptr(G), FMM_ACCUMULATE if accumulate else 0, _stream(stream)))
+    _check(load().fgt_h2p(grid_log2, n_cut, p, prec, float(sigma), _ptr(A), _ptr(y), n, _ptr(perm),
+                          _ptr(box_start), _ptr(G), FMM_ACCUMULATE if accumulate else 0, _stream(stream)))
 
 
 def fmm_sync_status(stream=None):

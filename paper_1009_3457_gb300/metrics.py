@@ -75,3 +75,22 @@ def fgt_h2p_pairs(g: int, ncut: int, target_counts, source_nonempty) -> int:
                 x0, x1 = max(0, tx - ncut), min(n - 1, tx + ncut) + 1
                 total += int(t[ty, tx]) * int(c[y1, x1] - c[y0, x1] - c[y1, x0] + c[y0, x0])
     return total
+
+
+def fgt_h2p_tc_mma_flops(g: int, ncut: int, target_counts, products: int = 3, p: int = 16, rows: int = 128) -> int:
+    """Tensor-core flops that the tensor-core Hermite evaluation issues: per claim of up to
+    `rows` targets of a box, one [rows x p] x [p x (w p)] product per source row and precision
+    product, w x h the box's clipped neighbourhood (every box evaluated, full M tiles)."""
+    import numpy as np
+
+    n = 1 << g
+    t = np.asarray(target_counts, dtype=np.int64).reshape(n, n)
+    total = 0
+    for ty in range(n):
+        h = min(n - 1, ty + ncut) - max(0, ty - ncut) + 1
+        for tx in range(n):
+            if t[ty, tx]:
+                w = min(n - 1, tx + ncut) - max(0, tx - ncut) + 1
+                tiles = -(-int(t[ty, tx]) // rows)
+                total += tiles * h * 2 * rows * (w * p) * p
+    return total * products

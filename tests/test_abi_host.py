@@ -229,11 +229,15 @@ def test_fgt_hermite_entry_points_reject_bad_arguments(fmm):
     assert lib.fgt_p2h_binned(3, 8, -0.1, 64, 128, 10, 256, 512, 0, None) == fmm.FMM_EINVAL  # sigma
     assert lib.fgt_p2h_binned(3, 8, 0.1, 64, 128, 10, None, 512, 0, None) == fmm.FMM_EINVAL  # perm
     assert lib.fgt_p2h_binned(3, 8, 0.1, 64, 128, 10, 256, 512, 4, None) == fmm.FMM_EINVAL   # flags
-    # fgt_h2p(g, ncut, p, sigma, A, y, n, perm, box_start, G, flags, stream)
-    assert lib.fgt_h2p(3, 17, 8, 0.1, 64, 128, 10, 256, 512, 1024, 0, None) == fmm.FMM_EINVAL  # n_cut
-    assert lib.fgt_h2p(3, 2, 10, 0.1, 64, 128, 10, 256, 512, 1024, 0, None) == fmm.FMM_EINVAL  # p
-    assert lib.fgt_h2p(3, 2, 8, 0.0, 64, 128, 10, 256, 512, 1024, 0, None) == fmm.FMM_EINVAL   # sigma
-    assert lib.fgt_h2p(3, 2, 8, 0.1, 72, 128, 10, 256, 512, 1024, 0, None) == fmm.FMM_EINVAL   # A misaligned
-    assert lib.fgt_h2p(3, 2, 8, 0.1, 64, 128, 10, 256, None, 1024, 0, None) == fmm.FMM_EINVAL  # box_start
-    assert lib.fgt_h2p(3, 2, 8, 0.1, 64, 128, 10, 256, 512, 1024, 2, None) == fmm.FMM_EINVAL   # flags
-    assert "n_cut" in fmm.fmm_last_error() or "flags" in fmm.fmm_last_error()
+    # fgt_h2p(g, ncut, p, prec, sigma, A, y, n, perm, box_start, G, flags, stream)
+    F, T3 = fmm.FMM_FP32, fmm.FMM_TC_BF16X3
+    assert lib.fgt_h2p(3, 17, 8, F, 0.1, 64, 128, 10, 256, 512, 1024, 0, None) == fmm.FMM_EINVAL  # n_cut
+    assert lib.fgt_h2p(3, 2, 10, F, 0.1, 64, 128, 10, 256, 512, 1024, 0, None) == fmm.FMM_EINVAL  # p
+    assert lib.fgt_h2p(3, 2, 8, F, 0.0, 64, 128, 10, 256, 512, 1024, 0, None) == fmm.FMM_EINVAL   # sigma
+    assert lib.fgt_h2p(3, 2, 8, F, 0.1, 72, 128, 10, 256, 512, 1024, 0, None) == fmm.FMM_EINVAL   # A misaligned
+    assert lib.fgt_h2p(3, 2, 8, F, 0.1, 64, 128, 10, 256, None, 1024, 0, None) == fmm.FMM_EINVAL  # box_start
+    assert lib.fgt_h2p(3, 2, 8, F, 0.1, 64, 128, 10, 256, 512, 1024, 2, None) == fmm.FMM_EINVAL   # flags
+    assert "flags" in fmm.fmm_last_error()
+    assert lib.fgt_h2p(3, 2, 8, 7, 0.1, 64, 128, 10, 256, 512, 1024, 0, None) == fmm.FMM_EINVAL   # precision
+    assert lib.fgt_h2p(3, 2, 8, T3, 0.1, 64, 128, 10, 256, 512, 1024, 0, None) == fmm.FMM_EUNSUPPORTED   # TC p
+    assert lib.fgt_h2p(3, 16, 16, T3, 0.1, 64, 128, 10, 256, 512, 1024, 0, None) == fmm.FMM_EUNSUPPORTED  # TC n_cut

@@ -217,3 +217,91 @@ def test_h2p_full_size_workload_sampled(fmm, orc, sigma, p):
     A64 = A.cpu().numpy().astype(np.float64)
     ref = orc.fgt_hermite_eval_grid(g, workloads.FGT_NCUT, p, sigma, A64, y[pick])
     _check(G.cpu().numpy().astype(np.float64)[pick], ref)
+
+
+# ---------------------------------------------------------------------------
+# tensor-core forms (p = 16): bar = the oracle's truncation error + 1e-4 in relative L2
+# (split BF16, three products); the single-product form is checked at 1e-2.
+# ---------------------------------------------------------------------------
+TC_BAR = {"bf16x3": 1e-4, "bf16": 1e-2}
+
+
+def _prec(fmm, name):
+    return {"bf16x3": fmm.FMM_TC_BF16X3, "bf16": fmm.FMM_TC_BF16}[name]
+
+
+def _h2p_tc(fmm, g, ncut, sigma, A32, y, prec, G=None, accumulate=False):
+    import torch
+
+    yd = torch.from_numpy(np.ascontiguousarray(y, dtype=np.float64)).cuda()
+    perm, start = _bin(fmm, g, yd)
+    if G is None:
+        G = torch.empty(len(y), dtype=torch.float32, device="cuda")
+    fmm.fgt_h2p(g, ncut, 16, sigma, torch.from_numpy(A32).cuda(), yd, perm, start, G, accumulate=accumulate,
+                prec=prec)
+    fmm.fmm_sync_status()
+    return G.cpu().numpy().astype(np.float64)
+
+
+def _rel(got, ref):
+    return np.linalg.norm(got - ref) / np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("name", ["bf16x3", "bf16"])
+@pytest.mark.parametrize("sigma,ncut", [(0.2, 10), (0.1, 10), (0.05, 10), (0.1, 3), (0.05, 1), (0.1, 0), (0.05, 15)])
+def test_h2p_tc_matches_oracle(fmm, orc, gmm_sources, name, sigma, ncut):
+    x, q = gmm_sources
+    g = workloads.fgt_grid_log2(sigma)
+    rng = np.random.default_rng(ncut + int(sigma * 100))
+    y = np.concatenate([rng.random((2500, 2)), 0.52 + 0.001 * rng.random((700, 2))])
+    A32 = orc.fgt_p2h_grid(g, 16, sigma, x, q).astype(np.float32)
+    got = _h2p_tc(fmm, g, ncut, sigma, A32, y, _prec(fmm, name))
+    ref = orc.fgt_hermite_eval_grid(g, ncut, 16, sigma, A32.astype(np.float64), y)
+    trunc = _rel(orc.fgt_hermite_eval_grid(g, ncut, 16, sigma, orc.fgt_p2h_grid(g, 16, sigma, x, q), y),
+                 orc.fgt_direct(x, q, sigma, y)) if ncut == 10 else 0.0
+    err = _rel(got, ref)
+    assert err <= trunc + TC_BAR[name], f"relative L2 {err:.3e}"
+    assert np.abs(got - ref).max() <= 10 * TC_BAR[name] * np.abs(ref).max()
+
+
+def test_h2p_tc_ragged_counts_and_accumulate(fmm, orc, gmm_sources):
+    import torch
+
+    x, q = gmm_sources
+    sigma, ncut = 0.1, 4
+    g = workloads.fgt_grid_log2(sigma)
+    A32 = orc.fgt_p2h_grid(g, 16, sigma, x, q).astype(np.float32)
+    for n in (1, 127, 128, 129, 300):
+        y = np.random.default_rng(n + 5).random((n, 2))
+        ref = orc.fgt_hermite_eval_grid(g, ncut, 16, sigma, A32.astype(np.float64), y)
+        assert _rel(_h2p_tc(fmm, g, ncut, sigma, A32, y, fmm.FMM_TC_BF16X3), ref) <= 1e-4
+        G = torch.full((n,), 0.5, dtype=torch.float32, device="cuda")
+        got = _h2p_tc(fmm, g, ncut, sigma, A32, y, fmm.FMM_TC_BF16X3, G=G, accumulate=True)
+        assert _rel(got, ref + 0.5) <= 1e-4
+
+
+def test_h2p_tc_agrees_with_fp32_path_at_full_size(fmm, orc):
+    """2^20 mixture targets, sigma 0.05, n_cut 10 (the benchmark's launch): the tensor-core
+    result against the FP32 path everywhere and the oracle on 1,500 sampled targets."""
+    import torch
+
+    n = 1 << 20
+    x, q = workloads.gmm_particles(n, np.random.default_rng(2024))
+    y, _ = workloads.gmm_particles(n, np.random.default_rng(2025))
+    sigma, ncut = 0.05, workloads.FGT_NCUT
+    g = workloads.fgt_grid_log2(sigma)
+    xd, yd = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    perm, _ = _bin(fmm, g, xd)
+    A = torch.empty((4 ** g, 16, 16), dtype=torch.float32, device="cuda")
+    fmm.fgt_p2h_binned(g, 16, sigma, xd, torch.from_numpy(q).cuda(), perm, A)
+    tperm, tstart = _bin(fmm, g, yd)
+    G32 = torch.empty(n, dtype=torch.float32, device="cuda")
+    Gtc = torch.empty(n, dtype=torch.float32, device="cuda")
+    fmm.fgt_h2p(g, ncut, 16, sigma, A, yd, tperm, tstart, G32)
+    fmm.fgt_h2p(g, ncut, 16, sigma, A, yd, tperm, tstart, Gtc, prec=fmm.FMM_TC_BF16X3)
+    fmm.fmm_sync_status()
+    g32, gtc = G32.cpu().numpy().astype(np.float64), Gtc.cpu().numpy().astype(np.float64)
+    assert _rel(gtc, g32) <= 1e-4
+    pick = np.random.default_rng(6).choice(n, 1500, replace=False)
+    ref = orc.fgt_hermite_eval_grid(g, ncut, 16, sigma, A.cpu().numpy().astype(np.float64), y[pick])
+    assert _rel(gtc[pick], ref) <= 1e-4
