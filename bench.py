@@ -702,7 +702,11 @@ def run_ours(args):
                 A = torch.empty((4 ** g, fp, fp), dtype=torch.float32, device=dev)
                 Cf = torch.empty_like(A)
                 W = torch.empty_like(A)
-                fmmgb.fgt_p2h(g, fp, sigma, fxd, fqd, A)
+                sperm = torch.empty(fcfg["n"], dtype=torch.int32, device=dev)
+                sstart = torch.empty(4 ** g + 1, dtype=torch.int32, device=dev)
+                swork = torch.empty(4 ** g, dtype=torch.int32, device=dev)
+                fmmgb.fgt_bin_points(g, fxd, sperm, sstart, swork)
+                fmmgb.fgt_p2h_binned(g, fp, sigma, fxd, fqd, sperm, A)
 
                 def fgt():
                     fmmgb.fgt_h2t(g, fcfg["ncut"], fp, sigma, A, Cf, work=W)
@@ -715,9 +719,6 @@ def run_ours(args):
                     fy = torch.rand((fcfg["n"], 2), dtype=torch.float64, device=dev,
                                     generator=torch.Generator(device=dev).manual_seed(workloads.SEED_BASE + 5))
                     Gy = torch.empty(fcfg["n"], dtype=torch.float32, device=dev)
-                    sperm = torch.empty(fcfg["n"], dtype=torch.int32, device=dev)
-                    sstart = torch.empty(4 ** g + 1, dtype=torch.int32, device=dev)
-                    swork = torch.empty(4 ** g, dtype=torch.int32, device=dev)
 
                     def fgt_all():
                         fmmgb.fgt_bin_points(g, fxd, sperm, sstart, swork)
