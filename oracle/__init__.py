@@ -84,6 +84,7 @@ _SIGS = {
     "orc_fgt_h2t_targets": (None, [_i, _i, _i, _d, _D, _i64, _I64, _D]),
     "orc_fgt_p2h_grid": (None, [_i, _i, _d, _i64, _D, _D, _D]),
     "orc_fgt_hermite_eval_grid": (None, [_i, _i, _i, _d, _D, _i64, _D, _D]),
+    "orc_p2p_uniform": (None, [_i, _i64, _D, _D, _i64, _D, _D]),
 }
 
 
@@ -242,6 +243,36 @@ def direct(xy, c, z) -> np.ndarray:
     phi = np.zeros_like(zr)
     lib().orc_direct(len(c), _dp(xy), _dp(c), zr.shape[0], _dp(zr), _dp(phi))
     return _r2c(phi)
+
+
+def p2p_uniform(level: int, xy, c, z) -> np.ndarray:
+    """Near field of a uniform tree at `level` (reading R15): at each z the direct sum over
+    the sources of its box and the adjacent boxes, skipping sources at exactly z."""
+    xy, c = _f64(xy), _f64(c)
+    zr = _c2r(np.asarray(z, dtype=np.complex128))
+    phi = np.zeros_like(zr)
+    lib().orc_p2p_uniform(level, len(c), _dp(xy), _dp(c), zr.shape[0], _dp(zr), _dp(phi))
+    return _r2c(phi)
+
+
+def fmm_potential_uniform(level: int, p: int, xy, c, z) -> np.ndarray:
+    """The whole FMM on a uniform tree to `level` (Sec. 2.1 stages 2-5): P2M at every level
+    2..level, M2L over the interaction lists of each level, L2L down, L2P at each z's box of
+    the finest level, plus the near field there (``p2p_uniform``)."""
+    xy, c = _f64(xy), _f64(c)
+    z = np.asarray(z, dtype=np.complex128)
+    L = {}
+    full = np.ones(sum(4 ** k for k in range(level + 1)), dtype=np.uint8)  # every box of levels 0..level exists
+    for l in range(2, level + 1):
+        Lr = _c2r(m2l_uniform(l, p, p2m_uniform(l, p, xy, c)))
+        if l > 2:
+            lib().orc_l2l_level(l, p, full.ctypes.data_as(_U8), _dp(_c2r(L[l - 1])), _dp(Lr))
+        L[l] = _r2c(Lr)
+    n = 1 << level
+    zb = np.clip(np.floor(z.real * n), 0, n - 1).astype(np.int64) + n * np.clip(
+        np.floor(z.imag * n), 0, n - 1).astype(np.int64)
+    far = _l2p_at_leaves(p, L, z, np.full(len(z), level), zb) if level >= 2 else 0.0
+    return far + p2p_uniform(level, xy, c, z)
 
 
 def l2l(p: int, lp: np.ndarray, shift: complex) -> np.ndarray:

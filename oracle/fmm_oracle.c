@@ -53,6 +53,10 @@
  *       fixed evaluation points, phi_far(z) the L2P of the LE of z's leaf
  *       after M2L over V-lists at every level and L2L down; the topology
  *       (each point's leaf) is frozen when points move.
+ *   R15 near field of a uniform tree at its finest level: a target takes the
+ *       sources of its own box and of the (up to 8) adjacent boxes, the
+ *       complement of the interaction lists of every level above; a source at
+ *       exactly the target's position (the point itself) is skipped.
  *   R14 FGT Hermite evaluation on the grid (Sec. 4.2 takes the clusters of a
  *       target as given): a target takes every box within Chebyshev distance
  *       ncut of its own box, the neighbourhood the H2T uses (R9).
@@ -410,6 +414,30 @@ void orc_direct(int64_t n, const double* xy, const double* c, int64_t nz, const 
         cplx zj = z[2 * j] + I * z[2 * j + 1];
         cplx s = 0.0;
         for (int64_t i = 0; i < n; ++i) s += c[i] / (zj - (xy[2 * i] + I * xy[2 * i + 1]));
+        phi[2 * j] = creal(s);
+        phi[2 * j + 1] = cimag(s);
+    }
+}
+
+/* Near field (Sec. 2.1 stage 5, Eq. n_body restricted, reading R15): for each
+ * target z, the direct sum over the sources whose level-`level` box is its own
+ * box or adjacent to it (Chebyshev distance <= 1), skipping sources at exactly
+ * z's position:  phi(z) = sum_{i near z, y_i != z} c_i / (z - y_i). */
+void orc_p2p_uniform(int level, int64_t n, const double* xy, const double* c, int64_t nz, const double* z,
+                     double* phi)
+{
+    for (int64_t j = 0; j < nz; ++j) {
+        int tx, ty;
+        point_box(level, z[2 * j], z[2 * j + 1], &tx, &ty);
+        cplx zj = z[2 * j] + I * z[2 * j + 1];
+        cplx s = 0.0;
+        for (int64_t i = 0; i < n; ++i) {
+            int sx, sy;
+            point_box(level, xy[2 * i], xy[2 * i + 1], &sx, &sy);
+            if (abs(sx - tx) > 1 || abs(sy - ty) > 1) continue;
+            if (xy[2 * i] == z[2 * j] && xy[2 * i + 1] == z[2 * j + 1]) continue;
+            s += c[i] / (zj - (xy[2 * i] + I * xy[2 * i + 1]));
+        }
         phi[2 * j] = creal(s);
         phi[2 * j + 1] = cimag(s);
     }
