@@ -463,6 +463,20 @@ def run_ours(args):
         if rank == 0:
             print(json.dumps({"mode": "kernels", "steps": args.steps, "launches_per_step": 2}))
         return 0
+    if args.mode == "kernels" and args.prec == "p2p":
+        # profiling case: the near field at level 8 of the 2^22-point headline workload
+        from paper_1009_3457_gb300 import farfield
+
+        xy, c = workloads.uniform_particles(CFG["n"], workloads.rng_for(WORKLOAD))
+        xyd, cd = torch.from_numpy(xy).to(dev), torch.from_numpy(c).to(dev)
+        pot = farfield.FmmPotential(fmmgb.fmm_build_lists(None, MAXL), P, xyd, cd, xyd)
+        for _ in range(args.steps):
+            fmmgb.fmm_p2p(MAXL, xyd, cd, pot.sperm, pot.sstart, xyd, pot.tperm, pot.tstart, pot.phi)
+        torch.cuda.synchronize()
+        fmmgb.fmm_sync_status()
+        if rank == 0:
+            print(json.dumps({"mode": "kernels", "steps": args.steps, "launches_per_step": 2}))
+        return 0
     if args.mode == "kernels" and args.prec == "h2p":
         # profiling case: FGT Hermite evaluation, sigma = 0.05, p = 16, 2^20 mixture targets
         fcfg = workloads.CONFIGS["fgt"]
@@ -623,7 +637,31 @@ def run_ours(args):
                 "paper_tesla_c1060_translations_per_s": paper_c1060[pp],
                 "ratio_to_paper_c1060": ntr_p / (ms * 1e-3) / paper_c1060[pp]}
             del Mq, Mqs, Lqs
-        del xyd, cd
+
+        # near field at level 8 (2^22 uniform points, targets = sources) and the whole FMM on the
+        # device: P2M, M2M, M2L (levels 2..8), L2L, L2P and P2P, every stage a library kernel
+        from paper_1009_3457_gb300 import farfield
+
+        tree8 = fmmgb.fmm_build_lists(None, MAXL)
+        pot = farfield.FmmPotential(tree8, P, xyd, cd, xyd)
+
+        def near():
+            fmmgb.fmm_p2p(MAXL, xyd, cd, pot.sperm, pot.sstart, xyd, pot.tperm, pot.tstart, pot.phi)
+
+        ms_p2p = statistics.median(_timed(torch, _graph(torch, near), args.steps, stream, flush))
+        counts = torch.diff(pot.sstart).cpu().numpy()
+        pairs = metrics.p2p_pairs(MAXL, counts, counts, self_pairs=int(CFG["n"]))
+        sfu_peak = SM_COUNT * 16 * SM_MAX_MHZ * 1e6  # one reciprocal per pair, 16 per SM per cycle
+        rows["fmm_p2p_level8"] = {
+            "ms": ms_p2p, "points": int(CFG["n"]), "pairs": pairs, "pairs_per_s": pairs / (ms_p2p * 1e-3),
+            "sfu_frac": pairs / (ms_p2p * 1e-3) / sfu_peak, "launches": 2,
+            "note": "claim table + kernel; targets = sources (each point skips itself)"}
+        ms_fmm = statistics.median(_timed(torch, _graph(torch, pot), args.steps, stream, flush))
+        rows["fmm_potential_level8_p16"] = {
+            "ms": ms_fmm, "points": int(CFG["n"]), "points_per_s": CFG["n"] / (ms_fmm * 1e-3),
+            "m2l_translations": NTR, "near_pairs": pairs,
+            "note": "P2M, M2M, M2L (levels 2-8, one launch), L2L, L2P, P2P: the potential at all 2^22 points"}
+        del pot, tree8, xyd, cd
 
         # adaptive tree: 2^20 Gaussian-mixture points, q = 64, levels 2..9, p = 16: V-list M2L,
         # its adjoint, and one gradient of the far-field objective (forward + backward)
@@ -788,7 +826,7 @@ def main():
     ap.add_argument("--mode", default="full", choices=["full", "kernels"],
                     help="kernels: only the timed step's launches (for ncu captures)")
     ap.add_argument("--tc", action="store_true", help="with --prec h2p: the tensor-core (BF16x3) form")
-    ap.add_argument("--prec", default="fp32", choices=["fp32", "tc3", "tc1", "batched", "fgt", "h2p"],
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "tc3", "tc1", "batched", "fgt", "h2p", "p2p"],
                     help="launches of --mode kernels: the step at this precision, or the 256-problem batch, "
                          "or the FGT H2T at sigma 0.05, p 16")
     ap.add_argument("--nprob", type=int, default=None,

@@ -447,6 +447,37 @@ int fgt_p2h_binned(int32_t grid_log2, int32_t p, double sigma, const double* x, 
 int fgt_h2p(int32_t grid_log2, int32_t n_cut, int32_t p, int32_t prec, double sigma, const float* A, const double* y,
             int64_t n, const int32_t* perm, const int32_t* box_start, float* G, int32_t flags, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Near field of a uniform quadtree at its finest level (Sec. 2.1 stage 5,
+ * Eq. n_body restricted to the own and adjacent boxes):
+ *
+ * fmm_bin_points -- fgt_bin_points on the 2^level x 2^level boxes of a
+ *   quadtree level (box floor(x 2^l), clamped): the same counting sort.
+ *
+ * fmm_p2p -- for every target z_j,
+ *     phi_j (+)= sum_{i : max(|sx - tx|, |sy - ty|) <= 1, y_i != z_j} c_i / (z_j - y_i),
+ *   (tx, ty) the level-`level` box of z_j, (sx, sy) that of source y_i.  With
+ *   fmm_m2l over levels 2..level, L2L down and L2P at level `level`, this is
+ *   the whole FMM potential at the targets.
+ *   xy: device float64 [n][2] source positions; c: device float64 [n]
+ *   strengths; src_perm, src_start: fmm_bin_points(level, xy, n, ...);
+ *   z: device float64 [nz][2] targets; tgt_perm, tgt_start:
+ *   fmm_bin_points(level, z, nz, ...); phi: device complex64 [nz], indexed
+ *   like z.  level 0..10, n and nz < 2^31, flags FMM_ACCUMULATE or 0.
+ *   FP32 arithmetic on positions taken relative to the target box's centre;
+ *   1e-30 is added to every squared distance, so a source at exactly a
+ *   target's position (e.g. the points themselves) contributes nothing
+ *   (strengths |c| < 3e8) and other pairs change by a relative 1e-30 / r^2.  Uses the per-device scratch of
+ *   fgt_h2p (calls that overlap on the GPU must be serialised).  A
+ *   permutation entry outside range or inconsistent box starts set the device
+ *   error word's check bit; the affected pairs are skipped.
+ * ------------------------------------------------------------------------- */
+int fmm_bin_points(int32_t level, const double* y, int64_t n, int32_t* perm, int32_t* box_start, int32_t* work,
+                   void* stream);
+int fmm_p2p(int32_t level, const double* xy, const double* c, int64_t n, const int32_t* src_perm,
+            const int32_t* src_start, const double* z, int64_t nz, const int32_t* tgt_perm, const int32_t* tgt_start,
+            void* phi, int32_t flags, void* stream);
+
 /* Read and clear the device error word after synchronising `stream`.
  * Returns FMM_OK, FMM_ETIMEOUT or FMM_EDEVICE. */
 int fmm_sync_status(void* stream);

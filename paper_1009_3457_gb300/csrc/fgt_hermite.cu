@@ -483,6 +483,13 @@ extern "C" int fgt_bin_points(int32_t grid_log2, const double* y, int64_t n, int
     return FMM_OK;
 }
 
+extern "C" int fmm_bin_points(int32_t level, const double* y, int64_t n, int32_t* perm, int32_t* box_start,
+                              int32_t* work, void* stream)
+{
+    // the boxes of quadtree level l are the cells of the 2^l x 2^l grid (reading R5)
+    return fgt_bin_points(level, y, n, perm, box_start, work, stream);
+}
+
 extern "C" int fgt_p2h_binned(int32_t grid_log2, int32_t p, double sigma, const double* x, const double* q, int64_t n,
                               const int32_t* perm, float* A, int32_t flags, void* stream)
 {

@@ -44,7 +44,10 @@ constexpr int kPlane = kHalo * kHalo + 1;  // float2 stride between k-planes
 
 template <int P>
 struct M2LCfg {
-    static constexpr bool SPLIT_ROWS = P > 16;     // p = 24: the two half-warps split the rows
+    // p <= 16: packed two-lane FP32 (f32x2) multiply-adds, the half-warps split the rows;
+    // p = 24: the half-warps split the rows (registers)
+    static constexpr bool PACKED = P >= 6 && P <= 16;
+    static constexpr bool SPLIT_ROWS = P > 16 || PACKED;
     static constexpr int RN = SPLIT_ROWS ? P / 2 : P;  // rows per lane
     static constexpr int NH = 2 * P - 1;           // Hankel diagonals
     static constexpr int CS = P * kPlane;          // float2 stride between class planes
@@ -60,6 +63,29 @@ __device__ __forceinline__ void cmac(float2& acc, const float2 w, const float2 m
     acc.x = fmaf(-w.y, m.y, acc.x);
     acc.y = fmaf(w.x, m.y, acc.y);
     acc.y = fmaf(w.y, m.x, acc.y);
+}
+
+// Packed two-lane FP32 (PTX f32x2): a complex number is one 64-bit register
+// pair (re, im), so acc += w m is two packed multiply-adds,
+//   acc += (w.x, w.y) (m.x, m.x) + (-w.y, w.x) (m.y, m.y),
+// each issuing the work of two FFMAs in one slot.
+__device__ __forceinline__ unsigned long long pk2(float a, float b)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float2 upk2(unsigned long long v)
+{
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+    return r;
+}
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b, unsigned long long c)
+{
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
 }
 
 // Number of 4 x 4-parent tiles of a level (levels 0 and 1 have no lists).
@@ -225,6 +251,45 @@ __device__ __forceinline__ void m2l_tile(unsigned char* raw, const TileGeom& g, 
                 }
             }
         }
+    } else if constexpr (C::PACKED) {
+        // half-warp `half` takes rows [RN half, RN half + RN); all 27 entries; packed
+        // accumulators and operator window (w and i w), m broadcast per k
+        const int n0 = half * RN;
+        unsigned long long pacc[RN];
+#pragma unroll
+        for (int i = 0; i < RN; ++i) pacc[i] = 0ull;
+#pragma unroll 1
+        for (int e = 0; e < 27; ++e) {
+            const int2 ent = mylist[e];
+            const float2* hrow = s.hs + ent.x + n0;
+            const float2* src = tbase + ent.y;
+            unsigned long long w[RN], wr[RN];
+#pragma unroll
+            for (int i = 0; i < RN; ++i) {
+                const float2 h = hrow[i];
+                w[i] = pk2(h.x, h.y);
+                wr[i] = pk2(-h.y, h.x);
+            }
+#pragma unroll
+            for (int k = 0; k < P; ++k) {
+                const float2 m = src[k * kPlane];
+                const unsigned long long mx = pk2(m.x, m.x), my = pk2(m.y, m.y);
+#pragma unroll
+                for (int i = 0; i < RN; ++i) pacc[i] = fma2(wr[i], my, fma2(w[i], mx, pacc[i]));
+                if (k + 1 < P) {
+#pragma unroll
+                    for (int i = 0; i + 1 < RN; ++i) {
+                        w[i] = w[i + 1];
+                        wr[i] = wr[i + 1];
+                    }
+                    const float2 h = hrow[RN + k];
+                    w[RN - 1] = pk2(h.x, h.y);
+                    wr[RN - 1] = pk2(-h.y, h.x);
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < RN; ++i) acc[i] = upk2(pacc[i]);
     } else {
         // half-warp `half` takes rows [RN half, RN half + RN); all 27 entries
         const int n0 = half * RN;

@@ -1,0 +1,300 @@
+// p2p.cu -- the near field of a uniform quadtree at its finest level
+// (Sec. 2.1 stage 5: Eq. n_body restricted to each target's own and adjacent
+// boxes, the complement of the interaction lists of every level):
+//
+//   phi(z) (+)= sum_{i : box(y_i) adjacent to or equal box(z), y_i != z} c_i / (z - y_i).
+//
+// Targets and sources are binned by box (fmm_bin_points); a pre-pass copies the
+// sources into box order (x, y, c in FP64), so a box's sources are one
+// contiguous range.  Persistent CTAs of
+// 128 threads claim runs of up to 64 targets of one box from a claim table
+// (a finest-level box holds a few dozen points), gather the sources of the
+// 3 x 3 neighbourhood through the source permutation into shared memory in
+// batches -- position relative to the target box's centre (formed in FP64,
+// kept in FP32) and strength -- and each warp sums all the run's targets (two
+// per lane) against a quarter of every batch; the four partial sums of a
+// target meet in shared memory.  In FP32:
+//   1/(dx + i dy) = (dx - i dy) / r2 with one approximate reciprocal per pair.
+// Positions relative to the target box keep |dx|, |dy| <= 1.5 box sides, so
+// FP32 carries the difference of two nearby points to ~2^-24 of a box side.
+// A source at the target's position (the point itself, when targets are the
+// sources) contributes nothing: r^2 carries a 1e-30 offset and dx = dy = 0.
+#include <mutex>
+
+#include "fgt_hermite.cuh"
+
+namespace fmmgb {
+
+constexpr int kP2pThreads = 128;
+constexpr int kP2pWarps = kP2pThreads / 32;     // each takes a quarter of the sources
+constexpr int kP2pR = 2;                        // targets per lane
+constexpr int kP2pRun = 32 * kP2pR;             // targets per claim
+constexpr int kP2pBatch = 1024;                 // sources per shared-memory batch
+// added to every r^2: a source at the target's position (dx = dy = 0) then contributes
+// exactly 0 -- c / 1e-30 is finite for |c| < 3e8 -- and any other pair changes by a
+// relative 1e-30 / r^2 (below FP32 rounding for distances above 1e-11)
+constexpr float kP2pTiny = 1e-30f;
+
+struct P2pArgs {
+    int level, n, nz, accumulate;
+    const double* xy;
+    const double* c;
+    const double4* src;  // sources in box order: x, y, c (p2p_sort_kernel)
+    const int* sperm;
+    const int* sstart;
+    const double* z;
+    const int* tperm;
+    const int* tstart;
+    const int* claims;
+    float2* phi;
+    int* cursor;  // [0] next claim index, [1] CTAs finished
+    int* err;
+};
+
+// sources in box order, so that a box's sources are one contiguous range
+__global__ void p2p_sort_kernel(const double* __restrict__ xy, const double* __restrict__ c, const int* __restrict__ perm,
+                                int n, double4* __restrict__ out, int* err)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int i = __ldg(perm + k);
+    if ((unsigned)i >= (unsigned)n) {
+        atomicOr(err, DEV_ERR_CHECK);
+        out[k] = make_double4(0.0, 0.0, 0.0, 0.0);
+        return;
+    }
+    out[k] = make_double4(__ldg(xy + 2 * (size_t)i), __ldg(xy + 2 * (size_t)i + 1), __ldg(c + i), 0.0);
+}
+
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__global__ void __launch_bounds__(kP2pThreads) fmm_p2p_kernel(P2pArgs a)
+{
+    __shared__ float4 s_src[kP2pBatch];  // x - cx, y - cy, c
+    __shared__ int s_claim[3];
+    __shared__ int s_box[9], s_pre[10];  // first sorted source of each neighbour box, prefix of their counts
+    __shared__ float2 s_part[kP2pWarps - 1][kP2pRun];  // partial sums of warps 1..3
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int side = 1 << a.level, nbox = side * side;
+    const double inv_side = 1.0 / side;
+    const int total = __ldg(a.claims + nbox);
+
+    for (;;) {
+        if (tid == 0) {
+            const int k = atomicAdd(a.cursor, 1);
+            int f = -1, e = -1, b = 0;
+            if (k < total) {
+                h2p_claim_range(a.claims, a.tstart, nbox, a.nz, kP2pRun, k, &f, &e, &b);
+                if (f >= e) atomicOr(a.err, DEV_ERR_CHECK);  // box_start does not bin [0, nz)
+            }
+            s_claim[0] = f;
+            s_claim[1] = e;
+            s_claim[2] = b;
+        }
+        if (tid < 9) {
+            s_box[tid] = -1;
+        }
+        __syncthreads();
+        const int first = s_claim[0], end = s_claim[1], box = s_claim[2];
+        if (first < 0) break;
+        const int tx = box & (side - 1), ty = box >> a.level;
+        const double cx = (tx + 0.5) * inv_side, cy = (ty + 0.5) * inv_side;
+        if (tid == 0) {
+            int acc = 0;
+            for (int q = 0; q < 9; ++q) {
+                const int sx = tx + q % 3 - 1, sy = ty + q / 3 - 1;
+                s_pre[q] = acc;
+                if (sx < 0 || sy < 0 || sx >= side || sy >= side) continue;
+                const int b = sy * side + sx;
+                const int b0 = __ldg(a.sstart + b), m = __ldg(a.sstart + b + 1) - b0;
+                if (m <= 0 || b0 < 0 || b0 + m > a.n) continue;
+                s_box[q] = b0;
+                acc += m;
+            }
+            s_pre[9] = acc;
+        }
+
+        int tj[kP2pR];
+        float zx[kP2pR], zy[kP2pR], re[kP2pR], im[kP2pR];
+#pragma unroll
+        for (int r = 0; r < kP2pR; ++r) {
+            const int pos = first + r * 32 + lane;
+            tj[r] = -1;
+            zx[r] = zy[r] = re[r] = im[r] = 0.f;
+            if (pos < end) {
+                const int j = __ldg(a.tperm + pos);
+                if ((unsigned)j < (unsigned)a.nz) {
+                    tj[r] = j;
+                    zx[r] = (float)(__ldg(a.z + 2 * (size_t)j) - cx);
+                    zy[r] = (float)(__ldg(a.z + 2 * (size_t)j + 1) - cy);
+                } else if (warp == 0) {
+                    atomicOr(a.err, DEV_ERR_CHECK);
+                }
+            }
+        }
+        __syncthreads();
+        const int S = s_pre[9];
+
+        for (int base = 0; base < S; base += kP2pBatch) {
+            const int cnt = min(kP2pBatch, S - base);
+            for (int i = tid; i < cnt; i += kP2pThreads) {
+                const int g = base + i;
+                int q = 0;
+                while (q < 8 && s_pre[q + 1] <= g) ++q;
+                const int b0 = s_box[q];
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (b0 >= 0) {
+                    const double4 u = a.src[b0 + (g - s_pre[q])];
+                    v.x = (float)(u.x - cx);
+                    v.y = (float)(u.y - cy);
+                    v.z = (float)u.z;
+                }
+                s_src[i] = v;
+            }
+            __syncthreads();
+            {
+#pragma unroll 4
+                for (int i = warp; i < cnt; i += kP2pWarps) {
+                    const float4 v = s_src[i];
+#pragma unroll
+                    for (int r = 0; r < kP2pR; ++r) {
+                        const float dx = zx[r] - v.x, dy = zy[r] - v.y;
+                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, kP2pTiny));
+                        const float w = v.z * rcp_approx(r2);
+                        re[r] = fmaf(w, dx, re[r]);
+                        im[r] = fmaf(-w, dy, im[r]);
+                    }
+                }
+            }
+            __syncthreads();  // the batch buffer is refilled next
+        }
+        if (warp > 0) {
+#pragma unroll
+            for (int r = 0; r < kP2pR; ++r) s_part[warp - 1][r * 32 + lane] = make_float2(re[r], im[r]);
+        }
+        __syncthreads();
+        if (warp > 0) continue;  // warp 0 writes; every warp is back at the claim's barrier next
+#pragma unroll
+        for (int r = 0; r < kP2pR; ++r) {
+            if (tj[r] < 0) continue;
+            float2 o = make_float2(re[r], im[r]);
+#pragma unroll
+            for (int q = 0; q < kP2pWarps - 1; ++q) {
+                o.x += s_part[q][r * 32 + lane].x;
+                o.y += s_part[q][r * 32 + lane].y;
+            }
+            if (a.accumulate) {
+                const float2 old = a.phi[tj[r]];
+                o.x += old.x;
+                o.y += old.y;
+            }
+            a.phi[tj[r]] = o;
+        }
+    }
+    // the last CTA to finish returns the cursor slot to zero for its next use
+    if (tid == 0) {
+        __threadfence();
+        if (atomicAdd(a.cursor + 1, 1) == (int)gridDim.x - 1) {
+            atomicExch(a.cursor, 0);
+            atomicExch(a.cursor + 1, 0);
+        }
+    }
+}
+
+// Per-device buffer of sorted sources (grown on demand).
+static std::mutex g_src_mu;
+static double4* g_src[64];
+static size_t g_src_bytes[64];
+
+static int p2p_source_buffer(size_t bytes, double4** out)
+{
+    int dev = 0;
+    FMM_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(FMM_EUNSUPPORTED, "fmm_p2p: device ordinal %d above 63", dev);
+    std::lock_guard<std::mutex> lk(g_src_mu);
+    if (g_src_bytes[dev] < bytes) {
+        if (g_src[dev]) {
+            FMM_CUDA_TRY(cudaDeviceSynchronize());
+            cudaFree(g_src[dev]);
+            g_src[dev] = nullptr;
+            g_src_bytes[dev] = 0;
+        }
+        FMM_CUDA_TRY(cudaMalloc(&g_src[dev], bytes));
+        g_src_bytes[dev] = bytes;
+    }
+    *out = g_src[dev];
+    return FMM_OK;
+}
+
+}  // namespace fmmgb
+
+using namespace fmmgb;
+
+extern "C" int fmm_p2p(int32_t level, const double* xy, const double* c, int64_t n, const int32_t* src_perm,
+                       const int32_t* src_start, const double* z, int64_t nz, const int32_t* tgt_perm,
+                       const int32_t* tgt_start, void* phi, int32_t flags, void* stream)
+{
+    clear_error();
+    if (level < 0 || level > 10) return fail(FMM_EINVAL, "fmm_p2p: level %d outside 0..10", level);
+    if (n < 0 || n > INT32_MAX || nz < 0 || nz > INT32_MAX)
+        return fail(FMM_EINVAL, "fmm_p2p: point counts must lie in 0..2^31-1");
+    if (!src_start || !tgt_start || (n > 0 && (!xy || !c || !src_perm)) || (nz > 0 && (!z || !tgt_perm || !phi)))
+        return fail(FMM_EINVAL, "fmm_p2p: NULL pointer");
+    if (((uintptr_t)xy & 7) || ((uintptr_t)c & 7) || ((uintptr_t)z & 7) || ((uintptr_t)phi & 7) ||
+        ((uintptr_t)src_perm & 3) || ((uintptr_t)src_start & 3) || ((uintptr_t)tgt_perm & 3) ||
+        ((uintptr_t)tgt_start & 3))
+        return fail(FMM_EINVAL, "fmm_p2p: misaligned pointer (xy, c, z, phi 8 bytes; int32 arrays 4)");
+    if (flags & ~FMM_ACCUMULATE) return fail(FMM_EINVAL, "fmm_p2p: unknown flags 0x%x", flags);
+    if (nz == 0) return FMM_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    P2pArgs args;
+    args.level = level;
+    args.n = (int)n;
+    args.nz = (int)nz;
+    args.accumulate = (flags & FMM_ACCUMULATE) ? 1 : 0;
+    args.xy = xy;
+    args.c = c;
+    args.sperm = src_perm;
+    args.sstart = src_start;
+    args.z = z;
+    args.tperm = tgt_perm;
+    args.tstart = tgt_start;
+    args.phi = reinterpret_cast<float2*>(phi);
+    if (int rc = tile_counter(&args.cursor, st)) return rc;
+    if (int rc = device_error_word(&args.err)) return rc;
+    unsigned char* scratch = nullptr;
+    if (int rc = fgt_flag_buffer(&scratch)) return rc;
+    int* claims = reinterpret_cast<int*>(scratch + kFgtFlagBytes);
+    args.claims = claims;
+    const int nbox = 1 << (2 * level);
+    if (int rc = launch_h2p_claims(nbox, tgt_start, kP2pRun, claims, args.err, st)) return rc;
+    double4* src = nullptr;
+    if (n > 0) {
+        if (int rc = p2p_source_buffer((size_t)n * sizeof(double4), &src)) return rc;
+        p2p_sort_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(xy, c, src_perm, (int)n, src, args.err);
+        FMM_CUDA_TRY(cudaGetLastError());
+    }
+    args.src = src;
+    static int occ;
+    static std::mutex mu;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (!occ) {
+            FMM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fmm_p2p_kernel, kP2pThreads, 0));
+            if (occ < 1) occ = 1;
+        }
+    }
+    int sms = 0;
+    if (int rc = device_sm_count(&sms)) return rc;
+    const int64_t most = nz / kP2pRun + nbox;  // claims can be no more
+    const int grid = (int)std::min<int64_t>((int64_t)occ * sms, most);
+    fmm_p2p_kernel<<<grid, kP2pThreads, 0, st>>>(args);
+    FMM_CUDA_TRY(cudaGetLastError());
+    return FMM_OK;
+}

@@ -97,3 +97,53 @@ def far_field_objective(tree, p: int, xy: torch.Tensor, c: torch.Tensor, leaf, z
     zlev, zbox = z_leaf
     return FarFieldObjective.apply(xy.contiguous(), tree, p, c.contiguous(), zxy, zlev.to(torch.int32).contiguous(),
                                    zbox.to(torch.int64).contiguous(), w.contiguous())
+
+
+class FmmPotential:
+    """The whole FMM on a uniform tree to level L (Sec. 2.1 stages 2-5), every stage a
+    library kernel: P2M at level L, M2M up, M2L over the interaction lists of levels 2..L,
+    L2L down, L2P at each target's level-L box, plus the near field (own and adjacent
+    boxes) by ``fmm_p2p``.
+
+        phi(z) = sum_i c_i / (z - y_i)   (sources at exactly z skipped)
+
+    Buffers are allocated once; ``__call__`` enqueues the whole evaluation on the
+    current stream (capturable as a CUDA graph after a first call)."""
+
+    def __init__(self, tree, p: int, xy: torch.Tensor, c: torch.Tensor, z: torch.Tensor, prec: int = 0):
+        if tree.adaptive or tree.periodic or tree.max_level < 2:
+            raise ValueError("FmmPotential takes a uniform, non-periodic tree of depth >= 2")
+        self.tree, self.p, self.prec = tree, p, prec
+        self.L = L = tree.max_level
+        dev = xy.device
+        self.xy, self.c, self.z = xy.contiguous(), c.contiguous(), z.contiguous()
+        self.levels = list(range(2, L + 1))
+        self.Ms = [torch.empty((4 ** l, p), dtype=torch.complex64, device=dev) for l in self.levels]
+        self.Ls = [torch.empty_like(M) for M in self.Ms]
+        nb = 4 ** L
+
+        def bins(pts):
+            perm = torch.empty(pts.shape[0], dtype=torch.int32, device=dev)
+            start = torch.empty(nb + 1, dtype=torch.int32, device=dev)
+            work = torch.empty(nb, dtype=torch.int32, device=dev)
+            fmmgb.fmm_bin_points(L, pts, perm, start, work)
+            return perm, start
+
+        self.sperm, self.sstart = bins(self.xy)
+        self.tperm, self.tstart = bins(self.z)
+        lev, box = leaf_boxes(tree, self.z)
+        self.zlev, self.zbox = lev.contiguous(), box.contiguous()
+        self.phi = torch.empty(self.z.shape[0], dtype=torch.complex64, device=dev)
+
+    def __call__(self) -> torch.Tensor:
+        p, L = self.p, self.L
+        fmmgb.fmm_p2m(L, p, self.xy, self.c, self.Ms[-1])
+        for i in range(len(self.levels) - 1, 0, -1):
+            fmmgb.fmm_m2m(self.levels[i], p, self.Ms[i], self.Ms[i - 1])
+        fmmgb.fmm_m2l_levels(self.tree, 2, p, self.Ms, self.Ls, prec=self.prec)
+        for i in range(1, len(self.levels)):
+            fmmgb.fmm_l2l(self.levels[i], p, self.Ls[i - 1], self.Ls[i], accumulate=True)
+        fmmgb.fmm_l2p(p, self.z, self.zlev, self.zbox, dict(zip(self.levels, self.Ls)), L, self.phi)
+        fmmgb.fmm_p2p(L, self.xy, self.c, self.sperm, self.sstart, self.z, self.tperm, self.tstart, self.phi,
+                      accumulate=True)
+        return self.phi

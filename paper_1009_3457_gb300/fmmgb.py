@@ -107,6 +107,8 @@ SIGNATURES = {
     "fgt_t2p": (ctypes.c_int, [_i32, _i32, _d, _vp, _vp, _i64, _vp, _i32, _vp]),
     "fgt_p2h": (ctypes.c_int, [_i32, _i32, _d, _vp, _vp, _i64, _vp, _i32, _vp]),
     "fgt_bin_points": (ctypes.c_int, [_i32, _vp, _i64, _vp, _vp, _vp, _vp]),
+    "fmm_bin_points": (ctypes.c_int, [_i32, _vp, _i64, _vp, _vp, _vp, _vp]),
+    "fmm_p2p": (ctypes.c_int, [_i32, _vp, _vp, _i64, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _i32, _vp]),
     "fgt_p2h_binned": (ctypes.c_int, [_i32, _i32, _d, _vp, _vp, _i64, _vp, _vp, _i32, _vp]),
     "fgt_h2p": (ctypes.c_int, [_i32, _i32, _i32, _i32, _d, _vp, _vp, _i64, _vp, _vp, _vp, _i32, _vp]),
     "fmm_sync_status": (ctypes.c_int, [_vp]),
@@ -391,6 +393,24 @@ def fgt_bin_points(grid_log2: int, y, perm, box_start, work, stream=None):
     n = 0 if y is None else y.shape[0]
     _check(load().fgt_bin_points(grid_log2, _ptr(y), n, _ptr(perm), _ptr(box_start), _ptr(work),
                                  _stream(stream)))
+
+
+def fmm_bin_points(level: int, y, perm, box_start, work, stream=None):
+    """fgt_bin_points on the boxes of quadtree level `level`."""
+    n = 0 if y is None else y.shape[0]
+    _check(load().fmm_bin_points(level, _ptr(y), n, _ptr(perm), _ptr(box_start), _ptr(work), _stream(stream)))
+
+
+def fmm_p2p(level: int, xy, c, src_perm, src_start, z, tgt_perm, tgt_start, phi, accumulate: bool = False,
+            stream=None):
+    """Near field at the finest level of a uniform tree: phi (complex64 [nz]) at the targets z
+    (float64 [nz, 2]) from the sources xy, c in the own and adjacent boxes; both sets binned
+    by fmm_bin_points at `level`."""
+    n = 0 if c is None else c.numel()
+    nz = 0 if z is None else z.shape[0]
+    _check(load().fmm_p2p(level, _ptr(xy), _ptr(c), n, _ptr(src_perm), _ptr(src_start), _ptr(z), nz,
+                          _ptr(tgt_perm), _ptr(tgt_start), _ptr(phi), FMM_ACCUMULATE if accumulate else 0,
+                          _stream(stream)))
 
 
 def fgt_p2h_binned(grid_log2: int, p: int, sigma: float, x, q, perm, A, accumulate: bool = False, stream=None):

@@ -94,3 +94,14 @@ def fgt_h2p_tc_mma_flops(g: int, ncut: int, target_counts, products: int = 3, p:
                 tiles = -(-int(t[ty, tx]) // rows)
                 total += tiles * h * 2 * rows * (w * p) * p
     return total * products
+
+
+def p2p_pairs(level: int, target_counts, source_counts, self_pairs: int = 0) -> int:
+    """(target, source) pairs of the near field at `level`: each target times the sources of
+    its box and the adjacent boxes, less `self_pairs` (targets that are sources)."""
+    import numpy as np
+
+    n = 1 << level
+    s = np.pad(np.asarray(source_counts, dtype=np.int64).reshape(n, n), 1)
+    near = sum(s[1 + dy:1 + dy + n, 1 + dx:1 + dx + n] for dy in (-1, 0, 1) for dx in (-1, 0, 1))
+    return int((np.asarray(target_counts, dtype=np.int64).reshape(n, n) * near).sum()) - int(self_pairs)

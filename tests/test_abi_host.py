@@ -241,3 +241,14 @@ def test_fgt_hermite_entry_points_reject_bad_arguments(fmm):
     assert lib.fgt_h2p(3, 2, 8, 7, 0.1, 64, 128, 10, 256, 512, 1024, 0, None) == fmm.FMM_EINVAL   # precision
     assert lib.fgt_h2p(3, 2, 8, T3, 0.1, 64, 128, 10, 256, 512, 1024, 0, None) == fmm.FMM_EUNSUPPORTED   # TC p
     assert lib.fgt_h2p(3, 16, 16, T3, 0.1, 64, 128, 10, 256, 512, 1024, 0, None) == fmm.FMM_EUNSUPPORTED  # TC n_cut
+
+
+def test_p2p_rejects_bad_arguments(fmm):
+    lib = fmm.load()
+    # fmm_p2p(level, xy, c, n, sperm, sstart, z, nz, tperm, tstart, phi, flags, stream)
+    assert lib.fmm_p2p(11, 64, 128, 10, 256, 512, 1024, 10, 2048, 4096, 8192, 0, None) == fmm.FMM_EINVAL  # level
+    assert lib.fmm_p2p(3, 64, 128, -1, 256, 512, 1024, 10, 2048, 4096, 8192, 0, None) == fmm.FMM_EINVAL  # n
+    assert lib.fmm_p2p(3, 64, 128, 10, 256, None, 1024, 10, 2048, 4096, 8192, 0, None) == fmm.FMM_EINVAL  # src_start
+    assert lib.fmm_p2p(3, 64, 128, 10, 256, 512, 1028, 10, 2048, 4096, 8192, 0, None) == fmm.FMM_EINVAL  # z misaligned
+    assert lib.fmm_p2p(3, 64, 128, 10, 256, 512, 1024, 10, 2048, 4096, 8192, 8, None) == fmm.FMM_EINVAL  # flags
+    assert lib.fmm_bin_points(11, 64, 10, 128, 256, 512, None) == fmm.FMM_EINVAL
