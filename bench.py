@@ -610,6 +610,23 @@ def run_ours(args):
                                                   "measured coefficient errors in tests/test_m2l_tc_gpu.py"}
         rows["tc_vs_fp32_speedup_p16"] = {"speedup": statistics.median(step_ms) / rows["m2l_tc_bf16x3_levels_2_8"]["ms"]}
         del M24, L24, M24s, L24s
+        # the paper's two-kernel data flow (per-translation LEs written to HBM, then a separate
+        # reduction) on the headline workload, against the fused stencil
+        work = torch.empty((4 ** MAXL, 27, P), dtype=torch.complex64, device=dev)
+        Lpd = [torch.empty_like(m) for m in Ms]
+
+        def paper_design():
+            for i, l in enumerate(LEVELS):
+                fmmgb.fmm_m2l_paper_design(tree, l, P, Ms[i], Lpd[i], work)
+
+        ms_pd = statistics.median(_timed(torch, _graph(torch, paper_design), args.steps, stream, flush))
+        rows["m2l_paper_design_levels_2_8"] = {
+            "translations_per_s": NTR / (ms_pd * 1e-3), "ms": ms_pd, "launches": 2 * len(LEVELS),
+            "le_bytes_through_hbm": 2 * NTR * P * 8,
+            "fused_speedup": ms_pd / statistics.median(step_ms),
+            "note": "block per source ME, thread per LE row, one LE per translation to HBM, then a reduction "
+                    "kernel per level (Sec. 4.1.1-4.1.2); the same operator tables"}
+        del work, Lpd
         # paper-shape periodic runs (27 translations per box, levels 2..8, Tables m2ltesla and
         # m2lfermi): p = 8, 12, 16; the C1060 rates of the largest size printed in Table m2ltesla
         # go beside them as context

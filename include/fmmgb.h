@@ -478,6 +478,19 @@ int fmm_p2p(int32_t level, const double* xy, const double* c, int64_t n, const i
             const int32_t* src_start, const double* z, int64_t nz, const int32_t* tgt_perm, const int32_t* tgt_start,
             void* phi, int32_t flags, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * fmm_m2l_paper_design -- the paper's own M2L data flow (Sec. 4.1.1-4.1.2),
+ * for comparison with fmm_m2l: a thread block per source ME translates it to
+ * every target whose interaction list holds it, one thread per LE row, and
+ * writes one LE per translation to `work`; a second kernel sums each
+ * target's translated LEs (the paper's separate reduction).  Same result as
+ * fmm_m2l (FP32, up to summation order) at one level of a uniform,
+ * non-periodic tree; p 8, 12 or 16.  work: device, 4^level * 27 * p complex64
+ * (16-byte aligned), overwritten.  flags: FMM_ACCUMULATE.
+ * ------------------------------------------------------------------------- */
+int fmm_m2l_paper_design(const fmm_tree* tree, int32_t level, int32_t p, const void* M, void* L, void* work,
+                         int32_t flags, void* stream);
+
 /* Read and clear the device error word after synchronising `stream`.
  * Returns FMM_OK, FMM_ETIMEOUT or FMM_EDEVICE. */
 int fmm_sync_status(void* stream);

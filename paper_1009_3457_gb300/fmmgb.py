@@ -108,6 +108,7 @@ SIGNATURES = {
     "fgt_p2h": (ctypes.c_int, [_i32, _i32, _d, _vp, _vp, _i64, _vp, _i32, _vp]),
     "fgt_bin_points": (ctypes.c_int, [_i32, _vp, _i64, _vp, _vp, _vp, _vp]),
     "fmm_bin_points": (ctypes.c_int, [_i32, _vp, _i64, _vp, _vp, _vp, _vp]),
+    "fmm_m2l_paper_design": (ctypes.c_int, [_vp, _i32, _i32, _vp, _vp, _vp, _i32, _vp]),
     "fmm_p2p": (ctypes.c_int, [_i32, _vp, _vp, _i64, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _i32, _vp]),
     "fgt_p2h_binned": (ctypes.c_int, [_i32, _i32, _d, _vp, _vp, _i64, _vp, _vp, _i32, _vp]),
     "fgt_h2p": (ctypes.c_int, [_i32, _i32, _i32, _i32, _d, _vp, _vp, _i64, _vp, _vp, _vp, _i32, _vp]),
@@ -393,6 +394,12 @@ def fgt_bin_points(grid_log2: int, y, perm, box_start, work, stream=None):
     n = 0 if y is None else y.shape[0]
     _check(load().fgt_bin_points(grid_log2, _ptr(y), n, _ptr(perm), _ptr(box_start), _ptr(work),
                                  _stream(stream)))
+
+
+def fmm_m2l_paper_design(tree: Tree, level: int, p: int, M, L, work, accumulate: bool = False, stream=None):
+    """The paper's two-kernel M2L (per-translation LEs in `work`, then a reduction); for comparison."""
+    _check(load().fmm_m2l_paper_design(tree.handle, level, p, _ptr(M), _ptr(L), _ptr(work),
+                                       FMM_ACCUMULATE if accumulate else 0, _stream(stream)))
 
 
 def fmm_bin_points(level: int, y, perm, box_start, work, stream=None):

@@ -252,3 +252,15 @@ def test_p2p_rejects_bad_arguments(fmm):
     assert lib.fmm_p2p(3, 64, 128, 10, 256, 512, 1028, 10, 2048, 4096, 8192, 0, None) == fmm.FMM_EINVAL  # z misaligned
     assert lib.fmm_p2p(3, 64, 128, 10, 256, 512, 1024, 10, 2048, 4096, 8192, 8, None) == fmm.FMM_EINVAL  # flags
     assert lib.fmm_bin_points(11, 64, 10, 128, 256, 512, None) == fmm.FMM_EINVAL
+
+
+def test_paper_design_rejects_bad_arguments(fmm):
+    lib = fmm.load()
+    assert lib.fmm_m2l_paper_design(None, 3, 8, 64, 128, 256, 0, None) == fmm.FMM_EINVAL
+    tree = fmm.fmm_build_lists(None, 4)
+    assert lib.fmm_m2l_paper_design(tree.handle, 1, 8, 64, 128, 256, 0, None) == fmm.FMM_EINVAL   # level
+    assert lib.fmm_m2l_paper_design(tree.handle, 3, 6, 64, 128, 256, 0, None) == fmm.FMM_EINVAL   # p
+    assert lib.fmm_m2l_paper_design(tree.handle, 3, 8, 64, 136, 256, 0, None) == fmm.FMM_EINVAL   # misaligned
+    assert lib.fmm_m2l_paper_design(tree.handle, 3, 8, 64, 128, None, 0, None) == fmm.FMM_EINVAL  # work
+    ptree = fmm.fmm_build_lists(None, 4, periodic=True)
+    assert lib.fmm_m2l_paper_design(ptree.handle, 3, 8, 64, 128, 256, 0, None) == fmm.FMM_EUNSUPPORTED
