@@ -33,13 +33,13 @@
 namespace fmmgb {
 
 constexpr int kFgtSeg = 4;       // boxes per CTA along the pass axis
-constexpr int kFgtGroups = 3;    // tap groups per box: partial sums reduced in shared memory
+constexpr int kFgtGroups = 7;    // tap groups per box: partial sums reduced in shared memory
 constexpr int kFgtMaxCut = 16;   // largest n_cut accepted
 
 // Thread mapping: (tap group, box of the segment, 4-row block, 4-column block);
-// a thread accumulates a 4 x 4 block of one box's output over a third of the
+// a thread accumulates a 4 x 4 block of one box's output over a seventh of the
 // taps.  At sigma = 0.05 (32 x 32 boxes) and p = 16 a pass runs 256 CTAs of
-// 192 threads.
+// 448 threads: enough warps per SM to hide the halo staging of this small grid.
 template <int P>
 struct FgtCfg {
     static constexpr int RB = 4;                // output rows (b) per thread
