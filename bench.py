@@ -10,7 +10,8 @@ scaled MEs) are built on the device by fmm_p2m / fmm_m2m before timing.
 
 Prints one JSON line.  `value` is whole-job translations/s with inputs resident
 in HBM; `e2e` is the same metric with a pinned-host -> device copy of the
-step's MEs and a device -> host copy of its LEs inside the timed region.
+step's MEs and a device -> host copy of its LEs inside the timed region
+(pipeline.HostStreamM2L: consecutive steps overlap on three streams).
 Under torchrun each rank runs an independent replica of the workload (the
 single-tree M2L step has no cross-GPU exchange in this build: replicas only).
 """
@@ -46,9 +47,11 @@ CONFIG = {
                 "p=16, FP32 complex coefficients, all interaction-list translations of levels 2-8 "
                 "(one multi-level launch; one-launch-per-level timing under rows)",
     "points": CFG["n"], "max_level": MAXL, "p": P, "translations_per_step": NTR,
-    "levels": f"{LEVELS[0]}-{LEVELS[-1]}", "l2": "flushed between timed steps (256 MiB write)",
+    "levels": f"{LEVELS[0]}-{LEVELS[-1]}",
+    "l2": "flushed between timed device-resident steps (256 MiB write); in e2e every step's MEs arrive by copy",
     "timing": "device-resident step captured once as a CUDA graph (one kernel) and replayed between "
-              "CUDA events; e2e calls the library from the host every step",
+              "CUDA events; e2e calls the library from the host every step, MEs in from and LEs out to "
+              "pinned host memory, consecutive steps overlapped on three streams",
     "parallelism": "replicas",
 }
 SM_COUNT = 152
@@ -533,26 +536,27 @@ def run_ours(args):
     tot_ms = fdist.max_over_ranks(sum(step_ms))
     value = fdist.job_rate(NTR * args.steps, sum(step_ms) * 1e-3)
 
-    # --- e2e: host buffers through the same public call ---
-    Mh = {l: torch.empty_like(M[l], device="cpu").pin_memory() for l in LEVELS}
-    Lh = {l: torch.empty_like(Lx[l], device="cpu").pin_memory() for l in LEVELS}
-    for l in LEVELS:
-        Mh[l].copy_(M[l])
+    # --- e2e: host buffers through the library's public API: every step copies its MEs in
+    # from pinned host memory and its LEs back out; consecutive steps overlap on three
+    # streams (pipeline.HostStreamM2L), the way a stream of problems is served ---
+    from paper_1009_3457_gb300 import pipeline
+
+    pipe = pipeline.HostStreamM2L(tree, LEVELS[0], LEVELS[-1], P)
+    Mh = torch.empty(pipe.flat_size(), dtype=torch.complex64).pin_memory()  # the levels back to back
+    for v, l in zip(pipe.level_views(Mh), LEVELS):
+        v.copy_(M[l])
+    Lh = [torch.empty_like(Mh).pin_memory() for _ in range(2)]
     h2d = sum(M[l].numel() * 8 for l in LEVELS)
     d2h = sum(Lx[l].numel() * 8 for l in LEVELS)
-
-    def e2e_step():
-        for l in LEVELS:
-            M[l].copy_(Mh[l], non_blocking=True)
-        step()
-        for l in LEVELS:
-            Lh[l].copy_(Lx[l], non_blocking=True)
-
-    for _ in range(3):
-        e2e_step()
-        flush.zero_()
+    pipe.run([Mh] * max(3, args.warmup), [Lh[i % 2] for i in range(max(3, args.warmup))])
     torch.cuda.synchronize()
-    e2e_ms = sum(_timed(torch, e2e_step, args.steps, stream, flush))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(pipe.h2d)
+    pipe.run([Mh] * args.steps, [Lh[i % 2] for i in range(args.steps)])
+    e1.record(pipe.d2h)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    e2e_matches = all(bool((v == Lx[l].cpu()).all()) for v, l in zip(pipe.level_views(Lh[(args.steps - 1) % 2]), LEVELS))
     e2e_value = fdist.job_rate(NTR * args.steps, e2e_ms * 1e-3)
     clocks = clk.stop() if rank == 0 else None
 
@@ -813,7 +817,11 @@ def run_ours(args):
                 "frac_at_sampled_clock": (achieved / (peak * clocks["sm_mhz"] / SM_MAX_MHZ))
                 if clocks and clocks.get("sm_mhz") else None,
             },
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "matches_device_result": e2e_matches,
+                    "how": "K consecutive steps through pipeline.HostStreamM2L: each copies its MEs from pinned "
+                           "host memory and its LEs back; copies in, translation and copies out of neighbouring "
+                           "steps overlap on three streams; CUDA events around all K steps"},
             "gpu_launches": args.steps,
             "graph_replay_matches_direct_call": graph_matches,
             "clocks": clocks,

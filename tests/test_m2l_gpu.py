@@ -303,3 +303,36 @@ def test_level_11_sampled_targets(fmm, orc, prec_name):
     got = _host(Ld)[targets]
     tol = TOL_L2 if prec == fmm.FMM_FP32 else 1e-4
     assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= tol
+
+
+def test_host_stream_pipeline_matches_direct_calls(fmm, orc):
+    """pipeline.HostStreamM2L: five steps with different host ME sets (two device buffer
+    sets, three streams) give exactly the LEs of fmm_m2l_levels on each set."""
+    import torch
+    from paper_1009_3457_gb300 import pipeline
+
+    p, L = 8, 5
+    tree = fmm.fmm_build_lists(None, L)
+    levels = list(range(2, L + 1))
+    rng = np.random.default_rng(17)
+    host_in, host_out, refs = [], [], []
+    for _ in range(5):
+        Ms = [torch.from_numpy((rng.standard_normal((4 ** l, p)) + 1j * rng.standard_normal((4 ** l, p)))
+                               .astype(np.complex64)).pin_memory() for l in levels]
+        host_in.append(Ms)
+        host_out.append([torch.empty_like(m).pin_memory() for m in Ms])
+        Md = [m.cuda() for m in Ms]
+        Ld = [torch.empty_like(m) for m in Md]
+        fmm.fmm_m2l_levels(tree, 2, p, Md, Ld)
+        refs.append([x.cpu() for x in Ld])
+    pipe = pipeline.HostStreamM2L(tree, 2, L, p)
+    pipe.run(host_in, host_out)
+    # the flat form: all levels in one pinned buffer, one copy per direction
+    flat_in = [torch.cat([m.reshape(-1) for m in ms]).pin_memory() for ms in host_in]
+    flat_out = [torch.empty(pipe.flat_size(), dtype=torch.complex64).pin_memory() for _ in host_in]
+    pipe.run(flat_in, flat_out)
+    torch.cuda.synchronize()
+    fmm.fmm_sync_status()
+    for out, fo, ref in zip(host_out, flat_out, refs):
+        for a, f, b in zip(out, pipe.level_views(fo), ref):
+            assert torch.equal(a, b) and torch.equal(f, b)
