@@ -368,6 +368,15 @@ int fmm_l2p(int32_t p, int64_t n, const double* z, const int32_t* lev, const int
 int fmm_l2p_adjoint(int32_t p, int64_t n, const double* z, const int32_t* lev, const int64_t* box,
                     const void* cot, void* const* G_levels, int32_t max_level, void* stream);
 
+/* fmm_p2m_binned: fmm_p2m for points binned by fmm_bin_points(level, xy, n, ...)
+ *   (perm, box_start): one thread block per box sums its points (powers in FP32
+ *   of d formed in FP64), one store per coefficient -- no atomics, the same
+ *   result on every run.  p 6, 8, 12, 16 or 24; level 0..10; flags FMM_ACCUMULATE.
+ *   A perm entry or box start out of range sets the device error word's check
+ *   bit and is skipped. */
+int fmm_p2m_binned(int32_t level, int32_t p, const double* xy, const double* c, int64_t n, const int32_t* perm,
+                   const int32_t* box_start, void* M, int32_t flags, void* stream);
+
 /* fmm_p2m_adjoint: for the P2M of fmm_p2m at `level` (M~_b[k] = sum_i c_i d_i^k,
  *   d_i = (y_i - x_b) / r_l) and G = dJ/dM~ of a real objective J, the gradient
  *   in the point positions:

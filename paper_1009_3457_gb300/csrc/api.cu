@@ -709,6 +709,25 @@ int fmm_p2m(int32_t level, int32_t p, const double* xy, const double* c, int64_t
     return launch_p2m(level, p, xy, c, n, (float2*)M, (flags & FMM_ACCUMULATE) != 0, (cudaStream_t)stream);
 }
 
+int fmm_p2m_binned(int32_t level, int32_t p, const double* xy, const double* c, int64_t n, const int32_t* perm,
+                   const int32_t* box_start, void* M, int32_t flags, void* stream)
+{
+    clear_error();
+    if (level < 0 || level > 10) return fail(FMM_EINVAL, "fmm_p2m_binned: level %d outside 0..10", level);
+    if (p != 6 && p != 8 && p != 12 && p != 16 && p != 24)
+        return fail(FMM_EINVAL, "fmm_p2m_binned: unsupported p = %d (6, 8, 12, 16, 24)", p);
+    if (n < 0 || n > INT32_MAX) return fail(FMM_EINVAL, "fmm_p2m_binned: n = %lld outside 0..2^31-1", (long long)n);
+    if (!M || !box_start || (n > 0 && (!xy || !c || !perm))) return fail(FMM_EINVAL, "fmm_p2m_binned: NULL pointer");
+    if (((uintptr_t)M & 7) || ((uintptr_t)xy & 7) || ((uintptr_t)c & 7) || ((uintptr_t)perm & 3) ||
+        ((uintptr_t)box_start & 3))
+        return fail(FMM_EINVAL, "fmm_p2m_binned: misaligned pointer");
+    if (flags & ~FMM_ACCUMULATE) return fail(FMM_EINVAL, "fmm_p2m_binned: unknown flags 0x%x", flags);
+    int* err = nullptr;
+    if (int rc = device_error_word(&err)) return rc;
+    return launch_p2m_binned(level, p, xy, c, (int)n, perm, box_start, (float2*)M, (flags & FMM_ACCUMULATE) != 0,
+                             err, (cudaStream_t)stream);
+}
+
 int fmm_m2m_adjoint(int32_t child_level, int32_t p, const void* Wp, void* Wc, int32_t flags, void* stream)
 {
     clear_error();

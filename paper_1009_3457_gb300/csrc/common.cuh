@@ -145,6 +145,8 @@ int fgt_check_args(const char* who, int g, int ncut, int p, double sigma, const 
                    const float* work, int flags);
 
 // launchers (upward.cu)
+int launch_p2m_binned(int level, int p, const double* xy, const double* c, int n, const int* perm,
+                      const int* box_start, float2* M, bool acc, int* err, cudaStream_t st);
 int launch_p2m(int level, int p, const double* xy, const double* c, int64_t n, float2* M, bool accumulate,
                cudaStream_t st);
 int launch_m2m(int child_level, int p, const float2* Mc, float2* Mp, bool accumulate, cudaStream_t st);

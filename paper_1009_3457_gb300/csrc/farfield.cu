@@ -5,7 +5,7 @@
 //   L2P   phi(z) = (1/r) sum_n L~[leaf][n] w^n,  w = (z - x_leaf) / r
 //   P2M^T grad of sum_k <G_k, M~_k(y)> in the point positions, M~_k = sum_i c_i d_i^k, d = (y - x_b)/r
 // The L2L entries (binomials, powers of (+-1 +- i)/4, powers of 2) are exact
-// in FP32; L2P forms w in FP64.  Adjoints are conjugate transposes (the
+// in FP32; L2P forms w in FP64 and evaluates in FP32.  Adjoints are conjugate transposes (the
 // gradient of a real objective in PyTorch's convention for complex tensors).
 #include "common.cuh"
 
@@ -92,7 +92,8 @@ struct LevelOutPtrs {
     float2* G[FMM_MAX_LEVEL + 1];
 };
 
-// One thread per point: phi_j (+)= (1/r) sum_n L~[leaf][n] w^n (Horner in FP64).
+// One thread per point: phi_j (+)= (1/r) sum_n L~[leaf][n] w^n, w formed in FP64 and the
+// Horner recurrence in FP32 (|w| <= 1/sqrt(2) in radius-scaled units, so it is stable).
 // A point's (level, box) must address an existing array; otherwise it is
 // skipped and the device error word records the failed check.
 __device__ __forceinline__ bool leaf_ok(int l, int64_t b, const void* const* tab, int max_level, int* err)
@@ -109,22 +110,23 @@ __global__ void l2p_kernel(int p, int64_t n, const double* __restrict__ z, const
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int l = lev[i];
-    double ar = 0.0, ai = 0.0;
+    float ar = 0.f, ai = 0.f;
     if (l >= 2 && leaf_ok(l, box[i], (const void* const*)Ls.L, max_level, err)) {
         const int side = 1 << l;
         const int64_t b = box[i];
-        const double wr = z[2 * i] * side - ((double)(b % side) + 0.5);
-        const double wi = z[2 * i + 1] * side - ((double)(b / side) + 0.5);
+        const float wr = (float)(z[2 * i] * side - ((double)(b % side) + 0.5));
+        const float wi = (float)(z[2 * i + 1] * side - ((double)(b / side) + 0.5));
         const float2* lb = Ls.L[l] + (size_t)b * p;
         for (int k = p - 1; k >= 0; --k) {
-            const double tr = ar * wr - ai * wi + (double)lb[k].x;
-            ai = ar * wi + ai * wr + (double)lb[k].y;
+            const float2 v = lb[k];
+            const float tr = fmaf(ar, wr, fmaf(-ai, wi, v.x));
+            ai = fmaf(ar, wi, fmaf(ai, wr, v.y));
             ar = tr;
         }
-        ar *= side;
-        ai *= side;
+        ar *= (float)side;
+        ai *= (float)side;
     }
-    float2 o = make_float2((float)ar, (float)ai);
+    float2 o = make_float2(ar, ai);
     if (accumulate) {
         o.x += phi[i].x;
         o.y += phi[i].y;

@@ -30,6 +30,95 @@ __global__ void p2m_kernel(int level, int p, const double* __restrict__ xy, cons
     }
 }
 
+// P2M from points binned by box (fmm_bin_points at `level`): one CTA per box
+// sums its points' c d^k (d formed in FP64, powers in FP32: |d| <= 1/sqrt(2)),
+// each thread over a strided share of the box's points, then a block
+// reduction; one store per coefficient, no atomics, a fixed summation order.
+constexpr int kP2mThreads = 128;
+
+template <int P>
+__global__ void __launch_bounds__(kP2mThreads) p2m_binned_kernel(int level, const double* __restrict__ xy,
+                                                                 const double* __restrict__ c, int n,
+                                                                 const int* __restrict__ perm,
+                                                                 const int* __restrict__ box_start,
+                                                                 float2* __restrict__ M, int accumulate, int* err)
+{
+    __shared__ float2 s_red[kP2mThreads / 32][P];
+    const int side = 1 << level;
+    const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int bx = b & (side - 1), by = b >> level;
+    int first = box_start[b], end = box_start[b + 1];
+    if (first < 0 || end > n || first > end) {
+        if (tid == 0) atomicOr(err, DEV_ERR_CHECK);
+        first = end = 0;
+    }
+    float2 acc[P];
+#pragma unroll
+    for (int k = 0; k < P; ++k) acc[k] = make_float2(0.f, 0.f);
+    for (int q = first + tid; q < end; q += kP2mThreads) {
+        const int i = perm[q];
+        if ((unsigned)i >= (unsigned)n) {
+            atomicOr(err, DEV_ERR_CHECK);
+            continue;
+        }
+        const float wr = (float)(xy[2 * (size_t)i] * side - (bx + 0.5));
+        const float wi = (float)(xy[2 * (size_t)i + 1] * side - (by + 0.5));
+        float pr = (float)c[i], pi = 0.f;
+#pragma unroll
+        for (int k = 0; k < P; ++k) {
+            acc[k].x += pr;
+            acc[k].y += pi;
+            const float t = fmaf(pr, wr, -pi * wi);
+            pi = fmaf(pr, wi, pi * wr);
+            pr = t;
+        }
+    }
+    // warp sums, then the warps' sums in shared memory
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            acc[k].x += __shfl_xor_sync(0xffffffffu, acc[k].x, o);
+            acc[k].y += __shfl_xor_sync(0xffffffffu, acc[k].y, o);
+        }
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < P; ++k) s_red[warp][k] = acc[k];
+    }
+    __syncthreads();
+    if (tid < P) {
+        float2 v = s_red[0][tid];
+#pragma unroll
+        for (int w = 1; w < kP2mThreads / 32; ++w) {
+            v.x += s_red[w][tid].x;
+            v.y += s_red[w][tid].y;
+        }
+        float2* dst = M + (size_t)b * P + tid;
+        if (accumulate) {
+            v.x += dst->x;
+            v.y += dst->y;
+        }
+        *dst = v;
+    }
+}
+
+int launch_p2m_binned(int level, int p, const double* xy, const double* c, int n, const int* perm,
+                      const int* box_start, float2* M, bool acc, int* err, cudaStream_t st)
+{
+    const unsigned nbox = 1u << (2 * level);
+    switch (p) {
+        case 6: p2m_binned_kernel<6><<<nbox, kP2mThreads, 0, st>>>(level, xy, c, n, perm, box_start, M, acc, err); break;
+        case 8: p2m_binned_kernel<8><<<nbox, kP2mThreads, 0, st>>>(level, xy, c, n, perm, box_start, M, acc, err); break;
+        case 12: p2m_binned_kernel<12><<<nbox, kP2mThreads, 0, st>>>(level, xy, c, n, perm, box_start, M, acc, err); break;
+        case 16: p2m_binned_kernel<16><<<nbox, kP2mThreads, 0, st>>>(level, xy, c, n, perm, box_start, M, acc, err); break;
+        case 24: p2m_binned_kernel<24><<<nbox, kP2mThreads, 0, st>>>(level, xy, c, n, perm, box_start, M, acc, err); break;
+        default: return fail(FMM_EINVAL, "fmm_p2m_binned: unsupported p = %d (6, 8, 12, 16, 24)", p);
+    }
+    FMM_CUDA_TRY(cudaGetLastError());
+    return FMM_OK;
+}
+
 // Scaled M2M: parent box side R = 2r, child offset z = (x_c - x_P)/R = (+-1/4, +-1/4):
 //   M~P_j = sum_{k<=j} C(j,k) z^(j-k) 2^-k M~c_k, summed over the 4 children.
 // The entries (binomials, powers of (+-1 +- i)/4, powers of 2) are exact in FP32.

@@ -101,7 +101,7 @@ def far_field_objective(tree, p: int, xy: torch.Tensor, c: torch.Tensor, leaf, z
 
 class FmmPotential:
     """The whole FMM on a uniform tree to level L (Sec. 2.1 stages 2-5), every stage a
-    library kernel: P2M at level L, M2M up, M2L over the interaction lists of levels 2..L,
+    library kernel: P2M at level L (on the binned points), M2M up, M2L over the interaction lists of levels 2..L,
     L2L down, L2P at each target's level-L box, plus the near field (own and adjacent
     boxes) by ``fmm_p2p``.
 
@@ -137,7 +137,7 @@ class FmmPotential:
 
     def __call__(self) -> torch.Tensor:
         p, L = self.p, self.L
-        fmmgb.fmm_p2m(L, p, self.xy, self.c, self.Ms[-1])
+        fmmgb.fmm_p2m_binned(L, p, self.xy, self.c, self.sperm, self.sstart, self.Ms[-1])
         for i in range(len(self.levels) - 1, 0, -1):
             fmmgb.fmm_m2m(self.levels[i], p, self.Ms[i], self.Ms[i - 1])
         fmmgb.fmm_m2l_levels(self.tree, 2, p, self.Ms, self.Ls, prec=self.prec)

@@ -109,6 +109,7 @@ SIGNATURES = {
     "fgt_bin_points": (ctypes.c_int, [_i32, _vp, _i64, _vp, _vp, _vp, _vp]),
     "fmm_bin_points": (ctypes.c_int, [_i32, _vp, _i64, _vp, _vp, _vp, _vp]),
     "fmm_m2l_paper_design": (ctypes.c_int, [_vp, _i32, _i32, _vp, _vp, _vp, _i32, _vp]),
+    "fmm_p2m_binned": (ctypes.c_int, [_i32, _i32, _vp, _vp, _i64, _vp, _vp, _vp, _i32, _vp]),
     "fmm_p2p": (ctypes.c_int, [_i32, _vp, _vp, _i64, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _i32, _vp]),
     "fgt_p2h_binned": (ctypes.c_int, [_i32, _i32, _d, _vp, _vp, _i64, _vp, _vp, _i32, _vp]),
     "fgt_h2p": (ctypes.c_int, [_i32, _i32, _i32, _i32, _d, _vp, _vp, _i64, _vp, _vp, _vp, _i32, _vp]),
@@ -316,6 +317,13 @@ def fmm_p2m(level: int, p: int, xy, c, M, accumulate: bool = False, stream=None)
     n = 0 if c is None else c.numel()
     _check(load().fmm_p2m(level, p, _ptr(xy), _ptr(c), n, _ptr(M), FMM_ACCUMULATE if accumulate else 0,
                           _stream(stream)))
+
+
+def fmm_p2m_binned(level: int, p: int, xy, c, perm, box_start, M, accumulate: bool = False, stream=None):
+    """fmm_p2m for points binned by fmm_bin_points at `level` (deterministic, no atomics)."""
+    n = 0 if c is None else c.numel()
+    _check(load().fmm_p2m_binned(level, p, _ptr(xy), _ptr(c), n, _ptr(perm), _ptr(box_start), _ptr(M),
+                                 FMM_ACCUMULATE if accumulate else 0, _stream(stream)))
 
 
 def fmm_m2m(child_level: int, p: int, Mc, Mp, accumulate: bool = False, stream=None):
