@@ -5,8 +5,10 @@
 //   phi(z) (+)= sum_{i : box(y_i) adjacent to or equal box(z), y_i != z} c_i / (z - y_i).
 //
 // Targets and sources are binned by box (fmm_bin_points); a pre-pass copies the
-// sources into box order (x, y, c in FP64), so a box's sources are one
-// contiguous range.  Persistent CTAs of
+// sources into box order, each as its position relative to its own box's
+// centre (formed in FP64, kept in FP32) and strength, so a box's sources are
+// one contiguous range and staging adds only the exact offset between box
+// centres -- no FP64 arithmetic per staged source.  Persistent CTAs of
 // 128 threads claim runs of up to 64 targets of one box from a claim table
 // (a finest-level box holds a few dozen points), gather the sources of the
 // 3 x 3 neighbourhood through the source permutation into shared memory in
@@ -39,7 +41,7 @@ struct P2pArgs {
     int level, n, nz, accumulate;
     const double* xy;
     const double* c;
-    const double4* src;  // sources in box order: x, y, c (p2p_sort_kernel)
+    const float4* src;  // sources in box order: x, y relative to their own box's centre, c (p2p_sort_kernel)
     const int* sperm;
     const int* sstart;
     const double* z;
@@ -51,19 +53,25 @@ struct P2pArgs {
     int* err;
 };
 
-// sources in box order, so that a box's sources are one contiguous range
-__global__ void p2p_sort_kernel(const double* __restrict__ xy, const double* __restrict__ c, const int* __restrict__ perm,
-                                int n, double4* __restrict__ out, int* err)
+// sources in box order, so that a box's sources are one contiguous range; positions relative to
+// the centre of their own box (formed in FP64, kept in FP32: |x - c| <= half a box side)
+__global__ void p2p_sort_kernel(int level, const double* __restrict__ xy, const double* __restrict__ c,
+                                const int* __restrict__ perm, int n, float4* __restrict__ out, int* err)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const int i = __ldg(perm + k);
     if ((unsigned)i >= (unsigned)n) {
         atomicOr(err, DEV_ERR_CHECK);
-        out[k] = make_double4(0.0, 0.0, 0.0, 0.0);
+        out[k] = make_float4(0.f, 0.f, 0.f, 0.f);
         return;
     }
-    out[k] = make_double4(__ldg(xy + 2 * (size_t)i), __ldg(xy + 2 * (size_t)i + 1), __ldg(c + i), 0.0);
+    const int side = 1 << level;
+    const double x = __ldg(xy + 2 * (size_t)i), y = __ldg(xy + 2 * (size_t)i + 1);
+    const double px = x * side, py = y * side;
+    const int ix = !(px >= 0.0) ? 0 : (px >= side ? side - 1 : (int)px);
+    const int iy = !(py >= 0.0) ? 0 : (py >= side ? side - 1 : (int)py);
+    out[k] = make_float4((float)(x - (ix + 0.5) / side), (float)(y - (iy + 0.5) / side), (float)__ldg(c + i), 0.f);
 }
 
 __device__ __forceinline__ float rcp_approx(float x)
@@ -78,6 +86,7 @@ __global__ void __launch_bounds__(kP2pThreads) fmm_p2p_kernel(P2pArgs a)
     __shared__ float4 s_src[kP2pBatch];  // x - cx, y - cy, c
     __shared__ int s_claim[3];
     __shared__ int s_box[9], s_pre[10];  // first sorted source of each neighbour box, prefix of their counts
+    __shared__ float s_ox[9], s_oy[9];     // centre of each neighbour box minus the target box's
     __shared__ float2 s_part[kP2pWarps - 1][kP2pRun];  // partial sums of warps 1..3
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -110,6 +119,8 @@ __global__ void __launch_bounds__(kP2pThreads) fmm_p2p_kernel(P2pArgs a)
             for (int q = 0; q < 9; ++q) {
                 const int sx = tx + q % 3 - 1, sy = ty + q / 3 - 1;
                 s_pre[q] = acc;
+                s_ox[q] = (float)((q % 3 - 1) * inv_side);  // exact: a power of two or zero
+                s_oy[q] = (float)((q / 3 - 1) * inv_side);
                 if (sx < 0 || sy < 0 || sx >= side || sy >= side) continue;
                 const int b = sy * side + sx;
                 const int b0 = __ldg(a.sstart + b), m = __ldg(a.sstart + b + 1) - b0;
@@ -150,10 +161,10 @@ __global__ void __launch_bounds__(kP2pThreads) fmm_p2p_kernel(P2pArgs a)
                 const int b0 = s_box[q];
                 float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (b0 >= 0) {
-                    const double4 u = a.src[b0 + (g - s_pre[q])];
-                    v.x = (float)(u.x - cx);
-                    v.y = (float)(u.y - cy);
-                    v.z = (float)u.z;
+                    const float4 u = a.src[b0 + (g - s_pre[q])];
+                    v.x = u.x + s_ox[q];
+                    v.y = u.y + s_oy[q];
+                    v.z = u.z;
                 }
                 s_src[i] = v;
             }
@@ -209,10 +220,10 @@ __global__ void __launch_bounds__(kP2pThreads) fmm_p2p_kernel(P2pArgs a)
 
 // Per-device buffer of sorted sources (grown on demand).
 static std::mutex g_src_mu;
-static double4* g_src[64];
+static float4* g_src[64];
 static size_t g_src_bytes[64];
 
-static int p2p_source_buffer(size_t bytes, double4** out)
+static int p2p_source_buffer(size_t bytes, float4** out)
 {
     int dev = 0;
     FMM_CUDA_TRY(cudaGetDevice(&dev));
@@ -274,10 +285,10 @@ extern "C" int fmm_p2p(int32_t level, const double* xy, const double* c, int64_t
     args.claims = claims;
     const int nbox = 1 << (2 * level);
     if (int rc = launch_h2p_claims(nbox, tgt_start, kP2pRun, claims, args.err, st)) return rc;
-    double4* src = nullptr;
+    float4* src = nullptr;
     if (n > 0) {
-        if (int rc = p2p_source_buffer((size_t)n * sizeof(double4), &src)) return rc;
-        p2p_sort_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(xy, c, src_perm, (int)n, src, args.err);
+        if (int rc = p2p_source_buffer((size_t)n * sizeof(float4), &src)) return rc;
+        p2p_sort_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(level, xy, c, src_perm, (int)n, src, args.err);
         FMM_CUDA_TRY(cudaGetLastError());
     }
     args.src = src;
