@@ -28,6 +28,43 @@ void clear_error();
 enum : int { DEV_ERR_CHECK = 1, DEV_ERR_TIMEOUT = 2 };
 int device_error_word(int** out);
 
+// ---------------------------------------------------------------------------
+// Placing points in the 2^g x 2^g grid over [0, 1)^2 without FP64 arithmetic.
+// FP64 runs at a small fraction of the FP32 rate on this part, so a handful of
+// FP64 operations per point sets the time of the kernels that only locate
+// points (binning, P2M, L2P, the near-field sort).  A v in [0, 1) is
+// m 2^(e - 52) with m its 53-bit significand and e < 0, so
+//   X = floor(v 2^(g + 31)) = m >> (21 - e - g)
+// exactly; X >> 31 = floor(v 2^g) is v's cell and the low 31 bits are its
+// place in the cell in units of 2^-31 of a side.
+// ---------------------------------------------------------------------------
+// X for v in [0, 1) (g <= 20); false for v outside it (negative, -0, >= 1, infinite, NaN).
+__device__ __forceinline__ bool grid_fixed31(double v, int g, long long& X)
+{
+    const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+    if (u >= 0x3FF0000000000000ull) return false;  // sign bit set, or v >= 1, inf, NaN
+    const int e = (int)(u >> 52) - 1023;            // -1023 for 0 and subnormals: X = 0 below
+    const int sh = 21 - e - g;
+    const unsigned long long m = (u & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
+    X = sh >= 64 ? 0ll : (long long)(m >> sh);
+    return true;
+}
+
+// floor(v 2^g) clamped to 0..2^g-1, NaN to 0 (the cell of a coordinate).
+__device__ __forceinline__ int grid_cell(double v, int g)
+{
+    long long X;
+    if (grid_fixed31(v, g, X)) return (int)(X >> 31);
+    return v >= 1.0 ? (1 << g) - 1 : 0;
+}
+
+// v's offset from the centre of its cell, in cell sides, from X (|result| <= 1/2;
+// truncated to 2^-31 of a side, then rounded to FP32).
+__device__ __forceinline__ float cell_offset31(long long X)
+{
+    return (float)((int)(X & 0x7FFFFFFFll) - (1 << 30)) * 4.656612873077393e-10f;  // 2^-31
+}
+
 // Number of SMs of the current device (cached).
 int device_sm_count(int* out);
 

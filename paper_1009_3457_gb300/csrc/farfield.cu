@@ -114,8 +114,17 @@ __global__ void l2p_kernel(int p, int64_t n, const double* __restrict__ z, const
     if (l >= 2 && leaf_ok(l, box[i], (const void* const*)Ls.L, max_level, err)) {
         const int side = 1 << l;
         const int64_t b = box[i];
-        const float wr = (float)(z[2 * i] * side - ((double)(b % side) + 0.5));
-        const float wi = (float)(z[2 * i + 1] * side - ((double)(b / side) + 0.5));
+        const int bx = (int)(b & (side - 1)), by = (int)(b >> l);
+        const double x = z[2 * i], y = z[2 * i + 1];
+        long long X, Y;
+        float wr, wi;  // offset from the leaf's centre in leaf sides
+        if (grid_fixed31(x, l, X) && grid_fixed31(y, l, Y) && (int)(X >> 31) == bx && (int)(Y >> 31) == by) {
+            wr = cell_offset31(X);  // no FP64 arithmetic for a point inside its leaf
+            wi = cell_offset31(Y);
+        } else {
+            wr = (float)(x * side - (bx + 0.5));
+            wi = (float)(y * side - (by + 0.5));
+        }
         const float2* lb = Ls.L[l] + (size_t)b * p;
         for (int k = p - 1; k >= 0; --k) {
             const float2 v = lb[k];

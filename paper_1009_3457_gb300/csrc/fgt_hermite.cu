@@ -42,18 +42,36 @@ constexpr int kScanThreads = 1024;
 
 __device__ __forceinline__ int fgt_grid_box(double x, double y, int g)
 {
-    const int side = 1 << g;
-    const double px = x * side, py = y * side;
-    // !(v >= 0) also sends NaN to box 0
-    int ix = !(px >= 0.0) ? 0 : (px >= side ? side - 1 : (int)px);
-    int iy = !(py >= 0.0) ? 0 : (py >= side ? side - 1 : (int)py);
-    return iy * side + ix;
+    // floor(v 2^g) per coordinate, clamped to the grid; NaN and negatives to cell 0
+    return grid_cell(y, g) * (1 << g) + grid_cell(x, g);
 }
 
+// Warp-aggregated counting: the lanes of a warp whose points share a box make
+// one atomic between them (clustered inputs put many points of a warp in one
+// box), and each lane learns its rank among them.  Every lane of the warp calls
+// it (key < 0: no point); returns the box's count before the warp's additions
+// plus the lane's rank, or -1 without a point.
+__device__ __forceinline__ int warp_box_claim(int* __restrict__ counter, int key)
+{
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
+    int base = 0;
+    if (key >= 0 && lane == leader) base = atomicAdd(&counter[key], __popc(peers));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    return key >= 0 ? base + __popc(peers & ((1u << lane) - 1u)) : -1;
+}
+
+// grid-stride over warps: all 32 lanes of a warp take part in every round
 __global__ void bin_count_kernel(int g, const double* __restrict__ y, int64_t n, int* __restrict__ counts)
 {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        atomicAdd(&counts[fgt_grid_box(y[2 * i], y[2 * i + 1], g)], 1);
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t w = w0; 32 * w < n; w += nw) {
+        const int64_t i = 32 * w + lane;
+        const int key = i < n ? fgt_grid_box(__ldg(y + 2 * i), __ldg(y + 2 * i + 1), g) : -1;
+        warp_box_claim(counts, key);
+    }
 }
 
 // One CTA: exclusive scan of v(0..nbox-1) into out[0..nbox] (out[nbox] = total); put(i, prefix)
@@ -109,8 +127,15 @@ __global__ void __launch_bounds__(kScanThreads) bin_scan_kernel(int nbox, int* c
 __global__ void bin_scatter_kernel(int g, const double* __restrict__ y, int64_t n, int* __restrict__ cursor,
                                    int* __restrict__ perm)
 {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        perm[atomicAdd(&cursor[fgt_grid_box(y[2 * i], y[2 * i + 1], g)], 1)] = (int)i;
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t w = w0; 32 * w < n; w += nw) {
+        const int64_t i = 32 * w + lane;
+        const int key = i < n ? fgt_grid_box(__ldg(y + 2 * i), __ldg(y + 2 * i + 1), g) : -1;
+        const int slot = warp_box_claim(cursor, key);
+        if (slot >= 0) perm[slot] = (int)i;
+    }
 }
 
 static int bin_grid(int64_t n)
@@ -130,7 +155,8 @@ static int bin_grid(int64_t n)
 constexpr int kP2hPoints = 256;
 
 template <int P>
-__global__ void __launch_bounds__(kP2hPoints) fgt_p2h_binned_kernel(int g, double inv_c, const double* __restrict__ x,
+__global__ void __launch_bounds__(kP2hPoints) fgt_p2h_binned_kernel(int g, double inv_c, float dcell,
+                                                                    const double* __restrict__ x,
                                                                     const double* __restrict__ q, int n,
                                                                     const int* __restrict__ perm,
                                                                     float* __restrict__ A, int* err)
@@ -145,10 +171,20 @@ __global__ void __launch_bounds__(kP2hPoints) fgt_p2h_binned_kernel(int g, doubl
         const int j = perm[base + tid];
         if ((unsigned)j < (unsigned)n) {
             const double x0 = x[2 * (size_t)j], x1 = x[2 * (size_t)j + 1];
-            const int b = fgt_grid_box(x0, x1, g);
             const int side = 1 << g;
-            const float t1 = (float)((x0 * side - ((b & (side - 1)) + 0.5)) / side * inv_c);
-            const float t2 = (float)((x1 * side - ((b >> g) + 0.5)) / side * inv_c);
+            int b;
+            float t1, t2;
+            long long X0, X1;
+            if (grid_fixed31(x0, g, X0) && grid_fixed31(x1, g, X1)) {
+                // offsets from the box centre in box sides, times side / (sqrt2 sigma)
+                b = (int)(X1 >> 31) * side + (int)(X0 >> 31);
+                t1 = cell_offset31(X0) * dcell;
+                t2 = cell_offset31(X1) * dcell;
+            } else {  // outside the unit square: clamped box, offset in FP64
+                b = fgt_grid_box(x0, x1, g);
+                t1 = (float)((x0 * side - ((b & (side - 1)) + 0.5)) / side * inv_c);
+                t2 = (float)((x1 * side - ((b >> g) + 0.5)) / side * inv_c);
+            }
             float w1 = (float)q[j], w2 = 1.f;
 #pragma unroll
             for (int a = 0; a < P; ++a) {
@@ -510,12 +546,13 @@ extern "C" int fgt_p2h_binned(int32_t grid_log2, int32_t p, double sigma, const 
     if (int rc = device_error_word(&err)) return rc;
     const unsigned grid = (unsigned)((n + kP2hPoints - 1) / kP2hPoints);
     const double inv_c = 1.0 / (sqrt(2.0) * sigma);
+    const float dcell = (float)(ldexp(1.0, -grid_log2) * inv_c);  // box side / (sqrt2 sigma)
     const int nn = (int)n;
     switch (p) {
-        case 4: fgt_p2h_binned_kernel<4><<<grid, kP2hPoints, 0, st>>>(grid_log2, inv_c, x, q, nn, perm, A, err); break;
-        case 8: fgt_p2h_binned_kernel<8><<<grid, kP2hPoints, 0, st>>>(grid_log2, inv_c, x, q, nn, perm, A, err); break;
-        case 12: fgt_p2h_binned_kernel<12><<<grid, kP2hPoints, 0, st>>>(grid_log2, inv_c, x, q, nn, perm, A, err); break;
-        default: fgt_p2h_binned_kernel<16><<<grid, kP2hPoints, 0, st>>>(grid_log2, inv_c, x, q, nn, perm, A, err); break;
+        case 4: fgt_p2h_binned_kernel<4><<<grid, kP2hPoints, 0, st>>>(grid_log2, inv_c, dcell, x, q, nn, perm, A, err); break;
+        case 8: fgt_p2h_binned_kernel<8><<<grid, kP2hPoints, 0, st>>>(grid_log2, inv_c, dcell, x, q, nn, perm, A, err); break;
+        case 12: fgt_p2h_binned_kernel<12><<<grid, kP2hPoints, 0, st>>>(grid_log2, inv_c, dcell, x, q, nn, perm, A, err); break;
+        default: fgt_p2h_binned_kernel<16><<<grid, kP2hPoints, 0, st>>>(grid_log2, inv_c, dcell, x, q, nn, perm, A, err); break;
     }
     FMM_CUDA_TRY(cudaGetLastError());
     return FMM_OK;

@@ -61,6 +61,9 @@ static inline int batch_p_index(int p)
 
 constexpr size_t kBatchSmem = M2LCfg<16>::smem;  // the largest batched order
 constexpr int kBatchMinCtas = 6;
+// halo loads in flight per thread: the one kernel holds every order's code, so the
+// register budget is the largest order's (more spills)
+constexpr int kBatchLoads = 3;
 
 __global__ void __launch_bounds__(kThreads, kBatchMinCtas)
     m2l_batched_kernel(const BatchDesc* __restrict__ desc, const int2* __restrict__ items, int nitems,
@@ -88,10 +91,10 @@ __global__ void __launch_bounds__(kThreads, kBatchMinCtas)
             const TileGeom g = tile_geom_of(d.M, d.L, nullptr, d.level, item.y);
             __syncthreads();  // operator visible; previous tile done with the halo buffer
             switch (d.p) {
-                case 6: m2l_tile<6>(smem_raw, g, d.periodic, accumulate); break;
-                case 8: m2l_tile<8>(smem_raw, g, d.periodic, accumulate); break;
-                case 12: m2l_tile<12>(smem_raw, g, d.periodic, accumulate); break;
-                default: m2l_tile<16>(smem_raw, g, d.periodic, accumulate); break;
+                case 6: m2l_tile<6, false, kBatchLoads>(smem_raw, g, d.periodic, accumulate); break;
+                case 8: m2l_tile<8, false, kBatchLoads>(smem_raw, g, d.periodic, accumulate); break;
+                case 12: m2l_tile<12, false, kBatchLoads>(smem_raw, g, d.periodic, accumulate); break;
+                default: m2l_tile<16, false, kBatchLoads>(smem_raw, g, d.periodic, accumulate); break;
             }
         }
         if (!counter) break;  // one chunk per CTA (grid covers every item)

@@ -52,7 +52,9 @@ struct M2LCfg {
     static constexpr int NH = 2 * P - 1;           // Hankel diagonals
     static constexpr int CS = P * kPlane;          // float2 stride between class planes
     static constexpr int HALO = 4 * CS;            // float2 per halo buffer
-    static constexpr int MIN_CTAS = P == 16 ? 6 : 1;  // p = 16: 6 resident CTAs per SM (<= 80 registers)
+    static constexpr int MIN_CTAS = P == 16 ? 7 : 1;  // p = 16: 7 resident CTAs per SM (<= 72 registers)
+    // halo loads a thread keeps in flight while staging a tile (register budget of the order)
+    static constexpr int LOADS = P <= 6 ? 2 : (P <= 8 ? 3 : 4);
     static constexpr size_t smem = sizeof(float2) * (HALO + kOffsetSlots * NH) + sizeof(float) * 2 * P +
                                    sizeof(int2) * 4 * 27;
 };
@@ -149,7 +151,15 @@ __device__ __forceinline__ void m2l_load_operator(unsigned char* raw, const floa
     constexpr int NH = C::NH;
     const TileSmem<P> s(raw);
     const int tid = threadIdx.x;
-    for (int i = tid; i < kOffsetSlots * NH; i += kThreads) s.hs[i] = hsel[i];
+    // 16-byte copies, several in flight per thread (the table and the shared-memory
+    // copy are 16-byte aligned): the copy is on every launch's critical path
+    constexpr int N4 = kOffsetSlots * NH / 2;
+    const float4* h4 = reinterpret_cast<const float4*>(hsel);
+    float4* d4 = reinterpret_cast<float4*>(s.hs);
+#pragma unroll 4
+    for (int i = tid; i < N4; i += kThreads) d4[i] = __ldg(h4 + i);
+    if ((kOffsetSlots * NH) & 1)
+        if (tid == 0) s.hs[kOffsetSlots * NH - 1] = hsel[kOffsetSlots * NH - 1];
     for (int i = tid; i < P; i += kThreads) {
         s.as[i] = ascale[i];
         s.bs[i] = bscale[i];
@@ -172,7 +182,7 @@ __device__ __forceinline__ void m2l_load_operator(unsigned char* raw, const floa
 // sources are read and existing targets written).  Requires the operator of order P in shared
 // memory (m2l_load_operator + a barrier) and no thread still reading the halo
 // buffer of a previous tile (a barrier).  All 128 threads call it.
-template <int P, bool ADAPTIVE = false>
+template <int P, bool ADAPTIVE = false, int UMAX = M2LCfg<P>::LOADS>
 __device__ __forceinline__ void m2l_tile(unsigned char* raw, const TileGeom& g, int periodic, int accumulate)
 {
     using C = M2LCfg<P>;
@@ -183,25 +193,43 @@ __device__ __forceinline__ void m2l_tile(unsigned char* raw, const TileGeom& g, 
     // Stage the 2 kHalo x 2 kHalo halo boxes, pre-scaled by b_k, into the
     // class-split transposed layout; consecutive threads read consecutive
     // 16-byte chunks of a row of boxes (coalesced); zero outside the level.
+    // Each thread first issues up to U (<= UMAX, a register budget) loads, then scales
+    // and stores them, so that a tile's staging costs a memory round trip or two
+    // instead of one per chunk.
     const float4* M4 = reinterpret_cast<const float4*>(g.M);
-    for (int i = tid; i < (2 * kHalo) * (2 * kHalo) * Q; i += kThreads) {
-        const int q = i % Q, bxy = i / Q;
-        const int hxb = bxy % (2 * kHalo), hyb = bxy / (2 * kHalo);
-        int ix = 2 * g.PX0 - 2 + hxb, iy = 2 * g.PY0 - 2 + hyb;
-        bool in = ix >= 0 && iy >= 0 && ix < g.side && iy < g.side;
-        if (periodic) {
-            ix = (ix + 2 * g.side) % g.side;
-            iy = (iy + 2 * g.side) % g.side;
-            in = true;
+    constexpr int NCH = (2 * kHalo) * (2 * kHalo) * Q;  // 16-byte chunks of the halo
+    constexpr int U = (NCH + kThreads - 1) / kThreads < UMAX ? (NCH + kThreads - 1) / kThreads : UMAX;
+    for (int i0 = tid; i0 < NCH; i0 += U * kThreads) {
+        float4 v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = i0 + u * kThreads;
+            v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (i >= NCH) continue;
+            const int q = i % Q, bxy = i / Q;
+            const int hxb = bxy % (2 * kHalo), hyb = bxy / (2 * kHalo);
+            int ix = 2 * g.PX0 - 2 + hxb, iy = 2 * g.PY0 - 2 + hyb;
+            bool in = ix >= 0 && iy >= 0 && ix < g.side && iy < g.side;
+            if (periodic) {
+                ix = (ix + 2 * g.side) % g.side;
+                iy = (iy + 2 * g.side) % g.side;
+                in = true;
+            }
+            if constexpr (ADAPTIVE)
+                if (in && g.exists) in = g.exists[(size_t)iy * g.side + ix] != 0;  // V-list: existing sources only
+            if (in) v[u] = __ldg(M4 + ((size_t)iy * g.side + ix) * Q + q);
         }
-        if constexpr (ADAPTIVE)
-            if (in && g.exists) in = g.exists[(size_t)iy * g.side + ix] != 0;  // V-list: existing sources only
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (in) v = __ldg(M4 + ((size_t)iy * g.side + ix) * Q + q);
-        float2* dst = s.buf + ((hxb & 1) + 2 * (hyb & 1)) * C::CS + (hyb >> 1) * kHalo + (hxb >> 1);
-        const float b0 = s.bs[2 * q], b1 = s.bs[2 * q + 1];
-        dst[(2 * q) * kPlane] = make_float2(v.x * b0, v.y * b0);
-        dst[(2 * q + 1) * kPlane] = make_float2(v.z * b1, v.w * b1);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = i0 + u * kThreads;
+            if (i >= NCH) continue;
+            const int q = i % Q, bxy = i / Q;
+            const int hxb = bxy % (2 * kHalo), hyb = bxy / (2 * kHalo);
+            float2* dst = s.buf + ((hxb & 1) + 2 * (hyb & 1)) * C::CS + (hyb >> 1) * kHalo + (hxb >> 1);
+            const float b0 = s.bs[2 * q], b1 = s.bs[2 * q + 1];
+            dst[(2 * q) * kPlane] = make_float2(v[u].x * b0, v[u].y * b0);
+            dst[(2 * q + 1) * kPlane] = make_float2(v[u].z * b1, v[u].w * b1);
+        }
     }
     __syncthreads();
 

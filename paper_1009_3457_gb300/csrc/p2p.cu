@@ -6,16 +6,17 @@
 //
 // Targets and sources are binned by box (fmm_bin_points); a pre-pass copies the
 // sources into box order, each as its position relative to its own box's
-// centre (formed in FP64, kept in FP32) and strength, so a box's sources are
-// one contiguous range and staging adds only the exact offset between box
-// centres -- no FP64 arithmetic per staged source.  Persistent CTAs of
-// 128 threads claim runs of up to 64 targets of one box from a claim table
-// (a finest-level box holds a few dozen points), gather the sources of the
-// 3 x 3 neighbourhood through the source permutation into shared memory in
-// batches -- position relative to the target box's centre (formed in FP64,
-// kept in FP32) and strength -- and each warp sums all the run's targets (two
-// per lane) against a quarter of every batch; the four partial sums of a
-// target meet in shared memory.  In FP32:
+// centre (read off the bits of the FP64 position, kept in FP32) and
+// strength, so a box's sources are one contiguous range and staging adds only
+// the exact offset between box centres -- no FP64 arithmetic per staged
+// source.  Persistent CTAs of 128 threads claim runs of up to 96 targets of
+// one box from a claim table (a finest-level box holds a few dozen points, so
+// nearly every box is one claim), gather the sources of the 3 x 3
+// neighbourhood into shared memory in batches -- position relative to the
+// target box's centre and strength -- and each warp sums the run's targets
+// (one to three rows of 32, as many as the run fills, one target per lane and
+// row) against a quarter of every batch; the four partial sums of a target
+// meet in shared memory.  In FP32:
 //   1/(dx + i dy) = (dx - i dy) / r2 with one approximate reciprocal per pair.
 // Positions relative to the target box keep |dx|, |dy| <= 1.5 box sides, so
 // FP32 carries the difference of two nearby points to ~2^-24 of a box side.
@@ -29,7 +30,7 @@ namespace fmmgb {
 
 constexpr int kP2pThreads = 128;
 constexpr int kP2pWarps = kP2pThreads / 32;     // each takes a quarter of the sources
-constexpr int kP2pR = 2;                        // targets per lane
+constexpr int kP2pR = 3;                        // targets per lane (rows of 32 targets per claim)
 constexpr int kP2pRun = 32 * kP2pR;             // targets per claim
 constexpr int kP2pBatch = 1024;                 // sources per shared-memory batch
 // added to every r^2: a source at the target's position (dx = dy = 0) then contributes
@@ -54,7 +55,8 @@ struct P2pArgs {
 };
 
 // sources in box order, so that a box's sources are one contiguous range; positions relative to
-// the centre of their own box (formed in FP64, kept in FP32: |x - c| <= half a box side)
+// the centre of their own box, read off the bits of the FP64 coordinates and kept in FP32
+// (|x - c| <= half a box side)
 __global__ void p2p_sort_kernel(int level, const double* __restrict__ xy, const double* __restrict__ c,
                                 const int* __restrict__ perm, int n, float4* __restrict__ out, int* err)
 {
@@ -66,12 +68,21 @@ __global__ void p2p_sort_kernel(int level, const double* __restrict__ xy, const 
         out[k] = make_float4(0.f, 0.f, 0.f, 0.f);
         return;
     }
-    const int side = 1 << level;
     const double x = __ldg(xy + 2 * (size_t)i), y = __ldg(xy + 2 * (size_t)i + 1);
+    const float cf = (float)__ldg(c + i);
+    long long X, Y;
+    if (grid_fixed31(x, level, X) && grid_fixed31(y, level, Y)) {
+        // offset from the box centre in box sides, scaled by the side 2^-level (exact)
+        const float hs = __int_as_float((127 - level) << 23);
+        out[k] = make_float4(cell_offset31(X) * hs, cell_offset31(Y) * hs, cf, 0.f);
+        return;
+    }
+    // outside the unit square: the clamped box, offset in FP64
+    const int side = 1 << level;
     const double px = x * side, py = y * side;
     const int ix = !(px >= 0.0) ? 0 : (px >= side ? side - 1 : (int)px);
     const int iy = !(py >= 0.0) ? 0 : (py >= side ? side - 1 : (int)py);
-    out[k] = make_float4((float)(x - (ix + 0.5) / side), (float)(y - (iy + 0.5) / side), (float)__ldg(c + i), 0.f);
+    out[k] = make_float4((float)(x - (ix + 0.5) / side), (float)(y - (iy + 0.5) / side), cf, 0.f);
 }
 
 __device__ __forceinline__ float rcp_approx(float x)
@@ -79,6 +90,26 @@ __device__ __forceinline__ float rcp_approx(float x)
     float r;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
+}
+
+// One warp's share of a staged batch (sources warp, warp + 4, ...) against the
+// claim's NR occupied rows of 32 targets (NR warp-uniform: empty rows cost nothing).
+template <int NR>
+__device__ __forceinline__ void p2p_batch(const float4* __restrict__ s_src, int cnt, int warp, const float* zx,
+                                          const float* zy, float* re, float* im)
+{
+#pragma unroll 4
+    for (int i = warp; i < cnt; i += kP2pWarps) {
+        const float4 v = s_src[i];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            const float dx = zx[r] - v.x, dy = zy[r] - v.y;
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, kP2pTiny));
+            const float w = v.z * rcp_approx(r2);
+            re[r] = fmaf(w, dx, re[r]);
+            im[r] = fmaf(-w, dy, im[r]);
+        }
+    }
 }
 
 __global__ void __launch_bounds__(kP2pThreads) fmm_p2p_kernel(P2pArgs a)
@@ -92,6 +123,7 @@ __global__ void __launch_bounds__(kP2pThreads) fmm_p2p_kernel(P2pArgs a)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int side = 1 << a.level, nbox = side * side;
     const double inv_side = 1.0 / side;
+    const float hs = __int_as_float((127 - a.level) << 23);  // the box side 2^-level
     const int total = __ldg(a.claims + nbox);
 
     for (;;) {
@@ -112,6 +144,7 @@ __global__ void __launch_bounds__(kP2pThreads) fmm_p2p_kernel(P2pArgs a)
         __syncthreads();
         const int first = s_claim[0], end = s_claim[1], box = s_claim[2];
         if (first < 0) break;
+        const int nrow = (end - first + 31) >> 5;  // occupied rows of 32 targets (1..kP2pR)
         const int tx = box & (side - 1), ty = box >> a.level;
         const double cx = (tx + 0.5) * inv_side, cy = (ty + 0.5) * inv_side;
         if (tid == 0) {
@@ -142,8 +175,16 @@ __global__ void __launch_bounds__(kP2pThreads) fmm_p2p_kernel(P2pArgs a)
                 const int j = __ldg(a.tperm + pos);
                 if ((unsigned)j < (unsigned)a.nz) {
                     tj[r] = j;
-                    zx[r] = (float)(__ldg(a.z + 2 * (size_t)j) - cx);
-                    zy[r] = (float)(__ldg(a.z + 2 * (size_t)j + 1) - cy);
+                    const double x = __ldg(a.z + 2 * (size_t)j), y = __ldg(a.z + 2 * (size_t)j + 1);
+                    long long X, Y;
+                    if (grid_fixed31(x, a.level, X) && grid_fixed31(y, a.level, Y) && (int)(X >> 31) == tx &&
+                        (int)(Y >> 31) == ty) {
+                        zx[r] = cell_offset31(X) * hs;  // in the claimed box: no FP64 arithmetic
+                        zy[r] = cell_offset31(Y) * hs;
+                    } else {
+                        zx[r] = (float)(x - cx);
+                        zy[r] = (float)(y - cy);
+                    }
                 } else if (warp == 0) {
                     atomicOr(a.err, DEV_ERR_CHECK);
                 }
@@ -169,25 +210,17 @@ __global__ void __launch_bounds__(kP2pThreads) fmm_p2p_kernel(P2pArgs a)
                 s_src[i] = v;
             }
             __syncthreads();
-            {
-#pragma unroll 4
-                for (int i = warp; i < cnt; i += kP2pWarps) {
-                    const float4 v = s_src[i];
-#pragma unroll
-                    for (int r = 0; r < kP2pR; ++r) {
-                        const float dx = zx[r] - v.x, dy = zy[r] - v.y;
-                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, kP2pTiny));
-                        const float w = v.z * rcp_approx(r2);
-                        re[r] = fmaf(w, dx, re[r]);
-                        im[r] = fmaf(-w, dy, im[r]);
-                    }
-                }
+            switch (nrow) {
+                case 1: p2p_batch<1>(s_src, cnt, warp, zx, zy, re, im); break;
+                case 2: p2p_batch<2>(s_src, cnt, warp, zx, zy, re, im); break;
+                default: p2p_batch<3>(s_src, cnt, warp, zx, zy, re, im); break;
             }
             __syncthreads();  // the batch buffer is refilled next
         }
         if (warp > 0) {
 #pragma unroll
-            for (int r = 0; r < kP2pR; ++r) s_part[warp - 1][r * 32 + lane] = make_float2(re[r], im[r]);
+            for (int r = 0; r < kP2pR; ++r)
+                if (r < nrow) s_part[warp - 1][r * 32 + lane] = make_float2(re[r], im[r]);
         }
         __syncthreads();
         if (warp > 0) continue;  // warp 0 writes; every warp is back at the claim's barrier next

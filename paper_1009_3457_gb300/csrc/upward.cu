@@ -61,8 +61,16 @@ __global__ void __launch_bounds__(kP2mThreads) p2m_binned_kernel(int level, cons
             atomicOr(err, DEV_ERR_CHECK);
             continue;
         }
-        const float wr = (float)(xy[2 * (size_t)i] * side - (bx + 0.5));
-        const float wi = (float)(xy[2 * (size_t)i + 1] * side - (by + 0.5));
+        const double x = xy[2 * (size_t)i], y = xy[2 * (size_t)i + 1];
+        long long X, Y;
+        float wr, wi;  // offset from the box centre in box sides
+        if (grid_fixed31(x, level, X) && grid_fixed31(y, level, Y) && (int)(X >> 31) == bx && (int)(Y >> 31) == by) {
+            wr = cell_offset31(X);  // no FP64 arithmetic for a point inside its box
+            wi = cell_offset31(Y);
+        } else {
+            wr = (float)(x * side - (bx + 0.5));
+            wi = (float)(y * side - (by + 0.5));
+        }
         float pr = (float)c[i], pi = 0.f;
 #pragma unroll
         for (int k = 0; k < P; ++k) {

@@ -148,6 +148,11 @@ def test_fgt_t2p_matches_oracle(fmm, orc, p):
     g = 4
     C = rng.standard_normal((4 ** g, p, p)) / (1.0 + np.add.outer(np.arange(p), np.arange(p)))[None]
     y = rng.random((3000, 2))
+    # on and next to box boundaries, at the ends of [0, 1) and just outside it (the nearest box)
+    k = np.arange(17) / 16
+    edge = np.concatenate([k, np.nextafter(k, -1.0), np.nextafter(k, 2.0), [1 - 2.0 ** -53, 1.01, -0.01, 0.0]])
+    y[:len(edge), 0] = edge
+    y[len(edge):2 * len(edge), 1] = edge
     G = torch.empty(3000, dtype=torch.float32, device="cuda")
     fmm.fgt_t2p(g, p, 0.1, _dev(C), torch.from_numpy(y).cuda(), G)
     fmm.fmm_sync_status()

@@ -93,6 +93,37 @@ def test_bin_points_is_an_exact_counting_sort(fmm):
     np.testing.assert_array_equal(box[perm], owner)
 
 
+def _edge_values(g):
+    """Coordinates on and next to every cell boundary of the 2^g grid, the ends of [0, 1),
+    subnormals, signed zeros, and values outside [0, 1) (clamped), infinities and NaN."""
+    k = np.arange((1 << g) + 1) / (1 << g)
+    v = np.concatenate([k, np.nextafter(k, -np.inf), np.nextafter(k, np.inf),
+                        [0.0, -0.0, 5e-324, 1e-310, 1e-300, 1 - 2.0 ** -53, 1.0, 1.5, 2.0 ** 40, -1e-300, -3.0,
+                         np.inf, -np.inf, np.nan, 0.5, 1.0 / 3.0]])
+    return v
+
+
+@pytest.mark.parametrize("g", [0, 1, 5, 10])
+def test_bin_points_edge_coordinates(fmm, g):
+    """The device places a coordinate by floor(v 2^g) exactly (read off the bits of the
+    FP64 value), clamped to the grid, NaN to cell 0."""
+    import torch
+
+    v = _edge_values(g)
+    rng = np.random.default_rng(17 + g)
+    y = np.stack([np.concatenate([v, rng.permutation(v)]), np.concatenate([rng.permutation(v), v])], axis=1)
+    side = 1 << g
+    with np.errstate(invalid="ignore", over="ignore"):
+        cell = np.floor(y * side)
+    cell = np.clip(np.where(np.isnan(cell), 0.0, cell), 0, side - 1).astype(np.int64)
+    box = cell[:, 1] * side + cell[:, 0]
+    perm, start = _bin(fmm, g, torch.from_numpy(y).cuda())
+    perm, start = perm.cpu().numpy(), start.cpu().numpy()
+    counts = np.bincount(box, minlength=4 ** g)
+    np.testing.assert_array_equal(np.diff(start), counts)
+    np.testing.assert_array_equal(box[perm], np.repeat(np.arange(4 ** g), counts))
+
+
 def test_bin_points_empty_and_single(fmm):
     import torch
 

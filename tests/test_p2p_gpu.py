@@ -69,6 +69,21 @@ def test_p2p_matches_oracle(fmm, orc, level, bar):
     _check(_p2p(fmm, level, xy, c, z), orc.p2p_uniform(level, xy, c, z), l2=bar, worst=max(1e-4, 2 * bar))
 
 
+def test_p2p_points_on_box_boundaries_and_outside(fmm, orc):
+    """Sources on the level's box boundaries, targets one ulp either side of them, and
+    points at 1.0 and just outside the unit square (clamped to the edge boxes)."""
+    rng = np.random.default_rng(44)
+    level, side = 3, 8
+    xy, c = workloads.uniform_particles(3000, rng)
+    k = np.arange(side + 1) / side
+    xy[:side + 1, 0] = k
+    xy[side + 1:2 * side + 2, 1] = k
+    xy[-4:] = [[1.0, 0.3], [1.004, 0.6], [-0.003, 0.2], [0.7, 1.002]]
+    zx = np.concatenate([np.nextafter(k, -1.0), np.nextafter(k, 2.0), rng.random(300), [1.0, 1.006, -0.002]])
+    zy = rng.random(len(zx))
+    _check(_p2p(fmm, level, xy, c, zx + 1j * zy), orc.p2p_uniform(level, xy, c, zx + 1j * zy))
+
+
 def test_p2p_targets_on_sources_skip_themselves(fmm, orc):
     xy, c = workloads.uniform_particles(5000, np.random.default_rng(3))
     z = xy[:, 0] + 1j * xy[:, 1]
