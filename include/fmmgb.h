@@ -368,12 +368,25 @@ int fmm_l2p(int32_t p, int64_t n, const double* z, const int32_t* lev, const int
 int fmm_l2p_adjoint(int32_t p, int64_t n, const double* z, const int32_t* lev, const int64_t* box,
                     const void* cot, void* const* G_levels, int32_t max_level, void* stream);
 
+/* fmm_l2p_binned: fmm_l2p for the n points z of a uniform tree's `level`, binned
+ *   by fmm_bin_points(level, z, n, perm, box_start, ...) (Sec. 2.1 stage 4):
+ *     phi_j (+)= (1/r) sum_n L~[b][n] ((z_j - x_b) / r)^n,  b the box of z_j,
+ *   phi_j = 0 at levels 0 and 1 (no lists there).  One thread block per box
+ *   keeps the box's LE in shared memory; a point's offset from its box centre is
+ *   read off the bits of its FP64 coordinates.  z: device float64 [n][2];
+ *   perm, box_start: device int32 [n], [4^level + 1]; L: device complex64
+ *   [4^level][p] (may be NULL at levels 0, 1); phi: device complex64 [n].
+ *   p 1..64; level 0..10; flags FMM_ACCUMULATE.  A perm entry or box start out
+ *   of range sets the device error word's check bit and is skipped. */
+int fmm_l2p_binned(int32_t level, int32_t p, const double* z, int64_t n, const int32_t* perm,
+                   const int32_t* box_start, const void* L, void* phi, int32_t flags, void* stream);
+
 /* fmm_p2m_binned: fmm_p2m for points binned by fmm_bin_points(level, xy, n, ...)
  *   (perm, box_start): one thread block per box sums its points (powers in FP32
- *   of d formed in FP64), one store per coefficient -- no atomics, the same
- *   result on every run.  p 6, 8, 12, 16 or 24; level 0..10; flags FMM_ACCUMULATE.
- *   A perm entry or box start out of range sets the device error word's check
- *   bit and is skipped. */
+ *   of d read off the bits of the FP64 coordinates), one store per coefficient --
+ *   no atomics, the same result on every run.  p 6, 8, 12, 16 or 24; level
+ *   0..10; flags FMM_ACCUMULATE.  A perm entry or box start out of range sets the
+ *   device error word's check bit and is skipped. */
 int fmm_p2m_binned(int32_t level, int32_t p, const double* xy, const double* c, int64_t n, const int32_t* perm,
                    const int32_t* box_start, void* M, int32_t flags, void* stream);
 

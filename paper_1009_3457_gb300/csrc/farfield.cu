@@ -215,6 +215,63 @@ int launch_l2l(int child_level, int p, const float2* Lp, float2* Lc, bool acc, b
     return FMM_OK;
 }
 
+// L2P at points binned by box (fmm_bin_points): one block per box keeps the box's
+// LE in shared memory and evaluates it at each of the box's points.  The
+// per-point kernel above reads a random box's LE per thread (16 scattered
+// 8-byte loads, the SM's L1 serving one line per lane); here the LE is one
+// coalesced read per box and every point's Horner loop runs from shared memory.
+constexpr int kL2pThreads = 64;
+
+__global__ void __launch_bounds__(kL2pThreads) l2p_binned_kernel(int level, int p, const double* __restrict__ z,
+                                                                 int n, const int* __restrict__ perm,
+                                                                 const int* __restrict__ box_start,
+                                                                 const float2* __restrict__ L, float2* __restrict__ phi,
+                                                                 int accumulate, int* err)
+{
+    __shared__ float2 s_l[64];
+    const int side = 1 << level;
+    const int b = blockIdx.x, tid = threadIdx.x;
+    const int bx = b & (side - 1), by = b >> level;
+    int first = box_start[b], end = box_start[b + 1];
+    if (first < 0 || end > n || first > end) {
+        if (tid == 0) atomicOr(err, DEV_ERR_CHECK);
+        return;
+    }
+    if (first == end) return;
+    for (int k = tid; k < p; k += kL2pThreads) s_l[k] = level >= 2 ? L[(size_t)b * p + k] : make_float2(0.f, 0.f);
+    __syncthreads();
+    for (int q = first + tid; q < end; q += kL2pThreads) {
+        const int j = perm[q];
+        if ((unsigned)j >= (unsigned)n) {
+            atomicOr(err, DEV_ERR_CHECK);
+            continue;
+        }
+        const double x = z[2 * (size_t)j], y = z[2 * (size_t)j + 1];
+        long long X, Y;
+        float wr, wi;  // offset from the box centre in box sides
+        if (grid_fixed31(x, level, X) && grid_fixed31(y, level, Y) && (int)(X >> 31) == bx && (int)(Y >> 31) == by) {
+            wr = cell_offset31(X);
+            wi = cell_offset31(Y);
+        } else {
+            wr = (float)(x * side - (bx + 0.5));
+            wi = (float)(y * side - (by + 0.5));
+        }
+        float ar = 0.f, ai = 0.f;
+        for (int k = p - 1; k >= 0; --k) {
+            const float2 v = s_l[k];
+            const float tr = fmaf(ar, wr, fmaf(-ai, wi, v.x));
+            ai = fmaf(ar, wi, fmaf(ai, wr, v.y));
+            ar = tr;
+        }
+        float2 o = make_float2(ar * (float)side, ai * (float)side);
+        if (accumulate) {
+            o.x += phi[j].x;
+            o.y += phi[j].y;
+        }
+        phi[j] = o;
+    }
+}
+
 int launch_l2p(int p, int64_t n, const double* z, const int32_t* lev, const int64_t* box, const void* const* L,
                int max_level, void* phi, bool acc, bool adjoint, cudaStream_t st)
 {
@@ -305,6 +362,28 @@ int fmm_l2p(int32_t p, int64_t n, const double* z, const int32_t* lev, const int
     if (flags & ~FMM_ACCUMULATE) return fail(FMM_EINVAL, "fmm_l2p: unknown flags 0x%x", flags);
     return launch_l2p(p, n, z, lev, box, L_levels, max_level, phi, (flags & FMM_ACCUMULATE) != 0, false,
                       (cudaStream_t)stream);
+}
+
+int fmm_l2p_binned(int32_t level, int32_t p, const double* z, int64_t n, const int32_t* perm,
+                   const int32_t* box_start, const void* L, void* phi, int32_t flags, void* stream)
+{
+    clear_error();
+    if (level < 0 || level > 10) return fail(FMM_EINVAL, "fmm_l2p_binned: level %d outside 0..10", level);
+    if (p < 1 || p > 64) return fail(FMM_EINVAL, "fmm_l2p_binned: p = %d outside 1..64", p);
+    if (n < 0 || n > INT32_MAX) return fail(FMM_EINVAL, "fmm_l2p_binned: n = %lld outside 0..2^31-1", (long long)n);
+    if (!box_start || (n > 0 && (!z || !perm || !phi || (level >= 2 && !L))))
+        return fail(FMM_EINVAL, "fmm_l2p_binned: NULL pointer");
+    if (((uintptr_t)z & 7) || ((uintptr_t)phi & 7) || ((uintptr_t)L & 7) || ((uintptr_t)perm & 3) ||
+        ((uintptr_t)box_start & 3))
+        return fail(FMM_EINVAL, "fmm_l2p_binned: misaligned pointer");
+    if (flags & ~FMM_ACCUMULATE) return fail(FMM_EINVAL, "fmm_l2p_binned: unknown flags 0x%x", flags);
+    if (n == 0) return FMM_OK;
+    int* err = nullptr;
+    if (int rc = device_error_word(&err)) return rc;
+    l2p_binned_kernel<<<1u << (2 * level), kL2pThreads, 0, (cudaStream_t)stream>>>(
+        level, p, z, (int)n, perm, box_start, (const float2*)L, (float2*)phi, (flags & FMM_ACCUMULATE) ? 1 : 0, err);
+    FMM_CUDA_TRY(cudaGetLastError());
+    return FMM_OK;
 }
 
 int fmm_l2p_adjoint(int32_t p, int64_t n, const double* z, const int32_t* lev, const int64_t* box, const void* cot,

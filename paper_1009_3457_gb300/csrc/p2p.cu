@@ -49,6 +49,8 @@ struct P2pArgs {
     const int* tperm;
     const int* tstart;
     const int* claims;
+    const int4* tab;  // claim table (p2p_claim_table_kernel), ntab entries
+    int ntab;
     float2* phi;
     int* cursor;  // [0] next claim index, [1] CTAs finished
     int* err;
@@ -112,56 +114,75 @@ __device__ __forceinline__ void p2p_batch(const float4* __restrict__ s_src, int 
     }
 }
 
+// Claim table: entry k = (first, end, box) of the k-th run of at most kP2pRun
+// targets of one box (the runs of box b are claims[b] .. claims[b+1]-1), so a
+// CTA finds its claim with one load instead of a binary search over the boxes.
+// Runs past `cap` entries, or a box_start that does not bin [0, nz), set the
+// error word (the kernel then skips those runs).
+__global__ void p2p_claim_table_kernel(int nbox, const int* __restrict__ claims, const int* __restrict__ tstart,
+                                       int nz, int cap, int4* __restrict__ tab, int* err)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbox) return;
+    const int c0 = claims[b], c1 = claims[b + 1];
+    const int f0 = tstart[b], e0 = min(tstart[b + 1], nz);
+    for (int k = c0; k < c1; ++k) {
+        if (k < 0 || k >= cap) {
+            atomicOr(err, DEV_ERR_CHECK);
+            return;
+        }
+        const int f = f0 + (k - c0) * kP2pRun, e = min(f + kP2pRun, e0);
+        const bool ok = 0 <= f && f < e;
+        if (!ok) atomicOr(err, DEV_ERR_CHECK);
+        tab[k] = ok ? make_int4(f, e, b, 0) : make_int4(0, 0, b, 0);
+    }
+}
+
 __global__ void __launch_bounds__(kP2pThreads) fmm_p2p_kernel(P2pArgs a)
 {
     __shared__ float4 s_src[kP2pBatch];  // x - cx, y - cy, c
-    __shared__ int s_claim[3];
-    __shared__ int s_box[9], s_pre[10];  // first sorted source of each neighbour box, prefix of their counts
-    __shared__ float s_ox[9], s_oy[9];     // centre of each neighbour box minus the target box's
+    __shared__ int4 s_claim;
+    __shared__ int s_box[9], s_cnt[9];  // first sorted source and source count of each neighbour box
+    __shared__ float s_ox[9], s_oy[9];  // centre of each neighbour box minus the target box's
     __shared__ float2 s_part[kP2pWarps - 1][kP2pRun];  // partial sums of warps 1..3
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int side = 1 << a.level, nbox = side * side;
+    const int side = 1 << a.level;
     const double inv_side = 1.0 / side;
     const float hs = __int_as_float((127 - a.level) << 23);  // the box side 2^-level
-    const int total = __ldg(a.claims + nbox);
+    const int total = min(__ldg(a.claims + (side * side)), a.ntab);
+    // thread 0 fetches the index of the CTA's next claim one claim ahead
+    int knext = tid == 0 ? atomicAdd(a.cursor, 1) : 0;
 
     for (;;) {
         if (tid == 0) {
-            const int k = atomicAdd(a.cursor, 1);
-            int f = -1, e = -1, b = 0;
-            if (k < total) {
-                h2p_claim_range(a.claims, a.tstart, nbox, a.nz, kP2pRun, k, &f, &e, &b);
-                if (f >= e) atomicOr(a.err, DEV_ERR_CHECK);  // box_start does not bin [0, nz)
-            }
-            s_claim[0] = f;
-            s_claim[1] = e;
-            s_claim[2] = b;
-        }
-        if (tid < 9) {
-            s_box[tid] = -1;
+            const int k = knext;
+            s_claim = k < total ? __ldg(a.tab + k) : make_int4(-1, -1, 0, 0);
+            if (k < total) knext = atomicAdd(a.cursor, 1);
         }
         __syncthreads();
-        const int first = s_claim[0], end = s_claim[1], box = s_claim[2];
+        const int4 cl = s_claim;
+        const int first = cl.x, end = cl.y, box = cl.z;
         if (first < 0) break;
-        const int nrow = (end - first + 31) >> 5;  // occupied rows of 32 targets (1..kP2pR)
+        const int nrow = (end - first + 31) >> 5;  // occupied rows of 32 targets (0..kP2pR)
         const int tx = box & (side - 1), ty = box >> a.level;
         const double cx = (tx + 0.5) * inv_side, cy = (ty + 0.5) * inv_side;
-        if (tid == 0) {
-            int acc = 0;
-            for (int q = 0; q < 9; ++q) {
-                const int sx = tx + q % 3 - 1, sy = ty + q / 3 - 1;
-                s_pre[q] = acc;
-                s_ox[q] = (float)((q % 3 - 1) * inv_side);  // exact: a power of two or zero
-                s_oy[q] = (float)((q / 3 - 1) * inv_side);
-                if (sx < 0 || sy < 0 || sx >= side || sy >= side) continue;
+        if (tid < 9) {  // the 3 x 3 neighbourhood, one box per thread
+            const int sx = tx + tid % 3 - 1, sy = ty + tid / 3 - 1;
+            s_ox[tid] = (float)((tid % 3 - 1) * inv_side);  // exact: a power of two or zero
+            s_oy[tid] = (float)((tid / 3 - 1) * inv_side);
+            int b0 = -1, m = 0;
+            if (sx >= 0 && sy >= 0 && sx < side && sy < side) {
                 const int b = sy * side + sx;
-                const int b0 = __ldg(a.sstart + b), m = __ldg(a.sstart + b + 1) - b0;
-                if (m <= 0 || b0 < 0 || b0 + m > a.n) continue;
-                s_box[q] = b0;
-                acc += m;
+                b0 = __ldg(a.sstart + b);
+                m = __ldg(a.sstart + b + 1) - b0;
+                if (m <= 0 || b0 < 0 || b0 + m > a.n) {
+                    b0 = -1;
+                    m = 0;
+                }
             }
-            s_pre[9] = acc;
+            s_box[tid] = b0;
+            s_cnt[tid] = m;
         }
 
         int tj[kP2pR];
@@ -191,18 +212,26 @@ __global__ void __launch_bounds__(kP2pThreads) fmm_p2p_kernel(P2pArgs a)
             }
         }
         __syncthreads();
-        const int S = s_pre[9];
+        int pre[10];  // prefix of the neighbour boxes' source counts
+        pre[0] = 0;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) pre[q + 1] = pre[q] + s_cnt[q];
+        const int S = pre[9];
 
         for (int base = 0; base < S; base += kP2pBatch) {
             const int cnt = min(kP2pBatch, S - base);
             for (int i = tid; i < cnt; i += kP2pThreads) {
                 const int g = base + i;
                 int q = 0;
-                while (q < 8 && s_pre[q + 1] <= g) ++q;
+#pragma unroll
+                for (int t = 1; t < 9; ++t) q += pre[t] <= g;  // the neighbour box holding source g
                 const int b0 = s_box[q];
                 float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (b0 >= 0) {
-                    const float4 u = a.src[b0 + (g - s_pre[q])];
+                    int off = 0;  // pre[q], with registers indexed by constants only
+#pragma unroll
+                    for (int t = 1; t < 9; ++t) off = t == q ? pre[t] : off;
+                    const float4 u = a.src[b0 + (g - off)];
                     v.x = u.x + s_ox[q];
                     v.y = u.y + s_oy[q];
                     v.z = u.z;
@@ -211,6 +240,7 @@ __global__ void __launch_bounds__(kP2pThreads) fmm_p2p_kernel(P2pArgs a)
             }
             __syncthreads();
             switch (nrow) {
+                case 0: break;  // a run the claim table flagged (error word set)
                 case 1: p2p_batch<1>(s_src, cnt, warp, zx, zy, re, im); break;
                 case 2: p2p_batch<2>(s_src, cnt, warp, zx, zy, re, im); break;
                 default: p2p_batch<3>(s_src, cnt, warp, zx, zy, re, im); break;
@@ -318,13 +348,21 @@ extern "C" int fmm_p2p(int32_t level, const double* xy, const double* c, int64_t
     args.claims = claims;
     const int nbox = 1 << (2 * level);
     if (int rc = launch_h2p_claims(nbox, tgt_start, kP2pRun, claims, args.err, st)) return rc;
+    // one buffer: the sources in box order, then the claim table
+    const int64_t most = nz / kP2pRun + nbox;  // claims can be no more
     float4* src = nullptr;
+    if (int rc = p2p_source_buffer((size_t)(n + most) * sizeof(float4), &src)) return rc;
+    int4* tab = reinterpret_cast<int4*>(src + n);
+    p2p_claim_table_kernel<<<(unsigned)((nbox + 255) / 256), 256, 0, st>>>(nbox, claims, tgt_start, (int)nz, (int)most,
+                                                                          tab, args.err);
+    FMM_CUDA_TRY(cudaGetLastError());
     if (n > 0) {
-        if (int rc = p2p_source_buffer((size_t)n * sizeof(float4), &src)) return rc;
         p2p_sort_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(level, xy, c, src_perm, (int)n, src, args.err);
         FMM_CUDA_TRY(cudaGetLastError());
     }
     args.src = src;
+    args.tab = tab;
+    args.ntab = (int)most;
     static int occ;
     static std::mutex mu;
     {
@@ -336,7 +374,6 @@ extern "C" int fmm_p2p(int32_t level, const double* xy, const double* c, int64_t
     }
     int sms = 0;
     if (int rc = device_sm_count(&sms)) return rc;
-    const int64_t most = nz / kP2pRun + nbox;  // claims can be no more
     const int grid = (int)std::min<int64_t>((int64_t)occ * sms, most);
     fmm_p2p_kernel<<<grid, kP2pThreads, 0, st>>>(args);
     FMM_CUDA_TRY(cudaGetLastError());

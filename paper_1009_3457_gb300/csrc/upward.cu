@@ -30,11 +30,15 @@ __global__ void p2m_kernel(int level, int p, const double* __restrict__ xy, cons
     }
 }
 
-// P2M from points binned by box (fmm_bin_points at `level`): one CTA per box
-// sums its points' c d^k (d formed in FP64, powers in FP32: |d| <= 1/sqrt(2)),
-// each thread over a strided share of the box's points, then a block
-// reduction; one store per coefficient, no atomics, a fixed summation order.
+// P2M from points binned by box (fmm_bin_points at `level`): one warp per box
+// (four boxes per CTA) sums its points' c d^k (d read off the bits of the FP64
+// coordinates, powers in FP32: |d| <= 1/sqrt(2)), each lane over a strided
+// share of the box's points; the lanes' partial sums meet through a transpose in
+// shared memory (lane t < 2p adds up real t of the 32 lanes' partials), so a
+// box costs 2p + 32 shared-memory accesses per lane instead of a shuffle tree
+// per coefficient.  One store per real, no atomics, a fixed summation order.
 constexpr int kP2mThreads = 128;
+constexpr int kP2mBoxes = kP2mThreads / 32;
 
 template <int P>
 __global__ void __launch_bounds__(kP2mThreads) p2m_binned_kernel(int level, const double* __restrict__ xy,
@@ -43,19 +47,22 @@ __global__ void __launch_bounds__(kP2mThreads) p2m_binned_kernel(int level, cons
                                                                  const int* __restrict__ box_start,
                                                                  float2* __restrict__ M, int accumulate, int* err)
 {
-    __shared__ float2 s_red[kP2mThreads / 32][P];
-    const int side = 1 << level;
-    const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int R = 2 * P + 1;  // padded row of one lane's reals: conflict-free column reads
+    __shared__ float s_red[kP2mBoxes][32 * R];
+    const int side = 1 << level, nbox = side * side;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int b = blockIdx.x * kP2mBoxes + warp;
+    if (b >= nbox) return;  // whole warps only: no block barrier below
     const int bx = b & (side - 1), by = b >> level;
     int first = box_start[b], end = box_start[b + 1];
     if (first < 0 || end > n || first > end) {
-        if (tid == 0) atomicOr(err, DEV_ERR_CHECK);
+        if (lane == 0) atomicOr(err, DEV_ERR_CHECK);
         first = end = 0;
     }
     float2 acc[P];
 #pragma unroll
     for (int k = 0; k < P; ++k) acc[k] = make_float2(0.f, 0.f);
-    for (int q = first + tid; q < end; q += kP2mThreads) {
+    for (int q = first + lane; q < end; q += 32) {
         const int i = perm[q];
         if ((unsigned)i >= (unsigned)n) {
             atomicOr(err, DEV_ERR_CHECK);
@@ -81,32 +88,19 @@ __global__ void __launch_bounds__(kP2mThreads) p2m_binned_kernel(int level, cons
             pr = t;
         }
     }
-    // warp sums, then the warps' sums in shared memory
+    float* red = s_red[warp];
 #pragma unroll
     for (int k = 0; k < P; ++k) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            acc[k].x += __shfl_xor_sync(0xffffffffu, acc[k].x, o);
-            acc[k].y += __shfl_xor_sync(0xffffffffu, acc[k].y, o);
-        }
+        red[lane * R + 2 * k] = acc[k].x;
+        red[lane * R + 2 * k + 1] = acc[k].y;
     }
-    if (lane == 0) {
-#pragma unroll
-        for (int k = 0; k < P; ++k) s_red[warp][k] = acc[k];
-    }
-    __syncthreads();
-    if (tid < P) {
-        float2 v = s_red[0][tid];
-#pragma unroll
-        for (int w = 1; w < kP2mThreads / 32; ++w) {
-            v.x += s_red[w][tid].x;
-            v.y += s_red[w][tid].y;
-        }
-        float2* dst = M + (size_t)b * P + tid;
-        if (accumulate) {
-            v.x += dst->x;
-            v.y += dst->y;
-        }
+    __syncwarp();
+    for (int t = lane; t < 2 * P; t += 32) {
+        float v = 0.f;
+#pragma unroll 8
+        for (int l = 0; l < 32; ++l) v += red[l * R + t];
+        float* dst = reinterpret_cast<float*>(M + (size_t)b * P) + t;
+        if (accumulate) v += *dst;
         *dst = v;
     }
 }
@@ -114,13 +108,13 @@ __global__ void __launch_bounds__(kP2mThreads) p2m_binned_kernel(int level, cons
 int launch_p2m_binned(int level, int p, const double* xy, const double* c, int n, const int* perm,
                       const int* box_start, float2* M, bool acc, int* err, cudaStream_t st)
 {
-    const unsigned nbox = 1u << (2 * level);
+    const unsigned nbox = 1u << (2 * level), grid = (nbox + kP2mBoxes - 1) / kP2mBoxes;
     switch (p) {
-        case 6: p2m_binned_kernel<6><<<nbox, kP2mThreads, 0, st>>>(level, xy, c, n, perm, box_start, M, acc, err); break;
-        case 8: p2m_binned_kernel<8><<<nbox, kP2mThreads, 0, st>>>(level, xy, c, n, perm, box_start, M, acc, err); break;
-        case 12: p2m_binned_kernel<12><<<nbox, kP2mThreads, 0, st>>>(level, xy, c, n, perm, box_start, M, acc, err); break;
-        case 16: p2m_binned_kernel<16><<<nbox, kP2mThreads, 0, st>>>(level, xy, c, n, perm, box_start, M, acc, err); break;
-        case 24: p2m_binned_kernel<24><<<nbox, kP2mThreads, 0, st>>>(level, xy, c, n, perm, box_start, M, acc, err); break;
+        case 6: p2m_binned_kernel<6><<<grid, kP2mThreads, 0, st>>>(level, xy, c, n, perm, box_start, M, acc, err); break;
+        case 8: p2m_binned_kernel<8><<<grid, kP2mThreads, 0, st>>>(level, xy, c, n, perm, box_start, M, acc, err); break;
+        case 12: p2m_binned_kernel<12><<<grid, kP2mThreads, 0, st>>>(level, xy, c, n, perm, box_start, M, acc, err); break;
+        case 16: p2m_binned_kernel<16><<<grid, kP2mThreads, 0, st>>>(level, xy, c, n, perm, box_start, M, acc, err); break;
+        case 24: p2m_binned_kernel<24><<<grid, kP2mThreads, 0, st>>>(level, xy, c, n, perm, box_start, M, acc, err); break;
         default: return fail(FMM_EINVAL, "fmm_p2m_binned: unsupported p = %d (6, 8, 12, 16, 24)", p);
     }
     FMM_CUDA_TRY(cudaGetLastError());

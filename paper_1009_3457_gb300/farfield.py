@@ -102,8 +102,8 @@ def far_field_objective(tree, p: int, xy: torch.Tensor, c: torch.Tensor, leaf, z
 class FmmPotential:
     """The whole FMM on a uniform tree to level L (Sec. 2.1 stages 2-5), every stage a
     library kernel: P2M at level L (on the binned points), M2M up, M2L over the interaction lists of levels 2..L,
-    L2L down, L2P at each target's level-L box, plus the near field (own and adjacent
-    boxes) by ``fmm_p2p``.
+    L2L down, L2P at each target's level-L box (on the binned targets), plus the near
+    field (own and adjacent boxes) by ``fmm_p2p``.
 
         phi(z) = sum_i c_i / (z - y_i)   (sources at exactly z skipped)
 
@@ -131,8 +131,6 @@ class FmmPotential:
 
         self.sperm, self.sstart = bins(self.xy)
         self.tperm, self.tstart = bins(self.z)
-        lev, box = leaf_boxes(tree, self.z)
-        self.zlev, self.zbox = lev.contiguous(), box.contiguous()
         self.phi = torch.empty(self.z.shape[0], dtype=torch.complex64, device=dev)
 
     def __call__(self) -> torch.Tensor:
@@ -143,7 +141,7 @@ class FmmPotential:
         fmmgb.fmm_m2l_levels(self.tree, 2, p, self.Ms, self.Ls, prec=self.prec)
         for i in range(1, len(self.levels)):
             fmmgb.fmm_l2l(self.levels[i], p, self.Ls[i - 1], self.Ls[i], accumulate=True)
-        fmmgb.fmm_l2p(p, self.z, self.zlev, self.zbox, dict(zip(self.levels, self.Ls)), L, self.phi)
+        fmmgb.fmm_l2p_binned(L, p, self.z, self.tperm, self.tstart, self.Ls[-1], self.phi)
         fmmgb.fmm_p2p(L, self.xy, self.c, self.sperm, self.sstart, self.z, self.tperm, self.tstart, self.phi,
                       accumulate=True)
         return self.phi

@@ -110,6 +110,7 @@ SIGNATURES = {
     "fmm_bin_points": (ctypes.c_int, [_i32, _vp, _i64, _vp, _vp, _vp, _vp]),
     "fmm_m2l_paper_design": (ctypes.c_int, [_vp, _i32, _i32, _vp, _vp, _vp, _i32, _vp]),
     "fmm_p2m_binned": (ctypes.c_int, [_i32, _i32, _vp, _vp, _i64, _vp, _vp, _vp, _i32, _vp]),
+    "fmm_l2p_binned": (ctypes.c_int, [_i32, _i32, _vp, _i64, _vp, _vp, _vp, _vp, _i32, _vp]),
     "fmm_p2p": (ctypes.c_int, [_i32, _vp, _vp, _i64, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _i32, _vp]),
     "fgt_p2h_binned": (ctypes.c_int, [_i32, _i32, _d, _vp, _vp, _i64, _vp, _vp, _i32, _vp]),
     "fgt_h2p": (ctypes.c_int, [_i32, _i32, _i32, _i32, _d, _vp, _vp, _i64, _vp, _vp, _vp, _i32, _vp]),
@@ -355,6 +356,13 @@ def fmm_l2p(p: int, z, lev, box, L_levels: dict, max_level: int, phi, accumulate
     n = 0 if lev is None else lev.numel()
     _check(load().fmm_l2p(p, n, _ptr(z), _ptr(lev), _ptr(box), _level_table(L_levels, max_level), max_level,
                           _ptr(phi), FMM_ACCUMULATE if accumulate else 0, _stream(stream)))
+
+
+def fmm_l2p_binned(level: int, p: int, z, perm, box_start, L, phi, accumulate: bool = False, stream=None):
+    """fmm_l2p at the points z of level `level`, binned by fmm_bin_points (one block per box)."""
+    n = 0 if perm is None else perm.numel()
+    _check(load().fmm_l2p_binned(level, p, _ptr(z), n, _ptr(perm), _ptr(box_start), _ptr(L), _ptr(phi),
+                                 FMM_ACCUMULATE if accumulate else 0, _stream(stream)))
 
 
 def fmm_l2p_adjoint(p: int, z, lev, box, cot, G_levels: dict, max_level: int, stream=None):

@@ -6,8 +6,13 @@ Each step copies its MEs in, translates them and copies the LEs out; with
 ``depth`` device buffer sets and three CUDA streams (host-to-device copies,
 translation, device-to-host copies), step i's translation runs while step i+1's
 MEs are arriving and step i-1's LEs are leaving, so the link's two directions
-and the SMs work at the same time.  A buffer set is reused only after the step
-that last used it has copied its results out (CUDA events order the streams).
+and the SMs work at the same time.  The two halves of a buffer set are released
+separately (CUDA events order the streams): a step's MEs may arrive as soon as
+the translation that last read that ME buffer is done, while its translation
+waits until the LEs last written to its LE buffer have been copied out.  So the
+copy in of step i+1 overlaps the copy out of step i-1, and with two buffer sets
+a step costs the longest of the translation and the two concurrent copies, not
+their sum.
 """
 from __future__ import annotations
 
@@ -69,8 +74,10 @@ class HostStreamM2L:
         """host_in[i], host_out[i]: step i's pinned host MEs and LEs (per-level lists or flat tensors)."""
         for Mh, Lh in zip(host_in, host_out):
             b = self.steps % self.depth
-            if self.steps >= self.depth:  # buffer set b: its previous step has copied its LEs out
-                self.h2d.wait_event(self.returned[b])
+            if self.steps >= self.depth:
+                # set b's MEs were last read by the translation of step steps - depth, its
+                # LEs last copied out by that step's copy out
+                self.h2d.wait_event(self.translated[b])
                 self.comp.wait_event(self.returned[b])
             with torch.cuda.stream(self.h2d):
                 self._copy(self.Mflat[b], self.M[b], Mh)

@@ -128,6 +128,68 @@ def test_l2p_and_adjoint(fmm, orc, p):
     assert _rel(_host(G), ref) <= 1e-5
 
 
+@pytest.mark.parametrize("p", [8, 16])
+def test_l2p_binned_matches_oracle_and_per_point_kernel(fmm, orc, p):
+    """fmm_l2p_binned (one block per box over the binned points) against the oracle's
+    L2P at each point's box and the per-point kernel: points in random order, on box
+    boundaries, at 1.0 and just outside the unit square (clamped boxes)."""
+    import torch
+
+    rng = np.random.default_rng(40 + p)
+    level, npts = 5, 3000
+    side, nb = 1 << level, 4 ** level
+    z = rng.random((npts, 2))
+    k = np.arange(side + 1) / side
+    z[:side + 1, 0] = k
+    z[side + 1:2 * side + 2, 1] = np.nextafter(k, -1.0)
+    z[-3:] = [[1.0, 0.5], [1.004, 0.2], [-0.002, 0.7]]
+    Ls = rng.standard_normal((nb, p)) + 1j * rng.standard_normal((nb, p))
+    zd = torch.from_numpy(z).cuda()
+    perm = torch.empty(npts, dtype=torch.int32, device="cuda")
+    start = torch.empty(nb + 1, dtype=torch.int32, device="cuda")
+    fmm.fmm_bin_points(level, zd, perm, start, torch.empty(nb, dtype=torch.int32, device="cuda"))
+    phi = torch.empty(npts, dtype=torch.complex64, device="cuda")
+    fmm.fmm_l2p_binned(level, p, zd, perm, start, _dev(Ls), phi)
+    fmm.fmm_sync_status()
+    ix = np.clip(np.floor(z[:, 0] * side), 0, side - 1).astype(np.int64)
+    iy = np.clip(np.floor(z[:, 1] * side), 0, side - 1).astype(np.int64)
+    phys = orc.unscale_le(Ls, level)
+    ref = np.array([orc.l2p(p, phys[iy[j] * side + ix[j]], orc.box_centre(level, int(ix[j]), int(iy[j])),
+                            np.array([z[j, 0] + 1j * z[j, 1]]))[0] for j in range(npts)])
+    got = _host(phi)
+    assert _rel(got, ref) <= 1e-6
+    # the per-point kernel on the same boxes
+    phi2 = torch.empty_like(phi)
+    lev = torch.full((npts,), level, dtype=torch.int32, device="cuda")
+    fmm.fmm_l2p(p, zd, lev, torch.from_numpy(iy * side + ix).cuda(), {level: _dev(Ls)}, level, phi2)
+    fmm.fmm_sync_status()
+    assert _rel(got, _host(phi2)) <= 1e-6
+    # accumulate
+    fmm.fmm_l2p_binned(level, p, zd, perm, start, _dev(Ls), phi, accumulate=True)
+    fmm.fmm_sync_status()
+    assert _rel(_host(phi), 2 * ref) <= 1e-6
+
+
+def test_l2p_binned_coarse_levels_and_bad_bins(fmm):
+    """Levels 0 and 1 carry no LEs (phi = 0, L may be None); a box_start that does not bin
+    the points sets the device error word."""
+    import torch
+
+    z = torch.rand((50, 2), dtype=torch.float64, device="cuda")
+    perm = torch.arange(50, dtype=torch.int32, device="cuda")
+    phi = torch.full((50,), 3.0 + 1.0j, dtype=torch.complex64, device="cuda")
+    start = torch.tensor([0, 50], dtype=torch.int32, device="cuda")
+    fmm.fmm_l2p_binned(0, 8, z, perm, start, None, phi)
+    fmm.fmm_sync_status()
+    assert float(phi.abs().max()) == 0.0
+    bad = torch.tensor([0, 10, 5, 20, 50], dtype=torch.int32, device="cuda")  # a box with end < first
+    L1 = torch.zeros((4, 8), dtype=torch.complex64, device="cuda")
+    fmm.fmm_l2p_binned(1, 8, z, perm, bad, L1, phi)
+    with pytest.raises(fmm.FmmError) as e:
+        fmm.fmm_sync_status()
+    assert e.value.code == fmm.FMM_EDEVICE
+
+
 def test_l2p_reports_bad_leaves(fmm, orc):
     import torch
 
