@@ -778,19 +778,22 @@ def run_ours(args):
                     fy = torch.rand((fcfg["n"], 2), dtype=torch.float64, device=dev,
                                     generator=torch.Generator(device=dev).manual_seed(workloads.SEED_BASE + 5))
                     Gy = torch.empty(fcfg["n"], dtype=torch.float32, device=dev)
+                    tperm = torch.empty(fcfg["n"], dtype=torch.int32, device=dev)
+                    tstart = torch.empty(4 ** g + 1, dtype=torch.int32, device=dev)
 
                     def fgt_all():
                         fmmgb.fgt_bin_points(g, fxd, sperm, sstart, swork)
                         fmmgb.fgt_p2h_binned(g, fp, sigma, fxd, fqd, sperm, A)
                         fmmgb.fgt_h2t(g, fcfg["ncut"], fp, sigma, A, Cf, work=W)
-                        fmmgb.fgt_t2p(g, fp, sigma, Cf, fy, Gy)
+                        fmmgb.fgt_bin_points(g, fy, tperm, tstart, swork)
+                        fmmgb.fgt_t2p_binned(g, fp, sigma, Cf, fy, tperm, tstart, Gy)
 
                     ms_all = statistics.median(_timed(torch, _graph(torch, fgt_all), args.steps, stream, flush))
                     rows["fgt_transform_sigma0.05_p16"] = {
                         "ms": ms_all, "sources": int(fcfg["n"]), "targets": int(fcfg["n"]),
-                        "points_per_s": fcfg["n"] / (ms_all * 1e-3), "launches": 7,
-                        "note": "fgt_bin_points (3 kernels), fgt_p2h_binned, fgt_h2t (2 passes), fgt_t2p; "
-                                "uniform targets"}
+                        "points_per_s": fcfg["n"] / (ms_all * 1e-3), "launches": 10,
+                        "note": "fgt_bin_points of the sources (3 kernels), fgt_p2h_binned, fgt_h2t (2 passes), "
+                                "fgt_bin_points of the targets (3 kernels), fgt_t2p_binned; uniform targets"}
                 rows[f"fgt_h2t_sigma{sigma}_p{fp}"] = {
                     "translations_per_s": ntr / (ms * 1e-3), "ms": ms, "launches": 2, "grid": f"{1 << g}^2",
                     "gflops_separable": (4 ** g) * metrics.fgt_flops_per_box_separable(fp, taps, taps)

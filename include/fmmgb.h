@@ -417,6 +417,16 @@ int fgt_p2h(int32_t grid_log2, int32_t p, double sigma, const double* x, const d
 int fgt_t2p(int32_t grid_log2, int32_t p, double sigma, const float* C, const double* y, int64_t n,
             float* G, int32_t flags, void* stream);
 
+/* fgt_t2p_binned: fgt_t2p at targets binned by fgt_bin_points(grid_log2, y, n,
+ *   perm, box_start, ...): one thread block per box holds its p x p coefficients
+ *   in shared memory and evaluates them at the box's targets (a target's offset
+ *   from the box centre read off the bits of its FP64 coordinates).  Same
+ *   arguments as fgt_t2p plus perm, box_start (device int32 [n], [4^g + 1]);
+ *   grid_log2 0..10; C 4-byte aligned.  A perm entry or box start out of range
+ *   sets the device error word's check bit and is skipped. */
+int fgt_t2p_binned(int32_t grid_log2, int32_t p, double sigma, const float* C, const double* y, int64_t n,
+                   const int32_t* perm, const int32_t* box_start, float* G, int32_t flags, void* stream);
+
 /* ---------------------------------------------------------------------------
  * FGT Hermite-series evaluation at targets (Sec. 4.2, Eq. hermite), the
  * paper's own FGT GPU kernel, on the uniform 2^g x 2^g grid:

@@ -138,6 +138,48 @@ __global__ void bin_scatter_kernel(int g, const double* __restrict__ y, int64_t 
     }
 }
 
+// Small grids (up to 4^7 boxes): a block counts its contiguous chunk of points in a
+// shared-memory histogram, so contended boxes (clustered points) cost shared-memory
+// atomics, and the global counters see one addition per box a block touches.
+constexpr int kBinSmemMaxLog2 = 7;
+
+__global__ void __launch_bounds__(kBinThreads) bin_count_smem_kernel(int g, const double* __restrict__ y, int64_t n,
+                                                                     int64_t chunk, int* __restrict__ counts)
+{
+    extern __shared__ int s_cnt[];
+    const int nbox = 1 << (2 * g);
+    for (int b = threadIdx.x; b < nbox; b += kBinThreads) s_cnt[b] = 0;
+    __syncthreads();
+    const int64_t i0 = (int64_t)blockIdx.x * chunk, i1 = i0 + chunk < n ? i0 + chunk : n;
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += kBinThreads)
+        atomicAdd(&s_cnt[fgt_grid_box(__ldg(y + 2 * i), __ldg(y + 2 * i + 1), g)], 1);
+    __syncthreads();
+    for (int b = threadIdx.x; b < nbox; b += kBinThreads)
+        if (s_cnt[b]) atomicAdd(&counts[b], s_cnt[b]);
+}
+
+// The scatter over the same kind of chunks: recount the chunk, reserve each
+// touched box's range with one global atomic, then place the points with
+// shared-memory atomics.
+__global__ void __launch_bounds__(kBinThreads) bin_scatter_smem_kernel(int g, const double* __restrict__ y, int64_t n,
+                                                                       int64_t chunk, int* __restrict__ cursor,
+                                                                       int* __restrict__ perm)
+{
+    extern __shared__ int s_cnt[];
+    const int nbox = 1 << (2 * g);
+    for (int b = threadIdx.x; b < nbox; b += kBinThreads) s_cnt[b] = 0;
+    __syncthreads();
+    const int64_t i0 = (int64_t)blockIdx.x * chunk, i1 = i0 + chunk < n ? i0 + chunk : n;
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += kBinThreads)
+        atomicAdd(&s_cnt[fgt_grid_box(__ldg(y + 2 * i), __ldg(y + 2 * i + 1), g)], 1);
+    __syncthreads();
+    for (int b = threadIdx.x; b < nbox; b += kBinThreads)
+        if (s_cnt[b]) s_cnt[b] = atomicAdd(&cursor[b], s_cnt[b]);  // this block's first slot in box b
+    __syncthreads();
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += kBinThreads)
+        perm[atomicAdd(&s_cnt[fgt_grid_box(__ldg(y + 2 * i), __ldg(y + 2 * i + 1), g)], 1)] = (int)i;
+}
+
 static int bin_grid(int64_t n)
 {
     int sms = 0;
@@ -506,14 +548,34 @@ extern "C" int fgt_bin_points(int32_t grid_log2, const double* y, int64_t n, int
         return fail(FMM_EINVAL, "fgt_bin_points: work overlaps box_start");
     cudaStream_t st = (cudaStream_t)stream;
     FMM_CUDA_TRY(cudaMemsetAsync(work, 0, sizeof(int) * (size_t)nbox, st));
+    const bool smem = grid_log2 <= kBinSmemMaxLog2;
+    const int smem_bytes = smem ? (int)sizeof(int) * nbox : 0;
+    int grid = bin_grid(n);
+    int64_t chunk = 0;
+    if (smem && n > 0) {
+        static unsigned opted[2];  // opted in once per device, for the largest such grid
+        constexpr int kMaxBytes = (int)sizeof(int) << (2 * kBinSmemMaxLog2);
+        if (int rc = smem_opt_in((const void*)bin_count_smem_kernel, kMaxBytes, &opted[0])) return rc;
+        if (int rc = smem_opt_in((const void*)bin_scatter_smem_kernel, kMaxBytes, &opted[1])) return rc;
+        int sms = 0;
+        if (device_sm_count(&sms) || sms <= 0) sms = 148;
+        grid = (int)std::min<int64_t>(2LL * sms, (n + kBinThreads - 1) / kBinThreads);
+        chunk = (n + grid - 1) / grid;
+    }
     if (n > 0) {
-        bin_count_kernel<<<bin_grid(n), kBinThreads, 0, st>>>(grid_log2, y, n, work);
+        if (smem)
+            bin_count_smem_kernel<<<grid, kBinThreads, smem_bytes, st>>>(grid_log2, y, n, chunk, work);
+        else
+            bin_count_kernel<<<grid, kBinThreads, 0, st>>>(grid_log2, y, n, work);
         FMM_CUDA_TRY(cudaGetLastError());
     }
     bin_scan_kernel<<<1, kScanThreads, 0, st>>>(nbox, work, box_start);
     FMM_CUDA_TRY(cudaGetLastError());
     if (n > 0) {
-        bin_scatter_kernel<<<bin_grid(n), kBinThreads, 0, st>>>(grid_log2, y, n, work, perm);
+        if (smem)
+            bin_scatter_smem_kernel<<<grid, kBinThreads, smem_bytes, st>>>(grid_log2, y, n, chunk, work, perm);
+        else
+            bin_scatter_kernel<<<grid, kBinThreads, 0, st>>>(grid_log2, y, n, work, perm);
         FMM_CUDA_TRY(cudaGetLastError());
     }
     return FMM_OK;

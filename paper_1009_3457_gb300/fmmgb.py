@@ -111,6 +111,7 @@ SIGNATURES = {
     "fmm_m2l_paper_design": (ctypes.c_int, [_vp, _i32, _i32, _vp, _vp, _vp, _i32, _vp]),
     "fmm_p2m_binned": (ctypes.c_int, [_i32, _i32, _vp, _vp, _i64, _vp, _vp, _vp, _i32, _vp]),
     "fmm_l2p_binned": (ctypes.c_int, [_i32, _i32, _vp, _i64, _vp, _vp, _vp, _vp, _i32, _vp]),
+    "fgt_t2p_binned": (ctypes.c_int, [_i32, _i32, ctypes.c_double, _vp, _vp, _i64, _vp, _vp, _vp, _i32, _vp]),
     "fmm_p2p": (ctypes.c_int, [_i32, _vp, _vp, _i64, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _i32, _vp]),
     "fgt_p2h_binned": (ctypes.c_int, [_i32, _i32, _d, _vp, _vp, _i64, _vp, _vp, _i32, _vp]),
     "fgt_h2p": (ctypes.c_int, [_i32, _i32, _i32, _i32, _d, _vp, _vp, _i64, _vp, _vp, _vp, _i32, _vp]),
@@ -401,6 +402,14 @@ def fgt_t2p(grid_log2: int, p: int, sigma: float, C, y, G, accumulate: bool = Fa
     n = 0 if G is None else G.numel()
     _check(load().fgt_t2p(grid_log2, p, float(sigma), _ptr(C), _ptr(y), n, _ptr(G),
                           FMM_ACCUMULATE if accumulate else 0, _stream(stream)))
+
+
+def fgt_t2p_binned(grid_log2: int, p: int, sigma: float, C, y, perm, box_start, G, accumulate: bool = False,
+                   stream=None):
+    """fgt_t2p at targets binned by fgt_bin_points (one block per box, coefficients in shared memory)."""
+    n = 0 if perm is None else perm.numel()
+    _check(load().fgt_t2p_binned(grid_log2, p, float(sigma), _ptr(C), _ptr(y), n, _ptr(perm), _ptr(box_start),
+                                 _ptr(G), FMM_ACCUMULATE if accumulate else 0, _stream(stream)))
 
 
 def fgt_bin_points(grid_log2: int, y, perm, box_start, work, stream=None):

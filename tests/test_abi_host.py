@@ -261,6 +261,13 @@ def test_p2p_rejects_bad_arguments(fmm):
     assert lib.fmm_l2p_binned(3, 8, 68, 10, 128, 256, 512, 1024, 0, None) == fmm.FMM_EINVAL    # z misaligned
     assert lib.fmm_l2p_binned(3, 8, 64, 10, 128, 256, 512, 1024, 2, None) == fmm.FMM_EINVAL    # flags
     assert lib.fmm_l2p_binned(3, 8, 64, 0, None, 256, None, None, 0, None) == fmm.FMM_OK       # nothing to do
+    # fgt_t2p_binned(g, p, sigma, C, y, n, perm, box_start, G, flags, stream)
+    assert lib.fgt_t2p_binned(11, 8, 0.1, 64, 128, 10, 256, 512, 1024, 0, None) == fmm.FMM_EINVAL   # grid
+    assert lib.fgt_t2p_binned(3, 6, 0.1, 64, 128, 10, 256, 512, 1024, 0, None) == fmm.FMM_EINVAL    # p
+    assert lib.fgt_t2p_binned(3, 8, 0.0, 64, 128, 10, 256, 512, 1024, 0, None) == fmm.FMM_EINVAL    # sigma
+    assert lib.fgt_t2p_binned(3, 8, 0.1, 64, 128, 10, None, 512, 1024, 0, None) == fmm.FMM_EINVAL   # perm
+    assert lib.fgt_t2p_binned(3, 8, 0.1, 64, 132, 10, 256, 512, 1024, 0, None) == fmm.FMM_EINVAL    # y misaligned
+    assert lib.fgt_t2p_binned(3, 8, 0.1, 64, 128, 10, 256, 512, 1024, 4, None) == fmm.FMM_EINVAL    # flags
 
 
 def test_paper_design_rejects_bad_arguments(fmm):

@@ -161,6 +161,41 @@ def test_fgt_t2p_matches_oracle(fmm, orc, p):
     assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 1e-6
 
 
+@pytest.mark.parametrize("p", [4, 8, 12, 16])
+def test_fgt_t2p_binned_matches_oracle_and_per_target_kernel(fmm, orc, p):
+    """fgt_t2p_binned (targets binned by fgt_bin_points, one block per box) against the
+    oracle's evaluation and fgt_t2p, with targets on and next to box boundaries and just
+    outside the unit square; accumulate."""
+    import torch
+
+    rng = np.random.default_rng(80 + p)
+    g, n = 4, 3000
+    C = rng.standard_normal((4 ** g, p, p)) / (1.0 + np.add.outer(np.arange(p), np.arange(p)))[None]
+    y = rng.random((n, 2))
+    k = np.arange(17) / 16
+    edge = np.concatenate([k, np.nextafter(k, -1.0), np.nextafter(k, 2.0), [1 - 2.0 ** -53, 1.01, -0.01, 0.0]])
+    y[:len(edge), 0] = edge
+    y[len(edge):2 * len(edge), 1] = edge
+    yd = torch.from_numpy(y).cuda()
+    perm = torch.empty(n, dtype=torch.int32, device="cuda")
+    start = torch.empty(4 ** g + 1, dtype=torch.int32, device="cuda")
+    fmm.fgt_bin_points(g, yd, perm, start, torch.empty(4 ** g, dtype=torch.int32, device="cuda"))
+    G = torch.empty(n, dtype=torch.float32, device="cuda")
+    Cd = _dev(C)
+    fmm.fgt_t2p_binned(g, p, 0.1, Cd, yd, perm, start, G)
+    fmm.fmm_sync_status()
+    ref = orc.fgt_taylor_eval_grid(g, p, 0.1, C, y)
+    got = G.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 1e-6
+    G2 = torch.empty_like(G)
+    fmm.fgt_t2p(g, p, 0.1, Cd, yd, G2)
+    fmm.fmm_sync_status()
+    assert np.linalg.norm(got - G2.cpu().numpy()) / np.linalg.norm(ref) <= 1e-6
+    fmm.fgt_t2p_binned(g, p, 0.1, Cd, yd, perm, start, G, accumulate=True)
+    fmm.fmm_sync_status()
+    assert np.linalg.norm(G.cpu().numpy() - 2 * ref) / np.linalg.norm(2 * ref) <= 1e-6
+
+
 @pytest.mark.parametrize("sigma,p", [(0.1, 8), (0.05, 12), (0.2, 16)])
 def test_fgt_whole_transform_on_device(fmm, orc, sigma, p):
     """fgt_p2h -> fgt_h2t -> fgt_t2p on the device against the oracle's pipeline
