@@ -94,22 +94,85 @@ __device__ __forceinline__ float rcp_approx(float x)
     return r;
 }
 
+// Packed two-lane FP32 (PTX f32x2): two targets of a lane in one 64-bit register pair.
+__device__ __forceinline__ unsigned long long p2_pk(float a, float b)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float2 p2_upk(unsigned long long v)
+{
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+    return r;
+}
+__device__ __forceinline__ unsigned long long p2_sub(unsigned long long a, unsigned long long b)
+{
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ unsigned long long p2_mul(unsigned long long a, unsigned long long b)
+{
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ unsigned long long p2_fma(unsigned long long a, unsigned long long b, unsigned long long c)
+{
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
 // One warp's share of a staged batch (sources warp, warp + 4, ...) against the
 // claim's NR occupied rows of 32 targets (NR warp-uniform: empty rows cost nothing).
+// Rows 0 and 1 run as one packed pair (dx, dy, r^2, the weight and both sums in
+// f32x2 operations; the two reciprocals stay scalar), row 2 alone.
 template <int NR>
 __device__ __forceinline__ void p2p_batch(const float4* __restrict__ s_src, int cnt, int warp, const float* zx,
                                           const float* zy, float* re, float* im)
 {
+    if constexpr (NR >= 2) {
+        const unsigned long long zx01 = p2_pk(zx[0], zx[1]), zy01 = p2_pk(zy[0], zy[1]);
+        const unsigned long long tiny = p2_pk(kP2pTiny, kP2pTiny);
+        unsigned long long re01 = p2_pk(re[0], re[1]), im01 = p2_pk(-im[0], -im[1]);  // im01 sums +w dy
+        float re2 = NR > 2 ? re[2] : 0.f, im2 = NR > 2 ? im[2] : 0.f;
 #pragma unroll 4
-    for (int i = warp; i < cnt; i += kP2pWarps) {
-        const float4 v = s_src[i];
-#pragma unroll
-        for (int r = 0; r < NR; ++r) {
-            const float dx = zx[r] - v.x, dy = zy[r] - v.y;
+        for (int i = warp; i < cnt; i += kP2pWarps) {
+            const float4 v = s_src[i];
+            const unsigned long long dx = p2_sub(zx01, p2_pk(v.x, v.x)), dy = p2_sub(zy01, p2_pk(v.y, v.y));
+            const float2 r2 = p2_upk(p2_fma(dx, dx, p2_fma(dy, dy, tiny)));
+            const unsigned long long w = p2_mul(p2_pk(v.z, v.z), p2_pk(rcp_approx(r2.x), rcp_approx(r2.y)));
+            re01 = p2_fma(w, dx, re01);
+            im01 = p2_fma(w, dy, im01);
+            if constexpr (NR > 2) {
+                const float ex = zx[2] - v.x, ey = zy[2] - v.y;
+                const float q2 = fmaf(ex, ex, fmaf(ey, ey, kP2pTiny));
+                const float u = v.z * rcp_approx(q2);
+                re2 = fmaf(u, ex, re2);
+                im2 = fmaf(-u, ey, im2);
+            }
+        }
+        const float2 a = p2_upk(re01), b = p2_upk(im01);
+        re[0] = a.x;
+        re[1] = a.y;
+        im[0] = -b.x;
+        im[1] = -b.y;
+        if constexpr (NR > 2) {
+            re[2] = re2;
+            im[2] = im2;
+        }
+    } else {
+#pragma unroll 4
+        for (int i = warp; i < cnt; i += kP2pWarps) {
+            const float4 v = s_src[i];
+            const float dx = zx[0] - v.x, dy = zy[0] - v.y;
             const float r2 = fmaf(dx, dx, fmaf(dy, dy, kP2pTiny));
             const float w = v.z * rcp_approx(r2);
-            re[r] = fmaf(w, dx, re[r]);
-            im[r] = fmaf(-w, dy, im[r]);
+            re[0] = fmaf(w, dx, re[0]);
+            im[0] = fmaf(-w, dy, im[0]);
         }
     }
 }
