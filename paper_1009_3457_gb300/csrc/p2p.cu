@@ -139,7 +139,7 @@ __device__ __forceinline__ void p2p_batch(const float4* __restrict__ s_src, int 
         const unsigned long long tiny = p2_pk(kP2pTiny, kP2pTiny);
         unsigned long long re01 = p2_pk(re[0], re[1]), im01 = p2_pk(-im[0], -im[1]);  // im01 sums +w dy
         float re2 = NR > 2 ? re[2] : 0.f, im2 = NR > 2 ? im[2] : 0.f;
-#pragma unroll 4
+#pragma unroll 8
         for (int i = warp; i < cnt; i += kP2pWarps) {
             const float4 v = s_src[i];
             const unsigned long long dx = p2_sub(zx01, p2_pk(v.x, v.x)), dy = p2_sub(zy01, p2_pk(v.y, v.y));
