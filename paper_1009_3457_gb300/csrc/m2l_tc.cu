@@ -179,6 +179,8 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, i
 template <int P>
 __global__ void me_planes_kernel(M2LLaunch job, int split)
 {
+    // one thread per 16-byte unit of a plane row, consecutive threads along qx: the
+    // stores are coalesced, each thread reads one 32-byte chunk of one box
     using C = TcCfg<P>;
     int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int li = 0;
@@ -190,10 +192,12 @@ __global__ void me_planes_kernel(M2LLaunch job, int split)
     if (li >= job.nlev) return;
     const M2LLevel& lv = job.lv[li];
     const int side = 1 << lv.level, np = side >> 1;
-    const int ch = (int)(idx % C::KCH);
-    const int64_t box = idx / C::KCH;
-    const int ix = (int)(box % side), iy = (int)(box / side);
-    const float4* src = reinterpret_cast<const float4*>(lv.M) + box * (P / 2) + 2 * ch;
+    const int qx = (int)(idx % np);
+    const int64_t t = idx / np;
+    const int qy = (int)(t % np), cc = (int)(t / np);  // cc = class * KCH + chunk
+    const int c = cc / C::KCH, ch = cc % C::KCH;
+    const int ix = 2 * qx + (c & 1), iy = 2 * qy + (c >> 1);
+    const float4* src = reinterpret_cast<const float4*>(lv.M) + ((int64_t)iy * side + ix) * (P / 2) + 2 * ch;
     const float4 v0 = __ldg(src), v1 = __ldg(src + 1);
     const float f[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
     uint32_t h[4], l[4];
@@ -204,9 +208,8 @@ __global__ void me_planes_kernel(M2LLaunch job, int split)
         h[j] = *reinterpret_cast<uint32_t*>(&hv);
         l[j] = pack_bf16(f[2 * j] - hf.x, f[2 * j + 1] - hf.y);
     }
-    const int cc = ((ix & 1) + 2 * (iy & 1)) * C::KCH + ch;
     const size_t row = (size_t)np * 16;  // one (cc, qy, part) row of np positions
-    const size_t off = ((size_t)cc * np + (iy >> 1)) * 2 * row + (size_t)(ix >> 1) * 16;
+    const size_t off = ((size_t)cc * np + qy) * 2 * row + (size_t)qx * 16;
     *reinterpret_cast<uint4*>(lv.planes + off) = make_uint4(h[0], h[1], h[2], h[3]);
     *reinterpret_cast<uint4*>(lv.planes + off + row) = make_uint4(l[0], l[1], l[2], l[3]);
     (void)split;
