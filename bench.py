@@ -13,7 +13,7 @@ in HBM; `e2e` is the same metric with a pinned-host -> device copy of the
 step's MEs and a device -> host copy of its LEs inside the timed region
 (pipeline.HostStreamM2L: consecutive steps overlap on three streams).
 Under torchrun each rank runs an independent replica of the workload (the
-single-tree M2L step has no cross-GPU exchange in this build: replicas only).
+single-tree M2L step has no cross-GPU exchange: replicas only).
 """
 from __future__ import annotations
 

@@ -53,7 +53,7 @@ typedef enum {
     FMM_ENOMEM = -2,        /* device or host allocation failed */
     FMM_ECUDA = -3,         /* a CUDA runtime call failed */
     FMM_ETIMEOUT = -4,      /* a bounded device-side wait gave up */
-    FMM_EUNSUPPORTED = -5,  /* valid request this build does not implement */
+    FMM_EUNSUPPORTED = -5,  /* valid request the library does not implement */
     FMM_EDEVICE = -6        /* a device-side check failed (see fmm_last_error) */
 } fmm_status;
 
