@@ -419,9 +419,9 @@ int fgt_t2p(int32_t grid_log2, int32_t p, double sigma, const float* C, const do
 
 /* fgt_t2p_binned: fgt_t2p (Sec. 2.2, Eq. taylor) at targets binned by
  *   fgt_bin_points(grid_log2, y, n, perm, box_start, ...): one thread block per
- *   box holds its p x p coefficients
- *   in shared memory and evaluates them at the box's targets (a target's offset
- *   from the box centre read off the bits of its FP64 coordinates).  Same
+ *   box holds its p x p coefficients in shared memory and evaluates them at the
+ *   box's targets (a target's offset from the box centre read off the bits of
+ *   its FP64 coordinates).  Same
  *   arguments as fgt_t2p plus perm, box_start (device int32 [n], [4^g + 1]);
  *   grid_log2 0..10; C 4-byte aligned.  A perm entry or box start out of range
  *   sets the device error word's check bit and is skipped. */
