@@ -10,6 +10,9 @@ of them:
 * M2L: the exact Taylor coefficients of the Cauchy kernel (closed form),
   convergence of the far-field potential to the direct sum (Eq. n_body) at a
   geometric rate, and M2M-then-M2L consistency;
+* M2P: the exact potential of a centred source, one power per coefficient, a
+  cluster's ME converging to the direct sum within the geometric tail bound, and
+  agreement with L2P(M2L(.)) as p grows;
 * adjoint: the bilinear dot-product identity.
 """
 import math
@@ -162,6 +165,77 @@ def test_m2l_converges_to_exact_taylor_coefficients(orc):
         nchk = 8
         expect = np.array([(-1) ** n * c / (d - e) ** (n + 1) for n in range(nchk)])
         np.testing.assert_allclose(l[:nchk], expect, rtol=1e-11)
+
+
+def test_m2p_centred_source_is_exact(orc):
+    """M2P of the ME (c, 0, ..., 0) about x_s is c/(z - x_s) exactly, at any p
+    (Sec. 2.1: the ME of one source at the box centre)."""
+    cs = 0.3 + 0.6j
+    c = -0.8 + 0.1j
+    rng = np.random.default_rng(19)
+    z = cs + (rng.random(16) - 0.5) * 4 + 1j * (rng.random(16) - 0.5) * 4
+    for p in (1, 5, 16):
+        m = np.zeros(p, complex)
+        m[0] = c
+        np.testing.assert_allclose(orc.m2p(p, m, cs, z), c / (z - cs), rtol=1e-15, atol=0)
+
+
+def test_m2p_single_term_powers(orc):
+    """The k-th coefficient multiplies (z - x_s)^-(k+1): a unit ME in slot k alone
+    gives exactly that power, so a shifted or dropped index fails."""
+    cs = -0.25 + 0.5j
+    z = np.array([1.5 + 0.25j, -2.0 - 1.0j, 0.75 + 3.0j])
+    p = 9
+    for k in range(p):
+        m = np.zeros(p, complex)
+        m[k] = 1.0
+        np.testing.assert_allclose(orc.m2p(p, m, cs, z), (z - cs) ** -(k + 1), rtol=1e-14, atol=0)
+
+
+def test_m2p_of_cluster_converges_to_direct_sum(orc):
+    """The ME of a box's sources (P2M), evaluated two or more box sides away, tends
+    to the direct sum (Eq. n_body) geometrically: the error of p terms is at most
+    sum|c| rho^p / (|z - x_s| (1 - rho)) with rho = (side/sqrt 2) / |z - x_s|."""
+    rng = np.random.default_rng(23)
+    side = 0.125
+    cs = 0.4375 + 0.5625j
+    xy = np.column_stack([cs.real + (rng.random(200) - 0.5) * side,
+                          cs.imag + (rng.random(200) - 0.5) * side])
+    c = rng.uniform(-1, 1, 200)
+    ang = rng.random(32) * 2 * np.pi
+    rad = side * (2.0 + 2.0 * rng.random(32))
+    z = cs + rad * np.exp(1j * ang)
+    exact = orc.direct(xy, c, z)
+    prev = np.inf
+    for p in (2, 4, 8, 12, 16, 24, 32):
+        got = orc.m2p(p, orc.p2m_box(xy, c, cs, p), cs, z)
+        rho = (side / np.sqrt(2)) / np.abs(z - cs)
+        bound = np.abs(c).sum() * rho ** p / (np.abs(z - cs) * (1 - rho))
+        err = np.abs(got - exact)
+        assert np.all(err <= bound * (1 + 1e-9) + 1e-13)
+        e = np.linalg.norm(err)
+        assert e < prev or e < 1e-13
+        prev = e
+    assert prev < 1e-11 * np.linalg.norm(exact)
+
+
+def test_m2p_equals_l2p_of_m2l_in_the_limit(orc):
+    """Evaluating the ME directly at points of a well-separated target box equals
+    L2P(M2L(ME)) there as p grows (Eq. M2Lmat is the re-expansion of M2P)."""
+    rng = np.random.default_rng(29)
+    m = rng.normal(size=12) + 1j * rng.normal(size=12)
+    m *= 0.5 ** np.arange(12)
+    cs, ct = 0.0 + 0.0j, 2.0 + 1.0j
+    z = ct + (rng.random(8) - 0.5) * 0.5 + 1j * (rng.random(8) - 0.5) * 0.5
+    direct = orc.m2p(12, m, cs, z)
+    errs = []
+    for p in (12, 20, 28, 32):
+        mp = np.zeros(p, complex)
+        mp[:12] = m
+        le = orc.m2l_pair(p, ct - cs, mp)
+        errs.append(np.max(np.abs(orc.l2p(p, le, ct, z) - direct) / np.abs(direct)))
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[-1] < 1e-13
 
 
 def test_m2m_then_m2l_equals_parent_p2m(orc):
