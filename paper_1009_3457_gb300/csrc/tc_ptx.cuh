@@ -8,7 +8,8 @@
 
 namespace fmmgb {
 
-constexpr uint32_t kWaitCap = 1u << 22;  // bounded mbarrier waits
+constexpr uint32_t kWaitCap = 1u << 22;  // polls of a bounded mbarrier wait (sleeping form)
+constexpr uint32_t kSpinCap = kWaitCap << 6;  // polls of a bounded spin (non-sleeping form)
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -24,9 +25,11 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes)
 
 // Bounded wait that yields the issue slot between polls (for warps that are
 // not on the critical path: they share an SM sub-partition with the MMA warp).
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, uint32_t sleep_ns = 64)
+// Gives up (returns false) after `cap` polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, uint32_t sleep_ns = 64,
+                                          uint32_t cap = kWaitCap)
 {
-    for (uint32_t it = 0; it < kWaitCap; ++it) {
+    for (uint32_t it = 0; it < cap; ++it) {
         if (it) __nanosleep(sleep_ns);
         uint32_t ok;
         asm volatile(
@@ -40,10 +43,10 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, uint32_t
 }
 
 // Spin on a non-blocking test (a single issuing thread; a blocking try_wait
-// that finds the phase complete still costs ~150 cycles).
-__device__ __forceinline__ bool mbar_spin(uint64_t* b, uint32_t parity)
+// that finds the phase complete still costs ~150 cycles).  Gives up after `cap` polls.
+__device__ __forceinline__ bool mbar_spin(uint64_t* b, uint32_t parity, uint32_t cap = kSpinCap)
 {
-    for (uint32_t it = 0; it < (kWaitCap << 6); ++it) {
+    for (uint32_t it = 0; it < cap; ++it) {
         uint32_t ok;
         asm volatile(
             "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
