@@ -258,7 +258,7 @@ static int fgt_launch(int g, int ncut, double ustep, const float* A, float* Y, f
     using C = FgtCfg<P>;
     const int side = 1 << g;
     const size_t smem = fgt_smem_bytes<P>(ncut);
-    static unsigned opted;  // opted in once for the largest neighbourhood, so every n_cut fits
+    static unsigned long long opted;  // opted in once for the largest neighbourhood, so every n_cut fits
     if (int rc = smem_opt_in((const void*)fgt_pass_kernel<P>, (int)fgt_smem_bytes<P>(kFgtMaxCut), &opted)) return rc;
     const float* htab = nullptr;
     if (cached_table)
@@ -334,6 +334,8 @@ extern "C" int fgt_h2t_noalloc(int32_t grid_log2, int32_t n_cut, int32_t p, doub
                     grid_log2, grid_log2, p, need, kFgtStaticScratchFloats, kFgtStaticScratchFloats);
     float* Y = nullptr;
     if ((rc = static_scratch(&Y))) return rc;
+    // A or C inside the built-in array would be overwritten by the first pass
+    if ((rc = fgt_check_args("fgt_h2t_noalloc", grid_log2, n_cut, p, sigma, A, C, Y, flags))) return rc;
     // The first pass writes every element of Y before the second pass reads
     // it, so the scratch needs no clearing between calls.
     return launch_fgt_h2t(grid_log2, n_cut, p, sigma, A, Y, C, (flags & FMM_ACCUMULATE) != 0, false,
