@@ -124,11 +124,12 @@ int device_sm_count(int* out)
     return FMM_OK;
 }
 
-int smem_opt_in(const void* func, int bytes, unsigned* done)
+int smem_opt_in(const void* func, int bytes, unsigned long long* done)
 {
     int dev = 0;
     FMM_CUDA_TRY(cudaGetDevice(&dev));
-    const unsigned bit = 1u << (dev & 31);
+    if (dev < 0 || dev >= 64) return fail(FMM_EUNSUPPORTED, "device ordinal %d above 63", dev);
+    const unsigned long long bit = 1ull << dev;
     if (__atomic_load_n(done, __ATOMIC_ACQUIRE) & bit) return FMM_OK;
     FMM_CUDA_TRY(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     __atomic_fetch_or(done, bit, __ATOMIC_RELEASE);

@@ -69,10 +69,11 @@ __device__ __forceinline__ float cell_offset31(long long X)
 int device_sm_count(int* out);
 
 // Opt `func` into `bytes` of dynamic shared memory on the current device,
-// once per device (`done` is a per-kernel bitmask of devices): the attribute
+// once per device (`done` is a per-kernel bitmask of device ordinals 0..63;
+// higher ordinals are refused with FMM_EUNSUPPORTED): the attribute
 // persists, so later launches, including those inside a stream capture,
 // make no runtime call besides the launch itself.
-int smem_opt_in(const void* func, int bytes, unsigned* done);
+int smem_opt_in(const void* func, int bytes, unsigned long long* done);
 
 // A work counter for one persistent launch: a slot of two ints (claimed
 // work, CTAs finished) from a per-device ring of 256, zero when allocated.

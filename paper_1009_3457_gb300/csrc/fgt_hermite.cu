@@ -506,7 +506,7 @@ template <int P>
 static int h2p_launch(const H2pArgs& args, cudaStream_t st)
 {
     using C = H2pCfg<P>;
-    static unsigned opted;
+    static unsigned long long opted;
     static int occ;
     static std::mutex mu;
     if (int rc = smem_opt_in((const void*)fgt_h2p_kernel<P>, (int)C::smem, &opted)) return rc;
@@ -553,7 +553,7 @@ extern "C" int fgt_bin_points(int32_t grid_log2, const double* y, int64_t n, int
     int grid = bin_grid(n);
     int64_t chunk = 0;
     if (smem && n > 0) {
-        static unsigned opted[2];  // opted in once per device, for the largest such grid
+        static unsigned long long opted[2];  // opted in once per device, for the largest such grid
         constexpr int kMaxBytes = (int)sizeof(int) << (2 * kBinSmemMaxLog2);
         if (int rc = smem_opt_in((const void*)bin_count_smem_kernel, kMaxBytes, &opted[0])) return rc;
         if (int rc = smem_opt_in((const void*)bin_scatter_smem_kernel, kMaxBytes, &opted[1])) return rc;

@@ -455,7 +455,7 @@ int launch_fgt_h2p_tc(int g, int ncut, double d, bool split, const float* A, con
     const int64_t elems = (int64_t)nbox * 256;
     fgt_tc_image_kernel<<<(unsigned)((elems + 255) / 256), 256, 0, st>>>(A, nbox, img);
     FMM_CUDA_TRY(cudaGetLastError());
-    static unsigned opted;
+    static unsigned long long opted;
     if (int rc = smem_opt_in((const void*)fgt_h2p_tc_kernel, kTcSmemCap, &opted)) return rc;
     // as many stages as fit, released in groups of 3 (2 when fewer than 6 fit, 4 when 8 fit)
     const int stages = std::min(kTcMaxStages, (kTcSmemCap - tc_bar_bytes()) / tc_stage_bytes(ncut));

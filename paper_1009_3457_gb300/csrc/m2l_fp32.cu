@@ -80,7 +80,7 @@ static int launch_p(M2LLaunch& job, const float2* h, const float* a, const float
     int sms = 0, occ = 0;
     int rc = device_sm_count(&sms);
     if (rc) return rc;
-    static unsigned opted[2];
+    static unsigned long long opted[2];
     if ((rc = smem_opt_in((const void*)kern, (int)C::smem, &opted[adaptive]))) return rc;
     static int occ_cache[2];  // resident CTAs per SM (same on every device of one model)
     if (!(occ = __atomic_load_n(&occ_cache[adaptive], __ATOMIC_ACQUIRE))) {

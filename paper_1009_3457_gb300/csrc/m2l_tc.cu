@@ -602,7 +602,7 @@ static int launch_tc_p(M2LLaunch& job, const void* img, bool split, int* err, cu
         if (r != CUDA_SUCCESS) return fail(FMM_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
         maps.use_tma[i] = 1;
     }
-    static unsigned opted;
+    static unsigned long long opted;
     if ((rc = smem_opt_in((const void*)m2l_tc_kernel<P>, (int)C::smem, &opted))) return rc;
     const int grid = total < sms ? total : sms;
     m2l_tc_kernel<P><<<grid, kTcCtaThreads, C::smem, st>>>(job, maps, (const unsigned char*)img, split ? 1 : 0, total,
