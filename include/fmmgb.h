@@ -290,25 +290,27 @@ int fgt_h2t(int32_t grid_log2, int32_t n_cut, int32_t p, double sigma, const flo
 /* ---------------------------------------------------------------------------
  * fgt_h2t_noalloc -- fgt_h2t that never allocates device memory.
  *
- * The paper has no counterpart: this entry point exists for callers that
- * cannot call cudaMalloc -- for example code that runs while a CUDA graph is
- * being captured, under a caching allocator that owns all of the device's
- * memory, or in a latency-critical loop where an allocation (which may
- * synchronise the device) is not acceptable -- and that cannot pass a `work`
- * buffer either.  The intermediate of the two passes lives in a fixed
- * 1 MiB array compiled into the library: 4^g * p^2 must not exceed 262,144
- * floats (for example grids up to 32 x 32 boxes at p = 16, 64 x 64 at
- * p = 8); larger requests are rejected with FMM_EINVAL and a message, and
- * fgt_h2t serves them.  Every GPU that loads the library keeps that array
- * for the life of the process.
+ * The paper has no counterpart.  Some callers cannot call cudaMalloc and
+ * cannot hand the library a `work` buffer either: a host application whose
+ * caching allocator or fixed memory pool owns all of the device's memory, a
+ * plugin that is not allowed to allocate behind its host's back, or a
+ * latency-critical loop in which an allocation (which may synchronise the
+ * whole device) is not acceptable.  For them the intermediate of the two
+ * passes lives in a fixed 1 MiB array compiled into the library:
+ * 4^g * p^2 must not exceed 262,144 floats (for example grids up to 32 x 32
+ * boxes at p = 16, 64 x 64 at p = 8); larger requests are rejected with
+ * FMM_EINVAL and a message, and fgt_h2t serves them.  Every GPU that loads the
+ * library keeps that array for the life of the process.
  *
- * Arguments and results are those of fgt_h2t without `work`.  The first call
- * on a device looks up the array's device address once (no allocation); make
- * that first call before any stream capture.  All calls share the one array
- * and each overwrites it completely before reading it, so nothing needs
- * clearing; calls that overlap on the GPU (different streams, or a graph
- * replay running beside another call) race on it and must be serialised by
- * the caller.
+ * Arguments and results are those of fgt_h2t without `work`; A and C must not
+ * lie inside the built-in array (FMM_EINVAL).  Set-up on first use, none of it
+ * an allocation: the first call on a device looks up the array's device
+ * address, and the first call of each p on a device sets that kernel's
+ * shared-memory limit.  Make those first calls before any stream capture.
+ * All calls share the one array and each overwrites it completely before
+ * reading it, so nothing needs clearing; calls that overlap on the GPU
+ * (different streams, or a graph replay running beside another call) race on
+ * it and must be serialised by the caller.
  * ------------------------------------------------------------------------- */
 int fgt_h2t_noalloc(int32_t grid_log2, int32_t n_cut, int32_t p, double sigma, const float* A, float* C,
                     int32_t flags, void* stream);
@@ -350,6 +352,21 @@ int fmm_m2m_adjoint(int32_t child_level, int32_t p, const void* Wp, void* Wc, in
  * ------------------------------------------------------------------------- */
 int fmm_l2l(int32_t child_level, int32_t p, const void* Lp, void* Lc, int32_t flags, void* stream);
 int fmm_l2l_adjoint(int32_t child_level, int32_t p, const void* Wc, void* Wp, int32_t flags, void* stream);
+
+/* fmm_leaf_boxes: for each of n points, the deepest existing box of `tree`
+ *   that contains it (the leaf a point's far field is evaluated from, Sec. 2.1
+ *   stage 4): level[j] = the largest l <= max_level whose box
+ *   (floor(x 2^l), floor(y 2^l)), each clamped to 0..2^l - 1 (a point goes to
+ *   box floor(x 2^l), reading of Sec. 2.1), exists; box[j] = iy * 2^l + ix.
+ *   Every box exists on a uniform tree, so there level[j] = max_level.
+ *   Coordinates are read exactly (no rounding); a NaN coordinate goes to
+ *   cell 0.  xy: device float64 [n][2]; level: device int32 [n]; box: device
+ *   int64 [n].  The first call on an adaptive tree uploads its existence
+ *   masks (synchronously).  FMM_EINVAL for a NULL tree or pointer, n < 0, or
+ *   misaligned pointers.
+ */
+int fmm_leaf_boxes(const fmm_tree* tree, const double* xy, int64_t n, int32_t* level, int64_t* box,
+                   void* stream);
 
 /* fmm_l2p: far field at n points from the LE of each point's box:
  *     phi_j (+)= (1/r_l) sum_n L~_l[b][n] ((z_j - x_b) / r_l)^n,  l = lev[j], b = box[j],
@@ -523,6 +540,27 @@ int fmm_p2p(int32_t level, const double* xy, const double* c, int64_t n, const i
  * ------------------------------------------------------------------------- */
 int fmm_m2l_paper_design(const fmm_tree* tree, int32_t level, int32_t p, const void* M, void* L, void* work,
                          int32_t flags, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * fmm_wait_probe -- run the library's bounded device-side wait on purpose.
+ *
+ * The paper has no counterpart.  Every hand-over between warps in the
+ * tensor-core kernels waits on a shared-memory mbarrier with a poll limit;
+ * a wait that reaches it records a timeout in the device error word (read
+ * by fmm_sync_status as FMM_ETIMEOUT) and the kernel returns instead of
+ * hanging.  This call launches one 64-thread CTA in which thread 0 waits on
+ * a one-arrival barrier with both wait forms those kernels use (sleeping
+ * poll and busy spin).
+ *   polls   1..4,194,304: the poll limit of each wait; 0 = the limits the
+ *           kernels use.
+ *   arrive  1: a second warp completes the barrier, so the waits return
+ *           normally; 0: nothing arrives, so each wait gives up after
+ *           `polls` polls and the error word records a timeout.
+ * Asynchronous on `stream`; nothing is allocated after the first call on a
+ * device (which creates the error word).  Errors: FMM_EINVAL for arguments
+ * out of range.
+ * ------------------------------------------------------------------------- */
+int fmm_wait_probe(int32_t polls, int32_t arrive, void* stream);
 
 /* Read and clear the device error word after synchronising `stream`.
  * Returns FMM_OK, FMM_ETIMEOUT or FMM_EDEVICE. */

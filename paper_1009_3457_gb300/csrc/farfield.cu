@@ -302,6 +302,32 @@ int launch_p2m_adjoint(int level, int p, const double* xy, const double* c, int6
     return FMM_OK;
 }
 
+// Deepest existing box holding each point: the box of level l is
+// (floor(x 2^l), floor(y 2^l)) clamped to the level (reading R5), read off the
+// bits of the FP64 coordinates; levels without an existence mask have every box.
+struct LeafLevelMasks {
+    const uint8_t* ex[FMM_MAX_LEVEL + 1];
+};
+
+__global__ void leaf_boxes_kernel(int max_level, LeafLevelMasks m, const double* __restrict__ xy, int64_t n,
+                                  int32_t* __restrict__ lev, int64_t* __restrict__ box)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double x = xy[2 * i], y = xy[2 * i + 1];
+    int bl = 0;
+    int64_t bb = 0;
+    for (int l = 0; l <= max_level; ++l) {
+        const int64_t b = ((int64_t)grid_cell(y, l) << l) | grid_cell(x, l);
+        if (!m.ex[l] || m.ex[l][b]) {
+            bl = l;
+            bb = b;
+        }
+    }
+    lev[i] = bl;
+    box[i] = bb;
+}
+
 }  // namespace fmmgb
 
 using namespace fmmgb;
@@ -410,6 +436,27 @@ int fmm_p2m_adjoint(int32_t level, int32_t p, const double* xy, const double* c,
     if (flags & ~FMM_ACCUMULATE) return fail(FMM_EINVAL, "fmm_p2m_adjoint: unknown flags 0x%x", flags);
     return launch_p2m_adjoint(level, p, xy, c, n, (const float2*)G, grad, (flags & FMM_ACCUMULATE) != 0,
                               (cudaStream_t)stream);
+}
+
+int fmm_leaf_boxes(const fmm_tree* tree, const double* xy, int64_t n, int32_t* level, int64_t* box, void* stream)
+{
+    clear_error();
+    if (!tree) return fail(FMM_EINVAL, "fmm_leaf_boxes: NULL tree");
+    if (n < 0) return fail(FMM_EINVAL, "fmm_leaf_boxes: n < 0");
+    if (n > 0 && (!xy || !level || !box)) return fail(FMM_EINVAL, "fmm_leaf_boxes: NULL pointer");
+    if (((uintptr_t)xy & 7) || ((uintptr_t)box & 7) || ((uintptr_t)level & 3))
+        return fail(FMM_EINVAL, "fmm_leaf_boxes: misaligned pointer");
+    if (n == 0) return FMM_OK;
+    const int L = tree_max_level(tree);
+    LeafLevelMasks m = {};
+    for (int l = 0; l <= L; ++l) {
+        const int32_t* tiles = nullptr;
+        int ntiles = 0;
+        if (int rc = tree_device_level(tree, l, &m.ex[l], &tiles, &ntiles)) return rc;
+    }
+    leaf_boxes_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(L, m, xy, n, level, box);
+    FMM_CUDA_TRY(cudaGetLastError());
+    return FMM_OK;
 }
 
 }  // extern "C"

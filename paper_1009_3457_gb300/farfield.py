@@ -26,19 +26,14 @@ from . import fmmgb
 
 
 def leaf_boxes(tree, xy: torch.Tensor):
-    """(level, box) of the deepest existing box containing each point, from the
-    tree's existence masks.  xy: [N, 2] float64 (any device); returns (int32, int64)."""
-    lev = torch.zeros(xy.shape[0], dtype=torch.int64, device=xy.device)
-    box = torch.zeros_like(lev)
-    for l in range(tree.max_level + 1):
-        n = 1 << l
-        ix = torch.clamp(torch.floor(xy[:, 0] * n).to(torch.int64), 0, n - 1)
-        iy = torch.clamp(torch.floor(xy[:, 1] * n).to(torch.int64), 0, n - 1)
-        b = iy * n + ix
-        here = torch.from_numpy(tree.exists(l)).to(xy.device)[b]
-        lev = torch.where(here, torch.full_like(lev, l), lev)
-        box = torch.where(here, b, box)
-    return lev.to(torch.int32), box
+    """(level, box) of the deepest existing box containing each point (library
+    kernel ``fmm_leaf_boxes``).  xy: [N, 2] float64 on the device; returns
+    (int32, int64) device tensors."""
+    xy = xy.contiguous()
+    lev = torch.empty(xy.shape[0], dtype=torch.int32, device=xy.device)
+    box = torch.empty(xy.shape[0], dtype=torch.int64, device=xy.device)
+    fmmgb.fmm_leaf_boxes(tree, xy, lev, box)
+    return lev, box
 
 
 class FarFieldObjective(torch.autograd.Function):

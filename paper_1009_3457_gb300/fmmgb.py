@@ -97,6 +97,7 @@ SIGNATURES = {
     "fmm_m2m_adjoint": (ctypes.c_int, [_i32, _i32, _vp, _vp, _i32, _vp]),
     "fmm_l2l": (ctypes.c_int, [_i32, _i32, _vp, _vp, _i32, _vp]),
     "fmm_l2l_adjoint": (ctypes.c_int, [_i32, _i32, _vp, _vp, _i32, _vp]),
+    "fmm_leaf_boxes": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp, _vp]),
     "fmm_l2p": (ctypes.c_int, [_i32, _i64, _vp, _vp, _vp, ctypes.POINTER(_vp), _i32, _vp, _i32, _vp]),
     "fmm_l2p_adjoint": (ctypes.c_int, [_i32, _i64, _vp, _vp, _vp, _vp, ctypes.POINTER(_vp), _i32, _vp]),
     "fmm_p2m_adjoint": (ctypes.c_int, [_i32, _i32, _vp, _vp, _i64, _vp, _vp, _i32, _vp]),
@@ -115,6 +116,7 @@ SIGNATURES = {
     "fmm_p2p": (ctypes.c_int, [_i32, _vp, _vp, _i64, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _i32, _vp]),
     "fgt_p2h_binned": (ctypes.c_int, [_i32, _i32, _d, _vp, _vp, _i64, _vp, _vp, _i32, _vp]),
     "fgt_h2p": (ctypes.c_int, [_i32, _i32, _i32, _i32, _d, _vp, _vp, _i64, _vp, _vp, _vp, _i32, _vp]),
+    "fmm_wait_probe": (ctypes.c_int, [_i32, _i32, _vp]),
     "fmm_sync_status": (ctypes.c_int, [_vp]),
     "fmm_last_error": (ctypes.c_char_p, []),
     "fmm_version": (ctypes.c_char_p, []),
@@ -352,6 +354,12 @@ def _level_table(arrays, max_level):
     return (_vp * (max_level + 1))(*[_ptr(arrays[l]) if l in arrays else None for l in range(max_level + 1)])
 
 
+def fmm_leaf_boxes(tree, xy, level, box, stream=None):
+    """Deepest existing box of `tree` holding each point: level (int32 [n]), box (int64 [n])."""
+    n = 0 if level is None else level.numel()
+    _check(load().fmm_leaf_boxes(tree.handle, _ptr(xy), n, _ptr(level), _ptr(box), _stream(stream)))
+
+
 def fmm_l2p(p: int, z, lev, box, L_levels: dict, max_level: int, phi, accumulate: bool = False, stream=None):
     """phi (complex64 [n]) from the LEs of each point's (lev, box); L_levels: {level: [4^l, p] complex64}."""
     n = 0 if lev is None else lev.numel()
@@ -460,6 +468,11 @@ def fgt_h2p(grid_log2: int, n_cut: int, p: int, sigma: float, A, y, perm, box_st
     n = 0 if G is None else G.numel()
     _check(load().fgt_h2p(grid_log2, n_cut, p, prec, float(sigma), _ptr(A), _ptr(y), n, _ptr(perm),
                           _ptr(box_start), _ptr(G), FMM_ACCUMULATE if accumulate else 0, _stream(stream)))
+
+
+def fmm_wait_probe(polls: int, arrive: bool, stream=None):
+    """Launch the bounded-wait probe (see include/fmmgb.h); read the outcome with fmm_sync_status."""
+    _check(load().fmm_wait_probe(int(polls), 1 if arrive else 0, _stream(stream)))
 
 
 def fmm_sync_status(stream=None):

@@ -280,3 +280,11 @@ def test_paper_design_rejects_bad_arguments(fmm):
     assert lib.fmm_m2l_paper_design(tree.handle, 3, 8, 64, 128, None, 0, None) == fmm.FMM_EINVAL  # work
     ptree = fmm.fmm_build_lists(None, 4, periodic=True)
     assert lib.fmm_m2l_paper_design(ptree.handle, 3, 8, 64, 128, 256, 0, None) == fmm.FMM_EUNSUPPORTED
+
+
+def test_wait_probe_rejects_bad_arguments(fmm):
+    lib = fmm.load()
+    assert lib.fmm_wait_probe(-1, 1, None) == fmm.FMM_EINVAL
+    assert lib.fmm_wait_probe((1 << 22) + 1, 0, None) == fmm.FMM_EINVAL
+    assert "cap" in fmm.fmm_last_error()
+    assert lib.fmm_wait_probe(8, 2, None) == fmm.FMM_EINVAL

@@ -191,3 +191,35 @@ def test_tensor_core_precisions_refuse_adaptive_levels(fmm, orc):
     with pytest.raises(fmm.FmmError) as e:
         fmm.fmm_m2l_levels(tree, 2, 16, Md, Ld, prec=fmm.FMM_TC_BF16X3)
     assert e.value.code == fmm.FMM_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("adaptive", [True, False])
+def test_leaf_boxes_match_oracle_exactly(fmm, orc, adaptive):
+    """fmm_leaf_boxes equals the oracle's leaf assignment bit for bit: the tree's
+    own points, uniform points, and coordinates on and next to cell boundaries
+    of every level (0, 1 - ulp, exact multiples of 2^-l, 1.0 and above, below 0)."""
+    import torch
+
+    from paper_1009_3457_gb300 import farfield
+
+    rng = np.random.default_rng(91)
+    xy, _ = workloads.gmm_particles(30000, rng, ncomp=8)
+    L = 9
+    if adaptive:
+        tree = fmm.fmm_build_lists(xy, L, leaf_cap=32)
+        otree = orc.adaptive_tree(xy, 32, L)
+    else:
+        L = 6
+        tree = fmm.fmm_build_lists(None, L)
+        nall = ((1 << (2 * (L + 1))) - 1) // 3
+        otree = orc.AdaptiveTree(np.ones(nall, dtype=np.uint8), L, L, 0)  # every box of every level exists
+    edges = np.array([0.0, np.nextafter(1.0, 0.0), 1.0, 1.5, -0.25, -0.0] +
+                     [k * 2.0 ** -l for l in range(1, L + 1) for k in (1, 3, (1 << l) - 1)] +
+                     [np.nextafter(k * 2.0 ** -l, 0.0) for l in range(1, L + 1) for k in (1, 3)])
+    ex = np.array(np.meshgrid(edges, edges)).reshape(2, -1).T
+    pts = np.concatenate([xy, rng.random((5000, 2)), ex])
+    lev, box = farfield.leaf_boxes(tree, torch.from_numpy(pts).cuda())
+    fmm.fmm_sync_status()
+    olev, obox = orc.leaf_boxes(otree, pts)
+    np.testing.assert_array_equal(lev.cpu().numpy(), olev)
+    np.testing.assert_array_equal(box.cpu().numpy(), obox)
