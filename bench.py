@@ -54,8 +54,10 @@ CONFIG = {
               "pinned host memory, consecutive steps overlapped on three streams",
     "parallelism": "replicas",
 }
-SM_COUNT = 152
 FP32_LANES_PER_SM = 128
+FGT_H2T_LAUNCHES = 2  # kernel launches of one fgt_h2t call
+# replaced at start-up by the device's own SM count and maximum SM clock (device_peaks)
+SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 
 
@@ -69,6 +71,48 @@ def _measured_bf16_tflops() -> float:
 
 
 BF16_PEAK_TFLOPS = _measured_bf16_tflops()
+
+
+def device_peaks(torch, dev):
+    """SM count (device attribute), maximum SM clock (nvidia-smi clocks.max.sm) and a measured FP32
+    throughput (cuBLAS SGEMM 8192^3 with TF32 off, best of 5) of the current GPU; sets the globals
+    the ALU roofline uses."""
+    global SM_COUNT, SM_MAX_MHZ
+    SM_COUNT = torch.cuda.get_device_properties(dev).multi_processor_count
+    src = "nvidia-smi clocks.max.sm"
+    try:
+        out = subprocess.run(["nvidia-smi", "-i", str(dev.index or 0), "--query-gpu=clocks.max.sm",
+                              "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=20)
+        SM_MAX_MHZ = float(out.stdout.strip().splitlines()[0])
+    except Exception:
+        src = "fallback 2070 MHz (nvidia-smi unavailable)"
+    tf32 = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        n = 8192
+        a = torch.randn((n, n), device=dev)
+        b = torch.randn((n, n), device=dev)
+        c = torch.empty((n, n), device=dev)
+        torch.matmul(a, b, out=c)
+        best = float("inf")
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b, out=c)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        sgemm = 2.0 * n ** 3 / (best * 1e-3) / 1e12
+        del a, b, c
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+    return {"sm_count": SM_COUNT, "sm_max_mhz": SM_MAX_MHZ, "clock_source": src,
+            "alu_peak_tflops": alu_peak_tflops(), "sgemm_fp32_tflops": sgemm}
+
+
+def alu_peak_tflops() -> float:
+    """FP32 FMA peak from unit counts and clock: SMs x 128 lanes x 2 flop x max SM clock."""
+    return SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
 
 
 def _dist():
@@ -190,18 +234,53 @@ class OraclePool:
         self.pool.join()
 
 
-def cpu_baseline_all_cores(levels=None):
-    """Translations/s of the oracle over all host cores on the whole step."""
+def cpu_baseline_all_cores(levels=None, steps=3, warmup=1):
+    """Translations/s of the oracle over all host cores, timed the way the reference arm times it:
+    `warmup` whole steps untimed, then `steps` whole steps; rate = translations / total time."""
     levels = levels or LEVELS
     op = OraclePool()
     try:
-        t0 = time.perf_counter()
-        op.step(levels)
-        dt = time.perf_counter() - t0
+        for _ in range(warmup):
+            op.step(levels)
+        times = []
+        for _ in range(steps):
+            t0 = time.perf_counter()
+            op.step(levels)
+            times.append(time.perf_counter() - t0)
     finally:
         op.close()
     ntr = sum(metrics.uniform_translations(l) for l in levels)
-    return ntr / dt, dt, ntr, op.cores
+    return ntr * steps / sum(times), times, ntr, op.cores
+
+
+def tc_accuracy_vs_oracle(torch, fmmgb, dev):
+    """Coefficient error of the FP32 and the BF16x3 tensor-core M2L at p = 24 against the FP64
+    oracle on the precision workload's tree (4096 points, uniform to level 4): relative L2 of the
+    radius-scaled LEs, max over levels 2-4.  Part of the CPU-baseline leg (the one leg of this
+    benchmark that runs the oracle)."""
+    import oracle
+
+    cfg = workloads.CONFIGS["m2l_tc"]
+    p, L = cfg["p"], cfg["max_level"]
+    xy, c = workloads.uniform_particles(cfg["n"], workloads.rng_for("m2l_small"))  # the m2l_small points
+    Ms = oracle.upward_uniform(L, p, xy, c)
+    tree = fmmgb.fmm_build_lists(None, L)
+    err = {}
+    for name, prec in (("fp32", fmmgb.FMM_FP32), ("bf16x3", fmmgb.FMM_TC_BF16X3)):
+        worst = 0.0
+        for level in workloads.m2l_levels(L):
+            ref = oracle.scale_le(oracle.m2l_uniform(level, p, Ms[level]), level)
+            Md = torch.from_numpy(oracle.scale_me(Ms[level], level).astype(np.complex64)).to(dev)
+            Ld = torch.empty_like(Md)
+            fmmgb.fmm_m2l(tree, level, p, Md, Ld, prec=prec)
+            got = Ld.cpu().numpy().astype(np.complex128)
+            worst = max(worst, float(np.linalg.norm(got - ref) / np.linalg.norm(ref)))
+        err[name] = worst
+    fmmgb.fmm_sync_status()
+    return {"tree": f"{cfg['n']} points U[0,1)^2, uniform to level {L}, p = {p}, levels 2-{L}",
+            "fp32_rel_l2": err["fp32"], "bf16x3_rel_l2": err["bf16x3"], "bar_fp32": 1e-5,
+            "bar_tc": "oracle truncation + 1e-4", "metric": "relative L2 of radius-scaled LEs vs FP64 oracle, "
+                                                           "max over levels"}
 
 
 def run_reference(args):
@@ -272,7 +351,7 @@ def _fgt_hermite_rows(torch, fmmgb, dev, fxd, fqd, args, stream, flush):
     ncut = fcfg["ncut"]
     fy, _ = workloads.gmm_particles(fcfg["n"], workloads.rng_for("fgt_targets"))
     fyd = torch.from_numpy(fy).to(dev)
-    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    peak = alu_peak_tflops()
     rows = {}
     for sigma in fcfg["sigmas"]:
         for fp in fcfg["orders"]:
@@ -321,6 +400,26 @@ def _fgt_hermite_rows(torch, fmmgb, dev, fxd, fqd, args, stream, flush):
             del st
     fmmgb.fmm_sync_status()
     return rows
+
+
+SUMMARY_ROWS = ("m2l_adjoint_fp32_levels_2_8", "m2l_tc_bf16x3_levels_2_8", "m2l_fp32_p24_levels_2_8",
+                "m2l_tc_bf16x3_p24_levels_2_8", "m2l_adaptive_gmm_levels_2_9", "m2l_batched_256_problems",
+                "m2l_paper_design_levels_2_8", "fgt_h2t_sigma0.05_p16", "fgt_h2t_sigma0.1_p16",
+                "fgt_h2t_sigma0.2_p16", "fgt_h2p_sigma0.05_p16", "fgt_h2p_tc_bf16x3_sigma0.05_p16",
+                "fmm_p2p_level8", "fmm_potential_level8_p16", "far_field_gradient_gmm")
+
+
+def summarise(rows: dict) -> dict:
+    """The main rows in short (time and a headline fraction), 4 significant digits: the end of the
+    printed line, so a reader of its last few kilobytes sees them."""
+    keep = ("ms", "alu_frac", "sfu_frac", "tensor_frac", "tensor_frac_of_measured_bf16", "speedup_vs_fp32",
+            "fused_speedup")
+    out = {}
+    for name in SUMMARY_ROWS:
+        r = rows.get(name)
+        if r:
+            out[name] = {k: float(f"{r[k]:.4g}") for k in keep if isinstance(r.get(k), (int, float))}
+    return out
 
 
 def _traffic(kernel: str):
@@ -412,6 +511,7 @@ def run_ours(args):
     fmmgb.load()
     fmmgb.fmm_prepare(P)
     stream = torch.cuda.current_stream()
+    peaks = device_peaks(torch, dev)
 
     # --- inputs: particles -> device P2M/M2M (untimed) ---
     xy, c = workloads.uniform_particles(CFG["n"], workloads.rng_for(WORKLOAD))
@@ -586,8 +686,10 @@ def run_ours(args):
                                    ("m2l_tc_bf16_levels_2_8", tc_x1, 1),
                                    ("m2l_tc_bf16x3_adjoint_levels_2_8", tc_adjoint, 1)):
             ms = statistics.median(_timed(torch, _graph(torch, fn), args.steps, stream, flush))
-            rows[name] = {"translations_per_s": NTR / (ms * 1e-3), "ms": ms, "launches": launches,
-                          "gflops": NTR * metrics.m2l_flops_per_translation(P) / (ms * 1e-3) / 1e9}
+            gf = NTR * metrics.m2l_flops_per_translation(P) / (ms * 1e-3) / 1e9
+            rows[name] = {"translations_per_s": NTR / (ms * 1e-3), "ms": ms, "launches": launches, "gflops": gf}
+            if "fp32" in name:
+                rows[name]["alu_frac"] = gf / 1e3 / alu_peak_tflops()
         # precision study at p = 24 on the same tree: FP32 kernel vs tensor cores (BF16x3)
         p24 = workloads.CONFIGS["m2l_tc"]["p"]
         xyd = torch.from_numpy(xy).to(dev)
@@ -607,8 +709,10 @@ def run_ours(args):
 
             ms = statistics.median(_timed(torch, _graph(torch, run24), args.steps, stream, flush))
             t24[prec] = ms
-            rows[name] = {"translations_per_s": NTR / (ms * 1e-3), "ms": ms, "launches": 1,
-                          "gflops": NTR * metrics.m2l_flops_per_translation(p24) / (ms * 1e-3) / 1e9}
+            gf = NTR * metrics.m2l_flops_per_translation(p24) / (ms * 1e-3) / 1e9
+            rows[name] = {"translations_per_s": NTR / (ms * 1e-3), "ms": ms, "launches": 1, "gflops": gf}
+            if prec == fmmgb.FMM_FP32:
+                rows[name]["alu_frac"] = gf / 1e3 / alu_peak_tflops()
         rows["tc_vs_fp32_speedup_p24"] = {"speedup": t24[fmmgb.FMM_FP32] / t24[fmmgb.FMM_TC_BF16X3],
                                           "note": "both meet the tensor-core bar (truncation + 1e-4); "
                                                   "measured coefficient errors in tests/test_m2l_tc_gpu.py"}
@@ -706,6 +810,8 @@ def run_ours(args):
             ms = statistics.median(_timed(torch, _graph(torch, fn), args.steps, stream, flush))
             rows[name] = {"translations_per_s": gntr / (ms * 1e-3), "ms": ms, "launches": 1, "translations": gntr,
                           "gflops": gntr * metrics.m2l_flops_per_translation(gp) / (ms * 1e-3) / 1e9,
+                          "alu_frac": gntr * metrics.m2l_flops_per_translation(gp) / (ms * 1e-3) / 1e12
+                          / alu_peak_tflops(),
                           "boxes": {l: int(gtree.level_info(l).nexist) for l in glev}}
         from paper_1009_3457_gb300 import farfield
 
@@ -745,8 +851,7 @@ def run_ours(args):
         rows["m2l_batched_256_problems"] = {
             "translations_per_s": ntr_b / (ms * 1e-3), "ms": ms, "launches": 1, "translations": ntr_b,
             "gflops": bt["flops"] / (ms * 1e-3) / 1e9,
-            "alu_frac": bt["flops"] / (ms * 1e-3) / 1e12
-            / (SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12),
+            "alu_frac": bt["flops"] / (ms * 1e-3) / 1e12 / alu_peak_tflops(),
             "plan": bt["info"], "one_launch_per_problem_ms": ms_seq,
             "speedup_vs_one_launch_per_problem": ms_seq / ms}
         del bt, bplan
@@ -794,10 +899,10 @@ def run_ours(args):
                         "points_per_s": fcfg["n"] / (ms_all * 1e-3), "launches": 10,
                         "note": "fgt_bin_points of the sources (3 kernels), fgt_p2h_binned, fgt_h2t (2 passes), "
                                 "fgt_bin_points of the targets (3 kernels), fgt_t2p_binned; uniform targets"}
+                gfs = (4 ** g) * metrics.fgt_flops_per_box_separable(fp, taps, taps) / (ms * 1e-3) / 1e9
                 rows[f"fgt_h2t_sigma{sigma}_p{fp}"] = {
-                    "translations_per_s": ntr / (ms * 1e-3), "ms": ms, "launches": 2, "grid": f"{1 << g}^2",
-                    "gflops_separable": (4 ** g) * metrics.fgt_flops_per_box_separable(fp, taps, taps)
-                    / (ms * 1e-3) / 1e9}
+                    "translations_per_s": ntr / (ms * 1e-3), "ms": ms, "launches": FGT_H2T_LAUNCHES,
+                    "grid": f"{1 << g}^2", "gflops_separable": gfs, "alu_frac": gfs / 1e3 / alu_peak_tflops()}
         rows.update(_fgt_hermite_rows(torch, fmmgb, dev, fxd, fqd, args, stream, flush))
         fmmgb.fmm_sync_status()
 
@@ -805,7 +910,7 @@ def run_ours(args):
         flops = NTR * metrics.m2l_flops_per_translation(P)
         k_avg_s = statistics.mean(step_ms) * 1e-3
         achieved = flops / k_avg_s / 1e12
-        peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+        peak = alu_peak_tflops()
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
@@ -815,7 +920,10 @@ def run_ours(args):
             "roofline": {
                 "bound": "alu", "kernel": "m2l_fp32_kernel<16> (levels 2-8, one launch)", "achieved": achieved,
                 "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": _traffic(f"m2l_fp32_kernel<{P}>"),
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (max SM clock)",
+                "peak_source": f"{SM_COUNT} SMs (device attribute) x 128 FP32 lanes x 2 flop x {SM_MAX_MHZ:.0f} MHz "
+                               f"({peaks['clock_source']})",
+                "measured_sgemm_fp32_tflops": peaks["sgemm_fp32_tflops"],
+                "frac_of_measured_sgemm": achieved / peaks["sgemm_fp32_tflops"],
                 "flops_per_launch": flops, "launch_ms": statistics.mean(step_ms),
                 "frac_at_sampled_clock": (achieved / (peak * clocks["sm_mhz"] / SM_MAX_MHZ))
                 if clocks and clocks.get("sm_mhz") else None,
@@ -828,14 +936,29 @@ def run_ours(args):
             "gpu_launches": args.steps,
             "graph_replay_matches_direct_call": graph_matches,
             "clocks": clocks,
+            "device": peaks,
             "rows": rows,
         }
+        if rows:
+            out["summary"] = summarise(rows)
+            out["tc_vs_fp32"] = {
+                "p24_levels_2_8": {"fp32_ms": rows["m2l_fp32_p24_levels_2_8"]["ms"],
+                                   "bf16x3_ms": rows["m2l_tc_bf16x3_p24_levels_2_8"]["ms"],
+                                   "speedup": rows["tc_vs_fp32_speedup_p24"]["speedup"]},
+                "p16_levels_2_8": {"fp32_ms": statistics.median(step_ms),
+                                   "bf16x3_ms": rows["m2l_tc_bf16x3_levels_2_8"]["ms"],
+                                   "speedup": rows["tc_vs_fp32_speedup_p16"]["speedup"]},
+                "workload": "2^22 points, uniform to level 8, levels 2-8 (2,316,900 translations)"}
         if not args.no_cpu_baseline and ws == 1:
-            v, dt, ntr, cores = cpu_baseline_all_cores()
+            if rows:
+                out["tc_vs_fp32"]["accuracy"] = tc_accuracy_vs_oracle(torch, fmmgb, dev)
+            ksteps = 3
+            v, times, ntr, cores = cpu_baseline_all_cores(steps=ksteps, warmup=1)
             v1, dt1, _ = cpu_baseline_run()
             out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                   "sample": f"the whole step ({ntr} translations, levels 2-8) once, {dt:.2f} s, "
-                                             f"FP64 oracle in {cores} processes over disjoint target slices",
+                                   "sample": f"the whole step ({ntr} translations, levels 2-8): 1 untimed + "
+                                             f"{ksteps} timed steps ({sum(times):.2f} s), FP64 oracle in {cores} "
+                                             f"processes over disjoint target slices (as --impl reference)",
                                    "single_thread": {"value": v1, "cores": 1, "seconds": dt1}}
         print(json.dumps(out))
     if ws > 1:
