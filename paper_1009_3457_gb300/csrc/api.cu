@@ -68,6 +68,8 @@ struct DeviceState {
     size_t fgt_ws_bytes = 0;
     unsigned char* tc_planes = nullptr;  // tensor-core M2L: BF16 hi/lo copies of the MEs (grown on demand)
     size_t tc_planes_bytes = 0;
+    int* tc_flags = nullptr;  // tensor-core M2L: one flag per tile, zero between launches (grown on demand)
+    int tc_flag_count = 0;
     int sm_count = 0;
     int* counters = nullptr;  // ring of persistent-launch work counters
     unsigned next_counter = 0;
@@ -179,6 +181,27 @@ int tc_plane_workspace(size_t bytes, unsigned char** out)
         s->tc_planes_bytes = bytes;
     }
     *out = s->tc_planes;
+    return FMM_OK;
+}
+
+int tc_flag_workspace(int ntiles, int** flags)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    DeviceState* s = nullptr;
+    int rc = current_state(&s);
+    if (rc) return rc;
+    if (s->tc_flag_count < ntiles) {
+        if (s->tc_flags) {
+            FMM_CUDA_TRY(cudaDeviceSynchronize());
+            cudaFree(s->tc_flags);
+            s->tc_flags = nullptr;
+            s->tc_flag_count = 0;
+        }
+        FMM_CUDA_TRY(cudaMalloc(&s->tc_flags, (size_t)ntiles * sizeof(int)));
+        FMM_CUDA_TRY(cudaMemset(s->tc_flags, 0, (size_t)ntiles * sizeof(int)));
+        s->tc_flag_count = ntiles;
+    }
+    *flags = s->tc_flags;
     return FMM_OK;
 }
 

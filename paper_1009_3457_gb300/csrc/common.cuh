@@ -172,6 +172,9 @@ int launch_build_tc_image(int p, double s, int variant, void* img, cudaStream_t 
 int launch_m2l_tc(M2LLaunch& job, int p, const void* img, bool split, cudaStream_t st);
 int get_tc_image(int p, int variant, const void** out);
 int tc_plane_workspace(size_t bytes, unsigned char** out);
+// Per-device flags of the tensor-core M2L, one per tile (zero between
+// launches; grown on demand, zeroed when allocated).
+int tc_flag_workspace(int ntiles, int** flags);
 
 // launchers (fgt_h2t.cu)
 bool fgt_supported(int p);

@@ -14,31 +14,51 @@
 // -- a 3x3 convolution over the parent grid whose "channels" are the 4 child
 // classes x 2p real coefficients.  With D[rows][parents] in TMEM:
 //   M rows  = 4 classes x 2p       (128 at p = 16; 192 -> two M=128 tiles at p = 24)
-//   N       = the 8 x TPY parents of a tile
+//   N       = the 8 x 32 = 256 parents of a tile
 //   K       = 32 blocks (e, c') x 2p, processed 16 at a time.
-// A (the operator blocks) streams from an L2-resident image through a ring
-// of shared-memory stages (cp.async.bulk, mbarrier transaction counts).  B
-// (the source MEs) is the tile's halo, staged once: for block (e, c') the B
-// operand is the class-c' plane seen through a descriptor whose start is
-// shifted by e -- the 8 parents of one tile row are 8 consecutive 16-byte
-// rows, and the stride to the next tile row is the halo row pitch (SBO).
+// A (the operator block of (e, c')) streams from an L2-resident image
+// through a ring of shared-memory stages (cp.async.bulk).  B (the source MEs)
+// is the class-c' halo of the tile, 10 x 34 parents, seen through a
+// descriptor whose start is shifted by e: the 8 parents of one tile row are
+// 8 consecutive 16-byte rows, and the stride to the next tile row is the halo
+// row pitch (SBO).
 //
 // Precision.  BF16 keeps 8 significant bits.  With the hi/lo split
 // x = hi + lo (both BF16), the three products A_hi B_hi + A_hi B_lo +
-// A_lo B_hi recover ~16 bits per product, accumulated in FP32.
+// A_lo B_hi recover ~16 bits, all accumulated into the same FP32 TMEM
+// columns.
 //
-// Schedule.  A persistent CTA per SM takes tiles round-robin and runs four
-// roles concurrently: producer warps (eight at p = 16, three at p = 24; one
-// bulk copy in flight per warp, one ring stage each) stream the 32 operator
-// blocks of every tile through a ring of shared-memory stages; an MMA thread
-// (warp 8) issues the tcgen05 products into a TMEM accumulator; three staging
-// warps (9-11) load the next tile's halo (TMA tensor-map copies of the BF16
-// hi/lo planes that a pre-pass writes, or bulk copies where a level is too
-// small for the tensor map); four epilogue warps (12-15) drain the
-// accumulator.
-// Hand-overs use mbarriers; every wait is bounded: on timeout the CTA records
-// FMM_ETIMEOUT in the device error word, waits (bounded) for its own copies,
-// frees its TMEM and returns.
+// Why N = 256.  A tcgen05 MMA reads its operands from shared memory at about
+// 128 B per cycle: an M = 128, K = 16 product reads 4 KB of A and N/16 KB of
+// B and executes in N/2 cycles, so N = 128 products are bound by the
+// shared-memory port (64 cycles either way) with no room for the operator
+// stream, while N = 256 products (128 cycles for 96 cycles of operand reads)
+// leave the port time the 16 KB ring refill of each block needs.  One
+// 256-column accumulator holds the three products, so two accumulators fit in
+// TMEM at p = 16 and a segment's epilogue overlaps the next one's MMAs.
+//
+// Work split (stream-K).  The U = tiles x 32 units (tile, block) are cut into
+// equal contiguous ranges, one per CTA, so every SM does the same number of
+// MMAs whatever the tile count.  A CTA walks its range's tiles from last to
+// first.  For a tile cut between CTAs, the part holding its first unit (the
+// head) is the first segment its CTA processes: it stores into L and then
+// publishes the tile's flag; every other part of the tile, held by higher
+// CTAs, waits for that flag (long published when the waiting CTA gets there)
+// and adds its sums with fire-and-forget reductions.  No CTA waits on a
+// higher one, every wait is bounded, and the kernel's last CTA to finish
+// clears the flags for the next launch.
+//
+// Schedule.  One CTA per SM (grid = min(SMs, U / 8)), four roles: producer
+// warps (eight at p = 16, two at p = 24, one ring stage and one bulk copy in
+// flight each) stream the operator blocks of the range; an MMA thread (warp
+// 8, which also owns the TMEM allocation) issues the products; three staging
+// warps (9-11) load the class halos into two buffers (one TMA tensor copy of
+// the BF16 hi/lo planes that a pre-pass writes, or cp.async where a level is
+// too small for the tensor map or the lists are periodic); four epilogue
+// warps (12-15) drain the accumulators.  Every mbarrier and flag wait is
+// bounded: on timeout the waiting role records FMM_ETIMEOUT in the device
+// error word and stops; producers wait (bounded) for their own copies in
+// flight, and the TMEM is freed before the CTA exits.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -50,7 +70,11 @@
 
 namespace fmmgb {
 
-constexpr int kTcTileX = 8;               // parents per tile row (one core-matrix group)
+constexpr int kTcTileX = 8;     // parents per tile row (one core-matrix group of the N operand)
+constexpr int kTcTileY = 32;    // parent rows per tile
+constexpr int kTcBlocks = 32;   // (e != 0) x 4 source classes
+constexpr int kTcReplicas = 4;  // copies of the operator image in global memory
+constexpr int kTcMinUnits = 8;  // fewest units per CTA: a tile is cut between at most 5 CTAs
 
 template <int P>
 struct TcCfg {
@@ -58,40 +82,27 @@ struct TcCfg {
     static constexpr int KCH = K2 / 8;                // 16-byte BF16 chunks per block row
     static constexpr int KSTEP = K2 / 16;             // MMA K steps of 16 per block
     static constexpr int MT = (8 * P + 127) / 128;    // M tiles of 128 rows
-    static constexpr int TPY = P <= 16 ? 16 : 8;      // parent rows per tile
-    static constexpr int N = kTcTileX * TPY;          // parents per tile (the split MMA has N = 2 x this)
-    static constexpr int HX = kTcTileX + 2, HY = TPY + 2;
+    static constexpr int N = kTcTileX * kTcTileY;     // parents per tile = MMA N
+    static constexpr int HX = kTcTileX + 2, HY = kTcTileY + 2;
     static constexpr int NPOS = HX * HY;              // halo parent positions
-    // one (class, chunk) plane of a halo buffer: 2 HY rows (halo row, hi/lo interleaved) x HX x 16 B
+    // one chunk plane of a class halo: HY rows x (hi, lo) x HX positions x 16 B
     static constexpr int ROWB = HX * 16;
     static constexpr int IPLANE = 2 * HY * ROWB;
-    static constexpr int BBUF = 4 * KCH * IPLANE;     // bytes of one halo buffer (hi and lo)
-    static constexpr int APART = MT * 128 * K2 * 2;   // bytes of one block's hi (or lo) operator image
-    static constexpr int NBUF = 1;                    // halo buffers
-    // Producer warps, one ring stage each.  A stage is refilled only after the
-    // MMAs that read it complete, so the operator stream is bound by the ring
-    // depth over that round trip (completion, wake-up, one bulk-copy latency):
-    // as many stages as shared memory holds (8 x 16 KB at p = 16, 3 x 48 KB at
-    // p = 24, beside the halo buffer).
-    static constexpr int NPROD = P <= 16 ? 8 : 3;
-    static constexpr int SP = 1;                      // ring stages per producer
-    static constexpr int STAGES = NPROD * SP;         // operator ring depth
-    // Stages are released in groups of G by one tcgen05.commit: the arrival
-    // of a commit on its mbarrier comes ~600 cycles after the previous one
-    // (measured), so a commit per 16 KB block caps the stream below the
-    // tensor pipe's rate at p = 16.  Blocks per CTA (32 per tile) are a
-    // multiple of G.
-    static constexpr int G = P <= 16 ? 2 : 1;
-    static_assert(STAGES % G == 0 && 32 % G == 0, "stage groups");
-    // TMEM: per M tile a 2N-column accumulator (A_hi x [B_hi|B_lo] interleaved) + an N-column one (A_lo x B_hi)
-    static constexpr int SETCOLS = MT * 3 * N;
-    static constexpr int NACC = 2 * SETCOLS <= 512 ? 2 : 1;
+    static constexpr int HBUF = KCH * IPLANE;         // one class halo (hi and lo)
+    static constexpr int APART = MT * 128 * K2 * 2;   // one block's hi (or lo) operator image
+    static constexpr int STAGE = 2 * APART;           // a ring stage: hi then lo
+    static constexpr int NHB = 2;                     // class halo buffers
+    // ring stages, one producer warp each: as many as shared memory holds
+    // beside the halo buffers (8 x 16 KB at p = 16, 2 x 48 KB at p = 24)
+    static constexpr int STAGES = P <= 16 ? 8 : 2;
+    static constexpr int DCOLS = MT * N;              // TMEM columns of one accumulator
+    static constexpr int NACC = 2 * DCOLS <= 512 ? 2 : 1;
     static constexpr int TMEM_COLS = 512;
-    static constexpr size_t smem = (size_t)NBUF * BBUF + (size_t)STAGES * 2 * APART + 1024;
+    static constexpr size_t smem = (size_t)NHB * HBUF + (size_t)STAGES * STAGE + 1024;
+    static_assert(STAGES <= 8, "producer warps 0-7");
+    static_assert(smem <= 232448, "dynamic shared memory");
+    static_assert(DCOLS * NACC <= TMEM_COLS, "TMEM");
 };
-
-constexpr int kTcBlocks = 32;   // (e != 0) x 4 source classes
-constexpr int kTcReplicas = 4;  // copies of the operator image in global memory
 
 // block index b = pe * 4 + c', pe = 0..7 enumerating the 8 non-central parent offsets
 __host__ __device__ inline void tc_block(int b, int& ex, int& ey, int& cs)
@@ -159,6 +170,10 @@ __global__ void build_tc_image_kernel(double s, int variant, unsigned char* __re
     *reinterpret_cast<__nv_bfloat16*>(blk + C::APART + off) = wlo;
 }
 
+// unit order within a tile: u & 31 = c' * 8 + pe (class-major, so a class
+// halo serves 8 consecutive units); the image stores block b = pe * 4 + c'
+__host__ __device__ inline int tc_image_block(int blk) { return (blk & 7) * 4 + (blk >> 3); }
+
 // tensor-map load (the other PTX helpers are in tc_ptx.cuh)
 __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
                                             uint64_t* bar)
@@ -182,6 +197,9 @@ __global__ void me_planes_kernel(M2LLaunch job, int split)
     // one thread per 16-byte unit of a plane row, consecutive threads along qx: the
     // stores are coalesced, each thread reads one 32-byte chunk of one box
     using C = TcCfg<P>;
+    // the translation kernel may start now: only its halo staging reads the planes, after
+    // it has waited for this grid to complete (griddepcontrol.wait)
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int li = 0;
     for (; li < job.nlev; ++li) {
@@ -217,24 +235,14 @@ __global__ void me_planes_kernel(M2LLaunch job, int split)
 
 
 // ---------------------------------------------------------------------------
-// the kernel: persistent, one CTA per SM, warp-specialised
-//   warps 0-2, lane 0  producers: operator block g of the continuous stream
-//                   (32 per tile) comes from producer g % 3 into that
-//                   producer's share of the ring; each issuing thread keeps
-//                   one bulk copy in flight, so three producers triple the rate
-//   warp 4, lane 0  MMA issuer (warp 4 also owns the TMEM allocation)
-//   warps 5-7       halo staging: one TMA tensor load of the tile's halo from
-//                   the BF16 hi/lo planes written by me_planes_kernel (cp.async
-//                   when the halo is larger than the level or lists are periodic)
-//   warps 8-11      epilogue: TMEM -> registers -> coalesced LE stores; two
-//                   TMEM accumulators so tile i's epilogue overlaps tile i+1's MMAs
-// Tiles are handed out round-robin (tile = blockIdx.x + i * gridDim.x); all
-// tiles cost the same.
+// the kernel: persistent, one CTA per SM, warp-specialised, stream-K ranges
 // ---------------------------------------------------------------------------
-// warps 0-7 producers (NPROD of them active), 8 MMA issuer, 9-11 halo staging,
+// warps 0-7 producers (STAGES of them active), 8 MMA issuer, 9-11 halo staging,
 // 12-15 epilogue (a multiple of 4, so that warp % 4 is its TMEM lane quarter)
 constexpr int kTcCtaThreads = 512;
 constexpr int kMmaWarp = 8, kStageWarp0 = 9, kStageWarps = 3, kEpiWarp0 = 12;
+// named barriers: staging warps (wait outcome; cp.async completion), epilogue warps (wait outcome; publish)
+constexpr int kStageBar = 1, kStageCopyBar = 2, kEpiBar = 3, kPubBar = 4;
 
 struct TcTile {
     const unsigned char* planes;
@@ -242,10 +250,8 @@ struct TcTile {
     int side, np, PX0, PY0, li;
 };
 
-template <int P>
 __device__ __forceinline__ TcTile tc_tile(const M2LLaunch& job, int tile)
 {
-    using C = TcCfg<P>;
     int li = 0;
     while (li + 1 < job.nlev && tile >= job.lv[li + 1].tile_begin) ++li;
     const M2LLevel& lv = job.lv[li];
@@ -257,61 +263,104 @@ __device__ __forceinline__ TcTile tc_tile(const M2LLaunch& job, int tile)
     const int t = tile - lv.tile_begin;
     const int tpr = (g.np + kTcTileX - 1) / kTcTileX;
     g.PX0 = (t % tpr) * kTcTileX;
-    g.PY0 = (t / tpr) * C::TPY;
+    g.PY0 = (t / tpr) * kTcTileY;
     g.li = li;
     return g;
 }
 
-
 struct TcMaps {
-    CUtensorMap map[kMaxLaunchLevels];  // per launch level: 5-D map over its planes (when use_tma)
+    CUtensorMap map[kMaxLaunchLevels];  // per launch level: 4-D map over its planes (when use_tma)
     int use_tma[kMaxLaunchLevels];
 };
 
+// first unit of CTA j's range: the U units in `grid` equal contiguous shares
+__device__ __forceinline__ int tc_range_begin(int j, int grid, int units)
+{
+    return (int)(((long long)units * j) / grid);
+}
+
+// A CTA's range [u0, u1) is walked tile by tile from its last tile to its first
+// (segment i = the units of tile t1 - i inside the range), units in order
+// within a segment.  Every role runs this walk.
+struct TcSeg {
+    int t, sa, sb;  // tile, units [sa, sb)
+};
+__device__ __forceinline__ TcSeg tc_seg(int u0, int u1, int i)
+{
+    TcSeg s;
+    s.t = ((u1 - 1) >> 5) - i;
+    s.sa = max(u0, s.t * kTcBlocks);
+    s.sb = min(u1, (s.t + 1) * kTcBlocks);
+    return s;
+}
+__device__ __forceinline__ int tc_nseg(int u0, int u1) { return u1 > u0 ? ((u1 - 1) >> 5) - (u0 >> 5) + 1 : 0; }
+
+// AND of `v` over the `n` threads of named barrier `id` (uniform control flow after a bounded wait)
+__device__ __forceinline__ bool bar_and(int id, int n, bool v)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 q, %1, 0;\n\tbar.red.and.pred p, %2, %3, q;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(r)
+        : "r"((uint32_t)v), "r"(id), "r"(n)
+        : "memory");
+    return r != 0;
+}
+
+// bounded wait for a flag that another CTA of this launch publishes with release semantics
+__device__ __forceinline__ bool wait_flag(const int* f)
+{
+    for (uint32_t it = 0; it < kWaitCap; ++it) {
+        int v;
+        asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(f) : "memory");
+        if (v) return true;
+        __nanosleep(128);
+    }
+    return false;
+}
+
 template <int P>
-__global__ void __launch_bounds__(kTcCtaThreads, 1) m2l_tc_kernel(M2LLaunch job, const __grid_constant__ TcMaps maps,
-                                                                   const unsigned char* __restrict__ img, int split,
-                                                                   int total_tiles, int* __restrict__ err)
+__global__ void __launch_bounds__(kTcCtaThreads, 1)
+    m2l_tc_kernel(M2LLaunch job, const __grid_constant__ TcMaps maps, const unsigned char* __restrict__ img, int split,
+                  int units, int* __restrict__ flags, int* __restrict__ done, int* __restrict__ err)
 {
     using C = TcCfg<P>;
     extern __shared__ __align__(1024) unsigned char tsm[];
-    unsigned char* bbuf = tsm;                                 // NBUF halo buffers
-    unsigned char* astage = tsm + (size_t)C::NBUF * C::BBUF;   // STAGES x (hi APART, lo APART)
-    uint64_t* afull = reinterpret_cast<uint64_t*>(astage + (size_t)C::STAGES * 2 * C::APART);
+    unsigned char* hbuf = tsm;                                   // NHB class halos
+    unsigned char* astage = tsm + (size_t)C::NHB * C::HBUF;      // STAGES x (hi APART, lo APART)
+    uint64_t* afull = reinterpret_cast<uint64_t*>(astage + (size_t)C::STAGES * C::STAGE);
     uint64_t* aempty = afull + C::STAGES;
-    uint64_t* bfull = aempty + C::STAGES;
-    uint64_t* bfree = bfull + 2;
-    uint64_t* dfull = bfree + 2;
+    uint64_t* hfull = aempty + C::STAGES;
+    uint64_t* hfree = hfull + C::NHB;
+    uint64_t* dfull = hfree + C::NHB;
     uint64_t* dfree = dfull + 2;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(dfree + 2);
-    uint32_t* boff16 = tmem_slot + 4;  // [32] B-operand offset of each (e, c') block, in 16-byte units
+    uint64_t* mdone = dfree + 2;  // the MMA thread's final commit: every issued MMA has completed
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mdone + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int ntiles = blockIdx.x < (unsigned)total_tiles ? (total_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-    const uint32_t abytes = split ? 2u * C::APART : (uint32_t)C::APART;
-    // Every CTA walks the same operator blocks; starting at a CTA-dependent
-    // block and reading one of kTcReplicas copies of the image spreads the
-    // simultaneous reads of all SMs over many L2 lines.
-    const int rot = (int)(blockIdx.x % kTcBlocks);
-    const unsigned char* rimg = img + (size_t)(blockIdx.x % kTcReplicas) * kTcBlocks * 2 * C::APART;
+    const int cta = (int)blockIdx.x, grid = (int)gridDim.x;
+    const int u0 = tc_range_begin(cta, grid, units), u1 = tc_range_begin(cta + 1, grid, units);
+    const int nseg = tc_nseg(u0, u1);
+    const uint32_t abytes = split ? (uint32_t)C::STAGE : (uint32_t)C::APART;
+    // CTAs read one of kTcReplicas copies of the image, spreading the
+    // simultaneous reads of all SMs over more L2 lines
+    const unsigned char* rimg = img + (size_t)(cta % kTcReplicas) * kTcBlocks * C::STAGE;
 
     if (tid == 0) {
         for (int s = 0; s < C::STAGES; ++s) {
             mbar_init(&afull[s], 1);
-            if (s % C::G == 0) mbar_init(&aempty[s / C::G], 1);
+            mbar_init(&aempty[s], 1);
+        }
+        for (int i = 0; i < C::NHB; ++i) {
+            mbar_init(&hfull[i], 1);
+            mbar_init(&hfree[i], 1);
         }
         for (int i = 0; i < 2; ++i) {
-            mbar_init(&bfull[i], 1);
-            mbar_init(&bfree[i], 1);
             mbar_init(&dfull[i], 1);
             mbar_init(&dfree[i], 4);
         }
+        mbar_init(mdone, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (tid < kTcBlocks) {
-        int ex, ey, cs;
-        tc_block(tid, ex, ey, cs);
-        boff16[tid] = (uint32_t)((cs * C::KCH * C::IPLANE + 2 * (ey + 1) * C::ROWB + (ex + 1) * 16) >> 4);
     }
     if (warp == kMmaWarp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
@@ -324,176 +373,267 @@ __global__ void __launch_bounds__(kTcCtaThreads, 1) m2l_tc_kernel(M2LLaunch job,
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
 
-    if (warp < C::NPROD) {
-        // ---------------- producer `warp` ----------------
+    if (warp < C::STAGES) {
+        // ---------------- producer `warp`: units g = warp, warp + STAGES, ... of the walk ----------------
         if (lane == 0) {
-            const int pr = warp;
-            const int total_blocks = ntiles * kTcBlocks;
-            int k = 0;  // local fill index of this producer
+            const int s = warp;
+            int k = 0;  // fills issued into stage s
             bool ok = true;
-            for (int g = pr; g < total_blocks; g += C::NPROD, ++k) {
-                const int s = pr * C::SP + k % C::SP;
-                if (k >= C::SP && !mbar_wait(&aempty[s / C::G], (uint32_t)(((k / C::SP) - 1) & 1))) {
-                    ok = false;
-                    break;
+            int g = 0;  // walk position
+            for (int i = 0; i < nseg && ok; ++i) {
+                const TcSeg sg = tc_seg(u0, u1, i);
+                for (int u = sg.sa; u < sg.sb; ++u, ++g) {
+                    if (g % C::STAGES != s) continue;
+                    if (k >= 1 && !mbar_wait(&aempty[s], (uint32_t)((k - 1) & 1))) {
+                        ok = false;
+                        break;
+                    }
+                    const int b = tc_image_block(u & 31);
+                    mbar_expect_tx(&afull[s], abytes);
+                    bulk_load(astage + (size_t)s * C::STAGE, rimg + (size_t)b * C::STAGE, abytes, &afull[s]);
+                    ++k;
                 }
-                const int b = (g % kTcBlocks + rot) % kTcBlocks;
-                mbar_expect_tx(&afull[s], abytes);
-                bulk_load(astage + (size_t)s * 2 * C::APART, rimg + (size_t)b * 2 * C::APART, abytes, &afull[s]);
             }
             if (!ok) atomicOr(err, DEV_ERR_TIMEOUT);
-            // do not leave while copies are in flight: this producer's last min(k, SP) fills must have landed
-            for (int q = (k > C::SP ? k - C::SP : 0); q < k; ++q)
-                if (!mbar_wait(&afull[pr * C::SP + q % C::SP], (uint32_t)((q / C::SP) & 1))) atomicOr(err, DEV_ERR_TIMEOUT);
+            // do not leave while a copy is in flight: the last fill of stage s must have landed
+            if (k > 0 && !mbar_wait(&afull[s], (uint32_t)((k - 1) & 1))) atomicOr(err, DEV_ERR_TIMEOUT);
         }
     } else if (warp == kMmaWarp && lane == 0) {
         // ---------------- MMA issuer ----------------
-        // per K step of 16: D1 (2N cols) += A_hi x [B_hi | B_lo] (rows interleaved, N = 2 x 64),
-        //                   D2 (N cols)  += A_lo x B_hi; result = D1 hi cols + D1 lo cols + D2.
-        // Without the split: D2 += A_hi x B_hi only.
-        const uint32_t id2n = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)((2 * C::N) >> 3) << 17) | ((128u >> 4) << 24);
-        const uint32_t idn = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(C::N >> 3) << 17) | ((128u >> 4) << 24);
-        const uint64_t a0 = umma_desc(su32(astage), 128, C::KCH * 128);  // stage 0, hi part
+        // per K step of 16 and M tile: D += A_hi B_hi (+ A_hi B_lo + A_lo B_hi with the split),
+        // all N = 256 products into the same accumulator columns
+        const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(C::N >> 3) << 17) | ((128u >> 4) << 24);
+        const uint32_t abase = su32(astage), hbase = su32(hbuf);
         constexpr uint64_t alo_off = (uint64_t)(C::APART >> 4);
-        int g = 0;
+        int g = 0, hg = 0;
         bool ok = true;
-        for (int i = 0; i < ntiles && ok; ++i) {
-            const int ts = i % C::NBUF, td = i % C::NACC;
-            if (!mbar_spin(&bfull[ts], (uint32_t)((i / C::NBUF) & 1))) ok = false;
-            if (ok && i >= C::NACC && !mbar_spin(&dfree[td], (uint32_t)(((i / C::NACC) - 1) & 1))) ok = false;
-            if (!ok) break;
+        for (int i = 0; i < nseg && ok; ++i) {
+            const TcSeg sg = tc_seg(u0, u1, i);
+            const int d = i % C::NACC;
+            if (i >= C::NACC && !mbar_spin(&dfree[d], (uint32_t)(((i / C::NACC) - 1) & 1))) {
+                ok = false;
+                break;
+            }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t bb = su32(bbuf + (size_t)ts * C::BBUF);
-            const uint64_t bint0 = umma_desc(bb, C::IPLANE, C::ROWB);     // hi/lo rows interleaved
-            const uint64_t bhi0 = umma_desc(bb, C::IPLANE, 2 * C::ROWB);  // hi rows only
-            const uint32_t dset = tmem + (uint32_t)(td * C::SETCOLS);
-            for (int bi = 0; bi < kTcBlocks; ++bi, ++g) {
-                const int b = (bi + rot) % kTcBlocks;
-                const int pk = g / C::NPROD;  // fill index within producer g % NPROD
-                const int s = (g % C::NPROD) * C::SP + pk % C::SP;
-                if (!mbar_spin(&afull[s], (uint32_t)((pk / C::SP) & 1))) {
+            const uint32_t dset = tmem + (uint32_t)(d * C::DCOLS);
+            bool first = true;
+            for (int u = sg.sa; u < sg.sb && ok;) {
+                const int cls = (u & 31) >> 3;
+                const int grp_end = min(sg.sb, sg.t * kTcBlocks + (cls + 1) * 8);
+                const int hb = hg % C::NHB;
+                if (!mbar_spin(&hfull[hb], (uint32_t)((hg / C::NHB) & 1))) {
                     ok = false;
                     break;
                 }
-                const uint64_t boff = (uint64_t)boff16[b];
+                const uint32_t hbb = hbase + (uint32_t)(hb * C::HBUF);
+                for (; u < grp_end; ++u, ++g) {
+                    const int s = g % C::STAGES;
+                    if (!mbar_spin(&afull[s], (uint32_t)((g / C::STAGES) & 1))) {
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    int ex, ey, cs;
+                    tc_block(tc_image_block(u & 31), ex, ey, cs);
+                    const uint32_t bst = hbb + (uint32_t)((ey + 1) * 2 * C::ROWB + (ex + 1) * 16);
+                    const uint64_t bhi = umma_desc(bst, C::IPLANE, 2 * C::ROWB);
+                    const uint64_t blo = umma_desc(bst + C::ROWB, C::IPLANE, 2 * C::ROWB);
+                    const uint64_t ahi = umma_desc(abase + (uint32_t)(s * C::STAGE), 128, C::KCH * 128);
 #pragma unroll
-                for (int kk = 0; kk < C::KSTEP; ++kk) {
-                    const uint64_t kb = (uint64_t)((2 * kk * C::IPLANE) >> 4);
-                    const uint64_t dbi = bint0 + boff + kb, dbh = bhi0 + boff + kb;
+                    for (int kk = 0; kk < C::KSTEP; ++kk) {
+                        const uint64_t kb = (uint64_t)((2 * kk * C::IPLANE) >> 4);
 #pragma unroll
-                    for (int mt = 0; mt < C::MT; ++mt) {
-                        const uint64_t da = a0 + (uint64_t)(((size_t)s * 2 * C::APART + mt * 16 * C::KCH * 128 + 2 * kk * 128) >> 4);
-                        const uint32_t d1 = dset + (uint32_t)(mt * 3 * C::N), d2 = d1 + (uint32_t)(2 * C::N);
-                        const uint32_t acc = (bi | kk) ? 1u : 0u;
-                        if (split) {
-                            umma_bf16(d1, da, dbi, id2n, acc);
-                            umma_bf16(d2, da + alo_off, dbh, idn, acc);
-                        } else {
-                            umma_bf16(d2, da, dbh, idn, acc);
+                        for (int mt = 0; mt < C::MT; ++mt) {
+                            const uint64_t da = ahi + (uint64_t)((mt * 16 * C::KCH * 128 + 2 * kk * 128) >> 4);
+                            const uint32_t dm = dset + (uint32_t)(mt * C::N);
+                            umma_bf16(dm, da, bhi + kb, idesc, (first && kk == 0) ? 0u : 1u);
+                            if (split) {
+                                umma_bf16(dm, da, blo + kb, idesc, 1u);
+                                umma_bf16(dm, da + alo_off, bhi + kb, idesc, 1u);
+                            }
                         }
                     }
+                    first = false;
+                    umma_commit(&aempty[s]);  // stage s is free once these MMAs have read it
                 }
-                if (s % C::G == C::G - 1) umma_commit(&aempty[s / C::G]);  // the group's stages are free once read
+                if (!ok) break;
+                umma_commit(&hfree[hb]);  // the class halo may be restaged
+                ++hg;
             }
-            umma_commit(&dfull[td]);  // accumulator set td holds tile i
-            umma_commit(&bfree[ts]);  // halo buffer ts may be restaged
+            if (!ok) break;
+            umma_commit(&dfull[d]);  // accumulator d holds segment i
         }
         if (!ok) atomicOr(err, DEV_ERR_TIMEOUT);
+        // before the TMEM is freed, every MMA issued here must have completed (also after a timeout)
+        umma_commit(mdone);
+        if (!mbar_wait(mdone, 0)) atomicOr(err, DEV_ERR_TIMEOUT);
     } else if (warp >= kStageWarp0 && warp < kStageWarp0 + kStageWarps) {
-        // ---------------- halo staging ----------------
+        // ---------------- class-halo staging ----------------
         constexpr int NST = 32 * kStageWarps;
         const int st = tid - 32 * kStageWarp0;
-        for (int i = 0; i < ntiles; ++i) {
-            const int ts = i % C::NBUF;
-            if (i >= C::NBUF && !mbar_wait(&bfree[ts], (uint32_t)(((i / C::NBUF) - 1) & 1), 256)) {
-                atomicOr(err, DEV_ERR_TIMEOUT);
-                break;
-            }
-            const TcTile g = tc_tile<P>(job, (int)blockIdx.x + i * (int)gridDim.x);
-            unsigned char* bb = bbuf + (size_t)ts * C::BBUF;
-            if (maps.use_tma[g.li]) {
-                // one TMA box: {HX columns x 8 bf16 (160 contiguous bytes), 2 parts, HY rows, 4 KCH planes},
-                // zero-filled outside the level; x = 8 (PX0 - 1) elements is a multiple of 16 bytes
-                if (st == 0) {
-                    mbar_expect_tx(&bfull[ts], (uint32_t)C::BBUF);
-                    tma_load_4d(bb, &maps.map[g.li], 8 * (g.PX0 - 1), 0, g.PY0 - 1, 0, &bfull[ts]);
+        // the planes come from the pre-pass launched just before this grid: wait for it to
+        // complete (a no-op when this grid was not launched as its programmatic dependent)
+        asm volatile("griddepcontrol.wait;" ::: "memory");
+        int hg = 0;
+        // per buffer: phase parity of a tensor copy not yet known to have landed, or -1 (a
+        // successful wait for the buffer's release implies its previous fill landed)
+        int pend[C::NHB];
+#pragma unroll
+        for (int b = 0; b < C::NHB; ++b) pend[b] = -1;
+        bool ok = true;
+        for (int i = 0; i < nseg && ok; ++i) {
+            const TcSeg sg = tc_seg(u0, u1, i);
+            const TcTile tl = tc_tile(job, sg.t);
+            for (int u = sg.sa; u < sg.sb;) {
+                const int cls = (u & 31) >> 3;
+                u = min(sg.sb, sg.t * kTcBlocks + (cls + 1) * 8);
+                const int hb = hg % C::NHB;
+                bool w = true;
+                if (hg >= C::NHB) w = mbar_wait(&hfree[hb], (uint32_t)(((hg / C::NHB) - 1) & 1), 256);
+                if (!bar_and(kStageBar, NST, w)) {
+                    ok = false;
+                    break;
                 }
-                continue;
-            }
-            const size_t row = (size_t)g.np * 16;
-            const int units = 2 * 4 * C::KCH * C::NPOS;  // 16-byte halo units
-            for (int it = st; it < units; it += NST) {
-                const int pos = it % C::NPOS;
-                const int pc = it / C::NPOS;  // (part, cc)
-                const int part = pc / (4 * C::KCH), cc = pc % (4 * C::KCH);
-                const int hx = pos % C::HX, hy = pos / C::HX;
-                int qx = g.PX0 - 1 + hx, qy = g.PY0 - 1 + hy;  // source parent
-                bool in = qx >= 0 && qy >= 0 && qx < g.np && qy < g.np;
-                if (job.periodic) {
-                    qx = (qx + g.np) % g.np;
-                    qy = (qy + g.np) % g.np;
-                    in = true;
+                if (hg >= C::NHB) pend[hb] = -1;
+                unsigned char* buf = hbuf + (size_t)hb * C::HBUF;
+                if (maps.use_tma[tl.li]) {
+                    // one TMA box: {HX columns x 8 bf16 (contiguous), 2 parts, HY rows, KCH chunks of class cls},
+                    // zero-filled outside the level; x = 8 (PX0 - 1) elements is a multiple of 16 bytes
+                    if (st == 0) {
+                        mbar_expect_tx(&hfull[hb], (uint32_t)C::HBUF);
+                        tma_load_4d(buf, &maps.map[tl.li], 8 * (tl.PX0 - 1), 0, tl.PY0 - 1, cls * C::KCH, &hfull[hb]);
+                        pend[hb] = (hg / C::NHB) & 1;
+                    }
+                } else {
+                    const size_t row = (size_t)tl.np * 16;
+                    const int nu = 2 * C::KCH * C::NPOS;  // 16-byte halo units of one class
+                    for (int it = st; it < nu; it += NST) {
+                        const int pos = it % C::NPOS;
+                        const int pc = it / C::NPOS;  // (part, chunk)
+                        const int part = pc / C::KCH, ch = pc % C::KCH;
+                        const int hx = pos % C::HX, hy = pos / C::HX;
+                        int qx = tl.PX0 - 1 + hx, qy = tl.PY0 - 1 + hy;  // source parent
+                        bool in = qx >= 0 && qy >= 0 && qx < tl.np && qy < tl.np;
+                        if (job.periodic) {
+                            qx = ((qx % tl.np) + tl.np) % tl.np;
+                            qy = ((qy % tl.np) + tl.np) % tl.np;
+                            in = true;
+                        }
+                        const int cc = cls * C::KCH + ch;
+                        const unsigned char* src =
+                            in ? tl.planes + (((size_t)cc * tl.np + qy) * 2 + part) * row + (size_t)qx * 16 : tl.planes;
+                        cp_async16(buf + (size_t)ch * C::IPLANE + (size_t)(2 * hy + part) * C::ROWB + (size_t)hx * 16,
+                                   src, in);
+                    }
+                    asm volatile("cp.async.commit_group;\n" ::: "memory");
+                    asm volatile("cp.async.wait_all;\n" ::: "memory");
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    asm volatile("bar.sync %0, %1;" ::"n"(kStageCopyBar), "n"(NST) : "memory");
+                    if (st == 0) mbar_arrive(&hfull[hb]);
                 }
-                const unsigned char* src =
-                    in ? g.planes + (((size_t)cc * g.np + qy) * 2 + part) * row + (size_t)qx * 16 : g.planes;
-                cp_async16(bb + (size_t)cc * C::IPLANE + (size_t)(2 * hy + part) * C::ROWB + (size_t)hx * 16, src, in);
+                ++hg;
             }
-            asm volatile("cp.async.commit_group;\n" ::: "memory");
-            asm volatile("cp.async.wait_all;\n" ::: "memory");
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            asm volatile("bar.sync 1, %0;" ::"n"(NST) : "memory");
-            if (st == 0) mbar_arrive(&bfull[ts]);
         }
+        if (!ok && st == 0) atomicOr(err, DEV_ERR_TIMEOUT);
+        // do not leave while a tensor copy is in flight (it lands whether or not the MMAs consume it)
+        if (st == 0)
+            for (int b = 0; b < C::NHB; ++b)
+                if (pend[b] >= 0 && !mbar_wait(&hfull[b], (uint32_t)pend[b])) atomicOr(err, DEV_ERR_TIMEOUT);
     } else if (warp >= kEpiWarp0) {
         // ---------------- epilogue ----------------
+        // A tile cut between CTAs: the part holding its first unit (the head, always the
+        // first segment its CTA processes) stores into L and then publishes the tile's flag;
+        // every other part waits for that flag (published early by a lower CTA) and adds
+        // its sums with fire-and-forget reductions.
         const int q4 = warp - kEpiWarp0;  // TMEM lane quarter (= warp % 4)
-        for (int i = 0; i < ntiles; ++i) {
-            const int td = i % C::NACC;
-            const bool fin = mbar_wait(&dfull[td], (uint32_t)((i / C::NACC) & 1), 256);
-            if (!fin) {
-                if (lane == 0) atomicOr(err, DEV_ERR_TIMEOUT);
+        const uint32_t lanes = (uint32_t)(q4 * 32) << 16;
+        for (int i = 0; i < nseg; ++i) {
+            const TcSeg sg = tc_seg(u0, u1, i);
+            const int d = i % C::NACC;
+            const bool fin = mbar_wait(&dfull[d], (uint32_t)((i / C::NACC) & 1), 256);
+            if (!bar_and(kEpiBar, 128, fin)) {
+                if (q4 == 0 && lane == 0) atomicOr(err, DEV_ERR_TIMEOUT);
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const TcTile g = tc_tile<P>(job, (int)blockIdx.x + i * (int)gridDim.x);
-            const uint32_t lanes = (uint32_t)(q4 * 32) << 16;
+            const TcTile tl = tc_tile(job, sg.t);
+            const bool head = sg.sa == sg.t * kTcBlocks;
+            const bool whole = head && sg.sb == (sg.t + 1) * kTcBlocks;
+            if (!head) {
+                bool got = true;
+                if (lane == 0) got = wait_flag(flags + sg.t);
+                got = __shfl_sync(0xffffffffu, got ? 1 : 0, 0) != 0;
+                if (got) {  // every lane's own acquire of the published flag
+                    int v;
+                    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(flags + sg.t) : "memory");
+                    (void)v;
+                } else if (lane == 0) {
+                    atomicOr(err, DEV_ERR_TIMEOUT);
+                }
+            }
+            // a tile row (8 parents) of one output row lands in 8 boxes 2 apart: one base pointer per
+            // tile row, the columns at constant offsets; rows and columns outside the level are clipped
+            const int xlim = min(kTcTileX, tl.np - tl.PX0), ylim = min(kTcTileY, tl.np - tl.PY0);
+            const size_t ystride = (size_t)4 * tl.side * P;  // floats between tile rows (two box rows)
+            constexpr int XS = 4 * P;                         // floats between neighbouring parents' boxes
 #pragma unroll 1
             for (int mt = 0; mt < C::MT; ++mt) {
                 const int R = mt * 128 + q4 * 32 + lane;  // output row (c, n, re/im)
                 const bool valid_row = R < 8 * P;
-                const int c = R / (2 * P), q = R % (2 * P);
-                const uint32_t d1 = tmem + lanes + (uint32_t)(td * C::SETCOLS + mt * 3 * C::N);
-                const uint32_t d2 = d1 + (uint32_t)(2 * C::N);
+                const int c = valid_row ? R / (2 * P) : 0, q = R % (2 * P);
+                float* base = reinterpret_cast<float*>(tl.L + ((size_t)(2 * tl.PY0 + (c >> 1)) * tl.side +
+                                                               2 * tl.PX0 + (c & 1)) * P) + q;
+                const uint32_t dcol = tmem + lanes + (uint32_t)(d * C::DCOLS + mt * C::N);
 #pragma unroll 1
-                for (int y2 = 0; y2 < C::TPY / 2; ++y2) {  // two tile rows = 16 parents per round
-                    uint32_t a0[16], a1[16], b[16];
-                    tmem_ld16_async(d2 + (uint32_t)(16 * y2), b);  // D2 columns of tile rows 2y2, 2y2+1
-                    if (split) {
-                        tmem_ld16_async(d1 + (uint32_t)(32 * y2), a0);       // row 2y2: hi cols 0-7, lo cols 8-15
-                        tmem_ld16_async(d1 + (uint32_t)(32 * y2 + 16), a1);  // row 2y2+1
-                    }
+                for (int j0 = 0; j0 < C::N && j0 / kTcTileX < ylim; j0 += 32) {
+                    uint32_t r[32];
+                    tmem_ld16_async(dcol + (uint32_t)j0, *reinterpret_cast<uint32_t(*)[16]>(&r[0]));
+                    tmem_ld16_async(dcol + (uint32_t)(j0 + 16), *reinterpret_cast<uint32_t(*)[16]>(&r[16]));
                     tmem_wait_ld();
                     if (!valid_row) continue;
 #pragma unroll
-                    for (int jj = 0; jj < 16; ++jj) {
-                        const int yy = 2 * y2 + (jj >> 3), xx = jj & 7;
-                        float v = __uint_as_float(b[jj]);
-                        if (split) {
-                            const uint32_t* a = (jj >> 3) ? a1 : a0;
-                            v += __uint_as_float(a[xx]) + __uint_as_float(a[8 + xx]);
+                    for (int yy = 0; yy < 4; ++yy) {
+                        const int y = j0 / kTcTileX + yy;
+                        if (y >= ylim) break;
+                        float* b = base + (size_t)y * ystride;
+                        if (xlim == kTcTileX) {
+                            if (head) {
+                                if (job.accumulate) {
+                                    float old[kTcTileX];
+#pragma unroll
+                                    for (int x = 0; x < kTcTileX; ++x) old[x] = b[x * XS];
+#pragma unroll
+                                    for (int x = 0; x < kTcTileX; ++x) b[x * XS] = old[x] + __uint_as_float(r[8 * yy + x]);
+                                } else {
+#pragma unroll
+                                    for (int x = 0; x < kTcTileX; ++x) b[x * XS] = __uint_as_float(r[8 * yy + x]);
+                                }
+                            } else {
+#pragma unroll
+                                for (int x = 0; x < kTcTileX; ++x) atomicAdd(b + x * XS, __uint_as_float(r[8 * yy + x]));
+                            }
+                        } else {
+#pragma unroll
+                            for (int x = 0; x < kTcTileX; ++x) {
+                                if (x >= xlim) break;
+                                const float o = __uint_as_float(r[8 * yy + x]);
+                                if (!head) atomicAdd(b + x * XS, o);
+                                else b[x * XS] = job.accumulate ? o + b[x * XS] : o;
+                            }
                         }
-                        const int px = g.PX0 + xx, py = g.PY0 + yy;
-                        if (px >= g.np || py >= g.np) continue;
-                        const int ix = 2 * px + (c & 1), iy = 2 * py + (c >> 1);
-                        float* dst = reinterpret_cast<float*>(g.L + ((size_t)iy * g.side + ix) * P) + q;
-                        if (job.accumulate) v += *dst;
-                        *dst = v;
                     }
                 }
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
-            if (lane == 0) mbar_arrive(&dfree[td]);
+            if (lane == 0) mbar_arrive(&dfree[d]);
+            if (head && !whole) {
+                // publish the head: every writer's stores, then one release of the tile's flag
+                __threadfence();
+                asm volatile("bar.sync %0, %1;" ::"n"(kPubBar), "n"(128) : "memory");
+                if (q4 == 0 && lane == 0)
+                    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(flags + sg.t), "r"(1) : "memory");
+            }
         }
     }
 
@@ -502,6 +642,15 @@ __global__ void __launch_bounds__(kTcCtaThreads, 1) m2l_tc_kernel(M2LLaunch job,
     if (warp == kMmaWarp)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)C::TMEM_COLS)
                      : "memory");
+    // the last CTA to finish clears the flags and the counter for the next launch
+    if (tid == 0) {
+        __threadfence();
+        if (atomicAdd(done, 1) == grid - 1) {
+            for (int j = 0; j < (units >> 5); ++j) flags[j] = 0;
+            __threadfence();
+            atomicExch(done, 0);
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -564,7 +713,7 @@ static int launch_tc_p(M2LLaunch& job, const void* img, bool split, int* err, cu
     for (int i = 0; i < job.nlev; ++i) {
         job.lv[i].tile_begin = total;
         const int np = 1 << (job.lv[i].level - 1);
-        total += ((np + kTcTileX - 1) / kTcTileX) * ((np + C::TPY - 1) / C::TPY);
+        total += ((np + kTcTileX - 1) / kTcTileX) * ((np + kTcTileY - 1) / kTcTileY);
     }
     if (total == 0) return FMM_OK;
     int sms = 0;
@@ -583,6 +732,13 @@ static int launch_tc_p(M2LLaunch& job, const void* img, bool split, int* err, cu
         job.lv[i].planes = ws;
         ws += ((size_t)1 << (2 * job.lv[i].level)) * (size_t)P * 8;
     }
+    const int units = total * kTcBlocks;
+    int grid = units / kTcMinUnits;
+    grid = grid < 1 ? 1 : (grid > sms ? sms : grid);
+    int* flags = nullptr;
+    if ((rc = tc_flag_workspace(total, &flags))) return rc;
+    int* ctr = nullptr;
+    if ((rc = tile_counter(&ctr, st))) return rc;
     me_planes_kernel<P><<<(unsigned)((items + 255) / 256), 256, 0, st>>>(job, split ? 1 : 0);
     FMM_CUDA_TRY(cudaGetLastError());
     TcMaps maps;
@@ -591,10 +747,11 @@ static int launch_tc_p(M2LLaunch& job, const void* img, bool split, int* err, cu
     for (int i = 0; i < job.nlev; ++i) {
         const int np = 1 << (job.lv[i].level - 1);
         if (!encode || job.periodic || np < C::HX || np < C::HY) continue;  // halo larger than the level: cp.async path
-        // planes [cc][qy][part][qx][8 bf16]: (qx, 8) merge into one contiguous dimension of 8 np elements
+        // planes [cc][qy][part][qx][8 bf16]: (qx, 8) merge into one contiguous dimension of 8 np elements;
+        // one box = the KCH chunk planes of one class
         const cuuint64_t dims[4] = {(cuuint64_t)np * 8, 2, (cuuint64_t)np, (cuuint64_t)(4 * C::KCH)};
         const cuuint64_t strides[3] = {(cuuint64_t)np * 16, (cuuint64_t)np * 32, (cuuint64_t)np * np * 32};
-        const cuuint32_t box[4] = {(cuuint32_t)(8 * C::HX), 2, (cuuint32_t)C::HY, (cuuint32_t)(4 * C::KCH)};
+        const cuuint32_t box[4] = {(cuuint32_t)(8 * C::HX), 2, (cuuint32_t)C::HY, (cuuint32_t)C::KCH};
         const cuuint32_t estr[4] = {1, 1, 1, 1};
         const CUresult r = encode(&maps.map[i], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)job.lv[i].planes, dims,
                                   strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -604,10 +761,20 @@ static int launch_tc_p(M2LLaunch& job, const void* img, bool split, int* err, cu
     }
     static unsigned long long opted;
     if ((rc = smem_opt_in((const void*)m2l_tc_kernel<P>, (int)C::smem, &opted))) return rc;
-    const int grid = total < sms ? total : sms;
-    m2l_tc_kernel<P><<<grid, kTcCtaThreads, C::smem, st>>>(job, maps, (const unsigned char*)img, split ? 1 : 0, total,
-                                                            err);
-    FMM_CUDA_TRY(cudaGetLastError());
+    // launched as the pre-pass's programmatic dependent: the set-up and the operator stream
+    // overlap the pre-pass's tail, and the halo staging waits for the planes
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kTcCtaThreads);
+    cfg.dynamicSmemBytes = C::smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    FMM_CUDA_TRY(cudaLaunchKernelEx(&cfg, m2l_tc_kernel<P>, job, maps, (const unsigned char*)img, split ? 1 : 0, units,
+                                    flags, ctr + 1, err));
     return FMM_OK;
 }
 
