@@ -66,8 +66,6 @@ struct DeviceState {
     std::map<int, M2LTables*> m2l;
     float* fgt_ws = nullptr;  // FGT H2T intermediate (grown on demand)
     size_t fgt_ws_bytes = 0;
-    unsigned char* tc_planes = nullptr;  // tensor-core M2L: BF16 hi/lo copies of the MEs (grown on demand)
-    size_t tc_planes_bytes = 0;
     int* tc_flags = nullptr;  // tensor-core M2L: one flag per tile, zero between launches (grown on demand)
     int tc_flag_count = 0;
     int sm_count = 0;
@@ -161,26 +159,6 @@ int fgt_flag_buffer(unsigned char** out)
     if (rc) return rc;
     if (!s->fgt_flags) FMM_CUDA_TRY(cudaMalloc(&s->fgt_flags, kFgtScratchBytes));
     *out = s->fgt_flags;
-    return FMM_OK;
-}
-
-int tc_plane_workspace(size_t bytes, unsigned char** out)
-{
-    std::lock_guard<std::mutex> lk(g_mu);
-    DeviceState* s = nullptr;
-    int rc = current_state(&s);
-    if (rc) return rc;
-    if (s->tc_planes_bytes < bytes) {
-        if (s->tc_planes) {
-            FMM_CUDA_TRY(cudaDeviceSynchronize());
-            cudaFree(s->tc_planes);
-            s->tc_planes = nullptr;
-            s->tc_planes_bytes = 0;
-        }
-        FMM_CUDA_TRY(cudaMalloc(&s->tc_planes, bytes));
-        s->tc_planes_bytes = bytes;
-    }
-    *out = s->tc_planes;
     return FMM_OK;
 }
 

@@ -138,7 +138,6 @@ struct M2LLevel {
     float2* L;                // [4^level][p] scaled LEs
     int level;
     int tile_begin;           // first CTA of this level (filled by the launcher)
-    unsigned char* planes;    // tensor-core path: BF16 hi/lo planes of M (library scratch)
     const uint8_t* exists;    // adaptive level: [4^level] box existence, NULL = every box exists
     const int32_t* tiles;     // adaptive level: the tiles to run (ntiles of them), NULL = all
     int ntiles;
@@ -171,7 +170,6 @@ size_t m2l_tc_image_bytes(int p);
 int launch_build_tc_image(int p, double s, int variant, void* img, cudaStream_t st);
 int launch_m2l_tc(M2LLaunch& job, int p, const void* img, bool split, cudaStream_t st);
 int get_tc_image(int p, int variant, const void** out);
-int tc_plane_workspace(size_t bytes, unsigned char** out);
 // Per-device flags of the tensor-core M2L, one per tile (zero between
 // launches; grown on demand, zeroed when allocated).
 int tc_flag_workspace(int ntiles, int** flags);

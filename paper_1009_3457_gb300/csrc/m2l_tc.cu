@@ -52,17 +52,18 @@
 // warps (eight at p = 16, two at p = 24, one ring stage and one bulk copy in
 // flight each) stream the operator blocks of the range; an MMA thread (warp
 // 8, which also owns the TMEM allocation) issues the products; three staging
-// warps (9-11) load the class halos into two buffers (one TMA tensor copy of
-// the BF16 hi/lo planes that a pre-pass writes, or cp.async where a level is
-// too small for the tensor map or the lists are periodic); four epilogue
-// warps (12-15) drain the accumulators.  Every mbarrier and flag wait is
-// bounded: on timeout the waiting role records FMM_ETIMEOUT in the device
-// error word and stops; producers wait (bounded) for their own copies in
-// flight, and the TMEM is freed before the CTA exits.
+// warps (9-11) build the class halos in two shared-memory buffers, reading
+// the FP32 MEs and writing their BF16 hi/lo parts in the layout the MMAs read
+// (no pre-pass, no copy of the MEs in global memory); four epilogue warps
+// (12-15) drain the accumulators.  Every mbarrier and flag wait is bounded:
+// on timeout the waiting role records FMM_ETIMEOUT in the device error word
+// and stops; producers wait (bounded) for their own copies in flight, the
+// MMA thread for its own MMAs, and the TMEM is freed before the CTA exits.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
+#include <cstring>
 #include <mutex>
 
 #include "common.cuh"
@@ -91,14 +92,15 @@ struct TcCfg {
     static constexpr int HBUF = KCH * IPLANE;         // one class halo (hi and lo)
     static constexpr int APART = MT * 128 * K2 * 2;   // one block's hi (or lo) operator image
     static constexpr int STAGE = 2 * APART;           // a ring stage: hi then lo
-    static constexpr int NHB = 2;                     // class halo buffers
+    static constexpr int NHB = P <= 16 ? 2 : 1;       // class halo buffers (BF16 hi/lo)
+    static constexpr int LBUF = NPOS * K2 * 4;        // the FP32 landing buffer of one class halo
     // ring stages, one producer warp each: as many as shared memory holds
     // beside the halo buffers (8 x 16 KB at p = 16, 2 x 48 KB at p = 24)
-    static constexpr int STAGES = P <= 16 ? 8 : 2;
+    static constexpr int STAGES = P <= 16 ? 6 : 2;
     static constexpr int DCOLS = MT * N;              // TMEM columns of one accumulator
     static constexpr int NACC = 2 * DCOLS <= 512 ? 2 : 1;
     static constexpr int TMEM_COLS = 512;
-    static constexpr size_t smem = (size_t)NHB * HBUF + (size_t)STAGES * STAGE + 1024;
+    static constexpr size_t smem = (size_t)NHB * HBUF + (size_t)LBUF + (size_t)STAGES * STAGE + 1024;
     static_assert(STAGES <= 8, "producer warps 0-7");
     static_assert(smem <= 232448, "dynamic shared memory");
     static_assert(DCOLS * NACC <= TMEM_COLS, "TMEM");
@@ -174,66 +176,6 @@ __global__ void build_tc_image_kernel(double s, int variant, unsigned char* __re
 // halo serves 8 consecutive units); the image stores block b = pe * 4 + c'
 __host__ __device__ inline int tc_image_block(int blk) { return (blk & 7) * 4 + (blk >> 3); }
 
-// tensor-map load (the other PTX helpers are in tc_ptx.cuh)
-__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
-                                            uint64_t* bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(
-            su32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(su32(bar))
-        : "memory");
-}
-
-// ---------------------------------------------------------------------------
-// pre-pass: every level's MEs -> BF16 hi/lo planes laid out so that a tile's
-// halo is one TMA box that lands in exactly the shared-memory layout the MMAs
-// read: [cc = class * KCH + chunk][parent row qy][part: hi, lo][parent column qx]
-// x 16 bytes (a chunk = 8 consecutive real coefficients of a box)
-// ---------------------------------------------------------------------------
-template <int P>
-__global__ void me_planes_kernel(M2LLaunch job, int split)
-{
-    // one thread per 16-byte unit of a plane row, consecutive threads along qx: the
-    // stores are coalesced, each thread reads one 32-byte chunk of one box
-    using C = TcCfg<P>;
-    // the translation kernel may start now: only its halo staging reads the planes, after
-    // it has waited for this grid to complete (griddepcontrol.wait)
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int li = 0;
-    for (; li < job.nlev; ++li) {
-        const int64_t n = ((int64_t)1 << (2 * job.lv[li].level)) * C::KCH;
-        if (idx < n) break;
-        idx -= n;
-    }
-    if (li >= job.nlev) return;
-    const M2LLevel& lv = job.lv[li];
-    const int side = 1 << lv.level, np = side >> 1;
-    const int qx = (int)(idx % np);
-    const int64_t t = idx / np;
-    const int qy = (int)(t % np), cc = (int)(t / np);  // cc = class * KCH + chunk
-    const int c = cc / C::KCH, ch = cc % C::KCH;
-    const int ix = 2 * qx + (c & 1), iy = 2 * qy + (c >> 1);
-    const float4* src = reinterpret_cast<const float4*>(lv.M) + ((int64_t)iy * side + ix) * (P / 2) + 2 * ch;
-    const float4 v0 = __ldg(src), v1 = __ldg(src + 1);
-    const float f[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
-    uint32_t h[4], l[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        __nv_bfloat162 hv = __floats2bfloat162_rn(f[2 * j], f[2 * j + 1]);
-        const float2 hf = __bfloat1622float2(hv);
-        h[j] = *reinterpret_cast<uint32_t*>(&hv);
-        l[j] = pack_bf16(f[2 * j] - hf.x, f[2 * j + 1] - hf.y);
-    }
-    const size_t row = (size_t)np * 16;  // one (cc, qy, part) row of np positions
-    const size_t off = ((size_t)cc * np + qy) * 2 * row + (size_t)qx * 16;
-    *reinterpret_cast<uint4*>(lv.planes + off) = make_uint4(h[0], h[1], h[2], h[3]);
-    *reinterpret_cast<uint4*>(lv.planes + off + row) = make_uint4(l[0], l[1], l[2], l[3]);
-    (void)split;
-}
-
-
 // ---------------------------------------------------------------------------
 // the kernel: persistent, one CTA per SM, warp-specialised, stream-K ranges
 // ---------------------------------------------------------------------------
@@ -241,11 +183,12 @@ __global__ void me_planes_kernel(M2LLaunch job, int split)
 // 12-15 epilogue (a multiple of 4, so that warp % 4 is its TMEM lane quarter)
 constexpr int kTcCtaThreads = 512;
 constexpr int kMmaWarp = 8, kStageWarp0 = 9, kStageWarps = 3, kEpiWarp0 = 12;
+constexpr int kStageBatch = 5;  // halo items in flight per staging thread
 // named barriers: staging warps (wait outcome; cp.async completion), epilogue warps (wait outcome; publish)
 constexpr int kStageBar = 1, kStageCopyBar = 2, kEpiBar = 3, kPubBar = 4;
 
 struct TcTile {
-    const unsigned char* planes;
+    const float4* M;
     float2* L;
     int side, np, PX0, PY0, li;
 };
@@ -256,7 +199,7 @@ __device__ __forceinline__ TcTile tc_tile(const M2LLaunch& job, int tile)
     while (li + 1 < job.nlev && tile >= job.lv[li + 1].tile_begin) ++li;
     const M2LLevel& lv = job.lv[li];
     TcTile g;
-    g.planes = lv.planes;
+    g.M = reinterpret_cast<const float4*>(lv.M);
     g.L = lv.L;
     g.side = 1 << lv.level;
     g.np = g.side >> 1;
@@ -268,10 +211,24 @@ __device__ __forceinline__ TcTile tc_tile(const M2LLaunch& job, int tile)
     return g;
 }
 
+// Per launch level: a 5-D tensor map over its FP32 MEs, [qy][cy][qx][cx][2p floats]
+// (box (2 qx + cx, 2 qy + cy)), so that one box {2p, 1, 10, 1, 34} at (0, c'x,
+// PX0 - 1, c'y, PY0 - 1) is the class-c' halo of a tile, zero outside the level.
 struct TcMaps {
-    CUtensorMap map[kMaxLaunchLevels];  // per launch level: 4-D map over its planes (when use_tma)
-    int use_tma[kMaxLaunchLevels];
+    CUtensorMap map[kMaxLaunchLevels];
+    int use_tma[kMaxLaunchLevels];  // 0: the level is smaller than the box, or the lists are periodic
 };
+
+// tensor-map load into this CTA's shared memory, completion on an mbarrier
+__device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3, int c4,
+                                            uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
+        "%6}], [%7];" ::"r"(su32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(su32(bar))
+        : "memory");
+}
 
 // first unit of CTA j's range: the U units in `grid` equal contiguous shares
 __device__ __forceinline__ int tc_range_begin(int j, int grid, int units)
@@ -294,6 +251,41 @@ __device__ __forceinline__ TcSeg tc_seg(int u0, int u1, int i)
     return s;
 }
 __device__ __forceinline__ int tc_nseg(int u0, int u1) { return u1 > u0 ? ((u1 - 1) >> 5) - (u0 >> 5) + 1 : 0; }
+
+// class group k (0-based, in walk order) of the range [u0, u1): its tile and source class
+__device__ __forceinline__ bool tc_group(int u0, int u1, int k, int& t, int& cls)
+{
+    const int nseg = tc_nseg(u0, u1);
+    for (int i = 0; i < nseg; ++i) {
+        const TcSeg sg = tc_seg(u0, u1, i);
+        const int c0 = (sg.sa & 31) >> 3, c1 = ((sg.sb - 1) & 31) >> 3;
+        if (k <= c1 - c0) {
+            t = sg.t;
+            cls = c0 + k;
+            return true;
+        }
+        k -= c1 - c0 + 1;
+    }
+    return false;
+}
+
+
+// One chunk (4 complex = 8 floats) of a source ME -> its BF16 hi part at dst and lo part at dst + lo_off.
+__device__ __forceinline__ void tc_stage_chunk(const float4* a, const float4* b, unsigned char* dst, int lo_off)
+{
+    const float4 v0 = *a, v1 = *b;
+    const float f[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        __nv_bfloat162 hv = __floats2bfloat162_rn(f[2 * j], f[2 * j + 1]);
+        const float2 hf = __bfloat1622float2(hv);
+        h[j] = *reinterpret_cast<uint32_t*>(&hv);
+        l[j] = pack_bf16(f[2 * j] - hf.x, f[2 * j + 1] - hf.y);
+    }
+    *reinterpret_cast<uint4*>(dst) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4*>(dst + lo_off) = make_uint4(l[0], l[1], l[2], l[3]);
+}
 
 // AND of `v` over the `n` threads of named barrier `id` (uniform control flow after a bounded wait)
 __device__ __forceinline__ bool bar_and(int id, int n, bool v)
@@ -327,7 +319,8 @@ __global__ void __launch_bounds__(kTcCtaThreads, 1)
     using C = TcCfg<P>;
     extern __shared__ __align__(1024) unsigned char tsm[];
     unsigned char* hbuf = tsm;                                   // NHB class halos
-    unsigned char* astage = tsm + (size_t)C::NHB * C::HBUF;      // STAGES x (hi APART, lo APART)
+    unsigned char* lbuf = tsm + (size_t)C::NHB * C::HBUF;        // FP32 landing buffer of a class halo
+    unsigned char* astage = lbuf + C::LBUF;                      // STAGES x (hi APART, lo APART)
     uint64_t* afull = reinterpret_cast<uint64_t*>(astage + (size_t)C::STAGES * C::STAGE);
     uint64_t* aempty = afull + C::STAGES;
     uint64_t* hfull = aempty + C::STAGES;
@@ -335,7 +328,8 @@ __global__ void __launch_bounds__(kTcCtaThreads, 1)
     uint64_t* dfull = hfree + C::NHB;
     uint64_t* dfree = dfull + 2;
     uint64_t* mdone = dfree + 2;  // the MMA thread's final commit: every issued MMA has completed
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mdone + 1);
+    uint64_t* lfull = mdone + 1;  // a tensor copy into the landing buffer has landed
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(lfull + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int cta = (int)blockIdx.x, grid = (int)gridDim.x;
@@ -360,6 +354,7 @@ __global__ void __launch_bounds__(kTcCtaThreads, 1)
             mbar_init(&dfree[i], 4);
         }
         mbar_init(mdone, 1);
+        mbar_init(lfull, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == kMmaWarp) {
@@ -469,76 +464,114 @@ __global__ void __launch_bounds__(kTcCtaThreads, 1)
         if (!mbar_wait(mdone, 0)) atomicOr(err, DEV_ERR_TIMEOUT);
     } else if (warp >= kStageWarp0 && warp < kStageWarp0 + kStageWarps) {
         // ---------------- class-halo staging ----------------
+        // The halo of source class c' for a tile: the MEs of boxes (2 qx + c'x, 2 qy + c'y) for the
+        // 10 x 34 parents (qx, qy) around it, zero outside the level (periodic lists wrap), as BF16
+        // hi and lo in the layout the MMAs read: [chunk of 4 complex][halo row][hi, lo][halo
+        // column] x 16 bytes.  Levels at least as large as the box arrive as FP32 by one tensor
+        // copy into the landing buffer (prefetched while the previous class is converted and
+        // translated) and are converted shared-to-shared; smaller levels and periodic lists are
+        // read from global memory.  An item is one (parent, chunk): 32 bytes in, 2 x 16 out.
         constexpr int NST = 32 * kStageWarps;
+        constexpr int NIT = C::KCH * C::NPOS;
         const int st = tid - 32 * kStageWarp0;
-        // the planes come from the pre-pass launched just before this grid: wait for it to
-        // complete (a no-op when this grid was not launched as its programmatic dependent)
-        asm volatile("griddepcontrol.wait;" ::: "memory");
-        int hg = 0;
-        // per buffer: phase parity of a tensor copy not yet known to have landed, or -1 (a
-        // successful wait for the buffer's release implies its previous fill landed)
-        int pend[C::NHB];
-#pragma unroll
-        for (int b = 0; b < C::NHB; ++b) pend[b] = -1;
-        bool ok = true;
-        for (int i = 0; i < nseg && ok; ++i) {
+        int ngrp = 0;
+        for (int i = 0; i < nseg; ++i) {
             const TcSeg sg = tc_seg(u0, u1, i);
-            const TcTile tl = tc_tile(job, sg.t);
-            for (int u = sg.sa; u < sg.sb;) {
-                const int cls = (u & 31) >> 3;
-                u = min(sg.sb, sg.t * kTcBlocks + (cls + 1) * 8);
-                const int hb = hg % C::NHB;
-                bool w = true;
-                if (hg >= C::NHB) w = mbar_wait(&hfree[hb], (uint32_t)(((hg / C::NHB) - 1) & 1), 256);
-                if (!bar_and(kStageBar, NST, w)) {
-                    ok = false;
-                    break;
+            ngrp += (((sg.sb - 1) & 31) >> 3) - ((sg.sa & 31) >> 3) + 1;
+        }
+        // the next tensor copy into the landing buffer: the first group at or after `from` on the TMA path
+        auto issue_tma = [&](int from) -> int {
+            for (int k = from; k < ngrp; ++k) {
+                int t, cls;
+                tc_group(u0, u1, k, t, cls);
+                const TcTile tl = tc_tile(job, t);
+                if (!maps.use_tma[tl.li]) continue;
+                if (st == 0) {
+                    mbar_expect_tx(lfull, (uint32_t)C::LBUF);
+                    tma_load_5d(lbuf, &maps.map[tl.li], 0, cls & 1, tl.PX0 - 1, cls >> 1, tl.PY0 - 1, lfull);
                 }
-                if (hg >= C::NHB) pend[hb] = -1;
-                unsigned char* buf = hbuf + (size_t)hb * C::HBUF;
-                if (maps.use_tma[tl.li]) {
-                    // one TMA box: {HX columns x 8 bf16 (contiguous), 2 parts, HY rows, KCH chunks of class cls},
-                    // zero-filled outside the level; x = 8 (PX0 - 1) elements is a multiple of 16 bytes
-                    if (st == 0) {
-                        mbar_expect_tx(&hfull[hb], (uint32_t)C::HBUF);
-                        tma_load_4d(buf, &maps.map[tl.li], 8 * (tl.PX0 - 1), 0, tl.PY0 - 1, cls * C::KCH, &hfull[hb]);
-                        pend[hb] = (hg / C::NHB) & 1;
-                    }
-                } else {
-                    const size_t row = (size_t)tl.np * 16;
-                    const int nu = 2 * C::KCH * C::NPOS;  // 16-byte halo units of one class
-                    for (int it = st; it < nu; it += NST) {
-                        const int pos = it % C::NPOS;
-                        const int pc = it / C::NPOS;  // (part, chunk)
-                        const int part = pc / C::KCH, ch = pc % C::KCH;
-                        const int hx = pos % C::HX, hy = pos / C::HX;
-                        int qx = tl.PX0 - 1 + hx, qy = tl.PY0 - 1 + hy;  // source parent
-                        bool in = qx >= 0 && qy >= 0 && qx < tl.np && qy < tl.np;
-                        if (job.periodic) {
-                            qx = ((qx % tl.np) + tl.np) % tl.np;
-                            qy = ((qy % tl.np) + tl.np) % tl.np;
-                            in = true;
-                        }
-                        const int cc = cls * C::KCH + ch;
-                        const unsigned char* src =
-                            in ? tl.planes + (((size_t)cc * tl.np + qy) * 2 + part) * row + (size_t)qx * 16 : tl.planes;
-                        cp_async16(buf + (size_t)ch * C::IPLANE + (size_t)(2 * hy + part) * C::ROWB + (size_t)hx * 16,
-                                   src, in);
-                    }
-                    asm volatile("cp.async.commit_group;\n" ::: "memory");
-                    asm volatile("cp.async.wait_all;\n" ::: "memory");
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    asm volatile("bar.sync %0, %1;" ::"n"(kStageCopyBar), "n"(NST) : "memory");
-                    if (st == 0) mbar_arrive(&hfull[hb]);
-                }
-                ++hg;
+                return k;
             }
+            return -1;
+        };
+        int pending = issue_tma(0);  // group whose tensor copy is in flight, or -1
+        int nlanded = 0;             // tensor copies consumed so far (landing-buffer phase)
+        bool ok = true;
+        for (int k = 0; k < ngrp && ok; ++k) {
+            int t, cls;
+            tc_group(u0, u1, k, t, cls);
+            const TcTile tl = tc_tile(job, t);
+            const int hb = k % C::NHB;
+            bool w = true;
+            if (k >= C::NHB) w = mbar_wait(&hfree[hb], (uint32_t)(((k / C::NHB) - 1) & 1), 256);
+            if (pending == k) w = mbar_wait(lfull, (uint32_t)(nlanded & 1), 128) && w;
+            if (!bar_and(kStageBar, NST, w)) {
+                ok = false;
+                break;
+            }
+            unsigned char* buf = hbuf + (size_t)hb * C::HBUF;
+            if (pending == k) {
+                // FP32 [parent][2p] in the landing buffer -> BF16 hi/lo halo
+#pragma unroll 1
+                for (int it0 = st; it0 < NIT; it0 += NST * kStageBatch) {
+#pragma unroll
+                    for (int b = 0; b < kStageBatch; ++b) {
+                        const int it = it0 + b * NST;
+                        if (it >= NIT) break;
+                        const int pos = it / C::KCH, ch = it % C::KCH;
+                        const float4* src = reinterpret_cast<const float4*>(lbuf + (size_t)pos * (C::K2 * 4) + ch * 32);
+                        tc_stage_chunk(src, src + 1,
+                                       buf + (size_t)ch * C::IPLANE + (size_t)(2 * (pos / C::HX)) * C::ROWB +
+                                           (size_t)(pos % C::HX) * 16,
+                                       C::ROWB);
+                    }
+                }
+                ++nlanded;
+            } else {
+#pragma unroll 1
+                for (int it0 = st; it0 < NIT; it0 += NST * kStageBatch) {
+                    float4 v[kStageBatch][2];
+#pragma unroll
+                    for (int b = 0; b < kStageBatch; ++b) {
+                        const int it = it0 + b * NST;
+                        v[b][0] = v[b][1] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (it >= NIT) continue;
+                        const int pos = it / C::KCH, ch = it % C::KCH;
+                        int qx = tl.PX0 - 1 + pos % C::HX, qy = tl.PY0 - 1 + pos / C::HX;  // source parent
+                        if (job.periodic) {
+                            qx = (qx + tl.np) % tl.np;
+                            qy = (qy + tl.np) % tl.np;
+                        } else if (qx < 0 || qy < 0 || qx >= tl.np || qy >= tl.np) {
+                            continue;
+                        }
+                        const int ix = 2 * qx + (cls & 1), iy = 2 * qy + (cls >> 1);
+                        const float4* src = tl.M + ((size_t)iy * tl.side + ix) * (P / 2) + 2 * ch;
+                        v[b][0] = __ldg(src);
+                        v[b][1] = __ldg(src + 1);
+                    }
+#pragma unroll
+                    for (int b = 0; b < kStageBatch; ++b) {
+                        const int it = it0 + b * NST;
+                        if (it >= NIT) break;
+                        const int pos = it / C::KCH, ch = it % C::KCH;
+                        float4 f0 = v[b][0], f1 = v[b][1];
+                        tc_stage_chunk(&f0, &f1,
+                                       buf + (size_t)ch * C::IPLANE + (size_t)(2 * (pos / C::HX)) * C::ROWB +
+                                           (size_t)(pos % C::HX) * 16,
+                                       C::ROWB);
+                    }
+                }
+            }
+            // generic-proxy writes (and, for the landing buffer, reads), next touched by the async
+            // proxy: the MMAs read the halo, the next tensor copy overwrites the landing buffer
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("bar.sync %0, %1;" ::"n"(kStageCopyBar), "n"(NST) : "memory");
+            if (pending == k) pending = issue_tma(k + 1);
+            if (st == 0) mbar_arrive(&hfull[hb]);
         }
         if (!ok && st == 0) atomicOr(err, DEV_ERR_TIMEOUT);
-        // do not leave while a tensor copy is in flight (it lands whether or not the MMAs consume it)
-        if (st == 0)
-            for (int b = 0; b < C::NHB; ++b)
-                if (pend[b] >= 0 && !mbar_wait(&hfull[b], (uint32_t)pend[b])) atomicOr(err, DEV_ERR_TIMEOUT);
+        // do not leave while a tensor copy is in flight (after a timeout one may be)
+        if (pending >= 0 && st == 0 && !mbar_wait(lfull, (uint32_t)(nlanded & 1))) atomicOr(err, DEV_ERR_TIMEOUT);
     } else if (warp >= kEpiWarp0) {
         // ---------------- epilogue ----------------
         // A tile cut between CTAs: the part holding its first unit (the head, always the
@@ -719,19 +752,6 @@ static int launch_tc_p(M2LLaunch& job, const void* img, bool split, int* err, cu
     int sms = 0;
     int rc = device_sm_count(&sms);
     if (rc) return rc;
-    // BF16 hi/lo planes of every level's MEs (library scratch), then the main kernel
-    size_t bytes = 0;
-    int64_t items = 0;
-    for (int i = 0; i < job.nlev; ++i) {
-        bytes += ((size_t)1 << (2 * job.lv[i].level)) * (size_t)P * 8;
-        items += ((int64_t)1 << (2 * job.lv[i].level)) * C::KCH;
-    }
-    unsigned char* ws = nullptr;
-    if ((rc = tc_plane_workspace(bytes, &ws))) return rc;
-    for (int i = 0; i < job.nlev; ++i) {
-        job.lv[i].planes = ws;
-        ws += ((size_t)1 << (2 * job.lv[i].level)) * (size_t)P * 8;
-    }
     const int units = total * kTcBlocks;
     int grid = units / kTcMinUnits;
     grid = grid < 1 ? 1 : (grid > sms ? sms : grid);
@@ -739,42 +759,30 @@ static int launch_tc_p(M2LLaunch& job, const void* img, bool split, int* err, cu
     if ((rc = tc_flag_workspace(total, &flags))) return rc;
     int* ctr = nullptr;
     if ((rc = tile_counter(&ctr, st))) return rc;
-    me_planes_kernel<P><<<(unsigned)((items + 255) / 256), 256, 0, st>>>(job, split ? 1 : 0);
-    FMM_CUDA_TRY(cudaGetLastError());
     TcMaps maps;
     memset(&maps, 0, sizeof(maps));
     PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
     for (int i = 0; i < job.nlev; ++i) {
         const int np = 1 << (job.lv[i].level - 1);
-        if (!encode || job.periodic || np < C::HX || np < C::HY) continue;  // halo larger than the level: cp.async path
-        // planes [cc][qy][part][qx][8 bf16]: (qx, 8) merge into one contiguous dimension of 8 np elements;
-        // one box = the KCH chunk planes of one class
-        const cuuint64_t dims[4] = {(cuuint64_t)np * 8, 2, (cuuint64_t)np, (cuuint64_t)(4 * C::KCH)};
-        const cuuint64_t strides[3] = {(cuuint64_t)np * 16, (cuuint64_t)np * 32, (cuuint64_t)np * np * 32};
-        const cuuint32_t box[4] = {(cuuint32_t)(8 * C::HX), 2, (cuuint32_t)C::HY, (cuuint32_t)C::KCH};
-        const cuuint32_t estr[4] = {1, 1, 1, 1};
-        const CUresult r = encode(&maps.map[i], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)job.lv[i].planes, dims,
-                                  strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+        const int side = 2 * np;
+        if (!encode || job.periodic || np < C::HX || np < C::HY) continue;  // box larger than the level: global loads
+        // MEs [iy][ix][2p floats] read as [qy][cy][qx][cx][2p]: box (2 qx + cx, 2 qy + cy)
+        const cuuint64_t dims[5] = {(cuuint64_t)(2 * P), 2, (cuuint64_t)np, 2, (cuuint64_t)np};
+        const cuuint64_t rowb = (cuuint64_t)side * 2 * P * 4;  // bytes per box row
+        const cuuint64_t strides[4] = {(cuuint64_t)2 * P * 4, (cuuint64_t)4 * P * 4, rowb, 2 * rowb};
+        const cuuint32_t box[5] = {(cuuint32_t)(2 * P), 1, (cuuint32_t)C::HX, 1, (cuuint32_t)C::HY};
+        const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+        const CUresult r = encode(&maps.map[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, (void*)job.lv[i].M, dims, strides,
+                                  box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return fail(FMM_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
         maps.use_tma[i] = 1;
     }
     static unsigned long long opted;
     if ((rc = smem_opt_in((const void*)m2l_tc_kernel<P>, (int)C::smem, &opted))) return rc;
-    // launched as the pre-pass's programmatic dependent: the set-up and the operator stream
-    // overlap the pre-pass's tail, and the halo staging waits for the planes
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)grid);
-    cfg.blockDim = dim3(kTcCtaThreads);
-    cfg.dynamicSmemBytes = C::smem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    FMM_CUDA_TRY(cudaLaunchKernelEx(&cfg, m2l_tc_kernel<P>, job, maps, (const unsigned char*)img, split ? 1 : 0, units,
-                                    flags, ctr + 1, err));
+    m2l_tc_kernel<P><<<grid, kTcCtaThreads, C::smem, st>>>(job, maps, (const unsigned char*)img, split ? 1 : 0, units,
+                                                            flags, ctr + 1, err);
+    FMM_CUDA_TRY(cudaGetLastError());
     return FMM_OK;
 }
 
