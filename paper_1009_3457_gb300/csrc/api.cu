@@ -788,6 +788,8 @@ int fgt_h2t(int32_t grid_log2, int32_t n_cut, int32_t p, double sigma, const flo
     clear_error();
     int rc = fgt_check_args("fgt_h2t", grid_log2, n_cut, p, sigma, A, C, work, flags);
     if (rc) return rc;
+    if (fgt_fused_supported(grid_log2))
+        return launch_fgt_h2t_fused(grid_log2, n_cut, p, sigma, A, C, (flags & FMM_ACCUMULATE) != 0, (cudaStream_t)stream);
     float* Y = work;
     if (!Y) {
         const size_t bytes = ((size_t)1 << (2 * grid_log2)) * (size_t)p * p * sizeof(float);

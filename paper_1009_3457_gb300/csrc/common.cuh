@@ -177,6 +177,9 @@ int tc_flag_workspace(int ntiles, int** flags);
 // launchers (fgt_h2t.cu)
 bool fgt_supported(int p);
 int fgt_max_cut();
+// one launch (thread-block clusters, Y in distributed shared memory) for grids up to 32 x 32
+bool fgt_fused_supported(int g);
+int launch_fgt_h2t_fused(int g, int ncut, int p, double sigma, const float* A, float* C, bool acc, cudaStream_t st);
 int launch_fgt_h2t(int g, int ncut, int p, double sigma, const float* A, float* Y, float* C, bool acc,
                    bool cached_table, cudaStream_t st);
 int fgt_workspace(size_t bytes, float** out);

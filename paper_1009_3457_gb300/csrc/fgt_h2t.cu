@@ -23,12 +23,14 @@
 // scratch (one [4^g][p][p] float buffer per device, grown on demand).
 #include <math.h>
 
+#include <cooperative_groups.h>
 #include <cstring>
 #include <map>
 #include <mutex>
 #include <tuple>
 
 #include "common.cuh"
+#include "tc_ptx.cuh"
 
 namespace fmmgb {
 
@@ -104,6 +106,9 @@ __global__ void __launch_bounds__(FgtCfg<P>::THREADS) fgt_pass_kernel(int g, int
     const int seg0 = blockIdx.x * kFgtSeg;
     const int other = blockIdx.y;
     const int tid = threadIdx.x;
+    // the second pass may be scheduled now: it prepares its tables and waits for this grid
+    // (griddepcontrol.wait) before it reads what this pass writes
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
     // Hermite-function table: the cached copy, or computed here (allocation-free entry point)
     if (htab) {
@@ -116,19 +121,21 @@ __global__ void __launch_bounds__(FgtCfg<P>::THREADS) fgt_pass_kernel(int g, int
         for (int i = 2; i <= b; ++i) f *= (double)i;
         ss[b] = (float)(((b & 1) ? -1.0 : 1.0) / f);
     }
+    // the input may come from the grid launched just before (the first pass): wait for it
+    // (a no-op unless this grid was launched as its programmatic dependent)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     // stage the boxes [seg0 - ncut, seg0 + kFgtSeg + ncut) of this row/column, zero outside the grid
     const int nhb = kFgtSeg + 2 * ncut;
     const float4* in4 = reinterpret_cast<const float4*>(in);
-    for (int i = tid; i < nhb * (P * P / 4); i += blockDim.x) {
+    for (int i = tid; i < nhb * (P * P / 4); i += blockDim.x) {  // every copy in flight before any wait
         const int q = i % (P * P / 4), hb = i / (P * P / 4);
         const int pos = seg0 - ncut + hb;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (pos >= 0 && pos < side) {
-            const size_t box = axis == 0 ? (size_t)other * side + pos : (size_t)pos * side + other;
-            v = __ldg(in4 + box * (P * P / 4) + q);
-        }
-        *reinterpret_cast<float4*>(halo + (size_t)hb * BS + 4 * q) = v;
+        const bool inside = pos >= 0 && pos < side;
+        const size_t box = axis == 0 ? (size_t)other * side + pos : (size_t)pos * side + other;
+        cp_async16(halo + (size_t)hb * BS + 4 * q, inside ? (const void*)(in4 + box * (P * P / 4) + q) : in, inside);
     }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
     __syncthreads();
 
     const int grp = tid / (kFgtSeg * C::TPB);
@@ -266,8 +273,19 @@ static int fgt_launch(int g, int ncut, double ustep, const float* A, float* Y, f
     const dim3 grid((side + kFgtSeg - 1) / kFgtSeg, side);
     fgt_pass_kernel<P><<<grid, C::THREADS, smem, st>>>(g, ncut, ustep, 0, A, Y, 0, htab);
     FMM_CUDA_TRY(cudaGetLastError());
-    fgt_pass_kernel<P><<<grid, C::THREADS, smem, st>>>(g, ncut, ustep, 1, Y, Cout, acc ? 1 : 0, htab);
-    FMM_CUDA_TRY(cudaGetLastError());
+    // the second pass as the first's programmatic dependent: its set-up overlaps the first pass
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(C::THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    FMM_CUDA_TRY(cudaLaunchKernelEx(&cfg, fgt_pass_kernel<P>, g, ncut, ustep, 1, (const float*)Y, Cout, acc ? 1 : 0,
+                                    htab));
     return FMM_OK;
 }
 
@@ -280,6 +298,326 @@ int launch_fgt_h2t(int g, int ncut, int p, double sigma, const float* A, float* 
         case 8: return fgt_launch<8>(g, ncut, ustep, A, Y, Cout, acc, cached_table, st);
         case 12: return fgt_launch<12>(g, ncut, ustep, A, Y, Cout, acc, cached_table, st);
         case 16: return fgt_launch<16>(g, ncut, ustep, A, Y, Cout, acc, cached_table, st);
+        default: return fail(FMM_EINVAL, "fgt_h2t: unsupported p = %d", p);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// One launch for grids up to 32 x 32 boxes (every bandwidth down to
+// sigma = 0.05 with the grid of reading R9): a thread-block cluster owns C
+// columns of the grid and all of its rows, its CTA of rank r the rows
+// [r R, r R + R).  The x-pass writes the CTA's own boxes of Y into its
+// shared memory; after a cluster barrier each CTA copies the Y boxes its
+// y-pass needs (its columns, rows within n_cut of its own) from the other
+// CTAs' shared memory (distributed shared memory), and a second barrier
+// lets every CTA leave once nobody reads its memory.  Y never goes to
+// global memory and there is no second launch.
+// ---------------------------------------------------------------------------
+constexpr int kFusedMaxLog2 = 4;  // 32 x 32: only 8 clusters of 8 are resident at once, two passes are faster
+constexpr int kFusedCluster = 8;    // CTAs per cluster (portable size: a cluster always fits a GPC)
+constexpr int kFusedCopyBatch = 8;  // remote float4 loads in flight per thread
+constexpr size_t kFusedMaxSmem = 232448;  // dynamic shared memory a CTA may opt into (227 KB)
+
+struct FusedShape {
+    int R, C, CS, TG;  // rows and columns per CTA, CTAs per cluster, tap groups
+};
+
+template <int P>
+struct FusedSmem {
+    // float offsets: own Y [R C][BS], staging [max(R (C + 2 ncut), C (R + 2 ncut))][BS],
+    // partial sums [TG - 1][R C][P P], Hermite table [taps][NH], s_b [P]
+    size_t own, stage, part, hs, ss, total;
+    __host__ __device__ FusedSmem(const FusedShape& f, int ncut)
+    {
+        using Cf = FgtCfg<P>;
+        const int nst1 = f.R * (f.C + 2 * ncut), nst2 = f.C * (f.R + 2 * ncut);
+        own = 0;
+        stage = own + (size_t)f.R * f.C * Cf::BS;
+        part = stage + (size_t)(nst1 > nst2 ? nst1 : nst2) * Cf::BS;
+        hs = part + (size_t)(f.TG - 1) * f.R * f.C * P * P;
+        ss = hs + (size_t)(2 * ncut + 1) * Cf::NH;
+        total = ss + P;
+    }
+};
+
+// acc[b][c] = sum over taps d in [d0, d1) of sum_a h_{a+b}(u_d) src(d)[a][c], the 4 x 4 block
+// (b0.., c0..) of one box; src(d) is a shared-memory box or NULL (outside the grid)
+template <int P, typename SrcFn>
+__device__ __forceinline__ void fgt_taps(const float* hs, int b0, int c0, int d0, int d1, SrcFn src, float (&acc)[4][4])
+{
+    using Cf = FgtCfg<P>;
+    constexpr int NH = Cf::NH;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) acc[i][cc] = 0.f;
+    for (int d = d0; d < d1; ++d) {
+        const float* box = src(d);
+        if (!box) continue;
+        const float* hrow = hs + d * NH + b0;
+        const float* in = box + c0;
+        float w[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) w[i] = hrow[i];
+#pragma unroll
+        for (int a = 0; a < P; ++a) {
+            const float4 v = *reinterpret_cast<const float4*>(in + a * P);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                acc[i][0] = fmaf(w[i], v.x, acc[i][0]);
+                acc[i][1] = fmaf(w[i], v.y, acc[i][1]);
+                acc[i][2] = fmaf(w[i], v.z, acc[i][2]);
+                acc[i][3] = fmaf(w[i], v.w, acc[i][3]);
+            }
+            if (a + 1 < P) {
+#pragma unroll
+                for (int i = 0; i < 3; ++i) w[i] = w[i + 1];
+                w[3] = hrow[4 + a];
+            }
+        }
+    }
+}
+
+template <int P>
+__global__ void __launch_bounds__(512) fgt_fused_kernel(int g, int ncut, FusedShape f, const float* __restrict__ A,
+                                                         float* __restrict__ Cout, int accumulate,
+                                                         const float* __restrict__ htab)
+{
+    namespace cg = cooperative_groups;
+    using Cf = FgtCfg<P>;
+    constexpr int BS = Cf::BS, NH = Cf::NH, TPB = Cf::TPB;
+    extern __shared__ __align__(16) float fsm[];
+    cg::cluster_group cl = cg::this_cluster();
+    const FusedSmem<P> L(f, ncut);
+    float* own = fsm + L.own;
+    float* stage = fsm + L.stage;
+    float* part = fsm + L.part;
+    float* hs = fsm + L.hs;
+    float* ss = fsm + L.ss;
+
+    const int n = 1 << g, taps = 2 * ncut + 1;
+    const int rank = (int)cl.block_rank();
+    const int y0 = rank * f.R, x0 = (int)(blockIdx.x / f.CS) * f.C;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int nbox = f.R * f.C;
+
+    // x-pass inputs: rows [y0, y0 + R), columns [x0 - ncut, x0 + C + ncut), zero outside the grid;
+    // every copy is issued before anything waits on one
+    const int w1 = f.C + 2 * ncut;
+    const float4* A4 = reinterpret_cast<const float4*>(A);
+    for (int i = tid; i < f.R * w1 * (P * P / 4); i += nthr) {
+        const int q = i % (P * P / 4), hb = i / (P * P / 4);
+        const int yy = y0 + hb / w1, xx = x0 - ncut + hb % w1;
+        const bool in = xx >= 0 && xx < n;
+        cp_async16(stage + (size_t)hb * BS + 4 * q, in ? (const void*)(A4 + ((size_t)yy * n + xx) * (P * P / 4) + q) : A,
+                   in);
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    for (int i = tid; i < taps * NH; i += nthr) hs[i] = __ldg(htab + i);
+    for (int b = tid; b < P; b += nthr) {
+        float fct = 1.f;
+        for (int i = 2; i <= b; ++i) fct *= (float)i;  // b! exact in FP32 for b <= 13, to 1 ulp beyond
+        ss[b] = ((b & 1) ? -1.f : 1.f) / fct;
+    }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    __syncthreads();
+
+    // thread -> (tap group, box of the CTA, 4 x 4 output block)
+    const int grp = tid / (nbox * TPB), rem = tid % (nbox * TPB);
+    const int j = rem / TPB, r = rem % TPB;
+    const int jr = j / f.C, jc = j % f.C;
+    const int b0 = (r % Cf::RBLK) * 4, c0 = (r / Cf::RBLK) * 4;
+    const int per = (taps + f.TG - 1) / f.TG;
+    const int d0 = grp * per, d1 = min(taps, d0 + per);
+    const bool active = grp < f.TG;
+    float acc[4][4];
+
+    // ---- x-pass: Y[box][c][b] = s_b sum_dx sum_a h_{a+b} A[box + dx][a][c] ----
+    const int x = x0 + jc;
+    if (active) {
+        fgt_taps<P>(hs, b0, c0, d0, d1,
+                    [&](int d) -> const float* {
+                        const int sx = x + d - ncut;
+                        return (sx >= 0 && sx < n) ? stage + (size_t)(jr * w1 + jc + d) * BS : nullptr;
+                    },
+                    acc);
+        if (grp > 0) {
+            float* pp = part + ((size_t)(grp - 1) * nbox + j) * (P * P);
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                *reinterpret_cast<float4*>(pp + (b0 + i) * P + c0) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+        }
+    }
+    __syncthreads();
+    if (active && grp == 0) {
+        for (int q = 0; q < f.TG - 1; ++q) {
+            const float* pp = part + ((size_t)q * nbox + j) * (P * P);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float4 v = *reinterpret_cast<const float4*>(pp + (b0 + i) * P + c0);
+                acc[i][0] += v.x;
+                acc[i][1] += v.y;
+                acc[i][2] += v.z;
+                acc[i][3] += v.w;
+            }
+        }
+        float* dst = own + (size_t)j * BS;
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc)
+            *reinterpret_cast<float4*>(dst + (c0 + cc) * P + b0) =
+                make_float4(ss[b0] * acc[0][cc], ss[b0 + 1] * acc[1][cc], ss[b0 + 2] * acc[2][cc], ss[b0 + 3] * acc[3][cc]);
+    }
+    cl.sync();  // every CTA's Y is in its shared memory
+
+    // ---- y-pass inputs: columns [x0, x0 + C), rows [y0 - ncut, y0 + R + ncut) of Y, from their owners ----
+    const int h2 = f.R + 2 * ncut;
+    const int n2 = f.C * h2 * (P * P / 4);
+    for (int i0 = tid; i0 < n2; i0 += nthr * kFusedCopyBatch) {
+        float4 v[kFusedCopyBatch];  // a batch of remote loads in flight before any store
+#pragma unroll
+        for (int k = 0; k < kFusedCopyBatch; ++k) {
+            const int i = i0 + k * nthr;
+            v[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (i >= n2) continue;
+            const int q = i % (P * P / 4), hb = i / (P * P / 4);
+            const int yy = y0 - ncut + hb / f.C, cc = hb % f.C;
+            if (yy >= 0 && yy < n) {
+                const float* peer = cl.map_shared_rank(own, (unsigned)(yy / f.R));
+                v[k] = *reinterpret_cast<const float4*>(peer + (size_t)((yy % f.R) * f.C + cc) * BS + 4 * q);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kFusedCopyBatch; ++k) {
+            const int i = i0 + k * nthr;
+            if (i >= n2) break;
+            const int q = i % (P * P / 4), hb = i / (P * P / 4);
+            *reinterpret_cast<float4*>(stage + (size_t)hb * BS + 4 * q) = v[k];
+        }
+    }
+    cl.sync();  // nobody reads another CTA's shared memory after this
+
+    // ---- y-pass: C[box][b1][b2] = s_b2 sum_dy sum_a2 h_{a2+b2} Y[box + dy][a2][b1] ----
+    const int y = y0 + jr;
+    if (active) {
+        fgt_taps<P>(hs, b0, c0, d0, d1,
+                    [&](int d) -> const float* {
+                        const int sy = y + d - ncut;
+                        return (sy >= 0 && sy < n) ? stage + (size_t)((jr + d) * f.C + jc) * BS : nullptr;
+                    },
+                    acc);
+        if (grp > 0) {
+            float* pp = part + ((size_t)(grp - 1) * nbox + j) * (P * P);
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                *reinterpret_cast<float4*>(pp + (b0 + i) * P + c0) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+        }
+    }
+    __syncthreads();
+    if (active && grp == 0) {
+        for (int q = 0; q < f.TG - 1; ++q) {
+            const float* pp = part + ((size_t)q * nbox + j) * (P * P);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float4 v = *reinterpret_cast<const float4*>(pp + (b0 + i) * P + c0);
+                acc[i][0] += v.x;
+                acc[i][1] += v.y;
+                acc[i][2] += v.z;
+                acc[i][3] += v.w;
+            }
+        }
+        float* dst = Cout + ((size_t)y * n + x) * (P * P);
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) {
+            float* row = dst + (size_t)(c0 + cc) * P + b0;
+            float4 o = make_float4(ss[b0] * acc[0][cc], ss[b0 + 1] * acc[1][cc], ss[b0 + 2] * acc[2][cc],
+                                   ss[b0 + 3] * acc[3][cc]);
+            if (accumulate) {
+                const float4 old = *reinterpret_cast<const float4*>(row);
+                o.x += old.x;
+                o.y += old.y;
+                o.z += old.z;
+                o.w += old.w;
+            }
+            *reinterpret_cast<float4*>(row) = o;
+        }
+    }
+}
+
+bool fgt_fused_supported(int g) { return g <= kFusedMaxLog2; }
+
+template <int P>
+static int fused_launch(int g, int ncut, double ustep, const float* A, float* Cout, bool acc, cudaStream_t st)
+{
+    using Cf = FgtCfg<P>;
+    const int n = 1 << g, taps = 2 * ncut + 1;
+    const float* htab = nullptr;
+    if (int rc = fgt_table(P, ncut, ustep, &htab)) return rc;
+    // opted into the most a CTA may use; each launch asks for its own shape's need, which the
+    // shape selection below keeps within that limit
+    static unsigned long long opted;
+    if (int rc = smem_opt_in((const void*)fgt_fused_kernel<P>, (int)kFusedMaxSmem, &opted)) return rc;
+    // shape: the cluster holds every row (R rows per CTA); C columns per cluster, the fewest that
+    // let every cluster be resident at once (about 128 CTAs when they fit)
+    FusedShape f;
+    f.R = n > kFusedCluster ? n / kFusedCluster : 1;
+    f.CS = n / f.R;
+    for (f.C = n >= 32 ? 2 : 1;; f.C *= 2) {
+        const int pt = f.R * f.C * Cf::TPB;
+        f.TG = 512 / pt;
+        if (f.TG > taps) f.TG = taps;
+        if (f.TG < 1) f.TG = 1;
+        if (f.C >= n) break;
+        {  // a wider shape must still fit the shared memory of an SM
+            FusedShape w = f;
+            w.C *= 2;
+            w.TG = 512 / (w.R * w.C * Cf::TPB);
+            w.TG = w.TG > taps ? taps : (w.TG < 1 ? 1 : w.TG);
+            if (sizeof(float) * FusedSmem<P>(w, ncut).total > kFusedMaxSmem) break;
+        }
+        cudaLaunchConfig_t q = {};
+        q.gridDim = dim3((unsigned)(f.CS * (n / f.C)));
+        q.blockDim = dim3((unsigned)(f.TG * pt));
+        q.dynamicSmemBytes = sizeof(float) * FusedSmem<P>(f, ncut).total;
+        cudaLaunchAttribute qa[1];
+        qa[0].id = cudaLaunchAttributeClusterDimension;
+        qa[0].val.clusterDim.x = (unsigned)f.CS;
+        qa[0].val.clusterDim.y = 1;
+        qa[0].val.clusterDim.z = 1;
+        q.attrs = qa;
+        q.numAttrs = 1;
+        int active = 0;
+        if (cudaOccupancyMaxActiveClusters(&active, (const void*)fgt_fused_kernel<P>, &q) != cudaSuccess) {
+            (void)cudaGetLastError();
+            break;
+        }
+        if (active >= n / f.C) break;
+    }
+    const int per_tg = f.R * f.C * Cf::TPB;
+    const FusedSmem<P> L(f, ncut);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(f.CS * (n / f.C)));
+    cfg.blockDim = dim3((unsigned)(f.TG * per_tg));
+    cfg.dynamicSmemBytes = sizeof(float) * L.total;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)f.CS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    FMM_CUDA_TRY(cudaLaunchKernelEx(&cfg, fgt_fused_kernel<P>, g, ncut, f, A, Cout, acc ? 1 : 0, htab));
+    return FMM_OK;
+}
+
+int launch_fgt_h2t_fused(int g, int ncut, int p, double sigma, const float* A, float* Cout, bool acc, cudaStream_t st)
+{
+    const double ustep = ldexp(1.0, -g) / (sqrt(2.0) * sigma);
+    switch (p) {
+        case 4: return fused_launch<4>(g, ncut, ustep, A, Cout, acc, st);
+        case 8: return fused_launch<8>(g, ncut, ustep, A, Cout, acc, st);
+        case 12: return fused_launch<12>(g, ncut, ustep, A, Cout, acc, st);
+        case 16: return fused_launch<16>(g, ncut, ustep, A, Cout, acc, st);
         default: return fail(FMM_EINVAL, "fgt_h2t: unsupported p = %d", p);
     }
 }
