@@ -218,9 +218,16 @@ int fmm_m2l_adjoint_levels(const fmm_tree* tree, int32_t lmin, int32_t lmax, int
  *             none overlapping its own level's input.
  *   prec      FMM_FP32 (the only precision of the batched path).
  *   flags     FMM_ACCUMULATE (add into L), FMM_BATCH_AUTOTUNE (time the
- *             candidate launch configurations on this plan before returning,
- *             writing only library scratch, never L; the choice is cached per
- *             device and workload signature).
+ *             candidate launch configurations -- grid size, claim chunk -- and
+ *             then the work-unit variants -- rows per lane, packed or scalar
+ *             multiply-adds, halo loads in flight -- on this plan before
+ *             returning, writing only library scratch, never L).  The choice
+ *             is cached per GPU (name, SM count), precision and workload
+ *             signature (p, level, periodicity and count of every (problem,
+ *             level), accumulate) in memory and in a JSON file that later
+ *             processes reload without timing: $FMMGB_TUNE_CACHE, else
+ *             $HOME/.cache/fmmgb/m2l_batched_tune.json (none when neither
+ *             is set).
  *   stream    the plan's device arrays are uploaded on this stream; the call
  *             returns after they are resident (it synchronises the stream).
  *   out       receives the plan.
@@ -248,6 +255,11 @@ typedef struct {
     int32_t persistent;    /* 1: grid < items, CTAs loop over claimed items */
     int32_t tuned;         /* 1: configuration chosen by timing (FMM_BATCH_AUTOTUNE) */
     float tuned_ms;        /* best timed run of the autotuner, 0 if not tuned */
+    int32_t variant;       /* work-unit variant: index into the tuned set */
+    int32_t form;          /* 0: p/2 rows per lane, packed multiply-adds; 1: p rows per lane, half
+                              the list entries each; 2: p/2 rows per lane, scalar multiply-adds */
+    int32_t loads;         /* halo loads a thread keeps in flight while staging a tile */
+    int32_t from_cache;    /* 1: the tuned choice was reused (memory or cache file), not timed */
 } fmm_batch_info_t;
 int fmm_batch_info(const fmm_batch* batch, fmm_batch_info_t* out);
 

@@ -14,9 +14,12 @@
 //
 // A run is a 4-byte counter reset plus one kernel launch: the plan holds an
 // instantiated CUDA graph of the two, and a caller's stream capture records
-// them as they are.  The autotuner times the candidate grid sizes (resident
-// CTAs per SM) and claim chunks on the plan itself, with every output pointer
-// redirected to library scratch, and caches the choice per workload signature.
+// them as they are.  The autotuner times, on the plan itself with every output
+// pointer redirected to library scratch, first the grid sizes (resident CTAs
+// per SM) and claim chunks, then the work-unit variants (how a warp's lanes
+// share a target's rows and list entries, and the halo loads a thread keeps in
+// flight) at the best of those; the choice is cached per GPU and workload
+// signature in memory and in a JSON file that later processes reload.
 #include "m2l_fp32_tile.cuh"
 
 #include <algorithm>
@@ -27,6 +30,9 @@
 #include <new>
 #include <string>
 #include <vector>
+
+#include <sys/stat.h>
+#include <unistd.h>
 
 namespace fmmgb {
 
@@ -61,10 +67,17 @@ static inline int batch_p_index(int p)
 
 constexpr size_t kBatchSmem = M2LCfg<16>::smem;  // the largest batched order
 constexpr int kBatchMinCtas = 6;
-// halo loads in flight per thread: the one kernel holds every order's code, so the
-// register budget is the largest order's (more spills)
-constexpr int kBatchLoads = 3;
 
+// Work-unit variants the autotuner chooses between: the lane form of the work unit
+// (m2l_fp32_tile.cuh) and the halo loads a thread keeps in flight while staging (the
+// one kernel holds every order's code, so its register budget is the largest order's).
+struct BatchVariant {
+    int form, loads;
+};
+constexpr BatchVariant kBatchVariants[] = {{kFormRowsPacked, 3}, {kFormRowsPacked, 2}, {kFormEntries, 3}, {kFormRows, 3}};
+constexpr int kBatchNumVariants = 4;
+
+template <int FORM, int LOADS>
 __global__ void __launch_bounds__(kThreads, kBatchMinCtas)
     m2l_batched_kernel(const BatchDesc* __restrict__ desc, const int2* __restrict__ items, int nitems,
                        int* __restrict__ counter, int chunk, int accumulate, BatchTables tabs)
@@ -91,10 +104,10 @@ __global__ void __launch_bounds__(kThreads, kBatchMinCtas)
             const TileGeom g = tile_geom_of(d.M, d.L, nullptr, d.level, item.y);
             __syncthreads();  // operator visible; previous tile done with the halo buffer
             switch (d.p) {
-                case 6: m2l_tile<6, false, kBatchLoads>(smem_raw, g, d.periodic, accumulate); break;
-                case 8: m2l_tile<8, false, kBatchLoads>(smem_raw, g, d.periodic, accumulate); break;
-                case 12: m2l_tile<12, false, kBatchLoads>(smem_raw, g, d.periodic, accumulate); break;
-                default: m2l_tile<16, false, kBatchLoads>(smem_raw, g, d.periodic, accumulate); break;
+                case 6: m2l_tile<6, false, LOADS, FORM>(smem_raw, g, d.periodic, accumulate); break;
+                case 8: m2l_tile<8, false, LOADS, FORM>(smem_raw, g, d.periodic, accumulate); break;
+                case 12: m2l_tile<12, false, LOADS, FORM>(smem_raw, g, d.periodic, accumulate); break;
+                default: m2l_tile<16, false, LOADS, FORM>(smem_raw, g, d.periodic, accumulate); break;
             }
         }
         if (!counter) break;  // one chunk per CTA (grid covers every item)
@@ -103,6 +116,17 @@ __global__ void __launch_bounds__(kThreads, kBatchMinCtas)
         if (threadIdx.x == 0) s_next = gridDim.x * chunk + atomicAdd(counter, chunk);
         __syncthreads();
         base = s_next;
+    }
+}
+
+// the kernel of variant v (kBatchVariants order)
+static const void* batch_kernel(int v)
+{
+    switch (v) {
+        case 1: return (const void*)m2l_batched_kernel<kFormRowsPacked, 2>;
+        case 2: return (const void*)m2l_batched_kernel<kFormEntries, 3>;
+        case 3: return (const void*)m2l_batched_kernel<kFormRows, 3>;
+        default: return (const void*)m2l_batched_kernel<kFormRowsPacked, 3>;
     }
 }
 
@@ -121,7 +145,7 @@ struct fmm_batch {
     int2* items = nullptr;
     std::vector<BatchDesc> host_desc;
     BatchTables tabs{};
-    int grid = 0, chunk = 1, persistent = 1, tuned = 0;
+    int grid = 0, chunk = 1, persistent = 1, tuned = 0, variant = 0, from_cache = 0;
     float tuned_ms = 0.f;
     size_t max_level_bytes = 0;
     std::string signature;
@@ -131,26 +155,99 @@ struct fmm_batch {
 namespace {
 
 struct TuneChoice {
-    int grid, chunk, persistent;
+    int grid, chunk, persistent, variant;
     float ms;
 };
 std::mutex g_tune_mu;
 std::map<std::string, TuneChoice> g_tune_cache;
+bool g_tune_loaded = false;
 
-int batch_occupancy(int* occ)
+// The persistent cache: $FMMGB_TUNE_CACHE, else $HOME/.cache/fmmgb/m2l_batched_tune.json (no file
+// when neither is set).  One JSON object, one entry per line:
+//   "<gpu name>|<SMs>|fp32|<workload signature>": {"grid": G, "chunk": C, "persistent": P, "variant": V, "ms": T},
+std::string tune_cache_path()
 {
-    FMM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, m2l_batched_kernel, kThreads, kBatchSmem));
-    if (*occ < 1) return fail(FMM_ECUDA, "batched M2L: kernel cannot be resident (occupancy 0)");
+    if (const char* e = getenv("FMMGB_TUNE_CACHE")) return e;
+    if (const char* h = getenv("HOME")) {
+        const std::string dir = std::string(h) + "/.cache/fmmgb";
+        mkdir((std::string(h) + "/.cache").c_str(), 0755);
+        mkdir(dir.c_str(), 0755);
+        return dir + "/m2l_batched_tune.json";
+    }
+    return "";
+}
+
+// under g_tune_mu
+void tune_cache_load()
+{
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    const std::string path = tune_cache_path();
+    if (path.empty()) return;
+    FILE* f = fopen(path.c_str(), "r");
+    if (!f) return;
+    char line[2048], key[1024];
+    while (fgets(line, sizeof line, f)) {
+        TuneChoice c{};
+        if (sscanf(line, " \"%1023[^\"]\": {\"grid\": %d, \"chunk\": %d, \"persistent\": %d, \"variant\": %d, \"ms\": %f}",
+                   key, &c.grid, &c.chunk, &c.persistent, &c.variant, &c.ms) == 6 &&
+            c.grid > 0 && c.chunk > 0 && c.variant >= 0 && c.variant < kBatchNumVariants)
+            g_tune_cache.emplace(key, c);
+    }
+    fclose(f);
+}
+
+// under g_tune_mu: rewrite the whole file (written aside, then renamed into place)
+void tune_cache_store()
+{
+    const std::string path = tune_cache_path();
+    if (path.empty()) return;
+    const std::string tmp = path + ".tmp" + std::to_string((long)getpid());
+    FILE* f = fopen(tmp.c_str(), "w");
+    if (!f) return;
+    fprintf(f, "{\n");
+    size_t i = 0;
+    for (const auto& kv : g_tune_cache) {
+        const TuneChoice& c = kv.second;
+        fprintf(f, "\"%s\": {\"grid\": %d, \"chunk\": %d, \"persistent\": %d, \"variant\": %d, \"ms\": %.6f}%s\n",
+                kv.first.c_str(), c.grid, c.chunk, c.persistent, c.variant, c.ms, ++i < g_tune_cache.size() ? "," : "");
+    }
+    fprintf(f, "}\n");
+    const bool ok = fclose(f) == 0;
+    if (ok) rename(tmp.c_str(), path.c_str());
+    else remove(tmp.c_str());
+}
+
+// the cache key of a plan: the GPU (name and SM count), the precision and the workload signature
+int tune_key(const fmm_batch* b, std::string* key)
+{
+    cudaDeviceProp prop;
+    FMM_CUDA_TRY(cudaGetDeviceProperties(&prop, b->dev));
+    std::string name = prop.name;
+    for (char& ch : name)
+        if (ch == '"' || ch == '|' || ch == '\\') ch = '_';
+    *key = name + "|" + std::to_string(prop.multiProcessorCount) + "|fp32|" + b->signature;
     return FMM_OK;
 }
 
-int launch_batch(const fmm_batch* b, const BatchDesc* desc, int grid, int chunk, int persistent, cudaStream_t st)
+int batch_occupancy(int v, int* occ)
+{
+    FMM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, batch_kernel(v), kThreads, kBatchSmem));
+    if (*occ < 1) return fail(FMM_ECUDA, "batched M2L: kernel variant %d cannot be resident (occupancy 0)", v);
+    return FMM_OK;
+}
+
+int launch_batch(const fmm_batch* b, const BatchDesc* desc, int grid, int chunk, int persistent, int variant,
+                 cudaStream_t st)
 {
     FMM_CUDA_TRY(cudaMemsetAsync(b->counter, 0, sizeof(int), st));
-    m2l_batched_kernel<<<grid, kThreads, kBatchSmem, st>>>(desc, b->items, (int)b->nitems,
-                                                           persistent ? b->counter : nullptr, chunk, b->accumulate,
-                                                           b->tabs);
-    FMM_CUDA_TRY(cudaGetLastError());
+    const int2* items = b->items;
+    int nitems = (int)b->nitems;
+    int* ctr = persistent ? b->counter : nullptr;
+    int acc = b->accumulate;
+    BatchTables tabs = b->tabs;
+    void* args[] = {(void*)&desc, (void*)&items, (void*)&nitems, (void*)&ctr, (void*)&chunk, (void*)&acc, (void*)&tabs};
+    FMM_CUDA_TRY(cudaLaunchKernel(batch_kernel(variant), dim3((unsigned)grid), dim3(kThreads), args, kBatchSmem, st));
     return FMM_OK;
 }
 
@@ -176,7 +273,7 @@ int build_graph(fmm_batch* b)
     void* args[] = {(void*)&desc, (void*)&items, (void*)&nitems, (void*)&ctr, (void*)&chunk, (void*)&acc, (void*)&tabs};
     if (e == cudaSuccess) {
         cudaKernelNodeParams kp{};
-        kp.func = (void*)m2l_batched_kernel;
+        kp.func = const_cast<void*>(batch_kernel(b->variant));
         kp.gridDim = dim3((unsigned)b->grid);
         kp.blockDim = dim3(kThreads);
         kp.sharedMemBytes = (unsigned)kBatchSmem;
@@ -192,32 +289,33 @@ int build_graph(fmm_batch* b)
     return FMM_OK;
 }
 
-// Time every candidate configuration on the plan with outputs redirected to
-// scratch; keep the fastest.  Synchronous.
+// Time the candidate configurations on the plan with outputs redirected to scratch:
+// first the grid sizes and claim chunks with the default work unit, then every work-unit
+// variant at the best of those; keep the fastest.  A choice stored for this GPU and
+// workload (in memory or in the cache file) is reused without timing.  Synchronous.
 int autotune(fmm_batch* b, cudaStream_t st)
 {
+    std::string key;
+    int rc = tune_key(b, &key);
+    if (rc) return rc;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        auto it = g_tune_cache.find(b->signature);
+        tune_cache_load();
+        auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
             b->grid = it->second.grid;
             b->chunk = it->second.chunk;
             b->persistent = it->second.persistent;
+            b->variant = it->second.variant;
             b->tuned = 1;
+            b->from_cache = 1;
             b->tuned_ms = it->second.ms;
             return FMM_OK;
         }
     }
-    int sms = 0, occ = 0, rc;
-    if ((rc = device_sm_count(&sms)) || (rc = batch_occupancy(&occ))) return rc;
-    std::vector<TuneChoice> cand;
+    int sms = 0, occ = 0;
+    if ((rc = device_sm_count(&sms)) || (rc = batch_occupancy(0, &occ))) return rc;
     const int64_t n = b->nitems;
-    cand.push_back({(int)n, 1, 0, 0.f});  // one CTA per item, hardware scheduling
-    for (int r = 1; r <= occ; ++r)
-        for (int c : {1, 2, 4}) {
-            const int64_t g = std::min<int64_t>((int64_t)r * sms, (n + c - 1) / c);
-            if (g >= 1) cand.push_back({(int)g, c, 1, 0.f});
-        }
     float2* scratch = nullptr;
     BatchDesc* sdesc = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -230,22 +328,44 @@ int autotune(fmm_batch* b, cudaStream_t st)
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     rc = (e == cudaSuccess) ? FMM_OK : cuda_fail(e, "batched M2L autotuner setup");
-    TuneChoice best{0, 0, 0, 1e30f};
-    for (auto& c : cand) {
-        if (rc) break;
-        if ((rc = launch_batch(b, sdesc, c.grid, c.chunk, c.persistent, st))) break;  // warm-up
+    auto time_one = [&](TuneChoice& c) {
+        if (rc) return;
+        if ((rc = launch_batch(b, sdesc, c.grid, c.chunk, c.persistent, c.variant, st))) return;  // warm-up
         float t = 1e30f;
         for (int rep = 0; rep < 3 && !rc; ++rep) {
             float ms = 0.f;
-            if ((e = cudaEventRecord(e0, st)) != cudaSuccess) { rc = cuda_fail(e, "cudaEventRecord"); break; }
-            if ((rc = launch_batch(b, sdesc, c.grid, c.chunk, c.persistent, st))) break;
-            if ((e = cudaEventRecord(e1, st)) != cudaSuccess) { rc = cuda_fail(e, "cudaEventRecord"); break; }
-            if ((e = cudaEventSynchronize(e1)) != cudaSuccess) { rc = cuda_fail(e, "cudaEventSynchronize"); break; }
+            if ((e = cudaEventRecord(e0, st)) != cudaSuccess) { rc = cuda_fail(e, "cudaEventRecord"); return; }
+            if ((rc = launch_batch(b, sdesc, c.grid, c.chunk, c.persistent, c.variant, st))) return;
+            if ((e = cudaEventRecord(e1, st)) != cudaSuccess) { rc = cuda_fail(e, "cudaEventRecord"); return; }
+            if ((e = cudaEventSynchronize(e1)) != cudaSuccess) { rc = cuda_fail(e, "cudaEventSynchronize"); return; }
             cudaEventElapsedTime(&ms, e0, e1);
             t = std::min(t, ms);
         }
         c.ms = t;
-        if (t < best.ms) best = c;
+    };
+    // stage 1: launch configurations with the default work unit
+    std::vector<TuneChoice> cand;
+    cand.push_back({(int)n, 1, 0, 0, 0.f});  // one CTA per item, hardware scheduling
+    for (int r = 1; r <= occ; ++r)
+        for (int c : {1, 2, 4}) {
+            const int64_t g = std::min<int64_t>((int64_t)r * sms, (n + c - 1) / c);
+            if (g >= 1) cand.push_back({(int)g, c, 1, 0, 0.f});
+        }
+    TuneChoice best{0, 0, 0, 0, 1e30f};
+    for (auto& c : cand) {
+        time_one(c);
+        if (!rc && c.ms < best.ms) best = c;
+    }
+    // stage 2: the other work-unit variants at that configuration (a persistent grid is
+    // clamped to what the variant keeps resident)
+    for (int v = 1; v < kBatchNumVariants && !rc; ++v) {
+        int occ_v = 0;
+        if ((rc = batch_occupancy(v, &occ_v))) break;
+        TuneChoice c = best;
+        c.variant = v;
+        if (c.persistent) c.grid = (int)std::min<int64_t>(c.grid, (int64_t)occ_v * sms);
+        time_one(c);
+        if (!rc && c.ms < best.ms) best = c;
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
@@ -256,10 +376,14 @@ int autotune(fmm_batch* b, cudaStream_t st)
     b->grid = best.grid;
     b->chunk = best.chunk;
     b->persistent = best.persistent;
+    b->variant = best.variant;
     b->tuned = 1;
+    b->from_cache = 0;
     b->tuned_ms = best.ms;
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune_cache[b->signature] = best;
+    tune_cache_load();
+    g_tune_cache[key] = best;
+    tune_cache_store();
     return FMM_OK;
 }
 
@@ -364,7 +488,8 @@ int create_batch(const fmm_tree* const* trees, const int32_t* p, int32_t nprob, 
         b->tabs.b[j] = t->b;
     }
     int sms = 0, occ = 0, rc;
-    if ((rc = device_sm_count(&sms)) || (rc = batch_occupancy(&occ))) { delete b; return rc; }
+    FMM_CUDA_TRY(cudaGetDevice(&b->dev));
+    if ((rc = device_sm_count(&sms)) || (rc = batch_occupancy(0, &occ))) { delete b; return rc; }
     b->persistent = 1;
     b->chunk = 1;
     b->grid = (int)std::min<int64_t>((int64_t)occ * sms, b->nitems);
@@ -418,7 +543,7 @@ int fmm_batch_run(fmm_batch* b, void* stream)
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     FMM_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
     if (cs != cudaStreamCaptureStatusNone)  // the caller's capture records the two operations
-        return launch_batch(b, b->desc, b->grid, b->chunk, b->persistent, st);
+        return launch_batch(b, b->desc, b->grid, b->chunk, b->persistent, b->variant, st);
     if (!b->exec) {
         int rc = build_graph(b);
         if (rc) return rc;
@@ -438,6 +563,10 @@ int fmm_batch_info(const fmm_batch* b, fmm_batch_info_t* out)
     out->persistent = b->persistent;
     out->tuned = b->tuned;
     out->tuned_ms = b->tuned_ms;
+    out->variant = b->variant;
+    out->form = kBatchVariants[b->variant].form;
+    out->loads = kBatchVariants[b->variant].loads;
+    out->from_cache = b->from_cache;
     return FMM_OK;
 }
 
@@ -452,7 +581,7 @@ int fmm_m2l_batched(const fmm_tree* const* trees, const int32_t* p, int32_t npro
     fmm_batch* b = nullptr;
     int rc = create_batch(trees, p, nprob, M_levels, L_levels, prec, flags, st, false, &b);
     if (rc) return rc;
-    rc = b->nitems ? launch_batch(b, b->desc, b->grid, b->chunk, b->persistent, st) : FMM_OK;
+    rc = b->nitems ? launch_batch(b, b->desc, b->grid, b->chunk, b->persistent, b->variant, st) : FMM_OK;
     free_batch(b, st);
     return rc;
 }

@@ -178,15 +178,25 @@ __device__ __forceinline__ void m2l_load_operator(unsigned char* raw, const floa
     }
 }
 
+// How a warp's lanes share the work of its 16 targets (two lanes per target):
+//   kFormRowsPacked  each lane p/2 rows, all 27 list entries, packed f32x2 multiply-adds;
+//   kFormEntries     each lane all p rows, 14 or 13 of the 27 entries, one shuffle adds the halves;
+//   kFormRows        each lane p/2 rows, all 27 entries, scalar FFMAs;
+//   kFormAuto        the order's default (M2LCfg: packed rows for p <= 16, scalar rows for p = 24).
+enum : int { kFormAuto = -1, kFormRowsPacked = 0, kFormEntries = 1, kFormRows = 2 };
+
 // Translate and reduce one tile (ADAPTIVE and g.exists set: only existing
 // sources are read and existing targets written).  Requires the operator of order P in shared
 // memory (m2l_load_operator + a barrier) and no thread still reading the halo
 // buffer of a previous tile (a barrier).  All 128 threads call it.
-template <int P, bool ADAPTIVE = false, int UMAX = M2LCfg<P>::LOADS>
+template <int P, bool ADAPTIVE = false, int UMAX = M2LCfg<P>::LOADS, int FORM = kFormAuto>
 __device__ __forceinline__ void m2l_tile(unsigned char* raw, const TileGeom& g, int periodic, int accumulate)
 {
     using C = M2LCfg<P>;
-    constexpr int RN = C::RN, Q = P / 2;
+    constexpr int F = FORM != kFormAuto ? FORM
+                                        : (C::PACKED ? kFormRowsPacked : (C::SPLIT_ROWS ? kFormRows : kFormEntries));
+    constexpr bool SPLIT = F != kFormEntries;
+    constexpr int RN = SPLIT ? P / 2 : P, Q = P / 2;
     const TileSmem<P> s(raw);
     const int tid = threadIdx.x;
 
@@ -255,7 +265,7 @@ __device__ __forceinline__ void m2l_tile(unsigned char* raw, const TileGeom& g, 
     const float2* tbase = s.buf + tpy * kHalo + tpx;
     if (!work) {
         // nothing to store for this warp
-    } else if constexpr (!C::SPLIT_ROWS) {
+    } else if constexpr (!SPLIT) {
         // half-warp `half` takes list entries [14 half, 14 half + 14) of 27; all p rows
 #pragma unroll 1
         for (int j = 0; j < 14; ++j) {
@@ -279,7 +289,7 @@ __device__ __forceinline__ void m2l_tile(unsigned char* raw, const TileGeom& g, 
                 }
             }
         }
-    } else if constexpr (C::PACKED) {
+    } else if constexpr (F == kFormRowsPacked) {
         // half-warp `half` takes rows [RN half, RN half + RN); all 27 entries; packed
         // accumulators and operator window (w and i w), m broadcast per k
         const int n0 = half * RN;
@@ -346,7 +356,7 @@ __device__ __forceinline__ void m2l_tile(unsigned char* raw, const TileGeom& g, 
     // ---- combine the half-warps: each lane ends with p/2 finished rows ----
     constexpr int HR = P / 2;
     float2 res[HR];
-    if constexpr (!C::SPLIT_ROWS) {
+    if constexpr (!SPLIT) {
 #pragma unroll
         for (int i = 0; i < HR; ++i) {
             const float2 send = half ? acc[i] : acc[HR + i];

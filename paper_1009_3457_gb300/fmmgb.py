@@ -65,6 +65,10 @@ class fmm_batch_info_t(ctypes.Structure):
         ("persistent", ctypes.c_int32),
         ("tuned", ctypes.c_int32),
         ("tuned_ms", ctypes.c_float),
+        ("variant", ctypes.c_int32),
+        ("form", ctypes.c_int32),
+        ("loads", ctypes.c_int32),
+        ("from_cache", ctypes.c_int32),
     ]
 
 

@@ -192,3 +192,73 @@ def test_batched_full_workload(fmm, orc):
             got = _host(out) if tg is None else _host(out)[tg]
             worst = max(worst, _rel(got, r))
     assert worst <= TOL, worst
+
+
+_TUNE_CHILD = r'''
+import json, sys
+import numpy as np
+import torch
+sys.path.insert(0, sys.argv[1])
+import workloads
+from paper_1009_3457_gb300 import fmmgb
+fmmgb.load()
+rng = np.random.default_rng(2024)
+shapes = workloads.batched_problems(6, rng, depths=(3, 5), n_range=(500, 2000))
+trees, ps, Ms, Ls = [], [], [], []
+for sh in shapes:
+    L, p = sh["max_level"], sh["p"]
+    xy, c = workloads.uniform_particles(sh["n"], rng)
+    M = {l: torch.empty((4 ** l, p), dtype=torch.complex64, device="cuda") for l in range(2, L + 1)}
+    fmmgb.fmm_p2m(L, p, torch.from_numpy(xy).cuda(), torch.from_numpy(c).cuda(), M[L])
+    for l in range(L, 2, -1):
+        fmmgb.fmm_m2m(l, p, M[l], M[l - 1])
+    trees.append(fmmgb.fmm_build_lists(None, L))
+    ps.append(p)
+    Ms.append([M[l] for l in range(2, L + 1)])
+    Ls.append([torch.empty_like(M[l]) for l in range(2, L + 1)])
+infos = []
+for k in range(2):  # the second plan of this process reuses the first one's choice
+    plan = fmmgb.fmm_batch_create(trees, ps, Ms, Ls, autotune=True)
+    plan.run()
+    infos.append(plan.info())
+worst = 0.0
+for tr, p, m, l in zip(trees, ps, Ms, Ls):
+    ref = [torch.empty_like(x) for x in m]
+    fmmgb.fmm_m2l_levels(tr, 2, p, m, ref)
+    for a, b in zip(l, ref):
+        worst = max(worst, float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b)))
+fmmgb.fmm_sync_status()
+print(json.dumps({"infos": infos, "worst": worst}))
+'''
+
+
+def test_batched_autotune_choice_persists_across_processes(fmm, tmp_path):
+    """FMM_BATCH_AUTOTUNE stores its choice (launch configuration and work-unit variant) in the
+    cache file; a second plan in the same process and every plan of a later process reuse it
+    without timing, and the tuned plans agree with fmm_m2l_levels."""
+    import json
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    cache = tmp_path / "tune.json"
+    env = dict(os.environ, FMMGB_TUNE_CACHE=str(cache))
+    runs = []
+    for _ in range(2):
+        out = subprocess.run([sys.executable, "-c", _TUNE_CHILD, root], env=env, capture_output=True, text=True,
+                             timeout=600)
+        assert out.returncode == 0, out.stderr[-2000:]
+        runs.append(json.loads(out.stdout.strip().splitlines()[-1]))
+    first, second = runs
+    a, b = first["infos"]
+    assert a["tuned"] == 1 and a["from_cache"] == 0 and a["tuned_ms"] > 0.0
+    assert b["tuned"] == 1 and b["from_cache"] == 1
+    text = cache.read_text()
+    assert '"variant"' in text and "|fp32|" in text
+    for info in second["infos"]:
+        assert info["from_cache"] == 1
+        for k in ("grid", "chunk", "persistent", "variant", "form", "loads"):
+            assert info[k] == a[k], (k, info[k], a[k])
+    assert a["form"] in (0, 1, 2) and a["loads"] in (2, 3)
+    assert first["worst"] <= TOL and second["worst"] <= TOL
