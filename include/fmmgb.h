@@ -166,7 +166,14 @@ int fmm_m2l(const fmm_tree* tree, int32_t level, int32_t p, int32_t prec,
 /* fmm_m2l_levels -- fmm_m2l for every level lmin..lmax in ONE launch (the
  * levels are independent given their MEs).  M[i], L[i] are the arrays of
  * level lmin + i (host array of device pointers, read during the call).
- * Equivalent to lmax - lmin + 1 calls of fmm_m2l. */
+ * Equivalent to lmax - lmin + 1 calls of fmm_m2l.
+ * Host-resident problems: the library takes device pointers only.  The Python
+ * package's pipeline.HostStreamM2L overlaps, over a stream of problems, each
+ * problem's copy in, this call and the previous problem's copy out on three
+ * CUDA streams (it exists only in Python); a C caller does the same with its
+ * own streams, pinned buffers, cudaMemcpyAsync and events around this call.
+ * Tensor-core precisions: one kernel per call; calls on different streams
+ * must not overlap on the GPU (they share the library's per-device flags). */
 int fmm_m2l_levels(const fmm_tree* tree, int32_t lmin, int32_t lmax, int32_t p, int32_t prec,
                    const void* const* M, void* const* L, int32_t flags, void* stream);
 
