@@ -55,7 +55,9 @@ CONFIG = {
     "parallelism": "replicas",
 }
 FP32_LANES_PER_SM = 128
-FGT_H2T_LAUNCHES = 2  # kernel launches of one fgt_h2t call
+def fgt_h2t_launches(g: int) -> int:
+    """Kernel launches of one fgt_h2t call: one fused launch for grids up to 16 x 16, two passes beyond."""
+    return 1 if g <= 4 else 2
 # replaced at start-up by the device's own SM count and maximum SM clock (device_peaks)
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
@@ -550,10 +552,10 @@ def run_ours(args):
             print(json.dumps({"mode": "kernels", "steps": args.steps, "launches_per_step": 1, "batch": bt["info"]}))
         return 0
     if args.mode == "kernels" and args.prec == "fgt":
-        # profiling case: the FGT H2T of the sigma = 0.05, p = 16 workload (two passes per call)
+        # profiling case: the FGT H2T of the sigma (default 0.05), p = 16 workload
         fcfg = workloads.CONFIGS["fgt"]
         fx, fq = workloads.gmm_particles(fcfg["n"], workloads.rng_for("fgt"))
-        sigma, fp = 0.05, 16
+        sigma, fp = args.sigma, 16
         g = workloads.fgt_grid_log2(sigma)
         A = torch.empty((4 ** g, fp, fp), dtype=torch.float32, device=dev)
         Cf = torch.empty_like(A)
@@ -564,7 +566,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         fmmgb.fmm_sync_status()
         if rank == 0:
-            print(json.dumps({"mode": "kernels", "steps": args.steps, "launches_per_step": 2}))
+            print(json.dumps({"mode": "kernels", "steps": args.steps, "launches_per_step": fgt_h2t_launches(g)}))
         return 0
     if args.mode == "kernels" and args.prec == "p2p":
         # profiling case: the near field at level 8 of the 2^22-point headline workload
@@ -896,12 +898,12 @@ def run_ours(args):
                     ms_all = statistics.median(_timed(torch, _graph(torch, fgt_all), args.steps, stream, flush))
                     rows["fgt_transform_sigma0.05_p16"] = {
                         "ms": ms_all, "sources": int(fcfg["n"]), "targets": int(fcfg["n"]),
-                        "points_per_s": fcfg["n"] / (ms_all * 1e-3), "launches": 10,
-                        "note": "fgt_bin_points of the sources (3 kernels), fgt_p2h_binned, fgt_h2t (2 passes), "
+                        "points_per_s": fcfg["n"] / (ms_all * 1e-3), "launches": 8 + fgt_h2t_launches(g),
+                        "note": "fgt_bin_points of the sources (3 kernels), fgt_p2h_binned, fgt_h2t, "
                                 "fgt_bin_points of the targets (3 kernels), fgt_t2p_binned; uniform targets"}
                 gfs = (4 ** g) * metrics.fgt_flops_per_box_separable(fp, taps, taps) / (ms * 1e-3) / 1e9
                 rows[f"fgt_h2t_sigma{sigma}_p{fp}"] = {
-                    "translations_per_s": ntr / (ms * 1e-3), "ms": ms, "launches": FGT_H2T_LAUNCHES,
+                    "translations_per_s": ntr / (ms * 1e-3), "ms": ms, "launches": fgt_h2t_launches(g),
                     "grid": f"{1 << g}^2", "gflops_separable": gfs, "alu_frac": gfs / 1e3 / alu_peak_tflops()}
         rows.update(_fgt_hermite_rows(torch, fmmgb, dev, fxd, fqd, args, stream, flush))
         fmmgb.fmm_sync_status()
@@ -980,6 +982,7 @@ def main():
     ap.add_argument("--prec", default="fp32", choices=["fp32", "tc3", "tc1", "batched", "fgt", "h2p", "p2p"],
                     help="launches of --mode kernels: the step at this precision, or the 256-problem batch, "
                          "or the FGT H2T at sigma 0.05, p 16")
+    ap.add_argument("--sigma", type=float, default=0.05, help="--mode kernels --prec fgt: the FGT bandwidth")
     ap.add_argument("--nprob", type=int, default=None,
                     help="--mode kernels --prec batched: the first N problems of the batch (profiling case)")
     args = ap.parse_args()
