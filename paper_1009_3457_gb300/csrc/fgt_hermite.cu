@@ -270,8 +270,12 @@ constexpr int kH2pStages = 3;                 // ring depth (two batches in flig
 
 template <int P>
 struct H2pCfg {
-    static constexpr int R = P <= 8 ? 4 : 2;   // targets per thread
-    static constexpr int CH = kH2pThreads * R; // targets per claim
+    // 4 targets per thread: each broadcast 16-byte load of A feeds 16 FMAs; 64-thread CTAs at
+    // p >= 12 keep a claim at 256 targets (a box's last claim is partly idle)
+    static constexpr int R = 4;                        // targets per thread
+    static constexpr int THREADS = P >= 12 ? 64 : 128;
+    static constexpr int WARPS = THREADS / 32;
+    static constexpr int CH = THREADS * R;             // targets per claim
     static constexpr int PP = P * P;
     static constexpr size_t smem = (size_t)kH2pStages * kH2pBatch * PP * sizeof(float);
 };
@@ -340,16 +344,17 @@ __device__ bool h2p_claim(const H2pArgs& a, int nbox, int ch, int* first, int* e
 }
 
 template <int P>
-__global__ void __launch_bounds__(kH2pThreads) fgt_h2p_kernel(H2pArgs a)
+__global__ void __launch_bounds__(H2pCfg<P>::THREADS) fgt_h2p_kernel(H2pArgs a)
 {
     using C = H2pCfg<P>;
     constexpr int R = C::R;
     constexpr int PP = C::PP;
+    constexpr int NT = C::THREADS;
     extern __shared__ float4 h2p_smem[];
     float* sA = reinterpret_cast<float*>(h2p_smem);  // [kH2pStages][kH2pBatch][P][P]
     __shared__ float s_off[2 * kH2pMaxCut + 1];       // k d, k = -ncut .. ncut
     __shared__ short s_list[kH2pMaxBoxes];            // non-empty source boxes, row-major, as (dy + ncut) * 64 + dx + ncut
-    __shared__ int s_warp_cnt[kH2pWarps];
+    __shared__ int s_warp_cnt[C::WARPS];
     __shared__ int s_claim[4];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -379,7 +384,7 @@ __global__ void __launch_bounds__(kH2pThreads) fgt_h2p_kernel(H2pArgs a)
 
         // ordered compaction of the neighbourhood's non-empty source boxes (row-major)
         int total = 0;
-        for (int base = 0; base < nb; base += kH2pThreads) {
+        for (int base = 0; base < nb; base += NT) {
             const int i = base + tid;
             bool keep = false;
             int code = 0;
@@ -394,7 +399,7 @@ __global__ void __launch_bounds__(kH2pThreads) fgt_h2p_kernel(H2pArgs a)
             int off = total;
             for (int q = 0; q < warp; ++q) off += s_warp_cnt[q];
             if (keep) s_list[off + __popc(bal & ((1u << lane) - 1))] = (short)code;
-            for (int q = 0; q < kH2pWarps; ++q) total += s_warp_cnt[q];
+            for (int q = 0; q < C::WARPS; ++q) total += s_warp_cnt[q];
             __syncthreads();
         }
 
@@ -403,7 +408,7 @@ __global__ void __launch_bounds__(kH2pThreads) fgt_h2p_kernel(H2pArgs a)
         float u1[R], u2[R], acc[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const int pos = first + warp * 32 * R + r * 32 + lane;
+            const int pos = first + warp * 32 * R + r * 32 + lane;  // a warp's 32 R targets
             tj[r] = -1;
             u1[r] = u2[r] = acc[r] = 0.f;
             if (pos < end) {
@@ -424,7 +429,7 @@ __global__ void __launch_bounds__(kH2pThreads) fgt_h2p_kernel(H2pArgs a)
             if (k < nbatch) {
                 float4* dst = reinterpret_cast<float4*>(sA + (size_t)(k % kH2pStages) * kH2pBatch * PP);
                 const int cnt = min(kH2pBatch, total - k * kH2pBatch) * (PP / 4);
-                for (int i = tid; i < cnt; i += kH2pThreads) {
+                for (int i = tid; i < cnt; i += NT) {
                     const int code = s_list[k * kH2pBatch + i / (PP / 4)];
                     const int sx = tx + (code & 63) - a.ncut, sy = ty + (code >> 6) - a.ncut;
                     cp_async_16(dst + i, reinterpret_cast<const float4*>(a.A + ((size_t)sy * side + sx) * PP) +
@@ -453,9 +458,15 @@ __global__ void __launch_bounds__(kH2pThreads) fgt_h2p_kernel(H2pArgs a)
 #pragma unroll
                         for (int r = 0; r < R; ++r) hermite_functions<P>(u2[r] + s_off[2 * a.ncut - dy], h2[r]);
                     }
-                    float h1[R][P];
+                    // h1 by its recurrence, one order per a1 (h_{a+1} = 2t h_a - 2a h_{a-1})
+                    float hp[R], hc[R], tt[R];
 #pragma unroll
-                    for (int r = 0; r < R; ++r) hermite_functions<P>(u1[r] + s_off[2 * a.ncut - dx], h1[r]);
+                    for (int r = 0; r < R; ++r) {
+                        const float t = u1[r] + s_off[2 * a.ncut - dx];
+                        tt[r] = t + t;
+                        hp[r] = 0.f;
+                        hc[r] = __expf(-t * t);
+                    }
                     const float4* Ab = reinterpret_cast<const float4*>(sb + e * PP);
 #pragma unroll
                     for (int a1 = 0; a1 < P; ++a1) {
@@ -474,7 +485,12 @@ __global__ void __launch_bounds__(kH2pThreads) fgt_h2p_kernel(H2pArgs a)
                             }
                         }
 #pragma unroll
-                        for (int r = 0; r < R; ++r) acc[r] = fmaf(h1[r][a1], t[r], acc[r]);
+                        for (int r = 0; r < R; ++r) {
+                            acc[r] = fmaf(hc[r], t[r], acc[r]);
+                            const float hn = fmaf(tt[r], hc[r], -(float)(2 * a1) * hp[r]);
+                            hp[r] = hc[r];
+                            hc[r] = hn;
+                        }
                     }
                 }
             }
@@ -513,7 +529,7 @@ static int h2p_launch(const H2pArgs& args, cudaStream_t st)
     {
         std::lock_guard<std::mutex> lk(mu);
         if (!occ) {
-            FMM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fgt_h2p_kernel<P>, kH2pThreads, C::smem));
+            FMM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fgt_h2p_kernel<P>, C::THREADS, C::smem));
             if (occ < 1) occ = 1;
         }
     }
@@ -525,7 +541,7 @@ static int h2p_launch(const H2pArgs& args, cudaStream_t st)
     if (int rc = launch_h2p_claims(nbox, args.box_start, C::CH, const_cast<int*>(args.claims), args.err, st)) return rc;
     const int64_t most = (int64_t)args.n / C::CH + nbox;  // claims can be no more
     const int grid = (int)std::min<int64_t>((int64_t)occ * sms, most > 0 ? most : 1);
-    fgt_h2p_kernel<P><<<grid, kH2pThreads, C::smem, st>>>(args);
+    fgt_h2p_kernel<P><<<grid, C::THREADS, C::smem, st>>>(args);
     FMM_CUDA_TRY(cudaGetLastError());
     return FMM_OK;
 }
