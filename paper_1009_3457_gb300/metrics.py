@@ -105,3 +105,15 @@ def p2p_pairs(level: int, target_counts, source_counts, self_pairs: int = 0) -> 
     s = np.pad(np.asarray(source_counts, dtype=np.int64).reshape(n, n), 1)
     near = sum(s[1 + dy:1 + dy + n, 1 + dx:1 + dx + n] for dy in (-1, 0, 1) for dx in (-1, 0, 1))
     return int((np.asarray(target_counts, dtype=np.int64).reshape(n, n) * near).sum()) - int(self_pairs)
+
+
+def m2l_tc_mma_flops(levels, p: int, products: int = 3) -> int:
+    """Tensor-core flops the tensor-core M2L issues over the given uniform levels: per tile of
+    8 x 32 parents, 32 operator blocks x (2p / 16) K steps x ceil(8p / 128) M tiles of
+    M = 128, N = 256, K = 16 products, `products` per step (3 for the BF16 hi/lo split)."""
+    mt = -(-8 * p // 128)
+    tiles = 0
+    for lv in levels:
+        np_ = 1 << (lv - 1)
+        tiles += -(-np_ // 8) * -(-np_ // 32)
+    return tiles * 32 * (2 * p // 16) * mt * products * 2 * 128 * 256 * 16
