@@ -49,13 +49,15 @@
 // clears the flags for the next launch.
 //
 // Schedule.  One CTA per SM (grid = min(SMs, U / 8)), four roles: producer
-// warps (eight at p = 16, two at p = 24, one ring stage and one bulk copy in
+// warps (six at p = 16, two at p = 24, one ring stage and one bulk copy in
 // flight each) stream the operator blocks of the range; an MMA thread (warp
-// 8, which also owns the TMEM allocation) issues the products; three staging
-// warps (9-11) build the class halos in two shared-memory buffers, reading
-// the FP32 MEs and writing their BF16 hi/lo parts in the layout the MMAs read
+// 8, which also owns the TMEM allocation) issues the products; the staging
+// warps (the rest of warps 0-7 and warps 9-11: five at p = 16, nine at p = 24)
+// build the class halos in shared memory, converting the FP32 MEs that a
+// tensor copy lands into their BF16 hi/lo parts in the layout the MMAs read
 // (no pre-pass, no copy of the MEs in global memory); four epilogue warps
-// (12-15) drain the accumulators.  Every mbarrier and flag wait is bounded:
+// (12-15) drain the accumulators.  The first operator fills and the first halo
+// copy are issued before the TMEM allocation.  Every mbarrier and flag wait is bounded:
 // on timeout the waiting role records FMM_ETIMEOUT in the device error word
 // and stops; producers wait (bounded) for their own copies in flight, the
 // MMA thread for its own MMAs, and the TMEM is freed before the CTA exits.
@@ -179,11 +181,12 @@ __host__ __device__ inline int tc_image_block(int blk) { return (blk & 7) * 4 + 
 // ---------------------------------------------------------------------------
 // the kernel: persistent, one CTA per SM, warp-specialised, stream-K ranges
 // ---------------------------------------------------------------------------
-// warps 0-7 producers (STAGES of them active), 8 MMA issuer, 9-11 halo staging,
-// 12-15 epilogue (a multiple of 4, so that warp % 4 is its TMEM lane quarter)
+// warps 0-7 producers (the first STAGES of them; the others join the staging),
+// 8 MMA issuer, 9-11 halo staging, 12-15 epilogue (a multiple of 4, so that
+// warp % 4 is its TMEM lane quarter)
 constexpr int kTcCtaThreads = 512;
 constexpr int kMmaWarp = 8, kStageWarp0 = 9, kStageWarps = 3, kEpiWarp0 = 12;
-constexpr int kStageBatch = 5;  // halo items in flight per staging thread
+constexpr int kStageBatch = 5;  // halo items in flight per staging thread (global-load path)
 // named barriers: staging warps (wait outcome; cp.async completion), epilogue warps (wait outcome; publish)
 constexpr int kStageBar = 1, kStageCopyBar = 2, kEpiBar = 3, kPubBar = 4;
 
@@ -252,6 +255,18 @@ __device__ __forceinline__ TcSeg tc_seg(int u0, int u1, int i)
 }
 __device__ __forceinline__ int tc_nseg(int u0, int u1) { return u1 > u0 ? ((u1 - 1) >> 5) - (u0 >> 5) + 1 : 0; }
 
+// the unit at walk position g (0 <= g < u1 - u0) of the range [u0, u1)
+__device__ __forceinline__ int tc_walk_unit(int u0, int u1, int g)
+{
+    const int nseg = tc_nseg(u0, u1);
+    for (int i = 0; i < nseg; ++i) {
+        const TcSeg sg = tc_seg(u0, u1, i);
+        if (g < sg.sb - sg.sa) return sg.sa + g;
+        g -= sg.sb - sg.sa;
+    }
+    return u0;
+}
+
 // class group k (0-based, in walk order) of the range [u0, u1): its tile and source class
 __device__ __forceinline__ bool tc_group(int u0, int u1, int k, int& t, int& cls)
 {
@@ -285,6 +300,36 @@ __device__ __forceinline__ void tc_stage_chunk(const float4* a, const float4* b,
     }
     *reinterpret_cast<uint4*>(dst) = make_uint4(h[0], h[1], h[2], h[3]);
     *reinterpret_cast<uint4*>(dst + lo_off) = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+// A class halo that a tensor copy landed as FP32 [parent][2p] -> its BF16 hi/lo parts in the
+// layout the MMAs read, by NT threads (this one is `st`).  Thread st converts parents st,
+// st + NT, ..., each one's chunks in the order (st + s) % KCH and the two 16-byte halves of a
+// chunk in the order set by bit 2 of st, so that 8 consecutive threads read 8 different
+// 16-byte bank groups of the landing buffer and write 8 consecutive parents of a halo row.
+template <int P, int NT>
+__device__ __forceinline__ void tc_convert_landed(const unsigned char* lbuf, unsigned char* buf, int st)
+{
+    using C = TcCfg<P>;
+    const int h = (st >> 2) & 1, c0 = st % C::KCH;
+#pragma unroll 1
+    for (int pos = st; pos < C::NPOS; pos += NT) {
+        const float4* src = reinterpret_cast<const float4*>(lbuf + (size_t)pos * (C::K2 * 4));
+        unsigned char* dst = buf + (size_t)(2 * (pos / C::HX)) * C::ROWB + (size_t)(pos % C::HX) * 16;
+        float4 x[C::KCH], y[C::KCH];
+#pragma unroll
+        for (int s = 0; s < C::KCH; ++s) {
+            const int ch = c0 + s < C::KCH ? c0 + s : c0 + s - C::KCH;
+            x[s] = src[2 * ch + h];
+            y[s] = src[2 * ch + 1 - h];
+        }
+#pragma unroll
+        for (int s = 0; s < C::KCH; ++s) {
+            const int ch = c0 + s < C::KCH ? c0 + s : c0 + s - C::KCH;
+            const float4 f0 = h ? y[s] : x[s], f1 = h ? x[s] : y[s];
+            tc_stage_chunk(&f0, &f1, dst + (size_t)ch * C::IPLANE, C::ROWB);
+        }
+    }
 }
 
 // AND of `v` over the `n` threads of named barrier `id` (uniform control flow after a bounded wait)
@@ -340,11 +385,37 @@ __global__ void __launch_bounds__(kTcCtaThreads, 1)
     // simultaneous reads of all SMs over more L2 lines
     const unsigned char* rimg = img + (size_t)(cta % kTcReplicas) * kTcBlocks * C::STAGE;
 
-    if (tid == 0) {
-        for (int s = 0; s < C::STAGES; ++s) {
-            mbar_init(&afull[s], 1);
-            mbar_init(&aempty[s], 1);
+    const int nunits = u1 - u0;
+    // halo staging: the producer warps beyond STAGES, then warps 9-11; stw = index among them (-1: other role)
+    constexpr int NST = 32 * (8 - C::STAGES + kStageWarps);
+    const int stw = (warp >= C::STAGES && warp < 8) ? warp - C::STAGES
+                    : (warp >= kStageWarp0 && warp < kStageWarp0 + kStageWarps) ? 8 - C::STAGES + warp - kStageWarp0
+                                                                                : -1;
+    const int st = stw * 32 + lane;
+    int ngrp = 0;  // class groups of the walk
+    for (int i = 0; i < nseg; ++i) {
+        const TcSeg sg = tc_seg(u0, u1, i);
+        ngrp += (((sg.sb - 1) & 31) >> 3) - ((sg.sa & 31) >> 3) + 1;
+    }
+    // the next tensor copy into the landing buffer: the first group at or after `from` on the
+    // tensor-copy path, issued by staging thread 0; every staging thread returns that group (-1: none)
+    auto issue_tma = [&](int from) -> int {
+        for (int k = from; k < ngrp; ++k) {
+            int t, cls;
+            tc_group(u0, u1, k, t, cls);
+            const TcTile tl = tc_tile(job, t);
+            if (!maps.use_tma[tl.li]) continue;
+            if (st == 0) {
+                mbar_expect_tx(lfull, (uint32_t)C::LBUF);
+                tma_load_5d(lbuf, &maps.map[tl.li], 0, cls & 1, tl.PX0 - 1, cls >> 1, tl.PY0 - 1, lfull);
+            }
+            return k;
         }
+        return -1;
+    };
+    int pending = -1;  // staging: the group whose tensor copy is in flight
+
+    if (tid == 0) {
         for (int i = 0; i < C::NHB; ++i) {
             mbar_init(&hfull[i], 1);
             mbar_init(&hfree[i], 1);
@@ -354,8 +425,27 @@ __global__ void __launch_bounds__(kTcCtaThreads, 1)
             mbar_init(&dfree[i], 4);
         }
         mbar_init(mdone, 1);
-        mbar_init(lfull, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // The first operator fill of every stage and the first halo copy leave before the setup
+    // barrier (the TMEM allocation): each issuing thread initialises the barrier its copy
+    // completes on, and the setup barrier orders that before any wait on it.
+    if (warp < C::STAGES && lane == 0) {
+        mbar_init(&afull[warp], 1);
+        mbar_init(&aempty[warp], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        if (warp < nunits) {
+            mbar_expect_tx(&afull[warp], abytes);
+            bulk_load(astage + (size_t)warp * C::STAGE,
+                      rimg + (size_t)tc_image_block(tc_walk_unit(u0, u1, warp) & 31) * C::STAGE, abytes, &afull[warp]);
+        }
+    }
+    if (stw >= 0) {
+        if (st == 0) {
+            mbar_init(lfull, 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        pending = issue_tma(0);
     }
     if (warp == kMmaWarp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
@@ -368,26 +458,39 @@ __global__ void __launch_bounds__(kTcCtaThreads, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
 
+    // No MMA can start before the first class halo: when it comes by tensor copy, the whole CTA
+    // converts it.  If that copy does not land in time, the staging warps take the group over.
+    bool first_done = false;
+    if (ngrp > 0) {
+        int t, cls;
+        tc_group(u0, u1, 0, t, cls);
+        if (maps.use_tma[tc_tile(job, t).li]) {
+            const bool landed = mbar_wait(lfull, 0, 64);
+            if (__syncthreads_and(landed ? 1 : 0)) {
+                tc_convert_landed<P, kTcCtaThreads>(lbuf, hbuf, tid);
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                first_done = true;
+            }
+            __syncthreads();
+            if (first_done && tid == 0) mbar_arrive(&hfull[0]);
+        }
+    }
+
     if (warp < C::STAGES) {
         // ---------------- producer `warp`: units g = warp, warp + STAGES, ... of the walk ----------------
         if (lane == 0) {
             const int s = warp;
-            int k = 0;  // fills issued into stage s
+            int k = s < nunits ? 1 : 0;  // fills issued into stage s (the first left before the setup barrier)
             bool ok = true;
-            int g = 0;  // walk position
-            for (int i = 0; i < nseg && ok; ++i) {
-                const TcSeg sg = tc_seg(u0, u1, i);
-                for (int u = sg.sa; u < sg.sb; ++u, ++g) {
-                    if (g % C::STAGES != s) continue;
-                    if (k >= 1 && !mbar_wait(&aempty[s], (uint32_t)((k - 1) & 1))) {
-                        ok = false;
-                        break;
-                    }
-                    const int b = tc_image_block(u & 31);
-                    mbar_expect_tx(&afull[s], abytes);
-                    bulk_load(astage + (size_t)s * C::STAGE, rimg + (size_t)b * C::STAGE, abytes, &afull[s]);
-                    ++k;
+            for (int g = s + C::STAGES; g < nunits; g += C::STAGES) {
+                if (!mbar_wait(&aempty[s], (uint32_t)((k - 1) & 1))) {
+                    ok = false;
+                    break;
                 }
+                const int b = tc_image_block(tc_walk_unit(u0, u1, g) & 31);
+                mbar_expect_tx(&afull[s], abytes);
+                bulk_load(astage + (size_t)s * C::STAGE, rimg + (size_t)b * C::STAGE, abytes, &afull[s]);
+                ++k;
             }
             if (!ok) atomicOr(err, DEV_ERR_TIMEOUT);
             // do not leave while a copy is in flight: the last fill of stage s must have landed
@@ -462,7 +565,7 @@ __global__ void __launch_bounds__(kTcCtaThreads, 1)
         // before the TMEM is freed, every MMA issued here must have completed (also after a timeout)
         umma_commit(mdone);
         if (!mbar_wait(mdone, 0)) atomicOr(err, DEV_ERR_TIMEOUT);
-    } else if (warp >= kStageWarp0 && warp < kStageWarp0 + kStageWarps) {
+    } else if (stw >= 0) {
         // ---------------- class-halo staging ----------------
         // The halo of source class c' for a tile: the MEs of boxes (2 qx + c'x, 2 qy + c'y) for the
         // 10 x 34 parents (qx, qy) around it, zero outside the level (periodic lists wrap), as BF16
@@ -471,33 +574,11 @@ __global__ void __launch_bounds__(kTcCtaThreads, 1)
         // copy into the landing buffer (prefetched while the previous class is converted and
         // translated) and are converted shared-to-shared; smaller levels and periodic lists are
         // read from global memory.  An item is one (parent, chunk): 32 bytes in, 2 x 16 out.
-        constexpr int NST = 32 * kStageWarps;
         constexpr int NIT = C::KCH * C::NPOS;
-        const int st = tid - 32 * kStageWarp0;
-        int ngrp = 0;
-        for (int i = 0; i < nseg; ++i) {
-            const TcSeg sg = tc_seg(u0, u1, i);
-            ngrp += (((sg.sb - 1) & 31) >> 3) - ((sg.sa & 31) >> 3) + 1;
-        }
-        // the next tensor copy into the landing buffer: the first group at or after `from` on the TMA path
-        auto issue_tma = [&](int from) -> int {
-            for (int k = from; k < ngrp; ++k) {
-                int t, cls;
-                tc_group(u0, u1, k, t, cls);
-                const TcTile tl = tc_tile(job, t);
-                if (!maps.use_tma[tl.li]) continue;
-                if (st == 0) {
-                    mbar_expect_tx(lfull, (uint32_t)C::LBUF);
-                    tma_load_5d(lbuf, &maps.map[tl.li], 0, cls & 1, tl.PX0 - 1, cls >> 1, tl.PY0 - 1, lfull);
-                }
-                return k;
-            }
-            return -1;
-        };
-        int pending = issue_tma(0);  // group whose tensor copy is in flight, or -1
-        int nlanded = 0;             // tensor copies consumed so far (landing-buffer phase)
+        int nlanded = first_done ? 1 : 0;  // tensor copies consumed so far (landing-buffer phase)
+        if (first_done) pending = issue_tma(1);
         bool ok = true;
-        for (int k = 0; k < ngrp && ok; ++k) {
+        for (int k = first_done ? 1 : 0; k < ngrp && ok; ++k) {
             int t, cls;
             tc_group(u0, u1, k, t, cls);
             const TcTile tl = tc_tile(job, t);
@@ -511,21 +592,7 @@ __global__ void __launch_bounds__(kTcCtaThreads, 1)
             }
             unsigned char* buf = hbuf + (size_t)hb * C::HBUF;
             if (pending == k) {
-                // FP32 [parent][2p] in the landing buffer -> BF16 hi/lo halo
-#pragma unroll 1
-                for (int it0 = st; it0 < NIT; it0 += NST * kStageBatch) {
-#pragma unroll
-                    for (int b = 0; b < kStageBatch; ++b) {
-                        const int it = it0 + b * NST;
-                        if (it >= NIT) break;
-                        const int pos = it / C::KCH, ch = it % C::KCH;
-                        const float4* src = reinterpret_cast<const float4*>(lbuf + (size_t)pos * (C::K2 * 4) + ch * 32);
-                        tc_stage_chunk(src, src + 1,
-                                       buf + (size_t)ch * C::IPLANE + (size_t)(2 * (pos / C::HX)) * C::ROWB +
-                                           (size_t)(pos % C::HX) * 16,
-                                       C::ROWB);
-                    }
-                }
+                tc_convert_landed<P, NST>(lbuf, buf, st);
                 ++nlanded;
             } else {
 #pragma unroll 1
