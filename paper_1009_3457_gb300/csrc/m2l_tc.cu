@@ -216,7 +216,8 @@ __device__ __forceinline__ TcTile tc_tile(const M2LLaunch& job, int tile)
 
 // Per launch level: a 5-D tensor map over its FP32 MEs, [qy][cy][qx][cx][2p floats]
 // (box (2 qx + cx, 2 qy + cy)), so that one box {2p, 1, 10, 1, 34} at (0, c'x,
-// PX0 - 1, c'y, PY0 - 1) is the class-c' halo of a tile, zero outside the level.
+// PX0 - 1, c'y, PY0 - 1) is the class-c' halo of a tile, zero outside the level
+// (also for levels smaller than the box).
 struct TcMaps {
     CUtensorMap map[kMaxLaunchLevels];
     int use_tma[kMaxLaunchLevels];  // 0: the level is smaller than the box, or the lists are periodic
@@ -570,10 +571,10 @@ __global__ void __launch_bounds__(kTcCtaThreads, 1)
         // The halo of source class c' for a tile: the MEs of boxes (2 qx + c'x, 2 qy + c'y) for the
         // 10 x 34 parents (qx, qy) around it, zero outside the level (periodic lists wrap), as BF16
         // hi and lo in the layout the MMAs read: [chunk of 4 complex][halo row][hi, lo][halo
-        // column] x 16 bytes.  Levels at least as large as the box arrive as FP32 by one tensor
-        // copy into the landing buffer (prefetched while the previous class is converted and
-        // translated) and are converted shared-to-shared; smaller levels and periodic lists are
-        // read from global memory.  An item is one (parent, chunk): 32 bytes in, 2 x 16 out.
+        // column] x 16 bytes.  A halo arrives as FP32 by one tensor copy into the landing buffer
+        // (prefetched while the previous class is converted and translated) and is converted
+        // shared-to-shared; periodic lists (which wrap) are read from global memory (an item is
+        // one (parent, chunk): 32 bytes in, 2 x 16 out).
         constexpr int NIT = C::KCH * C::NPOS;
         int nlanded = first_done ? 1 : 0;  // tensor copies consumed so far (landing-buffer phase)
         if (first_done) pending = issue_tma(1);
@@ -832,7 +833,7 @@ static int launch_tc_p(M2LLaunch& job, const void* img, bool split, int* err, cu
     for (int i = 0; i < job.nlev; ++i) {
         const int np = 1 << (job.lv[i].level - 1);
         const int side = 2 * np;
-        if (!encode || job.periodic || np < C::HX || np < C::HY) continue;  // box larger than the level: global loads
+        if (!encode || job.periodic) continue;  // periodic lists wrap: global loads
         // MEs [iy][ix][2p floats] read as [qy][cy][qx][cx][2p]: box (2 qx + cx, 2 qy + cy)
         const cuuint64_t dims[5] = {(cuuint64_t)(2 * P), 2, (cuuint64_t)np, 2, (cuuint64_t)np};
         const cuuint64_t rowb = (cuuint64_t)side * 2 * P * 4;  // bytes per box row
@@ -842,7 +843,11 @@ static int launch_tc_p(M2LLaunch& job, const void* img, bool split, int* err, cu
         const CUresult r = encode(&maps.map[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, (void*)job.lv[i].M, dims, strides,
                                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r != CUDA_SUCCESS) return fail(FMM_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+        if (r != CUDA_SUCCESS) {
+            // a level smaller than the box may be refused: its halos are then read from global memory
+            if (np < C::HX || np < C::HY) continue;
+            return fail(FMM_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+        }
         maps.use_tma[i] = 1;
     }
     static unsigned long long opted;

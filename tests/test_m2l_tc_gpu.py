@@ -98,6 +98,27 @@ def test_tc_levels_periodic_accumulate(fmm, orc, particles):
         assert _rel(got, ref) <= 1e-4, l
 
 
+@pytest.mark.parametrize("p", [16, 24])
+def test_tc_levels_free_space_accumulate(fmm, orc, particles, p):
+    """Levels 2..7 in one launch (tiles cut between CTAs, every level by tensor copy),
+    free-space lists, accumulating into existing values: every part of a cut tile adds."""
+    xy, c = particles
+    Lmax = 7
+    Ms = orc.upward_uniform(Lmax, p, xy, c)
+    tree = fmm.fmm_build_lists(None, Lmax)
+    levels = list(range(2, Lmax + 1))
+    rng = np.random.default_rng(11)
+    X = {l: (rng.standard_normal((4 ** l, p)) + 1j * rng.standard_normal((4 ** l, p))) for l in levels}
+    Md = [_dev(orc.scale_me(Ms[l], l)) for l in levels]
+    Ld = [_dev(X[l]) for l in levels]
+    fmm.fmm_m2l_levels(tree, 2, p, Md, Ld, prec=fmm.FMM_TC_BF16X3, accumulate=True)
+    fmm.fmm_sync_status()
+    for l, out in zip(levels, Ld):
+        ref = _oracle_level(orc, l, p, Ms[l])
+        got = _host(out) - X[l].astype(np.complex64).astype(np.complex128)
+        assert _rel(got, ref) <= 1e-4, l
+
+
 def test_tc_precision_workload_p24_potential(fmm, orc):
     """The p = 24 precision workload (4096 points, uniform tree to level 4): the far-field
     potential from the tensor-core LEs is within the oracle's own truncation error + 1e-4."""
