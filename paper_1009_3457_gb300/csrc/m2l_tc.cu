@@ -76,7 +76,7 @@ namespace fmmgb {
 constexpr int kTcTileX = 8;     // parents per tile row (one core-matrix group of the N operand)
 constexpr int kTcTileY = 32;    // parent rows per tile
 constexpr int kTcBlocks = 32;   // (e != 0) x 4 source classes
-constexpr int kTcReplicas = 4;  // copies of the operator image in global memory
+constexpr int kTcReplicas = 1;  // copies of the operator image in global memory (1, 2 and 4 measured alike)
 constexpr int kTcMinUnits = 8;  // fewest units per CTA: a tile is cut between at most 5 CTAs
 
 template <int P>
