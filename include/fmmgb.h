@@ -263,8 +263,10 @@ typedef struct {
     int32_t tuned;         /* 1: configuration chosen by timing (FMM_BATCH_AUTOTUNE) */
     float tuned_ms;        /* best timed run of the autotuner, 0 if not tuned */
     int32_t variant;       /* work-unit variant: index into the tuned set */
-    int32_t form;          /* 0: p/2 rows per lane, packed multiply-adds; 1: p rows per lane, half
-                              the list entries each; 2: p/2 rows per lane, scalar multiply-adds */
+    int32_t form;          /* -1: each order's default (p/2 rows per lane, packed multiply-adds, the
+                              sums of w Re m and w Im m apart at p = 12, 16); 0: p/2 rows per lane,
+                              packed multiply-adds; 1: p rows per lane, half the list entries each;
+                              2: p/2 rows per lane, scalar multiply-adds */
     int32_t loads;         /* halo loads a thread keeps in flight while staging a tile */
     int32_t from_cache;    /* 1: the tuned choice was reused (memory or cache file), not timed */
 } fmm_batch_info_t;

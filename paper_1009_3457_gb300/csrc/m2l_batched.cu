@@ -74,8 +74,9 @@ constexpr int kBatchMinCtas = 6;
 struct BatchVariant {
     int form, loads;
 };
-constexpr BatchVariant kBatchVariants[] = {{kFormRowsPacked, 3}, {kFormRowsPacked, 2}, {kFormEntries, 3}, {kFormRows, 3}};
-constexpr int kBatchNumVariants = 4;
+constexpr BatchVariant kBatchVariants[] = {
+    {kFormAuto, 3}, {kFormRowsPacked, 3}, {kFormRowsPacked, 2}, {kFormEntries, 3}, {kFormRows, 3}};
+constexpr int kBatchNumVariants = 5;
 
 template <int FORM, int LOADS>
 __global__ void __launch_bounds__(kThreads, kBatchMinCtas)
@@ -123,10 +124,11 @@ __global__ void __launch_bounds__(kThreads, kBatchMinCtas)
 static const void* batch_kernel(int v)
 {
     switch (v) {
-        case 1: return (const void*)m2l_batched_kernel<kFormRowsPacked, 2>;
-        case 2: return (const void*)m2l_batched_kernel<kFormEntries, 3>;
-        case 3: return (const void*)m2l_batched_kernel<kFormRows, 3>;
-        default: return (const void*)m2l_batched_kernel<kFormRowsPacked, 3>;
+        case 1: return (const void*)m2l_batched_kernel<kFormRowsPacked, 3>;
+        case 2: return (const void*)m2l_batched_kernel<kFormRowsPacked, 2>;
+        case 3: return (const void*)m2l_batched_kernel<kFormEntries, 3>;
+        case 4: return (const void*)m2l_batched_kernel<kFormRows, 3>;
+        default: return (const void*)m2l_batched_kernel<kFormAuto, 3>;
     }
 }
 

@@ -182,8 +182,11 @@ __device__ __forceinline__ void m2l_load_operator(unsigned char* raw, const floa
 //   kFormRowsPacked  each lane p/2 rows, all 27 list entries, packed f32x2 multiply-adds;
 //   kFormEntries     each lane all p rows, 14 or 13 of the 27 entries, one shuffle adds the halves;
 //   kFormRows        each lane p/2 rows, all 27 entries, scalar FFMAs;
-//   kFormAuto        the order's default (M2LCfg: packed rows for p <= 16, scalar rows for p = 24).
-enum : int { kFormAuto = -1, kFormRowsPacked = 0, kFormEntries = 1, kFormRows = 2 };
+//   kFormRowsPacked2 as kFormRowsPacked, with the sums of w m.re and of w m.im in separate
+//                    packed accumulators (no (-w.im, w.re) copy of the operator window);
+//   kFormAuto        the order's default: packed rows with separate sums at p = 12, 16 (measured
+//                    faster there, slower at p = 8), packed rows at p = 6, 8, scalar rows at p = 24.
+enum : int { kFormAuto = -1, kFormRowsPacked = 0, kFormEntries = 1, kFormRows = 2, kFormRowsPacked2 = 3 };
 
 // Translate and reduce one tile (ADAPTIVE and g.exists set: only existing
 // sources are read and existing targets written).  Requires the operator of order P in shared
@@ -194,7 +197,8 @@ __device__ __forceinline__ void m2l_tile(unsigned char* raw, const TileGeom& g, 
 {
     using C = M2LCfg<P>;
     constexpr int F = FORM != kFormAuto ? FORM
-                                        : (C::PACKED ? kFormRowsPacked : (C::SPLIT_ROWS ? kFormRows : kFormEntries));
+                                        : (C::PACKED ? (P >= 12 ? kFormRowsPacked2 : kFormRowsPacked)
+                                                     : (C::SPLIT_ROWS ? kFormRows : kFormEntries));
     constexpr bool SPLIT = F != kFormEntries;
     constexpr int RN = SPLIT ? P / 2 : P, Q = P / 2;
     const TileSmem<P> s(raw);
@@ -328,6 +332,45 @@ __device__ __forceinline__ void m2l_tile(unsigned char* raw, const TileGeom& g, 
         }
 #pragma unroll
         for (int i = 0; i < RN; ++i) acc[i] = upk2(pacc[i]);
+    } else if constexpr (F == kFormRowsPacked2) {
+        // as above; acc = sum w m.re + i sum w m.im, the two sums in separate packed accumulators
+        const int n0 = half * RN;
+        unsigned long long pa[RN], pb[RN];
+#pragma unroll
+        for (int i = 0; i < RN; ++i) pa[i] = pb[i] = 0ull;
+#pragma unroll 1
+        for (int e = 0; e < 27; ++e) {
+            const int2 ent = mylist[e];
+            const float2* hrow = s.hs + ent.x + n0;
+            const float2* src = tbase + ent.y;
+            unsigned long long w[RN];
+#pragma unroll
+            for (int i = 0; i < RN; ++i) {
+                const float2 h = hrow[i];
+                w[i] = pk2(h.x, h.y);
+            }
+#pragma unroll
+            for (int k = 0; k < P; ++k) {
+                const float2 m = src[k * kPlane];
+                const unsigned long long mx = pk2(m.x, m.x), my = pk2(m.y, m.y);
+#pragma unroll
+                for (int i = 0; i < RN; ++i) {
+                    pa[i] = fma2(w[i], mx, pa[i]);
+                    pb[i] = fma2(w[i], my, pb[i]);
+                }
+                if (k + 1 < P) {
+#pragma unroll
+                    for (int i = 0; i + 1 < RN; ++i) w[i] = w[i + 1];
+                    const float2 h = hrow[RN + k];
+                    w[RN - 1] = pk2(h.x, h.y);
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < RN; ++i) {
+            const float2 a = upk2(pa[i]), b = upk2(pb[i]);
+            acc[i] = make_float2(a.x - b.y, a.y + b.x);
+        }
     } else {
         // half-warp `half` takes rows [RN half, RN half + RN); all 27 entries
         const int n0 = half * RN;
