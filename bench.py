@@ -409,8 +409,8 @@ def _fgt_hermite_rows(torch, fmmgb, dev, fxd, fqd, args, stream, flush):
 
 SUMMARY_ROWS = ("m2l_adjoint_fp32_levels_2_8", "m2l_tc_bf16x3_levels_2_8", "m2l_fp32_p24_levels_2_8",
                 "m2l_tc_bf16x3_p24_levels_2_8", "m2l_adaptive_gmm_levels_2_9", "m2l_batched_256_problems",
-                "m2l_paper_design_levels_2_8", "fgt_h2t_sigma0.05_p16", "fgt_h2t_sigma0.1_p16",
-                "fgt_h2t_sigma0.2_p16", "fgt_h2p_sigma0.05_p16", "fgt_h2p_tc_bf16x3_sigma0.05_p16",
+                "m2l_paper_design_levels_2_8", "fgt_h2t_sigma0.05_p16", "fgt_h2t_tc_bf16x3_sigma0.05_p16",
+                "fgt_h2t_sigma0.1_p16", "fgt_h2t_sigma0.2_p16", "fgt_h2p_sigma0.05_p16", "fgt_h2p_tc_bf16x3_sigma0.05_p16",
                 "fmm_p2p_level8", "fmm_potential_level8_p16", "far_field_gradient_gmm")
 
 
@@ -554,8 +554,8 @@ def run_ours(args):
         if rank == 0:
             print(json.dumps({"mode": "kernels", "steps": args.steps, "launches_per_step": 1, "batch": bt["info"]}))
         return 0
-    if args.mode == "kernels" and args.prec == "fgt":
-        # profiling case: the FGT H2T of the sigma (default 0.05), p = 16 workload
+    if args.mode == "kernels" and args.prec in ("fgt", "fgt_tc"):
+        # profiling case: the FGT H2T of the sigma (default 0.05), p = 16 workload (fgt_tc: tensor cores)
         fcfg = workloads.CONFIGS["fgt"]
         fx, fq = workloads.gmm_particles(fcfg["n"], workloads.rng_for("fgt"))
         sigma, fp = args.sigma, 16
@@ -564,12 +564,15 @@ def run_ours(args):
         Cf = torch.empty_like(A)
         W = torch.empty_like(A)
         fmmgb.fgt_p2h(g, fp, sigma, torch.from_numpy(fx).to(dev), torch.from_numpy(fq).to(dev), A)
+        tc = args.prec == "fgt_tc"
         for _ in range(args.steps):
-            fmmgb.fgt_h2t(g, fcfg["ncut"], fp, sigma, A, Cf, work=W)
+            fmmgb.fgt_h2t(g, fcfg["ncut"], fp, sigma, A, Cf, work=W,
+                          prec=fmmgb.FMM_TC_BF16X3 if tc else fmmgb.FMM_FP32)
         torch.cuda.synchronize()
         fmmgb.fmm_sync_status()
         if rank == 0:
-            print(json.dumps({"mode": "kernels", "steps": args.steps, "launches_per_step": fgt_h2t_launches(g)}))
+            print(json.dumps({"mode": "kernels", "steps": args.steps,
+                              "launches_per_step": 1 if tc else fgt_h2t_launches(g)}))
         return 0
     if args.mode == "kernels" and args.prec == "p2p":
         # profiling case: the near field at level 8 of the 2^22-point headline workload
@@ -918,6 +921,21 @@ def run_ours(args):
                 rows[f"fgt_h2t_sigma{sigma}_p{fp}"] = {
                     "translations_per_s": ntr / (ms * 1e-3), "ms": ms, "launches": fgt_h2t_launches(g),
                     "grid": f"{1 << g}^2", "gflops_separable": gfs, "alu_frac": gfs / 1e3 / alu_peak_tflops()}
+                if fp == 16:
+                    # the same translation on the tensor cores (one cooperative launch, both passes)
+                    Ct = torch.empty_like(A)
+
+                    def fgt_tc():
+                        fmmgb.fgt_h2t(g, fcfg["ncut"], fp, sigma, A, Ct, work=W, prec=fmmgb.FMM_TC_BF16X3)
+
+                    ms_tc = statistics.median(_timed(torch, _graph(torch, fgt_tc), args.steps, stream, flush))
+                    mma = metrics.fgt_h2t_tc_mma_flops(g, fcfg["ncut"]) / (ms_tc * 1e-3) / 1e12
+                    rel = float(torch.linalg.vector_norm((Ct - Cf).double()) / torch.linalg.vector_norm(Cf.double()))
+                    rows[f"fgt_h2t_tc_bf16x3_sigma{sigma}_p16"] = {
+                        "ms": ms_tc, "translations_per_s": ntr / (ms_tc * 1e-3), "launches": 1,
+                        "tensor_tflops": mma, "tensor_frac": mma / BF16_PEAK_TFLOPS,
+                        "speedup_vs_fp32": ms / ms_tc, "rel_l2_vs_fp32_path": rel,
+                        "note": "one cooperative launch: both separable passes, grid barrier between"}
         rows.update(_fgt_hermite_rows(torch, fmmgb, dev, fxd, fqd, args, stream, flush))
         fmmgb.fmm_sync_status()
 
@@ -992,7 +1010,7 @@ def main():
     ap.add_argument("--mode", default="full", choices=["full", "kernels"],
                     help="kernels: only the timed step's launches (for ncu captures)")
     ap.add_argument("--tc", action="store_true", help="with --prec h2p: the tensor-core (BF16x3) form")
-    ap.add_argument("--prec", default="fp32", choices=["fp32", "tc3", "tc1", "batched", "fgt", "h2p", "p2p"],
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "tc3", "tc1", "batched", "fgt", "fgt_tc", "h2p", "p2p"],
                     help="launches of --mode kernels: the step at this precision, or the 256-problem batch, "
                          "or the FGT H2T at sigma 0.05, p 16")
     ap.add_argument("--sigma", type=float, default=0.05, help="--mode kernels --prec fgt: the FGT bandwidth")

@@ -294,6 +294,12 @@ int fmm_m2l_batched(const fmm_tree* const* trees, const int32_t* p, int32_t npro
  *   grid_log2  g, 0..12; box b = iy * 2^g + ix, centre ((ix+1/2) 2^-g, (iy+1/2) 2^-g).
  *   n_cut      neighbourhood half-width in boxes, 0..16.
  *   p          Hermite order per dimension: 4, 8, 12 or 16.
+ *   prec       FMM_FP32 (CUDA cores), or FMM_TC_BF16X3 / FMM_TC_BF16 (tcgen05
+ *              tensor cores: each separable pass as a dense product of 8 target
+ *              boxes x 16 rows by (2 n_cut + 1) x 16 over the BF16 hi/lo split,
+ *              three products or one, FP32 accumulation; p = 16, grid_log2 >= 3,
+ *              one cooperative launch; FMM_EUNSUPPORTED otherwise).  Any other
+ *              value: FMM_EINVAL.
  *   sigma      Gaussian width (exp(-|x-y|^2 / (2 sigma^2))), > 0.
  *   A          device, const, [4^g][p][p] float32 Hermite coefficients
  *              A[b][a1][a2] (a1: x order, a2: y order), Eq. A_alpha.
@@ -305,7 +311,7 @@ int fmm_m2l_batched(const fmm_tree* const* trees, const int32_t* p, int32_t npro
  *   flags      FMM_ACCUMULATE or 0.
  * All pointers 16-byte aligned; A and C must not overlap.
  * ------------------------------------------------------------------------- */
-int fgt_h2t(int32_t grid_log2, int32_t n_cut, int32_t p, double sigma, const float* A, float* C,
+int fgt_h2t(int32_t grid_log2, int32_t n_cut, int32_t p, int32_t prec, double sigma, const float* A, float* C,
             float* work, int32_t flags, void* stream);
 
 /* ---------------------------------------------------------------------------
@@ -323,7 +329,7 @@ int fgt_h2t(int32_t grid_log2, int32_t n_cut, int32_t p, double sigma, const flo
  * FMM_EINVAL and a message, and fgt_h2t serves them.  Every GPU that loads the
  * library keeps that array for the life of the process.
  *
- * Arguments and results are those of fgt_h2t without `work`; A and C must not
+ * Arguments and results are those of fgt_h2t (FMM_FP32) without `prec` and `work`; A and C must not
  * lie inside the built-in array (FMM_EINVAL).  Set-up on first use, none of it
  * an allocation: the first call on a device looks up the array's device
  * address, and the first call of each p on a device sets that kernel's

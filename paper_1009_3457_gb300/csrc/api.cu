@@ -782,12 +782,25 @@ int fmmgb::fgt_check_args(const char* who, int g, int n_cut, int p, double sigma
 
 extern "C" {
 
-int fgt_h2t(int32_t grid_log2, int32_t n_cut, int32_t p, double sigma, const float* A, float* C, float* work,
-            int32_t flags, void* stream)
+int fgt_h2t(int32_t grid_log2, int32_t n_cut, int32_t p, int32_t prec, double sigma, const float* A, float* C,
+            float* work, int32_t flags, void* stream)
 {
     clear_error();
     int rc = fgt_check_args("fgt_h2t", grid_log2, n_cut, p, sigma, A, C, work, flags);
     if (rc) return rc;
+    if (prec != FMM_FP32 && prec != FMM_TC_BF16X3 && prec != FMM_TC_BF16)
+        return fail(FMM_EINVAL, "fgt_h2t: unknown precision %d", prec);
+    if (prec != FMM_FP32) {
+        if (!fgt_h2t_tc_supported(grid_log2, n_cut, p))
+            return fail(FMM_EUNSUPPORTED, "fgt_h2t: tensor-core precisions take p = 16, grid_log2 >= 3, n_cut <= 16");
+        float* Y = work;
+        if (!Y) {
+            const size_t bytes = ((size_t)1 << (2 * grid_log2)) * (size_t)p * p * sizeof(float);
+            if ((rc = fgt_workspace(bytes, &Y))) return rc;
+        }
+        return launch_fgt_h2t_tc(grid_log2, n_cut, sigma, prec == FMM_TC_BF16X3, A, Y, C, (flags & FMM_ACCUMULATE) != 0,
+                                 (cudaStream_t)stream);
+    }
     if (fgt_fused_supported(grid_log2))
         return launch_fgt_h2t_fused(grid_log2, n_cut, p, sigma, A, C, (flags & FMM_ACCUMULATE) != 0, (cudaStream_t)stream);
     float* Y = work;

@@ -192,6 +192,10 @@ int launch_p2m_binned(int level, int p, const double* xy, const double* c, int n
 int launch_p2m(int level, int p, const double* xy, const double* c, int64_t n, float2* M, bool accumulate,
                cudaStream_t st);
 int launch_m2m(int child_level, int p, const float2* Mc, float2* Mp, bool accumulate, cudaStream_t st);
+// FGT H2T on the tensor cores (fgt_h2t_tc.cu): p = 16, grid_log2 >= 3, n_cut <= 16
+bool fgt_h2t_tc_supported(int g, int ncut, int p);
+int launch_fgt_h2t_tc(int g, int ncut, double sigma, bool split, const float* A, float* Y, float* C, bool acc,
+                      cudaStream_t st);
 int launch_m2m_adjoint(int child_level, int p, const float2* Wp, float2* Wc, bool accumulate, cudaStream_t st);
 int launch_fgt_p2h(int g, int p, double sigma, const double* x, const double* q, int64_t n, float* A, bool acc,
                    cudaStream_t st);

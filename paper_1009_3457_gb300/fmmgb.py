@@ -107,7 +107,7 @@ SIGNATURES = {
     "fmm_p2m_adjoint": (ctypes.c_int, [_i32, _i32, _vp, _vp, _i64, _vp, _vp, _i32, _vp]),
     "fmm_p2m": (ctypes.c_int, [_i32, _i32, _vp, _vp, _i64, _vp, _i32, _vp]),
     "fmm_m2m": (ctypes.c_int, [_i32, _i32, _vp, _vp, _i32, _vp]),
-    "fgt_h2t": (ctypes.c_int, [_i32, _i32, _i32, _d, _vp, _vp, _vp, _i32, _vp]),
+    "fgt_h2t": (ctypes.c_int, [_i32, _i32, _i32, _i32, _d, _vp, _vp, _vp, _i32, _vp]),
     "fgt_h2t_noalloc": (ctypes.c_int, [_i32, _i32, _i32, _d, _vp, _vp, _i32, _vp]),
     "fgt_t2p": (ctypes.c_int, [_i32, _i32, _d, _vp, _vp, _i64, _vp, _i32, _vp]),
     "fgt_p2h": (ctypes.c_int, [_i32, _i32, _d, _vp, _vp, _i64, _vp, _i32, _vp]),
@@ -391,8 +391,8 @@ def fmm_p2m_adjoint(level: int, p: int, xy, c, G, grad, accumulate: bool = False
 
 
 def fgt_h2t(grid_log2: int, n_cut: int, p: int, sigma: float, A, C, work=None, accumulate: bool = False,
-            stream=None):
-    _check(load().fgt_h2t(grid_log2, n_cut, p, float(sigma), _ptr(A), _ptr(C), _ptr(work),
+            stream=None, prec: int = FMM_FP32):
+    _check(load().fgt_h2t(grid_log2, n_cut, p, prec, float(sigma), _ptr(A), _ptr(C), _ptr(work),
                           FMM_ACCUMULATE if accumulate else 0, _stream(stream)))
 
 

@@ -117,3 +117,12 @@ def m2l_tc_mma_flops(levels, p: int, products: int = 3) -> int:
         np_ = 1 << (lv - 1)
         tiles += -(-np_ // 8) * -(-np_ // 32)
     return tiles * 32 * (2 * p // 16) * mt * products * 2 * 128 * 256 * 16
+
+
+def fgt_h2t_tc_mma_flops(g: int, ncut: int, products: int = 3) -> int:
+    """Tensor-core flops the tensor-core H2T issues: per pass, 2^g lines x 2^g / 8 segments of
+    M = 128 rows, and per source offset (2 n_cut + 1 of them) one N = 32 product (the hi and lo
+    planes of H_d) and one N = 16 product with the split, or one N = 16 product without; K = 16."""
+    segs = (1 << g) * ((1 << g) // 8)
+    per_d = 2 * 128 * 16 * (32 + 16) if products == 3 else 2 * 128 * 16 * 16
+    return 2 * segs * (2 * ncut + 1) * per_d

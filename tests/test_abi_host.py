@@ -241,6 +241,14 @@ def test_fgt_hermite_entry_points_reject_bad_arguments(fmm):
     assert lib.fgt_h2p(3, 2, 8, 7, 0.1, 64, 128, 10, 256, 512, 1024, 0, None) == fmm.FMM_EINVAL   # precision
     assert lib.fgt_h2p(3, 2, 8, T3, 0.1, 64, 128, 10, 256, 512, 1024, 0, None) == fmm.FMM_EUNSUPPORTED   # TC p
     assert lib.fgt_h2p(3, 16, 16, T3, 0.1, 64, 128, 10, 256, 512, 1024, 0, None) == fmm.FMM_EUNSUPPORTED  # TC n_cut
+    # fgt_h2t(g, ncut, p, prec, sigma, A, C, work, flags, stream)
+    A_, C_ = 1 << 20, 1 << 22
+    assert lib.fgt_h2t(3, 2, 8, 7, 0.1, A_, C_, None, 0, None) == fmm.FMM_EINVAL            # precision
+    assert "precision" in fmm.fmm_last_error()
+    assert lib.fgt_h2t(3, 2, 8, T3, 0.1, A_, C_, None, 0, None) == fmm.FMM_EUNSUPPORTED     # TC p
+    assert lib.fgt_h2t(2, 2, 16, T3, 0.1, A_, C_, None, 0, None) == fmm.FMM_EUNSUPPORTED    # TC grid under 8 x 8
+    assert lib.fgt_h2t(3, 17, 16, T3, 0.1, A_, C_, None, 0, None) == fmm.FMM_EINVAL         # n_cut
+    assert lib.fgt_h2t(3, 2, 16, T3, 0.1, A_, C_ + 8, None, 0, None) == fmm.FMM_EINVAL      # C misaligned
 
 
 def test_p2p_rejects_bad_arguments(fmm):
