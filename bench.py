@@ -408,7 +408,8 @@ def _fgt_hermite_rows(torch, fmmgb, dev, fxd, fqd, args, stream, flush):
 
 
 SUMMARY_ROWS = ("m2l_adjoint_fp32_levels_2_8", "m2l_tc_bf16x3_levels_2_8", "m2l_fp32_p24_levels_2_8",
-                "m2l_tc_bf16x3_p24_levels_2_8", "m2l_adaptive_gmm_levels_2_9", "m2l_batched_256_problems",
+                "m2l_tc_bf16x3_p24_levels_2_8", "m2l_adaptive_gmm_levels_2_9", "m2l_tc_bf16x3_adaptive_gmm_levels_2_9",
+                "m2l_batched_256_problems",
                 "m2l_paper_design_levels_2_8", "fgt_h2t_sigma0.05_p16", "fgt_h2t_tc_bf16x3_sigma0.05_p16",
                 "fgt_h2t_sigma0.1_p16", "fgt_h2t_sigma0.2_p16", "fgt_h2p_sigma0.05_p16", "fgt_h2p_tc_bf16x3_sigma0.05_p16",
                 "fmm_p2p_level8", "fmm_potential_level8_p16", "far_field_gradient_gmm")
@@ -821,16 +822,25 @@ def run_ours(args):
         gL = [torch.zeros_like(m) for m in gM]
         gG = [torch.zeros_like(m) for m in gM]
         gntr = sum(gtree.translations(l) for l in glev)
+        gLt = [torch.zeros_like(m) for m in gM]
         for name, fn in (("m2l_adaptive_gmm_levels_2_9",
                           lambda: fmmgb.fmm_m2l_levels(gtree, 2, gp, gM, gL)),
                          ("m2l_adjoint_adaptive_gmm_levels_2_9",
-                          lambda: fmmgb.fmm_m2l_adjoint_levels(gtree, 2, gp, gL, gG, conj=True))):
+                          lambda: fmmgb.fmm_m2l_adjoint_levels(gtree, 2, gp, gL, gG, conj=True)),
+                         ("m2l_tc_bf16x3_adaptive_gmm_levels_2_9",
+                          lambda: fmmgb.fmm_m2l_levels(gtree, 2, gp, gM, gLt, prec=fmmgb.FMM_TC_BF16X3))):
             ms = statistics.median(_timed(torch, _graph(torch, fn), args.steps, stream, flush))
             rows[name] = {"translations_per_s": gntr / (ms * 1e-3), "ms": ms, "launches": 1, "translations": gntr,
                           "gflops": gntr * metrics.m2l_flops_per_translation(gp) / (ms * 1e-3) / 1e9,
-                          "alu_frac": gntr * metrics.m2l_flops_per_translation(gp) / (ms * 1e-3) / 1e12
-                          / alu_peak_tflops(),
                           "boxes": {l: int(gtree.level_info(l).nexist) for l in glev}}
+            if "tc" in name:
+                rows[name]["speedup_vs_fp32"] = rows["m2l_adaptive_gmm_levels_2_9"]["ms"] / ms
+                rows[name]["rel_l2_vs_fp32_path"] = float(
+                    sum(torch.linalg.vector_norm((a - b).to(torch.complex128)) ** 2 for a, b in zip(gLt, gL)) ** 0.5
+                    / sum(torch.linalg.vector_norm(b.to(torch.complex128)) ** 2 for b in gL) ** 0.5)
+            else:
+                rows[name]["alu_frac"] = (gntr * metrics.m2l_flops_per_translation(gp) / (ms * 1e-3) / 1e12
+                                          / alu_peak_tflops())
         from paper_1009_3457_gb300 import farfield
 
         zr = np.random.default_rng(workloads.SEED_BASE + 5)

@@ -154,7 +154,9 @@ int fmm_prepare(int32_t p, int32_t prec);
  *          zeroed, or left unchanged with FMM_ACCUMULATE).
  *   p      number of terms: 6, 8, 12, 16 or 24.
  *   prec   FMM_FP32, FMM_TC_BF16X3 or FMM_TC_BF16 (tensor-core forms: p = 16
- *          or 24, uniform trees; FMM_EUNSUPPORTED otherwise).
+ *          or 24, FMM_EUNSUPPORTED otherwise; on an adaptive level they run the
+ *          8 x 32-parent tiles that hold an existing box, with absent sources
+ *          read as zero and absent targets left untouched).
  *   M      device, const, [4^level][p] complex64 scaled MEs (input).
  *   L      device, [4^level][p] complex64 scaled LEs (output; must not
  *          overlap M).

@@ -302,6 +302,9 @@ struct fmm_tree {
         uint8_t* exists_dev = nullptr;
         int32_t* tiles_dev = nullptr;  // 4 x 4-parent tiles holding at least one existing box
         int32_t ntiles = 0;
+        bool tc_ready = false;
+        int32_t* tc_tiles_dev = nullptr;  // 8 x 32-parent tiles (tensor-core M2L) holding an existing box
+        int32_t tc_ntiles = 0;
     };
     Level levels[FMM_MAX_LEVEL + 1];
     std::mutex mu;
@@ -437,6 +440,44 @@ int fmmgb::tree_device_level(const fmm_tree* ctree, int level, const uint8_t** e
     return FMM_OK;
 }
 
+// The 8 x 32-parent tiles of an adaptive level (tensor-core M2L, tile t = ty * ceil(np / 8) + tx)
+// that hold at least one existing box, uploaded on first use; NULL, -1 for a level where every
+// box exists.
+int fmmgb::tree_device_tc_tiles(const fmm_tree* ctree, int level, const int32_t** tiles, int* ntiles)
+{
+    fmm_tree* t = const_cast<fmm_tree*>(ctree);
+    auto& L = t->levels[level];
+    *tiles = nullptr;
+    *ntiles = -1;
+    if (L.exists.empty()) return FMM_OK;
+    std::lock_guard<std::mutex> lk(t->mu);
+    if (!L.tc_ready) {
+        const int64_t side = (int64_t)1 << level, np = side / 2;
+        const int64_t tpr = (np + 7) / 8, rows = (np + 31) / 32;
+        std::vector<int32_t> tl;
+        for (int64_t tt = 0; tt < tpr * rows; ++tt) {
+            const int64_t x0 = (tt % tpr) * 16, y0 = (tt / tpr) * 64;  // boxes of the tile's parents
+            bool any = false;
+            for (int64_t y = y0; y < y0 + 64 && y < side && !any; ++y)
+                for (int64_t x = x0; x < x0 + 16 && x < side; ++x)
+                    if (L.exists[(size_t)(y * side + x)]) {
+                        any = true;
+                        break;
+                    }
+            if (any) tl.push_back((int32_t)tt);
+        }
+        if (!tl.empty()) {
+            FMM_CUDA_TRY(cudaMalloc(&L.tc_tiles_dev, tl.size() * sizeof(int32_t)));
+            FMM_CUDA_TRY(cudaMemcpy(L.tc_tiles_dev, tl.data(), tl.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+        }
+        L.tc_ntiles = (int32_t)tl.size();
+        L.tc_ready = true;
+    }
+    *tiles = L.tc_tiles_dev;
+    *ntiles = L.tc_ntiles;
+    return FMM_OK;
+}
+
 extern "C" {
 
 const char* fmm_last_error(void) { return g_msg; }
@@ -552,6 +593,7 @@ void fmm_tree_destroy(fmm_tree* tree)
         if (L.code_dev) cudaFree(L.code_dev);
         if (L.exists_dev) cudaFree(L.exists_dev);
         if (L.tiles_dev) cudaFree(L.tiles_dev);
+        if (L.tc_tiles_dev) cudaFree(L.tc_tiles_dev);
     }
     delete tree;
 }
@@ -621,8 +663,9 @@ static int m2l_dispatch(const char* who, const fmm_tree* tree, int32_t lmin, int
         int ntiles = -1;
         if ((rc = tree_device_level(tree, l, &ex, &tiles, &ntiles))) return rc;
         if (ntiles == 0) continue;  // no existing box at this level
-        if (ex && prec != FMM_FP32)
-            return fail(FMM_EUNSUPPORTED, "%s: tensor-core precisions are provided for uniform trees", who);
+        const int32_t* tc_tiles = nullptr;
+        int tc_ntiles = -1;
+        if (ex && prec != FMM_FP32 && (rc = tree_device_tc_tiles(tree, l, &tc_tiles, &tc_ntiles))) return rc;
         M2LLevel& d = job.lv[job.nlev++];
         d.M = (const float2*)in[l - lmin];
         d.L = (float2*)out[l - lmin];
@@ -630,6 +673,8 @@ static int m2l_dispatch(const char* who, const fmm_tree* tree, int32_t lmin, int
         d.exists = ex;
         d.tiles = tiles;
         d.ntiles = ntiles;
+        d.tc_tiles = tc_tiles;
+        d.tc_ntiles = tc_ntiles;
     }
     if (job.nlev == 0) return FMM_OK;
     // The adjoint is the forward stencil with the table of -a(D) (plain) or

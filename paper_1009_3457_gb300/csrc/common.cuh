@@ -141,6 +141,8 @@ struct M2LLevel {
     const uint8_t* exists;    // adaptive level: [4^level] box existence, NULL = every box exists
     const int32_t* tiles;     // adaptive level: the tiles to run (ntiles of them), NULL = all
     int ntiles;
+    const int32_t* tc_tiles;  // adaptive level, tensor cores: the 8 x 32-parent tiles to run, NULL = all
+    int tc_ntiles;
 };
 constexpr int kMaxLaunchLevels = FMM_MAX_LEVEL + 1;
 struct M2LLaunch {
@@ -158,6 +160,7 @@ int tree_adaptive(const fmm_tree* t);
 // 4 x 4-parent tiles that hold an existing box (uploaded on first use,
 // synchronously).  For a level where every box exists: NULL, NULL, -1.
 int tree_device_level(const fmm_tree* t, int level, const uint8_t** exists, const int32_t** tiles, int* ntiles);
+int tree_device_tc_tiles(const fmm_tree* t, int level, const int32_t** tiles, int* ntiles);
 
 // launchers (m2l_fp32.cu)
 int launch_build_m2l_tables(const M2LTables& t, cudaStream_t st);

@@ -187,12 +187,14 @@ __host__ __device__ inline int tc_image_block(int blk) { return (blk & 7) * 4 + 
 constexpr int kTcCtaThreads = 512;
 constexpr int kMmaWarp = 8, kStageWarp0 = 9, kStageWarps = 3, kEpiWarp0 = 12;
 constexpr int kStageBatch = 5;  // halo items in flight per staging thread (global-load path)
-// named barriers: staging warps (wait outcome; cp.async completion), epilogue warps (wait outcome; publish)
-constexpr int kStageBar = 1, kStageCopyBar = 2, kEpiBar = 3, kPubBar = 4;
+// named barriers: staging warps (wait outcome; cp.async completion), epilogue warps (wait outcome;
+// publish; the target-existence mask of an adaptive tile)
+constexpr int kStageBar = 1, kStageCopyBar = 2, kEpiBar = 3, kPubBar = 4, kMaskBar = 5;
 
 struct TcTile {
     const float4* M;
     float2* L;
+    const uint8_t* ex;  // adaptive level: box existence, NULL = every box exists
     int side, np, PX0, PY0, li;
 };
 
@@ -204,9 +206,11 @@ __device__ __forceinline__ TcTile tc_tile(const M2LLaunch& job, int tile)
     TcTile g;
     g.M = reinterpret_cast<const float4*>(lv.M);
     g.L = lv.L;
+    g.ex = lv.exists;
     g.side = 1 << lv.level;
     g.np = g.side >> 1;
-    const int t = tile - lv.tile_begin;
+    int t = tile - lv.tile_begin;
+    if (lv.tc_tiles) t = __ldg(lv.tc_tiles + t);  // adaptive level: the active tiles only
     const int tpr = (g.np + kTcTileX - 1) / kTcTileX;
     g.PX0 = (t % tpr) * kTcTileX;
     g.PY0 = (t / tpr) * kTcTileY;
@@ -309,12 +313,22 @@ __device__ __forceinline__ void tc_stage_chunk(const float4* a, const float4* b,
 // chunk in the order set by bit 2 of st, so that 8 consecutive threads read 8 different
 // 16-byte bank groups of the landing buffer and write 8 consecutive parents of a halo row.
 template <int P, int NT>
-__device__ __forceinline__ void tc_convert_landed(const unsigned char* lbuf, unsigned char* buf, int st)
+__device__ __forceinline__ void tc_convert_landed(const unsigned char* lbuf, unsigned char* buf, int st, uint32_t keep)
 {
     using C = TcCfg<P>;
     const int h = (st >> 2) & 1, c0 = st % C::KCH;
+    int j = 0;
 #pragma unroll 1
-    for (int pos = st; pos < C::NPOS; pos += NT) {
+    for (int pos = st; pos < C::NPOS; pos += NT, ++j) {
+        if (!((keep >> j) & 1)) {  // an absent source box (adaptive level): zero
+            unsigned char* dst = buf + (size_t)(2 * (pos / C::HX)) * C::ROWB + (size_t)(pos % C::HX) * 16;
+#pragma unroll
+            for (int s = 0; s < C::KCH; ++s) {
+                *reinterpret_cast<uint4*>(dst + (size_t)s * C::IPLANE) = make_uint4(0u, 0u, 0u, 0u);
+                *reinterpret_cast<uint4*>(dst + (size_t)s * C::IPLANE + C::ROWB) = make_uint4(0u, 0u, 0u, 0u);
+            }
+            continue;
+        }
         const float4* src = reinterpret_cast<const float4*>(lbuf + (size_t)pos * (C::K2 * 4));
         unsigned char* dst = buf + (size_t)(2 * (pos / C::HX)) * C::ROWB + (size_t)(pos % C::HX) * 16;
         float4 x[C::KCH], y[C::KCH];
@@ -331,6 +345,28 @@ __device__ __forceinline__ void tc_convert_landed(const unsigned char* lbuf, uns
             tc_stage_chunk(&f0, &f1, dst + (size_t)ch * C::IPLANE, C::ROWB);
         }
     }
+}
+
+// Bit j: the source box at halo position st + j NT of class `cls` exists (adaptive levels; every
+// bit set on a level where every box exists, and for positions outside the level, which the
+// tensor copy zero-fills).  Read before the copy is waited for, so the loads overlap it.
+template <int P, int NT>
+__device__ __forceinline__ uint32_t tc_halo_keep(const TcTile& tl, int cls, int st)
+{
+    using C = TcCfg<P>;
+    uint32_t keep = ~0u;
+    if (!tl.ex) return keep;
+    constexpr int NJ = (C::NPOS + NT - 1) / NT;
+    static_assert(NJ <= 32, "keep mask");
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+        const int pos = st + j * NT;
+        if (pos >= C::NPOS) break;
+        const int qx = tl.PX0 - 1 + pos % C::HX, qy = tl.PY0 - 1 + pos / C::HX;
+        if (qx < 0 || qy < 0 || qx >= tl.np || qy >= tl.np) continue;
+        if (!__ldg(tl.ex + (size_t)(2 * qy + (cls >> 1)) * tl.side + 2 * qx + (cls & 1))) keep &= ~(1u << j);
+    }
+    return keep;
 }
 
 // AND of `v` over the `n` threads of named barrier `id` (uniform control flow after a bounded wait)
@@ -376,6 +412,7 @@ __global__ void __launch_bounds__(kTcCtaThreads, 1)
     uint64_t* mdone = dfree + 2;  // the MMA thread's final commit: every issued MMA has completed
     uint64_t* lfull = mdone + 1;  // a tensor copy into the landing buffer has landed
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(lfull + 1);
+    uint8_t* s_tmask = reinterpret_cast<uint8_t*>(tmem_slot + 1);  // [4 classes][32 tile rows]: bit x, target exists
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int cta = (int)blockIdx.x, grid = (int)gridDim.x;
@@ -465,10 +502,12 @@ __global__ void __launch_bounds__(kTcCtaThreads, 1)
     if (ngrp > 0) {
         int t, cls;
         tc_group(u0, u1, 0, t, cls);
-        if (maps.use_tma[tc_tile(job, t).li]) {
+        const TcTile tl0 = tc_tile(job, t);
+        if (maps.use_tma[tl0.li]) {
+            const uint32_t keep = tc_halo_keep<P, kTcCtaThreads>(tl0, cls, tid);
             const bool landed = mbar_wait(lfull, 0, 64);
             if (__syncthreads_and(landed ? 1 : 0)) {
-                tc_convert_landed<P, kTcCtaThreads>(lbuf, hbuf, tid);
+                tc_convert_landed<P, kTcCtaThreads>(lbuf, hbuf, tid, keep);
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 first_done = true;
             }
@@ -585,6 +624,7 @@ __global__ void __launch_bounds__(kTcCtaThreads, 1)
             const TcTile tl = tc_tile(job, t);
             const int hb = k % C::NHB;
             bool w = true;
+            const uint32_t keep = pending == k ? tc_halo_keep<P, NST>(tl, cls, st) : ~0u;
             if (k >= C::NHB) w = mbar_wait(&hfree[hb], (uint32_t)(((k / C::NHB) - 1) & 1), 256);
             if (pending == k) w = mbar_wait(lfull, (uint32_t)(nlanded & 1), 128) && w;
             if (!bar_and(kStageBar, NST, w)) {
@@ -593,7 +633,7 @@ __global__ void __launch_bounds__(kTcCtaThreads, 1)
             }
             unsigned char* buf = hbuf + (size_t)hb * C::HBUF;
             if (pending == k) {
-                tc_convert_landed<P, NST>(lbuf, buf, st);
+                tc_convert_landed<P, NST>(lbuf, buf, st, keep);
                 ++nlanded;
             } else {
 #pragma unroll 1
@@ -613,6 +653,7 @@ __global__ void __launch_bounds__(kTcCtaThreads, 1)
                             continue;
                         }
                         const int ix = 2 * qx + (cls & 1), iy = 2 * qy + (cls >> 1);
+                        if (tl.ex && !__ldg(tl.ex + (size_t)iy * tl.side + ix)) continue;  // absent source
                         const float4* src = tl.M + ((size_t)iy * tl.side + ix) * (P / 2) + 2 * ch;
                         v[b][0] = __ldg(src);
                         v[b][1] = __ldg(src + 1);
@@ -660,6 +701,21 @@ __global__ void __launch_bounds__(kTcCtaThreads, 1)
             const TcTile tl = tc_tile(job, sg.t);
             const bool head = sg.sa == sg.t * kTcBlocks;
             const bool whole = head && sg.sb == (sg.t + 1) * kTcBlocks;
+            // adaptive level: which of the tile's targets exist (absent ones are left untouched)
+            const bool adapt = tl.ex != nullptr;
+            if (adapt) {
+                const int e = tid - 32 * kEpiWarp0, ce = e >> 5, py = tl.PY0 + (e & 31);
+                uint32_t m = 0;
+                if (py < tl.np)
+#pragma unroll
+                    for (int x = 0; x < kTcTileX; ++x) {
+                        const int px = tl.PX0 + x;
+                        if (px < tl.np && __ldg(tl.ex + (size_t)(2 * py + (ce >> 1)) * tl.side + 2 * px + (ce & 1)))
+                            m |= 1u << x;
+                    }
+                s_tmask[e] = (uint8_t)m;
+                asm volatile("bar.sync %0, %1;" ::"n"(kMaskBar), "n"(128) : "memory");
+            }
             if (!head) {
                 bool got = true;
                 if (lane == 0) got = wait_flag(flags + sg.t);
@@ -697,7 +753,7 @@ __global__ void __launch_bounds__(kTcCtaThreads, 1)
                         const int y = j0 / kTcTileX + yy;
                         if (y >= ylim) break;
                         float* b = base + (size_t)y * ystride;
-                        if (xlim == kTcTileX) {
+                        if (xlim == kTcTileX && !adapt) {
                             if (head) {
                                 if (job.accumulate) {
                                     float old[kTcTileX];
@@ -714,9 +770,11 @@ __global__ void __launch_bounds__(kTcCtaThreads, 1)
                                 for (int x = 0; x < kTcTileX; ++x) atomicAdd(b + x * XS, __uint_as_float(r[8 * yy + x]));
                             }
                         } else {
+                            const uint32_t tm = adapt ? s_tmask[c * 32 + y] : 0xFFu;
 #pragma unroll
                             for (int x = 0; x < kTcTileX; ++x) {
                                 if (x >= xlim) break;
+                                if (!((tm >> x) & 1u)) continue;  // absent target (adaptive level)
                                 const float o = __uint_as_float(r[8 * yy + x]);
                                 if (!head) atomicAdd(b + x * XS, o);
                                 else b[x * XS] = job.accumulate ? o + b[x * XS] : o;
@@ -814,7 +872,8 @@ static int launch_tc_p(M2LLaunch& job, const void* img, bool split, int* err, cu
     for (int i = 0; i < job.nlev; ++i) {
         job.lv[i].tile_begin = total;
         const int np = 1 << (job.lv[i].level - 1);
-        total += ((np + kTcTileX - 1) / kTcTileX) * ((np + kTcTileY - 1) / kTcTileY);
+        total += job.lv[i].tc_tiles ? job.lv[i].tc_ntiles
+                                    : ((np + kTcTileX - 1) / kTcTileX) * ((np + kTcTileY - 1) / kTcTileY);
     }
     if (total == 0) return FMM_OK;
     int sms = 0;

@@ -180,17 +180,66 @@ def test_gradient_matches_oracle_fd_gmm_workload(fmm, orc):
     assert np.linalg.norm(g - fd) <= 1e-4 * np.linalg.norm(fd), np.linalg.norm(g - fd) / np.linalg.norm(fd)
 
 
-def test_tensor_core_precisions_refuse_adaptive_levels(fmm, orc):
-    import torch
+@pytest.mark.parametrize("p", [16, 24])
+def test_tensor_core_adaptive_levels(fmm, orc, p):
+    """BF16x3 on an adaptive tree, levels 2..8 in one launch: V-list translations within the
+    tensor-core bar (1e-4) at existing boxes; absent source boxes hold garbage that must not
+    enter, absent targets keep their values; then accumulating into existing values."""
+    xy, c, tree, otree, _ = _case(orc, fmm, 30000, 40, 8, 15)
+    lev, box = orc.leaf_boxes(otree, xy)
+    levels = list(range(2, 9))
+    Ms = {l: orc.p2m_assigned(l, p, xy, c, orc.ancestor_box(lev, box, l)) for l in levels}
+    Min = {}
+    for l in levels:
+        m = orc.scale_me(Ms[l], l)
+        m[~otree.level(l)] = 1e3 + 1e3j  # absent sources: ignored on input
+        Min[l] = m
+    Md = [_dev(Min[l]) for l in levels]
+    Ld = [m.new_full(m.shape, 5.0 + 0j) for m in Md]
+    fmm.fmm_m2l_levels(tree, 2, p, Md, Ld, prec=fmm.FMM_TC_BF16X3)
+    fmm.fmm_sync_status()
+    refs = {}
+    for l, out in zip(levels, Ld):
+        ex = otree.level(l)
+        got = _host(out)
+        refs[l] = orc.scale_le(orc.m2l_adaptive(otree, l, p, Ms[l]), l)
+        if ex.any():
+            assert _rel(got[ex], refs[l][ex]) <= 1e-4, l
+        assert (got[~ex] == 5.0).all(), l  # absent boxes untouched
+    # accumulate: L0 + M2L(M) at existing boxes
+    rng = np.random.default_rng(2)
+    X = {l: rng.standard_normal((4 ** l, p)) + 1j * rng.standard_normal((4 ** l, p)) for l in levels}
+    Ld = [_dev(X[l]) for l in levels]
+    fmm.fmm_m2l_levels(tree, 2, p, Md, Ld, prec=fmm.FMM_TC_BF16X3, accumulate=True)
+    fmm.fmm_sync_status()
+    for l, out in zip(levels, Ld):
+        ex = otree.level(l)
+        got = _host(out) - X[l].astype(np.complex64).astype(np.complex128)
+        if ex.any():
+            assert _rel(got[ex], refs[l][ex]) <= 1e-4, l
 
-    xy, c = workloads.gmm_particles(20000, np.random.default_rng(3), ncomp=4)
-    tree = fmm.fmm_build_lists(xy, 7, leaf_cap=30)
+
+@pytest.mark.parametrize("conj", [False, True])
+def test_tensor_core_adaptive_adjoint(fmm, orc, conj):
+    """The adjoint on the tensor cores over an adaptive tree's V-lists, all levels in one launch."""
+    xy, c, tree, otree, _ = _case(orc, fmm, 20000, 30, 7, 17)
+    rng = np.random.default_rng(19)
+    p = 16
     levels = list(range(2, 8))
-    Md = [torch.zeros((4 ** l, 16), dtype=torch.complex64, device="cuda") for l in levels]
-    Ld = [torch.zeros_like(m) for m in Md]
-    with pytest.raises(fmm.FmmError) as e:
-        fmm.fmm_m2l_levels(tree, 2, 16, Md, Ld, prec=fmm.FMM_TC_BF16X3)
-    assert e.value.code == fmm.FMM_EUNSUPPORTED
+    W = {l: rng.standard_normal((4 ** l, p)) + 1j * rng.standard_normal((4 ** l, p)) for l in levels}
+    Wd = [_dev(W[l]) for l in levels]
+    Gd = [w.new_zeros(w.shape) for w in Wd]
+    fmm.fmm_m2l_adjoint_levels(tree, 2, p, Wd, Gd, prec=fmm.FMM_TC_BF16X3, conj=conj)
+    fmm.fmm_sync_status()
+    for l, g in zip(levels, Gd):
+        ex = otree.level(l)
+        Win = np.conj(W[l]) if conj else W[l]
+        G = orc.unscale_me(orc.m2l_adjoint_adaptive(otree, l, p, orc.scale_le(Win, l)), l)
+        if conj:
+            G = np.conj(G)
+        if ex.any() and np.linalg.norm(G[ex]) > 0:
+            assert _rel(_host(g)[ex], G[ex]) <= 1e-4, l
+        assert (_host(g)[~ex] == 0).all()
 
 
 @pytest.mark.parametrize("adaptive", [True, False])
