@@ -44,9 +44,8 @@ constexpr int kPlane = kHalo * kHalo + 1;  // float2 stride between k-planes
 
 template <int P>
 struct M2LCfg {
-    // p <= 16: packed two-lane FP32 (f32x2) multiply-adds, the half-warps split the rows;
-    // p = 24: the half-warps split the rows (registers)
-    static constexpr bool PACKED = P >= 6 && P <= 16;
+    // packed two-lane FP32 (f32x2) multiply-adds, the half-warps split the rows
+    static constexpr bool PACKED = P >= 6 && P <= 24;
     static constexpr bool SPLIT_ROWS = P > 16 || PACKED;
     static constexpr int RN = SPLIT_ROWS ? P / 2 : P;  // rows per lane
     static constexpr int NH = 2 * P - 1;           // Hankel diagonals
@@ -184,8 +183,8 @@ __device__ __forceinline__ void m2l_load_operator(unsigned char* raw, const floa
 //   kFormRows        each lane p/2 rows, all 27 entries, scalar FFMAs;
 //   kFormRowsPacked2 as kFormRowsPacked, with the sums of w m.re and of w m.im in separate
 //                    packed accumulators (no (-w.im, w.re) copy of the operator window);
-//   kFormAuto        the order's default: packed rows with separate sums at p = 12, 16 (measured
-//                    faster there, slower at p = 8), packed rows at p = 6, 8, scalar rows at p = 24.
+//   kFormAuto        the order's default: packed rows with separate sums at p = 12, 16, 24
+//                    (measured faster there, slower at p = 8), packed rows at p = 6, 8.
 enum : int { kFormAuto = -1, kFormRowsPacked = 0, kFormEntries = 1, kFormRows = 2, kFormRowsPacked2 = 3 };
 
 // Translate and reduce one tile (ADAPTIVE and g.exists set: only existing
