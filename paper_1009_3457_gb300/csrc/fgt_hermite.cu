@@ -21,9 +21,10 @@
 //     are contiguous in A and are copied to shared memory with cp.async,
 //     double-buffered, while the previous row is evaluated;
 //   - per thread R targets; per row h_b(t2) is formed once by the three-term
-//     recurrence h_{n+1} = 2t h_n - 2n h_{n-1}, per box h_a(t1), then
-//     acc += sum_a h_a(t1) sum_b A[a][b] h_b(t2) (p^2 + p FMAs, the A rows
-//     read as broadcast float4 from shared memory);
+//     recurrence h_{n+1} = 2t h_n - 2n h_{n-1}; per box
+//     acc += sum_a h_a(t1) sum_b A[a][b] h_b(t2), the outer sum by Clenshaw's
+//     backward recurrence (p^2 + 2p multiply-adds, the A rows read as broadcast
+//     float4 from shared memory);
 //   - t = u + k d with u = (y - t_C)/(sqrt2 sigma) formed once per target in
 //     FP64 and k d (k = tx - sx, d = side/(sqrt2 sigma)) from a small table,
 //     so no FP64 arithmetic runs per box;
@@ -458,21 +459,25 @@ __global__ void __launch_bounds__(H2pCfg<P>::THREADS) fgt_h2p_kernel(H2pArgs a)
 #pragma unroll
                         for (int r = 0; r < R; ++r) hermite_functions<P>(u2[r] + s_off[2 * a.ncut - dy], h2[r]);
                     }
-                    // h1 by its recurrence, one order per a1 (h_{a+1} = 2t h_a - 2a h_{a-1})
-                    float hp[R], hc[R], tt[R];
+                    // sum_a1 h_a1(t1) T[a1], T[a1] = sum_a2 A[a1][a2] h_a2(t2), by Clenshaw's backward
+                    // recurrence for h_{a+1} = 2t h_a - 2a h_{a-1}:
+                    //   c_a = T[a] + 2t c_{a+1} - 2(a+1) c_{a+2},  c_p = c_{p+1} = 0,  sum = h_0(t1) c_0,
+                    // two multiply-adds per a1 beside the p of T[a1] (the forward recurrence and the
+                    // accumulation take three)
+                    float c1[R], c2[R], tt[R], e0[R];
 #pragma unroll
                     for (int r = 0; r < R; ++r) {
                         const float t = u1[r] + s_off[2 * a.ncut - dx];
                         tt[r] = t + t;
-                        hp[r] = 0.f;
-                        hc[r] = __expf(-t * t);
+                        e0[r] = __expf(-t * t);
+                        c1[r] = c2[r] = 0.f;
                     }
                     const float4* Ab = reinterpret_cast<const float4*>(sb + e * PP);
 #pragma unroll
-                    for (int a1 = 0; a1 < P; ++a1) {
+                    for (int a1 = P - 1; a1 >= 0; --a1) {
                         float t[R];
 #pragma unroll
-                        for (int r = 0; r < R; ++r) t[r] = 0.f;
+                        for (int r = 0; r < R; ++r) t[r] = fmaf(tt[r], c1[r], -(float)(2 * (a1 + 1)) * c2[r]);
 #pragma unroll
                         for (int qd = 0; qd < P / 4; ++qd) {
                             const float4 v = Ab[a1 * (P / 4) + qd];
@@ -486,12 +491,12 @@ __global__ void __launch_bounds__(H2pCfg<P>::THREADS) fgt_h2p_kernel(H2pArgs a)
                         }
 #pragma unroll
                         for (int r = 0; r < R; ++r) {
-                            acc[r] = fmaf(hc[r], t[r], acc[r]);
-                            const float hn = fmaf(tt[r], hc[r], -(float)(2 * a1) * hp[r]);
-                            hp[r] = hc[r];
-                            hc[r] = hn;
+                            c2[r] = c1[r];
+                            c1[r] = t[r];
                         }
                     }
+#pragma unroll
+                    for (int r = 0; r < R; ++r) acc[r] = fmaf(e0[r], c1[r], acc[r]);
                 }
             }
         }
