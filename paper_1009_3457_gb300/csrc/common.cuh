@@ -88,7 +88,10 @@ int tile_counter(int** out, cudaStream_t st);
 // ints of the claim table; refilled before each evaluation, allocated on
 // first use (or by fmm_prepare).
 constexpr size_t kFgtFlagBytes = (size_t)1 << 20;
-constexpr size_t kFgtScratchBytes = kFgtFlagBytes + (((size_t)1 << 20) + 1) * sizeof(int);
+// flags [2^20 bytes], claims [2^20 + 1], then the Hermite evaluation's claim order: order [2^20],
+// row prefix [2^20], key histogram [1091], cursors [1092], keys [2^20] (ints)
+constexpr size_t kFgtScratchBytes = kFgtFlagBytes + (((size_t)1 << 20) + 1) * sizeof(int) +
+                                    (3 * ((size_t)1 << 20) + 2 * 1091 + 1) * sizeof(int);
 int fgt_flag_buffer(unsigned char** out);
 
 // ---------------------------------------------------------------------------

@@ -289,7 +289,8 @@ struct H2pArgs {
     const int* perm;
     const int* box_start;
     const unsigned char* nz;  // per source box: any non-zero coefficient
-    const int* claims;        // [nbox + 1] claim-index prefix per box (h2p_claims_kernel)
+    const int* claims;        // [nbox + 1] claim-index prefix over the boxes in `order`
+    const int* order;         // [nbox] the boxes, heaviest neighbourhood first (h2p_order_*)
     float* G;
     int accumulate;
     int* cursor;  // [0] next claim index, [1] CTAs finished
@@ -332,15 +333,173 @@ __global__ void __launch_bounds__(kScanThreads) h2p_claims_kernel(int nbox, cons
         [](int, int) {}, claims);
 }
 
-// Claim k = the next unclaimed index: run [first, end) of at most ch binned targets of one box.
-// Returns false when no claim is left.
+// ---------------------------------------------------------------------------
+// Claim order.  A claim's work is its targets times the non-empty source boxes of
+// its box's n_cut neighbourhood, and a claim is large (a few hundred microseconds
+// of one CTA), so claims handed out in box order leave SMs idle at the end of the
+// launch.  The boxes are counting-sorted by that count, heaviest first (longest
+// processing time first), and the claim table runs over that order.  Only the order
+// in which claims are taken changes: every target is still evaluated by one thread
+// with the same arithmetic.
+// ---------------------------------------------------------------------------
+constexpr int kH2pKeys = kH2pMaxBoxes + 2;  // neighbourhood counts 0..kH2pMaxBoxes, and "no targets"
+
+// rp[y][x] = nz[y][0] + ... + nz[y][x]: one warp per grid row, 32 columns per step
+__global__ void h2p_row_prefix_kernel(const unsigned char* __restrict__ nz, int g, int* __restrict__ rp)
+{
+    const int side = 1 << g, lane = threadIdx.x & 31;
+    const int y = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    if (y >= side) return;
+    int carry = 0;
+    for (int x0 = 0; x0 < side; x0 += 32) {
+        const int x = x0 + lane;
+        int v = x < side ? (int)(nz[(size_t)y * side + x] != 0) : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += t;
+        }
+        if (x < side) rp[(size_t)y * side + x] = carry + v;
+        carry += __shfl_sync(0xffffffffu, v, 31);
+    }
+}
+
+// key[b] = kH2pMaxBoxes - (non-empty source boxes within n_cut of b), or kH2pKeys - 1 for a box
+// without targets; hist[key] counts the boxes of each key
+__global__ void h2p_order_keys_kernel(const int* __restrict__ rp, const int* __restrict__ box_start, int g, int ncut,
+                                      int* __restrict__ key, int* __restrict__ hist)
+{
+    const int side = 1 << g, nbox = side * side;
+    const int b = (int)(blockIdx.x * (size_t)blockDim.x + threadIdx.x);
+    if (b >= nbox) return;
+    int k = kH2pKeys - 1;
+    if (box_start[b + 1] > box_start[b]) {
+        const int tx = b & (side - 1), ty = b >> g;
+        const int x0 = max(tx - ncut, 0), x1 = min(tx + ncut, side - 1);
+        const int y0 = max(ty - ncut, 0), y1 = min(ty + ncut, side - 1);
+        int w = 0;
+        for (int yy = y0; yy <= y1; ++yy) {
+            const int* r = rp + (size_t)yy * side;
+            w += r[x1] - (x0 > 0 ? r[x0 - 1] : 0);
+        }
+        k = kH2pMaxBoxes - w;
+    }
+    key[b] = k;
+    atomicAdd(hist + k, 1);
+}
+
+// the boxes in key order (within a key in no particular order): a counting sort's scatter
+__global__ void h2p_order_scatter_kernel(const int* __restrict__ key, int nbox, int* __restrict__ cursor,
+                                         int* __restrict__ order)
+{
+    const int b = (int)(blockIdx.x * (size_t)blockDim.x + threadIdx.x);
+    if (b >= nbox) return;
+    order[atomicAdd(cursor + key[b], 1)] = b;
+}
+
+// cursor[0..kH2pKeys]: exclusive scan of the key histogram, the scatter cursors (one CTA)
+__global__ void __launch_bounds__(kScanThreads) h2p_order_scan_kernel(const int* __restrict__ hist,
+                                                                      int* __restrict__ cursor)
+{
+    block_exclusive_scan(
+        kH2pKeys, [&](int i) { return hist[i]; }, [](int, int) {}, cursor);
+}
+
+// claims[0..nbox]: exclusive scan over the boxes in `order` of ceil(targets / ch)
+__global__ void __launch_bounds__(kScanThreads) h2p_claims_ordered_kernel(int nbox, const int* __restrict__ box_start,
+                                                                          const int* __restrict__ order, int ch,
+                                                                          int* __restrict__ claims, int* err)
+{
+    block_exclusive_scan(
+        nbox,
+        [&](int i) {
+            const int b = order[i];
+            const int m = box_start[b + 1] - box_start[b];
+            if (m < 0) atomicOr(err, DEV_ERR_CHECK);
+            return m > 0 ? (m + ch - 1) / ch : 0;
+        },
+        [](int, int) {}, claims);
+}
+
+// The same for grids of up to kH2pOrderSmall boxes in one CTA (one launch instead of five):
+// row prefix and key histogram in shared memory, then order and claims.
+constexpr int kH2pOrderSmall = 4096;
+constexpr int kH2pOrderPer = kH2pOrderSmall / kScanThreads;  // boxes per thread
+__global__ void __launch_bounds__(kScanThreads) h2p_order_small_kernel(const unsigned char* __restrict__ nz,
+                                                                       const int* __restrict__ box_start, int g,
+                                                                       int ncut, int ch, int* __restrict__ order,
+                                                                       int* __restrict__ claims, int* err)
+{
+    __shared__ int s_rp[kH2pOrderSmall];
+    __shared__ int s_hist[kH2pKeys];
+    __shared__ int s_cur[kH2pKeys + 1];
+    const int tid = threadIdx.x, side = 1 << g, nbox = side * side;
+    for (int b = tid; b < nbox; b += kScanThreads) s_rp[b] = nz[b] != 0;
+    for (int k = tid; k < kH2pKeys; k += kScanThreads) s_hist[k] = 0;
+    __syncthreads();
+    if (tid < side) {
+        int c = 0;
+        for (int x = 0; x < side; ++x) s_rp[tid * side + x] = (c += s_rp[tid * side + x]);
+    }
+    __syncthreads();
+    int key[kH2pOrderPer];
+#pragma unroll
+    for (int j = 0; j < kH2pOrderPer; ++j) {
+        const int b = tid + j * kScanThreads;
+        key[j] = -1;
+        if (b >= nbox) continue;
+        int k = kH2pKeys - 1;
+        if (box_start[b + 1] > box_start[b]) {
+            const int tx = b & (side - 1), ty = b >> g;
+            const int x0 = max(tx - ncut, 0), x1 = min(tx + ncut, side - 1);
+            const int y0 = max(ty - ncut, 0), y1 = min(ty + ncut, side - 1);
+            int w = 0;
+            for (int yy = y0; yy <= y1; ++yy) w += s_rp[yy * side + x1] - (x0 > 0 ? s_rp[yy * side + x0 - 1] : 0);
+            k = kH2pMaxBoxes - w;
+        }
+        key[j] = k;
+        atomicAdd(s_hist + k, 1);
+    }
+    __syncthreads();
+    block_exclusive_scan(
+        kH2pKeys, [&](int i) { return s_hist[i]; }, [](int, int) {}, s_cur);
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kH2pOrderPer; ++j)
+        if (key[j] >= 0) order[atomicAdd(s_cur + key[j], 1)] = tid + j * kScanThreads;
+    __syncthreads();  // the order, written by this block, is visible to it
+    block_exclusive_scan(
+        nbox,
+        [&](int i) {
+            const int b = order[i];
+            const int m = box_start[b + 1] - box_start[b];
+            if (m < 0) atomicOr(err, DEV_ERR_CHECK);
+            return m > 0 ? (m + ch - 1) / ch : 0;
+        },
+        [](int, int) {}, claims);
+}
+
+// Claim k = the next unclaimed index: run [first, end) of at most ch binned targets of one box
+// (the claim table runs over the boxes in a.order).  Returns false when no claim is left.
 __device__ bool h2p_claim(const H2pArgs& a, int nbox, int ch, int* first, int* end, int* box)
 {
     const int total = __ldg(a.claims + nbox);
     const int k = atomicAdd(a.cursor, 1);
     if (k >= total) return false;
-    h2p_claim_range(a.claims, a.box_start, nbox, a.n, ch, k, first, end, box);
-    if (*first >= *end) atomicOr(a.err, DEV_ERR_CHECK);  // box_start does not bin [0, n)
+    int lo = 0, hi = nbox;  // largest position i with claims[i] <= k
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(a.claims + mid) <= k) lo = mid;
+        else hi = mid;
+    }
+    const int b = __ldg(a.order + lo);
+    const int f = __ldg(a.box_start + b) + (k - __ldg(a.claims + lo)) * ch;
+    const int e = min(min(f + ch, __ldg(a.box_start + b + 1)), a.n);
+    const bool ok = 0 <= f && f < e && (unsigned)b < (unsigned)nbox;
+    *first = ok ? f : 0;
+    *end = ok ? e : 0;
+    *box = ok ? b : 0;
+    if (!ok) atomicOr(a.err, DEV_ERR_CHECK);  // box_start does not bin [0, n)
     return true;
 }
 
@@ -523,6 +682,38 @@ int launch_h2p_claims(int nbox, const int* box_start, int ch, int* claims, int* 
     return FMM_OK;
 }
 
+// The claim order and the claim table over it (flags in args.nz already set): one CTA for
+// grids of up to kH2pOrderSmall boxes, else row prefix, keys, histogram scan, scatter and
+// claims as five launches.
+static int h2p_order_claims(const H2pArgs& args, int ch, cudaStream_t st)
+{
+    const int nbox = 1 << (2 * args.g), side = 1 << args.g;
+    int* order = const_cast<int*>(args.order);
+    int* claims = const_cast<int*>(args.claims);
+    if (nbox <= kH2pOrderSmall) {
+        h2p_order_small_kernel<<<1, kScanThreads, 0, st>>>(args.nz, args.box_start, args.g, args.ncut, ch, order, claims,
+                                                           args.err);
+        FMM_CUDA_TRY(cudaGetLastError());
+        return FMM_OK;
+    }
+    int* rp = order + nbox;               // [nbox] row prefix of the flags
+    int* hist = rp + nbox;                // [kH2pKeys] key histogram
+    int* cursor = hist + kH2pKeys;        // [kH2pKeys + 1] scatter cursors (their scan, total last)
+    int* key = cursor + kH2pKeys + 1;     // [nbox]
+    FMM_CUDA_TRY(cudaMemsetAsync(hist, 0, sizeof(int) * kH2pKeys, st));
+    h2p_row_prefix_kernel<<<(side * 32 + 255) / 256, 256, 0, st>>>(args.nz, args.g, rp);
+    FMM_CUDA_TRY(cudaGetLastError());
+    h2p_order_keys_kernel<<<(nbox + 255) / 256, 256, 0, st>>>(rp, args.box_start, args.g, args.ncut, key, hist);
+    FMM_CUDA_TRY(cudaGetLastError());
+    h2p_order_scan_kernel<<<1, kScanThreads, 0, st>>>(hist, cursor);
+    FMM_CUDA_TRY(cudaGetLastError());
+    h2p_order_scatter_kernel<<<(nbox + 255) / 256, 256, 0, st>>>(key, nbox, cursor, order);
+    FMM_CUDA_TRY(cudaGetLastError());
+    h2p_claims_ordered_kernel<<<1, kScanThreads, 0, st>>>(nbox, args.box_start, order, ch, claims, args.err);
+    FMM_CUDA_TRY(cudaGetLastError());
+    return FMM_OK;
+}
+
 template <int P>
 static int h2p_launch(const H2pArgs& args, cudaStream_t st)
 {
@@ -543,7 +734,8 @@ static int h2p_launch(const H2pArgs& args, cudaStream_t st)
     const int nbox = 1 << (2 * args.g);
     fgt_box_flags_kernel<<<(nbox + 7) / 8, 256, 0, st>>>(args.A, nbox, C::PP, const_cast<unsigned char*>(args.nz));
     FMM_CUDA_TRY(cudaGetLastError());
-    if (int rc = launch_h2p_claims(nbox, args.box_start, C::CH, const_cast<int*>(args.claims), args.err, st)) return rc;
+    // the claim order (heaviest neighbourhood first), then the claim table over it
+    if (int rc = h2p_order_claims(args, C::CH, st)) return rc;
     const int64_t most = (int64_t)args.n / C::CH + nbox;  // claims can be no more
     const int grid = (int)std::min<int64_t>((int64_t)occ * sms, most > 0 ? most : 1);
     fgt_h2p_kernel<P><<<grid, C::THREADS, C::smem, st>>>(args);
@@ -681,6 +873,7 @@ extern "C" int fgt_h2p(int32_t grid_log2, int32_t n_cut, int32_t p, int32_t prec
     if (int rc = fgt_flag_buffer(&nzbuf)) return rc;
     args.nz = nzbuf;
     args.claims = reinterpret_cast<const int*>(nzbuf + kFgtFlagBytes);
+    args.order = args.claims + ((size_t)1 << 20) + 1;
     if (prec != FMM_FP32) {
         const int nbox = 1 << (2 * grid_log2);
         if (int rc = launch_h2p_claims(nbox, box_start, 128, const_cast<int*>(args.claims), args.err, st)) return rc;

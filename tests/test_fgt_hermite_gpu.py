@@ -186,6 +186,38 @@ def test_h2p_accumulate_and_ragged_counts(fmm, orc, gmm_sources):
         _check(_h2p(fmm, g, ncut, p, sigma, A32, y, G=G, accumulate=True), ref + 0.25)
 
 
+@pytest.mark.parametrize("g", [6, 7])
+def test_h2p_claim_order_on_large_grids(fmm, orc, g):
+    """Claims are handed out heaviest neighbourhood first: one CTA builds that order for grids
+    of up to 64 x 64 boxes, five launches (row prefix, keys, scan, scatter, claims) above.
+    A 64 x 64 and a 128 x 128 grid, a third of the source boxes empty, clustered targets (per
+    box counts from 0 to hundreds, most boxes without targets), G pre-filled with NaN: every
+    target is evaluated once, against the oracle."""
+    import math
+    import torch
+
+    rng = np.random.default_rng(300 + g)
+    p, ncut = 8, 3
+    n = 1 << g
+    sigma = 2.0 ** -g / (math.sqrt(2.0) * 0.442)
+    fact = np.array([math.factorial(a) for a in range(p)], float)
+    A = rng.standard_normal((n * n, p, p)) * (0.3 ** (np.arange(p)[:, None] + np.arange(p)[None, :])) / np.outer(fact, fact)
+    A[rng.random(n * n) < 0.33] = 0.0
+    A32 = A.astype(np.float32)
+    c = rng.random((6, 2))
+    y = np.concatenate([np.clip(c[i] + 0.03 * rng.standard_normal((3000, 2)), 0.0, 0.999999) for i in range(6)]
+                       + [rng.random((2000, 2))])
+    yd = torch.from_numpy(np.ascontiguousarray(y)).cuda()
+    perm, start = _bin(fmm, g, yd)
+    G = torch.full((len(y),), float("nan"), dtype=torch.float32, device="cuda")
+    fmm.fgt_h2p(g, ncut, p, sigma, torch.from_numpy(A32).cuda(), yd, perm, start, G)
+    fmm.fmm_sync_status()
+    got = G.cpu().numpy().astype(np.float64)
+    assert np.isfinite(got).all()
+    ref = orc.fgt_hermite_eval_grid(g, ncut, p, sigma, A32.astype(np.float64), y)
+    _check(got, ref)
+
+
 def test_h2p_bad_permutation_sets_error_word(fmm):
     """A perm entry outside [0, n) is caught by the kernel's own bounds check: the
     target is skipped and fmm_sync_status reports FMM_EDEVICE; the context stays usable."""
