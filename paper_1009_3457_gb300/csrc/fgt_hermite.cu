@@ -486,20 +486,8 @@ __device__ bool h2p_claim(const H2pArgs& a, int nbox, int ch, int* first, int* e
     const int total = __ldg(a.claims + nbox);
     const int k = atomicAdd(a.cursor, 1);
     if (k >= total) return false;
-    int lo = 0, hi = nbox;  // largest position i with claims[i] <= k
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (__ldg(a.claims + mid) <= k) lo = mid;
-        else hi = mid;
-    }
-    const int b = __ldg(a.order + lo);
-    const int f = __ldg(a.box_start + b) + (k - __ldg(a.claims + lo)) * ch;
-    const int e = min(min(f + ch, __ldg(a.box_start + b + 1)), a.n);
-    const bool ok = 0 <= f && f < e && (unsigned)b < (unsigned)nbox;
-    *first = ok ? f : 0;
-    *end = ok ? e : 0;
-    *box = ok ? b : 0;
-    if (!ok) atomicOr(a.err, DEV_ERR_CHECK);  // box_start does not bin [0, n)
+    h2p_claim_range_ordered(a.claims, a.order, a.box_start, nbox, a.n, ch, k, first, end, box);
+    if (*first >= *end) atomicOr(a.err, DEV_ERR_CHECK);  // box_start does not bin [0, n)
     return true;
 }
 
@@ -682,17 +670,16 @@ int launch_h2p_claims(int nbox, const int* box_start, int ch, int* claims, int* 
     return FMM_OK;
 }
 
-// The claim order and the claim table over it (flags in args.nz already set): one CTA for
-// grids of up to kH2pOrderSmall boxes, else row prefix, keys, histogram scan, scatter and
-// claims as five launches.
-static int h2p_order_claims(const H2pArgs& args, int ch, cudaStream_t st)
+// The claim order and the claim table over it, runs of ch targets: one CTA for grids of up to
+// kH2pOrderSmall boxes, else row prefix, keys, histogram scan, scatter and claims as five
+// launches.  nz: the source boxes' non-empty flags (already set); order points at the scratch
+// words after the claims array.
+static int h2p_order_claims(const unsigned char* nz, const int* box_start, int g, int ncut, int ch, int* order, int* claims,
+                     int* err, cudaStream_t st)
 {
-    const int nbox = 1 << (2 * args.g), side = 1 << args.g;
-    int* order = const_cast<int*>(args.order);
-    int* claims = const_cast<int*>(args.claims);
+    const int nbox = 1 << (2 * g), side = 1 << g;
     if (nbox <= kH2pOrderSmall) {
-        h2p_order_small_kernel<<<1, kScanThreads, 0, st>>>(args.nz, args.box_start, args.g, args.ncut, ch, order, claims,
-                                                           args.err);
+        h2p_order_small_kernel<<<1, kScanThreads, 0, st>>>(nz, box_start, g, ncut, ch, order, claims, err);
         FMM_CUDA_TRY(cudaGetLastError());
         return FMM_OK;
     }
@@ -701,15 +688,15 @@ static int h2p_order_claims(const H2pArgs& args, int ch, cudaStream_t st)
     int* cursor = hist + kH2pKeys;        // [kH2pKeys + 1] scatter cursors (their scan, total last)
     int* key = cursor + kH2pKeys + 1;     // [nbox]
     FMM_CUDA_TRY(cudaMemsetAsync(hist, 0, sizeof(int) * kH2pKeys, st));
-    h2p_row_prefix_kernel<<<(side * 32 + 255) / 256, 256, 0, st>>>(args.nz, args.g, rp);
+    h2p_row_prefix_kernel<<<(side * 32 + 255) / 256, 256, 0, st>>>(nz, g, rp);
     FMM_CUDA_TRY(cudaGetLastError());
-    h2p_order_keys_kernel<<<(nbox + 255) / 256, 256, 0, st>>>(rp, args.box_start, args.g, args.ncut, key, hist);
+    h2p_order_keys_kernel<<<(nbox + 255) / 256, 256, 0, st>>>(rp, box_start, g, ncut, key, hist);
     FMM_CUDA_TRY(cudaGetLastError());
     h2p_order_scan_kernel<<<1, kScanThreads, 0, st>>>(hist, cursor);
     FMM_CUDA_TRY(cudaGetLastError());
     h2p_order_scatter_kernel<<<(nbox + 255) / 256, 256, 0, st>>>(key, nbox, cursor, order);
     FMM_CUDA_TRY(cudaGetLastError());
-    h2p_claims_ordered_kernel<<<1, kScanThreads, 0, st>>>(nbox, args.box_start, order, ch, claims, args.err);
+    h2p_claims_ordered_kernel<<<1, kScanThreads, 0, st>>>(nbox, box_start, order, ch, claims, err);
     FMM_CUDA_TRY(cudaGetLastError());
     return FMM_OK;
 }
@@ -735,7 +722,9 @@ static int h2p_launch(const H2pArgs& args, cudaStream_t st)
     fgt_box_flags_kernel<<<(nbox + 7) / 8, 256, 0, st>>>(args.A, nbox, C::PP, const_cast<unsigned char*>(args.nz));
     FMM_CUDA_TRY(cudaGetLastError());
     // the claim order (heaviest neighbourhood first), then the claim table over it
-    if (int rc = h2p_order_claims(args, C::CH, st)) return rc;
+    if (int rc = h2p_order_claims(args.nz, args.box_start, args.g, args.ncut, C::CH, const_cast<int*>(args.order),
+                                  const_cast<int*>(args.claims), args.err, st))
+        return rc;
     const int64_t most = (int64_t)args.n / C::CH + nbox;  // claims can be no more
     const int grid = (int)std::min<int64_t>((int64_t)occ * sms, most > 0 ? most : 1);
     fgt_h2p_kernel<P><<<grid, C::THREADS, C::smem, st>>>(args);

@@ -40,6 +40,27 @@ __device__ __forceinline__ void h2p_claim_range(const int* __restrict__ claims, 
     *box = lo;
 }
 
+// The same with the claim table over the boxes in `order` (position i holds box order[i]).
+__device__ __forceinline__ void h2p_claim_range_ordered(const int* __restrict__ claims, const int* __restrict__ order,
+                                                        const int* __restrict__ box_start, int nbox, int n, int ch,
+                                                        int k, int* first, int* end, int* box)
+{
+    int lo = 0, hi = nbox;  // largest position i with claims[i] <= k
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(claims + mid) <= k) lo = mid;
+        else hi = mid;
+    }
+    const int b = __ldg(order + lo);
+    const bool inb = (unsigned)b < (unsigned)nbox;
+    const int f = inb ? __ldg(box_start + b) + (k - __ldg(claims + lo)) * ch : 0;
+    const int e = inb ? min(min(f + ch, __ldg(box_start + b + 1)), n) : 0;
+    const bool ok = inb && 0 <= f && f < e;
+    *first = ok ? f : 0;
+    *end = ok ? e : 0;
+    *box = ok ? b : 0;
+}
+
 // Host: claims[0..nbox] for runs of ch targets (one CTA, on `st`).
 int launch_h2p_claims(int nbox, const int* box_start, int ch, int* claims, int* err, cudaStream_t st);
 
