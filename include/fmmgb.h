@@ -501,11 +501,14 @@ int fgt_t2p_binned(int32_t grid_log2, int32_t p, double sigma, const float* C, c
  *   y, n, ...) of these targets; G: device float32 [n], indexed like y.
  *   n_cut 0..16, p 4, 8, 12 or 16, flags FMM_ACCUMULATE or 0.
  *   prec FMM_FP32: CUDA cores.  Source boxes whose coefficients are all zero
- *   are skipped: a first
- *   kernel writes one flag per box into a 1 MiB per-device array that the
- *   library allocates on the first call (or in fmm_prepare; make one of them
- *   before any stream capture); calls that overlap on the GPU (different
- *   streams) share that array and must be serialised by the caller.  A perm
+ *   are skipped: a first kernel writes one flag per box.  The targets are
+ *   taken in runs of up to 256 of one box, the boxes with the most non-empty
+ *   source boxes within n_cut first (an order built on the device in every
+ *   call; G does not depend on it).  Flags, claim order and claim table live
+ *   in a ~17 MiB per-device scratch that the library allocates on the first
+ *   call (or in fmm_prepare; make one of them before any stream capture);
+ *   calls that overlap on the GPU (different streams) share it and must be
+ *   serialised by the caller.  A perm
  *   entry outside [0, n) or a box_start that does not bin [0, n) sets the
  *   device error word's check bit (fmm_sync_status returns FMM_EDEVICE); the
  *   affected targets are skipped.
