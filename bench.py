@@ -73,6 +73,7 @@ def _measured_bf16_tflops() -> float:
 
 
 BF16_PEAK_TFLOPS = _measured_bf16_tflops()
+TF32_PER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor rate (per GPU)
 
 
 def device_peaks(torch, dev):
@@ -256,33 +257,40 @@ def cpu_baseline_all_cores(levels=None, steps=3, warmup=1):
 
 
 def tc_accuracy_vs_oracle(torch, fmmgb, dev):
-    """Coefficient error of the FP32 and the BF16x3 tensor-core M2L at p = 24 against the FP64
-    oracle on the precision workload's tree (4096 points, uniform to level 4): relative L2 of the
-    radius-scaled LEs, max over levels 2-4.  Part of the CPU-baseline leg (the one leg of this
-    benchmark that runs the oracle)."""
+    """Coefficient error of the FP32 and the tensor-core M2L against the FP64 oracle on the
+    precision workload's tree (4096 points, uniform to level 4): relative L2 of the radius-scaled
+    LEs, max over levels 2-4; at p = 24 FP32 and BF16x3, at p = 16 FP32, BF16x3 and TF32x3.  Part
+    of the CPU-baseline leg (the one leg of this benchmark that runs the oracle)."""
     import oracle
 
     cfg = workloads.CONFIGS["m2l_tc"]
-    p, L = cfg["p"], cfg["max_level"]
+    L = cfg["max_level"]
     xy, c = workloads.uniform_particles(cfg["n"], workloads.rng_for("m2l_small"))  # the m2l_small points
-    Ms = oracle.upward_uniform(L, p, xy, c)
     tree = fmmgb.fmm_build_lists(None, L)
-    err = {}
-    for name, prec in (("fp32", fmmgb.FMM_FP32), ("bf16x3", fmmgb.FMM_TC_BF16X3)):
-        worst = 0.0
+
+    def worst(p, Ms, prec):
+        w = 0.0
         for level in workloads.m2l_levels(L):
             ref = oracle.scale_le(oracle.m2l_uniform(level, p, Ms[level]), level)
             Md = torch.from_numpy(oracle.scale_me(Ms[level], level).astype(np.complex64)).to(dev)
             Ld = torch.empty_like(Md)
             fmmgb.fmm_m2l(tree, level, p, Md, Ld, prec=prec)
             got = Ld.cpu().numpy().astype(np.complex128)
-            worst = max(worst, float(np.linalg.norm(got - ref) / np.linalg.norm(ref)))
-        err[name] = worst
+            w = max(w, float(np.linalg.norm(got - ref) / np.linalg.norm(ref)))
+        return w
+
+    p = cfg["p"]
+    Ms = oracle.upward_uniform(L, p, xy, c)
+    out = {"tree": f"{cfg['n']} points U[0,1)^2, uniform to level {L}, p = {p}, levels 2-{L}",
+           "fp32_rel_l2": worst(p, Ms, fmmgb.FMM_FP32), "bf16x3_rel_l2": worst(p, Ms, fmmgb.FMM_TC_BF16X3)}
+    Ms16 = oracle.upward_uniform(L, 16, xy, c)
+    out["p16"] = {"fp32_rel_l2": worst(16, Ms16, fmmgb.FMM_FP32),
+                  "bf16x3_rel_l2": worst(16, Ms16, fmmgb.FMM_TC_BF16X3),
+                  "tf32x3_rel_l2": worst(16, Ms16, fmmgb.FMM_TC_TF32X3)}
     fmmgb.fmm_sync_status()
-    return {"tree": f"{cfg['n']} points U[0,1)^2, uniform to level {L}, p = {p}, levels 2-{L}",
-            "fp32_rel_l2": err["fp32"], "bf16x3_rel_l2": err["bf16x3"], "bar_fp32": 1e-5,
-            "bar_tc": "oracle truncation + 1e-4", "metric": "relative L2 of radius-scaled LEs vs FP64 oracle, "
-                                                           "max over levels"}
+    out.update({"bar_fp32": 1e-5, "bar_tc": "oracle truncation + 1e-4 (TF32x3 is tested at the FP32 bar)",
+                "metric": "relative L2 of radius-scaled LEs vs FP64 oracle, max over levels"})
+    return out
 
 
 def run_reference(args):
@@ -407,7 +415,8 @@ def _fgt_hermite_rows(torch, fmmgb, dev, fxd, fqd, args, stream, flush):
     return rows
 
 
-SUMMARY_ROWS = ("m2l_adjoint_fp32_levels_2_8", "m2l_tc_bf16x3_levels_2_8", "m2l_fp32_p24_levels_2_8",
+SUMMARY_ROWS = ("m2l_adjoint_fp32_levels_2_8", "m2l_tc_bf16x3_levels_2_8", "m2l_tc_tf32x3_levels_2_8",
+                "m2l_fp32_p24_levels_2_8",
                 "m2l_tc_bf16x3_p24_levels_2_8", "m2l_adaptive_gmm_levels_2_9", "m2l_tc_bf16x3_adaptive_gmm_levels_2_9",
                 "m2l_batched_256_problems",
                 "m2l_paper_design_levels_2_8", "fgt_h2t_sigma0.05_p16", "fgt_h2t_tc_bf16x3_sigma0.05_p16",
@@ -609,7 +618,8 @@ def run_ours(args):
         return 0
     if args.mode == "kernels":
         # profiling case: the step's launch only (no e2e copies, no CPU baseline, no other rows)
-        prec = {"fp32": fmmgb.FMM_FP32, "tc3": fmmgb.FMM_TC_BF16X3, "tc1": fmmgb.FMM_TC_BF16}[args.prec]
+        prec = {"fp32": fmmgb.FMM_FP32, "tc3": fmmgb.FMM_TC_BF16X3, "tc1": fmmgb.FMM_TC_BF16,
+                "tf3": fmmgb.FMM_TC_TF32X3}[args.prec]
         for _ in range(args.steps):
             fmmgb.fmm_m2l_levels(tree, LEVELS[0], P, Ms, Ls, prec=prec, stream=stream)
         torch.cuda.synchronize()
@@ -688,23 +698,31 @@ def run_ours(args):
         def tc_adjoint():
             fmmgb.fmm_m2l_adjoint_levels(tree, LEVELS[0], P, Ls, Gs, prec=fmmgb.FMM_TC_BF16X3, conj=True)
 
+        def tc_tf32():
+            fmmgb.fmm_m2l_levels(tree, LEVELS[0], P, Ms, Ls, prec=fmmgb.FMM_TC_TF32X3)
+
         # every row below times a CUDA-graph replay of its library calls (as the headline step does)
         for name, fn, launches in (("m2l_fp32_one_launch_per_level", per_level, len(LEVELS)),
                                    ("m2l_adjoint_fp32_levels_2_8", adjoint, 1),
                                    ("m2l_tc_bf16x3_levels_2_8", tc_x3, 1),
                                    ("m2l_tc_bf16_levels_2_8", tc_x1, 1),
-                                   ("m2l_tc_bf16x3_adjoint_levels_2_8", tc_adjoint, 1)):
+                                   ("m2l_tc_bf16x3_adjoint_levels_2_8", tc_adjoint, 1),
+                                   ("m2l_tc_tf32x3_levels_2_8", tc_tf32, 1)):
             ms = statistics.median(_timed(torch, _graph(torch, fn), args.steps, stream, flush))
             gf = NTR * metrics.m2l_flops_per_translation(P) / (ms * 1e-3) / 1e9
             rows[name] = {"translations_per_s": NTR / (ms * 1e-3), "ms": ms, "launches": launches, "gflops": gf}
             if "fp32" in name:
                 rows[name]["alu_frac"] = gf / 1e3 / alu_peak_tflops()
-            else:  # tensor cores: issued MMA work against the measured BF16 peak, and the useful part
+            else:  # tensor cores: issued MMA work against the measured peak of the operand type
+                # (TF32: the measured BF16 peak x the nominal dense ratio 1.1 / 2.25), and the useful part
                 prods = 1 if name == "m2l_tc_bf16_levels_2_8" else 3
+                peak = BF16_PEAK_TFLOPS * (TF32_PER_BF16 if "tf32" in name else 1.0)
                 tt = metrics.m2l_tc_mma_flops(LEVELS, P, prods) / (ms * 1e-3) / 1e12
-                rows[name].update({"tensor_tflops": tt, "tensor_frac": tt / BF16_PEAK_TFLOPS,
+                rows[name].update({"tensor_tflops": tt, "tensor_frac": tt / peak,
                                    "useful_tflops": gf / 1e3 * prods,
-                                   "useful_frac": gf / 1e3 * prods / BF16_PEAK_TFLOPS})
+                                   "useful_frac": gf / 1e3 * prods / peak})
+                if "tf32" in name:
+                    rows[name]["peak_note"] = "TF32 peak = measured BF16 peak x 1.1 / 2.25 (nominal dense ratio)"
         # precision study at p = 24 on the same tree: FP32 kernel vs tensor cores (BF16x3)
         p24 = workloads.CONFIGS["m2l_tc"]["p"]
         xyd = torch.from_numpy(xy).to(dev)
@@ -736,6 +754,9 @@ def run_ours(args):
                                           "note": "both meet the tensor-core bar (truncation + 1e-4); "
                                                   "measured coefficient errors in tests/test_m2l_tc_gpu.py"}
         rows["tc_vs_fp32_speedup_p16"] = {"speedup": statistics.median(step_ms) / rows["m2l_tc_bf16x3_levels_2_8"]["ms"]}
+        rows["tc_tf32x3_vs_fp32_speedup_p16"] = {
+            "speedup": statistics.median(step_ms) / rows["m2l_tc_tf32x3_levels_2_8"]["ms"],
+            "note": "TF32x3 is held to the FP32 bar (1e-5) in tests/test_m2l_tc_tf32_gpu.py"}
         del M24, L24, M24s, L24s
         # the paper's two-kernel data flow (per-translation LEs written to HBM, then a separate
         # reduction) on the headline workload, against the fused stencil
@@ -990,7 +1011,9 @@ def run_ours(args):
                                    "speedup": rows["tc_vs_fp32_speedup_p24"]["speedup"]},
                 "p16_levels_2_8": {"fp32_ms": statistics.median(step_ms),
                                    "bf16x3_ms": rows["m2l_tc_bf16x3_levels_2_8"]["ms"],
-                                   "speedup": rows["tc_vs_fp32_speedup_p16"]["speedup"]},
+                                   "speedup": rows["tc_vs_fp32_speedup_p16"]["speedup"],
+                                   "tf32x3_ms": rows["m2l_tc_tf32x3_levels_2_8"]["ms"],
+                                   "tf32x3_speedup": rows["tc_tf32x3_vs_fp32_speedup_p16"]["speedup"]},
                 "workload": "2^22 points, uniform to level 8, levels 2-8 (2,316,900 translations)"}
         if not args.no_cpu_baseline and ws == 1:
             if rows:
@@ -1020,7 +1043,8 @@ def main():
     ap.add_argument("--mode", default="full", choices=["full", "kernels"],
                     help="kernels: only the timed step's launches (for ncu captures)")
     ap.add_argument("--tc", action="store_true", help="with --prec h2p: the tensor-core (BF16x3) form")
-    ap.add_argument("--prec", default="fp32", choices=["fp32", "tc3", "tc1", "batched", "fgt", "fgt_tc", "h2p", "p2p"],
+    ap.add_argument("--prec", default="fp32",
+                    choices=["fp32", "tc3", "tc1", "tf3", "batched", "fgt", "fgt_tc", "h2p", "p2p"],
                     help="launches of --mode kernels: the step at this precision, or the 256-problem batch, "
                          "or the FGT H2T at sigma 0.05, p 16")
     ap.add_argument("--sigma", type=float, default=0.05, help="--mode kernels --prec fgt: the FGT bandwidth")

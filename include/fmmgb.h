@@ -60,7 +60,8 @@ typedef enum {
 typedef enum {
     FMM_FP32 = 0,           /* FP32 FFMA path (Hankel-structured stencil kernel) */
     FMM_TC_BF16X3 = 1,      /* tcgen05 tensor cores, BF16 hi/lo split, 3 products, FP32 accumulate */
-    FMM_TC_BF16 = 2         /* tcgen05 tensor cores, plain BF16 inputs, FP32 accumulate */
+    FMM_TC_BF16 = 2,        /* tcgen05 tensor cores, plain BF16 inputs, FP32 accumulate */
+    FMM_TC_TF32X3 = 3       /* tcgen05 tensor cores, TF32 hi/lo split, 3 products, FP32 accumulate (M2L, p = 16) */
 } fmm_prec;
 
 /* flags for fmm_m2l / fmm_m2l_adjoint / fgt_h2t */
@@ -138,8 +139,8 @@ int64_t fmm_tree_translations(const fmm_tree* tree, int32_t level);
 void fmm_tree_destroy(fmm_tree* tree);
 
 /* Build the operator tables for order p on the current device (FP64 GPU
- * kernel, then FP32/BF16 copies).  Optional: fmm_m2l does it on first use.
- * Synchronous. */
+ * kernel, then FP32 copies, and the BF16 or TF32 tensor-core image for a
+ * tensor-core prec).  Optional: fmm_m2l does it on first use.  Synchronous. */
 int fmm_prepare(int32_t p, int32_t prec);
 
 /* ---------------------------------------------------------------------------
@@ -153,10 +154,13 @@ int fmm_prepare(int32_t p, int32_t prec);
  *   level  0 .. max_level; levels 0 and 1 have empty lists (the output is
  *          zeroed, or left unchanged with FMM_ACCUMULATE).
  *   p      number of terms: 6, 8, 12, 16 or 24.
- *   prec   FMM_FP32, FMM_TC_BF16X3 or FMM_TC_BF16 (tensor-core forms: p = 16
- *          or 24, FMM_EUNSUPPORTED otherwise; on an adaptive level they run the
- *          8 x 32-parent tiles that hold an existing box, with absent sources
- *          read as zero and absent targets left untouched).
+ *   prec   FMM_FP32, FMM_TC_BF16X3, FMM_TC_BF16 or FMM_TC_TF32X3 (tensor-core
+ *          forms: p = 16 or 24, FMM_TC_TF32X3 p = 16 only, FMM_EUNSUPPORTED
+ *          otherwise; on an adaptive level they run the 8 x 32-parent tiles that
+ *          hold an existing box, with absent sources read as zero and absent
+ *          targets left untouched).  FMM_TC_TF32X3 splits operator and MEs into
+ *          TF32 hi + lo (~21 significant bits each) and issues three products:
+ *          close to FP32 accuracy, at twice the MMA count of FMM_TC_BF16X3.
  *   M      device, const, [4^level][p] complex64 scaled MEs (input).
  *   L      device, [4^level][p] complex64 scaled LEs (output; must not
  *          overlap M).
@@ -300,8 +304,8 @@ int fmm_m2l_batched(const fmm_tree* const* trees, const int32_t* p, int32_t npro
  *              tensor cores: each separable pass as a dense product of 8 target
  *              boxes x 16 rows by (2 n_cut + 1) x 16 over the BF16 hi/lo split,
  *              three products or one, FP32 accumulation; p = 16, grid_log2 >= 3,
- *              one cooperative launch; FMM_EUNSUPPORTED otherwise).  Any other
- *              value: FMM_EINVAL.
+ *              one cooperative launch; FMM_EUNSUPPORTED otherwise, also for
+ *              FMM_TC_TF32X3).  Any other value: FMM_EINVAL.
  *   sigma      Gaussian width (exp(-|x-y|^2 / (2 sigma^2))), > 0.
  *   A          device, const, [4^g][p][p] float32 Hermite coefficients
  *              A[b][a1][a2] (a1: x order, a2: y order), Eq. A_alpha.
@@ -513,7 +517,7 @@ int fgt_t2p_binned(int32_t grid_log2, int32_t p, double sigma, const float* C, c
  *   device error word's check bit (fmm_sync_status returns FMM_EDEVICE); the
  *   affected targets are skipped.
  *   prec FMM_TC_BF16X3 / FMM_TC_BF16: tensor cores, p = 16 and n_cut <= 15
- *   only (else FMM_EUNSUPPORTED).  Per target box the evaluation is the
+ *   only (else FMM_EUNSUPPORTED; FMM_TC_TF32X3 is FMM_EUNSUPPORTED here).  Per target box the evaluation is the
  *   product of the targets' y-direction Hermite values with the
  *   neighbourhood's coefficients, reduced against the x-direction values;
  *   FP32 accumulation, BF16 operands split into hi + lo (three products,

@@ -252,28 +252,31 @@ int get_m2l_tables(int p, const M2LTables** out)
     return FMM_OK;
 }
 
-int get_tc_image(int p, int variant, const void** out)
+int get_tc_image(int p, int variant, bool tf32, const void** out)
 {
     if (!m2l_tc_supported(p)) return fail(FMM_EUNSUPPORTED, "tensor-core M2L is provided for p = 16 and 24, not %d", p);
+    if (tf32 && !m2l_tc_tf32_supported(p))
+        return fail(FMM_EUNSUPPORTED, "tensor-core M2L with TF32 operands is provided for p = 16, not %d", p);
+    const int f = tf32 ? 1 : 0;
     const M2LTables* tc = nullptr;
     int rc = get_m2l_tables(p, &tc);
     if (rc) return rc;
     M2LTables* t = const_cast<M2LTables*>(tc);
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!t->tc_ready[variant]) {
-        const size_t bytes = m2l_tc_image_bytes(p);
-        cudaError_t e = cudaMalloc(&t->tc_w[variant], bytes);
+    if (!t->tc_ready[f][variant]) {
+        const size_t bytes = m2l_tc_image_bytes(p, tf32);
+        cudaError_t e = cudaMalloc(&t->tc_w[f][variant], bytes);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(tensor-core operator image)");
         cudaStream_t st;
         FMM_CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
-        rc = launch_build_tc_image(p, t->s, variant, t->tc_w[variant], st);
+        rc = launch_build_tc_image(p, t->s, variant, tf32, t->tc_w[f][variant], st);
         cudaError_t es = cudaStreamSynchronize(st);
         cudaStreamDestroy(st);
         if (rc) return rc;
         if (es != cudaSuccess) return cuda_fail(es, "building the tensor-core operator image");
-        t->tc_ready[variant] = 1;
+        t->tc_ready[f][variant] = 1;
     }
-    *out = t->tc_w[variant];
+    *out = t->tc_w[f][variant];
     return FMM_OK;
 }
 
@@ -600,18 +603,22 @@ void fmm_tree_destroy(fmm_tree* tree)
 
 static bool valid_p(int p) { return m2l_fp32_supported(p); }
 
+static bool m2l_prec_known(int prec)
+{
+    return prec == FMM_FP32 || prec == FMM_TC_BF16X3 || prec == FMM_TC_BF16 || prec == FMM_TC_TF32X3;
+}
+
 int fmm_prepare(int32_t p, int32_t prec)
 {
     clear_error();
     if (!valid_p(p)) return fail(FMM_EINVAL, "fmm_prepare: unsupported p = %d (6, 8, 12, 16, 24)", p);
-    if (prec != FMM_FP32 && prec != FMM_TC_BF16X3 && prec != FMM_TC_BF16)
-        return fail(FMM_EINVAL, "fmm_prepare: unknown precision %d", prec);
+    if (!m2l_prec_known(prec)) return fail(FMM_EINVAL, "fmm_prepare: unknown precision %d", prec);
     const M2LTables* t = nullptr;
     int rc = get_m2l_tables(p, &t);
     if (rc) return rc;
     if (prec != FMM_FP32) {
         const void* img = nullptr;
-        if ((rc = get_tc_image(p, 0, &img))) return rc;
+        if ((rc = get_tc_image(p, 0, prec == FMM_TC_TF32X3, &img))) return rc;
     }
     int* ctr = nullptr;
     if ((rc = tile_counter(&ctr, nullptr))) return rc;
@@ -627,8 +634,7 @@ static int m2l_common(const char* who, const fmm_tree* tree, int32_t level, int3
     if (level < 0 || level > tree->max_level)
         return fail(FMM_EINVAL, "%s: level %d outside 0..%d", who, level, tree->max_level);
     if (!valid_p(p)) return fail(FMM_EINVAL, "%s: unsupported p = %d (6, 8, 12, 16, 24)", who, p);
-    if (prec != FMM_FP32 && prec != FMM_TC_BF16X3 && prec != FMM_TC_BF16)
-        return fail(FMM_EINVAL, "%s: unknown precision %d", who, prec);
+    if (!m2l_prec_known(prec)) return fail(FMM_EINVAL, "%s: unknown precision %d", who, prec);
     if (!in || !out) return fail(FMM_EINVAL, "%s: NULL coefficient pointer", who);
     if (((uintptr_t)in & 15) || ((uintptr_t)out & 15))
         return fail(FMM_EINVAL, "%s: coefficient pointers must be 16-byte aligned", who);
@@ -651,6 +657,8 @@ static int m2l_dispatch(const char* who, const fmm_tree* tree, int32_t lmin, int
     if (lmax < 2) return FMM_OK;
     if (prec != FMM_FP32 && !m2l_tc_supported(p))
         return fail(FMM_EUNSUPPORTED, "%s: tensor-core precision %d is provided at p = 16, 24", who, prec);
+    if (prec == FMM_TC_TF32X3 && !m2l_tc_tf32_supported(p))
+        return fail(FMM_EUNSUPPORTED, "%s: FMM_TC_TF32X3 is provided at p = 16", who);
     const M2LTables* t = nullptr;
     int rc = get_m2l_tables(p, &t);
     if (rc) return rc;
@@ -682,8 +690,9 @@ static int m2l_dispatch(const char* who, const fmm_tree* tree, int32_t lmin, int
     if (prec != FMM_FP32) {
         const int variant = !adjoint ? 0 : ((flags & FMM_CONJ) ? 2 : 1);
         const void* img = nullptr;
-        if ((rc = get_tc_image(p, variant, &img))) return rc;
-        return launch_m2l_tc(job, p, img, prec == FMM_TC_BF16X3, st);
+        const bool tf32 = prec == FMM_TC_TF32X3;
+        if ((rc = get_tc_image(p, variant, tf32, &img))) return rc;
+        return launch_m2l_tc(job, p, img, prec != FMM_TC_BF16, tf32, st);
     }
     const float2* h = !adjoint ? t->h_fwd : ((flags & FMM_CONJ) ? t->h_adjc : t->h_adj);
     return launch_m2l_fp32(job, p, h, t->a, t->b, st);
@@ -833,6 +842,7 @@ int fgt_h2t(int32_t grid_log2, int32_t n_cut, int32_t p, int32_t prec, double si
     clear_error();
     int rc = fgt_check_args("fgt_h2t", grid_log2, n_cut, p, sigma, A, C, work, flags);
     if (rc) return rc;
+    if (prec == FMM_TC_TF32X3) return fail(FMM_EUNSUPPORTED, "fgt_h2t: FMM_TC_TF32X3 is an M2L precision");
     if (prec != FMM_FP32 && prec != FMM_TC_BF16X3 && prec != FMM_TC_BF16)
         return fail(FMM_EINVAL, "fgt_h2t: unknown precision %d", prec);
     if (prec != FMM_FP32) {

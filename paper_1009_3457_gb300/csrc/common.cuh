@@ -129,8 +129,9 @@ struct M2LTables {
     float* b = nullptr;        // [p] pre-scale
     // dense scaled operators for the tensor-core path, built on demand:
     // [0] forward, [1] plain adjoint (-T), [2] conjugate adjoint (-conj T)
-    void* tc_w[3] = {nullptr, nullptr, nullptr};
-    int tc_ready[3] = {0, 0, 0};
+    // [0] BF16 hi/lo, [1] TF32 hi/lo operands
+    void* tc_w[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+    int tc_ready[2][3] = {{0, 0, 0}, {0, 0, 0}};
 };
 int get_m2l_tables(int p, const M2LTables** out);
 double m2l_balance(int p);
@@ -172,10 +173,11 @@ int launch_m2l_fp32(M2LLaunch& job, int p, const float2* hsel, const float* a, c
 
 // launchers (m2l_tc.cu)
 bool m2l_tc_supported(int p);
-size_t m2l_tc_image_bytes(int p);
-int launch_build_tc_image(int p, double s, int variant, void* img, cudaStream_t st);
-int launch_m2l_tc(M2LLaunch& job, int p, const void* img, bool split, cudaStream_t st);
-int get_tc_image(int p, int variant, const void** out);
+bool m2l_tc_tf32_supported(int p);
+size_t m2l_tc_image_bytes(int p, bool tf32);
+int launch_build_tc_image(int p, double s, int variant, bool tf32, void* img, cudaStream_t st);
+int launch_m2l_tc(M2LLaunch& job, int p, const void* img, bool split, bool tf32, cudaStream_t st);
+int get_tc_image(int p, int variant, bool tf32, const void** out);
 // Per-device flags of the tensor-core M2L, one per tile (zero between
 // launches; grown on demand, zeroed when allocated).
 int tc_flag_workspace(int ntiles, int** flags);

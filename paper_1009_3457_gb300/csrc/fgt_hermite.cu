@@ -827,6 +827,7 @@ extern "C" int fgt_h2p(int32_t grid_log2, int32_t n_cut, int32_t p, int32_t prec
                        int32_t flags, void* stream)
 {
     clear_error();
+    if (prec == FMM_TC_TF32X3) return fail(FMM_EUNSUPPORTED, "fgt_h2p: FMM_TC_TF32X3 is an M2L precision");
     if (prec != FMM_FP32 && prec != FMM_TC_BF16X3 && prec != FMM_TC_BF16)
         return fail(FMM_EINVAL, "fgt_h2p: unknown precision %d", prec);
     if (prec != FMM_FP32 && p != 16)

@@ -407,7 +407,7 @@ int create_batch(const fmm_tree* const* trees, const int32_t* p, int32_t nprob, 
     if (nprob < 1 || nprob > 65536) return fail(FMM_EINVAL, "%s: nprob %d outside 1..65536", who, nprob);
     if (flags & ~(FMM_ACCUMULATE | FMM_BATCH_AUTOTUNE)) return fail(FMM_EINVAL, "%s: unknown flags 0x%x", who, flags);
     if (prec != FMM_FP32) {
-        if (prec == FMM_TC_BF16X3 || prec == FMM_TC_BF16)
+        if (prec == FMM_TC_BF16X3 || prec == FMM_TC_BF16 || prec == FMM_TC_TF32X3)
             return fail(FMM_EUNSUPPORTED, "%s: the batched path computes in FMM_FP32 only", who);
         return fail(FMM_EINVAL, "%s: unknown precision %d", who, prec);
     }

@@ -79,11 +79,14 @@ constexpr int kTcBlocks = 32;   // (e != 0) x 4 source classes
 constexpr int kTcReplicas = 1;  // copies of the operator image in global memory (1, 2 and 4 measured alike)
 constexpr int kTcMinUnits = 8;  // fewest units per CTA: a tile is cut between at most 5 CTAs
 
-template <int P>
+// TF: TF32 operands (hi/lo in 32-bit containers, K = 8 per MMA) instead of BF16 (K = 16)
+template <int P, bool TF = false>
 struct TcCfg {
+    static constexpr int ES = TF ? 4 : 2;             // operand element bytes
+    static constexpr int EPC = 16 / ES;               // elements per 16-byte chunk
     static constexpr int K2 = 2 * P;                  // real K per block
-    static constexpr int KCH = K2 / 8;                // 16-byte BF16 chunks per block row
-    static constexpr int KSTEP = K2 / 16;             // MMA K steps of 16 per block
+    static constexpr int KCH = K2 / EPC;              // 16-byte chunks per block row
+    static constexpr int KSTEP = K2 * ES / 32;        // MMA K steps (32 bytes of K each) per block
     static constexpr int MT = (8 * P + 127) / 128;    // M tiles of 128 rows
     static constexpr int N = kTcTileX * kTcTileY;     // parents per tile = MMA N
     static constexpr int HX = kTcTileX + 2, HY = kTcTileY + 2;
@@ -92,13 +95,13 @@ struct TcCfg {
     static constexpr int ROWB = HX * 16;
     static constexpr int IPLANE = 2 * HY * ROWB;
     static constexpr int HBUF = KCH * IPLANE;         // one class halo (hi and lo)
-    static constexpr int APART = MT * 128 * K2 * 2;   // one block's hi (or lo) operator image
+    static constexpr int APART = MT * 128 * K2 * ES;  // one block's hi (or lo) operator image
     static constexpr int STAGE = 2 * APART;           // a ring stage: hi then lo
-    static constexpr int NHB = P <= 16 ? 2 : 1;       // class halo buffers (BF16 hi/lo)
+    static constexpr int NHB = (P <= 16 && !TF) ? 2 : 1;  // class halo buffers (hi/lo)
     static constexpr int LBUF = NPOS * K2 * 4;        // the FP32 landing buffer of one class halo
     // ring stages, one producer warp each: as many as shared memory holds
-    // beside the halo buffers (8 x 16 KB at p = 16, 2 x 48 KB at p = 24)
-    static constexpr int STAGES = P <= 16 ? 6 : 2;
+    // beside the halo buffers (6 x 16 KB at p = 16, 2 x 48 KB at p = 24; TF32 at p = 16: 3 x 32 KB)
+    static constexpr int STAGES = TF ? 3 : (P <= 16 ? 6 : 2);
     static constexpr int DCOLS = MT * N;              // TMEM columns of one accumulator
     static constexpr int NACC = 2 * DCOLS <= 512 ? 2 : 1;
     static constexpr int TMEM_COLS = 512;
@@ -119,15 +122,16 @@ __host__ __device__ inline void tc_block(int b, int& ex, int& ey, int& cs)
 }
 
 // ---------------------------------------------------------------------------
-// operator image: W[(c, n, r_out)][(k, r_in)] per block, BF16 hi and lo, in
-// the canonical K-major no-swizzle layout (8-row x 16-byte core matrices):
-//   byte offset of (row R, real column q) = (R / 8) * (KCH * 128) + (q / 8) * 128 + (R % 8) * 16 + (q % 8) * 2
+// operator image: W[(c, n, r_out)][(k, r_in)] per block, hi and lo (BF16, or TF32
+// in 32-bit containers), in the canonical K-major no-swizzle layout (8-row x
+// 16-byte core matrices of EPC elements of ES bytes):
+//   byte offset of (row R, real column q) = (R / 8) * (KCH * 128) + (q / EPC) * 128 + (R % 8) * 16 + (q % EPC) * ES
 // built in FP64 on the GPU from a(D) = (-1)^n C(n+k,k) D^-(n+k+1).
 // ---------------------------------------------------------------------------
-template <int P>
+template <int P, bool TF>
 __global__ void build_tc_image_kernel(double s, int variant, unsigned char* __restrict__ img)
 {
-    using C = TcCfg<P>;
+    using C = TcCfg<P, TF>;
     const int rows = C::MT * 128;
     const int64_t total = (int64_t)kTcBlocks * rows * C::K2;
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -166,12 +170,20 @@ __global__ void build_tc_image_kernel(double s, int variant, unsigned char* __re
             w = ro == 0 ? (ri == 0 ? tr : -ti) : (ri == 0 ? ti : tr);
         }
     }
-    const __nv_bfloat16 whi = __double2bfloat16(w);
-    const __nv_bfloat16 wlo = __double2bfloat16(w - (double)__bfloat162float(whi));
-    const size_t off = (size_t)(R / 8) * (C::KCH * 128) + (size_t)(q / 8) * 128 + (R % 8) * 16 + (q % 8) * 2;
+    const size_t off =
+        (size_t)(R / 8) * (C::KCH * 128) + (size_t)(q / C::EPC) * 128 + (R % 8) * 16 + (q % C::EPC) * C::ES;
     unsigned char* blk = img + (size_t)b * 2 * C::APART;
-    *reinterpret_cast<__nv_bfloat16*>(blk + off) = whi;
-    *reinterpret_cast<__nv_bfloat16*>(blk + C::APART + off) = wlo;
+    if constexpr (TF) {
+        const uint32_t whi = f32_to_tf32((float)w);
+        const uint32_t wlo = f32_to_tf32((float)(w - (double)__uint_as_float(whi)));
+        *reinterpret_cast<uint32_t*>(blk + off) = whi;
+        *reinterpret_cast<uint32_t*>(blk + C::APART + off) = wlo;
+    } else {
+        const __nv_bfloat16 whi = __double2bfloat16(w);
+        const __nv_bfloat16 wlo = __double2bfloat16(w - (double)__bfloat162float(whi));
+        *reinterpret_cast<__nv_bfloat16*>(blk + off) = whi;
+        *reinterpret_cast<__nv_bfloat16*>(blk + C::APART + off) = wlo;
+    }
 }
 
 // unit order within a tile: u & 31 = c' * 8 + pe (class-major, so a class
@@ -307,15 +319,27 @@ __device__ __forceinline__ void tc_stage_chunk(const float4* a, const float4* b,
     *reinterpret_cast<uint4*>(dst + lo_off) = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
-// A class halo that a tensor copy landed as FP32 [parent][2p] -> its BF16 hi/lo parts in the
-// layout the MMAs read, by NT threads (this one is `st`).  Thread st converts parents st,
+// One TF32 chunk (2 complex = 4 floats) -> its TF32 hi part at dst and lo part at dst + lo_off.
+__device__ __forceinline__ void tc_stage_chunk_tf32(const float4 v, unsigned char* dst, int lo_off)
+{
+    const uint32_t h0 = f32_to_tf32(v.x), h1 = f32_to_tf32(v.y), h2 = f32_to_tf32(v.z), h3 = f32_to_tf32(v.w);
+    *reinterpret_cast<uint4*>(dst) = make_uint4(h0, h1, h2, h3);
+    *reinterpret_cast<uint4*>(dst + lo_off) =
+        make_uint4(f32_to_tf32(v.x - __uint_as_float(h0)), f32_to_tf32(v.y - __uint_as_float(h1)),
+                   f32_to_tf32(v.z - __uint_as_float(h2)), f32_to_tf32(v.w - __uint_as_float(h3)));
+}
+
+// A class halo that a tensor copy landed as FP32 [parent][2p] -> its hi/lo parts in the
+// layout the MMAs read, by NT threads (this one is `st`).  TF32: thread st converts parents
+// st, st + NT, ..., each one's chunks from (st + s) % KCH on (8 consecutive threads read 8
+// different 16-byte bank groups and write 8 consecutive parents of a halo row).  BF16:  Thread st converts parents st,
 // st + NT, ..., each one's chunks in the order (st + s) % KCH and the two 16-byte halves of a
 // chunk in the order set by bit 2 of st, so that 8 consecutive threads read 8 different
 // 16-byte bank groups of the landing buffer and write 8 consecutive parents of a halo row.
-template <int P, int NT>
+template <int P, int NT, bool TF = false>
 __device__ __forceinline__ void tc_convert_landed(const unsigned char* lbuf, unsigned char* buf, int st, uint32_t keep)
 {
-    using C = TcCfg<P>;
+    using C = TcCfg<P, TF>;
     const int h = (st >> 2) & 1, c0 = st % C::KCH;
     int j = 0;
 #pragma unroll 1
@@ -331,6 +355,17 @@ __device__ __forceinline__ void tc_convert_landed(const unsigned char* lbuf, uns
         }
         const float4* src = reinterpret_cast<const float4*>(lbuf + (size_t)pos * (C::K2 * 4));
         unsigned char* dst = buf + (size_t)(2 * (pos / C::HX)) * C::ROWB + (size_t)(pos % C::HX) * 16;
+        if constexpr (TF) {
+            float4 x[C::KCH];
+#pragma unroll
+            for (int s = 0; s < C::KCH; ++s) x[s] = src[c0 + s < C::KCH ? c0 + s : c0 + s - C::KCH];
+#pragma unroll
+            for (int s = 0; s < C::KCH; ++s) {
+                const int ch = c0 + s < C::KCH ? c0 + s : c0 + s - C::KCH;
+                tc_stage_chunk_tf32(x[s], dst + (size_t)ch * C::IPLANE, C::ROWB);
+            }
+            continue;
+        }
         float4 x[C::KCH], y[C::KCH];
 #pragma unroll
         for (int s = 0; s < C::KCH; ++s) {
@@ -393,12 +428,12 @@ __device__ __forceinline__ bool wait_flag(const int* f)
     return false;
 }
 
-template <int P>
+template <int P, bool TF>
 __global__ void __launch_bounds__(kTcCtaThreads, 1)
     m2l_tc_kernel(M2LLaunch job, const __grid_constant__ TcMaps maps, const unsigned char* __restrict__ img, int split,
                   int units, int* __restrict__ flags, int* __restrict__ done, int* __restrict__ err)
 {
-    using C = TcCfg<P>;
+    using C = TcCfg<P, TF>;
     extern __shared__ __align__(1024) unsigned char tsm[];
     unsigned char* hbuf = tsm;                                   // NHB class halos
     unsigned char* lbuf = tsm + (size_t)C::NHB * C::HBUF;        // FP32 landing buffer of a class halo
@@ -507,7 +542,7 @@ __global__ void __launch_bounds__(kTcCtaThreads, 1)
             const uint32_t keep = tc_halo_keep<P, kTcCtaThreads>(tl0, cls, tid);
             const bool landed = mbar_wait(lfull, 0, 64);
             if (__syncthreads_and(landed ? 1 : 0)) {
-                tc_convert_landed<P, kTcCtaThreads>(lbuf, hbuf, tid, keep);
+                tc_convert_landed<P, kTcCtaThreads, TF>(lbuf, hbuf, tid, keep);
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 first_done = true;
             }
@@ -538,9 +573,12 @@ __global__ void __launch_bounds__(kTcCtaThreads, 1)
         }
     } else if (warp == kMmaWarp && lane == 0) {
         // ---------------- MMA issuer ----------------
-        // per K step of 16 and M tile: D += A_hi B_hi (+ A_hi B_lo + A_lo B_hi with the split),
-        // all N = 256 products into the same accumulator columns
-        const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(C::N >> 3) << 17) | ((128u >> 4) << 24);
+        // per K step (32 bytes of K: 16 BF16 or 8 TF32) and M tile: D += A_hi B_hi (+ A_hi B_lo +
+        // A_lo B_hi with the split), all N = 256 products into the same accumulator columns;
+        // instruction descriptor: D F32, A and B BF16 (1) or TF32 (2), K-major, N, M = 128
+        constexpr uint32_t kFmt = TF ? 2u : 1u;
+        const uint32_t idesc =
+            (1u << 4) | (kFmt << 7) | (kFmt << 10) | ((uint32_t)(C::N >> 3) << 17) | ((128u >> 4) << 24);
         const uint32_t abase = su32(astage), hbase = su32(hbuf);
         constexpr uint64_t alo_off = (uint64_t)(C::APART >> 4);
         int g = 0, hg = 0;
@@ -584,10 +622,16 @@ __global__ void __launch_bounds__(kTcCtaThreads, 1)
                         for (int mt = 0; mt < C::MT; ++mt) {
                             const uint64_t da = ahi + (uint64_t)((mt * 16 * C::KCH * 128 + 2 * kk * 128) >> 4);
                             const uint32_t dm = dset + (uint32_t)(mt * C::N);
-                            umma_bf16(dm, da, bhi + kb, idesc, (first && kk == 0) ? 0u : 1u);
-                            if (split) {
-                                umma_bf16(dm, da, blo + kb, idesc, 1u);
-                                umma_bf16(dm, da + alo_off, bhi + kb, idesc, 1u);
+                            if constexpr (TF) {
+                                umma_tf32(dm, da, bhi + kb, idesc, (first && kk == 0) ? 0u : 1u);
+                                umma_tf32(dm, da, blo + kb, idesc, 1u);
+                                umma_tf32(dm, da + alo_off, bhi + kb, idesc, 1u);
+                            } else {
+                                umma_bf16(dm, da, bhi + kb, idesc, (first && kk == 0) ? 0u : 1u);
+                                if (split) {
+                                    umma_bf16(dm, da, blo + kb, idesc, 1u);
+                                    umma_bf16(dm, da + alo_off, bhi + kb, idesc, 1u);
+                                }
                             }
                         }
                     }
@@ -633,7 +677,7 @@ __global__ void __launch_bounds__(kTcCtaThreads, 1)
             }
             unsigned char* buf = hbuf + (size_t)hb * C::HBUF;
             if (pending == k) {
-                tc_convert_landed<P, NST>(lbuf, buf, st, keep);
+                tc_convert_landed<P, NST, TF>(lbuf, buf, st, keep);
                 ++nlanded;
             } else {
 #pragma unroll 1
@@ -654,9 +698,9 @@ __global__ void __launch_bounds__(kTcCtaThreads, 1)
                         }
                         const int ix = 2 * qx + (cls & 1), iy = 2 * qy + (cls >> 1);
                         if (tl.ex && !__ldg(tl.ex + (size_t)iy * tl.side + ix)) continue;  // absent source
-                        const float4* src = tl.M + ((size_t)iy * tl.side + ix) * (P / 2) + 2 * ch;
+                        const float4* src = tl.M + ((size_t)iy * tl.side + ix) * (P / 2) + (TF ? ch : 2 * ch);
                         v[b][0] = __ldg(src);
-                        v[b][1] = __ldg(src + 1);
+                        if (!TF) v[b][1] = __ldg(src + 1);
                     }
 #pragma unroll
                     for (int b = 0; b < kStageBatch; ++b) {
@@ -664,10 +708,10 @@ __global__ void __launch_bounds__(kTcCtaThreads, 1)
                         if (it >= NIT) break;
                         const int pos = it / C::KCH, ch = it % C::KCH;
                         float4 f0 = v[b][0], f1 = v[b][1];
-                        tc_stage_chunk(&f0, &f1,
-                                       buf + (size_t)ch * C::IPLANE + (size_t)(2 * (pos / C::HX)) * C::ROWB +
-                                           (size_t)(pos % C::HX) * 16,
-                                       C::ROWB);
+                        unsigned char* dst = buf + (size_t)ch * C::IPLANE + (size_t)(2 * (pos / C::HX)) * C::ROWB +
+                                             (size_t)(pos % C::HX) * 16;
+                        if constexpr (TF) tc_stage_chunk_tf32(f0, dst, C::ROWB);
+                        else tc_stage_chunk(&f0, &f1, dst, C::ROWB);
                     }
                 }
             }
@@ -817,8 +861,12 @@ __global__ void __launch_bounds__(kTcCtaThreads, 1)
 // ---------------------------------------------------------------------------
 bool m2l_tc_supported(int p) { return p == 16 || p == 24; }
 
-size_t m2l_tc_image_bytes(int p)
+// TF32 operands double the halo and operator bytes: they fit shared memory at p = 16 only
+bool m2l_tc_tf32_supported(int p) { return p == 16; }
+
+size_t m2l_tc_image_bytes(int p, bool tf32)
 {
+    if (tf32) return p == 16 ? (size_t)kTcReplicas * kTcBlocks * 2 * TcCfg<16, true>::APART : 0;
     switch (p) {
         case 16: return (size_t)kTcReplicas * kTcBlocks * 2 * TcCfg<16>::APART;
         case 24: return (size_t)kTcReplicas * kTcBlocks * 2 * TcCfg<24>::APART;
@@ -826,23 +874,27 @@ size_t m2l_tc_image_bytes(int p)
     }
 }
 
-template <int P>
+template <int P, bool TF>
 static int build_image_p(double s, int variant, unsigned char* img, cudaStream_t st)
 {
-    using C = TcCfg<P>;
+    using C = TcCfg<P, TF>;
     const int64_t total = (int64_t)kTcBlocks * C::MT * 128 * C::K2;
-    build_tc_image_kernel<P><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(s, variant, img);
+    build_tc_image_kernel<P, TF><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(s, variant, img);
     FMM_CUDA_TRY(cudaGetLastError());
     const size_t one = (size_t)kTcBlocks * 2 * C::APART;
     for (int r = 1; r < kTcReplicas; ++r) FMM_CUDA_TRY(cudaMemcpyAsync(img + r * one, img, one, cudaMemcpyDeviceToDevice, st));
     return FMM_OK;
 }
 
-int launch_build_tc_image(int p, double s, int variant, void* img, cudaStream_t st)
+int launch_build_tc_image(int p, double s, int variant, bool tf32, void* img, cudaStream_t st)
 {
+    if (tf32) {
+        if (p == 16) return build_image_p<16, true>(s, variant, (unsigned char*)img, st);
+        return fail(FMM_EUNSUPPORTED, "M2L TC TF32x3: unsupported p = %d (16)", p);
+    }
     switch (p) {
-        case 16: return build_image_p<16>(s, variant, (unsigned char*)img, st);
-        case 24: return build_image_p<24>(s, variant, (unsigned char*)img, st);
+        case 16: return build_image_p<16, false>(s, variant, (unsigned char*)img, st);
+        case 24: return build_image_p<24, false>(s, variant, (unsigned char*)img, st);
         default: return fail(FMM_EINVAL, "M2L TC: unsupported p = %d", p);
     }
 }
@@ -864,10 +916,10 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
     return fn;
 }
 
-template <int P>
+template <int P, bool TF>
 static int launch_tc_p(M2LLaunch& job, const void* img, bool split, int* err, cudaStream_t st)
 {
-    using C = TcCfg<P>;
+    using C = TcCfg<P, TF>;
     int total = 0;
     for (int i = 0; i < job.nlev; ++i) {
         job.lv[i].tile_begin = total;
@@ -910,21 +962,25 @@ static int launch_tc_p(M2LLaunch& job, const void* img, bool split, int* err, cu
         maps.use_tma[i] = 1;
     }
     static unsigned long long opted;
-    if ((rc = smem_opt_in((const void*)m2l_tc_kernel<P>, (int)C::smem, &opted))) return rc;
-    m2l_tc_kernel<P><<<grid, kTcCtaThreads, C::smem, st>>>(job, maps, (const unsigned char*)img, split ? 1 : 0, units,
-                                                            flags, ctr + 1, err);
+    if ((rc = smem_opt_in((const void*)m2l_tc_kernel<P, TF>, (int)C::smem, &opted))) return rc;
+    m2l_tc_kernel<P, TF><<<grid, kTcCtaThreads, C::smem, st>>>(job, maps, (const unsigned char*)img, split ? 1 : 0,
+                                                                units, flags, ctr + 1, err);
     FMM_CUDA_TRY(cudaGetLastError());
     return FMM_OK;
 }
 
-int launch_m2l_tc(M2LLaunch& job, int p, const void* img, bool split, cudaStream_t st)
+int launch_m2l_tc(M2LLaunch& job, int p, const void* img, bool split, bool tf32, cudaStream_t st)
 {
     int* err = nullptr;
     int rc = device_error_word(&err);
     if (rc) return rc;
+    if (tf32) {
+        if (p == 16) return launch_tc_p<16, true>(job, img, true, err, st);
+        return fail(FMM_EUNSUPPORTED, "M2L TC TF32x3: unsupported p = %d (16)", p);
+    }
     switch (p) {
-        case 16: return launch_tc_p<16>(job, img, split, err, st);
-        case 24: return launch_tc_p<24>(job, img, split, err, st);
+        case 16: return launch_tc_p<16, false>(job, img, split, err, st);
+        case 24: return launch_tc_p<24, false>(job, img, split, err, st);
         default: return fail(FMM_EINVAL, "M2L TC: unsupported p = %d", p);
     }
 }

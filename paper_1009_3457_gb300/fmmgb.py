@@ -24,6 +24,7 @@ FMM_EDEVICE = -6
 FMM_FP32 = 0
 FMM_TC_BF16X3 = 1
 FMM_TC_BF16 = 2
+FMM_TC_TF32X3 = 3
 
 FMM_ACCUMULATE = 1
 FMM_CONJ = 2

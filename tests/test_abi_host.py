@@ -71,6 +71,11 @@ def test_m2l_rejects_bad_arguments_before_launch(fmm):
     assert lib.fmm_m2l(tree.handle, 3, 8, 0, 4096, 1 << 20, 8, None) == fmm.FMM_EINVAL
     assert "overlap" in fmm.fmm_last_error() or "flags" in fmm.fmm_last_error()
     assert lib.fmm_m2l_adjoint(tree.handle, 3, 8, 0, 4096, 1 << 20, 16, None) == fmm.FMM_EINVAL
+    # FMM_TC_TF32X3 is provided at p = 16 only (refused before any device work); 4 is no precision
+    TF = fmm.FMM_TC_TF32X3
+    assert lib.fmm_m2l(tree.handle, 3, 24, TF, 1 << 20, 1 << 24, 0, None) == fmm.FMM_EUNSUPPORTED
+    assert "p = 16" in fmm.fmm_last_error()
+    assert lib.fmm_m2l(tree.handle, 3, 16, 4, 1 << 20, 1 << 24, 0, None) == fmm.FMM_EINVAL
 
 
 def test_p2m_m2m_reject_bad_arguments(fmm):
@@ -128,6 +133,7 @@ def test_batch_rejects_bad_arguments_before_launch(fmm):
     assert call([t3.handle], [7], good_M, good_L) == fmm.FMM_EINVAL
     assert call([t3.handle], [24], good_M, good_L) == fmm.FMM_EUNSUPPORTED
     assert call([t3.handle], [8], good_M, good_L, prec=fmm.FMM_TC_BF16X3) == fmm.FMM_EUNSUPPORTED
+    assert call([t3.handle], [8], good_M, good_L, prec=fmm.FMM_TC_TF32X3) == fmm.FMM_EUNSUPPORTED
     assert call([t3.handle], [8], good_M, good_L, prec=9) == fmm.FMM_EINVAL
     assert call([t3.handle], [8], good_M, good_L, flags=16) == fmm.FMM_EINVAL
     assert call([t3.handle], [8], [1 << 20, None], good_L) == fmm.FMM_EINVAL
@@ -241,6 +247,8 @@ def test_fgt_hermite_entry_points_reject_bad_arguments(fmm):
     assert lib.fgt_h2p(3, 2, 8, 7, 0.1, 64, 128, 10, 256, 512, 1024, 0, None) == fmm.FMM_EINVAL   # precision
     assert lib.fgt_h2p(3, 2, 8, T3, 0.1, 64, 128, 10, 256, 512, 1024, 0, None) == fmm.FMM_EUNSUPPORTED   # TC p
     assert lib.fgt_h2p(3, 16, 16, T3, 0.1, 64, 128, 10, 256, 512, 1024, 0, None) == fmm.FMM_EUNSUPPORTED  # TC n_cut
+    TF = fmm.FMM_TC_TF32X3  # an M2L precision only
+    assert lib.fgt_h2p(3, 2, 16, TF, 0.1, 64, 128, 10, 256, 512, 1024, 0, None) == fmm.FMM_EUNSUPPORTED
     # fgt_h2t(g, ncut, p, prec, sigma, A, C, work, flags, stream)
     A_, C_ = 1 << 20, 1 << 22
     assert lib.fgt_h2t(3, 2, 8, 7, 0.1, A_, C_, None, 0, None) == fmm.FMM_EINVAL            # precision
@@ -249,6 +257,7 @@ def test_fgt_hermite_entry_points_reject_bad_arguments(fmm):
     assert lib.fgt_h2t(2, 2, 16, T3, 0.1, A_, C_, None, 0, None) == fmm.FMM_EUNSUPPORTED    # TC grid under 8 x 8
     assert lib.fgt_h2t(3, 17, 16, T3, 0.1, A_, C_, None, 0, None) == fmm.FMM_EINVAL         # n_cut
     assert lib.fgt_h2t(3, 2, 16, T3, 0.1, A_, C_ + 8, None, 0, None) == fmm.FMM_EINVAL      # C misaligned
+    assert lib.fgt_h2t(3, 2, 16, TF, 0.1, A_, C_, None, 0, None) == fmm.FMM_EUNSUPPORTED    # TF32x3: M2L only
 
 
 def test_p2p_rejects_bad_arguments(fmm):

@@ -180,11 +180,14 @@ def test_gradient_matches_oracle_fd_gmm_workload(fmm, orc):
     assert np.linalg.norm(g - fd) <= 1e-4 * np.linalg.norm(fd), np.linalg.norm(g - fd) / np.linalg.norm(fd)
 
 
-@pytest.mark.parametrize("p", [16, 24])
-def test_tensor_core_adaptive_levels(fmm, orc, p):
-    """BF16x3 on an adaptive tree, levels 2..8 in one launch: V-list translations within the
-    tensor-core bar (1e-4) at existing boxes; absent source boxes hold garbage that must not
-    enter, absent targets keep their values; then accumulating into existing values."""
+@pytest.mark.parametrize("p,prec_name,tol", [(16, "FMM_TC_BF16X3", 1e-4), (24, "FMM_TC_BF16X3", 1e-4),
+                                              (16, "FMM_TC_TF32X3", 1e-5)])
+def test_tensor_core_adaptive_levels(fmm, orc, p, prec_name, tol):
+    """The tensor cores on an adaptive tree, levels 2..8 in one launch: V-list translations within
+    the precision's bar (BF16x3 1e-4, TF32x3 the FP32 bar 1e-5) at existing boxes; absent source
+    boxes hold garbage that must not enter, absent targets keep their values; then accumulating
+    into existing values."""
+    prec = getattr(fmm, prec_name)
     xy, c, tree, otree, _ = _case(orc, fmm, 30000, 40, 8, 15)
     lev, box = orc.leaf_boxes(otree, xy)
     levels = list(range(2, 9))
@@ -196,7 +199,7 @@ def test_tensor_core_adaptive_levels(fmm, orc, p):
         Min[l] = m
     Md = [_dev(Min[l]) for l in levels]
     Ld = [m.new_full(m.shape, 5.0 + 0j) for m in Md]
-    fmm.fmm_m2l_levels(tree, 2, p, Md, Ld, prec=fmm.FMM_TC_BF16X3)
+    fmm.fmm_m2l_levels(tree, 2, p, Md, Ld, prec=prec)
     fmm.fmm_sync_status()
     refs = {}
     for l, out in zip(levels, Ld):
@@ -204,19 +207,19 @@ def test_tensor_core_adaptive_levels(fmm, orc, p):
         got = _host(out)
         refs[l] = orc.scale_le(orc.m2l_adaptive(otree, l, p, Ms[l]), l)
         if ex.any():
-            assert _rel(got[ex], refs[l][ex]) <= 1e-4, l
+            assert _rel(got[ex], refs[l][ex]) <= tol, l
         assert (got[~ex] == 5.0).all(), l  # absent boxes untouched
     # accumulate: L0 + M2L(M) at existing boxes
     rng = np.random.default_rng(2)
     X = {l: rng.standard_normal((4 ** l, p)) + 1j * rng.standard_normal((4 ** l, p)) for l in levels}
     Ld = [_dev(X[l]) for l in levels]
-    fmm.fmm_m2l_levels(tree, 2, p, Md, Ld, prec=fmm.FMM_TC_BF16X3, accumulate=True)
+    fmm.fmm_m2l_levels(tree, 2, p, Md, Ld, prec=prec, accumulate=True)
     fmm.fmm_sync_status()
     for l, out in zip(levels, Ld):
         ex = otree.level(l)
         got = _host(out) - X[l].astype(np.complex64).astype(np.complex128)
         if ex.any():
-            assert _rel(got[ex], refs[l][ex]) <= 1e-4, l
+            assert _rel(got[ex], refs[l][ex]) <= tol, l
 
 
 @pytest.mark.parametrize("conj", [False, True])
