@@ -127,7 +127,7 @@ __device__ __forceinline__ TcH2pTile tc_h2p_tile(const H2pTcArgs& a, int4 ti)
     return t;
 }
 
-// one lane waits, the warp follows its verdict (all lanes leave together); the
+// one lane waits, the warp follows its outcome (all lanes leave together); the
 // __syncwarp orders the other lanes' later accesses after lane 0's acquire
 __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, int lane, uint32_t sleep_ns = 128)
 {

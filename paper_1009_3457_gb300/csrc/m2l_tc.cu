@@ -899,7 +899,7 @@ int launch_build_tc_image(int p, double s, int variant, bool tf32, void* img, cu
     }
 }
 
-// cuTensorMapEncodeTiled from the driver, looked up once (no link against libcuda)
+// cuTensorMapEncodeTiled from the CUDA driver API, looked up once (no link against libcuda)
 static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
 {
     static std::once_flag once;
