@@ -58,7 +58,7 @@ def test_translation_after_a_timeout_is_correct(fmm, orc):
     p, L = 16, 4
     Ms = orc.upward_uniform(L, p, xy, c)
     tree = fmm.fmm_build_lists(None, L)
-    for prec in (fmm.FMM_TC_BF16X3, fmm.FMM_FP32):
+    for prec in (fmm.FMM_TC_BF16X3, fmm.FMM_TC_TF32X3, fmm.FMM_FP32):
         for level in range(2, L + 1):
             Md = torch.from_numpy(orc.scale_me(Ms[level], level).astype(np.complex64)).cuda()
             Ld = torch.empty_like(Md)
