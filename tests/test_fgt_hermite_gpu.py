@@ -186,13 +186,13 @@ def test_h2p_accumulate_and_ragged_counts(fmm, orc, gmm_sources):
         _check(_h2p(fmm, g, ncut, p, sigma, A32, y, G=G, accumulate=True), ref + 0.25)
 
 
-@pytest.mark.parametrize("g", [6, 7])
-def test_h2p_claim_order_on_large_grids(fmm, orc, g):
+@pytest.mark.parametrize("g", [0, 1, 6, 7])
+def test_h2p_claim_order_grids(fmm, orc, g):
     """Claims are handed out heaviest neighbourhood first: one CTA builds that order for grids
     of up to 64 x 64 boxes, five launches (row prefix, keys, scan, scatter, claims) above.
-    A 64 x 64 and a 128 x 128 grid, a third of the source boxes empty, clustered targets (per
-    box counts from 0 to hundreds, most boxes without targets), G pre-filled with NaN: every
-    target is evaluated once, against the oracle."""
+    Grids of 1 x 1, 2 x 2 (the neighbourhood clipped to the grid), 64 x 64 and 128 x 128 boxes,
+    a third of the source boxes empty, clustered targets (per box counts from 0 to thousands),
+    G pre-filled with NaN: every target is evaluated once, against the oracle."""
     import math
     import torch
 
@@ -202,7 +202,9 @@ def test_h2p_claim_order_on_large_grids(fmm, orc, g):
     sigma = 2.0 ** -g / (math.sqrt(2.0) * 0.442)
     fact = np.array([math.factorial(a) for a in range(p)], float)
     A = rng.standard_normal((n * n, p, p)) * (0.3 ** (np.arange(p)[:, None] + np.arange(p)[None, :])) / np.outer(fact, fact)
-    A[rng.random(n * n) < 0.33] = 0.0
+    empty = rng.random(n * n) < 0.33
+    empty[0] = False  # at least one source box holds coefficients
+    A[empty] = 0.0
     A32 = A.astype(np.float32)
     c = rng.random((6, 2))
     y = np.concatenate([np.clip(c[i] + 0.03 * rng.standard_normal((3000, 2)), 0.0, 0.999999) for i in range(6)]
