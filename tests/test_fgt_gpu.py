@@ -85,6 +85,29 @@ def test_fgt_h2t_edge_sizes(fmm, orc, g, ncut):
     _check(Cd.cpu().numpy().astype(np.float64)[tg], ref)
 
 
+@pytest.mark.parametrize("g,ncut,p", [(9, 10, 8), (10, 3, 4)])
+def test_fgt_h2t_large_grids_sampled(fmm, orc, g, ncut, p):
+    """Grids of 512 x 512 (n_cut 10, p 8) and 1024 x 1024 boxes (n_cut 3, p 4): the two pass
+    kernels over thousands of segments; corners, edges and random interior boxes against the
+    oracle."""
+    import torch
+
+    rng = np.random.default_rng(500 + g)
+    sigma = 0.5 * 2.0 ** -g
+    n = 1 << g
+    fact = np.array([math.factorial(a) for a in range(p)], float)
+    scale = ((0.3 ** (np.arange(p)[:, None] + np.arange(p)[None, :])) / np.outer(fact, fact)).astype(np.float32)
+    A = rng.standard_normal((n * n, p, p), dtype=np.float32) * scale
+    edges = [0, n - 1, n * n - 1, n * (n - 1), n // 2, n // 2 * n, n // 2 * n + n - 1, n * (n - 1) + n // 2]
+    tg = np.unique(np.concatenate([edges, rng.integers(0, n * n, 40)]))
+    ref = orc.fgt_h2t_targets(g, ncut, p, sigma, A, tg)
+    Ad = _dev(A)
+    Cd = torch.empty_like(Ad)
+    fmm.fgt_h2t(g, ncut, p, sigma, Ad, Cd)
+    fmm.fmm_sync_status()
+    _check(Cd.cpu().numpy().astype(np.float64)[tg], ref)
+
+
 def test_fgt_h2t_accumulate_and_work_buffer(fmm, orc, gmm_sources):
     import torch
 

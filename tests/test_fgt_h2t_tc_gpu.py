@@ -74,10 +74,11 @@ def test_fgt_h2t_tc_bf16x3(fmm, orc, gmm_sources, sigma):
     assert l2 <= TOL_L2_X3 and box <= TOL_BOX_X3, (l2, box)
 
 
-@pytest.mark.parametrize("g,ncut", [(3, 0), (4, 3), (6, 2), (5, 16)])
+@pytest.mark.parametrize("g,ncut", [(3, 0), (4, 3), (6, 2), (5, 16), (8, 10)])
 def test_fgt_h2t_tc_neighbourhoods_and_grids(fmm, orc, g, ncut):
     """n_cut 0 (one offset: the second MMA issuer has none), 3, 2 on a 64 x 64 grid (several
-    segments per CTA and pass), and the largest n_cut, 16."""
+    segments per CTA and pass), the largest n_cut, 16, and a 256 x 256 grid at n_cut 10 (8,192
+    segments per pass over the co-resident CTAs)."""
     import torch
     import math
 
