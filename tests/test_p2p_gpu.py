@@ -61,10 +61,12 @@ def _check(got, ref, l2=1e-5, worst=1e-4):
     assert err <= l2 and w <= worst, f"relative L2 {err:.3e}, worst {w:.3e}"
 
 
-@pytest.mark.parametrize("level,bar", [(0, 2e-4), (2, 1e-4), (3, 1e-5), (5, 1e-5)])
-def test_p2p_matches_oracle(fmm, orc, level, bar):
+@pytest.mark.parametrize("level,bar,nsrc", [(0, 2e-4, 4000), (2, 1e-4, 4000), (3, 1e-5, 4000), (5, 1e-5, 4000),
+                                            (8, 1e-5, 262144), (10, 1e-5, 1048576)])
+def test_p2p_matches_oracle(fmm, orc, level, bar, nsrc):
+    """Levels 0 to 10, the finest (1M boxes) with ~1 source per box."""
     rng = np.random.default_rng(40 + level)
-    xy, c = workloads.uniform_particles(4000, rng)
+    xy, c = workloads.uniform_particles(nsrc, rng)
     z = rng.random(3000) + 1j * rng.random(3000)
     _check(_p2p(fmm, level, xy, c, z), orc.p2p_uniform(level, xy, c, z), l2=bar, worst=max(1e-4, 2 * bar))
 
