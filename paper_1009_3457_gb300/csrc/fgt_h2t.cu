@@ -34,21 +34,25 @@
 
 namespace fmmgb {
 
-constexpr int kFgtSeg = 4;       // boxes per CTA along the pass axis
-constexpr int kFgtGroups = 7;    // tap groups per box: partial sums reduced in shared memory
 constexpr int kFgtMaxCut = 16;   // largest n_cut accepted
 
 // Thread mapping: (tap group, box of the segment, 4-row block, 4-column block);
-// a thread accumulates a 4 x 4 block of one box's output over a seventh of the
-// taps.  At sigma = 0.05 (32 x 32 boxes) and p = 16 a pass runs 256 CTAs of
-// 448 threads: enough warps per SM to hide the halo staging of this small grid.
+// a thread accumulates a 4 x 4 block of one box's output over its group's share
+// of the taps, and the groups' partial sums are reduced in shared memory.
+// p = 16 runs segments of 8 boxes with 3 tap groups (384 threads): the halo of
+// 2 n_cut boxes is staged once per 8 outputs.  Smaller p keep 4 boxes and 7
+// groups, which give them enough warps per SM (at sigma = 0.05, 32 x 32 boxes,
+// a pass of p = 8 is 256 CTAs of 112 threads).  Both shapes were timed on the
+// sigma = 0.05 grid (n_cut = 10) against 2-32 boxes and 1-11 groups.
 template <int P>
 struct FgtCfg {
+    static constexpr int SEG = P == 16 ? 8 : 4;     // boxes per CTA along the pass axis
+    static constexpr int GROUPS = P == 16 ? 3 : 7;  // tap groups per box
     static constexpr int RB = 4;                // output rows (b) per thread
     static constexpr int RBLK = P / RB;         // row blocks per box
     static constexpr int CB = P / 4;            // column blocks of 4 per box
     static constexpr int TPB = RBLK * CB;       // threads per box and tap group
-    static constexpr int THREADS = kFgtGroups * kFgtSeg * TPB;
+    static constexpr int THREADS = GROUPS * SEG * TPB;
     static constexpr int NH = 2 * P - 1;
     static constexpr int BS = P * P + 16;       // padded float stride between boxes in shared memory
     static_assert(P % 4 == 0 && BS % 4 == 0, "16-byte aligned float4 rows");
@@ -58,8 +62,8 @@ template <int P>
 size_t fgt_smem_bytes(int ncut)
 {
     using C = FgtCfg<P>;
-    return sizeof(float) * ((size_t)(kFgtSeg + 2 * ncut) * C::BS + (size_t)(2 * ncut + 1) * C::NH + P +
-                            (size_t)(kFgtGroups - 1) * kFgtSeg * P * P);
+    return sizeof(float) * ((size_t)(C::SEG + 2 * ncut) * C::BS + (size_t)(2 * ncut + 1) * C::NH + P +
+                            (size_t)(C::GROUPS - 1) * C::SEG * P * P);
 }
 
 // Hermite-function values h_j(u_d), j < nh, u_d = -(d - ncut) * ustep (source
@@ -92,18 +96,18 @@ __global__ void __launch_bounds__(FgtCfg<P>::THREADS) fgt_pass_kernel(int g, int
                                                                       const float* __restrict__ htab)
 {
     using C = FgtCfg<P>;
-    constexpr int RB = C::RB, NH = C::NH, BS = C::BS;
+    constexpr int RB = C::RB, NH = C::NH, BS = C::BS, SEG = C::SEG, GROUPS = C::GROUPS;
     extern __shared__ __align__(16) float fsm[];
     const int taps = 2 * ncut + 1;
     // float4-accessed arrays first: BS and P * P are multiples of 4 floats, so
     // halo and part start on 16-byte boundaries; the scalar tables follow
-    float* halo = fsm;                                              // [kFgtSeg + 2 ncut][BS]
-    float* part = halo + (size_t)(kFgtSeg + 2 * ncut) * BS;         // [kFgtGroups - 1][kFgtSeg][P][P]
-    float* hs = part + (size_t)(kFgtGroups - 1) * kFgtSeg * P * P;  // [taps][NH]
+    float* halo = fsm;                                      // [SEG + 2 ncut][BS]
+    float* part = halo + (size_t)(SEG + 2 * ncut) * BS;     // [GROUPS - 1][SEG][P][P]
+    float* hs = part + (size_t)(GROUPS - 1) * SEG * P * P;  // [taps][NH]
     float* ss = hs + taps * NH;                                     // [P]
 
     const int side = 1 << g;
-    const int seg0 = blockIdx.x * kFgtSeg;
+    const int seg0 = blockIdx.x * SEG;
     const int other = blockIdx.y;
     const int tid = threadIdx.x;
     // the second pass may be scheduled now: it prepares its tables and waits for this grid
@@ -124,8 +128,8 @@ __global__ void __launch_bounds__(FgtCfg<P>::THREADS) fgt_pass_kernel(int g, int
     // the input may come from the grid launched just before (the first pass): wait for it
     // (a no-op unless this grid was launched as its programmatic dependent)
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    // stage the boxes [seg0 - ncut, seg0 + kFgtSeg + ncut) of this row/column, zero outside the grid
-    const int nhb = kFgtSeg + 2 * ncut;
+    // stage the boxes [seg0 - ncut, seg0 + SEG + ncut) of this row/column, zero outside the grid
+    const int nhb = SEG + 2 * ncut;
     const float4* in4 = reinterpret_cast<const float4*>(in);
     for (int i = tid; i < nhb * (P * P / 4); i += blockDim.x) {  // every copy in flight before any wait
         const int q = i % (P * P / 4), hb = i / (P * P / 4);
@@ -138,14 +142,14 @@ __global__ void __launch_bounds__(FgtCfg<P>::THREADS) fgt_pass_kernel(int g, int
     asm volatile("cp.async.wait_all;\n" ::: "memory");
     __syncthreads();
 
-    const int grp = tid / (kFgtSeg * C::TPB);
-    const int rem = tid % (kFgtSeg * C::TPB);
+    const int grp = tid / (SEG * C::TPB);
+    const int rem = tid % (SEG * C::TPB);
     const int j = rem / C::TPB;                  // box within the segment
     const int r = rem % C::TPB;
     const int b0 = (r % C::RBLK) * RB;           // first output row
     const int c0 = (r / C::RBLK) * 4;            // first of 4 columns
     const int pos = seg0 + j;
-    const int per = (taps + kFgtGroups - 1) / kFgtGroups;
+    const int per = (taps + GROUPS - 1) / GROUPS;
     const int d0 = grp * per, d1 = min(taps, d0 + per);
 
     float acc[RB][4];
@@ -183,7 +187,7 @@ __global__ void __launch_bounds__(FgtCfg<P>::THREADS) fgt_pass_kernel(int g, int
     }
     // tap groups 1.. hand their partial sums to group 0 through shared memory
     if (grp > 0) {
-        float* pp = part + ((size_t)(grp - 1) * kFgtSeg + j) * (P * P);
+        float* pp = part + ((size_t)(grp - 1) * SEG + j) * (P * P);
 #pragma unroll
         for (int i = 0; i < RB; ++i)
             *reinterpret_cast<float4*>(pp + (b0 + i) * P + c0) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
@@ -191,8 +195,8 @@ __global__ void __launch_bounds__(FgtCfg<P>::THREADS) fgt_pass_kernel(int g, int
     __syncthreads();
     if (grp != 0 || pos >= side) return;
 #pragma unroll
-    for (int q = 0; q < kFgtGroups - 1; ++q) {
-        const float* pp = part + ((size_t)q * kFgtSeg + j) * (P * P);
+    for (int q = 0; q < GROUPS - 1; ++q) {
+        const float* pp = part + ((size_t)q * SEG + j) * (P * P);
 #pragma unroll
         for (int i = 0; i < RB; ++i) {
             const float4 v = *reinterpret_cast<const float4*>(pp + (b0 + i) * P + c0);
@@ -270,7 +274,7 @@ static int fgt_launch(int g, int ncut, double ustep, const float* A, float* Y, f
     const float* htab = nullptr;
     if (cached_table)
         if (int rc = fgt_table(P, ncut, ustep, &htab)) return rc;
-    const dim3 grid((side + kFgtSeg - 1) / kFgtSeg, side);
+    const dim3 grid((side + C::SEG - 1) / C::SEG, side);
     fgt_pass_kernel<P><<<grid, C::THREADS, smem, st>>>(g, ncut, ustep, 0, A, Y, 0, htab);
     FMM_CUDA_TRY(cudaGetLastError());
     // the second pass as the first's programmatic dependent: its set-up overlaps the first pass
