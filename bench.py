@@ -11,7 +11,8 @@ scaled MEs) are built on the device by fmm_p2m / fmm_m2m before timing.
 Prints one JSON line.  `value` is whole-job translations/s with inputs resident
 in HBM; `e2e` is the same metric with a pinned-host -> device copy of the
 step's MEs and a device -> host copy of its LEs inside the timed region
-(pipeline.HostStreamM2L: consecutive steps overlap on three streams).
+(the library's fmm_host_stream_submit, one C call per step with host
+buffers: consecutive steps overlap on its three streams).
 Under torchrun each rank runs an independent replica of the workload (the
 single-tree M2L step has no cross-GPU exchange: replicas only).
 """
@@ -50,8 +51,9 @@ CONFIG = {
     "levels": f"{LEVELS[0]}-{LEVELS[-1]}",
     "l2": "flushed between timed device-resident steps (256 MiB write); in e2e every step's MEs arrive by copy",
     "timing": "device-resident step captured once as a CUDA graph (one kernel) and replayed between "
-              "CUDA events; e2e calls the library from the host every step, MEs in from and LEs out to "
-              "pinned host memory, consecutive steps overlapped on three streams",
+              "CUDA events; e2e makes one C call per step with host buffers (fmm_host_stream_submit), MEs "
+              "in from and LEs out to pinned host memory, consecutive steps overlapped on the library's "
+              "three streams",
     "parallelism": "replicas",
 }
 FP32_LANES_PER_SM = 128
@@ -655,9 +657,10 @@ def run_ours(args):
     tot_ms = fdist.max_over_ranks(sum(step_ms))
     value = fdist.job_rate(NTR * args.steps, sum(step_ms) * 1e-3)
 
-    # --- e2e: host buffers through the library's public API: every step copies its MEs in
-    # from pinned host memory and its LEs back out; consecutive steps overlap on three
-    # streams (pipeline.HostStreamM2L), the way a stream of problems is served ---
+    # --- e2e: host buffers through the library's C entry point fmm_host_stream_submit (wrapped by
+    # pipeline.HostStreamM2L): every step copies its MEs in from pinned host memory and its LEs
+    # back out; consecutive steps overlap on the library's three streams, the way a stream of
+    # problems is served ---
     from paper_1009_3457_gb300 import pipeline
 
     pipe = pipeline.HostStreamM2L(tree, LEVELS[0], LEVELS[-1], P)
@@ -994,9 +997,10 @@ def run_ours(args):
             },
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "matches_device_result": e2e_matches,
-                    "how": "K consecutive steps through pipeline.HostStreamM2L: each copies its MEs from pinned "
-                           "host memory and its LEs back; copies in, translation and copies out of neighbouring "
-                           "steps overlap on three streams; CUDA events around all K steps"},
+                    "how": "K consecutive fmm_host_stream_submit calls (the C ABI's host-buffer entry point, "
+                           "through pipeline.HostStreamM2L): each copies its MEs from pinned host memory and its "
+                           "LEs back; copies in, translation and copies out of neighbouring steps overlap on the "
+                           "library's three streams; CUDA events around all K steps"},
             "gpu_launches": args.steps,
             "graph_replay_matches_direct_call": graph_matches,
             "clocks": clocks,

@@ -173,11 +173,8 @@ int fmm_m2l(const fmm_tree* tree, int32_t level, int32_t p, int32_t prec,
  * levels are independent given their MEs).  M[i], L[i] are the arrays of
  * level lmin + i (host array of device pointers, read during the call).
  * Equivalent to lmax - lmin + 1 calls of fmm_m2l.
- * Host-resident problems: the library takes device pointers only.  The Python
- * package's pipeline.HostStreamM2L overlaps, over a stream of problems, each
- * problem's copy in, this call and the previous problem's copy out on three
- * CUDA streams (it exists only in Python); a C caller does the same with its
- * own streams, pinned buffers, cudaMemcpyAsync and events around this call.
+ * Host-resident problems: fmm_host_stream_* (below) runs this call over a
+ * stream of problems in host memory with the transfers overlapped.
  * Tensor-core precisions: one kernel per call; calls on different streams
  * must not overlap on the GPU (they share the library's per-device flags). */
 int fmm_m2l_levels(const fmm_tree* tree, int32_t lmin, int32_t lmax, int32_t p, int32_t prec,
@@ -198,8 +195,82 @@ int fmm_m2l_adjoint(const fmm_tree* tree, int32_t level, int32_t p, int32_t prec
                     const void* W, void* G, int32_t flags, void* stream);
 
 /* fmm_m2l_adjoint over levels lmin..lmax in one launch (as fmm_m2l_levels). */
+
 int fmm_m2l_adjoint_levels(const fmm_tree* tree, int32_t lmin, int32_t lmax, int32_t p, int32_t prec,
                            const void* const* W, void* const* G, int32_t flags, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Host-resident problems (Sec. 4.1's M2L stage served from host memory):
+ * fmm_m2l_levels over a stream of problems whose MEs and LEs live in host
+ * memory, each problem's copy in, translation and copy out overlapped with
+ * its neighbours'.  The pipeline owns `depth` device buffer sets (MEs and LEs
+ * of every level) and three non-blocking CUDA streams on the device current
+ * at creation: host-to-device copies, translations, device-to-host copies.
+ * Step i uses buffer set i mod depth.  Its MEs are copied in once the
+ * translation that last read that set has finished; its translation waits
+ * for its MEs and for the copy out of the LEs last written to that set; its
+ * LEs are copied out once it has finished.  With depth >= 2 step i's
+ * translation runs while step i+1's MEs arrive and step i-1's LEs leave.
+ *
+ * fmm_host_stream_create
+ *   tree        uniform, periodic or adaptive tree handle; must outlive the
+ *               pipeline.
+ *   lmin, lmax  levels translated per step (as fmm_m2l_levels).
+ *   p, prec     as fmm_m2l_levels (FMM_EUNSUPPORTED where it is).
+ *   depth       device buffer sets, 1..8.
+ *   out         receives the handle.
+ * Allocates 2 * depth * entries * 8 bytes of device memory, entries =
+ * p * sum_{l = lmin..lmax} 4^l complex64 values per direction and step.
+ * Errors: FMM_EINVAL (tree, levels, order, depth, NULL out), FMM_EUNSUPPORTED,
+ * FMM_ENOMEM / FMM_ECUDA (allocation, stream or event creation; nothing is
+ * left allocated).
+ * ------------------------------------------------------------------------- */
+typedef struct fmm_host_stream fmm_host_stream; /* opaque, library-owned */
+int fmm_host_stream_create(const fmm_tree* tree, int32_t lmin, int32_t lmax, int32_t p, int32_t prec,
+                           int32_t depth, fmm_host_stream** out);
+
+/* fmm_host_stream_submit -- enqueue one step and return.
+ *   M_host  host array [lmax - lmin + 1] of HOST pointers: entry i is level
+ *           lmin + i's const complex64 [4^l][p] scaled MEs.
+ *   L_host  the same layout for the scaled LEs (output, overwritten).
+ *   flags   0: one copy per level and direction.
+ *           FMM_HOST_CONTIGUOUS: M_host[0] and L_host[0] each address ONE
+ *           buffer (one allocation) holding all levels back to back, level
+ *           lmin first; one copy per direction; the other entries are not
+ *           read.  (Adjacent addresses alone do not make one buffer: two
+ *           page-locked allocations can be neighbours, and a copy may not
+ *           span them.)
+ * The host buffers must stay valid, M_host unmodified and L_host
+ * unread, until fmm_host_stream_sync() returns.  Page-locked buffers
+ * (cudaHostAlloc, cudaHostRegister) let the copies run asynchronously;
+ * pageable ones are accepted, and their copies then return only after the
+ * data has been staged (no overlap on the host side).  A NULL entry, an
+ * unknown flag, or an M level overlapping an L level is FMM_EINVAL, and
+ * nothing is enqueued. */
+#define FMM_HOST_CONTIGUOUS 8
+int fmm_host_stream_submit(fmm_host_stream* hs, const void* const* M_host, void* const* L_host, int32_t flags);
+
+/* Wait for every submitted step; returns what fmm_sync_status() returns for
+ * the translation stream (device-side checks and timeouts included). */
+int fmm_host_stream_sync(fmm_host_stream* hs);
+
+/* Sizes, progress and streams of a pipeline.  The stream handles
+ * (cudaStream_t) let a caller record events around submitted steps. */
+typedef struct {
+    int64_t entries;       /* complex64 values per step and direction */
+    int64_t bytes_in;      /* host-to-device bytes per step (entries * 8) */
+    int64_t bytes_out;     /* device-to-host bytes per step */
+    int64_t steps;         /* steps submitted so far */
+    int32_t depth;
+    int32_t lmin, lmax, p, prec;
+    void* h2d_stream;
+    void* compute_stream;
+    void* d2h_stream;
+} fmm_host_stream_info_t;
+int fmm_host_stream_info(const fmm_host_stream* hs, fmm_host_stream_info_t* out);
+
+/* Wait for the pipeline's work, then free its buffers, events and streams. */
+void fmm_host_stream_destroy(fmm_host_stream* hs);
 
 /* ---------------------------------------------------------------------------
  * Batched M2L: many independent uniform-tree problems (each with its own

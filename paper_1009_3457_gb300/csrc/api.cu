@@ -811,6 +811,26 @@ int fmm_m2m(int32_t child_level, int32_t p, const void* Mc, void* Mp, int32_t fl
 
 }  // extern "C"
 
+int fmmgb::m2l_levels_check(const char* who, const fmm_tree* tree, int32_t lmin, int32_t lmax, int32_t p,
+                            int32_t prec, const void* const* in, void* const* out)
+{
+    if (in || out) {
+        int rc = levels_common(who, tree, lmin, lmax, p, prec, in, out, 0, 0);
+        if (rc) return rc;
+    } else {  // the arguments alone, before the caller allocates its buffers
+        if (!tree) return fail(FMM_EINVAL, "%s: tree is NULL", who);
+        if (lmin < 0 || lmax > tree->max_level || lmin > lmax)
+            return fail(FMM_EINVAL, "%s: levels %d..%d outside 0..%d", who, lmin, lmax, tree->max_level);
+        if (!valid_p(p)) return fail(FMM_EINVAL, "%s: unsupported p = %d (6, 8, 12, 16, 24)", who, p);
+        if (!m2l_prec_known(prec)) return fail(FMM_EINVAL, "%s: unknown precision %d", who, prec);
+    }
+    if (lmax >= 2 && prec != FMM_FP32 && !m2l_tc_supported(p))
+        return fail(FMM_EUNSUPPORTED, "%s: tensor-core precision %d is provided at p = 16, 24", who, prec);
+    if (lmax >= 2 && prec == FMM_TC_TF32X3 && !m2l_tc_tf32_supported(p))
+        return fail(FMM_EUNSUPPORTED, "%s: FMM_TC_TF32X3 is provided at p = 16", who);
+    return FMM_OK;
+}
+
 int fmmgb::fgt_check_args(const char* who, int g, int n_cut, int p, double sigma, const float* A, const float* C,
                           const float* work, int flags)
 {

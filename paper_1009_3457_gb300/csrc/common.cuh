@@ -178,6 +178,11 @@ size_t m2l_tc_image_bytes(int p, bool tf32);
 int launch_build_tc_image(int p, double s, int variant, bool tf32, void* img, cudaStream_t st);
 int launch_m2l_tc(M2LLaunch& job, int p, const void* img, bool split, bool tf32, cudaStream_t st);
 int get_tc_image(int p, int variant, bool tf32, const void** out);
+// Every check fmm_m2l_levels makes before it launches (flags 0), for a caller
+// that validates its buffers once; with in = out = NULL the arguments other
+// than the buffers (api.cu).
+int m2l_levels_check(const char* who, const fmm_tree* tree, int32_t lmin, int32_t lmax, int32_t p, int32_t prec,
+                     const void* const* in, void* const* out);
 // Per-device flags of the tensor-core M2L, one per tile (zero between
 // launches; grown on demand, zeroed when allocated).
 int tc_flag_workspace(int ntiles, int** flags);

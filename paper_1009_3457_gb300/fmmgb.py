@@ -31,6 +31,7 @@ FMM_CONJ = 2
 FMM_TREE_PERIODIC = 1
 FMM_MAX_LEVEL = 14
 FMM_BATCH_AUTOTUNE = 4
+FMM_HOST_CONTIGUOUS = 8
 
 STATUS_NAMES = {0: "FMM_OK", -1: "FMM_EINVAL", -2: "FMM_ENOMEM", -3: "FMM_ECUDA", -4: "FMM_ETIMEOUT",
                 -5: "FMM_EUNSUPPORTED", -6: "FMM_EDEVICE"}
@@ -73,6 +74,23 @@ class fmm_batch_info_t(ctypes.Structure):
     ]
 
 
+class fmm_host_stream_info_t(ctypes.Structure):
+    _fields_ = [
+        ("entries", ctypes.c_int64),
+        ("bytes_in", ctypes.c_int64),
+        ("bytes_out", ctypes.c_int64),
+        ("steps", ctypes.c_int64),
+        ("depth", ctypes.c_int32),
+        ("lmin", ctypes.c_int32),
+        ("lmax", ctypes.c_int32),
+        ("p", ctypes.c_int32),
+        ("prec", ctypes.c_int32),
+        ("h2d_stream", ctypes.c_void_p),
+        ("compute_stream", ctypes.c_void_p),
+        ("d2h_stream", ctypes.c_void_p),
+    ]
+
+
 _vp = ctypes.c_void_p
 _i32 = ctypes.c_int32
 _i64 = ctypes.c_int64
@@ -99,6 +117,11 @@ SIGNATURES = {
     "fmm_batch_destroy": (None, [_vp, _vp]),
     "fmm_m2l_batched": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(_i32), _i32, ctypes.POINTER(_vp),
                                        ctypes.POINTER(_vp), _i32, _i32, _vp]),
+    "fmm_host_stream_create": (ctypes.c_int, [_vp, _i32, _i32, _i32, _i32, _i32, ctypes.POINTER(_vp)]),
+    "fmm_host_stream_submit": (ctypes.c_int, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i32]),
+    "fmm_host_stream_sync": (ctypes.c_int, [_vp]),
+    "fmm_host_stream_info": (ctypes.c_int, [_vp, ctypes.POINTER(fmm_host_stream_info_t)]),
+    "fmm_host_stream_destroy": (None, [_vp]),
     "fmm_m2m_adjoint": (ctypes.c_int, [_i32, _i32, _vp, _vp, _i32, _vp]),
     "fmm_l2l": (ctypes.c_int, [_i32, _i32, _vp, _vp, _i32, _vp]),
     "fmm_l2l_adjoint": (ctypes.c_int, [_i32, _i32, _vp, _vp, _i32, _vp]),
@@ -320,6 +343,66 @@ def fmm_batch_create(trees, ps, Ms, Ls, prec: int = FMM_FP32, accumulate: bool =
 def fmm_m2l_batched(trees, ps, Ms, Ls, prec: int = FMM_FP32, accumulate: bool = False, stream=None):
     tr, pa, n, mp, lp = _batch_args(trees, ps, Ms, Ls)
     _check(load().fmm_m2l_batched(tr, pa, n, mp, lp, prec, FMM_ACCUMULATE if accumulate else 0, _stream(stream)))
+
+
+def _host_ptr(t) -> int:
+    """Host address of a CPU tensor (or an int address)."""
+    if isinstance(t, int):
+        return t
+    if t.is_cuda:
+        raise FmmError(FMM_EINVAL, "tensor must live in host memory")
+    if not t.is_contiguous():
+        raise FmmError(FMM_EINVAL, "tensor must be contiguous")
+    return t.data_ptr()
+
+
+class HostStream:
+    """Owning wrapper of an ``fmm_host_stream*`` (fmm_host_stream_create / submit / sync / info / destroy)."""
+
+    def __init__(self, handle: int, tree: Tree, nlev: int, entries: int):
+        self.handle = handle
+        self._tree = tree  # the pipeline points into the tree's lists
+        self.nlev = nlev
+        self.entries = entries
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h and _lib is not None:
+            _lib.fmm_host_stream_destroy(h)
+            self.handle = None
+
+    def submit(self, M_host, L_host):
+        """One step.  M_host, L_host: per-level lists of host tensors (levels lmin..lmax; one copy
+        per level), or one complex64 host tensor each holding every level back to back (one copy
+        per direction, FMM_HOST_CONTIGUOUS)."""
+        if isinstance(M_host, list) and isinstance(L_host, list):
+            if len(M_host) != self.nlev or len(L_host) != self.nlev:
+                raise FmmError(FMM_EINVAL, f"one M and one L per level ({self.nlev} levels)")
+            mp = (_vp * self.nlev)(*[_host_ptr(t) for t in M_host])
+            lp = (_vp * self.nlev)(*[_host_ptr(t) for t in L_host])
+            flags = 0
+        else:
+            for t in (M_host, L_host):
+                if isinstance(t, list) or t.numel() != self.entries:
+                    raise FmmError(FMM_EINVAL, f"a flat buffer holds all {self.entries} entries")
+            mp, lp = (_vp * 1)(_host_ptr(M_host)), (_vp * 1)(_host_ptr(L_host))
+            flags = FMM_HOST_CONTIGUOUS
+        _check(load().fmm_host_stream_submit(self.handle, mp, lp, flags))
+
+    def sync(self):
+        _check(load().fmm_host_stream_sync(self.handle))
+
+    def info(self) -> dict:
+        inf = fmm_host_stream_info_t()
+        _check(load().fmm_host_stream_info(self.handle, ctypes.byref(inf)))
+        return {k: getattr(inf, k) for k, _ in fmm_host_stream_info_t._fields_}
+
+
+def fmm_host_stream_create(tree: Tree, lmin: int, lmax: int, p: int, prec: int = FMM_FP32,
+                           depth: int = 2) -> HostStream:
+    h = _vp()
+    _check(load().fmm_host_stream_create(tree.handle, lmin, lmax, p, prec, depth, ctypes.byref(h)))
+    return HostStream(h.value, tree, lmax - lmin + 1, p * sum(4 ** l for l in range(lmin, lmax + 1)))
 
 
 def fmm_p2m(level: int, p: int, xy, c, M, accumulate: bool = False, stream=None):

@@ -78,6 +78,35 @@ def test_m2l_rejects_bad_arguments_before_launch(fmm):
     assert lib.fmm_m2l(tree.handle, 3, 16, 4, 1 << 20, 1 << 24, 0, None) == fmm.FMM_EINVAL
 
 
+def test_host_stream_rejects_bad_arguments_before_any_cuda_call(fmm):
+    """fmm_host_stream_create checks its arguments before it creates a stream or allocates;
+    the other entry points refuse a NULL handle."""
+    import ctypes
+
+    lib = fmm.load()
+    tree = fmm.fmm_build_lists(None, 4)
+    h = ctypes.c_void_p()
+    create = lib.fmm_host_stream_create
+    assert create(tree.handle, 2, 4, 8, 0, 2, None) == fmm.FMM_EINVAL          # NULL out
+    assert create(None, 2, 4, 8, 0, 2, ctypes.byref(h)) == fmm.FMM_EINVAL       # NULL tree
+    assert create(tree.handle, 2, 5, 8, 0, 2, ctypes.byref(h)) == fmm.FMM_EINVAL  # level beyond the tree
+    assert create(tree.handle, 3, 2, 8, 0, 2, ctypes.byref(h)) == fmm.FMM_EINVAL  # lmin > lmax
+    assert create(tree.handle, -1, 2, 8, 0, 2, ctypes.byref(h)) == fmm.FMM_EINVAL
+    assert create(tree.handle, 2, 4, 7, 0, 2, ctypes.byref(h)) == fmm.FMM_EINVAL  # no such order
+    assert create(tree.handle, 2, 4, 8, 9, 2, ctypes.byref(h)) == fmm.FMM_EINVAL  # no such precision
+    for depth in (0, 9):
+        assert create(tree.handle, 2, 4, 8, 0, depth, ctypes.byref(h)) == fmm.FMM_EINVAL
+        assert "depth" in fmm.fmm_last_error()
+    assert create(tree.handle, 2, 4, 8, fmm.FMM_TC_BF16X3, 2, ctypes.byref(h)) == fmm.FMM_EUNSUPPORTED
+    assert create(tree.handle, 2, 4, 24, fmm.FMM_TC_TF32X3, 2, ctypes.byref(h)) == fmm.FMM_EUNSUPPORTED
+    assert h.value is None
+    one = (ctypes.c_void_p * 3)(4096, 8192, 16384)
+    assert lib.fmm_host_stream_submit(None, one, one, 0) == fmm.FMM_EINVAL
+    assert lib.fmm_host_stream_sync(None) == fmm.FMM_EINVAL
+    assert lib.fmm_host_stream_info(None, ctypes.byref(fmm.fmm_host_stream_info_t())) == fmm.FMM_EINVAL
+    lib.fmm_host_stream_destroy(None)
+
+
 def test_p2m_m2m_reject_bad_arguments(fmm):
     lib = fmm.load()
     assert lib.fmm_p2m(-1, 8, 64, 64, 10, 64, 0, None) == fmm.FMM_EINVAL
