@@ -6,10 +6,10 @@
 //
 // Targets and sources are binned by box (fmm_bin_points); a pre-pass copies the
 // sources into box order, each as its position relative to its own box's
-// centre (read off the bits of the FP64 position, kept in FP32) and
-// strength, so a box's sources are one contiguous range and staging adds only
-// the exact offset between box centres -- no FP64 arithmetic per staged
-// source.  Persistent CTAs of 128 threads claim runs of up to 96 targets of
+// centre in box sides (read off the bits of the FP64 position, kept in FP32)
+// and strength, so a box's sources are one contiguous range and staging adds
+// only the exact offset between box centres (-1, 0 or 1) -- no FP64
+// arithmetic per staged source or per claim.  Persistent CTAs of 128 threads claim runs of up to 96 targets of
 // one box from a claim table (a finest-level box holds a few dozen points, so
 // nearly every box is one claim), gather the sources of the 3 x 3
 // neighbourhood into shared memory in batches -- position relative to the
@@ -17,7 +17,8 @@
 // (one to three rows of 32, as many as the run fills, one target per lane and
 // row) against a quarter of every batch; the four partial sums of a target
 // meet in shared memory.  In FP32:
-//   1/(dx + i dy) = (dx - i dy) / r2 with one approximate reciprocal per pair.
+//   1/(dx + i dy) = (dx - i dy) / r2 with one approximate reciprocal per pair,
+// dx, dy in box sides, and the sums scaled by 2^level (exact) at the end.
 // Positions relative to the target box keep |dx|, |dy| <= 1.5 box sides, so
 // FP32 carries the difference of two nearby points to ~2^-24 of a box side.
 // A source at the target's position (the point itself, when targets are the
@@ -33,9 +34,10 @@ constexpr int kP2pWarps = kP2pThreads / 32;     // each takes a quarter of the s
 constexpr int kP2pR = 3;                        // targets per lane (rows of 32 targets per claim)
 constexpr int kP2pRun = 32 * kP2pR;             // targets per claim
 constexpr int kP2pBatch = 1024;                 // sources per shared-memory batch
-// added to every r^2: a source at the target's position (dx = dy = 0) then contributes
-// exactly 0 -- c / 1e-30 is finite for |c| < 3e8 -- and any other pair changes by a
-// relative 1e-30 / r^2 (below FP32 rounding for distances above 1e-11)
+// added to every r^2 (in box sides squared): a source at the target's position
+// (dx = dy = 0) then contributes exactly 0 -- c / 1e-30 is finite for |c| < 3e8 -- and
+// any other pair changes by a relative 1e-30 / r^2 (below FP32 rounding for distances
+// above 1e-11 box sides; positions resolve 2^-31 of a side, 4.7e-10)
 constexpr float kP2pTiny = 1e-30f;
 
 struct P2pArgs {
@@ -57,8 +59,8 @@ struct P2pArgs {
 };
 
 // sources in box order, so that a box's sources are one contiguous range; positions relative to
-// the centre of their own box, read off the bits of the FP64 coordinates and kept in FP32
-// (|x - c| <= half a box side)
+// the centre of their own box in box sides, read off the bits of the FP64 coordinates and kept
+// in FP32 (|x - c| <= 1/2)
 __global__ void p2p_sort_kernel(int level, const double* __restrict__ xy, const double* __restrict__ c,
                                 const int* __restrict__ perm, int n, float4* __restrict__ out, int* err)
 {
@@ -74,17 +76,15 @@ __global__ void p2p_sort_kernel(int level, const double* __restrict__ xy, const 
     const float cf = (float)__ldg(c + i);
     long long X, Y;
     if (grid_fixed31(x, level, X) && grid_fixed31(y, level, Y)) {
-        // offset from the box centre in box sides, scaled by the side 2^-level (exact)
-        const float hs = __int_as_float((127 - level) << 23);
-        out[k] = make_float4(cell_offset31(X) * hs, cell_offset31(Y) * hs, cf, 0.f);
+        out[k] = make_float4(cell_offset31(X), cell_offset31(Y), cf, 0.f);  // offset in box sides
         return;
     }
-    // outside the unit square: the clamped box, offset in FP64
+    // outside the unit square: the clamped box, offset in FP64 (x 2^level is exact)
     const int side = 1 << level;
     const double px = x * side, py = y * side;
     const int ix = !(px >= 0.0) ? 0 : (px >= side ? side - 1 : (int)px);
     const int iy = !(py >= 0.0) ? 0 : (py >= side ? side - 1 : (int)py);
-    out[k] = make_float4((float)(x - (ix + 0.5) / side), (float)(y - (iy + 0.5) / side), cf, 0.f);
+    out[k] = make_float4((float)(px - (ix + 0.5)), (float)(py - (iy + 0.5)), cf, 0.f);
 }
 
 __device__ __forceinline__ float rcp_approx(float x)
@@ -203,16 +203,14 @@ __global__ void p2p_claim_table_kernel(int nbox, const int* __restrict__ claims,
 
 __global__ void __launch_bounds__(kP2pThreads) fmm_p2p_kernel(P2pArgs a)
 {
-    __shared__ float4 s_src[kP2pBatch];  // x - cx, y - cy, c
+    __shared__ float4 s_src[kP2pBatch];  // position relative to the target box's centre (box sides), c
     __shared__ int4 s_claim;
     __shared__ int s_box[9], s_cnt[9];  // first sorted source and source count of each neighbour box
-    __shared__ float s_ox[9], s_oy[9];  // centre of each neighbour box minus the target box's
+    __shared__ float s_ox[9], s_oy[9];  // centre of each neighbour box minus the target box's (box sides)
     __shared__ float2 s_part[kP2pWarps - 1][kP2pRun];  // partial sums of warps 1..3
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int side = 1 << a.level;
-    const double inv_side = 1.0 / side;
-    const float hs = __int_as_float((127 - a.level) << 23);  // the box side 2^-level
     const int total = min(__ldg(a.claims + (side * side)), a.ntab);
     // thread 0 fetches the index of the CTA's next claim one claim ahead
     int knext = tid == 0 ? atomicAdd(a.cursor, 1) : 0;
@@ -229,11 +227,10 @@ __global__ void __launch_bounds__(kP2pThreads) fmm_p2p_kernel(P2pArgs a)
         if (first < 0) break;
         const int nrow = (end - first + 31) >> 5;  // occupied rows of 32 targets (0..kP2pR)
         const int tx = box & (side - 1), ty = box >> a.level;
-        const double cx = (tx + 0.5) * inv_side, cy = (ty + 0.5) * inv_side;
         if (tid < 9) {  // the 3 x 3 neighbourhood, one box per thread
             const int sx = tx + tid % 3 - 1, sy = ty + tid / 3 - 1;
-            s_ox[tid] = (float)((tid % 3 - 1) * inv_side);  // exact: a power of two or zero
-            s_oy[tid] = (float)((tid / 3 - 1) * inv_side);
+            s_ox[tid] = (float)(tid % 3 - 1);
+            s_oy[tid] = (float)(tid / 3 - 1);
             int b0 = -1, m = 0;
             if (sx >= 0 && sy >= 0 && sx < side && sy < side) {
                 const int b = sy * side + sx;
@@ -263,11 +260,11 @@ __global__ void __launch_bounds__(kP2pThreads) fmm_p2p_kernel(P2pArgs a)
                     long long X, Y;
                     if (grid_fixed31(x, a.level, X) && grid_fixed31(y, a.level, Y) && (int)(X >> 31) == tx &&
                         (int)(Y >> 31) == ty) {
-                        zx[r] = cell_offset31(X) * hs;  // in the claimed box: no FP64 arithmetic
-                        zy[r] = cell_offset31(Y) * hs;
-                    } else {
-                        zx[r] = (float)(x - cx);
-                        zy[r] = (float)(y - cy);
+                        zx[r] = cell_offset31(X);  // in the claimed box: no FP64 arithmetic
+                        zy[r] = cell_offset31(Y);
+                    } else {  // outside it (coordinates outside the unit square): FP64, x 2^level exact
+                        zx[r] = (float)(x * side - (tx + 0.5));
+                        zy[r] = (float)(y * side - (ty + 0.5));
                     }
                 } else if (warp == 0) {
                     atomicOr(a.err, DEV_ERR_CHECK);
@@ -326,6 +323,8 @@ __global__ void __launch_bounds__(kP2pThreads) fmm_p2p_kernel(P2pArgs a)
                 o.x += s_part[q][r * 32 + lane].x;
                 o.y += s_part[q][r * 32 + lane].y;
             }
+            o.x *= (float)side;  // 1/(z - y) = 2^level / ((z - y) in box sides): exact scaling
+            o.y *= (float)side;
             if (a.accumulate) {
                 const float2 old = a.phi[tj[r]];
                 o.x += old.x;
