@@ -828,7 +828,8 @@ def run_ours(args):
         rows["fmm_potential_level8_p16"] = {
             "ms": ms_fmm, "points": int(CFG["n"]), "points_per_s": CFG["n"] / (ms_fmm * 1e-3),
             "m2l_translations": NTR, "near_pairs": pairs,
-            "note": "P2M, M2M, M2L (levels 2-8, one launch), L2L, L2P, P2P: the potential at all 2^22 points"}
+            "note": "P2M, M2M, M2L (levels 2-8, one launch), L2L, L2P, P2P: the potential at all 2^22 points; "
+                    "the near field on a second stream beside the far field up to L2L (FMM_P2P_SHARE_SM)"}
         del pot, tree8, xyd, cd
 
         # adaptive tree: 2^20 Gaussian-mixture points, q = 64, levels 2..9, p = 16: V-list M2L,

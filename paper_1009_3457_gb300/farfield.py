@@ -102,8 +102,12 @@ class FmmPotential:
 
         phi(z) = sum_i c_i / (z - y_i)   (sources at exactly z skipped)
 
-    Buffers are allocated once; ``__call__`` enqueues the whole evaluation on the
-    current stream (capturable as a CUDA graph after a first call)."""
+    The near field and the far field up to L2L are independent: the near field runs on
+    a second stream (writing phi, with FMM_P2P_SHARE_SM so that the far-field kernels
+    find room on every SM), the far field on the current one, and L2P adds into phi
+    once both are done.  Buffers are allocated once; ``__call__`` enqueues the whole
+    evaluation, ending on the current stream (capturable as a CUDA graph after a
+    first call)."""
 
     def __init__(self, tree, p: int, xy: torch.Tensor, c: torch.Tensor, z: torch.Tensor, prec: int = 0):
         if tree.adaptive or tree.periodic or tree.max_level < 2:
@@ -127,16 +131,20 @@ class FmmPotential:
         self.sperm, self.sstart = bins(self.xy)
         self.tperm, self.tstart = bins(self.z)
         self.phi = torch.empty(self.z.shape[0], dtype=torch.complex64, device=dev)
+        self.side = torch.cuda.Stream(device=dev)
 
     def __call__(self) -> torch.Tensor:
         p, L = self.p, self.L
+        cur = torch.cuda.current_stream(self.phi.device)
+        self.side.wait_stream(cur)  # the inputs and phi are the current stream's until here
+        fmmgb.fmm_p2p(L, self.xy, self.c, self.sperm, self.sstart, self.z, self.tperm, self.tstart, self.phi,
+                      stream=self.side, share_sm=True)
         fmmgb.fmm_p2m_binned(L, p, self.xy, self.c, self.sperm, self.sstart, self.Ms[-1])
         for i in range(len(self.levels) - 1, 0, -1):
             fmmgb.fmm_m2m(self.levels[i], p, self.Ms[i], self.Ms[i - 1])
         fmmgb.fmm_m2l_levels(self.tree, 2, p, self.Ms, self.Ls, prec=self.prec)
         for i in range(1, len(self.levels)):
             fmmgb.fmm_l2l(self.levels[i], p, self.Ls[i - 1], self.Ls[i], accumulate=True)
-        fmmgb.fmm_l2p_binned(L, p, self.z, self.tperm, self.tstart, self.Ls[-1], self.phi)
-        fmmgb.fmm_p2p(L, self.xy, self.c, self.sperm, self.sstart, self.z, self.tperm, self.tstart, self.phi,
-                      accumulate=True)
+        cur.wait_stream(self.side)
+        fmmgb.fmm_l2p_binned(L, p, self.z, self.tperm, self.tstart, self.Ls[-1], self.phi, accumulate=True)
         return self.phi

@@ -32,6 +32,7 @@ FMM_TREE_PERIODIC = 1
 FMM_MAX_LEVEL = 14
 FMM_BATCH_AUTOTUNE = 4
 FMM_HOST_CONTIGUOUS = 8
+FMM_P2P_SHARE_SM = 16
 
 STATUS_NAMES = {0: "FMM_OK", -1: "FMM_EINVAL", -2: "FMM_ENOMEM", -3: "FMM_ECUDA", -4: "FMM_ETIMEOUT",
                 -5: "FMM_EUNSUPPORTED", -6: "FMM_EDEVICE"}
@@ -530,15 +531,16 @@ def fmm_bin_points(level: int, y, perm, box_start, work, stream=None):
 
 
 def fmm_p2p(level: int, xy, c, src_perm, src_start, z, tgt_perm, tgt_start, phi, accumulate: bool = False,
-            stream=None):
+            stream=None, share_sm: bool = False):
     """Near field at the finest level of a uniform tree: phi (complex64 [nz]) at the targets z
     (float64 [nz, 2]) from the sources xy, c in the own and adjacent boxes; both sets binned
-    by fmm_bin_points at `level`."""
+    by fmm_bin_points at `level`.  share_sm: leave room on every SM for kernels of other
+    streams (FMM_P2P_SHARE_SM)."""
     n = 0 if c is None else c.numel()
     nz = 0 if z is None else z.shape[0]
+    flags = (FMM_ACCUMULATE if accumulate else 0) | (FMM_P2P_SHARE_SM if share_sm else 0)
     _check(load().fmm_p2p(level, _ptr(xy), _ptr(c), n, _ptr(src_perm), _ptr(src_start), _ptr(z), nz,
-                          _ptr(tgt_perm), _ptr(tgt_start), _ptr(phi), FMM_ACCUMULATE if accumulate else 0,
-                          _stream(stream)))
+                          _ptr(tgt_perm), _ptr(tgt_start), _ptr(phi), flags, _stream(stream)))
 
 
 def fgt_p2h_binned(grid_log2: int, p: int, sigma: float, x, q, perm, A, accumulate: bool = False, stream=None):

@@ -297,6 +297,7 @@ def test_p2p_rejects_bad_arguments(fmm):
     assert lib.fmm_p2p(3, 64, 128, 10, 256, None, 1024, 10, 2048, 4096, 8192, 0, None) == fmm.FMM_EINVAL  # src_start
     assert lib.fmm_p2p(3, 64, 128, 10, 256, 512, 1028, 10, 2048, 4096, 8192, 0, None) == fmm.FMM_EINVAL  # z misaligned
     assert lib.fmm_p2p(3, 64, 128, 10, 256, 512, 1024, 10, 2048, 4096, 8192, 8, None) == fmm.FMM_EINVAL  # flags
+    assert lib.fmm_p2p(3, 64, 128, 10, 256, 512, 1024, 10, 2048, 4096, 8192, 32, None) == fmm.FMM_EINVAL
     assert lib.fmm_bin_points(11, 64, 10, 128, 256, 512, None) == fmm.FMM_EINVAL
     # fmm_l2p_binned(level, p, z, n, perm, box_start, L, phi, flags, stream)
     assert lib.fmm_l2p_binned(11, 8, 64, 10, 128, 256, 512, 1024, 0, None) == fmm.FMM_EINVAL   # level

@@ -71,6 +71,30 @@ def test_p2p_matches_oracle(fmm, orc, level, bar, nsrc):
     _check(_p2p(fmm, level, xy, c, z), orc.p2p_uniform(level, xy, c, z), l2=bar, worst=max(1e-4, 2 * bar))
 
 
+@pytest.mark.parametrize("level,nsrc", [(3, 4000), (8, 262144)])
+def test_p2p_shared_sm_grid_gives_the_same_result(fmm, orc, level, nsrc):
+    """FMM_P2P_SHARE_SM only shrinks the persistent grid: on the same binning (the binning's
+    order within a box is not fixed) every claim is summed the same way by whichever CTA
+    takes it, so the result is bit-identical, and on the oracle's bar."""
+    import torch
+
+    rng = np.random.default_rng(60 + level)
+    xy, c = workloads.uniform_particles(nsrc, rng)
+    z = rng.random(3000) + 1j * rng.random(3000)
+    xyd, cd = torch.from_numpy(xy).cuda(), torch.from_numpy(c).cuda()
+    zd = torch.from_numpy(np.stack([z.real, z.imag], 1).copy()).cuda()
+    sp, ss = _bins(fmm, level, xyd)
+    tp, ts = _bins(fmm, level, zd)
+    out = []
+    for share in (False, True):
+        phi = torch.zeros(len(z), dtype=torch.complex64, device="cuda")
+        fmm.fmm_p2p(level, xyd, cd, sp, ss, zd, tp, ts, phi, share_sm=share)
+        fmm.fmm_sync_status()
+        out.append(phi.cpu())
+    assert torch.equal(out[0], out[1])
+    _check(out[1].numpy().astype(np.complex128), orc.p2p_uniform(level, xy, c, z))
+
+
 def test_p2p_points_on_box_boundaries_and_outside(fmm, orc):
     """Sources on the level's box boundaries, targets one ulp either side of them, and
     points at 1.0 and just outside the unit square (clamped to the edge boxes)."""
