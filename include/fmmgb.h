@@ -251,7 +251,9 @@ int fmm_host_stream_create(const fmm_tree* tree, int32_t lmin, int32_t lmax, int
 int fmm_host_stream_submit(fmm_host_stream* hs, const void* const* M_host, void* const* L_host, int32_t flags);
 
 /* Wait for every submitted step; returns what fmm_sync_status() returns for
- * the translation stream (device-side checks and timeouts included). */
+ * the translation stream (device-side checks and timeouts included).
+ * A pipeline is used by one host thread at a time (its calls are not
+ * serialised against each other). */
 int fmm_host_stream_sync(fmm_host_stream* hs);
 
 /* Sizes, progress and streams of a pipeline.  The stream handles
