@@ -30,11 +30,16 @@ def _recursive_tree(xy, q, max_level):
     return out
 
 
-@pytest.fixture(scope="module")
-def small(orc):
+def small_case(orc):
+    """3000 mixture points, q = 20, depth <= 7, the tree built by `orc`."""
     xy, c = workloads.gmm_particles(3000, np.random.default_rng(17), ncomp=5)
     tree = orc.adaptive_tree(xy, 20, 7)
     return xy, c, tree
+
+
+@pytest.fixture(scope="module")
+def small(orc):
+    return small_case(orc)
 
 
 def test_tree_matches_recursive_builder(orc, small):

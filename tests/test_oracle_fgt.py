@@ -33,14 +33,19 @@ def _cluster(rng, centre, half, n):
     return x, q
 
 
-@pytest.fixture(scope="module")
-def fgt_setup():
+def fgt_case():
+    """200 sources in one box of the sigma = 0.1 grid, and the generator for the targets."""
     sigma = 0.1
     side = 2.0 ** -4  # box side for sigma = 0.1 (g = 4): side / (sqrt(2) sigma) = 0.442
     rng = np.random.default_rng(21)
     sB = np.array([0.40625, 0.53125])
     x, q = _cluster(rng, sB, side / 2, 200)
     return sigma, side, sB, x, q, rng
+
+
+@pytest.fixture(scope="module")
+def fgt_setup():
+    return fgt_case()
 
 
 def test_hermite_expansion_converges_to_direct(orc, fgt_setup):

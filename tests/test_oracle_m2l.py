@@ -253,11 +253,14 @@ def test_m2m_then_m2l_equals_parent_p2m(orc):
     np.testing.assert_allclose(L2b, L2, rtol=1e-10, atol=1e-10 * np.abs(L2).max())
 
 
+def small_tree_case():
+    rng = np.random.default_rng(11)
+    return workloads.uniform_particles(600, rng)
+
+
 @pytest.fixture(scope="module")
 def small_tree(orc):
-    rng = np.random.default_rng(11)
-    xy, c = workloads.uniform_particles(600, rng)
-    return xy, c
+    return small_tree_case()
 
 
 def _far_field_error(orc, xy, c, level, p, tx, ty, z):

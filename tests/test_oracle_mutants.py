@@ -21,6 +21,7 @@ import numpy as np
 import pytest
 
 import oracle
+import test_oracle_adaptive as ta
 import test_oracle_fgt as tf
 import test_oracle_m2l as tm
 import test_oracle_nearfield as tn
@@ -56,6 +57,28 @@ PINS = {
     "near": [
         lambda o: tn.test_near_field_skips_only_the_coincident_source(o, _pts()),
         lambda o: tn.test_near_field_is_the_sum_over_adjacent_boxes(o, _pts(), 3),
+    ],
+    "adjoint": [
+        lambda o: tm.test_adjoint_dot_product(o, False),
+        lambda o: tm.test_operator_transpose_identity(o),
+    ],
+    "farfield": [
+        lambda o: tm.test_m2p_centred_source_is_exact(o),
+        lambda o: tm.test_m2p_single_term_powers(o),
+        lambda o: tm.test_m2p_equals_l2p_of_m2l_in_the_limit(o),
+        lambda o: tm.test_far_field_potential_converges_geometrically(o, tm.small_tree_case()),
+        lambda o: tn.test_whole_fmm_converges_to_the_direct_sum(o, _pts(), 3),
+    ],
+    "adaptive": [
+        lambda o: ta.test_tree_matches_recursive_builder(o, ta.small_case(o)),
+        lambda o: ta.test_tree_invariants(o, ta.small_case(o)),
+        lambda o: ta.test_vlists_brute_force_and_symmetric(o, ta.small_case(o)),
+    ],
+    "fgt_expansions": [
+        lambda o: tf.test_hermite_expansion_converges_to_direct(o, tf.fgt_case()),
+        lambda o: tf.test_taylor_expansion_converges_to_direct(o, tf.fgt_case()),
+        lambda o: tf.test_full_fgt_grid_pipeline_matches_direct(o),
+        lambda o: tf.test_hermite_grid_eval_sums_exactly_the_neighbourhood(o, 2),
     ],
 }
 
@@ -103,6 +126,36 @@ MUTANTS = [
     ("near_field_self_not_skipped", "near",
      "if (xy[2 * i] == z[2 * j] && xy[2 * i + 1] == z[2 * j + 1]) continue;",
      ";"),
+    ("adjoint_not_transposed", "adjoint",
+     "cplx anks = a[2 * (nn * p + k)] + I * a[2 * (nn * p + k) + 1];",
+     "cplx anks = a[2 * (k * p + nn)] + I * a[2 * (k * p + nn) + 1];"),
+    ("l2l_power_index", "farfield",
+     "for (int n = j; n < p; ++n) s += binom(n, j) * zp[n - j] * (lp[2 * n] + I * lp[2 * n + 1]);",
+     "for (int n = j; n < p; ++n) s += binom(n, j) * zp[j] * (lp[2 * n] + I * lp[2 * n + 1]);"),
+    ("l2p_power_off_by_one", "farfield",
+     "cplx s = 0.0, pw = 1.0;",
+     "cplx s = 0.0, pw = w;"),
+    ("m2p_power_off_by_one", "farfield",
+     "cplx s = 0.0, pw = 1.0 / w;",
+     "cplx s = 0.0, pw = 1.0;"),
+    ("adaptive_split_at_q", "adaptive",
+     "int parent_split = exists[level_offset(l - 1) + pb] && cnt_parent[pb] > q;",
+     "int parent_split = exists[level_offset(l - 1) + pb] && cnt_parent[pb] >= q;"),
+    ("vlist_separation_too_strict", "adaptive",
+     "if ((adx > ady ? adx : ady) <= 1) continue; /* adjacent: U-list, near field */",
+     "if ((adx > ady ? adx : ady) <= 2) continue; /* adjacent: U-list, near field */"),
+    ("p2h_factorials_dropped", "fgt_expansions",
+     "A[a1 * p + a2] += q[j] * w1[a1] * w2[a2] / (f[a1] * f[a2]);",
+     "A[a1 * p + a2] += q[j] * w1[a1] * w2[a2];"),
+    ("taylor_power_off_by_one", "fgt_expansions",
+     "s += B[b1 * p + b2] * pow(t1, b1) * pow(t2, b2);",
+     "s += B[b1 * p + b2] * pow(t1, b1 + 1) * pow(t2, b2);"),
+    ("p2h_grid_box_corner_not_centre", "fgt_expansions",
+     "double t1 = (x[2 * j] - ((double)ix + 0.5) * side) / sc;",
+     "double t1 = (x[2 * j] - ((double)ix) * side) / sc;"),
+    ("hermite_grid_neighbourhood_short", "fgt_expansions",
+     "double acc = 0.0;\n        for (int sy = ty - ncut; sy <= ty + ncut; ++sy) {",
+     "double acc = 0.0;\n        for (int sy = ty - ncut; sy < ty + ncut; ++sy) {"),
 ]
 
 
