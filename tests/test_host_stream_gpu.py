@@ -56,6 +56,8 @@ def _direct(fmm, tree, lmin, p, prec, Ms):
     (3, "FMM_FP32", 12, 1e-5),
     (2, "FMM_TC_BF16X3", 16, 1e-4),
     (2, "FMM_TC_TF32X3", 16, 1e-5),
+    (2, "FMM_FP32", 24, 1e-5),
+    (4, "FMM_TC_BF16X3", 24, 1e-4),
 ])
 def test_steps_match_direct_calls_and_oracle(fmm, orc, depth, prec_name, p, tol):
     """Seven steps, more than the buffer sets, rotating between pageable per-level tensors,
