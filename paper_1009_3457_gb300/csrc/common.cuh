@@ -65,6 +65,30 @@ __device__ __forceinline__ float cell_offset31(long long X)
     return (float)((int)(X & 0x7FFFFFFFll) - (1 << 30)) * 4.656612873077393e-10f;  // 2^-31
 }
 
+// Binomials C(n, k), n, k < 64, as a table in device memory built at compile time
+// (Pascal's rule in FP64, exact up to 2^53, then rounded to FP32: exact while
+// C(n, k) < 2^24, every n < 25), row n at kBinom.v[64 n], zero for k > n.  The
+// M2M / L2L kernels and their adjoints read it instead of a per-step recurrence
+// with an FP32 division.
+struct BinomTable64 {
+    float v[64 * 64];
+};
+constexpr BinomTable64 make_binom_table64()
+{
+    BinomTable64 t{};
+    double row[64] = {1.0};
+    for (int n = 0; n < 64; ++n) {
+        if (n > 0)
+            for (int k = n; k > 0; --k) row[k] += row[k - 1];
+        for (int k = 0; k < 64; ++k) t.v[n * 64 + k] = k <= n ? (float)row[k] : 0.f;
+    }
+    return t;
+}
+__device__ constexpr BinomTable64 kBinom = make_binom_table64();
+
+// 2^-k as an FP32 bit pattern (0 <= k <= 126).
+__device__ __forceinline__ float pow2_neg(int k) { return __int_as_float((127 - k) << 23); }
+
 // Number of SMs of the current device (cached).
 int device_sm_count(int* out);
 

@@ -11,7 +11,8 @@
 
 namespace fmmgb {
 
-// One thread per (child box, j): Lc[child][j] (+)= sum_n T_c[j][n] Lp[parent][n].
+// One thread per (child box, j): Lc[child][j] (+)= sum_n T_c[j][n] Lp[parent][n]; the
+// binomials from the compile-time table.
 __global__ void l2l_kernel(int child_level, int p, const float2* __restrict__ Lp, float2* __restrict__ Lc,
                            int accumulate)
 {
@@ -24,18 +25,18 @@ __global__ void l2l_kernel(int child_level, int p, const float2* __restrict__ Lp
     const float ur = (ix & 1) ? 0.25f : -0.25f, ui = (iy & 1) ? 0.25f : -0.25f;
     const float2* lp = Lp + ((size_t)(iy >> 1) * ps + (ix >> 1)) * p;
     // n from j upward: C(n, j) u^(n-j)
-    float sr = 0.f, si = 0.f, binom = 1.f, pr = 1.f, pim = 0.f;
+    float sr = 0.f, si = 0.f, pr = 1.f, pim = 0.f;
     for (int n = j; n < p; ++n) {
         const float2 v = lp[n];
+        const float binom = kBinom.v[n * 64 + j];
         const float tr = pr * v.x - pim * v.y, ti = pr * v.y + pim * v.x;
         sr = fmaf(binom, tr, sr);
         si = fmaf(binom, ti, si);
-        binom = binom * (float)(n + 1) / (float)(n + 1 - j);  // C(n+1, j) = C(n, j) (n+1) / (n+1-j)
         const float nr = pr * ur - pim * ui;
         pim = pr * ui + pim * ur;
         pr = nr;
     }
-    const float sc = ldexpf(1.f, -(j + 1));
+    const float sc = pow2_neg(j + 1);
     float2* out = Lc + (size_t)b * p + j;
     float2 o = make_float2(sc * sr, sc * si);
     if (accumulate) {
@@ -62,15 +63,15 @@ __global__ void l2l_adjoint_kernel(int child_level, int p, const float2* __restr
             const float ur = cx ? 0.25f : -0.25f, ui = cy ? 0.25f : -0.25f;
             const float2* wc = Wc + ((size_t)(2 * py + cy) * side + (2 * px + cx)) * p;
             // j from n down to 0: entry C(n, j) u^(n-j) 2^-(j+1), conjugated
-            float binom = 1.f, pr = 1.f, pim = 0.f;  // C(n, n), u^0
+            const float* brow = kBinom.v + n * 64;
+            float pr = 1.f, pim = 0.f;  // u^(n-j)
             for (int j = n; j >= 0; --j) {
-                const float sc = binom * ldexpf(1.f, -(j + 1));
+                const float sc = brow[j] * pow2_neg(j + 1);
                 const float2 w = wc[j];
                 // conj(u^(n-j)) * w
                 const float tr = pr * w.x + pim * w.y, ti = pr * w.y - pim * w.x;
                 sr = fmaf(sc, tr, sr);
                 si = fmaf(sc, ti, si);
-                if (j > 0) binom = binom * (float)j / (float)(n - j + 1);  // C(n, j-1) = C(n, j) j / (n-j+1)
                 const float nr = pr * ur - pim * ui;
                 pim = pr * ui + pim * ur;
                 pr = nr;
@@ -169,36 +170,52 @@ __global__ void l2p_adjoint_kernel(int p, int64_t n, const double* __restrict__ 
 }
 
 // P2M adjoint in the positions: grad_i (+)= sum_k G[b][k] conj(c_i k d^(k-1) / r),
-// returned as (d/dx, d/dy) = (Re, Im) of that sum.
+// returned as (d/dx, d/dy) = (Re, Im) of that sum.  d (in box sides, |d| <= 1/sqrt 2)
+// is read off the bits of the FP64 coordinates (points outside the unit square: the
+// clamped box, in FP64) and the series runs in FP32, like the FP32 G it reads.
 __global__ void p2m_adjoint_kernel(int level, int p, const double* __restrict__ xy, const double* __restrict__ c,
                                    int64_t n, const float2* __restrict__ G, double* __restrict__ grad, int accumulate)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int side = 1 << level;
-    const double x = xy[2 * i] * side, y = xy[2 * i + 1] * side;
-    int ix = (int)floor(x), iy = (int)floor(y);
-    ix = ix < 0 ? 0 : (ix > side - 1 ? side - 1 : ix);
-    iy = iy < 0 ? 0 : (iy > side - 1 ? side - 1 : iy);
-    const double dr = x - (ix + 0.5), di = -(y - (iy + 0.5));  // conj(d)
+    const double x = xy[2 * i], y = xy[2 * i + 1];
+    int ix, iy;
+    float dr, di;  // conj(d)
+    long long X, Y;
+    if (grid_fixed31(x, level, X) && grid_fixed31(y, level, Y)) {
+        ix = (int)(X >> 31);
+        iy = (int)(Y >> 31);
+        dr = cell_offset31(X);
+        di = -cell_offset31(Y);
+    } else {
+        const double xs = x * side, ys = y * side;
+        ix = (int)floor(xs);
+        iy = (int)floor(ys);
+        ix = ix < 0 ? 0 : (ix > side - 1 ? side - 1 : ix);
+        iy = iy < 0 ? 0 : (iy > side - 1 ? side - 1 : iy);
+        dr = (float)(xs - (ix + 0.5));
+        di = (float)-(ys - (iy + 0.5));
+    }
     const float2* gb = G + ((size_t)iy * side + ix) * p;
     // sum_k G_k k conj(d)^(k-1)
-    double sr = 0.0, si = 0.0, pr = 1.0, pi = 0.0;
+    float sr = 0.f, si = 0.f, pr = 1.f, pi = 0.f;
     for (int k = 1; k < p; ++k) {
-        const double gr = (double)gb[k].x * k, gi = (double)gb[k].y * k;
-        sr += gr * pr - gi * pi;
-        si += gr * pi + gi * pr;
-        const double t = pr * dr - pi * di;
+        const float2 g = gb[k];
+        const float gr = g.x * (float)k, gi = g.y * (float)k;
+        sr = fmaf(gr, pr, fmaf(-gi, pi, sr));
+        si = fmaf(gr, pi, fmaf(gi, pr, si));
+        const float t = pr * dr - pi * di;
         pi = pr * di + pi * dr;
         pr = t;
     }
     const double f = c[i] * side;  // c_i / r
     if (accumulate) {
-        grad[2 * i] += f * sr;
-        grad[2 * i + 1] += f * si;
+        grad[2 * i] += f * (double)sr;
+        grad[2 * i + 1] += f * (double)si;
     } else {
-        grad[2 * i] = f * sr;
-        grad[2 * i + 1] = f * si;
+        grad[2 * i] = f * (double)sr;
+        grad[2 * i + 1] = f * (double)si;
     }
 }
 

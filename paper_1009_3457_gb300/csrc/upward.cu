@@ -123,7 +123,8 @@ int launch_p2m_binned(int level, int p, const double* xy, const double* c, int n
 
 // Scaled M2M: parent box side R = 2r, child offset z = (x_c - x_P)/R = (+-1/4, +-1/4):
 //   M~P_j = sum_{k<=j} C(j,k) z^(j-k) 2^-k M~c_k, summed over the 4 children.
-// The entries (binomials, powers of (+-1 +- i)/4, powers of 2) are exact in FP32.
+// The entries (binomials, powers of (+-1 +- i)/4, powers of 2) are exact in FP32;
+// the binomials come from the compile-time table.
 __global__ void m2m_kernel(int child_level, int p, const float2* __restrict__ Mc, float2* __restrict__ Mp,
                            int accumulate)
 {
@@ -140,14 +141,13 @@ __global__ void m2m_kernel(int child_level, int p, const float2* __restrict__ Mc
             const float zr = cxx ? 0.25f : -0.25f, zi = cyy ? 0.25f : -0.25f;
             const float2* mc = Mc + ((size_t)(2 * py + cyy) * nc + (2 * px + cxx)) * p;
             // k from j down to 0: term C(j,k) z^(j-k) 2^-k m_k
-            float binom = 1.f;          // C(j, k) for k = j
+            const float* brow = kBinom.v + j * 64;
             float zpr = 1.f, zpi = 0.f;  // z^(j-k)
             for (int k = j; k >= 0; --k) {
-                const float sc = binom * ldexpf(1.f, -k);
+                const float sc = brow[k] * pow2_neg(k);
                 const float2 m = mc[k];
                 sr = fmaf(sc, zpr * m.x - zpi * m.y, sr);
                 si = fmaf(sc, zpr * m.y + zpi * m.x, si);
-                if (k > 0) binom = binom * (float)k / (float)(j - k + 1);  // C(j, k-1)
                 const float nr = zpr * zr - zpi * zi;
                 zpi = zpr * zi + zpi * zr;
                 zpr = nr;
@@ -163,7 +163,8 @@ __global__ void m2m_kernel(int child_level, int p, const float2* __restrict__ Mc
 }
 
 // Conjugate transpose of M2M: one thread per (child box, k):
-//   Wc[child][k] (+)= sum_{j>=k} conj(C(j,k) z^(j-k) 2^-k) WP[parent][j].
+//   Wc[child][k] (+)= sum_{j>=k} conj(C(j,k) z^(j-k) 2^-k) WP[parent][j]
+// (binomials from the compile-time table).
 __global__ void m2m_adjoint_kernel(int child_level, int p, const float2* __restrict__ Wp, float2* __restrict__ Wc,
                                    int accumulate)
 {
@@ -175,18 +176,18 @@ __global__ void m2m_adjoint_kernel(int child_level, int p, const float2* __restr
     const int ix = (int)(b % side), iy = (int)(b / side);
     const float zr = (ix & 1) ? 0.25f : -0.25f, zi = (iy & 1) ? 0.25f : -0.25f;
     const float2* wp = Wp + ((size_t)(iy >> 1) * np + (ix >> 1)) * p;
-    float sr = 0.f, si = 0.f, binom = 1.f, pr = 1.f, pim = 0.f;  // C(j, k) for j = k; z^(j-k)
+    float sr = 0.f, si = 0.f, pr = 1.f, pim = 0.f;  // z^(j-k)
     for (int j = k; j < p; ++j) {
         const float2 w = wp[j];
+        const float binom = kBinom.v[j * 64 + k];  // C(j, k)
         // conj(z^(j-k)) w
         sr = fmaf(binom, pr * w.x + pim * w.y, sr);
         si = fmaf(binom, pr * w.y - pim * w.x, si);
-        binom = binom * (float)(j + 1) / (float)(j + 1 - k);  // C(j+1, k)
         const float nr = pr * zr - pim * zi;
         pim = pr * zi + pim * zr;
         pr = nr;
     }
-    const float sc = ldexpf(1.f, -k);
+    const float sc = pow2_neg(k);
     float2* out = Wc + (size_t)b * p + k;
     float2 o = make_float2(sc * sr, sc * si);
     if (accumulate) {
