@@ -7,25 +7,40 @@
 
 namespace fmmgb {
 
-// M~_b[k] += c_i w^k,  w = (y_i - x_b) / r_l  (|w| <= 1/sqrt 2)
+// M~_b[k] += c_i w^k,  w = (y_i - x_b) / r_l  (|w| <= 1/sqrt 2): w read off the bits of
+// the FP64 coordinates (points outside the unit square: the clamped box, in FP64), the
+// powers in FP32, added by FP32 atomics.
 __global__ void p2m_kernel(int level, int p, const double* __restrict__ xy, const double* __restrict__ c, int64_t n,
                            float2* __restrict__ M)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int side = 1 << level;
-    const double x = xy[2 * i] * side, y = xy[2 * i + 1] * side;
-    int ix = (int)floor(x), iy = (int)floor(y);
-    ix = ix < 0 ? 0 : (ix > side - 1 ? side - 1 : ix);
-    iy = iy < 0 ? 0 : (iy > side - 1 ? side - 1 : iy);
-    const double wr = x - (ix + 0.5), wi = y - (iy + 0.5);
-    double pr = c[i], pi = 0.0;
+    const double x = xy[2 * i], y = xy[2 * i + 1];
+    int ix, iy;
+    float wr, wi;
+    long long X, Y;
+    if (grid_fixed31(x, level, X) && grid_fixed31(y, level, Y)) {
+        ix = (int)(X >> 31);
+        iy = (int)(Y >> 31);
+        wr = cell_offset31(X);
+        wi = cell_offset31(Y);
+    } else {
+        const double xs = x * side, ys = y * side;
+        ix = (int)floor(xs);
+        iy = (int)floor(ys);
+        ix = ix < 0 ? 0 : (ix > side - 1 ? side - 1 : ix);
+        iy = iy < 0 ? 0 : (iy > side - 1 ? side - 1 : iy);
+        wr = (float)(xs - (ix + 0.5));
+        wi = (float)(ys - (iy + 0.5));
+    }
+    float pr = (float)c[i], pi = 0.f;
     float2* mb = M + ((size_t)iy * side + ix) * p;
     for (int k = 0; k < p; ++k) {
-        atomicAdd(&mb[k].x, (float)pr);
-        atomicAdd(&mb[k].y, (float)pi);
-        const double t = pr * wr - pi * wi;
-        pi = pr * wi + pi * wr;
+        atomicAdd(&mb[k].x, pr);
+        atomicAdd(&mb[k].y, pi);
+        const float t = fmaf(pr, wr, -pi * wi);
+        pi = fmaf(pr, wi, pi * wr);
         pr = t;
     }
 }

@@ -177,6 +177,27 @@ def test_upward_sweep_on_device(fmm, orc):
         assert err < 2e-6, (lv, err)
 
 
+def test_p2m_points_on_boundaries_and_outside(fmm, orc):
+    """fmm_p2m with points on every cell boundary of the level, at 1.0 and just outside the
+    unit square (clamped to the edge boxes): the offsets read off the coordinate bits and
+    the FP64 fallback both agree with the oracle's P2M (Sec. 2.1 stage 2)."""
+    import torch
+
+    rng = np.random.default_rng(98)
+    L, p, side = 4, 12, 16
+    xy, c = workloads.uniform_particles(4000, rng)
+    k = np.arange(side + 1) / side
+    xy[:side + 1, 0] = k
+    xy[side + 1:2 * side + 2, 1] = k
+    xy[-4:] = [[1.0, 0.3], [1.01, 0.6], [-0.02, 0.2], [0.7, 1.03]]
+    M = torch.zeros((4 ** L, p), dtype=torch.complex64, device="cuda")
+    fmm.fmm_p2m(L, p, torch.from_numpy(xy).cuda(), torch.from_numpy(c).cuda(), M)
+    fmm.fmm_sync_status()
+    ref = orc.scale_me(orc.p2m_uniform(L, p, xy, c), L)
+    err = np.linalg.norm(_host(M) - ref) / np.linalg.norm(ref)
+    assert err < 2e-6, err
+
+
 @pytest.mark.slow
 def test_m2l_full_size_workload(fmm, orc):
     """2^22 points, uniform tree to level 8, p = 16, one launch per level (the benchmark's
