@@ -31,6 +31,29 @@ def _declared_functions():
     return names
 
 
+@pytest.mark.parametrize("compiler,std", [("gcc", "-std=c99"), ("g++", "-std=c++17")])
+def test_header_compiles_as_plain_c_and_cpp(tmp_path, compiler, std):
+    """include/fmmgb.h is a C ABI: it compiles on its own as strict C99 (pedantic, no
+    warnings) and as C++, and a caller can name every status, precision and flag."""
+    import shutil
+    import subprocess
+
+    if shutil.which(compiler) is None:
+        pytest.skip(f"{compiler} not installed")
+    src = tmp_path / "use_header.c"
+    src.write_text(
+        '#include "fmmgb.h"\n'
+        "int main(void) {\n"
+        "    fmm_host_stream_info_t hi; fmm_batch_info_t bi; fmm_level_info li;\n"
+        "    (void)hi; (void)bi; (void)li;\n"
+        "    return FMM_OK + FMM_EDEVICE + FMM_TC_TF32X3 + FMM_ACCUMULATE + FMM_CONJ + FMM_TREE_PERIODIC\n"
+        "           + FMM_BATCH_AUTOTUNE + FMM_HOST_CONTIGUOUS + FMM_P2P_SHARE_SM + FMM_MAX_LEVEL;\n"
+        "}\n")
+    lang = ["-x", "c++"] if compiler == "g++" else []
+    subprocess.check_call([compiler, std, "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only",
+                           "-I", os.path.join(ROOT, "include")] + lang + [str(src)])
+
+
 def test_every_declared_symbol_is_exported(fmm):
     lib = fmm.load()
     names = _declared_functions()
